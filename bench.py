@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark of the spectral block SHT -> filter -> ISHT on GB300.
+
+Workload: 721 x 1440 pole-inclusive equiangular grid with Clenshaw-Curtis
+weights, lmax = mmax = 720, one member x 72 channels (the 72 prognostic
+variables of FourCastNet 3) of synthetic fields with (l+1)^-3 angular power
+spectra, complex channel-mixing filter W[720][72][72].  One step is one
+pass of the whole path over the 72 fields through the C ABI call
+``sht_spectral_block``.  The metric is field-transforms/s (one field through
+SHT, filter and ISHT = one field-transform), with the roofline fraction of
+the dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+
+Multi-GPU runs (torchrun) are independent replicas: the path has no
+exchange step, so every rank transforms its own batch (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SHT+filter+ISHT field-transforms/s at 721×1440, lmax=720; roofline fraction"
+UNIT = "field-transforms/s"
+NLAT, NLON, GRID, LMAX, MMAX = 721, 1440, "equiangular_cc", 720, 720
+MEMBERS, CHANNELS = 1, 72
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_config(precision: str) -> dict:
+    return {
+        "workload": "SHT+filter+ISHT, 721x1440 equiangular (Clenshaw-Curtis), lmax=mmax=720, "
+                    "1 member x 72 channels, W[720][72][72] complex",
+        "nlat": NLAT, "nlon": NLON, "grid": GRID, "lmax": LMAX, "mmax": MMAX,
+        "members": MEMBERS, "channels": CHANNELS, "precision": precision,
+        "spectrum": "(l+1)^-3 angular power, seeded",
+        "l2": "inputs larger than L2: 299 MB of fields in and 299 MB out per step",
+        "parallelism": "replicas",
+    }
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch (mandatory I/O of each kernel; tables excluded)
+# ---------------------------------------------------------------------------
+
+def n_triangle(L, M):
+    return sum(L - m for m in range(M))
+
+
+def algorithmic_bytes(kernel: str, fields: int, members: int, cin: int, cout: int) -> float:
+    tri = n_triangle(LMAX, MMAX) * 8.0          # complex64 l >= m coefficients of one field
+    four = NLAT * MMAX * 8.0                      # complex64 Fourier rows of one field
+    grid = NLAT * NLON * 4.0                      # float32 field
+    if kernel == "r2c":
+        return fields * (grid + four)
+    if kernel == "c2r":
+        return fields * (four + grid)
+    if kernel in ("leg_fwd", "leg_inv"):
+        return fields * (four + tri)
+    if kernel == "filter":
+        return members * (cin + cout) * tri + LMAX * cout * cin * 8.0
+    return float("nan")
+
+
+def source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "r2c": ["paper_2507_12144_gb300/csrc/fft.cu"],
+    "c2r": ["paper_2507_12144_gb300/csrc/fft.cu"],
+    "leg_fwd": ["paper_2507_12144_gb300/csrc/legendre_f32.cu"],
+    "leg_inv": ["paper_2507_12144_gb300/csrc/legendre_f32.cu"],
+    "filter": ["paper_2507_12144_gb300/csrc/filter.cu"],
+}
+
+
+def measured_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = table.get(f"{kernel}/{precision}")
+    if not ent:
+        return None
+    if ent.get("source_hash") != source_hash(KERNEL_SOURCES.get(kernel, [])):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        self.file.close()
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas; max-over-ranks timing)
+# ---------------------------------------------------------------------------
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(val: float, world: int, device) -> float:
+    if world == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle samples (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------
+
+class OracleSampler:
+    """Times the FP64 oracle, as it stands, on a slab of the workload: `f`
+    fields (one per host thread) through the forward transform restricted to
+    latitude rows [0, R), the filter over the degrees holding the same share
+    R/nlat of the (l, m) coefficients with 72 input channels, and the inverse
+    on rows [0, R).  Each slab is R/nlat of a field-transform per field."""
+
+    def __init__(self, seed: int = 2):
+        import oracle
+        from paper_2507_12144_gb300 import inputs
+        self.oracle = oracle
+        oracle.build()
+        self.cores = oracle.num_threads()
+        self.f = min(self.cores, CHANNELS)
+        g = inputs.rng(seed)
+        self.x = g.standard_normal((self.f, NLAT, NLON)).astype(np.float32).astype(np.float64)
+        self.xh_in = inputs.spectral_coeffs(seed + 1, (1, CHANNELS), LMAX, MMAX)
+        self.W = inputs.filter_weights(seed + 2, LMAX, self.f, CHANNELS)
+        tri = np.cumsum([min(l + 1, MMAX) for l in range(LMAX)])
+        self.tri_cum = tri
+
+    def degrees_for(self, rows: int) -> int:
+        share = rows / NLAT * self.tri_cum[-1]
+        return int(min(LMAX, max(1, np.searchsorted(self.tri_cum, share) + 1)))
+
+    def step(self, rows: int):
+        o = self.oracle
+        o.sht_forward_rows(self.x, NLAT, NLON, GRID, LMAX, MMAX, 0, rows)
+        o.spectral_filter_degrees(self.xh_in, self.W, 0, self.degrees_for(rows))
+        o.sht_inverse_rows(self.xh_in[0, :self.f], NLAT, NLON, GRID, LMAX, MMAX, 0, rows)
+
+    def fields_per_step(self, rows: int) -> float:
+        return self.f * rows / NLAT
+
+    def calibrate(self, target_s: float) -> int:
+        """Rows per step so that one step takes about target_s seconds."""
+        r = 4
+        t0 = time.perf_counter()
+        self.step(r)
+        dt = max(time.perf_counter() - t0, 1e-3)
+        return int(min(NLAT, max(1, round(r * target_s / dt))))
+
+    def describe(self, rows: int) -> str:
+        return (f"{self.f} fields x latitude rows [0,{rows}) of 721 for the forward and inverse transforms, "
+                f"filter (72 input channels) on degrees [0,{self.degrees_for(rows)}); "
+                f"counts {rows}/721 of a field-transform per field")
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        barrier(world)
+        return 0
+    s = OracleSampler()
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)
+    rows = s.calibrate(min(budget, 20.0))
+    for _ in range(args.warmup):
+        s.step(rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(rows)
+    dt = time.perf_counter() - t0
+    value = args.steps * s.fields_per_step(rows) / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config("fp64 oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+                         "sample": s.describe(rows)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    barrier(world)
+    return 0
+
+
+def cpu_baseline_line(target_s: float = 15.0) -> dict:
+    s = OracleSampler()
+    rows = s.calibrate(target_s)
+    t0 = time.perf_counter()
+    s.step(rows)
+    dt = time.perf_counter() - t0
+    return {"value": s.fields_per_step(rows) / dt, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+            "sample": s.describe(rows) + f"; one slab, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+
+    import paper_2507_12144_gb300 as shtgb
+    from paper_2507_12144_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fields = MEMBERS * CHANNELS
+    plan = shtgb.Plan(NLAT, NLON, GRID, LMAX, MMAX, precision=args.precision, device=dev, max_batch=fields)
+
+    # synthetic inputs: seeded (l+1)^-3 coefficients synthesised on the GPU
+    c = inputs.spectral_coeffs(2 + rank, (fields,), LMAX, MMAX)
+    x = shtgb.sht_inverse(plan, torch.from_numpy(c.astype(np.complex64)).to(dev))
+    x = x.reshape(MEMBERS, CHANNELS, NLAT, NLON).contiguous()
+    W = torch.from_numpy(inputs.filter_weights(3, LMAX, CHANNELS, CHANNELS).astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    lib = shtgb._abi.lib()
+
+    def step(xin, yout):
+        shtgb._abi.check(lib.sht_spectral_block(plan.handle, shtgb._ptr(xin), shtgb._ptr(W), shtgb._ptr(yout),
+                                                MEMBERS, CHANNELS, CHANNELS, shtgb._stream(xin)))
+
+    for _ in range(args.warmup):
+        step(x, y)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    plan.profile_begin(capacity=16 * (args.steps + 1))
+    plan.profile_collect()
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)  # let the sampler start before the timed region
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(x, y)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    ms_total = ev0.elapsed_time(ev1)
+    prof = plan.profile_collect()
+    plan.profile_end()
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+    value = world * fields / (ms_step * 1e-3)
+
+    # dominant kernel and its roofline
+    kernels = {k: v for k, v in prof.items() if not k.startswith("_") and v[0] > 0}
+    launches = sum(v[0] for v in kernels.values())
+    dom = max(kernels, key=lambda k: kernels[k][1])
+    dom_launches, dom_ms = kernels[dom]
+    per_launch_s = dom_ms / dom_launches * 1e-3
+    alg = algorithmic_bytes(dom, fields, MEMBERS, CHANNELS, CHANNELS)
+    achieved = alg / per_launch_s / 1e9
+    peak, peak_kind = load_peaks()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "traffic": measured_traffic(dom, args.precision),
+                "algorithmic_bytes_per_launch": alg,
+                "kernel_ms_per_launch": per_launch_s * 1e3,
+                "share_of_step": dom_ms / ms_total if world == 1 else None}
+    breakdown = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
+                     "share": v[1] / (ms_total if world == 1 else max(ms_total, 1e-9))}
+                 for k, v in kernels.items()}
+
+    # end to end through the public API with pinned host buffers
+    e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    xh = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    xh.copy_(x)
+    yh = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        xd = xh.to(dev, non_blocking=True)
+        yd = shtgb.sht_spectral_block(plan, xd, W)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = world * fields * e2e_steps / e2e_s
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+            "data": "synthetic: seeded (l+1)^-3 spectra synthesised on the GPU, random-init filter",
+            "config": workload_config(args.precision),
+            "roofline": roofline,
+            "kernels": breakdown,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 4),
+                    "d2h_bytes_per_step": int(y.numel() * 4), "steps": e2e_steps},
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_line(args.cpu_seconds)
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line))
+        sys.stdout.flush()
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="wall-clock budget of the reference arm's warm-up + timed steps")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

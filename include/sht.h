@@ -1,0 +1,238 @@
+/*
+ * shtgb: spherical harmonic transforms and per-degree spectral filtering on
+ * one NVIDIA GB300 GPU (sm_103a).  C ABI.
+ *
+ * The operation is the global convolution inside FourCastNet 3's spherical
+ * neural-operator blocks (arXiv 2507.12144):
+ *
+ *   forward SHT   xhat_lm = int u conj(Y_lm) dmu                       Eq. (sht)
+ *                 = sum_k w_k (2 pi / nlon) Phat_l^m(x_k) sum_j u_kj e^{-i m phi_j}
+ *                 (longitude FFT, then a Legendre contraction whose
+ *                 quadrature weights are folded in: Sec. B.3, Sec. F.2.2
+ *                 Algorithm 1)
+ *   filter        yhat[b][o][l][m] = sum_i W[l][o][i] xhat[b][i][l][m]
+ *                 (the convolution theorem Eq. (s2_spectral_conv), with the
+ *                 per-degree scalar generalised to complex channel mixing)
+ *   inverse SHT   u_kj = sum_{m} c_m Re(G_k(m) e^{i m phi_j}),
+ *                 G_k(m) = sum_l Phat_l^m(x_k) yhat_lm                  Eq. (isht)
+ *                 c_0 = 1, c_{nlon/2} = 1 (Nyquist), c_m = 2 otherwise.
+ *
+ * Y_l^m(theta, phi) = Phat_l^m(cos theta) e^{i m phi} with the orthonormal
+ * normalisation and one factor (-1)^m (Eq. spherical_harmonics).
+ *
+ * Conventions
+ *   - lmax and mmax are COUNTS: 0 <= l < lmax, 0 <= m < mmax, and
+ *     1 <= mmax <= lmax, mmax <= nlon/2 + 1.  Gaussian grids need
+ *     lmax <= nlat.
+ *   - Latitude row k = 0 is the northernmost.  Equiangular grids include
+ *     both poles, theta_k = pi k / (nlat - 1).
+ *   - Spatial arrays: float32 [B][nlat][nlon], row-major, contiguous.
+ *   - Spectral arrays: complex64 (interleaved re, im float32) in the dense
+ *     l-major rectangle [B][lmax][mmax] (the B x C x lmax x mmax layout of
+ *     Algorithm 1).  Outputs have exact zeros at l < m; inputs are read only
+ *     at l >= m.  The forward transform writes Im(m = 0) = 0 exactly, and
+ *     the inverse ignores Im of m = 0 and of the Nyquist column.
+ *   - Filter weights: complex64 W[lmax][Cout][Cin].
+ *   - Adjoints are taken under the real inner product <a, b> = Re sum
+ *     conj(a) b, which is PyTorch's convention for complex gradients.
+ *
+ * Memory and streams
+ *   - Every data pointer is a DEVICE pointer on the plan's device, owned by
+ *     the caller, 16-byte aligned and contiguous.  The plan owns its tables
+ *     and workspaces, all allocated in sht_plan().
+ *   - Execute calls allocate nothing and do not synchronise; they enqueue
+ *     work on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream).  A plan's workspace is shared by its execute calls,
+ *     so one plan must not be used from two streams at once.
+ *   - Batches larger than the plan's max_batch are processed in chunks of
+ *     max_batch fields inside one call.
+ *
+ * Errors
+ *   - Argument errors are returned before anything is enqueued.
+ *   - A CUDA launch error is returned as SHT_ERR_CUDA; asynchronous faults
+ *     surface on a later call.  Nothing aborts or prints.
+ *   - sht_last_error_message() gives a one-line description of the most
+ *     recent failure on the calling thread.
+ */
+#ifndef SHTGB_SHT_H_
+#define SHTGB_SHT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan_s *sht_plan_t;
+
+typedef enum {
+  SHT_GRID_GAUSS = 0,             /* Gauss-Legendre latitudes (Sec. B.1)   */
+  SHT_GRID_EQUIANGULAR_CC = 1,    /* pole-inclusive equiangular,
+                                     Clenshaw-Curtis weights (footnote to
+                                     Eq. latlon_quad_weights)              */
+  SHT_GRID_EQUIANGULAR_TRAPZ = 2  /* pole-inclusive equiangular, weights
+                                     sin(theta) dtheta (Eq.
+                                     latlon_quad_weights)                  */
+} sht_grid_t;
+
+typedef enum {
+  SHT_OK = 0,
+  SHT_ERR_INVALID_ARG = 1,
+  SHT_ERR_UNSUPPORTED = 2,
+  SHT_ERR_OOM = 3,
+  SHT_ERR_CUDA = 4,
+  SHT_ERR_TIMEOUT = 5,
+  SHT_ERR_INTERNAL = 6
+} sht_status_t;
+
+/* Arithmetic of the Legendre contractions (the dominant cost, Sec. B.3).
+ * FP32: FP32 table and data, FP32 accumulation (CUDA cores).
+ * BF16: table and data rounded to bf16, FP32 accumulation (tensor cores).
+ * SPLIT_BF16: a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi);
+ *   products hi*hi + hi*lo + lo*hi on the tensor cores, FP32 accumulation.
+ * Training in the paper uses bf16 mixed precision (Sec. E.3). */
+typedef enum {
+  SHT_PREC_FP32 = 0,
+  SHT_PREC_BF16 = 1,
+  SHT_PREC_SPLIT_BF16 = 2
+} sht_precision_t;
+
+typedef struct {
+  int precision;      /* sht_precision_t, default SHT_PREC_FP32            */
+  int device;         /* CUDA device ordinal, default: the current device  */
+  int64_t max_batch;  /* fields per internal chunk, default 256            */
+  int reserved[8];    /* must be zero                                      */
+} sht_plan_opts;
+
+/* Fill opts with the defaults (precision FP32, current device,
+ * max_batch 256). */
+void sht_plan_opts_default(sht_plan_opts *opts);
+
+/* Create a plan for an (nlat x nlon) grid and lmax x mmax coefficients.
+ * Computes the latitude nodes and weights (FP64, host), generates the
+ * normalised Legendre table Phat_l^m(x_k) in FP64 on the GPU and stores it
+ * in the precision's layout, and allocates the workspace for max_batch
+ * fields.  Blocks until the tables are built.  On success *out owns all
+ * device memory; release it with sht_plan_destroy.
+ * Errors: INVALID_ARG (sizes outside the conventions above, nlat < 2 for an
+ * equiangular grid, NULL out); UNSUPPORTED (nlon with a prime factor other
+ * than 2, 3, 5, or nlon > 8192); OOM; CUDA. */
+sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid,
+                      int lmax, int mmax, const sht_plan_opts *opts);
+
+sht_status_t sht_plan_destroy(sht_plan_t plan);
+
+/* Sizes and state of a plan.  Any output pointer may be NULL. */
+sht_status_t sht_plan_info(sht_plan_t plan, int *nlat, int *nlon, int *grid,
+                           int *lmax, int *mmax, int *precision,
+                           int64_t *max_batch, int64_t *table_bytes,
+                           int64_t *workspace_bytes);
+
+/* Copy the plan's latitude nodes x_k = cos(theta_k) and weights w_k (FP64,
+ * host arrays of nlat entries; the 2-D weight is w_k * 2 pi / nlon).
+ * Either pointer may be NULL. */
+sht_status_t sht_plan_grid(sht_plan_t plan, double *x, double *w);
+
+/* Forward SHT, Eq. (sht).  x: float32 [B][nlat][nlon] -> xhat: complex64
+ * [B][lmax][mmax].  B >= 0 (B = 0 is a no-op). */
+sht_status_t sht_forward(sht_plan_t plan, const float *x, void *xhat,
+                         int64_t B, void *stream);
+
+/* Inverse SHT, Eq. (isht).  xhat: complex64 [B][lmax][mmax] -> x: float32
+ * [B][nlat][nlon]. */
+sht_status_t sht_inverse(sht_plan_t plan, const void *xhat, float *x,
+                         int64_t B, void *stream);
+
+/* Adjoint of sht_forward: gxhat [B][lmax][mmax] -> gx [B][nlat][nlon],
+ *   gx_kj = w_k (2 pi / nlon) Re sum_m e^{i m phi_j} sum_l Phat_l^m(x_k) gy_lm
+ * (every m with weight 1; this is not the inverse transform). */
+sht_status_t sht_forward_adjoint(sht_plan_t plan, const void *gxhat,
+                                 float *gx, int64_t B, void *stream);
+
+/* Adjoint of sht_inverse: gx [B][nlat][nlon] -> gxhat [B][lmax][mmax],
+ *   gy_lm = sum_k Phat_l^m(x_k) c_m sum_j gx_kj e^{-i m phi_j}. */
+sht_status_t sht_inverse_adjoint(sht_plan_t plan, const float *gx,
+                                 void *gxhat, int64_t B, void *stream);
+
+/* Spectral filter (Eq. s2_spectral_conv with channel mixing).
+ * xhat: complex64 [Bm][Cin][lmax][mmax], W: complex64 [lmax][Cout][Cin],
+ * yhat: complex64 [Bm][Cout][lmax][mmax] (zero at l < m).  FP32 arithmetic. */
+sht_status_t spectral_filter(sht_plan_t plan, const void *xhat, const void *W,
+                             void *yhat, int64_t Bm, int Cin, int Cout,
+                             void *stream);
+
+/* Adjoint of the filter in both arguments:
+ *   gx[b][i][l][m] = sum_o conj(W[l][o][i]) gy[b][o][l][m]
+ *   gW[l][o][i]    = sum_{b, m <= l} gy[b][o][l][m] conj(xhat[b][i][l][m])
+ * gx and gW may each be NULL (not computed); gW is overwritten. */
+sht_status_t spectral_filter_adjoint(sht_plan_t plan, const void *gy,
+                                     const void *W, const void *xhat,
+                                     void *gx, void *gW, int64_t Bm, int Cin,
+                                     int Cout, void *stream);
+
+/* One spectral block: y = ISHT(filter(SHT(x), W)) with the intermediates
+ * kept in the plan's workspace.  x: float32 [Bm][Cin][nlat][nlon],
+ * W: complex64 [lmax][Cout][Cin], y: float32 [Bm][Cout][nlat][nlon]. */
+sht_status_t sht_spectral_block(sht_plan_t plan, const float *x,
+                                const void *W, float *y, int64_t Bm, int Cin,
+                                int Cout, void *stream);
+
+/* Fused filter + inverse SHT: y = ISHT(filter(xhat, W)).  xhat: complex64
+ * [Bm][Cin][lmax][mmax], y: float32 [Bm][Cout][nlat][nlon]. */
+sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,
+                                     const void *W, float *y, int64_t Bm,
+                                     int Cin, int Cout, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Per-kernel timing.  While profiling is on, every kernel a plan's execute
+ * calls launch is bracketed by two CUDA events recorded on the launch
+ * stream (up to `capacity` launches; later launches run unrecorded and are
+ * counted as dropped).  sht_profile_collect waits for the recorded events,
+ * adds each launch's duration to its kernel's total and resets the record.
+ * No paper counterpart: this is the library's tracing facility.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  SHT_KERNEL_R2C = 0,        /* longitude analysis (FFT), parity fold     */
+  SHT_KERNEL_LEG_FWD = 1,    /* forward Legendre contraction              */
+  SHT_KERNEL_ZERO = 2,       /* zero fill of l < m                        */
+  SHT_KERNEL_FILTER = 3,     /* spectral filter or its input adjoint      */
+  SHT_KERNEL_FILTER_DW = 4,  /* weight adjoint of the filter              */
+  SHT_KERNEL_LEG_INV = 5,    /* inverse Legendre contraction              */
+  SHT_KERNEL_C2R = 6,        /* longitude synthesis (inverse FFT)         */
+  SHT_KERNEL_COUNT = 7
+} sht_kernel_t;
+
+/* Start recording (capacity >= 1 launches); creates the events on the
+ * plan's device.  Calling it again while on resets the record. */
+sht_status_t sht_profile_begin(sht_plan_t plan, int capacity);
+
+/* Wait for the recorded launches and report, per sht_kernel_t id, the
+ * launch count and the summed device milliseconds (arrays of
+ * SHT_KERNEL_COUNT entries, either may be NULL); *dropped (may be NULL)
+ * receives the launches beyond capacity.  Recording continues. */
+sht_status_t sht_profile_collect(sht_plan_t plan, int64_t *launches,
+                                 double *ms, int64_t *dropped);
+
+/* Stop recording and release the events. */
+sht_status_t sht_profile_end(sht_plan_t plan);
+
+/* Name of a kernel id ("r2c", "leg_fwd", ...), or "?" when out of range. */
+const char *sht_kernel_name(int kernel);
+
+const char *sht_status_string(sht_status_t status);
+const char *sht_last_error_message(void);
+
+/* Library version, e.g. "0.1.0". */
+const char *sht_version(void);
+
+/* Test hook for failure handling: the n-th device allocation made by later
+ * sht_plan calls fails as if the device were out of memory (n = 0: the next
+ * one; n < 0: off).  The plan call then returns SHT_ERR_OOM and frees what
+ * it had allocated.  Not thread-safe; for tests only. */
+void sht_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHTGB_SHT_H_ */

@@ -79,6 +79,9 @@ def _load():
             "orc_sht_forward_bruteforce": ([i, i, i, i, i, p, p], i),
             "orc_spectral_filter": ([i, i, i, i, i, p, p, p], i),
             "orc_dft": ([i, i, p, p], i),
+            "orc_sht_forward_rows": ([i, i, i, i, i, i, p, p, i, i], i),
+            "orc_sht_inverse_rows": ([i, i, i, i, i, i, p, p, i, i], i),
+            "orc_spectral_filter_degrees": ([i, i, i, i, i, p, p, p, i, i], i),
             "orc_spectral_filter_adjoint": ([i, i, i, i, i, p, p, p, p, p], i),
         }
         for name, (args, res) in sig.items():
@@ -216,6 +219,40 @@ def sht_forward_bruteforce(x, nlat, nlon, grid, L, M):
     out = np.zeros((L, M), dtype=np.complex128)
     _check(_load().orc_sht_forward_bruteforce(nlat, nlon, _grid_id(grid), L, M,
                                               _ptr(x), _ptr(out)), "bruteforce")
+    return out
+
+
+def sht_forward_rows(x, nlat, nlon, grid, L, M, k0, k1):
+    """Forward sum over latitude rows k0 <= k < k1 only (timing samples)."""
+    x = _f64(x)
+    lead = x.shape[:-2]
+    B = int(np.prod(lead)) if lead else 1
+    out = np.zeros(lead + (L, M), dtype=np.complex128)
+    _check(_load().orc_sht_forward_rows(nlat, nlon, _grid_id(grid), L, M, B, _ptr(x), _ptr(out),
+                                        int(k0), int(k1)), "forward_rows")
+    return out
+
+
+def sht_inverse_rows(y, nlat, nlon, grid, L, M, k0, k1):
+    """Inverse evaluated on latitude rows k0 <= k < k1 only (timing samples)."""
+    y = _c128(y)
+    lead = y.shape[:-2]
+    B = int(np.prod(lead)) if lead else 1
+    out = np.zeros(lead + (nlat, nlon), dtype=np.float64)
+    _check(_load().orc_sht_inverse_rows(nlat, nlon, _grid_id(grid), L, M, B, _ptr(y), _ptr(out),
+                                        int(k0), int(k1)), "inverse_rows")
+    return out
+
+
+def spectral_filter_degrees(xhat, W, l0, l1):
+    """The filter for degrees l0 <= l < l1 only (timing samples)."""
+    xhat = _c128(xhat)
+    W = _c128(W)
+    Bm, Cin, L, M = xhat.shape
+    Cout = W.shape[1]
+    out = np.zeros((Bm, Cout, L, M), dtype=np.complex128)
+    _check(_load().orc_spectral_filter_degrees(L, M, Bm, Cin, Cout, _ptr(xhat), _ptr(W), _ptr(out),
+                                               int(l0), int(l1)), "filter_degrees")
     return out
 
 

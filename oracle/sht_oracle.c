@@ -356,8 +356,9 @@ static int check_sizes(int nlat, int nlon, int L, int M) {
  * forward: q_k = w_k 2 pi / nlon, c_m = 1;
  * inverse adjoint: q_k = 1, c_m = mode weight of the real inverse. */
 static int analysis(int nlat, int nlon, int grid, int L, int M, int B,
-                    const double *x, double *xhat, int adjoint) {
+                    const double *x, double *xhat, int adjoint, int k0, int k1) {
   if (check_sizes(nlat, nlon, L, M)) return -1;
+  if (k0 < 0 || k1 > nlat || k0 > k1) return -1;
   orc_geom g;
   int rc = geom_init(&g, nlat, nlon, grid, L, M);
   if (rc) {
@@ -380,7 +381,7 @@ static int analysis(int nlat, int nlon, int grid, int L, int M, int B,
       if (!P || !F) continue;
       double *out = xhat + (size_t)b * plm * 2;
       memset(out, 0, sizeof(double) * plm * 2);
-      for (int k = 0; k < nlat; k++) {
+      for (int k = k0; k < k1; k++) {
         dft_forward(nlon, M, g.cs, x + ((size_t)b * nlat + k) * nlon, F);
         legendre_with(L, M, g.x[k], g.s[k], g.a, g.b, P);
         for (int m = 0; m < M; m++) {
@@ -407,7 +408,15 @@ static int analysis(int nlat, int nlon, int grid, int L, int M, int B,
  * x: [B][nlat][nlon], xhat: [B][L][M] complex (interleaved). */
 int orc_sht_forward(int nlat, int nlon, int grid, int L, int M, int B,
                     const double *x, double *xhat) {
-  return analysis(nlat, nlon, grid, L, M, B, x, xhat, 0);
+  return analysis(nlat, nlon, grid, L, M, B, x, xhat, 0, 0, nlat);
+}
+
+/* The forward sum restricted to latitude rows k0 <= k < k1 (a partial
+ * quadrature; the full transform is the range [0, nlat)).  Used to time
+ * bounded samples of the oracle. */
+int orc_sht_forward_rows(int nlat, int nlon, int grid, int L, int M, int B,
+                         const double *x, double *xhat, int k0, int k1) {
+  return analysis(nlat, nlon, grid, L, M, B, x, xhat, 0, k0, k1);
 }
 
 /* Adjoint of the inverse SHT:
@@ -415,7 +424,7 @@ int orc_sht_forward(int nlat, int nlon, int grid, int L, int M, int B,
  *   gy_lm     = sum_k Phat_l^m(x_k) Gbar_k(m)   (l >= m; zero for l < m). */
 int orc_sht_inverse_adjoint(int nlat, int nlon, int grid, int L, int M, int B,
                             const double *gx, double *gy) {
-  return analysis(nlat, nlon, grid, L, M, B, gx, gy, 1);
+  return analysis(nlat, nlon, grid, L, M, B, gx, gy, 1, 0, nlat);
 }
 
 /* Shared body of the inverse SHT and of the forward-SHT adjoint (synthesis):
@@ -424,8 +433,9 @@ int orc_sht_inverse_adjoint(int nlat, int nlon, int grid, int L, int M, int B,
  * inverse: r_k = 1, c_m = mode weight; forward adjoint: r_k = w_k 2 pi / nlon,
  * c_m = 1. */
 static int synthesis(int nlat, int nlon, int grid, int L, int M, int B,
-                     const double *yhat, double *u, int adjoint) {
+                     const double *yhat, double *u, int adjoint, int k0, int k1) {
   if (check_sizes(nlat, nlon, L, M)) return -1;
+  if (k0 < 0 || k1 > nlat || k0 > k1) return -1;
   orc_geom g;
   int rc = geom_init(&g, nlat, nlon, grid, L, M);
   if (rc) {
@@ -449,7 +459,7 @@ static int synthesis(int nlat, int nlon, int grid, int L, int M, int B,
     for (int b = 0; b < B; b++) {
       if (!P || !G) continue;
       const double *in = yhat + (size_t)b * plm * 2;
-      for (int k = 0; k < nlat; k++) {
+      for (int k = k0; k < k1; k++) {
         legendre_with(L, M, g.x[k], g.s[k], g.a, g.b, P);
         for (int m = 0; m < M; m++) {
           double re = 0.0, im = 0.0;
@@ -483,7 +493,14 @@ static int synthesis(int nlat, int nlon, int grid, int L, int M, int B,
  * Nyquist mode) does not enter. */
 int orc_sht_inverse(int nlat, int nlon, int grid, int L, int M, int B,
                     const double *yhat, double *u) {
-  return synthesis(nlat, nlon, grid, L, M, B, yhat, u, 0);
+  return synthesis(nlat, nlon, grid, L, M, B, yhat, u, 0, 0, nlat);
+}
+
+/* The inverse evaluated only on latitude rows k0 <= k < k1 (other rows of
+ * u are left untouched). */
+int orc_sht_inverse_rows(int nlat, int nlon, int grid, int L, int M, int B,
+                         const double *yhat, double *u, int k0, int k1) {
+  return synthesis(nlat, nlon, grid, L, M, B, yhat, u, 0, k0, k1);
 }
 
 /* Adjoint of the forward SHT under <a, b> = Re sum conj(a) b:
@@ -491,7 +508,7 @@ int orc_sht_inverse(int nlat, int nlon, int grid, int L, int M, int B,
  *   G_k(m) = sum_l Phat_l^m(x_k) gy_lm   (every m with weight 1). */
 int orc_sht_forward_adjoint(int nlat, int nlon, int grid, int L, int M, int B,
                             const double *gy, double *gx) {
-  return synthesis(nlat, nlon, grid, L, M, B, gy, gx, 1);
+  return synthesis(nlat, nlon, grid, L, M, B, gy, gx, 1, 0, nlat);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -605,15 +622,17 @@ int orc_sht_forward_bruteforce(int nlat, int nlon, int grid, int L, int M,
 
 /* yhat[b][o][l][m] = sum_i W[l][o][i] xhat[b][i][l][m] for m <= l (zero
  * otherwise).  Complex arrays interleaved; W: [L][Cout][Cin]. */
-int orc_spectral_filter(int L, int M, int Bm, int Cin, int Cout,
-                        const double *xhat, const double *W, double *yhat) {
+static int filter_range(int L, int M, int Bm, int Cin, int Cout,
+                        const double *xhat, const double *W, double *yhat,
+                        int l0, int l1) {
   if (L < 1 || M < 1 || Bm < 0 || Cin < 1 || Cout < 1) return -1;
+  if (l0 < 0 || l1 > L || l0 > l1) return -1;
   size_t plm = (size_t)L * M;
 #pragma omp parallel for collapse(2) schedule(static)
   for (int b = 0; b < Bm; b++)
     for (int o = 0; o < Cout; o++) {
       double *out = yhat + ((size_t)b * Cout + o) * plm * 2;
-      for (int l = 0; l < L; l++)
+      for (int l = l0; l < l1; l++)
         for (int m = 0; m < M; m++) {
           double re = 0.0, im = 0.0;
           if (m <= l) {
@@ -630,6 +649,19 @@ int orc_spectral_filter(int L, int M, int Bm, int Cin, int Cout,
         }
     }
   return 0;
+}
+
+int orc_spectral_filter(int L, int M, int Bm, int Cin, int Cout,
+                        const double *xhat, const double *W, double *yhat) {
+  return filter_range(L, M, Bm, Cin, Cout, xhat, W, yhat, 0, L);
+}
+
+/* The filter evaluated only for degrees l0 <= l < l1 (other rows of yhat
+ * are left untouched). */
+int orc_spectral_filter_degrees(int L, int M, int Bm, int Cin, int Cout,
+                                const double *xhat, const double *W,
+                                double *yhat, int l0, int l1) {
+  return filter_range(L, M, Bm, Cin, Cout, xhat, W, yhat, l0, l1);
 }
 
 /* Adjoint of the filter in both arguments:

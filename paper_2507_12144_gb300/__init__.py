@@ -1,0 +1,285 @@
+"""shtgb: GB300-native spherical harmonic transforms and spectral filtering.
+
+The global operation of FourCastNet 3's spherical neural-operator blocks
+(arXiv 2507.12144, Sec. B.3 and Sec. F.2.2): forward SHT (longitude FFT +
+quadrature-weighted Legendre contraction), a per-degree complex
+channel-mixing filter (Eq. s2_spectral_conv generalised), and the inverse
+SHT, with their adjoints.
+
+Every step runs in the hand-written CUDA kernels of ``libshtgb.so`` behind
+the C ABI of ``include/sht.h``.  This module only marshals arguments:
+PyTorch supplies device memory and the current stream.  There is no CPU
+path; without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi
+from ._abi import ShtError
+
+__all__ = ["Plan", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
+           "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
+           "SpectralBlock", "spectral_block", "ShtError"]
+
+
+def _stream(t: torch.Tensor):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t: torch.Tensor, dtype, name: str, device) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the plan on {device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+class Plan:
+    """An SHT plan: grid, Legendre tables and workspace on one GPU.
+
+    ``grid`` is "gauss", "equiangular_cc" or "equiangular_trapz"; ``lmax``
+    and ``mmax`` are counts (l < lmax, m < mmax); ``precision`` is "fp32",
+    "bf16" or "split_bf16" for the Legendre contractions.
+    """
+
+    def __init__(self, nlat: int, nlon: int, grid: str = "gauss", lmax: int | None = None,
+                 mmax: int | None = None, precision: str = "fp32", device=None, max_batch: int = 256):
+        if lmax is None:
+            lmax = nlat if grid == "gauss" else nlat - 1
+        if mmax is None:
+            mmax = min(lmax, nlon // 2 + 1)
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("plans live on a CUDA device")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        opts = _abi.sht_plan_opts()
+        _abi.lib().sht_plan_opts_default(ctypes.byref(opts))
+        opts.precision = _abi.PRECISIONS[precision]
+        opts.device = dev.index
+        opts.max_batch = int(max_batch)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _abi.check(_abi.lib().sht_plan(ctypes.byref(h), int(nlat), int(nlon), _abi.GRIDS[grid], int(lmax),
+                                           int(mmax), ctypes.byref(opts)))
+        self._h = h
+        self.nlat, self.nlon, self.grid = int(nlat), int(nlon), grid
+        self.lmax, self.mmax, self.precision = int(lmax), int(mmax), precision
+        self.device = dev
+        self.max_batch = int(max_batch)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan has been destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        vals = [ctypes.c_int() for _ in range(6)] + [ctypes.c_int64() for _ in range(3)]
+        _abi.check(_abi.lib().sht_plan_info(self.handle, *[ctypes.byref(v) for v in vals]))
+        keys = ["nlat", "nlon", "grid", "lmax", "mmax", "precision", "max_batch", "table_bytes", "workspace_bytes"]
+        return {k: v.value for k, v in zip(keys, vals)}
+
+    def nodes_weights(self):
+        """(x = cos theta, w) as float64 CPU tensors of length nlat."""
+        import numpy as np
+        x = np.zeros(self.nlat)
+        w = np.zeros(self.nlat)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _abi.check(_abi.lib().sht_plan_grid(self.handle, x.ctypes.data_as(dp), w.ctypes.data_as(dp)))
+        return x, w
+
+    # -- per-kernel timing (CUDA events on the launch stream) ----------------
+    def profile_begin(self, capacity: int = 65536) -> None:
+        _abi.check(_abi.lib().sht_profile_begin(self.handle, int(capacity)))
+
+    def profile_collect(self) -> dict:
+        """{kernel name: (launches, total ms)} since the last collect."""
+        n = _abi.KERNEL_COUNT
+        launches = (ctypes.c_int64 * n)()
+        ms = (ctypes.c_double * n)()
+        dropped = ctypes.c_int64()
+        _abi.check(_abi.lib().sht_profile_collect(self.handle, launches, ms, ctypes.byref(dropped)))
+        out = {_abi.lib().sht_kernel_name(k).decode(): (int(launches[k]), float(ms[k])) for k in range(n)}
+        out["_dropped"] = (int(dropped.value), 0.0)
+        return out
+
+    def profile_end(self) -> None:
+        _abi.check(_abi.lib().sht_profile_end(self.handle))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            h, self._h = self._h, None
+            _abi.check(_abi.lib().sht_plan_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __repr__(self):
+        return (f"Plan(nlat={self.nlat}, nlon={self.nlon}, grid={self.grid!r}, lmax={self.lmax}, "
+                f"mmax={self.mmax}, precision={self.precision!r}, device={self.device})")
+
+
+def sht_plan(nlat, nlon, grid="gauss", lmax=None, mmax=None, **kw) -> Plan:
+    return Plan(nlat, nlon, grid, lmax, mmax, **kw)
+
+
+# ---------------------------------------------------------------------------
+# raw (non-differentiable) calls
+# ---------------------------------------------------------------------------
+
+def _spatial_in(plan: Plan, x: torch.Tensor, name="x"):
+    x = _need(x, torch.float32, name, plan.device)
+    if x.dim() < 2 or x.shape[-2:] != (plan.nlat, plan.nlon):
+        raise ValueError(f"{name} must end in ({plan.nlat}, {plan.nlon}), got {tuple(x.shape)}")
+    lead = tuple(x.shape[:-2])
+    return x, lead, int(torch.tensor(lead).prod().item()) if lead else 1
+
+
+def _spectral_in(plan: Plan, y: torch.Tensor, name="xhat"):
+    y = _need(y, torch.complex64, name, plan.device)
+    if y.dim() < 2 or y.shape[-2:] != (plan.lmax, plan.mmax):
+        raise ValueError(f"{name} must end in ({plan.lmax}, {plan.mmax}), got {tuple(y.shape)}")
+    lead = tuple(y.shape[:-2])
+    return y, lead, int(torch.tensor(lead).prod().item()) if lead else 1
+
+
+def sht_forward(plan: Plan, x: torch.Tensor) -> torch.Tensor:
+    """float32 [..., nlat, nlon] -> complex64 [..., lmax, mmax]."""
+    x, lead, B = _spatial_in(plan, x)
+    out = torch.empty(lead + (plan.lmax, plan.mmax), dtype=torch.complex64, device=x.device)
+    _abi.check(_abi.lib().sht_forward(plan.handle, _ptr(x), _ptr(out), B, _stream(x)))
+    return out
+
+
+def sht_inverse(plan: Plan, xhat: torch.Tensor) -> torch.Tensor:
+    """complex64 [..., lmax, mmax] -> float32 [..., nlat, nlon]."""
+    y, lead, B = _spectral_in(plan, xhat)
+    out = torch.empty(lead + (plan.nlat, plan.nlon), dtype=torch.float32, device=y.device)
+    _abi.check(_abi.lib().sht_inverse(plan.handle, _ptr(y), _ptr(out), B, _stream(y)))
+    return out
+
+
+def sht_forward_adjoint(plan: Plan, gxhat: torch.Tensor) -> torch.Tensor:
+    y, lead, B = _spectral_in(plan, gxhat, "gxhat")
+    out = torch.empty(lead + (plan.nlat, plan.nlon), dtype=torch.float32, device=y.device)
+    _abi.check(_abi.lib().sht_forward_adjoint(plan.handle, _ptr(y), _ptr(out), B, _stream(y)))
+    return out
+
+
+def sht_inverse_adjoint(plan: Plan, gx: torch.Tensor) -> torch.Tensor:
+    x, lead, B = _spatial_in(plan, gx, "gx")
+    out = torch.empty(lead + (plan.lmax, plan.mmax), dtype=torch.complex64, device=x.device)
+    _abi.check(_abi.lib().sht_inverse_adjoint(plan.handle, _ptr(x), _ptr(out), B, _stream(x)))
+    return out
+
+
+def _filter_shapes(plan: Plan, xhat: torch.Tensor, W: torch.Tensor):
+    if xhat.dim() != 4:
+        raise ValueError("xhat must be [Bm, Cin, lmax, mmax]")
+    Bm, Cin = xhat.shape[:2]
+    if W.dim() != 3 or W.shape[0] != plan.lmax or W.shape[2] != Cin:
+        raise ValueError(f"W must be [lmax={plan.lmax}, Cout, Cin={Cin}], got {tuple(W.shape)}")
+    return int(Bm), int(Cin), int(W.shape[1])
+
+
+def spectral_filter(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
+    """yhat[b, o, l, m] = sum_i W[l, o, i] xhat[b, i, l, m] (zero for m > l)."""
+    xhat, _, _ = _spectral_in(plan, xhat)
+    W = _need(W, torch.complex64, "W", plan.device)
+    Bm, Cin, Cout = _filter_shapes(plan, xhat, W)
+    out = torch.empty((Bm, Cout, plan.lmax, plan.mmax), dtype=torch.complex64, device=xhat.device)
+    _abi.check(_abi.lib().spectral_filter(plan.handle, _ptr(xhat), _ptr(W), _ptr(out), Bm, Cin, Cout,
+                                          _stream(xhat)))
+    return out
+
+
+def spectral_filter_adjoint(plan: Plan, gy: torch.Tensor, W: torch.Tensor, xhat: torch.Tensor | None,
+                            need_gx: bool = True, need_gW: bool = True):
+    gy, _, _ = _spectral_in(plan, gy, "gy")
+    W = _need(W, torch.complex64, "W", plan.device)
+    Bm, Cout = int(gy.shape[0]), int(gy.shape[1])
+    Cin = int(W.shape[2])
+    if W.shape != (plan.lmax, Cout, Cin):
+        raise ValueError("W shape does not match gy")
+    if need_gW:
+        xhat, _, _ = _spectral_in(plan, xhat)
+    gx = torch.empty((Bm, Cin, plan.lmax, plan.mmax), dtype=torch.complex64, device=gy.device) if need_gx else None
+    gW = torch.empty((plan.lmax, Cout, Cin), dtype=torch.complex64, device=gy.device) if need_gW else None
+    _abi.check(_abi.lib().spectral_filter_adjoint(plan.handle, _ptr(gy), _ptr(W), _ptr(xhat if need_gW else None),
+                                                  _ptr(gx), _ptr(gW), Bm, Cin, Cout, _stream(gy)))
+    return gx, gW
+
+
+def sht_spectral_block(plan: Plan, x: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
+    """y = ISHT(filter(SHT(x), W)); x [Bm, Cin, nlat, nlon] -> y [Bm, Cout, nlat, nlon]."""
+    x, lead, _ = _spatial_in(plan, x)
+    if len(lead) != 2:
+        raise ValueError("x must be [Bm, Cin, nlat, nlon]")
+    W = _need(W, torch.complex64, "W", plan.device)
+    Bm, Cin = lead
+    if W.dim() != 3 or W.shape[0] != plan.lmax or W.shape[2] != Cin:
+        raise ValueError("W must be [lmax, Cout, Cin]")
+    Cout = int(W.shape[1])
+    out = torch.empty((Bm, Cout, plan.nlat, plan.nlon), dtype=torch.float32, device=x.device)
+    _abi.check(_abi.lib().sht_spectral_block(plan.handle, _ptr(x), _ptr(W), _ptr(out), Bm, Cin, Cout, _stream(x)))
+    return out
+
+
+def spectral_filter_inverse(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
+    """y = ISHT(filter(xhat, W)); xhat [Bm, Cin, lmax, mmax] -> y [Bm, Cout, nlat, nlon]."""
+    xhat, _, _ = _spectral_in(plan, xhat)
+    W = _need(W, torch.complex64, "W", plan.device)
+    Bm, Cin, Cout = _filter_shapes(plan, xhat, W)
+    out = torch.empty((Bm, Cout, plan.nlat, plan.nlon), dtype=torch.float32, device=xhat.device)
+    _abi.check(_abi.lib().spectral_filter_inverse(plan.handle, _ptr(xhat), _ptr(W), _ptr(out), Bm, Cin, Cout,
+                                                  _stream(xhat)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+class SpectralBlock(torch.autograd.Function):
+    """y = ISHT(filter(SHT(x), W)) with hand-written adjoints.
+
+    The backward pass recomputes xhat = SHT(x) instead of storing the
+    spectral activations:
+      gyhat = ISHT^T(gy);  (gxhat, gW) = filter^T(gyhat);  gx = SHT^T(gxhat).
+    """
+
+    @staticmethod
+    def forward(ctx, x, W, plan):
+        ctx.plan = plan
+        ctx.save_for_backward(x, W)
+        return sht_spectral_block(plan, x, W)
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, W = ctx.saved_tensors
+        plan = ctx.plan
+        need_x, need_W = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gyhat = sht_inverse_adjoint(plan, gy.contiguous())
+        xhat = sht_forward(plan, x) if need_W else None
+        gxhat, gW = spectral_filter_adjoint(plan, gyhat, W, xhat, need_gx=need_x, need_gW=need_W)
+        gx = sht_forward_adjoint(plan, gxhat) if need_x else None
+        return gx, gW, None
+
+
+def spectral_block(x: torch.Tensor, W: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return SpectralBlock.apply(x, W, plan)

@@ -1,0 +1,698 @@
+// C ABI of shtgb: plan construction (grids, weights, FP64 Legendre table on
+// the GPU, workspaces) and the execute calls.  See include/sht.h for the
+// contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sht_internal.cuh"
+
+namespace shtgb {
+
+static thread_local std::string g_last_error = "";
+static int g_fail_alloc_after = -1;  // test hook: fail the n-th allocation
+
+sht_status_t fail(sht_status_t st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+sht_status_t cuda_fail(cudaError_t err, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(err);
+  return err == cudaErrorMemoryAllocation ? SHT_ERR_OOM : SHT_ERR_CUDA;
+}
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  if (g_fail_alloc_after == 0) {
+    g_fail_alloc_after = -1;
+    return cudaErrorMemoryAllocation;
+  }
+  if (g_fail_alloc_after > 0) g_fail_alloc_after--;
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc(p, bytes);
+}
+
+// Legendre polynomial P_n and P_{n-1} at z by Bonnet's recurrence.
+void bonnet(int n, double z, double &pn, double &pn1) {
+  double a = 1.0, b = z;
+  if (n == 0) {
+    pn = 1.0;
+    pn1 = 0.0;
+    return;
+  }
+  for (int j = 1; j < n; j++) {
+    double c = ((2 * j + 1) * z * b - j * a) / (j + 1);
+    a = b;
+    b = c;
+  }
+  pn = b;
+  pn1 = a;
+}
+
+// Latitude nodes (x = cos theta, s = sin theta) and weights w for the
+// northern half including the equator; the southern half mirrors it.
+void make_grid(int grid, int nlat, std::vector<double> &x, std::vector<double> &s, std::vector<double> &w) {
+  x.assign(nlat, 0.0);
+  s.assign(nlat, 0.0);
+  w.assign(nlat, 0.0);
+  const int half = (nlat + 1) / 2;
+  for (int k = 0; k < half; k++) {
+    double xk, sk, wk;
+    if (grid == SHT_GRID_GAUSS) {
+      // k-th root of P_nlat from the north, Newton from the asymptotic guess
+      double z = std::cos(kPi * (4.0 * k + 3.0) / (4.0 * nlat + 2.0));
+      if (2 * k + 1 == nlat) z = 0.0;
+      double pn, pn1;
+      for (int it = 0; it < 64 && 2 * k + 1 != nlat; it++) {
+        bonnet(nlat, z, pn, pn1);
+        double dp = nlat * (pn1 - z * pn) / ((1.0 - z) * (1.0 + z));
+        double dz = pn / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-17) break;
+      }
+      bonnet(nlat, z, pn, pn1);
+      double omz = (1.0 - z) * (1.0 + z);
+      double dp = nlat * (pn1 - z * pn) / omz;
+      xk = z;
+      sk = std::sqrt(omz);
+      wk = 2.0 / (omz * dp * dp);
+    } else {
+      const int N = nlat - 1;
+      double t = kPi * (double)k / (double)N;
+      xk = std::cos(t);
+      sk = std::sin(t);
+      if (2 * k == N) xk = 0.0, sk = 1.0;
+      if (grid == SHT_GRID_EQUIANGULAR_CC) {
+        double acc = 1.0;
+        for (int j = 1; 2 * j <= N; j++) {
+          double bj = (2 * j == N) ? 1.0 : 2.0;
+          acc -= bj * std::cos(2.0 * j * t) / (4.0 * (double)j * j - 1.0);
+        }
+        wk = ((k == 0) ? 1.0 : 2.0) * acc / (double)N;
+      } else {
+        wk = kPi / (double)N * sk;
+      }
+    }
+    x[k] = xk;
+    s[k] = sk;
+    w[k] = wk;
+    x[nlat - 1 - k] = -xk;
+    s[nlat - 1 - k] = sk;
+    w[nlat - 1 - k] = wk;
+  }
+}
+
+bool factor_radix(int n, RadixPlan &rp) {
+  rp.n = n;
+  rp.nstages = 0;
+  int r = n;
+  auto push = [&](int v) {
+    if (rp.nstages >= kMaxRadices) return false;
+    rp.r[rp.nstages++] = v;
+    return true;
+  };
+  while (r % 4 == 0) {
+    if (!push(4)) return false;
+    r /= 4;
+  }
+  while (r % 2 == 0) {
+    if (!push(2)) return false;
+    r /= 2;
+  }
+  while (r % 3 == 0) {
+    if (!push(3)) return false;
+    r /= 3;
+  }
+  while (r % 5 == 0) {
+    if (!push(5)) return false;
+    r /= 5;
+  }
+  return r == 1;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  cudaError_t e = dev_alloc((void **)dst, sizeof(T) * src.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+void profile_release(ProfileState &pr);
+
+void free_plan(sht_plan_s *p) {
+  if (!p) return;
+  DeviceGuard g(p->device);
+  profile_release(p->prof);
+  cudaFree(p->d_table);
+  cudaFree(p->d_tab_off);
+  cudaFree(p->d_twiddle);
+  cudaFree(p->d_ring_w);
+  cudaFree(p->d_fwd_tiles);
+  cudaFree(p->d_inv_tiles);
+  cudaFree(p->d_work);
+  cudaFree(p->d_spec_a);
+  cudaFree(p->d_spec_b);
+  delete p;
+}
+
+TableF32 table_view(const sht_plan_s *p) { return TableF32{p->d_table, p->d_tab_off, p->Khp}; }
+
+// Launch through the profiler: brackets the launch with the next pair of
+// events when profiling is on.
+template <class F>
+cudaError_t traced(sht_plan_s *p, int kernel, cudaStream_t st, F &&launch) {
+  ProfileState &pr = p->prof;
+  const bool rec = pr.on && pr.used < pr.capacity;
+  if (pr.on && !rec) pr.dropped++;
+  if (rec) {
+    cudaError_t e = cudaEventRecord(pr.start[pr.used], st);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = launch();
+  if (e != cudaSuccess) return e;
+  if (rec) {
+    e = cudaEventRecord(pr.stop[pr.used], st);
+    if (e != cudaSuccess) return e;
+    pr.kernel[pr.used] = kernel;
+    pr.used++;
+  }
+  return cudaSuccess;
+}
+
+void profile_release(ProfileState &pr) {
+  for (auto ev : pr.start) cudaEventDestroy(ev);
+  for (auto ev : pr.stop) cudaEventDestroy(ev);
+  pr.start.clear();
+  pr.stop.clear();
+  pr.kernel.clear();
+  pr.on = false;
+  pr.capacity = pr.used = 0;
+  pr.dropped = 0;
+}
+
+// ---- chunked execute bodies -------------------------------------------------
+
+sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cudaStream_t st, bool adjoint,
+                      bool zero_upper) {
+  const int64_t LM = (int64_t)p->L * p->M;
+  for (int64_t b0 = 0; b0 < B; b0 += p->max_batch) {
+    const int nb = (int)std::min<int64_t>(p->max_batch, B - b0);
+    cudaError_t e = traced(p, SHT_KERNEL_R2C, st, [&] {
+      return launch_r2c(x + b0 * p->nlat * (int64_t)p->nlon, p->d_work, p->nlat, p->nlon, p->M, nb, p->ldc,
+                        p->d_twiddle, p->radix, adjoint ? nullptr : p->d_ring_w, adjoint ? 1 : 0, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
+    e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
+      return launch_leg_fwd_f32(table_view(p), p->d_fwd_tiles, p->n_fwd_tiles, p->d_work, xhat + b0 * LM, p->L,
+                                p->M, p->Kh, p->ldc, nb, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "forward Legendre launch");
+    if (zero_upper) {
+      e = traced(p, SHT_KERNEL_ZERO, st, [&] { return launch_zero_upper(xhat + b0 * LM, p->L, p->M, nb, st); });
+      if (e != cudaSuccess) return cuda_fail(e, "zero fill launch");
+    }
+  }
+  return SHT_OK;
+}
+
+sht_status_t synthesis(sht_plan_s *p, const float2 *yhat, float *y, int64_t B, cudaStream_t st, bool adjoint) {
+  const int64_t LM = (int64_t)p->L * p->M;
+  for (int64_t b0 = 0; b0 < B; b0 += p->max_batch) {
+    const int nb = (int)std::min<int64_t>(p->max_batch, B - b0);
+    cudaError_t e = traced(p, SHT_KERNEL_LEG_INV, st, [&] {
+      return launch_leg_inv_f32(table_view(p), p->d_inv_tiles, p->n_inv_tiles, yhat + b0 * LM, p->d_work, p->L,
+                                p->M, p->Kh, p->ldc, nb, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "inverse Legendre launch");
+    e = traced(p, SHT_KERNEL_C2R, st, [&] {
+      return launch_c2r(p->d_work, y + b0 * p->nlat * (int64_t)p->nlon, p->nlat, p->nlon, p->M, nb, p->ldc,
+                        p->d_twiddle, p->radix, adjoint ? p->d_ring_w : nullptr, adjoint ? 0 : 1, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "longitude synthesis launch");
+  }
+  return SHT_OK;
+}
+
+sht_status_t filter_body(sht_plan_s *p, const float2 *x, const float2 *W, float2 *y, int64_t Bm, int Cin, int Cout,
+                         int adjoint, cudaStream_t st) {
+  const int64_t LM = (int64_t)p->L * p->M;
+  const int64_t chunk = 65535;
+  const int cin = adjoint ? Cout : Cin, cout = adjoint ? Cin : Cout;
+  for (int64_t b0 = 0; b0 < Bm; b0 += chunk) {
+    const int64_t nb = std::min<int64_t>(chunk, Bm - b0);
+    cudaError_t e = traced(p, SHT_KERNEL_FILTER, st, [&] {
+      return launch_filter(x + b0 * cin * LM, W, y + b0 * cout * LM, p->L, p->M, nb, Cin, Cout, adjoint, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+  }
+  return SHT_OK;
+}
+
+sht_status_t check_plan(sht_plan_t plan) {
+  if (!plan) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  return SHT_OK;
+}
+
+sht_status_t check_batch(int64_t B) {
+  if (B < 0) return fail(SHT_ERR_INVALID_ARG, "batch must be >= 0");
+  return SHT_OK;
+}
+
+sht_status_t check_ptr(const void *ptr, const char *name) {
+  if (!ptr) return fail(SHT_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (((uintptr_t)ptr) & 15) return fail(SHT_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+  return SHT_OK;
+}
+
+sht_status_t check_channels(sht_plan_s *p, int Cin, int Cout, bool block) {
+  if (Cin < 1 || Cout < 1) return fail(SHT_ERR_INVALID_ARG, "channel counts must be >= 1");
+  if (block && (int64_t)std::max(Cin, Cout) > p->max_batch)
+    return fail(SHT_ERR_INVALID_ARG, "max(Cin, Cout) exceeds the plan's max_batch");
+  return SHT_OK;
+}
+
+#define SHT_TRY(expr)                    \
+  do {                                   \
+    sht_status_t _s = (expr);            \
+    if (_s != SHT_OK) return _s;         \
+  } while (0)
+
+}  // namespace
+}  // namespace shtgb
+
+using namespace shtgb;
+
+extern "C" {
+
+void sht_plan_opts_default(sht_plan_opts *opts) {
+  if (!opts) return;
+  std::memset(opts, 0, sizeof(*opts));
+  opts->precision = SHT_PREC_FP32;
+  opts->device = -1;
+  opts->max_batch = 256;
+}
+
+sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, int mmax, const sht_plan_opts *opts) {
+  if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  sht_plan_opts o;
+  sht_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (grid != SHT_GRID_GAUSS && grid != SHT_GRID_EQUIANGULAR_CC && grid != SHT_GRID_EQUIANGULAR_TRAPZ)
+    return fail(SHT_ERR_INVALID_ARG, "unknown grid type");
+  if (nlat < 1 || nlon < 1 || lmax < 1 || mmax < 1)
+    return fail(SHT_ERR_INVALID_ARG, "nlat, nlon, lmax, mmax must be >= 1");
+  if (grid != SHT_GRID_GAUSS && nlat < 2) return fail(SHT_ERR_INVALID_ARG, "equiangular grids need nlat >= 2");
+  if (mmax > lmax) return fail(SHT_ERR_INVALID_ARG, "mmax must be <= lmax");
+  if (mmax > nlon / 2 + 1) return fail(SHT_ERR_INVALID_ARG, "mmax must be <= nlon/2 + 1");
+  if (grid == SHT_GRID_GAUSS && lmax > nlat) return fail(SHT_ERR_INVALID_ARG, "Gaussian grids need lmax <= nlat");
+  if (o.precision != SHT_PREC_FP32 && o.precision != SHT_PREC_BF16 && o.precision != SHT_PREC_SPLIT_BF16)
+    return fail(SHT_ERR_INVALID_ARG, "unknown precision");
+  if (o.max_batch < 1) return fail(SHT_ERR_INVALID_ARG, "max_batch must be >= 1");
+  for (int r : o.reserved)
+    if (r != 0) return fail(SHT_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (nlon > kMaxNlon) return fail(SHT_ERR_UNSUPPORTED, "nlon above 8192 is not supported");
+  RadixPlan rp;
+  if (!factor_radix(nlon, rp)) return fail(SHT_ERR_UNSUPPORTED, "nlon must factor into 2, 3 and 5");
+  if (o.precision != SHT_PREC_FP32)
+    return fail(SHT_ERR_UNSUPPORTED, "this build implements the FP32 Legendre path only");
+
+  int dev = o.device;
+  if (dev < 0) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (dev >= ndev) return fail(SHT_ERR_INVALID_ARG, "device ordinal out of range");
+  DeviceGuard guard(dev);
+
+  sht_plan_s *p = new (std::nothrow) sht_plan_s();
+  if (!p) return fail(SHT_ERR_OOM, "host allocation failed");
+  p->device = dev;
+  p->nlat = nlat;
+  p->nlon = nlon;
+  p->grid = grid;
+  p->L = lmax;
+  p->M = mmax;
+  p->precision = o.precision;
+  p->max_batch = o.max_batch;
+  p->Kh = (nlat + 1) / 2;
+  p->Khp = (p->Kh + 15) / 16 * 16;
+  p->ldc = (int)((2 * o.max_batch + 3) / 4 * 4);
+  p->radix = rp;
+  make_grid(grid, nlat, p->x, p->s, p->w);
+
+  auto bail = [&](cudaError_t err, const char *what) {
+    sht_status_t st = cuda_fail(err, what);
+    free_plan(p);
+    return st;
+  };
+
+  // table offsets (floats) of the folded blocks (m, p)
+  std::vector<int64_t> off(2 * (size_t)mmax + 1);
+  int64_t acc = 0;
+  for (int m = 0; m < mmax; m++)
+    for (int q = 0; q < 2; q++) {
+      off[2 * m + q] = acc;
+      acc += (int64_t)leg_rows(lmax, m, q) * p->Khp;
+    }
+  off[2 * mmax] = acc;
+  p->tab_off = off;
+  p->table_bytes = acc * (int64_t)sizeof(float);
+
+  // tile lists (row tiles of 64)
+  std::vector<LegTile> ft, it;
+  for (int r0 = 0; r0 < (lmax + 1) / 2 + 1; r0 += 64)
+    for (int m = 0; m < mmax; m++)
+      for (int q = 0; q < 2; q++)
+        if (r0 < leg_rows(lmax, m, q)) ft.push_back(LegTile{m, q, r0});
+  // every (m, p) block gets inverse tiles, also the empty one (m = lmax-1,
+  // odd parity): its tiles write the zeros that the synthesis reads
+  for (int m = 0; m < mmax; m++)
+    for (int q = 0; q < 2; q++)
+      for (int k0 = 0; k0 < p->Kh; k0 += 64) it.push_back(LegTile{m, q, k0});
+  p->n_fwd_tiles = (int)ft.size();
+  p->n_inv_tiles = (int)it.size();
+
+  // device tables
+  if ((e = dev_alloc((void **)&p->d_table, (size_t)p->table_bytes)) != cudaSuccess) return bail(e, "table allocation");
+  if ((e = cudaMemset(p->d_table, 0, (size_t)p->table_bytes)) != cudaSuccess) return bail(e, "table memset");
+  if ((e = upload(&p->d_tab_off, off)) != cudaSuccess) return bail(e, "offset upload");
+  if ((e = upload(&p->d_fwd_tiles, ft)) != cudaSuccess) return bail(e, "tile upload");
+  if ((e = upload(&p->d_inv_tiles, it)) != cudaSuccess) return bail(e, "tile upload");
+  std::vector<float2> tw(nlon);
+  for (int q = 0; q < nlon; q++) {
+    double ph = 2.0 * kPi * (double)q / (double)nlon;
+    tw[q] = make_float2((float)std::cos(ph), (float)-std::sin(ph));
+  }
+  if ((e = upload(&p->d_twiddle, tw)) != cudaSuccess) return bail(e, "twiddle upload");
+  std::vector<float> ringw(nlat);
+  for (int k = 0; k < nlat; k++) ringw[k] = (float)(p->w[k] * 2.0 * kPi / (double)nlon);
+  if ((e = upload(&p->d_ring_w, ringw)) != cudaSuccess) return bail(e, "weight upload");
+
+  // FP64 generation of the table on the device
+  {
+    std::vector<double> a((size_t)lmax * mmax, 0.0), b((size_t)lmax * mmax, 0.0), seed(mmax + 1, 0.0);
+    for (int m = 0; m < mmax; m++)
+      for (int l = m + 2; l < lmax; l++) {
+        double dl = l, dm = m;
+        a[(size_t)l * mmax + m] = std::sqrt((4.0 * dl * dl - 1.0) / (dl * dl - dm * dm));
+        b[(size_t)l * mmax + m] = std::sqrt(((dl - 1.0) * (dl - 1.0) - dm * dm) / (4.0 * (dl - 1.0) * (dl - 1.0) - 1.0));
+      }
+    for (int i = 1; i <= mmax; i++) seed[i] = -std::sqrt((2.0 * i + 1.0) / (2.0 * i));
+    std::vector<double> xh(p->x.begin(), p->x.begin() + p->Kh), sh(p->s.begin(), p->s.begin() + p->Kh);
+    double *d_x = nullptr, *d_s = nullptr, *d_a = nullptr, *d_b = nullptr, *d_seed = nullptr;
+    e = upload(&d_x, xh);
+    if (e == cudaSuccess) e = upload(&d_s, sh);
+    if (e == cudaSuccess) e = upload(&d_a, a);
+    if (e == cudaSuccess) e = upload(&d_b, b);
+    if (e == cudaSuccess) e = upload(&d_seed, seed);
+    if (e == cudaSuccess)
+      e = launch_table_gen_f32(p->d_table, p->d_tab_off, p->Khp, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_x);
+    cudaFree(d_s);
+    cudaFree(d_a);
+    cudaFree(d_b);
+    cudaFree(d_seed);
+    if (e != cudaSuccess) return bail(e, "table generation");
+  }
+
+  // workspaces
+  const size_t work = sizeof(float) * (size_t)mmax * 2 * p->Kh * p->ldc;
+  const size_t spec = sizeof(float2) * (size_t)o.max_batch * lmax * mmax;
+  if ((e = dev_alloc((void **)&p->d_work, work)) != cudaSuccess) return bail(e, "workspace allocation");
+  if ((e = dev_alloc((void **)&p->d_spec_a, spec)) != cudaSuccess) return bail(e, "workspace allocation");
+  if ((e = dev_alloc((void **)&p->d_spec_b, spec)) != cudaSuccess) return bail(e, "workspace allocation");
+  if ((e = cudaMemset(p->d_work, 0, work)) != cudaSuccess) return bail(e, "workspace memset");
+  p->workspace_bytes = (int64_t)(work + 2 * spec);
+  *out = p;
+  return SHT_OK;
+}
+
+sht_status_t sht_plan_destroy(sht_plan_t plan) {
+  if (!plan) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  cudaError_t pending;
+  {
+    DeviceGuard g(plan->device);
+    pending = cudaGetLastError();
+  }
+  free_plan(plan);
+  if (pending != cudaSuccess) return cuda_fail(pending, "pending CUDA error");
+  return SHT_OK;
+}
+
+sht_status_t sht_plan_info(sht_plan_t p, int *nlat, int *nlon, int *grid, int *lmax, int *mmax, int *precision,
+                           int64_t *max_batch, int64_t *table_bytes, int64_t *workspace_bytes) {
+  SHT_TRY(check_plan(p));
+  if (nlat) *nlat = p->nlat;
+  if (nlon) *nlon = p->nlon;
+  if (grid) *grid = p->grid;
+  if (lmax) *lmax = p->L;
+  if (mmax) *mmax = p->M;
+  if (precision) *precision = p->precision;
+  if (max_batch) *max_batch = p->max_batch;
+  if (table_bytes) *table_bytes = p->table_bytes;
+  if (workspace_bytes) *workspace_bytes = p->workspace_bytes;
+  return SHT_OK;
+}
+
+sht_status_t sht_plan_grid(sht_plan_t p, double *x, double *w) {
+  SHT_TRY(check_plan(p));
+  if (x) std::memcpy(x, p->x.data(), sizeof(double) * p->nlat);
+  if (w) std::memcpy(w, p->w.data(), sizeof(double) * p->nlat);
+  return SHT_OK;
+}
+
+sht_status_t sht_forward(sht_plan_t p, const float *x, void *xhat, int64_t B, void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(B));
+  if (B == 0) return SHT_OK;
+  SHT_TRY(check_ptr(x, "x"));
+  SHT_TRY(check_ptr(xhat, "xhat"));
+  DeviceGuard g(p->device);
+  return analysis(p, x, (float2 *)xhat, B, (cudaStream_t)stream, false, true);
+}
+
+sht_status_t sht_inverse_adjoint(sht_plan_t p, const float *gx, void *gxhat, int64_t B, void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(B));
+  if (B == 0) return SHT_OK;
+  SHT_TRY(check_ptr(gx, "gx"));
+  SHT_TRY(check_ptr(gxhat, "gxhat"));
+  DeviceGuard g(p->device);
+  return analysis(p, gx, (float2 *)gxhat, B, (cudaStream_t)stream, true, true);
+}
+
+sht_status_t sht_inverse(sht_plan_t p, const void *xhat, float *x, int64_t B, void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(B));
+  if (B == 0) return SHT_OK;
+  SHT_TRY(check_ptr(xhat, "xhat"));
+  SHT_TRY(check_ptr(x, "x"));
+  DeviceGuard g(p->device);
+  return synthesis(p, (const float2 *)xhat, x, B, (cudaStream_t)stream, false);
+}
+
+sht_status_t sht_forward_adjoint(sht_plan_t p, const void *gxhat, float *gx, int64_t B, void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(B));
+  if (B == 0) return SHT_OK;
+  SHT_TRY(check_ptr(gxhat, "gxhat"));
+  SHT_TRY(check_ptr(gx, "gx"));
+  DeviceGuard g(p->device);
+  return synthesis(p, (const float2 *)gxhat, gx, B, (cudaStream_t)stream, true);
+}
+
+sht_status_t spectral_filter(sht_plan_t p, const void *xhat, const void *W, void *yhat, int64_t Bm, int Cin, int Cout,
+                             void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, false));
+  if (Bm == 0) return SHT_OK;
+  SHT_TRY(check_ptr(xhat, "xhat"));
+  SHT_TRY(check_ptr(W, "W"));
+  SHT_TRY(check_ptr(yhat, "yhat"));
+  DeviceGuard g(p->device);
+  return filter_body(p, (const float2 *)xhat, (const float2 *)W, (float2 *)yhat, Bm, Cin, Cout, 0,
+                     (cudaStream_t)stream);
+}
+
+sht_status_t spectral_filter_adjoint(sht_plan_t p, const void *gy, const void *W, const void *xhat, void *gx, void *gW,
+                                     int64_t Bm, int Cin, int Cout, void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, false));
+  SHT_TRY(check_ptr(gy, "gy"));
+  SHT_TRY(check_ptr(W, "W"));
+  if (gW) SHT_TRY(check_ptr(xhat, "xhat"));
+  if (gx) SHT_TRY(check_ptr(gx, "gx"));
+  if (gW) SHT_TRY(check_ptr(gW, "gW"));
+  DeviceGuard g(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (gx && Bm > 0) SHT_TRY(filter_body(p, (const float2 *)gy, (const float2 *)W, (float2 *)gx, Bm, Cin, Cout, 1, st));
+  if (gW) {
+    cudaError_t e = traced(p, SHT_KERNEL_FILTER_DW, st, [&] {
+      return launch_filter_dw((const float2 *)gy, (const float2 *)xhat, (float2 *)gW, p->L, p->M, Bm, Cin, Cout, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "weight adjoint launch");
+  }
+  return SHT_OK;
+}
+
+sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, float *y, int64_t Bm, int Cin, int Cout,
+                                void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, true));
+  if (Bm == 0) return SHT_OK;
+  SHT_TRY(check_ptr(x, "x"));
+  SHT_TRY(check_ptr(W, "W"));
+  SHT_TRY(check_ptr(y, "y"));
+  DeviceGuard g(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t per = p->max_batch / std::max(Cin, Cout);
+  const int64_t npix = (int64_t)p->nlat * p->nlon;
+  for (int64_t b0 = 0; b0 < Bm; b0 += per) {
+    const int64_t nb = std::min(per, Bm - b0);
+    SHT_TRY(analysis(p, x + b0 * Cin * npix, p->d_spec_a, nb * Cin, st, false, false));
+    SHT_TRY(filter_body(p, p->d_spec_a, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 0, st));
+    SHT_TRY(synthesis(p, p->d_spec_b, y + b0 * Cout * npix, nb * Cout, st, false));
+  }
+  return SHT_OK;
+}
+
+sht_status_t spectral_filter_inverse(sht_plan_t p, const void *xhat, const void *W, float *y, int64_t Bm, int Cin,
+                                     int Cout, void *stream) {
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, true));
+  if (Bm == 0) return SHT_OK;
+  SHT_TRY(check_ptr(xhat, "xhat"));
+  SHT_TRY(check_ptr(W, "W"));
+  SHT_TRY(check_ptr(y, "y"));
+  DeviceGuard g(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t per = p->max_batch / std::max(Cin, Cout);
+  const int64_t LM = (int64_t)p->L * p->M;
+  const int64_t npix = (int64_t)p->nlat * p->nlon;
+  for (int64_t b0 = 0; b0 < Bm; b0 += per) {
+    const int64_t nb = std::min(per, Bm - b0);
+    SHT_TRY(filter_body(p, (const float2 *)xhat + b0 * Cin * LM, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 0, st));
+    SHT_TRY(synthesis(p, p->d_spec_b, y + b0 * Cout * npix, nb * Cout, st, false));
+  }
+  return SHT_OK;
+}
+
+sht_status_t sht_profile_begin(sht_plan_t p, int capacity) {
+  SHT_TRY(check_plan(p));
+  if (capacity < 1) return fail(SHT_ERR_INVALID_ARG, "capacity must be >= 1");
+  DeviceGuard g(p->device);
+  profile_release(p->prof);
+  ProfileState &pr = p->prof;
+  pr.start.resize(capacity);
+  pr.stop.resize(capacity);
+  pr.kernel.assign(capacity, -1);
+  for (int i = 0; i < capacity; i++) {
+    cudaError_t e1 = cudaEventCreate(&pr.start[i]);
+    cudaError_t e2 = cudaEventCreate(&pr.stop[i]);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      pr.start.resize(e1 == cudaSuccess ? i + 1 : i);
+      pr.stop.resize(e2 == cudaSuccess ? i + 1 : i);
+      profile_release(pr);
+      return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaEventCreate");
+    }
+  }
+  pr.capacity = capacity;
+  pr.used = 0;
+  pr.dropped = 0;
+  pr.on = true;
+  return SHT_OK;
+}
+
+sht_status_t sht_profile_collect(sht_plan_t p, int64_t *launches, double *ms, int64_t *dropped) {
+  SHT_TRY(check_plan(p));
+  ProfileState &pr = p->prof;
+  if (launches)
+    for (int k = 0; k < SHT_KERNEL_COUNT; k++) launches[k] = 0;
+  if (ms)
+    for (int k = 0; k < SHT_KERNEL_COUNT; k++) ms[k] = 0.0;
+  if (dropped) *dropped = pr.dropped;
+  if (!pr.on) return SHT_OK;
+  DeviceGuard g(p->device);
+  for (int i = 0; i < pr.used; i++) {
+    cudaError_t e = cudaEventSynchronize(pr.stop[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, pr.start[i], pr.stop[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    const int k = pr.kernel[i];
+    if (k >= 0 && k < SHT_KERNEL_COUNT) {
+      if (launches) launches[k]++;
+      if (ms) ms[k] += t;
+    }
+  }
+  pr.used = 0;
+  pr.dropped = 0;
+  return SHT_OK;
+}
+
+sht_status_t sht_profile_end(sht_plan_t p) {
+  SHT_TRY(check_plan(p));
+  DeviceGuard g(p->device);
+  profile_release(p->prof);
+  return SHT_OK;
+}
+
+const char *sht_kernel_name(int k) {
+  static const char *names[SHT_KERNEL_COUNT] = {"r2c", "leg_fwd", "zero_upper", "filter", "filter_dw", "leg_inv",
+                                                "c2r"};
+  return (k >= 0 && k < SHT_KERNEL_COUNT) ? names[k] : "?";
+}
+
+const char *sht_status_string(sht_status_t s) {
+  switch (s) {
+    case SHT_OK: return "SHT_OK";
+    case SHT_ERR_INVALID_ARG: return "SHT_ERR_INVALID_ARG";
+    case SHT_ERR_UNSUPPORTED: return "SHT_ERR_UNSUPPORTED";
+    case SHT_ERR_OOM: return "SHT_ERR_OOM";
+    case SHT_ERR_CUDA: return "SHT_ERR_CUDA";
+    case SHT_ERR_TIMEOUT: return "SHT_ERR_TIMEOUT";
+    case SHT_ERR_INTERNAL: return "SHT_ERR_INTERNAL";
+  }
+  return "SHT_ERR_UNKNOWN";
+}
+
+const char *sht_last_error_message(void) { return g_last_error.c_str(); }
+
+const char *sht_version(void) { return "0.1.0"; }
+
+/* Test hook: make the n-th device allocation of later sht_plan calls fail
+ * (n = 0 fails the next one; n < 0 disables). */
+void sht_debug_fail_alloc_after(int n) { g_fail_alloc_after = n; }
+
+}  // extern "C"

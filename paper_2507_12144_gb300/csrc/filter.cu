@@ -1,0 +1,193 @@
+// Spectral filter of the global block: the convolution theorem on the
+// sphere (Eq. s2_spectral_conv) multiplies each degree l by one filter
+// value; with channel mixing the filter becomes a complex matrix per degree,
+//   y[b][o][l][m] = sum_i W[l][o][i] x[b][i][l][m],   m <= l,
+// and its adjoints
+//   gx[b][i][l][m] = sum_o conj(W[l][o][i]) gy[b][o][l][m]
+//   gW[l][o][i]    = sum_{b, m <= l} gy[b][o][l][m] conj(x[b][i][l][m]).
+// FP32 complex arithmetic on the CUDA cores.
+#include "sht_internal.cuh"
+
+namespace shtgb {
+namespace {
+
+constexpr int kTO = 32;   // output channels per CTA
+constexpr int kTM = 64;   // orders m per CTA
+constexpr int kTK = 16;   // reduction chunk (input channels)
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+
+// grid: x = l * mtiles + mt, y = output-channel tile, z = member b
+template <bool kAdjoint>
+__global__ void __launch_bounds__(kThreads)
+filter_kernel(const float2 *__restrict__ x, const float2 *__restrict__ W, float2 *__restrict__ y, int L, int M,
+              int Cin, int Cout) {
+  __shared__ __align__(16) float2 Ws[kTK][kTO];
+  __shared__ __align__(16) float2 Xs[kTK][kTM];
+  const int mtiles = (M + kTM - 1) / kTM;
+  const int l = blockIdx.x / mtiles;
+  const int m0 = (blockIdx.x - l * mtiles) * kTM;
+  const int o0 = blockIdx.y * kTO;
+  const int64_t b = blockIdx.z;
+  // roles: kAdjoint swaps which channel count is the output
+  const int Cout_ = kAdjoint ? Cin : Cout;
+  const int Cred = kAdjoint ? Cout : Cin;
+  const int64_t LM = (int64_t)L * M;
+  const float2 *xb = x + b * Cred * LM + (int64_t)l * M;
+  float2 *yb = y + b * Cout_ * LM + (int64_t)l * M;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty: 2 outputs, tx: 4 orders
+  if (m0 > l) {
+    // whole tile above the diagonal: zeros
+    for (int e = threadIdx.x; e < kTO * kTM; e += kThreads) {
+      const int oo = e / kTM, mm = e - oo * kTM;
+      if (o0 + oo < Cout_ && m0 + mm < M) yb[(int64_t)(o0 + oo) * LM + m0 + mm] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
+  float2 acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+  const int mlim = min(M, l + 1);
+  for (int k0 = 0; k0 < Cred; k0 += kTK) {
+    // W tile: Ws[kk][oo] = Wmat(o0 + oo, k0 + kk)
+    for (int e = threadIdx.x; e < kTK * kTO; e += kThreads) {
+      int kk, oo;
+      float2 w = make_float2(0.f, 0.f);
+      if (!kAdjoint) {
+        oo = e / kTK;
+        kk = e - oo * kTK;  // consecutive threads read consecutive input channels
+        if (o0 + oo < Cout_ && k0 + kk < Cred) w = W[((int64_t)l * Cout + o0 + oo) * Cin + k0 + kk];
+      } else {
+        kk = e / kTO;
+        oo = e - kk * kTO;  // consecutive threads read consecutive "output" (= input channel) index
+        if (o0 + oo < Cout_ && k0 + kk < Cred) {
+          w = W[((int64_t)l * Cout + k0 + kk) * Cin + o0 + oo];
+          w.y = -w.y;
+        }
+      }
+      Ws[kk][oo] = w;
+    }
+    for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+      const int kk = e / kTM, mm = e - kk * kTM;
+      float2 v = make_float2(0.f, 0.f);
+      if (k0 + kk < Cred && m0 + mm < mlim) v = xb[(int64_t)(k0 + kk) * LM + m0 + mm];
+      Xs[kk][mm] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTK; kk++) {
+      const float2 w0 = Ws[kk][ty * 2 + 0], w1 = Ws[kk][ty * 2 + 1];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const float2 xv = Xs[kk][tx + 16 * j];
+        acc[0][j] = cfma(w0, xv, acc[0][j]);
+        acc[1][j] = cfma(w1, xv, acc[1][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const int o = o0 + ty * 2 + i;
+    if (o >= Cout_) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int m = m0 + tx + 16 * j;
+      if (m < M) yb[(int64_t)o * LM + m] = (m <= l) ? acc[i][j] : make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// gW[l][o][i] = sum_{b, m <= l} gy[b][o][l][m] conj(x[b][i][l][m])
+// grid: x = l, y = o tile (32), z = i tile (32).  Each thread owns 2 x 2
+// outputs; the reduction runs over (b, m) in chunks of 32.
+constexpr int kDW = 32;
+constexpr int kDK = 32;
+__global__ void __launch_bounds__(kThreads)
+filter_dw_kernel(const float2 *__restrict__ gy, const float2 *__restrict__ x, float2 *__restrict__ gW, int L, int M,
+                 int64_t Bm, int Cin, int Cout) {
+  __shared__ float2 Gs[kDW][kDK + 1];
+  __shared__ float2 Xs[kDW][kDK + 1];
+  const int l = blockIdx.x;
+  const int o0 = blockIdx.y * kDW, i0 = blockIdx.z * kDW;
+  const int64_t LM = (int64_t)L * M;
+  const int mlim = min(M, l + 1);
+  const int64_t K = Bm * mlim;
+  const int to = threadIdx.x >> 4, ti = threadIdx.x & 15;
+  float2 acc[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int c = 0; c < 2; c++) acc[a][c] = make_float2(0.f, 0.f);
+  for (int64_t k0 = 0; k0 < K; k0 += kDK) {
+    for (int e = threadIdx.x; e < kDW * kDK; e += kThreads) {
+      const int rr = e / kDK, kk = e - rr * kDK;
+      const int64_t kg = k0 + kk;
+      float2 g = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+      if (kg < K) {
+        const int64_t b = kg / mlim;
+        const int m = (int)(kg - b * mlim);
+        if (o0 + rr < Cout) g = gy[(b * Cout + o0 + rr) * LM + (int64_t)l * M + m];
+        if (i0 + rr < Cin) v = x[(b * Cin + i0 + rr) * LM + (int64_t)l * M + m];
+      }
+      Gs[rr][kk] = g;
+      Xs[rr][kk] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kDK; kk++) {
+      const float2 g0 = Gs[to * 2 + 0][kk], g1 = Gs[to * 2 + 1][kk];
+      const float2 v0 = Xs[ti * 2 + 0][kk], v1 = Xs[ti * 2 + 1][kk];
+      // g * conj(v)
+      acc[0][0].x += g0.x * v0.x + g0.y * v0.y;
+      acc[0][0].y += g0.y * v0.x - g0.x * v0.y;
+      acc[0][1].x += g0.x * v1.x + g0.y * v1.y;
+      acc[0][1].y += g0.y * v1.x - g0.x * v1.y;
+      acc[1][0].x += g1.x * v0.x + g1.y * v0.y;
+      acc[1][0].y += g1.y * v0.x - g1.x * v0.y;
+      acc[1][1].x += g1.x * v1.x + g1.y * v1.y;
+      acc[1][1].y += g1.y * v1.x - g1.x * v1.y;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      const int o = o0 + to * 2 + a, i = i0 + ti * 2 + c;
+      if (o < Cout && i < Cin) gW[((int64_t)l * Cout + o) * Cin + i] = acc[a][c];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L, int M, int64_t Bm, int Cin, int Cout,
+                          int adjoint, cudaStream_t st) {
+  if (Bm <= 0) return cudaSuccess;
+  const int mtiles = (M + kTM - 1) / kTM;
+  const int cout = adjoint ? Cin : Cout;
+  dim3 grid(L * mtiles, (cout + kTO - 1) / kTO, (unsigned)Bm);
+  if (adjoint)
+    filter_kernel<true><<<grid, kThreads, 0, st>>>(x, W, y, L, M, Cin, Cout);
+  else
+    filter_kernel<false><<<grid, kThreads, 0, st>>>(x, W, y, L, M, Cin, Cout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_dw(const float2 *gy, const float2 *x, float2 *gW, int L, int M, int64_t Bm, int Cin,
+                             int Cout, cudaStream_t st) {
+  dim3 grid(L, (Cout + kDW - 1) / kDW, (Cin + kDW - 1) / kDW);
+  filter_dw_kernel<<<grid, kThreads, 0, st>>>(gy, x, gW, L, M, Bm, Cin, Cout);
+  return cudaGetLastError();
+}
+
+}  // namespace shtgb

@@ -1,0 +1,152 @@
+// Internal declarations of the shtgb CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sht.h"
+
+namespace shtgb {
+
+constexpr int kMaxRadices = 16;
+constexpr int kMaxNlon = 8192;
+
+// Factorisation of nlon into radix-2/3/4/5 Stockham stages.
+struct RadixPlan {
+  int n;
+  int nstages;
+  int r[kMaxRadices];
+};
+
+// One tile of a Legendre contraction: order m, parity p of l + m, first row.
+struct LegTile {
+  int m;
+  int p;
+  int r0;
+};
+
+// Device-side view of the folded FP32 Legendre table.  For order m and
+// parity p the rows are l = m + p + 2 i (i < nrows(m, p)), the columns are
+// the northern half-rows k' = 0 .. Kh-1 (Kh = ceil(nlat / 2)), padded to Khp.
+struct TableF32 {
+  const float *data;
+  const int64_t *off;  // [2 M] float offset of block (m, p)
+  int Khp;
+};
+
+struct sht_plan_impl;
+
+// Record a failure message for sht_last_error_message() and return status.
+sht_status_t fail(sht_status_t st, const std::string &msg);
+sht_status_t cuda_fail(cudaError_t err, const char *what);
+
+// Number of l in parity class p at order m for lmax L.
+__host__ __device__ inline int leg_rows(int L, int m, int p) {
+  int n = L - m - p;
+  return n > 0 ? (n + 1) / 2 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns the launch status, nothing synchronises).
+// ---------------------------------------------------------------------------
+
+// Longitude analysis of pairs of rings (k, nlat-1-k):
+//   F_k(m) = ring_scale[k] * c_m * sum_j x_kj e^{-2 pi i j m / nlon}
+// folded by parity into Fw[m][p][k'][ldc] (p = 0: F_k + F_kbar, p = 1:
+// F_k - F_kbar; the equator row of odd nlat goes to p = 0 alone).  c_m = 1
+// when inverse_weights == 0, else the weight of the real inverse (1 for
+// m = 0 and the Nyquist mode, 2 otherwise).  ring_scale may be NULL (= 1).
+cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M,
+                       int B, int ldc, const float2 *twiddle,
+                       const RadixPlan &rp, const float *ring_scale,
+                       int inverse_weights, cudaStream_t st);
+
+// Longitude synthesis from folded Gw[m][p][k'][ldc]:
+//   u_kj = ring_scale[k] * sum_m c_m Re(G_k(m) e^{2 pi i j m / nlon})
+// with G_k = G_even + G_odd (north row k'), G_kbar = G_even - G_odd.
+cudaError_t launch_c2r(const float *Gw, float *y, int nlat, int nlon, int M,
+                       int B, int ldc, const float2 *twiddle,
+                       const RadixPlan &rp, const float *ring_scale,
+                       int inverse_weights, cudaStream_t st);
+
+// Forward Legendre contraction, FP32 CUDA cores:
+//   xhat[b][l][m] = sum_k' T[m][p][i][k'] Fw[m][p][k'][2b + {re, im}]
+cudaError_t launch_leg_fwd_f32(const TableF32 &T, const LegTile *tiles,
+                               int ntiles, const float *Fw, float2 *xhat,
+                               int L, int M, int Kh, int ldc, int B,
+                               cudaStream_t st);
+
+// Inverse Legendre contraction, FP32 CUDA cores:
+//   Gw[m][p][k'][2b + {re, im}] = sum_i T[m][p][i][k'] yhat[b][m + p + 2 i][m]
+cudaError_t launch_leg_inv_f32(const TableF32 &T, const LegTile *tiles,
+                               int ntiles, const float2 *yhat, float *Gw,
+                               int L, int M, int Kh, int ldc, int B,
+                               cudaStream_t st);
+
+// Zero the l < m part of B dense [L][M] coefficient blocks.
+cudaError_t launch_zero_upper(float2 *xhat, int L, int M, int64_t B,
+                              cudaStream_t st);
+
+// Spectral filter (adjoint = 0) or its input adjoint (adjoint = 1):
+//   adjoint 0: y[b][o][l][m] = sum_i W[l][o][i] x[b][i][l][m]
+//   adjoint 1: y[b][i][l][m] = sum_o conj(W[l][o][i]) x[b][o][l][m]
+// Output is zero for m > l.
+cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L,
+                          int M, int64_t Bm, int Cin, int Cout, int adjoint,
+                          cudaStream_t st);
+
+// Weight adjoint gW[l][o][i] = sum_{b, m <= l} gy[b][o][l][m] conj(x[b][i][l][m]).
+cudaError_t launch_filter_dw(const float2 *gy, const float2 *x, float2 *gW,
+                             int L, int M, int64_t Bm, int Cin, int Cout,
+                             cudaStream_t st);
+
+// FP64 generation of the folded FP32 table on the device.
+cudaError_t launch_table_gen_f32(float *table, const int64_t *off, int Khp,
+                                 const double *xk, const double *sk,
+                                 const double *a, const double *b,
+                                 const double *seed, int L, int M, int Kh,
+                                 cudaStream_t st);
+
+}  // namespace shtgb
+
+// Event record of the per-kernel profiler.
+struct ProfileState {
+  bool on = false;
+  int capacity = 0;
+  int used = 0;
+  int64_t dropped = 0;
+  std::vector<cudaEvent_t> start, stop;
+  std::vector<int> kernel;
+};
+
+// The opaque plan.
+struct sht_plan_s {
+  ProfileState prof;
+  int device = 0;
+  int nlat = 0, nlon = 0, grid = 0, L = 0, M = 0, precision = 0;
+  int64_t max_batch = 0;
+  int Kh = 0;    // ceil(nlat / 2)
+  int Khp = 0;   // Kh padded to a multiple of 16
+  int ldc = 0;   // row stride (floats) of the folded Fourier workspace
+  shtgb::RadixPlan radix{};
+  std::vector<double> x, s, w;  // nodes, sin(theta), latitude weights
+  std::vector<int64_t> tab_off;  // host copy of the table offsets
+  int64_t table_bytes = 0;
+  int64_t workspace_bytes = 0;
+
+  // device memory (all owned)
+  float *d_table = nullptr;
+  int64_t *d_tab_off = nullptr;
+  float2 *d_twiddle = nullptr;
+  float *d_ring_w = nullptr;  // w_k * 2 pi / nlon
+  shtgb::LegTile *d_fwd_tiles = nullptr;
+  int n_fwd_tiles = 0;
+  shtgb::LegTile *d_inv_tiles = nullptr;
+  int n_inv_tiles = 0;
+  float *d_work = nullptr;    // folded Fourier workspace [M][2][Kh][ldc]
+  float2 *d_spec_a = nullptr;  // [max_batch][L][M] spectral buffer
+  float2 *d_spec_b = nullptr;  // [max_batch][L][M] spectral buffer
+};

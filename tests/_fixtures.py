@@ -1,0 +1,78 @@
+"""Seeded inputs and oracle references shared by the GPU parity tests.
+
+Spatial inputs are synthesised from seeded spectral draws by the FP64
+oracle's inverse transform and rounded to float32; the oracle is then run on
+exactly those float32 values (widened to float64), so the GPU and the
+oracle see identical inputs.  Large batches are built from a few base fields
+by amplitude scaling and whole-cell longitude rolls; the oracle result of a
+rolled, scaled field is the base result times scale * exp(-i m phi_roll), so
+only the base fields need the oracle.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+import oracle
+from paper_2507_12144_gb300 import inputs
+
+
+def rel_l2(a, b, axis=None):
+    """||a - b|| / ||b|| (per field when axis is given)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if axis is None:
+        return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+    num = np.sqrt(np.sum(np.abs(a - b) ** 2, axis=axis))
+    den = np.sqrt(np.sum(np.abs(b) ** 2, axis=axis))
+    return num / np.maximum(den, 1e-300)
+
+
+def triangle_mask(L, M):
+    return np.arange(L)[:, None] >= np.arange(M)[None, :]
+
+
+def per_field_spec_err(gpu, ref):
+    """Per-field relative L2 over the stored l >= m triangle."""
+    L, M = ref.shape[-2:]
+    mask = triangle_mask(L, M)
+    g = gpu.reshape(-1, L, M)[:, mask]
+    r = ref.reshape(-1, L, M)[:, mask]
+    return rel_l2(g, r, axis=1)
+
+
+def per_field_spatial_err(gpu, ref):
+    n = ref.shape[-2] * ref.shape[-1]
+    return rel_l2(gpu.reshape(-1, n), ref.reshape(-1, n), axis=1)
+
+
+@functools.lru_cache(maxsize=None)
+def base_fields(nlat, nlon, grid, L, M, nbase, seed, spectrum="l-3"):
+    """float32 fields [nbase, nlat, nlon] from seeded coefficients."""
+    c = inputs.spectral_coeffs(seed, (nbase,), L, M, spectrum=spectrum, nyquist_nlon=nlon)
+    u = oracle.sht_inverse(c, nlat, nlon, grid, L, M)
+    return u.astype(np.float32)
+
+
+@functools.lru_cache(maxsize=None)
+def base_forward(nlat, nlon, grid, L, M, nbase, seed, spectrum="l-3"):
+    u = base_fields(nlat, nlon, grid, L, M, nbase, seed, spectrum)
+    return oracle.sht_forward(u.astype(np.float64), nlat, nlon, grid, L, M)
+
+
+def batch_from_bases(nlat, nlon, grid, L, M, n, nbase, seed, spectrum="l-3"):
+    """(fields float32 [n, nlat, nlon], oracle forward complex128 [n, L, M])."""
+    u = base_fields(nlat, nlon, grid, L, M, nbase, seed, spectrum)
+    c = base_forward(nlat, nlon, grid, L, M, nbase, seed, spectrum)
+    scale, roll = inputs.scales_and_rolls(seed + 1000, n, nlon)
+    # powers of two keep the scaling exact in float32
+    scale = np.exp2(np.round(np.log2(scale)))
+    fields = np.empty((n, nlat, nlon), np.float32)
+    ref = np.empty((n, L, M), np.complex128)
+    m = np.arange(M)
+    for i in range(n):
+        j = i % nbase
+        fields[i] = np.roll(u[j], roll[i], axis=1) * np.float32(scale[i])
+        ref[i] = c[j] * scale[i] * np.exp(-1j * m * 2 * np.pi * roll[i] / nlon)[None, :]
+    return fields, ref

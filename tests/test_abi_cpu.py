@@ -1,0 +1,98 @@
+"""The C ABI library loads, exports every declared symbol and rejects bad
+arguments before touching the GPU (runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sht.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_12144_gb300 import build
+    build.build()
+    from paper_2507_12144_gb300 import _abi
+    return _abi.lib()
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?\**\s*\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared_functions()
+    for required in ["sht_plan", "sht_plan_destroy", "sht_forward", "sht_inverse", "sht_forward_adjoint",
+                     "sht_inverse_adjoint", "spectral_filter", "spectral_filter_adjoint",
+                     "sht_spectral_block", "spectral_filter_inverse", "sht_status_string"]:
+        assert required in names, required
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in sht.h but not exported"
+
+
+def test_binding_covers_the_header():
+    from paper_2507_12144_gb300 import _abi
+    assert set(_declared_functions()) == set(_abi.SIGNATURES)
+
+
+def test_status_strings(lib):
+    for code, name in [(0, b"SHT_OK"), (1, b"SHT_ERR_INVALID_ARG"), (2, b"SHT_ERR_UNSUPPORTED"),
+                       (3, b"SHT_ERR_OOM"), (4, b"SHT_ERR_CUDA"), (5, b"SHT_ERR_TIMEOUT"),
+                       (6, b"SHT_ERR_INTERNAL")]:
+        assert lib.sht_status_string(code) == name
+    assert lib.sht_version().startswith(b"0.")
+
+
+@pytest.mark.parametrize("args,what", [
+    ((33, 64, 7, 32, 32), "grid"),
+    ((0, 64, 0, 32, 32), ">= 1"),
+    ((1, 64, 1, 1, 1), "nlat >= 2"),
+    ((33, 64, 0, 16, 17), "mmax must be <= lmax"),
+    ((33, 60, 0, 33, 32), "mmax must be <= nlon/2 + 1"),
+    ((33, 64, 0, 34, 16), "lmax <= nlat"),
+    ((33, 56, 0, 32, 20), "factor"),       # 56 = 2^3 * 7
+    ((33, 16384, 0, 32, 20), "8192"),
+])
+def test_plan_rejects_bad_sizes_before_any_cuda_call(lib, args, what):
+    h = ctypes.c_void_p()
+    st = lib.sht_plan(ctypes.byref(h), *args, None)
+    assert st in (1, 2)
+    assert what in lib.sht_last_error_message().decode()
+    assert not h.value
+
+
+def test_execute_calls_reject_null_plan(lib):
+    assert lib.sht_forward(None, None, None, 1, None) == 1
+    assert lib.sht_inverse(None, None, None, 1, None) == 1
+    assert lib.spectral_filter(None, None, None, None, 1, 1, 1, None) == 1
+    assert lib.sht_plan_destroy(None) == 1
+    assert b"NULL" in lib.sht_last_error_message()
+
+
+def test_reserved_options_must_be_zero(lib):
+    from paper_2507_12144_gb300 import _abi
+    o = _abi.sht_plan_opts()
+    lib.sht_plan_opts_default(ctypes.byref(o))
+    assert o.max_batch == 256 and o.precision == 0 and o.device == -1
+    o.reserved[3] = 1
+    h = ctypes.c_void_p()
+    assert lib.sht_plan(ctypes.byref(h), 33, 64, 0, 32, 32, ctypes.byref(o)) == 1
+    o.reserved[3] = 0
+    o.max_batch = 0
+    assert lib.sht_plan(ctypes.byref(h), 33, 64, 0, 32, 32, ctypes.byref(o)) == 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2507_12144_gb300 import _abi
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _abi.lib()

@@ -495,3 +495,22 @@ def test_block_gradient_by_fd_small_copy():
     D = inputs.filter_weights(44, L, C, C)
     fdw = (loss(x, W + eps * D) - loss(x, W - eps * D)) / (2 * eps)
     assert abs(fdw - _rip(D, gW)) < 1e-8 * (1 + abs(fdw))
+
+
+def test_row_and_degree_ranges_partition_the_full_transforms():
+    """The range-restricted loops used for timing samples add up to the
+    full transforms."""
+    nlat, nlon, L, grid = 17, 32, 16, "equiangular_cc"
+    u = inputs.spatial_noise(50, (2, nlat, nlon))
+    full = oracle.sht_forward(u, nlat, nlon, grid, L, L)
+    parts = sum(oracle.sht_forward_rows(u, nlat, nlon, grid, L, L, k0, min(k0 + 5, nlat))
+                for k0 in range(0, nlat, 5))
+    np.testing.assert_allclose(parts, full, atol=1e-14)
+    y = inputs.spectral_coeffs(51, (2,), L, L)
+    inv = oracle.sht_inverse(y, nlat, nlon, grid, L, L)
+    np.testing.assert_allclose(oracle.sht_inverse_rows(y, nlat, nlon, grid, L, L, 3, 9)[:, 3:9], inv[:, 3:9],
+                               atol=1e-14)
+    x = inputs.spectral_coeffs(52, (1, 3), L, L)
+    W = inputs.filter_weights(53, L, 2, 3)
+    f = oracle.spectral_filter(x, W)
+    np.testing.assert_allclose(oracle.spectral_filter_degrees(x, W, 4, 11)[:, :, 4:11], f[:, :, 4:11], atol=1e-15)
