@@ -183,6 +183,27 @@ sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,
                                      const void *W, float *y, int64_t Bm,
                                      int Cin, int Cout, void *stream);
 
+/* Forward SHT that allocates nothing: the same result as sht_forward, with
+ * its scratch (the folded longitude coefficients of a chunk of fields) in a
+ * 16 MiB static device array compiled into the library instead of the
+ * plan's workspace.  The paper has no counterpart.  It is meant for callers
+ * that may not request device memory while they run: hosts that own all
+ * device memory through their own pool and forbid cudaMalloc in plug-ins,
+ * or services held to a fixed memory budget.  The plan itself must have
+ * been made beforehand (sht_plan allocates its tables).
+ *   - Limit: one field of the plan's grid must fit, i.e. 16 * mmax *
+ *     ceil(nlat/2) bytes <= 16 MiB; larger grids get SHT_ERR_INVALID_ARG.
+ *     Larger batches are processed in chunks that fit.
+ *   - FP32 plans only (SHT_ERR_UNSUPPORTED otherwise).
+ *   - The array exists once per GPU that loads the library and stays until
+ *     the process exits.  Every call on a device shares it: calls whose
+ *     work overlaps on the GPU (two streams, or two host threads) race.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture. */
+sht_status_t sht_forward_static_scratch(sht_plan_t plan, const float *x,
+                                        void *xhat, int64_t B, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Per-kernel timing.  While profiling is on, every kernel a plan's execute
  * calls launch is bracketed by two CUDA events recorded on the launch

@@ -43,6 +43,7 @@ SIGNATURES = {
     "spectral_filter_adjoint": ([_p, _p, _p, _p, _p, _p, _i64, _i, _i, _p], _i),
     "sht_spectral_block": ([_p, _p, _p, _p, _i64, _i, _i, _p], _i),
     "spectral_filter_inverse": ([_p, _p, _p, _p, _i64, _i, _i, _p], _i),
+    "sht_forward_static_scratch": ([_p, _p, _p, _i64, _p], _i),
     "sht_profile_begin": ([_p, _i], _i),
     "sht_profile_collect": ([_p, _i64p, ctypes.POINTER(ctypes.c_double), _i64p], _i),
     "sht_profile_end": ([_p], _i),
