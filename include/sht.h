@@ -86,10 +86,14 @@ typedef enum {
 } sht_status_t;
 
 /* Arithmetic of the Legendre contractions (the dominant cost, Sec. B.3).
+ * With a = a_hi + a_lo, a_hi = bf16(a), a_lo = bf16(a - a_hi):
  * FP32: FP32 table and data, FP32 accumulation (CUDA cores).
- * BF16: table and data rounded to bf16, FP32 accumulation (tensor cores).
- * SPLIT_BF16: a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi);
- *   products hi*hi + hi*lo + lo*hi on the tensor cores, FP32 accumulation.
+ * BF16: data rounded to bf16, table split; T_hi D + T_lo D on the tensor
+ *   cores (tcgen05, operands by TMA), FP32 accumulation.  The table keeps
+ *   its lo part because a bf16-rounded table carries errors shared by every
+ *   field, up to the bf16 unit roundoff 2^-8.
+ * SPLIT_BF16: table and data split; T_hi D_hi + T_hi D_lo + T_lo D_hi,
+ *   FP32 accumulation.
  * Training in the paper uses bf16 mixed precision (Sec. E.3). */
 typedef enum {
   SHT_PREC_FP32 = 0,
@@ -127,6 +131,12 @@ sht_status_t sht_plan_info(sht_plan_t plan, int *nlat, int *nlon, int *grid,
                            int *lmax, int *mmax, int *precision,
                            int64_t *max_batch, int64_t *table_bytes,
                            int64_t *workspace_bytes);
+
+/* Wait for all work on the plan's device (cudaDeviceSynchronize) and report
+ * device-side failures of the plan's kernels: SHT_ERR_TIMEOUT when a bounded
+ * wait of a tensor-core kernel gave up (the error word is then cleared),
+ * SHT_ERR_CUDA for a pending CUDA error, else SHT_OK. */
+sht_status_t sht_plan_check(sht_plan_t plan);
 
 /* Copy the plan's latitude nodes x_k = cos(theta_k) and weights w_k (FP64,
  * host arrays of nlat entries; the 2-D weight is w_k * 2 pi / nlon).
@@ -220,7 +230,8 @@ typedef enum {
   SHT_KERNEL_FILTER_DW = 4,  /* weight adjoint of the filter              */
   SHT_KERNEL_LEG_INV = 5,    /* inverse Legendre contraction              */
   SHT_KERNEL_C2R = 6,        /* longitude synthesis (inverse FFT)         */
-  SHT_KERNEL_COUNT = 7
+  SHT_KERNEL_PACK = 7,       /* API coefficients -> internal bf16 rows    */
+  SHT_KERNEL_COUNT = 8
 } sht_kernel_t;
 
 /* Start recording (capacity >= 1 launches); creates the events on the

@@ -100,6 +100,11 @@ class Plan:
         _abi.check(_abi.lib().sht_plan_grid(self.handle, x.ctypes.data_as(dp), w.ctypes.data_as(dp)))
         return x, w
 
+    def check(self) -> None:
+        """Synchronise the device and raise if a kernel of this plan reported
+        a device-side failure (a bounded wait that timed out)."""
+        _abi.check(_abi.lib().sht_plan_check(self.handle))
+
     # -- per-kernel timing (CUDA events on the launch stream) ----------------
     def profile_begin(self, capacity: int = 65536) -> None:
         _abi.check(_abi.lib().sht_profile_begin(self.handle, int(capacity)))

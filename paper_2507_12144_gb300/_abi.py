@@ -17,7 +17,7 @@ STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3: "S
           4: "SHT_ERR_CUDA", 5: "SHT_ERR_TIMEOUT", 6: "SHT_ERR_INTERNAL"}
 GRIDS = {"gauss": 0, "equiangular_cc": 1, "equiangular_trapz": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "split_bf16": 2}
-KERNEL_COUNT = 7
+KERNEL_COUNT = 8
 
 
 class sht_plan_opts(ctypes.Structure):
@@ -35,6 +35,7 @@ SIGNATURES = {
     "sht_plan_destroy": ([_p], _i),
     "sht_plan_info": ([_p, _ip, _ip, _ip, _ip, _ip, _ip, _i64p, _i64p, _i64p], _i),
     "sht_plan_grid": ([_p, _d, _d], _i),
+    "sht_plan_check": ([_p], _i),
     "sht_forward": ([_p, _p, _p, _i64, _p], _i),
     "sht_inverse": ([_p, _p, _p, _i64, _p], _i),
     "sht_forward_adjoint": ([_p, _p, _p, _i64, _p], _i),

@@ -29,6 +29,12 @@ sht_status_t cuda_fail(cudaError_t err, const char *what) {
 
 namespace {
 
+#define SHT_TRY(expr)                    \
+  do {                                   \
+    sht_status_t _s = (expr);            \
+    if (_s != SHT_OK) return _s;         \
+  } while (0)
+
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 struct DeviceGuard {
@@ -165,6 +171,16 @@ void free_plan(sht_plan_s *p) {
   if (!p) return;
   DeviceGuard g(p->device);
   profile_release(p->prof);
+  cudaFree(p->d_err);
+  cudaFree(p->d_tf_hi);
+  cudaFree(p->d_tf_lo);
+  cudaFree(p->d_ti_hi);
+  cudaFree(p->d_ti_lo);
+  cudaFree(p->d_roff);
+  cudaFree(p->d_soff);
+  cudaFree(p->d_rows);
+  cudaFree(p->d_s_hi);
+  cudaFree(p->d_s_lo);
   cudaFree(p->d_table);
   cudaFree(p->d_tab_off);
   cudaFree(p->d_twiddle);
@@ -214,26 +230,79 @@ void profile_release(ProfileState &pr) {
 
 // ---- chunked execute bodies -------------------------------------------------
 
+bool is_tc(const sht_plan_s *p) { return p->precision != SHT_PREC_FP32; }
+
+__nv_bfloat16 *f_hi(sht_plan_s *p) { return reinterpret_cast<__nv_bfloat16 *>(p->d_work); }
+__nv_bfloat16 *f_lo(sht_plan_s *p) { return f_hi(p) + (size_t)p->M * 2 * p->Kh * p->ldcb; }
+// The lo half of the data exists only for split precision.
+__nv_bfloat16 *data_lo(sht_plan_s *p, __nv_bfloat16 *lo) { return p->precision == SHT_PREC_SPLIT_BF16 ? lo : nullptr; }
+
+// Forward transform (or the inverse adjoint) of B fields; the coefficients
+// go to the API layout xhat, or, when rows_out is set (tensor-core plans
+// only), to the internal rows.
 sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cudaStream_t st, bool adjoint,
-                      bool zero_upper) {
+                      bool zero_upper, float *rows_out = nullptr) {
   const int64_t LM = (int64_t)p->L * p->M;
   for (int64_t b0 = 0; b0 < B; b0 += p->max_batch) {
     const int nb = (int)std::min<int64_t>(p->max_batch, B - b0);
-    cudaError_t e = traced(p, SHT_KERNEL_R2C, st, [&] {
-      return launch_r2c(x + b0 * p->nlat * (int64_t)p->nlon, p->d_work, p->nlat, p->nlon, p->M, nb, p->ldc,
-                        p->d_twiddle, p->radix, adjoint ? nullptr : p->d_ring_w, adjoint ? 1 : 0, st);
-    });
-    if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
-    e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
-      return launch_leg_fwd_f32(table_view(p), p->d_fwd_tiles, p->n_fwd_tiles, p->d_work, xhat + b0 * LM, p->L,
-                                p->M, p->Kh, p->ldc, nb, st);
-    });
+    const float *xb = x + b0 * p->nlat * (int64_t)p->nlon;
+    const float *ring = adjoint ? nullptr : p->d_ring_w;
+    const int wts = adjoint ? 1 : 0;
+    cudaError_t e;
+    if (!is_tc(p)) {
+      e = traced(p, SHT_KERNEL_R2C, st, [&] {
+        if (fft45_supported(p->nlon))
+          return launch_r2c45(xb, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle,
+                              ring, wts, st);
+        return launch_r2c(xb, p->d_work, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, p->radix, ring, wts, st);
+      });
+      if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
+      e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
+        return launch_leg_fwd_f32(table_view(p), p->d_fwd_tiles, p->n_fwd_tiles, p->d_work, xhat + b0 * LM, p->L,
+                                  p->M, p->Kh, p->ldc, nb, st);
+      });
+    } else {
+      e = traced(p, SHT_KERNEL_R2C, st, [&] {
+        if (fft45_supported(p->nlon))
+          return launch_r2c45(xb, nullptr, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->ldcb,
+                              p->d_twiddle, ring, wts, st);
+        return launch_r2c_bf16(xb, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->ldcb, p->d_twiddle,
+                               p->radix, ring, wts, st);
+      });
+      if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
+      e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
+        return launch_leg_fwd_tc(p->tc, p->d_fwd_tiles, p->n_fwd_tiles, rows_out ? nullptr : xhat + b0 * LM,
+                                 rows_out, p->ldc, nb, st);
+      });
+    }
     if (e != cudaSuccess) return cuda_fail(e, "forward Legendre launch");
-    if (zero_upper) {
+    if (zero_upper && !rows_out) {
       e = traced(p, SHT_KERNEL_ZERO, st, [&] { return launch_zero_upper(xhat + b0 * LM, p->L, p->M, nb, st); });
       if (e != cudaSuccess) return cuda_fail(e, "zero fill launch");
     }
+    if (rows_out && B > p->max_batch) return fail(SHT_ERR_INTERNAL, "internal rows hold one chunk only");
   }
+  return SHT_OK;
+}
+
+// Longitude synthesis from the FP32 folded workspace.
+cudaError_t c2r_any(sht_plan_s *p, float *y, int nb, bool adjoint, cudaStream_t st) {
+  const float *ring = adjoint ? p->d_ring_w : nullptr;
+  const int wts = adjoint ? 0 : 1;
+  if (fft45_supported(p->nlon))
+    return launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, ring, wts, st);
+  return launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, p->radix, ring, wts, st);
+}
+
+// Inverse Legendre + longitude synthesis of B fields whose coefficients are
+// already in the tensor-core internal rows (bf16 hi/lo).
+sht_status_t synthesis_rows(sht_plan_s *p, float *y, int nb, cudaStream_t st, bool adjoint) {
+  cudaError_t e = traced(p, SHT_KERNEL_LEG_INV, st, [&] {
+    return launch_leg_inv_tc(p->tc, p->d_inv_tiles, p->n_inv_tiles, p->d_work, p->ldc, nb, st);
+  });
+  if (e != cudaSuccess) return cuda_fail(e, "inverse Legendre launch");
+  e = traced(p, SHT_KERNEL_C2R, st, [&] { return c2r_any(p, y, nb, adjoint, st); });
+  if (e != cudaSuccess) return cuda_fail(e, "longitude synthesis launch");
   return SHT_OK;
 }
 
@@ -241,15 +310,22 @@ sht_status_t synthesis(sht_plan_s *p, const float2 *yhat, float *y, int64_t B, c
   const int64_t LM = (int64_t)p->L * p->M;
   for (int64_t b0 = 0; b0 < B; b0 += p->max_batch) {
     const int nb = (int)std::min<int64_t>(p->max_batch, B - b0);
+    float *yb = y + b0 * p->nlat * (int64_t)p->nlon;
+    if (is_tc(p)) {
+      cudaError_t e = traced(p, SHT_KERNEL_PACK, st, [&] {
+        return launch_pack_rows(yhat + b0 * LM, p->d_s_hi, data_lo(p, p->d_s_lo), p->d_soff, p->L, p->M, p->ldcb, nb,
+                                st);
+      });
+      if (e != cudaSuccess) return cuda_fail(e, "coefficient repack launch");
+      SHT_TRY(synthesis_rows(p, yb, nb, st, adjoint));
+      continue;
+    }
     cudaError_t e = traced(p, SHT_KERNEL_LEG_INV, st, [&] {
       return launch_leg_inv_f32(table_view(p), p->d_inv_tiles, p->n_inv_tiles, yhat + b0 * LM, p->d_work, p->L,
                                 p->M, p->Kh, p->ldc, nb, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "inverse Legendre launch");
-    e = traced(p, SHT_KERNEL_C2R, st, [&] {
-      return launch_c2r(p->d_work, y + b0 * p->nlat * (int64_t)p->nlon, p->nlat, p->nlon, p->M, nb, p->ldc,
-                        p->d_twiddle, p->radix, adjoint ? p->d_ring_w : nullptr, adjoint ? 0 : 1, st);
-    });
+    e = traced(p, SHT_KERNEL_C2R, st, [&] { return c2r_any(p, yb, nb, adjoint, st); });
     if (e != cudaSuccess) return cuda_fail(e, "longitude synthesis launch");
   }
   return SHT_OK;
@@ -293,11 +369,6 @@ sht_status_t check_channels(sht_plan_s *p, int Cin, int Cout, bool block) {
   return SHT_OK;
 }
 
-#define SHT_TRY(expr)                    \
-  do {                                   \
-    sht_status_t _s = (expr);            \
-    if (_s != SHT_OK) return _s;         \
-  } while (0)
 
 }  // namespace
 }  // namespace shtgb
@@ -336,8 +407,6 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   if (nlon > kMaxNlon) return fail(SHT_ERR_UNSUPPORTED, "nlon above 8192 is not supported");
   RadixPlan rp;
   if (!factor_radix(nlon, rp)) return fail(SHT_ERR_UNSUPPORTED, "nlon must factor into 2, 3 and 5");
-  if (o.precision != SHT_PREC_FP32)
-    return fail(SHT_ERR_UNSUPPORTED, "this build implements the FP32 Legendre path only");
 
   int dev = o.device;
   if (dev < 0) {
@@ -384,9 +453,11 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   p->tab_off = off;
   p->table_bytes = acc * (int64_t)sizeof(float);
 
-  // tile lists (row tiles of 64)
+  // tile lists: row tiles of 64 (CUDA cores) or 128 (tensor cores)
+  const bool tc = o.precision != SHT_PREC_FP32;
+  const int trow = tc ? 128 : 64;
   std::vector<LegTile> ft, it;
-  for (int r0 = 0; r0 < (lmax + 1) / 2 + 1; r0 += 64)
+  for (int r0 = 0; r0 < (lmax + 1) / 2 + 1; r0 += trow)
     for (int m = 0; m < mmax; m++)
       for (int q = 0; q < 2; q++)
         if (r0 < leg_rows(lmax, m, q)) ft.push_back(LegTile{m, q, r0});
@@ -394,13 +465,20 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   // odd parity): its tiles write the zeros that the synthesis reads
   for (int m = 0; m < mmax; m++)
     for (int q = 0; q < 2; q++)
-      for (int k0 = 0; k0 < p->Kh; k0 += 64) it.push_back(LegTile{m, q, k0});
+      for (int k0 = 0; k0 < p->Kh; k0 += trow) it.push_back(LegTile{m, q, k0});
   p->n_fwd_tiles = (int)ft.size();
   p->n_inv_tiles = (int)it.size();
 
   // device tables
-  if ((e = dev_alloc((void **)&p->d_table, (size_t)p->table_bytes)) != cudaSuccess) return bail(e, "table allocation");
-  if ((e = cudaMemset(p->d_table, 0, (size_t)p->table_bytes)) != cudaSuccess) return bail(e, "table memset");
+  if ((e = dev_alloc((void **)&p->d_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
+  if ((e = cudaMemset(p->d_err, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word memset");
+  if (!tc) {
+    if ((e = dev_alloc((void **)&p->d_table, (size_t)p->table_bytes)) != cudaSuccess)
+      return bail(e, "table allocation");
+    if ((e = cudaMemset(p->d_table, 0, (size_t)p->table_bytes)) != cudaSuccess) return bail(e, "table memset");
+  } else {
+    p->table_bytes = 0;
+  }
   if ((e = upload(&p->d_tab_off, off)) != cudaSuccess) return bail(e, "offset upload");
   if ((e = upload(&p->d_fwd_tiles, ft)) != cudaSuccess) return bail(e, "tile upload");
   if ((e = upload(&p->d_inv_tiles, it)) != cudaSuccess) return bail(e, "tile upload");
@@ -431,8 +509,55 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     if (e == cudaSuccess) e = upload(&d_a, a);
     if (e == cudaSuccess) e = upload(&d_b, b);
     if (e == cudaSuccess) e = upload(&d_seed, seed);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !tc)
       e = launch_table_gen_f32(p->d_table, p->d_tab_off, p->Khp, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
+    if (e == cudaSuccess && tc) {
+      // bf16 hi/lo tables: forward [rows][Kp64], transposed [(2m+p) Kh + k'][Ip64]
+      const bool split = o.precision == SHT_PREC_SPLIT_BF16;
+      std::vector<int> roff(2 * (size_t)mmax), soff(2 * (size_t)mmax);
+      int64_t frows = 0, srows = 0;
+      for (int m = 0; m < mmax; m++)
+        for (int q = 0; q < 2; q++) {
+          roff[2 * m + q] = (int)frows;
+          soff[2 * m + q] = (int)srows;
+          frows += leg_rows(lmax, m, q);
+          srows += (leg_rows(lmax, m, q) + 63) / 64 * 64;
+        }
+      p->srows = srows;
+      const int Kp64 = (p->Kh + 63) / 64 * 64;
+      const int Ip64 = (leg_rows(lmax, 0, 0) + 63) / 64 * 64;
+      const int64_t irows = (int64_t)mmax * 2 * p->Kh;
+      const size_t fbytes = sizeof(__nv_bfloat16) * (size_t)frows * Kp64;
+      const size_t ibytes = sizeof(__nv_bfloat16) * (size_t)irows * Ip64;
+      e = upload(&p->d_roff, roff);
+      if (e == cudaSuccess) e = upload(&p->d_soff, soff);
+      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_hi, fbytes);
+      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_hi, ibytes);
+      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_lo, fbytes);
+      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_lo, ibytes);
+      if (e == cudaSuccess) e = cudaMemset(p->d_tf_hi, 0, fbytes);
+      if (e == cudaSuccess) e = cudaMemset(p->d_ti_hi, 0, ibytes);
+      if (e == cudaSuccess) e = cudaMemset(p->d_tf_lo, 0, fbytes);
+      if (e == cudaSuccess) e = cudaMemset(p->d_ti_lo, 0, ibytes);
+      if (e == cudaSuccess)
+        e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_ti_hi, p->d_ti_lo, p->d_roff, Kp64, Ip64, d_x, d_s,
+                                  d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
+      p->table_bytes = (int64_t)(fbytes + ibytes) * 2;
+      TcPlanView &T = p->tc;
+      T.roff = p->d_roff;
+      T.soff = p->d_soff;
+      T.L = lmax;
+      T.M = mmax;
+      T.Kh = p->Kh;
+      T.split = split;
+      T.err = p->d_err;
+      if (e == cudaSuccess &&
+          !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, Kp64, frows, 64, 128) &&
+            tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, Kp64, frows, 64, 128) &&
+            tc_encode_2d(&T.tab_inv_hi, p->d_ti_hi, Ip64, irows, 64, 128) &&
+            tc_encode_2d(&T.tab_inv_lo, p->d_ti_lo, Ip64, irows, 64, 128)))
+        e = cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_x);
     cudaFree(d_s);
@@ -443,13 +568,36 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   }
 
   // workspaces
-  const size_t work = sizeof(float) * (size_t)mmax * 2 * p->Kh * p->ldc;
+  p->ldcb = (int)std::max<int64_t>(64, (2 * o.max_batch + 7) / 8 * 8);
+  const size_t frow = (size_t)mmax * 2 * p->Kh;
+  const size_t work = std::max(sizeof(float) * frow * p->ldc, tc ? 2 * sizeof(__nv_bfloat16) * frow * p->ldcb : 0);
   const size_t spec = sizeof(float2) * (size_t)o.max_batch * lmax * mmax;
+  size_t extra = 0;
   if ((e = dev_alloc((void **)&p->d_work, work)) != cudaSuccess) return bail(e, "workspace allocation");
-  if ((e = dev_alloc((void **)&p->d_spec_a, spec)) != cudaSuccess) return bail(e, "workspace allocation");
+  if (!tc && (e = dev_alloc((void **)&p->d_spec_a, spec)) != cudaSuccess) return bail(e, "workspace allocation");
   if ((e = dev_alloc((void **)&p->d_spec_b, spec)) != cudaSuccess) return bail(e, "workspace allocation");
   if ((e = cudaMemset(p->d_work, 0, work)) != cudaSuccess) return bail(e, "workspace memset");
-  p->workspace_bytes = (int64_t)(work + 2 * spec);
+  if (tc) {
+    const size_t rbytes = sizeof(float) * (size_t)p->srows * p->ldc;
+    const size_t sbytes = sizeof(__nv_bfloat16) * (size_t)p->srows * p->ldcb;
+    if ((e = dev_alloc((void **)&p->d_rows, rbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = dev_alloc((void **)&p->d_s_hi, sbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = dev_alloc((void **)&p->d_s_lo, sbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = cudaMemset(p->d_rows, 0, rbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    if ((e = cudaMemset(p->d_s_hi, 0, sbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    if ((e = cudaMemset(p->d_s_lo, 0, sbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    extra = rbytes + 2 * sbytes;
+    TcPlanView &T = p->tc;
+    if (!(tc_encode_2d(&T.f_hi, f_hi(p), p->ldcb, (int64_t)frow, 64, 64) &&
+          tc_encode_2d(&T.f_lo, f_lo(p), p->ldcb, (int64_t)frow, 64, 64) &&
+          tc_encode_2d(&T.s_hi, p->d_s_hi, p->ldcb, p->srows, 64, 64) &&
+          tc_encode_2d(&T.s_lo, p->d_s_lo, p->ldcb, p->srows, 64, 64))) {
+      free_plan(p);
+      return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspaces");
+    }
+  }
+  p->workspace_bytes = (int64_t)(work + (tc ? 1 : 2) * spec + extra);
+
   *out = p;
   return SHT_OK;
 }
@@ -579,6 +727,18 @@ sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, flo
   const int64_t npix = (int64_t)p->nlat * p->nlon;
   for (int64_t b0 = 0; b0 < Bm; b0 += per) {
     const int64_t nb = std::min(per, Bm - b0);
+    if (is_tc(p)) {
+      // internal rows end to end: FP32 rows after the forward contraction,
+      // bf16 hi/lo rows after the filter
+      SHT_TRY(analysis(p, x + b0 * Cin * npix, nullptr, nb * Cin, st, false, false, p->d_rows));
+      cudaError_t e = traced(p, SHT_KERNEL_FILTER, st, [&] {
+        return launch_filter_rows(p->d_rows, p->ldc, (const float2 *)W, p->d_s_hi, data_lo(p, p->d_s_lo), p->ldcb,
+                                  p->d_soff, p->L, p->M, (int)nb, Cin, Cout, st);
+      });
+      if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+      SHT_TRY(synthesis_rows(p, y + b0 * Cout * npix, (int)(nb * Cout), st, false));
+      continue;
+    }
     SHT_TRY(analysis(p, x + b0 * Cin * npix, p->d_spec_a, nb * Cin, st, false, false));
     SHT_TRY(filter_body(p, p->d_spec_a, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 0, st));
     SHT_TRY(synthesis(p, p->d_spec_b, y + b0 * Cout * npix, nb * Cout, st, false));
@@ -604,6 +764,21 @@ sht_status_t spectral_filter_inverse(sht_plan_t p, const void *xhat, const void 
     const int64_t nb = std::min(per, Bm - b0);
     SHT_TRY(filter_body(p, (const float2 *)xhat + b0 * Cin * LM, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 0, st));
     SHT_TRY(synthesis(p, p->d_spec_b, y + b0 * Cout * npix, nb * Cout, st, false));
+  }
+  return SHT_OK;
+}
+
+sht_status_t sht_plan_check(sht_plan_t p) {
+  SHT_TRY(check_plan(p));
+  DeviceGuard g(p->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
+  unsigned word = 0;
+  e = cudaMemcpy(&word, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error word read");
+  if (word != 0) {
+    cudaMemset(p->d_err, 0, sizeof(unsigned));
+    return fail(SHT_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel timed out");
   }
   return SHT_OK;
 }
@@ -670,7 +845,7 @@ sht_status_t sht_profile_end(sht_plan_t p) {
 
 const char *sht_kernel_name(int k) {
   static const char *names[SHT_KERNEL_COUNT] = {"r2c", "leg_fwd", "zero_upper", "filter", "filter_dw", "leg_inv",
-                                                "c2r"};
+                                                "c2r", "pack"};
   return (k >= 0 && k < SHT_KERNEL_COUNT) ? names[k] : "?";
 }
 

@@ -114,8 +114,25 @@ __device__ __forceinline__ float mode_weight(int m, int n, int inverse_weights) 
   return 2.0f;
 }
 
+// Output of the analysis: FP32 pairs, or bf16 hi/lo pairs (split).
+struct OutF32 {
+  float *F;
+  __device__ __forceinline__ void put(int64_t idx, float2 v) const { *reinterpret_cast<float2 *>(F + idx) = v; }
+};
+struct OutBF16 {
+  __nv_bfloat16 *hi, *lo;
+  __device__ __forceinline__ void put(int64_t idx, float2 v) const {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+    *reinterpret_cast<__nv_bfloat162 *>(hi + idx) = h;
+    if (lo) *reinterpret_cast<__nv_bfloat162 *>(lo + idx) = l;
+  }
+};
+
+template <class Out>
 __global__ void __launch_bounds__(kThreads)
-r2c_pairs_kernel(const float *__restrict__ x, float *__restrict__ Fw, int nlat, int nlon, int M, int B, int ldc,
+r2c_pairs_kernel(const float *__restrict__ x, Out out, int nlat, int nlon, int M, int B, int ldc,
                  const float2 *__restrict__ twiddle, RadixPlan rp, const float *__restrict__ ring_scale,
                  int inverse_weights) {
   extern __shared__ float2 smem[];
@@ -163,8 +180,8 @@ r2c_pairs_kernel(const float *__restrict__ x, float *__restrict__ Fw, int nlat, 
       O = csub(Fk, Fs);
     }
     const int64_t col = 2 * (int64_t)(b0 + f);
-    *reinterpret_cast<float2 *>(Fw + (((int64_t)m * 2 + 0) * Kh + kp) * ldc + col) = E;
-    *reinterpret_cast<float2 *>(Fw + (((int64_t)m * 2 + 1) * Kh + kp) * ldc + col) = O;
+    out.put((((int64_t)m * 2 + 0) * Kh + kp) * ldc + col, E);
+    out.put((((int64_t)m * 2 + 1) * Kh + kp) * ldc + col, O);
   }
 }
 
@@ -258,10 +275,24 @@ cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M, int
   const int Kh = (nlat + 1) / 2;
   dim3 grid((B + kFields - 1) / kFields, Kh);
   size_t smem = fft_smem_bytes(nlon, 2);
-  cudaError_t e = set_smem((const void *)r2c_pairs_kernel, smem);
+  cudaError_t e = set_smem((const void *)r2c_pairs_kernel<OutF32>, smem);
   if (e != cudaSuccess) return e;
-  r2c_pairs_kernel<<<grid, kThreads, smem, st>>>(x, Fw, nlat, nlon, M, B, ldc, twiddle, rp, ring_scale,
-                                                 inverse_weights);
+  r2c_pairs_kernel<OutF32><<<grid, kThreads, smem, st>>>(x, OutF32{Fw}, nlat, nlon, M, B, ldc, twiddle, rp,
+                                                         ring_scale, inverse_weights);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,
+                            int ldb, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
+                            int inverse_weights, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  const int Kh = (nlat + 1) / 2;
+  dim3 grid((B + kFields - 1) / kFields, Kh);
+  size_t smem = fft_smem_bytes(nlon, 2);
+  cudaError_t e = set_smem((const void *)r2c_pairs_kernel<OutBF16>, smem);
+  if (e != cudaSuccess) return e;
+  r2c_pairs_kernel<OutBF16><<<grid, kThreads, smem, st>>>(x, OutBF16{Fhi, Flo}, nlat, nlon, M, B, ldb, twiddle, rp,
+                                                          ring_scale, inverse_weights);
   return cudaGetLastError();
 }
 

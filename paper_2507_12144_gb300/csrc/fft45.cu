@@ -1,0 +1,435 @@
+// Longitude transforms for nlon = 45 P (P = 4, 8, 16, 32: the 2, 1, 0.5 and
+// 0.25 degree grids with nlon = 180, 360, 720, 1440), as a "four-step" FFT
+// with the whole sequence in registers:
+//   n = t + P j (lane t < P, register j < 45),  k = k2 + 45 k1,
+//   X[k2 + 45 k1] = sum_t w_P^{t k1} w_N^{t k2} sum_j x[t + P j] w_45^{j k2}.
+// Each lane does one 45-point DFT in registers (radices 5, 3, 3), multiplies
+// by w_N^{t k2}, writes the 45 values to a padded row-per-k2 buffer, and then
+// runs P-point DFTs (radix 4/2, in registers) on the rows it owns, writing
+// them back in place.  Only warp-level synchronisation is needed inside a
+// transform.  As in the generic kernels, the two mirror rows (k, nlat-1-k) of
+// one field are packed into one complex sequence and separated afterwards;
+// a CTA handles 8 fields of 32 / P ring pairs so that the folded output rows
+// are written in contiguous 8-field segments.
+#include "sht_internal.cuh"
+
+namespace shtgb {
+namespace {
+
+constexpr int kQ = 45;
+constexpr int kThreads = 256;
+constexpr int kFB = 8;  // fields per CTA
+
+// exp(-2 pi i k / 45), k = 0..44 (rounded from double precision)
+__constant__ float2 kRoot45[45] = {
+    {1.000000000e+00f, 0.000000000e+00f}, {9.902680687e-01f, -1.391731010e-01f}, {9.612616959e-01f, -2.756373558e-01f},
+    {9.135454576e-01f, -4.067366431e-01f}, {8.480480962e-01f, -5.299192642e-01f}, {7.660444431e-01f, -6.427876097e-01f},
+    {6.691306064e-01f, -7.431448255e-01f}, {5.591929035e-01f, -8.290375726e-01f}, {4.383711468e-01f, -8.987940463e-01f},
+    {3.090169944e-01f, -9.510565163e-01f}, {1.736481777e-01f, -9.848077530e-01f}, {3.489949670e-02f, -9.993908270e-01f},
+    {-1.045284633e-01f, -9.945218954e-01f}, {-2.419218956e-01f, -9.702957263e-01f}, {-3.746065934e-01f, -9.271838546e-01f},
+    {-5.000000000e-01f, -8.660254038e-01f}, {-6.156614753e-01f, -7.880107536e-01f}, {-7.193398003e-01f, -6.946583705e-01f},
+    {-8.090169944e-01f, -5.877852523e-01f}, {-8.829475929e-01f, -4.694715628e-01f}, {-9.396926208e-01f, -3.420201433e-01f},
+    {-9.781476007e-01f, -2.079116908e-01f}, {-9.975640503e-01f, -6.975647374e-02f}, {-9.975640503e-01f, 6.975647374e-02f},
+    {-9.781476007e-01f, 2.079116908e-01f}, {-9.396926208e-01f, 3.420201433e-01f}, {-8.829475929e-01f, 4.694715628e-01f},
+    {-8.090169944e-01f, 5.877852523e-01f}, {-7.193398003e-01f, 6.946583705e-01f}, {-6.156614753e-01f, 7.880107536e-01f},
+    {-5.000000000e-01f, 8.660254038e-01f}, {-3.746065934e-01f, 9.271838546e-01f}, {-2.419218956e-01f, 9.702957263e-01f},
+    {-1.045284633e-01f, 9.945218954e-01f}, {3.489949670e-02f, 9.993908270e-01f}, {1.736481777e-01f, 9.848077530e-01f},
+    {3.090169944e-01f, 9.510565163e-01f}, {4.383711468e-01f, 8.987940463e-01f}, {5.591929035e-01f, 8.290375726e-01f},
+    {6.691306064e-01f, 7.431448255e-01f}, {7.660444431e-01f, 6.427876097e-01f}, {8.480480962e-01f, 5.299192642e-01f},
+    {9.135454576e-01f, 4.067366431e-01f}, {9.612616959e-01f, 2.756373558e-01f}, {9.902680687e-01f, 1.391731010e-01f},
+};
+// exp(-2 pi i k / 32), k = 0..31 (rounded from double precision)
+__constant__ float2 kRoot32[32] = {
+    {1.000000000e+00f, 0.000000000e+00f}, {9.807852804e-01f, -1.950903220e-01f}, {9.238795325e-01f, -3.826834324e-01f},
+    {8.314696123e-01f, -5.555702330e-01f}, {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f},
+    {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f}, {0.000000000e+00f, -1.000000000e+00f},
+    {-1.950903220e-01f, -9.807852804e-01f}, {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
+    {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f}, {-9.238795325e-01f, -3.826834324e-01f},
+    {-9.807852804e-01f, -1.950903220e-01f}, {-1.000000000e+00f, 0.000000000e+00f}, {-9.807852804e-01f, 1.950903220e-01f},
+    {-9.238795325e-01f, 3.826834324e-01f}, {-8.314696123e-01f, 5.555702330e-01f}, {-7.071067812e-01f, 7.071067812e-01f},
+    {-5.555702330e-01f, 8.314696123e-01f}, {-3.826834324e-01f, 9.238795325e-01f}, {-1.950903220e-01f, 9.807852804e-01f},
+    {0.000000000e+00f, 1.000000000e+00f}, {1.950903220e-01f, 9.807852804e-01f}, {3.826834324e-01f, 9.238795325e-01f},
+    {5.555702330e-01f, 8.314696123e-01f}, {7.071067812e-01f, 7.071067812e-01f}, {8.314696123e-01f, 5.555702330e-01f},
+    {9.238795325e-01f, 3.826834324e-01f}, {9.807852804e-01f, 1.950903220e-01f},
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+template <int N>
+__device__ __forceinline__ float2 root(int k);
+template <>
+__device__ __forceinline__ float2 root<45>(int k) { return kRoot45[k % 45]; }
+template <>
+__device__ __forceinline__ float2 root<32>(int k) { return kRoot32[k & 31]; }
+template <>
+__device__ __forceinline__ float2 root<16>(int k) { return kRoot32[(k & 15) * 2]; }
+template <>
+__device__ __forceinline__ float2 root<8>(int k) { return kRoot32[(k & 7) * 4]; }
+template <>
+__device__ __forceinline__ float2 root<4>(int k) { return kRoot32[(k & 3) * 8]; }
+
+// forward R-point DFT in place
+template <int R>
+__device__ __forceinline__ void butterfly(float2 (&v)[R]) {
+  if (R == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if (R == 3) {
+    const float h = 0.86602540378443864676f;
+    const float2 t1 = cadd(v[1], v[2]);
+    const float2 t2 = csub(v[0], cscale(t1, 0.5f));
+    const float2 t3 = mul_mi(cscale(csub(v[1], v[2]), h));
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+  } else if (R == 4) {
+    const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    const float2 b0 = cadd(v[1], v[3]), b1 = mul_mi(csub(v[1], v[3]));
+    v[0] = cadd(a0, b0);
+    v[1] = cadd(a1, b1);
+    v[2] = csub(a0, b0);
+    v[3] = csub(a1, b1);
+  } else if (R == 5) {
+    const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+    const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+    const float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    const float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    const float2 r1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+    const float2 r2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+    const float2 q1 = mul_mi(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+    const float2 q2 = mul_mi(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    v[0] = cadd(v[0], cadd(a1, a2));
+    v[1] = cadd(r1, q1);
+    v[4] = csub(r1, q1);
+    v[2] = cadd(r2, q2);
+    v[3] = csub(r2, q2);
+  }
+}
+
+// One Stockham stage (radix R, current span Ns) of an N-point DFT held in
+// registers; all indices are compile-time after unrolling.
+template <int N, int Ns, int R>
+__device__ __forceinline__ void reg_stage(float2 (&a)[N]) {
+  float2 t[N];
+#pragma unroll
+  for (int j = 0; j < N / R; j++) {
+    const int k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      v[r] = a[j + r * (N / R)];
+      if (r > 0 && k > 0) v[r] = cmul(v[r], root<N>(r * k * (N / (Ns * R))));
+    }
+    butterfly<R>(v);
+    const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int q = 0; q < R; q++) t[base + q * Ns] = v[q];
+  }
+#pragma unroll
+  for (int i = 0; i < N; i++) a[i] = t[i];
+}
+
+template <int N>
+struct RegDFT;
+template <>
+struct RegDFT<45> {
+  static __device__ __forceinline__ void run(float2 (&a)[45]) {
+    reg_stage<45, 1, 5>(a);
+    reg_stage<45, 5, 3>(a);
+    reg_stage<45, 15, 3>(a);
+  }
+};
+template <>
+struct RegDFT<32> {
+  static __device__ __forceinline__ void run(float2 (&a)[32]) {
+    reg_stage<32, 1, 4>(a);
+    reg_stage<32, 4, 4>(a);
+    reg_stage<32, 16, 2>(a);
+  }
+};
+template <>
+struct RegDFT<16> {
+  static __device__ __forceinline__ void run(float2 (&a)[16]) {
+    reg_stage<16, 1, 4>(a);
+    reg_stage<16, 4, 4>(a);
+  }
+};
+template <>
+struct RegDFT<8> {
+  static __device__ __forceinline__ void run(float2 (&a)[8]) {
+    reg_stage<8, 1, 4>(a);
+    reg_stage<8, 4, 2>(a);
+  }
+};
+template <>
+struct RegDFT<4> {
+  static __device__ __forceinline__ void run(float2 (&a)[4]) { reg_stage<4, 1, 4>(a); }
+};
+
+// Buffer of one sequence: rows k2 < 45 of P + 1 entries (padding against
+// bank conflicts).  After seq_fft, X[k2 + 45 k1] sits at row k2, column k1.
+template <int P>
+__device__ __forceinline__ int spec_index(int k) {
+  return (k % kQ) * (P + 1) + k / kQ;
+}
+
+// Forward DFT of the sequence held as v[j] = z[t + P j] by lane t.
+template <int P>
+__device__ __forceinline__ void seq_fft(float2 (&v)[kQ], int t, float2 *buf, const float2 *twN) {
+  RegDFT<kQ>::run(v);
+#pragma unroll
+  for (int k2 = 1; k2 < kQ; k2++) v[k2] = cmul(v[k2], twN[t * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < kQ; k2++) buf[k2 * (P + 1) + t] = v[k2];
+  __syncwarp();
+  for (int k2 = t; k2 < kQ; k2 += P) {
+    float2 u[P];
+#pragma unroll
+    for (int n = 0; n < P; n++) u[n] = buf[k2 * (P + 1) + n];
+    RegDFT<P>::run(u);
+#pragma unroll
+    for (int n = 0; n < P; n++) buf[k2 * (P + 1) + n] = u[n];
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ float mode_weight(int m, int n, int inverse_weights) {
+  if (!inverse_weights) return 1.0f;
+  if (m == 0) return 1.0f;
+  if ((n & 1) == 0 && 2 * m == n) return 1.0f;
+  return 2.0f;
+}
+
+struct OutF32 {
+  float *F;
+  __device__ __forceinline__ void put(int64_t idx, float2 v) const { *reinterpret_cast<float2 *>(F + idx) = v; }
+};
+struct OutBF16 {
+  __nv_bfloat16 *hi, *lo;
+  __device__ __forceinline__ void put(int64_t idx, float2 v) const {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    *reinterpret_cast<__nv_bfloat162 *>(hi + idx) = h;
+    if (lo) {
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162 *>(lo + idx) = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+    }
+  }
+};
+
+template <int P, class Out>
+__global__ void __launch_bounds__(kThreads, 2)
+r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int ldc, const float2 *__restrict__ twiddle,
+             const float *__restrict__ ring_scale, int inverse_weights) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int SEQ = kThreads / P;
+  constexpr int BUF = kQ * (P + 1);
+  extern __shared__ float2 smem[];
+  float2 *tw = smem;
+  float2 *bufs = smem + N;
+  const int Kh = (nlat + 1) / 2;
+  const int s = threadIdx.x / P, t = threadIdx.x % P;
+  const int f = s % kFB, pp = s / kFB;
+  const int b = blockIdx.x * kFB + f;
+  const int kp = blockIdx.y * NPAIR + pp;
+  const int ks = nlat - 1 - kp;
+  const bool live = (b < B) && (kp < Kh);
+  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[q];
+  float2 v[kQ];
+  if (live) {
+    const float *rn = x + ((int64_t)b * nlat + kp) * N;
+    const float *rs = x + ((int64_t)b * nlat + ks) * N;
+    const bool eq = (kp == ks);
+#pragma unroll
+    for (int j = 0; j < kQ; j++) v[j] = make_float2(__ldg(rn + t + P * j), eq ? 0.f : __ldg(rs + t + P * j));
+  } else {
+#pragma unroll
+    for (int j = 0; j < kQ; j++) v[j] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 *buf = bufs + s * BUF;
+  seq_fft<P>(v, t, buf, tw);
+  __syncthreads();
+  // separate the two real transforms, fold by parity, write 8-field segments
+  const int b0 = blockIdx.x * kFB;
+  for (int e = threadIdx.x; e < NPAIR * M * kFB; e += kThreads) {
+    const int ff = e % kFB;
+    const int m = (e / kFB) % M;
+    const int pq = e / (kFB * M);
+    const int kq = blockIdx.y * NPAIR + pq;
+    if (b0 + ff >= B || kq >= Kh) continue;
+    const int kqs = nlat - 1 - kq;
+    const float2 *Z = bufs + (pq * kFB + ff) * BUF;
+    const float2 zm = Z[spec_index<P>(m)];
+    const float2 zc = conjf2(Z[spec_index<P>((N - m) % N)]);
+    const float c = 0.5f * mode_weight(m, N, inverse_weights);
+    const float sn = ring_scale ? ring_scale[kq] : 1.0f;
+    const float ss = ring_scale ? ring_scale[kqs] : 1.0f;
+    const float2 Fk = cscale(cadd(zm, zc), c * sn);
+    const float2 Fs = cscale(mul_mi(csub(zm, zc)), c * ss);
+    float2 E, O;
+    if (kq == kqs) {
+      E = Fk;
+      O = make_float2(0.f, 0.f);
+    } else {
+      E = cadd(Fk, Fs);
+      O = csub(Fk, Fs);
+    }
+    const int64_t col = 2 * (int64_t)(b0 + ff);
+    out.put((((int64_t)m * 2 + 0) * Kh + kq) * ldc + col, E);
+    out.put((((int64_t)m * 2 + 1) * Kh + kq) * ldc + col, O);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 2)
+c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, int ldc,
+             const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = kQ * (P + 1);
+  extern __shared__ float2 smem[];
+  float2 *tw = smem;
+  float2 *bufs = smem + N;
+  const int Kh = (nlat + 1) / 2;
+  const int b0 = blockIdx.x * kFB;
+  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[q];
+  // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
+  // the southern row (entries M..2M-1) of every sequence buffer
+  for (int e = threadIdx.x; e < NPAIR * M * kFB; e += kThreads) {
+    const int ff = e % kFB;
+    const int m = (e / kFB) % M;
+    const int pq = e / (kFB * M);
+    const int kq = blockIdx.y * NPAIR + pq;
+    if (b0 + ff >= B || kq >= Kh) continue;
+    const int kqs = nlat - 1 - kq;
+    const int64_t col = 2 * (int64_t)(b0 + ff);
+    const float2 ge = *reinterpret_cast<const float2 *>(Gw + (((int64_t)m * 2 + 0) * Kh + kq) * ldc + col);
+    const float2 go = *reinterpret_cast<const float2 *>(Gw + (((int64_t)m * 2 + 1) * Kh + kq) * ldc + col);
+    const float c = 0.5f * mode_weight(m, N, inverse_weights);
+    const float sn = ring_scale ? ring_scale[kq] : 1.0f;
+    const float ss = ring_scale ? ring_scale[kqs] : 1.0f;
+    const bool eq = (kq == kqs);
+    float2 *Bq = bufs + (pq * kFB + ff) * BUF;
+    Bq[m] = cscale(eq ? ge : cadd(ge, go), c * sn);
+    Bq[M + m] = eq ? make_float2(0.f, 0.f) : cscale(csub(ge, go), c * ss);
+  }
+  __syncthreads();
+  const int s = threadIdx.x / P, t = threadIdx.x % P;
+  const int f = s % kFB, pp = s / kFB;
+  const int b = b0 + f;
+  const int kp = blockIdx.y * NPAIR + pp;
+  const int ksth = nlat - 1 - kp;
+  const bool live = (b < B) && (kp < Kh);
+  float2 *buf = bufs + s * BUF;
+  // Hermitian extension of both rows, packed Z = H_n + i H_s; the synthesis
+  // is an inverse DFT, evaluated as conj(FFT(conj Z)).
+  float2 v[kQ];
+#pragma unroll
+  for (int j = 0; j < kQ; j++) {
+    const int q = t + P * j;
+    float2 hn = make_float2(0.f, 0.f), hs = make_float2(0.f, 0.f);
+    if (live) {
+      if (q < M) {
+        hn = buf[q];
+        hs = buf[M + q];
+      }
+      const int qm = (N - q) % N;
+      if (qm < M) {
+        hn = cadd(hn, conjf2(buf[qm]));
+        hs = cadd(hs, conjf2(buf[M + qm]));
+      }
+    }
+    v[j] = conjf2(make_float2(hn.x - hs.y, hn.y + hs.x));
+  }
+  __syncwarp();
+  seq_fft<P>(v, t, buf, tw);
+  if (!live) return;
+  const bool eq = (kp == ksth);
+  float *rn = y + ((int64_t)b * nlat + kp) * N;
+  float *rs = y + ((int64_t)b * nlat + ksth) * N;
+  for (int j = t; j < N; j += P) {
+    const float2 o = buf[spec_index<P>(j)];
+    rn[j] = o.x;
+    if (!eq) rs[j] = -o.y;
+  }
+}
+
+template <int P>
+size_t smem45() {
+  return sizeof(float2) * ((size_t)kQ * P + (size_t)(kThreads / P) * kQ * (P + 1));
+}
+
+template <int P, class Out>
+cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, int ldc, const float2 *tw, const float *ring,
+                  int wts, cudaStream_t st) {
+  const int Kh = (nlat + 1) / 2;
+  constexpr int NPAIR = kThreads / P / kFB;
+  dim3 grid((B + kFB - 1) / kFB, (Kh + NPAIR - 1) / NPAIR);
+  const size_t smem = smem45<P>();
+  cudaError_t e = cudaFuncSetAttribute((const void *)r2c45_kernel<P, Out>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  r2c45_kernel<P, Out><<<grid, kThreads, smem, st>>>(x, out, nlat, M, B, ldc, tw, ring, wts);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, int ldc, const float2 *tw, const float *ring,
+                  int wts, cudaStream_t st) {
+  const int Kh = (nlat + 1) / 2;
+  constexpr int NPAIR = kThreads / P / kFB;
+  dim3 grid((B + kFB - 1) / kFB, (Kh + NPAIR - 1) / NPAIR);
+  const size_t smem = smem45<P>();
+  cudaError_t e = cudaFuncSetAttribute((const void *)c2r45_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  c2r45_kernel<P><<<grid, kThreads, smem, st>>>(G, y, nlat, M, B, ldc, tw, ring, wts);
+  return cudaGetLastError();
+}
+
+template <class Out>
+cudaError_t r2c45_dispatch(int nlon, const float *x, Out out, int nlat, int M, int B, int ldc, const float2 *tw,
+                           const float *ring, int wts, cudaStream_t st) {
+  switch (nlon / kQ) {
+    case 32: return r2c45<32>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
+    case 16: return r2c45<16>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
+    case 8: return r2c45<8>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
+    default: return r2c45<4>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
+  }
+}
+
+}  // namespace
+
+bool fft45_supported(int nlon) {
+  return nlon == 45 * 32 || nlon == 45 * 16 || nlon == 45 * 8 || nlon == 45 * 4;
+}
+
+cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon,
+                         int M, int B, int ldc, const float2 *twiddle, const float *ring_scale, int inverse_weights,
+                         cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  if (Fw) return r2c45_dispatch(nlon, x, OutF32{Fw}, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+  return r2c45_dispatch(nlon, x, OutBF16{Fhi, Flo}, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+}
+
+cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, int ldc,
+                         const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  switch (nlon / kQ) {
+    case 32: return c2r45<32>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+    case 16: return c2r45<16>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+    case 8: return c2r45<8>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+    default: return c2r45<4>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+  }
+}
+
+}  // namespace shtgb

@@ -1,6 +1,8 @@
 // Internal declarations of the shtgb CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,7 +39,47 @@ struct TableF32 {
   int Khp;
 };
 
-struct sht_plan_impl;
+// Everything the tensor-core contractions of one plan need: TMA descriptors
+// of the bf16 hi/lo Legendre tables (forward layout [rows][Kp64] with block
+// (m, p) at row roff[2m+p]; transposed layout [(2m+p) Kh + k'][Ip64]), of the
+// Fourier workspace F[(2m+p) Kh + k'][ldcb] (hi, lo) and of the internal
+// coefficient rows S[soff[2m+p] + i][ldcb] (hi, lo), plus the error word.
+struct TcPlanView {
+  CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;
+  CUtensorMap f_hi, f_lo, s_hi, s_lo;
+  const int *roff, *soff;
+  int L, M, Kh;
+  bool split;
+  unsigned *err;
+};
+
+bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows);
+cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
+                                  const int *roff, int Kp64, int Ip64, const double *xk, const double *sk,
+                                  const double *a, const double *b, const double *seed, int L, int M, int Kh,
+                                  cudaStream_t st);
+// Forward contraction on the tensor cores from the bf16 Fourier workspace;
+// output to the API layout xhat (out_rows == NULL) or to FP32 internal rows
+// out_rows[soff + i][ldo] (columns 2b + {re, im}).
+cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat, float *out_rows,
+                              int ldo, int B, cudaStream_t st);
+// Inverse contraction on the tensor cores from the bf16 internal rows to the
+// FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
+cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
+                              cudaStream_t st);
+// API-layout coefficients -> internal bf16 hi/lo rows.
+cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,
+                             int M, int ldb, int B, cudaStream_t st);
+// Longitude analysis writing the folded Fourier workspace as bf16 hi/lo
+// (same contract as launch_r2c).
+cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,
+                            int ldb, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
+                            int inverse_weights, cudaStream_t st);
+// Spectral filter on internal rows: for every (l, m) row r = soff[2m+p] + i,
+//   y[r][2(b Cout + o) + {re,im}] = sum_i W[l][o][i] x[r][2(b Cin + i) + {re,im}],
+// x FP32 [rows][ldx], y bf16 hi/lo [rows][ldy].
+cudaError_t launch_filter_rows(const float *x, int ldx, const float2 *W, __nv_bfloat16 *yhi, __nv_bfloat16 *ylo,
+                               int ldy, const int *soff, int L, int M, int Bm, int Cin, int Cout, cudaStream_t st);
 
 // Record a failure message for sht_last_error_message() and return status.
 sht_status_t fail(sht_status_t st, const std::string &msg);
@@ -63,6 +105,16 @@ cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M,
                        int B, int ldc, const float2 *twiddle,
                        const RadixPlan &rp, const float *ring_scale,
                        int inverse_weights, cudaStream_t st);
+
+// Four-step register FFT versions of launch_r2c / launch_c2r for nlon = 45 P,
+// P in {4, 8, 16, 32}.  The analysis writes FP32 (Fw != NULL) or bf16 hi
+// (and lo when Flo != NULL) with row stride ldc elements.
+bool fft45_supported(int nlon);
+cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon,
+                         int M, int B, int ldc, const float2 *twiddle, const float *ring_scale, int inverse_weights,
+                         cudaStream_t st);
+cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, int ldc,
+                         const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st);
 
 // Longitude synthesis from folded Gw[m][p][k'][ldc]:
 //   u_kj = ring_scale[k] * sum_m c_m Re(G_k(m) e^{2 pi i j m / nlon})
@@ -138,6 +190,15 @@ struct sht_plan_s {
   int64_t workspace_bytes = 0;
 
   // device memory (all owned)
+  unsigned *d_err = nullptr;   // error word of bounded device waits
+  shtgb::TcPlanView tc{};      // tensor-core view (bf16 precisions)
+  int ldcb = 0;                // bf16 row stride of the workspaces (elements)
+  int64_t srows = 0;           // rows of the internal coefficient layout
+  int *d_soff = nullptr;       // [2 M] first internal row of block (m, p)
+  float *d_rows = nullptr;     // FP32 internal rows [srows][ldc]
+  __nv_bfloat16 *d_s_hi = nullptr, *d_s_lo = nullptr;  // bf16 internal rows [srows][ldcb]
+  __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;
+  int *d_roff = nullptr;
   float *d_table = nullptr;
   int64_t *d_tab_off = nullptr;
   float2 *d_twiddle = nullptr;

@@ -52,15 +52,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Wait for the phase with the given parity to complete.  Gives up after
-// `limit` polls (each poll may itself suspend for a hardware time slice),
-// records kErrTimeout in *err and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, uint32_t limit = 1u << 22) {
-  for (uint32_t i = 0; i < limit; i++) {
-    if (mbar_try_wait(bar, parity)) return true;
+// about `timeout_ns` of wall time, records kErrTimeout in *err and returns
+// false, so that a broken pipeline ends the kernel instead of hanging it.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err,
+                                          uint64_t timeout_ns = 2000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    for (int i = 0; i < 64; i++)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > timeout_ns) {
+      if (err) atomicOr(err, kErrTimeout);
+      return false;
+    }
   }
-  if (err) atomicOr(err, kErrTimeout);
-  return false;
 }
 
 // ---------------------------------------------------------------- proxies
@@ -153,15 +165,32 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(const void *smem_tile) {
   return d;
 }
 
+// Shared-memory matrix descriptor, MN-major, 128-byte swizzle.  Swizzle atoms
+// are 64 MN-contiguous elements (128 B) by 8 K-rows (row stride 128 B,
+// 1024 B per atom).  `lbo` = byte stride between atoms along MN (64-element
+// column blocks), `sbo` = byte stride between atoms along K (8-row groups).
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(const void *smem_tile, uint32_t lbo, uint32_t sbo) {
+  const uint32_t addr = smem_addr(smem_tile);
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Advance a K-major SW128 descriptor by `kbytes` along K inside the 128-byte
 // row (the hardware applies the swizzle to the computed addresses).
 __device__ __forceinline__ uint64_t desc_advance(uint64_t desc, uint32_t kbytes) { return desc + (kbytes >> 4); }
 
 // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28; bit 16 set selects an
+// MN-major B operand.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool b_mn_major = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 // Byte offset of element (row r, k) in a K-major SW128 BF16 tile whose rows

@@ -18,6 +18,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
+# relative L2 tolerances per precision of the Legendre contractions.  BF16
+# rounds the input data to bf16, whose unit roundoff is 2^-8 (7 stored
+# fraction bits); for smooth fields the rounding errors of neighbouring rows
+# are alike and do not average out, so the bound is the unit roundoff itself.
+TOL = {"fp32": 1e-5, "split_bf16": 2e-5, "bf16": 2.0 ** -8}
+PRECS = ["fp32", "split_bf16", "bf16"]
 
 SHAPES = [
     # nlat, nlon, grid, L, M, B
@@ -30,6 +36,7 @@ SHAPES = [
     (64, 128, "gauss", 64, 64, 33),              # several column tiles, ragged
     (181, 360, "equiangular_cc", 180, 180, 3),   # several row tiles
     (46, 90, "gauss", 46, 46, 1),                # M = nlon/2 + 1, single field
+    (361, 720, "equiangular_cc", 360, 360, 10),  # 0.5 degree grid, 16-lane transforms
 ]
 
 
@@ -49,36 +56,42 @@ def _to_gpu(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_forward_matches_oracle(shtgb, shape):
+def test_forward_matches_oracle(shtgb, shape, prec):
     nlat, nlon, grid, L, M, B = shape
     fields, ref = batch_from_bases(nlat, nlon, grid, L, M, B, min(B, 3), 100)
-    plan = _plan(shtgb, nlat, nlon, grid, L, M)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     out = shtgb.sht_forward(plan, _to_gpu(fields, torch.float32)).cpu().numpy()
+    plan.check()
     err = per_field_spec_err(out, ref)
-    assert err.max() <= TOL_FP32, err
+    assert err.max() <= TOL[prec], err
     # exact zeros above the diagonal, exactly real m = 0
     assert np.all(out[:, ~triangle_mask(L, M)] == 0)
     assert np.all(out[..., 0].imag == 0)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_inverse_matches_oracle(shtgb, shape):
+def test_inverse_matches_oracle(shtgb, shape, prec):
     nlat, nlon, grid, L, M, B = shape
     c = inputs.spectral_coeffs(200, (B,), L, M, nyquist_nlon=nlon).astype(np.complex64)
     # garbage above the diagonal must be ignored
     c[:, ~triangle_mask(L, M)] = 7.0 + 3.0j
     ref = oracle.sht_inverse(np.where(triangle_mask(L, M), c, 0), nlat, nlon, grid, L, M)
-    plan = _plan(shtgb, nlat, nlon, grid, L, M)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     out = shtgb.sht_inverse(plan, _to_gpu(c, torch.complex64)).cpu().numpy()
+    plan.check()
     err = per_field_spatial_err(out, ref)
-    assert err.max() <= TOL_FP32, err
+    assert err.max() <= TOL[prec], err
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES[:6])
-def test_adjoints_match_oracle(shtgb, shape):
+def test_adjoints_match_oracle(shtgb, shape, prec):
     nlat, nlon, grid, L, M, B = shape
-    plan = _plan(shtgb, nlat, nlon, grid, L, M)
+    TOL_FP32 = TOL[prec]
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     gy = inputs.spectral_coeffs(300, (B,), L, M, spectrum="flat").astype(np.complex64)
     gx = inputs.spatial_noise(301, (B, nlat, nlon)).astype(np.float32)
     ref_fa = oracle.sht_forward_adjoint(gy, nlat, nlon, grid, L, M)
@@ -111,20 +124,30 @@ def test_filter_and_adjoints_match_oracle(shtgb, dims):
     assert rel_l2(gW.cpu().numpy(), rgW) <= TOL_FP32
 
 
-def test_block_and_fused_filter_inverse_match_oracle(shtgb):
+@pytest.mark.parametrize("prec", PRECS)
+def test_block_and_fused_filter_inverse_match_oracle(shtgb, prec):
+    TOL_FP32 = TOL[prec]
     nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
     Bm, Cin, Cout = 3, 5, 4
     fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, Bm * Cin, 3, 500)
     W = inputs.filter_weights(501, L, Cout, Cin).astype(np.complex64)
     ref_y = oracle.sht_inverse(oracle.spectral_filter(ref_x.reshape(Bm, Cin, L, M), W), nlat, nlon, grid, L, M)
-    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=10)  # forces member chunks
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=10, precision=prec)  # forces member chunks
     x = _to_gpu(fields.reshape(Bm, Cin, nlat, nlon), torch.float32)
     Wg = _to_gpu(W, torch.complex64)
     y = shtgb.sht_spectral_block(plan, x, Wg).cpu().numpy()
-    assert per_field_spatial_err(y, ref_y).max() <= TOL_FP32
     xh = shtgb.sht_forward(plan, x)
     y2 = shtgb.spectral_filter_inverse(plan, xh, Wg).cpu().numpy()
-    assert per_field_spatial_err(y2, ref_y).max() <= TOL_FP32
+    plan.check()
+    if prec == "bf16":
+        # the data is rounded twice (Fourier rows, filter output) and the
+        # channel mixing can shrink single output fields, so the bound is two
+        # roundings relative to the whole member
+        for out in (y, y2):
+            assert rel_l2(out, ref_y) <= 2 * TOL_FP32
+    else:
+        assert per_field_spatial_err(y, ref_y).max() <= TOL_FP32
+        assert per_field_spatial_err(y2, ref_y).max() <= TOL_FP32
 
 
 def test_round_trip_and_ylm_deltas_gauss_33x64(shtgb):
@@ -149,6 +172,24 @@ def test_round_trip_and_ylm_deltas_gauss_33x64(shtgb):
         assert np.abs(out[i] - want).max() < 5e-6
 
 
+@pytest.mark.parametrize("prec", ["split_bf16", "bf16"])
+def test_tensor_core_column_tiles(shtgb, prec):
+    """Batches above 128 fields span several 256-column tiles of the
+    tensor-core kernels, with a ragged last tile."""
+    nlat, nlon, grid, L, M = 33, 64, "gauss", 32, 32
+    B = 301
+    fields, ref = batch_from_bases(nlat, nlon, grid, L, M, B, 3, 660)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec, max_batch=512)
+    x = _to_gpu(fields, torch.float32)
+    out = shtgb.sht_forward(plan, x).cpu().numpy()
+    assert per_field_spec_err(out, ref).max() <= TOL[prec]
+    c = inputs.spectral_coeffs(661, (B,), L, M).astype(np.complex64)
+    ref_u = oracle.sht_inverse(c[:7], nlat, nlon, grid, L, M)
+    u = shtgb.sht_inverse(plan, _to_gpu(c, torch.complex64)).cpu().numpy()
+    plan.check()
+    assert per_field_spatial_err(u[:7], ref_u).max() <= TOL[prec]
+
+
 def test_batch_chunking_and_empty_batch(shtgb):
     nlat, nlon, grid, L, M = 33, 64, "gauss", 32, 32
     fields, ref = batch_from_bases(nlat, nlon, grid, L, M, 11, 3, 600)
@@ -159,12 +200,14 @@ def test_batch_chunking_and_empty_batch(shtgb):
     assert empty.shape == (0, L, M)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", [(17, 32, "gauss", 16, 16, 8), (20, 40, "equiangular_cc", 19, 19, 5)])
-def test_plan_reuse_across_calls(shtgb, shape):
+def test_plan_reuse_across_calls(shtgb, shape, prec):
     """One plan serves forward, inverse and both adjoints in any order: no
     call may read workspace left behind by another."""
     nlat, nlon, grid, L, M, B = shape
-    plan = _plan(shtgb, nlat, nlon, grid, L, M)
+    TOL_FP32 = TOL[prec]
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     x = inputs.spatial_noise(650, (B, nlat, nlon)).astype(np.float32)
     y = inputs.spectral_coeffs(651, (B,), L, M, spectrum="flat").astype(np.complex64)
     y[..., 0] += 0.5j  # imaginary m = 0 parts are ignored by the synthesis
@@ -274,11 +317,13 @@ def test_adjoint_identities_on_gpu(shtgb):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.slow
-def test_full_size_block_against_oracle(shtgb):
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_full_size_block_against_oracle(shtgb, prec):
     nlat, nlon, grid, L, M = 721, 1440, "equiangular_cc", 720, 720
+    TOL_FP32 = TOL[prec]
     C = 72
     fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, C, 4, 1000)
-    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=C)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=C, precision=prec)
     x = _to_gpu(fields, torch.float32)
     xh = shtgb.sht_forward(plan, x).cpu().numpy()
     err = per_field_spec_err(xh, ref_x)
