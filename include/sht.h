@@ -105,11 +105,14 @@ typedef struct {
   int precision;      /* sht_precision_t, default SHT_PREC_FP32            */
   int device;         /* CUDA device ordinal, default: the current device  */
   int64_t max_batch;  /* fields per internal chunk, default 256            */
-  int reserved[8];    /* must be zero                                      */
+  int max_channels;   /* tensor-core plans: largest Cin / Cout of the
+                         fused block (sizes the real filter weights);
+                         0 = min(max_batch, 128)                            */
+  int reserved[7];    /* must be zero                                      */
 } sht_plan_opts;
 
 /* Fill opts with the defaults (precision FP32, current device,
- * max_batch 256). */
+ * max_batch 256, max_channels 0). */
 void sht_plan_opts_default(sht_plan_opts *opts);
 
 /* Create a plan for an (nlat x nlon) grid and lmax x mmax coefficients.
@@ -231,7 +234,8 @@ typedef enum {
   SHT_KERNEL_LEG_INV = 5,    /* inverse Legendre contraction              */
   SHT_KERNEL_C2R = 6,        /* longitude synthesis (inverse FFT)         */
   SHT_KERNEL_PACK = 7,       /* API coefficients -> internal bf16 rows    */
-  SHT_KERNEL_COUNT = 8
+  SHT_KERNEL_FILTER_PREP = 8, /* real bf16 form of the filter weights    */
+  SHT_KERNEL_COUNT = 9
 } sht_kernel_t;
 
 /* Start recording (capacity >= 1 launches); creates the events on the

@@ -178,7 +178,11 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_ti_lo);
   cudaFree(p->d_roff);
   cudaFree(p->d_soff);
-  cudaFree(p->d_rows);
+  cudaFree(p->d_x_hi);
+  cudaFree(p->d_x_lo);
+  cudaFree(p->d_wr_hi);
+  cudaFree(p->d_wr_lo);
+  cudaFree(p->d_ftiles);
   cudaFree(p->d_s_hi);
   cudaFree(p->d_s_lo);
   cudaFree(p->d_table);
@@ -237,11 +241,18 @@ __nv_bfloat16 *f_lo(sht_plan_s *p) { return f_hi(p) + (size_t)p->M * 2 * p->Kh *
 // The lo half of the data exists only for split precision.
 __nv_bfloat16 *data_lo(sht_plan_s *p, __nv_bfloat16 *lo) { return p->precision == SHT_PREC_SPLIT_BF16 ? lo : nullptr; }
 
+// Destination of the forward contraction in the tensor-core block path: the
+// l-major bf16 rows with members of cin channels in blocks of kx columns.
+struct RowsOut {
+  __nv_bfloat16 *hi, *lo;
+  int ldo, cin, kx;
+};
+
 // Forward transform (or the inverse adjoint) of B fields; the coefficients
 // go to the API layout xhat, or, when rows_out is set (tensor-core plans
-// only), to the internal rows.
+// only, one chunk), to the l-major rows.
 sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cudaStream_t st, bool adjoint,
-                      bool zero_upper, float *rows_out = nullptr) {
+                      bool zero_upper, const RowsOut *rows_out = nullptr) {
   const int64_t LM = (int64_t)p->L * p->M;
   for (int64_t b0 = 0; b0 < B; b0 += p->max_batch) {
     const int nb = (int)std::min<int64_t>(p->max_batch, B - b0);
@@ -271,8 +282,11 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
       });
       if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
       e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
-        return launch_leg_fwd_tc(p->tc, p->d_fwd_tiles, p->n_fwd_tiles, rows_out ? nullptr : xhat + b0 * LM,
-                                 rows_out, p->ldc, nb, st);
+        if (rows_out)
+          return launch_leg_fwd_tc(p->tc, p->d_fwd_tiles, p->n_fwd_tiles, nullptr, rows_out->hi, rows_out->lo,
+                                   rows_out->ldo, rows_out->cin, rows_out->kx, nb, st);
+        return launch_leg_fwd_tc(p->tc, p->d_fwd_tiles, p->n_fwd_tiles, xhat + b0 * LM, nullptr, nullptr, 0, 1, 0,
+                                 nb, st);
       });
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward Legendre launch");
@@ -346,6 +360,35 @@ sht_status_t filter_body(sht_plan_s *p, const float2 *x, const float2 *W, float2
   return SHT_OK;
 }
 
+// One chunk of nb members through the tensor-core block path: forward into
+// the l-major rows, real filter weights, tensor-core filter into the split
+// rows of the inverse, inverse + synthesis.
+sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, int64_t nb, int Cin, int Cout,
+                      cudaStream_t st) {
+  const int kx = (2 * Cin + 63) / 64 * 64;
+  const int nwr = (2 * Cout + 15) / 16 * 16;
+  const bool split = p->precision == SHT_PREC_SPLIT_BF16;
+  RowsOut ro{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, kx};
+  SHT_TRY(analysis(p, x, nullptr, nb * Cin, st, false, false, &ro));
+  // real weights: [L][nwr][kx] bf16 hi/lo, TMA boxes of 64 columns x Nt rows
+  const int ntile_n = (2 * Cout + 255) / 256;
+  const int Nt = ((2 * Cout + ntile_n - 1) / ntile_n + 15) / 16 * 16;
+  CUtensorMap tw_hi, tw_lo;
+  if (!tc_encode_2d(&tw_hi, p->d_wr_hi, kx, (int64_t)p->L * nwr, 64, Nt) ||
+      !tc_encode_2d(&tw_lo, p->d_wr_lo, kx, (int64_t)p->L * nwr, 64, Nt))
+    return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the filter weights");
+  cudaError_t e = traced(p, SHT_KERNEL_FILTER_PREP, st, [&] {
+    return launch_filter_prep((const float2 *)W, p->d_wr_hi, p->d_wr_lo, p->L, Cout, Cin, nwr, kx, st);
+  });
+  if (e != cudaSuccess) return cuda_fail(e, "filter weight preparation launch");
+  e = traced(p, SHT_KERNEL_FILTER, st, [&] {
+    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, tw_hi, tw_lo, p->d_s_hi, data_lo(p, p->d_s_lo), p->ldcb,
+                            kx, nwr, (int)nb, Cin, Cout, st);
+  });
+  if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+  return synthesis_rows(p, y, (int)(nb * Cout), st, false);
+}
+
 sht_status_t check_plan(sht_plan_t plan) {
   if (!plan) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
   return SHT_OK;
@@ -404,6 +447,7 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   if (o.max_batch < 1) return fail(SHT_ERR_INVALID_ARG, "max_batch must be >= 1");
   for (int r : o.reserved)
     if (r != 0) return fail(SHT_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (o.max_channels < 0) return fail(SHT_ERR_INVALID_ARG, "max_channels must be >= 0");
   if (nlon > kMaxNlon) return fail(SHT_ERR_UNSUPPORTED, "nlon above 8192 is not supported");
   RadixPlan rp;
   if (!factor_radix(nlon, rp)) return fail(SHT_ERR_UNSUPPORTED, "nlon must factor into 2, 3 and 5");
@@ -456,11 +500,12 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   // tile lists: row tiles of 64 (CUDA cores) or 128 (tensor cores)
   const bool tc = o.precision != SHT_PREC_FP32;
   const int trow = tc ? 128 : 64;
+  // block-major order: the row tiles of one (m, p) block run back to back
+  // and share its Fourier rows in L2
   std::vector<LegTile> ft, it;
-  for (int r0 = 0; r0 < (lmax + 1) / 2 + 1; r0 += trow)
-    for (int m = 0; m < mmax; m++)
-      for (int q = 0; q < 2; q++)
-        if (r0 < leg_rows(lmax, m, q)) ft.push_back(LegTile{m, q, r0});
+  for (int m = 0; m < mmax; m++)
+    for (int q = 0; q < 2; q++)
+      for (int r0 = 0; r0 < leg_rows(lmax, m, q); r0 += trow) ft.push_back(LegTile{m, q, r0});
   // every (m, p) block gets inverse tiles, also the empty one (m = lmax-1,
   // odd parity): its tiles write the zeros that the synthesis reads
   for (int m = 0; m < mmax; m++)
@@ -578,16 +623,37 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   if ((e = dev_alloc((void **)&p->d_spec_b, spec)) != cudaSuccess) return bail(e, "workspace allocation");
   if ((e = cudaMemset(p->d_work, 0, work)) != cudaSuccess) return bail(e, "workspace memset");
   if (tc) {
-    const size_t rbytes = sizeof(float) * (size_t)p->srows * p->ldc;
     const size_t sbytes = sizeof(__nv_bfloat16) * (size_t)p->srows * p->ldcb;
-    if ((e = dev_alloc((void **)&p->d_rows, rbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_s_hi, sbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_s_lo, sbytes)) != cudaSuccess) return bail(e, "workspace allocation");
-    if ((e = cudaMemset(p->d_rows, 0, rbytes)) != cudaSuccess) return bail(e, "workspace memset");
     if ((e = cudaMemset(p->d_s_hi, 0, sbytes)) != cudaSuccess) return bail(e, "workspace memset");
     if ((e = cudaMemset(p->d_s_lo, 0, sbytes)) != cudaSuccess) return bail(e, "workspace memset");
-    extra = rbytes + 2 * sbytes;
+    // l-major forward rows for the tensor-core filter, real filter weights,
+    // filter tiles (l, m0)
+    p->max_channels = o.max_channels > 0 ? o.max_channels : (int)std::min<int64_t>(o.max_batch, 128);
+    p->ldx = (int)std::max<int64_t>(64, (2 * o.max_batch + 63) / 64 * 64);
+    const size_t xbytes = sizeof(__nv_bfloat16) * (size_t)lmax * mmax * p->ldx;
+    const int cm = p->max_channels;
+    p->wr_capacity = (int64_t)lmax * ((2 * cm + 15) / 16 * 16) * ((2 * cm + 63) / 64 * 64);
+    const size_t wbytes = sizeof(__nv_bfloat16) * (size_t)p->wr_capacity;
+    std::vector<int2> ftl;
+    for (int l = 0; l < lmax; l++)
+      for (int m0 = 0; m0 < std::min(l + 1, mmax); m0 += 128) ftl.push_back(make_int2(l, m0));
+    p->n_ftiles = (int)ftl.size();
+    if ((e = dev_alloc((void **)&p->d_x_hi, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = dev_alloc((void **)&p->d_x_lo, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = dev_alloc((void **)&p->d_wr_hi, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = dev_alloc((void **)&p->d_wr_lo, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = upload((int2 **)&p->d_ftiles, ftl)) != cudaSuccess) return bail(e, "tile upload");
+    if ((e = cudaMemset(p->d_x_hi, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    if ((e = cudaMemset(p->d_x_lo, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    extra = 2 * sbytes + 2 * xbytes + 2 * wbytes;
     TcPlanView &T = p->tc;
+    if (!(tc_encode_2d(&T.x_hi, p->d_x_hi, p->ldx, (int64_t)lmax * mmax, 64, 128) &&
+          tc_encode_2d(&T.x_lo, p->d_x_lo, p->ldx, (int64_t)lmax * mmax, 64, 128))) {
+      free_plan(p);
+      return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
+    }
     if (!(tc_encode_2d(&T.f_hi, f_hi(p), p->ldcb, (int64_t)frow, 64, 64) &&
           tc_encode_2d(&T.f_lo, f_lo(p), p->ldcb, (int64_t)frow, 64, 64) &&
           tc_encode_2d(&T.s_hi, p->d_s_hi, p->ldcb, p->srows, 64, 64) &&
@@ -723,20 +789,17 @@ sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, flo
   SHT_TRY(check_ptr(y, "y"));
   DeviceGuard g(p->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t per = p->max_batch / std::max(Cin, Cout);
+  int64_t per = p->max_batch / std::max(Cin, Cout);
+  if (is_tc(p)) {
+    if (std::max(Cin, Cout) > p->max_channels)
+      return fail(SHT_ERR_INVALID_ARG, "max(Cin, Cout) exceeds the plan's max_channels");
+    per = std::min<int64_t>(per, p->ldx / ((2 * Cin + 63) / 64 * 64));
+  }
   const int64_t npix = (int64_t)p->nlat * p->nlon;
   for (int64_t b0 = 0; b0 < Bm; b0 += per) {
     const int64_t nb = std::min(per, Bm - b0);
     if (is_tc(p)) {
-      // internal rows end to end: FP32 rows after the forward contraction,
-      // bf16 hi/lo rows after the filter
-      SHT_TRY(analysis(p, x + b0 * Cin * npix, nullptr, nb * Cin, st, false, false, p->d_rows));
-      cudaError_t e = traced(p, SHT_KERNEL_FILTER, st, [&] {
-        return launch_filter_rows(p->d_rows, p->ldc, (const float2 *)W, p->d_s_hi, data_lo(p, p->d_s_lo), p->ldcb,
-                                  p->d_soff, p->L, p->M, (int)nb, Cin, Cout, st);
-      });
-      if (e != cudaSuccess) return cuda_fail(e, "filter launch");
-      SHT_TRY(synthesis_rows(p, y + b0 * Cout * npix, (int)(nb * Cout), st, false));
+      SHT_TRY(block_tc(p, x + b0 * Cin * npix, W, y + b0 * Cout * npix, nb, Cin, Cout, st));
       continue;
     }
     SHT_TRY(analysis(p, x + b0 * Cin * npix, p->d_spec_a, nb * Cin, st, false, false));
@@ -845,7 +908,7 @@ sht_status_t sht_profile_end(sht_plan_t p) {
 
 const char *sht_kernel_name(int k) {
   static const char *names[SHT_KERNEL_COUNT] = {"r2c", "leg_fwd", "zero_upper", "filter", "filter_dw", "leg_inv",
-                                                "c2r", "pack"};
+                                                "c2r", "pack", "filter_prep"};
   return (k >= 0 && k < SHT_KERNEL_COUNT) ? names[k] : "?";
 }
 

@@ -182,11 +182,13 @@ __device__ __forceinline__ int spec_index(int k) {
 }
 
 // Forward DFT of the sequence held as v[j] = z[t + P j] by lane t.
+// twT[t * 45 + k2] = w_N^{t k2} (lane-major, so that the lanes of one k2 hit
+// distinct banks).
 template <int P>
-__device__ __forceinline__ void seq_fft(float2 (&v)[kQ], int t, float2 *buf, const float2 *twN) {
+__device__ __forceinline__ void seq_fft(float2 (&v)[kQ], int t, float2 *buf, const float2 *twT) {
   RegDFT<kQ>::run(v);
 #pragma unroll
-  for (int k2 = 1; k2 < kQ; k2++) v[k2] = cmul(v[k2], twN[t * k2]);
+  for (int k2 = 1; k2 < kQ; k2++) v[k2] = cmul(v[k2], twT[t * kQ + k2]);
 #pragma unroll
   for (int k2 = 0; k2 < kQ; k2++) buf[k2 * (P + 1) + t] = v[k2];
   __syncwarp();
@@ -242,7 +244,7 @@ r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int l
   const int kp = blockIdx.y * NPAIR + pp;
   const int ks = nlat - 1 - kp;
   const bool live = (b < B) && (kp < Kh);
-  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[q];
+  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
   float2 v[kQ];
   if (live) {
     const float *rn = x + ((int64_t)b * nlat + kp) * N;
@@ -260,10 +262,11 @@ r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int l
   __syncthreads();
   // separate the two real transforms, fold by parity, write 8-field segments
   const int b0 = blockIdx.x * kFB;
-  for (int e = threadIdx.x; e < NPAIR * M * kFB; e += kThreads) {
+#pragma unroll 1
+  for (int pq = 0; pq < NPAIR; pq++)
+  for (int e = threadIdx.x; e < M * kFB; e += kThreads) {
     const int ff = e % kFB;
-    const int m = (e / kFB) % M;
-    const int pq = e / (kFB * M);
+    const int m = e / kFB;
     const int kq = blockIdx.y * NPAIR + pq;
     if (b0 + ff >= B || kq >= Kh) continue;
     const int kqs = nlat - 1 - kq;
@@ -301,13 +304,14 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
   float2 *bufs = smem + N;
   const int Kh = (nlat + 1) / 2;
   const int b0 = blockIdx.x * kFB;
-  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[q];
+  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
   // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
   // the southern row (entries M..2M-1) of every sequence buffer
-  for (int e = threadIdx.x; e < NPAIR * M * kFB; e += kThreads) {
+#pragma unroll 1
+  for (int pq = 0; pq < NPAIR; pq++)
+  for (int e = threadIdx.x; e < M * kFB; e += kThreads) {
     const int ff = e % kFB;
-    const int m = (e / kFB) % M;
-    const int pq = e / (kFB * M);
+    const int m = e / kFB;
     const int kq = blockIdx.y * NPAIR + pq;
     if (b0 + ff >= B || kq >= Kh) continue;
     const int kqs = nlat - 1 - kq;

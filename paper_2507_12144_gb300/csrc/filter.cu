@@ -168,94 +168,7 @@ filter_dw_kernel(const float2 *__restrict__ gy, const float2 *__restrict__ x, fl
     }
 }
 
-// Filter on internal rows (one row per (l, m) pair, fields innermost).
-// grid: x = l * mtiles + mt (64 orders m per tile), y = 64-channel output
-// tile, z = member b.  Each thread owns 4 orders x 4 output channels.
-constexpr int kRM = 64, kRO = 64, kRK = 16;
-__global__ void __launch_bounds__(kThreads)
-filter_rows_kernel(const float *__restrict__ x, int ldx, const float2 *__restrict__ W, __nv_bfloat16 *__restrict__ yhi,
-                   __nv_bfloat16 *__restrict__ ylo, int ldy, const int *__restrict__ soff, int L, int M, int Cin,
-                   int Cout) {
-  __shared__ __align__(16) float2 Xs[kRK][kRM];
-  __shared__ __align__(16) float2 Ws[kRK][kRO];
-  __shared__ int rowof[kRM];
-  const int mtiles = (M + kRM - 1) / kRM;
-  const int l = blockIdx.x / mtiles;
-  const int m0 = (blockIdx.x - l * mtiles) * kRM;
-  const int mlim = min(M, l + 1);
-  if (m0 >= mlim) return;
-  const int o0 = blockIdx.y * kRO;
-  const int b = blockIdx.z;
-  if (threadIdx.x < kRM) {
-    const int m = m0 + threadIdx.x;
-    rowof[threadIdx.x] = (m < mlim) ? soff[2 * m + ((l - m) & 1)] + ((l - m) >> 1) : -1;
-  }
-  __syncthreads();
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float2 acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < Cin; k0 += kRK) {
-    for (int e = threadIdx.x; e < kRK * kRM; e += kThreads) {
-      const int mm = e / kRK, kk = e - mm * kRK;
-      const int r = rowof[mm];
-      float2 v = make_float2(0.f, 0.f);
-      if (r >= 0 && k0 + kk < Cin)
-        v = *reinterpret_cast<const float2 *>(x + (int64_t)r * ldx + 2 * ((int64_t)b * Cin + k0 + kk));
-      Xs[kk][mm] = v;
-    }
-    for (int e = threadIdx.x; e < kRK * kRO; e += kThreads) {
-      const int oo = e / kRK, kk = e - oo * kRK;
-      float2 w = make_float2(0.f, 0.f);
-      if (o0 + oo < Cout && k0 + kk < Cin) w = W[((int64_t)l * Cout + o0 + oo) * Cin + k0 + kk];
-      Ws[kk][oo] = w;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kRK; kk++) {
-      float2 xv[4], wv[4];
-#pragma unroll
-      for (int i = 0; i < 4; i++) xv[i] = Xs[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; j++) wv[j] = Ws[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = cfma(wv[j], xv[i], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const int r = rowof[ty * 4 + i];
-    if (r < 0) continue;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int o = o0 + tx * 4 + j;
-      if (o >= Cout) continue;
-      const float2 v = acc[i][j];
-      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
-      const float2 hf = __bfloat1622float2(h);
-      const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-      const int64_t idx = (int64_t)r * ldy + 2 * ((int64_t)b * Cout + o);
-      *reinterpret_cast<__nv_bfloat162 *>(yhi + idx) = h;
-      if (ylo) *reinterpret_cast<__nv_bfloat162 *>(ylo + idx) = lo;
-    }
-  }
-}
-
 }  // namespace
-
-cudaError_t launch_filter_rows(const float *x, int ldx, const float2 *W, __nv_bfloat16 *yhi, __nv_bfloat16 *ylo,
-                               int ldy, const int *soff, int L, int M, int Bm, int Cin, int Cout, cudaStream_t st) {
-  if (Bm <= 0) return cudaSuccess;
-  const int mtiles = (M + kRM - 1) / kRM;
-  dim3 grid(L * mtiles, (Cout + kRO - 1) / kRO, Bm);
-  filter_rows_kernel<<<grid, kThreads, 0, st>>>(x, ldx, W, yhi, ylo, ldy, soff, L, M, Cin, Cout);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L, int M, int64_t Bm, int Cin, int Cout,
                           int adjoint, cudaStream_t st) {

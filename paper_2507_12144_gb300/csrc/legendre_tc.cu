@@ -52,227 +52,348 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 a, __nv_bfloat16 b
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Stage buffers: A hi, A lo (split only), B hi, B lo; every buffer starts on
-// a 1024-byte boundary.  A tiles are 128 rows x 64 k (K-major, 16 KB); B
-// tiles are 64 k-rows x nbox column blocks of 64 (MN-major, nbox x 8 KB).
-struct Stage {
-  unsigned char *a_hi, *a_lo, *b_hi, *b_lo;
+__device__ __forceinline__ void put_bf16_pair(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t idx, float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  *reinterpret_cast<__nv_bfloat162 *>(hi + idx) = h;
+  if (lo) {
+    const float2 hf = __bfloat1622float2(h);
+    *reinterpret_cast<__nv_bfloat162 *>(lo + idx) = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  }
+}
+
+// Round 8 consecutive FP32 values to bf16 (and the remainder to bf16 when lo
+// is set) and store them as 16-byte chunks at hi + idx / lo + idx.
+__device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t idx, const float *v) {
+  uint32_t h[4], r[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+    const float2 hf = __bfloat1622float2(hh);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * u] - hf.x, v[2 * u + 1] - hf.y);
+    h[u] = *reinterpret_cast<const uint32_t *>(&hh);
+    r[u] = *reinterpret_cast<const uint32_t *>(&ll);
+  }
+  *reinterpret_cast<uint4 *>(hi + idx) = make_uint4(h[0], h[1], h[2], h[3]);
+  if (lo) *reinterpret_cast<uint4 *>(lo + idx) = make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent tensor-core kernel for the three contractions.  One CTA per SM
+// walks its tiles (tile = blockIdx.x + i gridDim.x).  A ring of `stages`
+// shared-memory stages carries TMA loads to the MMA thread continuously
+// across tiles; the accumulator is double-buffered in tensor memory so that
+// the epilogue warps drain tile i while the MMAs of tile i + 1 run.
+//   kFwd:  D[i][c]  = sum_k' T[m][p][i][k'] F[m][p][k'][c]   (A = table, B = data, MN-major)
+//   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[soff + i][c]   (A = table, B = data, MN-major)
+//   kFilt: D[m][n]  = sum_k  X[l M + m][b kx + k] WR[l][n][k] (A = data, B = weights, K-major)
+// Table and weights always enter split (hi + lo); data enters split for
+// split BF16 and rounded (hi only) for BF16.
+// ---------------------------------------------------------------------------
+enum Mode { kFwd = 0, kInv = 1, kFilt = 2 };
+
+struct FiltTile {
+  int l, m0;
 };
 
-__host__ __device__ inline uint32_t b_tile_bytes(int nbox) { return (uint32_t)nbox * 8192u; }
+// Destination of the forward contraction: the API layout xhat[b][l][m], or
+// l-major bf16 rows (row l M + m, member b's channel ch at column
+// b kx + 2 ch + {re, im}) for the tensor-core filter.
+struct FwdOut {
+  float2 *xhat;
+  __nv_bfloat16 *rows_hi, *rows_lo;
+  int ldo, cin, kx;
+};
 
-__host__ __device__ inline uint32_t stage_bytes(int nbox, bool split) {
-  return 2u * kABytes + (split ? 2u : 1u) * b_tile_bytes(nbox);
+struct TcArgs {
+  // geometry
+  int L, M, Kh, B, Nt, nct, stages, ntiles;
+  // forward / inverse
+  const LegTile *tiles;
+  const int *roff, *soff;
+  FwdOut fout;      // forward destination
+  float *Gw;        // inverse destination
+  int ldc;
+  // filter
+  const FiltTile *ftiles;
+  int Bm, ntn, kx, nwr, cin, cout, lds;
+  __nv_bfloat16 *s_hi, *s_lo;
+  unsigned *err;
+};
+
+__host__ __device__ inline int a_count(int mode, bool split) { return (mode == kFilt && !split) ? 1 : 2; }
+__host__ __device__ inline int b_count(int mode, bool split) { return (mode == kFilt || split) ? 2 : 1; }
+__host__ __device__ inline uint32_t b_bytes_of(int mode, int Nt) {
+  return mode == kFilt ? (uint32_t)Nt * 128u : (uint32_t)((Nt + 63) / 64) * 8192u;
+}
+__host__ __device__ inline uint32_t stage_bytes(int mode, bool split, int Nt) {
+  return (uint32_t)a_count(mode, split) * kABytes + (uint32_t)b_count(mode, split) * b_bytes_of(mode, Nt);
 }
 
-template <bool kSplit>
-__device__ __forceinline__ Stage stage_ptr(unsigned char *base, int s, int nbox) {
-  unsigned char *p = base + (size_t)s * stage_bytes(nbox, kSplit);
-  Stage S;
-  S.a_hi = p;
-  S.a_lo = p + kABytes;
-  S.b_hi = p + 2u * kABytes;
-  S.b_lo = kSplit ? S.b_hi + b_tile_bytes(nbox) : S.b_hi;
-  return S;
+struct TileInfo {
+  int nk;                // K chunks
+  int a_col0, a_row;     // A: K column of chunk 0, row
+  int b_col0, b_row0;    // B: for MN-major (col of box 0, K row of chunk 0); for K-major (K col 0, row)
+  // epilogue selectors
+  int m, p, r0, c0, l, b, n0;
+};
+
+template <int kMode>
+__device__ __forceinline__ TileInfo tile_info(const TcArgs &a, int t) {
+  TileInfo ti{};
+  if (kMode == kFilt) {
+    const int per = a.Bm * a.ntn;
+    const FiltTile ft = a.ftiles[t / per];
+    const int rem = t - (t / per) * per;
+    ti.l = ft.l;
+    ti.m = ft.m0;
+    ti.b = rem / a.ntn;
+    ti.n0 = (rem - ti.b * a.ntn) * a.Nt;
+    ti.nk = (2 * a.cin + kKc - 1) / kKc;
+    ti.a_col0 = ti.b * a.kx;
+    ti.a_row = ti.l * a.M + ti.m;
+    ti.b_col0 = 0;
+    ti.b_row0 = ti.l * a.nwr + ti.n0;
+  } else {
+    const LegTile tl = a.tiles[t / a.nct];
+    ti.m = tl.m;
+    ti.p = tl.p;
+    ti.r0 = tl.r0;
+    ti.c0 = (t % a.nct) * a.Nt;
+    ti.b_col0 = ti.c0;
+    ti.a_col0 = 0;
+    if (kMode == kFwd) {
+      ti.nk = (a.Kh + kKc - 1) / kKc;
+      ti.a_row = a.roff[2 * ti.m + ti.p] + ti.r0;
+      ti.b_row0 = (ti.m * 2 + ti.p) * a.Kh;
+    } else {
+      ti.nk = (leg_rows(a.L, ti.m, ti.p) + kKc - 1) / kKc;
+      ti.a_row = (ti.m * 2 + ti.p) * a.Kh + ti.r0;
+      ti.b_row0 = a.soff[2 * ti.m + ti.p];
+    }
+  }
+  return ti;
 }
 
-// One stage of MMAs: 4 k-steps of 16 rows.
-template <bool kSplit>
-__device__ __forceinline__ void issue_stage(const Stage &S, uint32_t tmem, uint32_t idesc, bool first) {
+template <int kMode, bool kSplit>
+__device__ __forceinline__ void issue_chunk(unsigned char *st, int Nt, uint32_t tmem, uint32_t idesc, bool first) {
+  const int na = a_count(kMode, kSplit);
+  const uint32_t bb = b_bytes_of(kMode, Nt);
+  unsigned char *a_hi = st, *a_lo = st + kABytes;
+  unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
 #pragma unroll
   for (int ks = 0; ks < kKc / 16; ks++) {
-    const uint64_t ah = desc_advance(desc_kmajor_sw128(S.a_hi), ks * 32);
-    const uint64_t al = desc_advance(desc_kmajor_sw128(S.a_lo), ks * 32);
-    const uint64_t bh = desc_mnmajor_sw128(S.b_hi + ks * 2048, 8192, 1024);
-    mma_bf16(tmem, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
-    mma_bf16(tmem, al, bh, idesc, 1u);
-    if (kSplit) {
-      const uint64_t bl = desc_mnmajor_sw128(S.b_lo + ks * 2048, 8192, 1024);
+    const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
+    const uint64_t ah = desc_advance(desc_kmajor_sw128(a_hi), ks * 32);
+    if (kMode == kFilt) {
+      const uint64_t bh = desc_advance(desc_kmajor_sw128(b_hi), ks * 32);
+      const uint64_t bl = desc_advance(desc_kmajor_sw128(b_lo), ks * 32);
+      mma_bf16(tmem, ah, bh, idesc, acc0);
       mma_bf16(tmem, ah, bl, idesc, 1u);
+      if (kSplit) mma_bf16(tmem, desc_advance(desc_kmajor_sw128(a_lo), ks * 32), bh, idesc, 1u);
+    } else {
+      const uint64_t al = desc_advance(desc_kmajor_sw128(a_lo), ks * 32);
+      const uint64_t bh = desc_mnmajor_sw128(b_hi + ks * 2048, 8192, 1024);
+      mma_bf16(tmem, ah, bh, idesc, acc0);
+      mma_bf16(tmem, al, bh, idesc, 1u);
+      if (kSplit) mma_bf16(tmem, ah, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
     }
   }
 }
 
-// Shared TMA -> MMA pipeline of both contractions.  A rows start at a_row
-// (K chunk kc at column 64 kc), B k-rows start at b_row + 64 kc, B columns at
-// c0 + 64 j.  Returns after the MMA thread committed the accumulator (or the
-// loop was empty); the epilogue warps then wait on done_bar.
-template <bool kSplit>
-__device__ __forceinline__ void run_pipeline(const CUtensorMap *ta_hi, const CUtensorMap *ta_lo,
-                                             const CUtensorMap *tb_hi, const CUtensorMap *tb_lo, int a_row,
-                                             int b_row, int c0, int nk, int nbox, int Nt, int stages,
-                                             unsigned char *base, uint64_t *full_bar, uint64_t *empty_bar,
-                                             uint64_t *done_bar, uint32_t tmem, unsigned *err) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(ta_hi);
-    tma_prefetch_desc(ta_lo);
-    tma_prefetch_desc(tb_hi);
-    if (kSplit) tma_prefetch_desc(tb_lo);
-    const uint32_t tx = 2u * kABytes + (kSplit ? 2u : 1u) * b_tile_bytes(nbox);
-    for (int kc = 0; kc < nk; kc++) {
-      const int s = kc % stages, it = kc / stages;
-      if (it > 0) mbar_wait(&empty_bar[s], (it - 1) & 1, err);
-      const Stage S = stage_ptr<kSplit>(base, s, nbox);
-      mbar_arrive_expect_tx(&full_bar[s], tx);
-      tma_load_2d(S.a_hi, ta_hi, &full_bar[s], kc * kKc, a_row);
-      tma_load_2d(S.a_lo, ta_lo, &full_bar[s], kc * kKc, a_row);
-      for (int j = 0; j < nbox; j++) {
-        tma_load_2d(S.b_hi + j * 8192, tb_hi, &full_bar[s], c0 + 64 * j, b_row + kc * kKc);
-        if (kSplit) tma_load_2d(S.b_lo + j * 8192, tb_lo, &full_bar[s], c0 + 64 * j, b_row + kc * kKc);
-      }
+template <int kMode, bool kSplit>
+__device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti, int kc, int Nt,
+                                           const CUtensorMap *ta_hi, const CUtensorMap *ta_lo,
+                                           const CUtensorMap *tb_hi, const CUtensorMap *tb_lo, uint64_t *bar) {
+  const int na = a_count(kMode, kSplit);
+  const uint32_t bb = b_bytes_of(kMode, Nt);
+  unsigned char *a_hi = st, *a_lo = st + kABytes;
+  unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
+  tma_load_2d(a_hi, ta_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  if (na == 2) tma_load_2d(a_lo, ta_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  if (kMode == kFilt) {
+    tma_load_2d(b_hi, tb_hi, bar, kc * kKc, ti.b_row0);
+    tma_load_2d(b_lo, tb_lo, bar, kc * kKc, ti.b_row0);
+  } else {
+    const int nbox = (Nt + 63) / 64;
+    for (int j = 0; j < nbox; j++) {
+      tma_load_2d(b_hi + j * 8192, tb_hi, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
+      if (kSplit) tma_load_2d(b_lo + j * 8192, tb_lo, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_bf16_f32(kRows, Nt, true);
-    for (int kc = 0; kc < nk; kc++) {
-      const int s = kc % stages, it = kc / stages;
-      mbar_wait(&full_bar[s], it & 1, err);
-      tc_fence_after();
-      issue_stage<kSplit>(stage_ptr<kSplit>(base, s, nbox), tmem, idesc, kc == 0);
-      mma_commit(&empty_bar[s]);
-    }
-    if (nk > 0) mma_commit(done_bar);
   }
 }
 
-// ---------------------------------------------------------------------------
-// Forward: D[i][c] = sum_k' T[m][p][i][k'] F[m][p][k'][c]
-// A = table rows i (TMA, K-major), B = Fourier workspace rows k' (TMA,
-// MN-major), D in TMEM.  Epilogue: to the API layout xhat[b][l][m]
-// (out_rows == nullptr) or to the internal rows out_rows[soff + i][c].
-// ---------------------------------------------------------------------------
-template <bool kSplit>
-__global__ void __launch_bounds__(kThreads, 1)
-leg_fwd_tc_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
-                  const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                  const int *__restrict__ roff, const int *__restrict__ soff, const LegTile *__restrict__ tiles,
-                  float2 *__restrict__ xhat, float *__restrict__ out_rows, int ldo, int L, int M, int Kh, int B,
-                  int Nt, int nct, int stages, unsigned *err) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *base = align1024(smem_raw);
-  __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
-  __shared__ uint32_t tmem_slot;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const LegTile tile = tiles[blockIdx.x / nct];
-  const int m = tile.m, p = tile.p, r0 = tile.r0;
-  const int nrows = leg_rows(L, m, p);
-  const int c0 = (blockIdx.x % nct) * Nt;
-  const int nk = (Kh + kKc - 1) / kKc;
-  const int nbox = (Nt + 63) / 64;
-  const uint32_t ncols = (uint32_t)tmem_cols_for(Nt);
-
-  if (warp == 2) tmem_alloc(&tmem_slot, ncols);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; s++) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
-    mbar_init(&done_bar, 1);
-    mbar_fence_init();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-  run_pipeline<kSplit>(&ta_hi, &ta_lo, &tb_hi, &tb_lo, roff[2 * m + p] + r0, (m * 2 + p) * Kh, c0, nk, nbox, Nt,
-                       stages, base, full_bar, empty_bar, &done_bar, tmem, err);
-  if (warp >= 4) {
-    const int q4 = warp - 4;
-    mbar_wait(&done_bar, 0, err);
-    tc_fence_after();
-    const int r = r0 + q4 * 32 + lane;
-    const bool row_ok = r < nrows;
-    const int l = m + p + 2 * r;
-    float *orow = out_rows ? out_rows + (int64_t)(soff[2 * m + p] + r) * ldo : nullptr;
+// Epilogue of one tile for the accumulator at tacc (zero: write zeros).
+template <int kMode>
+__device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, uint32_t tacc, int q4, int lane,
+                                         bool zero) {
+  const int Nt = a.Nt;
+  const uint32_t tl = tacc + ((uint32_t)(q4 * 32) << 16);
+  if (kMode == kFwd) {
+    const int r = ti.r0 + q4 * 32 + lane;
+    const bool row_ok = r < leg_rows(a.L, ti.m, ti.p);
+    const int l = ti.m + ti.p + 2 * r;
+    const FwdOut &out = a.fout;
+    const int64_t orow = ((int64_t)l * a.M + ti.m) * out.ldo;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(j * 16), v);
+      tmem_ld16(tl + (uint32_t)(j * 16), v);
       if (!row_ok) continue;
-      const int cb = c0 + j * 16;
-      if (orow) {
+      if (out.rows_hi) {
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (cb + 4 * u < 2 * B)
-            *reinterpret_cast<float4 *>(orow + cb + 4 * u) =
-                make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        for (int h = 0; h < 2; h++) {
+          const int f = (ti.c0 + j * 16) / 2 + 4 * h;  // first of 4 fields
+          if (f >= a.B) continue;
+          const int mb = f / out.cin, ch = f - mb * out.cin;
+          if ((ch & 3) == 0 && ch + 4 <= out.cin && f + 4 <= a.B) {
+            put_bf16x8(out.rows_hi, out.rows_lo, orow + (int64_t)mb * out.kx + 2 * ch, v + 8 * h);
+          } else {
+            for (int u = 0; u < 4 && f + u < a.B; u++) {
+              const int fu = f + u, mu = fu / out.cin, cu = fu - mu * out.cin;
+              put_bf16_pair(out.rows_hi, out.rows_lo, orow + (int64_t)mu * out.kx + 2 * cu, v[8 * h + 2 * u],
+                            v[8 * h + 2 * u + 1]);
+            }
+          }
+        }
       } else {
 #pragma unroll
-        for (int t = 0; t < 8; t++) {
-          const int b = cb / 2 + t;
-          if (b < B) xhat[((int64_t)b * L + l) * M + m] = make_float2(v[2 * t], v[2 * t + 1]);
+        for (int u = 0; u < 8; u++) {
+          const int f = (ti.c0 + j * 16) / 2 + u;
+          if (f < a.B) out.xhat[((int64_t)f * a.L + l) * a.M + ti.m] = make_float2(v[2 * u], v[2 * u + 1]);
         }
       }
     }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 2) {
-    tc_fence_after();
-    tmem_dealloc(tmem, ncols);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Inverse: G[m][p][k'][c] = sum_i T[m][p][i][k'] S[soff + i][c]
-// A = transposed table rows k' (TMA, K-major), B = coefficient rows i of the
-// internal layout (TMA, MN-major).  Blocks without rows write zeros.
-// ---------------------------------------------------------------------------
-template <bool kSplit>
-__global__ void __launch_bounds__(kThreads, 1)
-leg_inv_tc_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
-                  const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                  const int *__restrict__ soff, const LegTile *__restrict__ tiles, float *__restrict__ Gw, int L,
-                  int Kh, int ldc, int B, int Nt, int nct, int stages, unsigned *err) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *base = align1024(smem_raw);
-  __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
-  __shared__ uint32_t tmem_slot;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const LegTile tile = tiles[blockIdx.x / nct];
-  const int m = tile.m, p = tile.p, k0 = tile.r0;
-  const int nrows = leg_rows(L, m, p);
-  const int c0 = (blockIdx.x % nct) * Nt;
-  const int nk = (nrows + kKc - 1) / kKc;
-  const int nbox = (Nt + 63) / 64;
-  const uint32_t ncols = (uint32_t)tmem_cols_for(Nt);
-
-  if (warp == 2) tmem_alloc(&tmem_slot, ncols);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; s++) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
-    mbar_init(&done_bar, 1);
-    mbar_fence_init();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-  run_pipeline<kSplit>(&ta_hi, &ta_lo, &tb_hi, &tb_lo, (m * 2 + p) * Kh + k0, soff[2 * m + p], c0, nk, nbox, Nt,
-                       stages, base, full_bar, empty_bar, &done_bar, tmem, err);
-  if (warp >= 4) {
-    const int q4 = warp - 4;
-    if (nk > 0) mbar_wait(&done_bar, 0, err);
-    tc_fence_after();
-    const int k = k0 + q4 * 32 + lane;
-    float *G = Gw + (((int64_t)m * 2 + p) * Kh + k) * ldc;
+  } else if (kMode == kInv) {
+    const int k = ti.r0 + q4 * 32 + lane;
+    float *G = a.Gw + (((int64_t)ti.m * 2 + ti.p) * a.Kh + k) * a.ldc;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
-      if (nk > 0) {
-        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(j * 16), v);
+      if (!zero) {
+        tmem_ld16(tl + (uint32_t)(j * 16), v);
       } else {
 #pragma unroll
-        for (int t = 0; t < 16; t++) v[t] = 0.f;
+        for (int u = 0; u < 16; u++) v[u] = 0.f;
       }
-      if (k < Kh) {
+      if (k < a.Kh) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          const int c = c0 + j * 16 + 4 * u;
-          if (c < ldc)
+          const int c = ti.c0 + j * 16 + 4 * u;
+          if (c < a.ldc)
             *reinterpret_cast<float4 *>(G + c) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
         }
       }
+    }
+  } else {
+    const int m = ti.m + q4 * 32 + lane;
+    const bool ok = (m < a.M) && (m <= ti.l);
+    const int d = ti.l - m;
+    const int64_t srow =
+        ok ? (int64_t)(a.soff[2 * m + (d & 1)] + (d >> 1)) * a.lds + 2 * (int64_t)ti.b * a.cout : 0;
+    for (int j = 0; j < Nt / 16; j++) {
+      float v[16];
+      tmem_ld16(tl + (uint32_t)(j * 16), v);
+      if (!ok) continue;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int n = ti.n0 + j * 16 + 8 * h;  // 4 output channels
+        if (n + 8 <= 2 * a.cout && ((srow + n) & 7) == 0) {
+          put_bf16x8(a.s_hi, a.s_lo, srow + n, v + 8 * h);
+        } else {
+          for (int u = 0; u < 4; u++)
+            if (n + 2 * u < 2 * a.cout)
+              put_bf16_pair(a.s_hi, a.s_lo, srow + n + 2 * u, v[8 * h + 2 * u], v[8 * h + 2 * u + 1]);
+        }
+      }
+    }
+  }
+}
+
+template <int kMode, bool kSplit>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+                     const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+                     const TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = align1024(smem_raw);
+  __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t acc_cols = (uint32_t)tmem_cols_for(a.Nt);
+  const uint32_t ncols = 2 * acc_cols;
+  const uint32_t sbytes = stage_bytes(kMode, kSplit, a.Nt);
+  const int S = a.stages;
+
+  if (warp == 2) tmem_alloc(&tmem_slot, ncols);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; s++) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_fence_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    tma_prefetch_desc(&ta_hi);
+    tma_prefetch_desc(&ta_lo);
+    tma_prefetch_desc(&tb_hi);
+    tma_prefetch_desc(&tb_lo);
+    uint32_t g = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      const TileInfo ti = tile_info<kMode>(a, t);
+      for (int kc = 0; kc < ti.nk; kc++, g++) {
+        const int s = (int)(g % (uint32_t)S);
+        const uint32_t use = g / (uint32_t)S;
+        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, a.err);
+        unsigned char *st = base + (size_t)s * sbytes;
+        mbar_arrive_expect_tx(&full_bar[s], sbytes);
+        load_chunk<kMode, kSplit>(st, ti, kc, a.Nt, &ta_hi, &ta_lo, &tb_hi, &tb_lo, &full_bar[s]);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = idesc_bf16_f32(kRows, a.Nt, kMode != kFilt);
+    uint32_t g = 0, it = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, it++) {
+      const TileInfo ti = tile_info<kMode>(a, t);
+      const int acc = (int)(it & 1);
+      const uint32_t use_a = it >> 1;
+      if (use_a > 0) mbar_wait(&tempty[acc], (use_a - 1) & 1, a.err);
+      tc_fence_after();
+      const uint32_t tacc = tmem + (uint32_t)acc * acc_cols;
+      for (int kc = 0; kc < ti.nk; kc++, g++) {
+        const int s = (int)(g % (uint32_t)S);
+        const uint32_t use = g / (uint32_t)S;
+        mbar_wait(&full_bar[s], use & 1, a.err);
+        tc_fence_after();
+        issue_chunk<kMode, kSplit>(base + (size_t)s * sbytes, a.Nt, tacc, idesc, kc == 0);
+        mma_commit(&empty_bar[s]);
+      }
+      if (ti.nk > 0)
+        mma_commit(&tfull[acc]);
+      else
+        mbar_arrive(&tfull[acc]);
+    }
+  } else if (warp >= 4) {
+    // epilogue
+    const int q4 = warp - 4;
+    uint32_t it = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, it++) {
+      const TileInfo ti = tile_info<kMode>(a, t);
+      const int acc = (int)(it & 1);
+      mbar_wait(&tfull[acc], (it >> 1) & 1, a.err);
+      tc_fence_after();
+      epilogue<kMode>(a, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
     }
   }
   tc_fence_before();
@@ -301,6 +422,33 @@ __global__ void pack_rows_kernel(const float2 *__restrict__ yhat, __nv_bfloat16 
   const int64_t o = (int64_t)(soff[2 * m + p] + i) * ldb + 2 * b;
   *reinterpret_cast<uint32_t *>(shi + o) = pack_bf16x2(hr, hi_);
   if (slo) *reinterpret_cast<uint32_t *>(slo + o) = pack_bf16x2(lr, li);
+}
+
+// WR[l][n][k] (bf16 hi/lo), n < nwr rows, k < kx columns, from W[l][o][i]:
+// n = 2 o + a, k = 2 i + c: (a, c) = (0, 0) Re W, (0, 1) -Im W, (1, 0) Im W,
+// (1, 1) Re W; zero outside 2 Cout x 2 Cin.
+__global__ void filter_prep_kernel(const float2 *__restrict__ W, __nv_bfloat16 *__restrict__ whi,
+                                   __nv_bfloat16 *__restrict__ wlo, int L, int Cout, int Cin, int nwr, int kx) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (l, n, column pair)
+  const int kp = kx / 2;
+  if (e >= (int64_t)L * nwr * kp) return;
+  const int ip = (int)(e % kp);
+  const int64_t ln = e / kp;
+  const int n = (int)(ln % nwr);
+  const int l = (int)(ln / nwr);
+  const int o = n >> 1, a = n & 1;
+  float v0 = 0.f, v1 = 0.f;
+  if (o < Cout && ip < Cin) {
+    const float2 w = W[((int64_t)l * Cout + o) * Cin + ip];
+    v0 = a ? w.y : w.x;   // multiplies Re x_i
+    v1 = a ? w.x : -w.y;  // multiplies Im x_i
+  }
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+  const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+  const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+  const int64_t idx = ln * kx + 2 * ip;
+  *reinterpret_cast<uint32_t *>(whi + idx) = pack_bf16x2(h0, h1);
+  *reinterpret_cast<uint32_t *>(wlo + idx) = pack_bf16x2(l0, l1);
 }
 
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and
@@ -344,18 +492,41 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
   }
 }
 
-int choose_stages(int nbox, bool split) {
-  const int budget = 220 * 1024 - 1024;
-  return std::max(2, std::min(kMaxStages, budget / (int)stage_bytes(nbox, split)));
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
 }
-
-size_t smem_bytes(int nbox, bool split, int stages) { return 1024 + (size_t)stages * stage_bytes(nbox, split); }
 
 // Column tiling of the 2B real columns: tiles of at most 256, multiple of 16.
 void column_tiles(int B, int &Nt, int &nct) {
   const int C2 = 2 * B;
   nct = (C2 + 255) / 256;
   Nt = ((C2 + nct - 1) / nct + 15) / 16 * 16;
+}
+
+template <int kMode>
+cudaError_t launch_persistent(bool split, const CUtensorMap &ta_hi, const CUtensorMap &ta_lo,
+                              const CUtensorMap &tb_hi, const CUtensorMap &tb_lo, TcArgs &args, cudaStream_t st) {
+  if (args.ntiles <= 0) return cudaSuccess;
+  const int sb = (int)stage_bytes(kMode, split, args.Nt);
+  const int budget = 220 * 1024 - 1024;
+  args.stages = std::max(2, std::min(kMaxStages, budget / sb));
+  const size_t smem = 1024 + (size_t)args.stages * sb;
+  const void *fn = split ? (const void *)tc_persistent_kernel<kMode, true>
+                         : (const void *)tc_persistent_kernel<kMode, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min(args.ntiles, sm_count());
+  if (split)
+    tc_persistent_kernel<kMode, true><<<grid, kThreads, smem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  else
+    tc_persistent_kernel<kMode, false><<<grid, kThreads, smem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -391,48 +562,74 @@ cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_b
   return cudaGetLastError();
 }
 
-cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat, float *out_rows,
-                              int ldo, int B, cudaStream_t st) {
+cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
+                              __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
+                              cudaStream_t st) {
   if (ntiles == 0 || B <= 0) return cudaSuccess;
-  int Nt, nct;
-  column_tiles(B, Nt, nct);
-  const int nbox = (Nt + 63) / 64;
-  const int stages = choose_stages(nbox, T.split);
-  const size_t smem = smem_bytes(nbox, T.split, stages);
-  const void *fn = T.split ? (const void *)leg_fwd_tc_kernel<true> : (const void *)leg_fwd_tc_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)ntiles * (unsigned)nct;
-  if (T.split)
-    leg_fwd_tc_kernel<true><<<grid, kThreads, smem, st>>>(T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.f_lo, T.roff, T.soff,
-                                                           tiles, xhat, out_rows, ldo, T.L, T.M, T.Kh, B, Nt, nct,
-                                                           stages, T.err);
-  else
-    leg_fwd_tc_kernel<false><<<grid, kThreads, smem, st>>>(T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.f_hi, T.roff,
-                                                            T.soff, tiles, xhat, out_rows, ldo, T.L, T.M, T.Kh, B,
-                                                            Nt, nct, stages, T.err);
-  return cudaGetLastError();
+  TcArgs a{};
+  a.L = T.L;
+  a.M = T.M;
+  a.Kh = T.Kh;
+  a.B = B;
+  column_tiles(B, a.Nt, a.nct);
+  a.ntiles = ntiles * a.nct;
+  a.tiles = tiles;
+  a.roff = T.roff;
+  a.soff = T.soff;
+  a.fout = FwdOut{xhat, rows_hi, rows_lo, ldo, cin > 0 ? cin : 1, kx};
+  a.err = T.err;
+  return launch_persistent<kFwd>(T.split, T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.split ? T.f_lo : T.f_hi, a, st);
 }
 
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
                               cudaStream_t st) {
   if (ntiles == 0 || B <= 0) return cudaSuccess;
-  int Nt, nct;
-  column_tiles(B, Nt, nct);
-  const int nbox = (Nt + 63) / 64;
-  const int stages = choose_stages(nbox, T.split);
-  const size_t smem = smem_bytes(nbox, T.split, stages);
-  const void *fn = T.split ? (const void *)leg_inv_tc_kernel<true> : (const void *)leg_inv_tc_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)ntiles * (unsigned)nct;
-  if (T.split)
-    leg_inv_tc_kernel<true><<<grid, kThreads, smem, st>>>(T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.s_lo, T.soff, tiles,
-                                                           Gw, T.L, T.Kh, ldc, B, Nt, nct, stages, T.err);
-  else
-    leg_inv_tc_kernel<false><<<grid, kThreads, smem, st>>>(T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.s_hi, T.soff,
-                                                            tiles, Gw, T.L, T.Kh, ldc, B, Nt, nct, stages, T.err);
+  TcArgs a{};
+  a.L = T.L;
+  a.M = T.M;
+  a.Kh = T.Kh;
+  a.B = B;
+  column_tiles(B, a.Nt, a.nct);
+  a.ntiles = ntiles * a.nct;
+  a.tiles = tiles;
+  a.roff = T.roff;
+  a.soff = T.soff;
+  a.Gw = Gw;
+  a.ldc = ldc;
+  a.err = T.err;
+  return launch_persistent<kInv>(T.split, T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.split ? T.s_lo : T.s_hi, a, st);
+}
+
+cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
+                               int nwr, int kx, cudaStream_t st) {
+  const int64_t n = (int64_t)L * nwr * (kx / 2);
+  filter_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, whi, wlo, L, Cout, Cin, nwr, kx);
   return cudaGetLastError();
+}
+
+cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &tw_hi,
+                             const CUtensorMap &tw_lo, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx,
+                             int nwr, int Bm, int Cin, int Cout, cudaStream_t st) {
+  if (nftiles == 0 || Bm <= 0) return cudaSuccess;
+  TcArgs a{};
+  a.L = T.L;
+  a.M = T.M;
+  a.Kh = T.Kh;
+  a.ntn = (2 * Cout + 255) / 256;
+  a.Nt = ((2 * Cout + a.ntn - 1) / a.ntn + 15) / 16 * 16;
+  a.Bm = Bm;
+  a.ntiles = nftiles * Bm * a.ntn;
+  a.ftiles = reinterpret_cast<const FiltTile *>(ftiles);
+  a.soff = T.soff;
+  a.kx = kx;
+  a.nwr = nwr;
+  a.cin = Cin;
+  a.cout = Cout;
+  a.lds = lds;
+  a.s_hi = s_hi;
+  a.s_lo = s_lo;
+  a.err = T.err;
+  return launch_persistent<kFilt>(T.split, T.x_hi, T.split ? T.x_lo : T.x_hi, tw_hi, tw_lo, a, st);
 }
 
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,

@@ -47,6 +47,7 @@ struct TableF32 {
 struct TcPlanView {
   CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;
   CUtensorMap f_hi, f_lo, s_hi, s_lo;
+  CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
   const int *roff, *soff;
   int L, M, Kh;
   bool split;
@@ -59,10 +60,19 @@ cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_b
                                   const double *a, const double *b, const double *seed, int L, int M, int Kh,
                                   cudaStream_t st);
 // Forward contraction on the tensor cores from the bf16 Fourier workspace;
-// output to the API layout xhat (out_rows == NULL) or to FP32 internal rows
-// out_rows[soff + i][ldo] (columns 2b + {re, im}).
-cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat, float *out_rows,
-                              int ldo, int B, cudaStream_t st);
+// output to the API layout xhat (rows_hi == NULL) or to l-major bf16 rows
+// rows[l M + m][ldo] with member b = f / cin at columns b kx + 2 (f mod cin).
+cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
+                              __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
+                              cudaStream_t st);
+// Real form WR of the filter weights (bf16 hi/lo, [L][nwr][kx]).
+cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
+                               int nwr, int kx, cudaStream_t st);
+// Tensor-core filter from the l-major rows to the inverse's split rows.
+// ftiles: (l, m0) pairs covering m <= l, m < M in steps of 128.
+cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &tw_hi,
+                             const CUtensorMap &tw_lo, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx,
+                             int nwr, int Bm, int Cin, int Cout, cudaStream_t st);
 // Inverse contraction on the tensor cores from the bf16 internal rows to the
 // FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
@@ -75,11 +85,7 @@ cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat
 cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,
                             int ldb, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
                             int inverse_weights, cudaStream_t st);
-// Spectral filter on internal rows: for every (l, m) row r = soff[2m+p] + i,
-//   y[r][2(b Cout + o) + {re,im}] = sum_i W[l][o][i] x[r][2(b Cin + i) + {re,im}],
-// x FP32 [rows][ldx], y bf16 hi/lo [rows][ldy].
-cudaError_t launch_filter_rows(const float *x, int ldx, const float2 *W, __nv_bfloat16 *yhi, __nv_bfloat16 *ylo,
-                               int ldy, const int *soff, int L, int M, int Bm, int Cin, int Cout, cudaStream_t st);
+
 
 // Record a failure message for sht_last_error_message() and return status.
 sht_status_t fail(sht_status_t st, const std::string &msg);
@@ -195,7 +201,13 @@ struct sht_plan_s {
   int ldcb = 0;                // bf16 row stride of the workspaces (elements)
   int64_t srows = 0;           // rows of the internal coefficient layout
   int *d_soff = nullptr;       // [2 M] first internal row of block (m, p)
-  float *d_rows = nullptr;     // FP32 internal rows [srows][ldc]
+  int ldx = 0;                 // columns of the l-major forward rows
+  int max_channels = 0;        // capacity of the real filter weights
+  __nv_bfloat16 *d_x_hi = nullptr, *d_x_lo = nullptr;  // l-major forward rows [L M][ldx]
+  __nv_bfloat16 *d_wr_hi = nullptr, *d_wr_lo = nullptr;  // real filter weights
+  int64_t wr_capacity = 0;     // elements of each of d_wr_hi / d_wr_lo
+  void *d_ftiles = nullptr;    // filter tiles (l, m0)
+  int n_ftiles = 0;
   __nv_bfloat16 *d_s_hi = nullptr, *d_s_lo = nullptr;  // bf16 internal rows [srows][ldcb]
   __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;
   int *d_roff = nullptr;
