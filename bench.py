@@ -74,6 +74,8 @@ def algorithmic_bytes(kernel: str, fields: int, members: int, cin: int, cout: in
         return fields * (four + tri)
     if kernel == "filter":
         return members * (cin + cout) * tri + LMAX * cout * cin * 8.0
+    if kernel == "filter_prep":
+        return LMAX * cout * cin * 8.0
     return float("nan")
 
 
@@ -85,13 +87,20 @@ def source_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {
-    "r2c": ["paper_2507_12144_gb300/csrc/fft.cu"],
-    "c2r": ["paper_2507_12144_gb300/csrc/fft.cu"],
-    "leg_fwd": ["paper_2507_12144_gb300/csrc/legendre_f32.cu"],
-    "leg_inv": ["paper_2507_12144_gb300/csrc/legendre_f32.cu"],
-    "filter": ["paper_2507_12144_gb300/csrc/filter.cu"],
-}
+# source files of each kernel of the benchmark (nlon = 1440 uses the
+# four-step FFT); the committed DRAM traffic of a kernel is used only while
+# these files are unchanged
+def kernel_sources(kernel: str, precision: str):
+    tc = precision != "fp32"
+    table = {
+        "r2c": ["paper_2507_12144_gb300/csrc/fft45.cu"],
+        "c2r": ["paper_2507_12144_gb300/csrc/fft45.cu"],
+        "leg_fwd": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/legendre_f32.cu"],
+        "leg_inv": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/legendre_f32.cu"],
+        "filter": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/filter.cu"],
+        "filter_prep": ["paper_2507_12144_gb300/csrc/legendre_tc.cu"],
+    }
+    return table.get(kernel, [])
 
 
 def measured_traffic(kernel: str, precision: str):
@@ -106,7 +115,7 @@ def measured_traffic(kernel: str, precision: str):
     ent = table.get(f"{kernel}/{precision}")
     if not ent:
         return None
-    if ent.get("source_hash") != source_hash(KERNEL_SOURCES.get(kernel, [])):
+    if ent.get("source_hash") != source_hash(kernel_sources(kernel, precision)):
         return None
     return ent.get("bytes_per_launch")
 
@@ -428,7 +437,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -307,24 +307,41 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
   for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
   // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
   // the southern row (entries M..2M-1) of every sequence buffer
+  // loads are issued in batches of 8 iterations so that many are in flight
+  constexpr int kBatch = 8;
 #pragma unroll 1
-  for (int pq = 0; pq < NPAIR; pq++)
-  for (int e = threadIdx.x; e < M * kFB; e += kThreads) {
-    const int ff = e % kFB;
-    const int m = e / kFB;
+  for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = blockIdx.y * NPAIR + pq;
-    if (b0 + ff >= B || kq >= Kh) continue;
+    if (kq >= Kh) continue;
     const int kqs = nlat - 1 - kq;
-    const int64_t col = 2 * (int64_t)(b0 + ff);
-    const float2 ge = *reinterpret_cast<const float2 *>(Gw + (((int64_t)m * 2 + 0) * Kh + kq) * ldc + col);
-    const float2 go = *reinterpret_cast<const float2 *>(Gw + (((int64_t)m * 2 + 1) * Kh + kq) * ldc + col);
-    const float c = 0.5f * mode_weight(m, N, inverse_weights);
+    const bool eq = (kq == kqs);
     const float sn = ring_scale ? ring_scale[kq] : 1.0f;
     const float ss = ring_scale ? ring_scale[kqs] : 1.0f;
-    const bool eq = (kq == kqs);
-    float2 *Bq = bufs + (pq * kFB + ff) * BUF;
-    Bq[m] = cscale(eq ? ge : cadd(ge, go), c * sn);
-    Bq[M + m] = eq ? make_float2(0.f, 0.f) : cscale(csub(ge, go), c * ss);
+    const float *ge_row = Gw + ((int64_t)0 * Kh + kq) * ldc;
+    for (int e0 = threadIdx.x; e0 < M * kFB; e0 += kThreads * kBatch) {
+      float2 ge[kBatch], go[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; u++) {
+        const int e = e0 + u * kThreads;
+        const int ff = e % kFB, m = e / kFB;
+        ge[u] = go[u] = make_float2(0.f, 0.f);
+        if (e < M * kFB && b0 + ff < B) {
+          const int64_t col = 2 * (int64_t)(b0 + ff);
+          ge[u] = *reinterpret_cast<const float2 *>(ge_row + ((int64_t)m * 2 + 0) * Kh * ldc + col);
+          go[u] = *reinterpret_cast<const float2 *>(ge_row + ((int64_t)m * 2 + 1) * Kh * ldc + col);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; u++) {
+        const int e = e0 + u * kThreads;
+        const int ff = e % kFB, m = e / kFB;
+        if (e >= M * kFB || b0 + ff >= B) continue;
+        const float c = 0.5f * mode_weight(m, N, inverse_weights);
+        float2 *Bq = bufs + (pq * kFB + ff) * BUF;
+        Bq[m] = cscale(eq ? ge[u] : cadd(ge[u], go[u]), c * sn);
+        Bq[M + m] = eq ? make_float2(0.f, 0.f) : cscale(csub(ge[u], go[u]), c * ss);
+      }
+    }
   }
   __syncthreads();
   const int s = threadIdx.x / P, t = threadIdx.x % P;

@@ -429,26 +429,29 @@ __global__ void pack_rows_kernel(const float2 *__restrict__ yhat, __nv_bfloat16 
 // (1, 1) Re W; zero outside 2 Cout x 2 Cin.
 __global__ void filter_prep_kernel(const float2 *__restrict__ W, __nv_bfloat16 *__restrict__ whi,
                                    __nv_bfloat16 *__restrict__ wlo, int L, int Cout, int Cin, int nwr, int kx) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (l, n, column pair)
-  const int kp = kx / 2;
-  if (e >= (int64_t)L * nwr * kp) return;
-  const int ip = (int)(e % kp);
-  const int64_t ln = e / kp;
+  // one thread per (l, n, 4 input channels): 8 columns, one 16-byte store each
+  const int kq = kx / 8;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * nwr * kq) return;
+  const int iq = (int)(e % kq);
+  const int64_t ln = e / kq;
   const int n = (int)(ln % nwr);
   const int l = (int)(ln / nwr);
   const int o = n >> 1, a = n & 1;
-  float v0 = 0.f, v1 = 0.f;
-  if (o < Cout && ip < Cin) {
-    const float2 w = W[((int64_t)l * Cout + o) * Cin + ip];
-    v0 = a ? w.y : w.x;   // multiplies Re x_i
-    v1 = a ? w.x : -w.y;  // multiplies Im x_i
+  float v[8];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int i = 4 * iq + u;
+    float v0 = 0.f, v1 = 0.f;
+    if (o < Cout && i < Cin) {
+      const float2 w = W[((int64_t)l * Cout + o) * Cin + i];
+      v0 = a ? w.y : w.x;   // multiplies Re x_i
+      v1 = a ? w.x : -w.y;  // multiplies Im x_i
+    }
+    v[2 * u] = v0;
+    v[2 * u + 1] = v1;
   }
-  const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-  const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-  const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-  const int64_t idx = ln * kx + 2 * ip;
-  *reinterpret_cast<uint32_t *>(whi + idx) = pack_bf16x2(h0, h1);
-  *reinterpret_cast<uint32_t *>(wlo + idx) = pack_bf16x2(l0, l1);
+  put_bf16x8(whi, wlo, ln * kx + 8 * iq, v);
 }
 
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and
@@ -602,7 +605,7 @@ cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int nti
 
 cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
                                int nwr, int kx, cudaStream_t st) {
-  const int64_t n = (int64_t)L * nwr * (kx / 2);
+  const int64_t n = (int64_t)L * nwr * (kx / 8);
   filter_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, whi, wlo, L, Cout, Cin, nwr, kx);
   return cudaGetLastError();
 }
