@@ -10,7 +10,7 @@ pass of the whole path over the 72 fields through the C ABI call
 SHT, filter and ISHT = one field-transform), with the roofline fraction of
 the dominant kernel.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--table-source S]
   python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
 
 Multi-GPU runs (torchrun) are independent replicas: the path has no
@@ -42,12 +42,13 @@ MEMBERS, CHANNELS = 1, 72
 FALLBACK_HBM_GBS = 6800.0
 
 
-def workload_config(precision: str) -> dict:
+def workload_config(precision: str, table_source: str = "streamed") -> dict:
     return {
         "workload": "SHT+filter+ISHT, 721x1440 equiangular (Clenshaw-Curtis), lmax=mmax=720, "
                     "1 member x 72 channels, W[720][72][72] complex",
         "nlat": NLAT, "nlon": NLON, "grid": GRID, "lmax": LMAX, "mmax": MMAX,
         "members": MEMBERS, "channels": CHANNELS, "precision": precision,
+        "legendre_table": table_source if precision != "fp32" else "streamed",
         "spectrum": "(l+1)^-3 angular power, seeded",
         "l2": "inputs larger than L2: 299 MB of fields in and 299 MB out per step",
         "parallelism": "replicas",
@@ -91,7 +92,7 @@ def source_hash(paths) -> str:
 # four-step FFT); the committed DRAM traffic of a kernel is used only while
 # these files are unchanged
 def kernel_sources(kernel: str, precision: str):
-    tc = precision != "fp32"
+    tc = not precision.startswith("fp32")
     table = {
         "r2c": ["paper_2507_12144_gb300/csrc/fft45.cu"],
         "c2r": ["paper_2507_12144_gb300/csrc/fft45.cu"],
@@ -101,6 +102,13 @@ def kernel_sources(kernel: str, precision: str):
         "filter_prep": ["paper_2507_12144_gb300/csrc/legendre_tc.cu"],
     }
     return table.get(kernel, [])
+
+
+def variant_key(args) -> str:
+    """Key of the committed DRAM traffic table: precision, + "+rec" for the
+    on-chip recurrence table."""
+    rec = args.precision != "fp32" and args.table_source == "recurrence"
+    return args.precision + ("+rec" if rec else "")
 
 
 def measured_traffic(kernel: str, precision: str):
@@ -325,7 +333,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     fields = MEMBERS * CHANNELS
-    plan = shtgb.Plan(NLAT, NLON, GRID, LMAX, MMAX, precision=args.precision, device=dev, max_batch=fields)
+    plan = shtgb.Plan(NLAT, NLON, GRID, LMAX, MMAX, precision=args.precision, device=dev, max_batch=fields,
+                      table_source=args.table_source)
 
     # synthetic inputs: seeded (l+1)^-3 coefficients synthesised on the GPU
     c = inputs.spectral_coeffs(2 + rank, (fields,), LMAX, MMAX)
@@ -379,7 +388,7 @@ def run_gpu(args):
     peak, peak_kind = load_peaks()
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
-                "traffic": measured_traffic(dom, args.precision),
+                "traffic": measured_traffic(dom, variant_key(args)),
                 "algorithmic_bytes_per_launch": alg,
                 "kernel_ms_per_launch": per_launch_s * 1e3,
                 "share_of_step": dom_ms / ms_total if world == 1 else None}
@@ -410,7 +419,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
             "data": "synthetic: seeded (l+1)^-3 spectra synthesised on the GPU, random-init filter",
-            "config": workload_config(args.precision),
+            "config": workload_config(args.precision, args.table_source),
             "roofline": roofline,
             "kernels": breakdown,
             "gpu_launches": launches,
@@ -438,6 +447,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
+    ap.add_argument("--table-source", choices=["streamed", "recurrence"], default="streamed",
+                    help="Legendre table of the tensor-core precisions: precomputed and streamed, or "
+                         "generated on chip by the recurrence")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

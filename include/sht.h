@@ -101,6 +101,18 @@ typedef enum {
   SHT_PREC_SPLIT_BF16 = 2
 } sht_precision_t;
 
+/* Source of the Legendre table Phat_l^m(x_k) (Eq. sht_legendre_recursion)
+ * for the tensor-core precisions; FP32 plans always stream an FP32 table.
+ * STREAMED: bf16 hi/lo tables built once in FP64 at plan time and read by
+ *   TMA on every call (table bytes re-read per call, no recurrence work).
+ * RECURRENCE: only FP64 seeds every 32 degrees are stored; extra warps of
+ *   the Legendre kernels run the three-term recurrence in FP32 on chip
+ *   (about 1/16 of the table bytes, more instructions per call). */
+typedef enum {
+  SHT_TABLE_STREAMED = 0,
+  SHT_TABLE_RECURRENCE = 1
+} sht_table_source_t;
+
 typedef struct {
   int precision;      /* sht_precision_t, default SHT_PREC_FP32            */
   int device;         /* CUDA device ordinal, default: the current device  */
@@ -108,11 +120,12 @@ typedef struct {
   int max_channels;   /* tensor-core plans: largest Cin / Cout of the
                          fused block (sizes the real filter weights);
                          0 = min(max_batch, 128)                            */
-  int reserved[7];    /* must be zero                                      */
+  int table_source;   /* sht_table_source_t, default SHT_TABLE_STREAMED    */
+  int reserved[6];    /* must be zero                                      */
 } sht_plan_opts;
 
 /* Fill opts with the defaults (precision FP32, current device,
- * max_batch 256, max_channels 0). */
+ * max_batch 256, max_channels 0, table_source STREAMED). */
 void sht_plan_opts_default(sht_plan_opts *opts);
 
 /* Create a plan for an (nlat x nlon) grid and lmax x mmax coefficients.

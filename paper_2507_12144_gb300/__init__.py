@@ -50,11 +50,16 @@ class Plan:
 
     ``grid`` is "gauss", "equiangular_cc" or "equiangular_trapz"; ``lmax``
     and ``mmax`` are counts (l < lmax, m < mmax); ``precision`` is "fp32",
-    "bf16" or "split_bf16" for the Legendre contractions.
+    "bf16" or "split_bf16" for the Legendre contractions.  ``table_source``
+    ("streamed" or "recurrence") selects how the tensor-core precisions get
+    the Legendre table: read from a precomputed bf16 table, or generated on
+    chip by the three-term recurrence from stored seeds.  ``max_channels``
+    bounds Cin / Cout of the fused spectral block (0: min(max_batch, 128)).
     """
 
     def __init__(self, nlat: int, nlon: int, grid: str = "gauss", lmax: int | None = None,
-                 mmax: int | None = None, precision: str = "fp32", device=None, max_batch: int = 256):
+                 mmax: int | None = None, precision: str = "fp32", device=None, max_batch: int = 256,
+                 table_source: str = "streamed", max_channels: int = 0):
         if lmax is None:
             lmax = nlat if grid == "gauss" else nlat - 1
         if mmax is None:
@@ -69,6 +74,8 @@ class Plan:
         opts.precision = _abi.PRECISIONS[precision]
         opts.device = dev.index
         opts.max_batch = int(max_batch)
+        opts.max_channels = int(max_channels)
+        opts.table_source = _abi.TABLE_SOURCES[table_source]
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _abi.check(_abi.lib().sht_plan(ctypes.byref(h), int(nlat), int(nlon), _abi.GRIDS[grid], int(lmax),
@@ -76,6 +83,7 @@ class Plan:
         self._h = h
         self.nlat, self.nlon, self.grid = int(nlat), int(nlon), grid
         self.lmax, self.mmax, self.precision = int(lmax), int(mmax), precision
+        self.table_source = table_source
         self.device = dev
         self.max_batch = int(max_batch)
 

@@ -17,12 +17,13 @@ STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3: "S
           4: "SHT_ERR_CUDA", 5: "SHT_ERR_TIMEOUT", 6: "SHT_ERR_INTERNAL"}
 GRIDS = {"gauss": 0, "equiangular_cc": 1, "equiangular_trapz": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "split_bf16": 2}
+TABLE_SOURCES = {"streamed": 0, "recurrence": 1}
 KERNEL_COUNT = 9
 
 
 class sht_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("max_batch", ctypes.c_int64),
-                ("max_channels", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("max_channels", ctypes.c_int), ("table_source", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 _i, _i64, _p, _d = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)

@@ -176,6 +176,10 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_tf_lo);
   cudaFree(p->d_ti_hi);
   cudaFree(p->d_ti_lo);
+  cudaFree(p->d_seeds);
+  cudaFree(p->d_coef);
+  cudaFree(p->d_xh);
+  cudaFree(p->d_xl);
   cudaFree(p->d_roff);
   cudaFree(p->d_soff);
   cudaFree(p->d_x_hi);
@@ -448,6 +452,8 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   for (int r : o.reserved)
     if (r != 0) return fail(SHT_ERR_INVALID_ARG, "reserved option fields must be zero");
   if (o.max_channels < 0) return fail(SHT_ERR_INVALID_ARG, "max_channels must be >= 0");
+  if (o.table_source != SHT_TABLE_STREAMED && o.table_source != SHT_TABLE_RECURRENCE)
+    return fail(SHT_ERR_INVALID_ARG, "unknown table_source");
   if (nlon > kMaxNlon) return fail(SHT_ERR_UNSUPPORTED, "nlon above 8192 is not supported");
   RadixPlan rp;
   if (!factor_radix(nlon, rp)) return fail(SHT_ERR_UNSUPPORTED, "nlon must factor into 2, 3 and 5");
@@ -557,8 +563,13 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     if (e == cudaSuccess && !tc)
       e = launch_table_gen_f32(p->d_table, p->d_tab_off, p->Khp, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
     if (e == cudaSuccess && tc) {
-      // bf16 hi/lo tables: forward [rows][Kp64], transposed [(2m+p) Kh + k'][Ip64]
+      // tensor-core plans: the Legendre table either as bf16 hi/lo tables
+      // streamed by TMA (forward [rows][Kp64], transposed
+      // [(2m + p) Kh + k'][Ip64]), or generated on chip from FP64 seeds every
+      // 32 rows of every (m, p), FP32 recurrence coefficients (zero past
+      // lmax) and the latitudes as hi + lo
       const bool split = o.precision == SHT_PREC_SPLIT_BF16;
+      const bool gen = o.table_source == SHT_TABLE_RECURRENCE;
       std::vector<int> roff(2 * (size_t)mmax), soff(2 * (size_t)mmax);
       int64_t frows = 0, srows = 0;
       for (int m = 0; m < mmax; m++)
@@ -569,26 +580,63 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
           srows += (leg_rows(lmax, m, q) + 63) / 64 * 64;
         }
       p->srows = srows;
-      const int Kp64 = (p->Kh + 63) / 64 * 64;
-      const int Ip64 = (leg_rows(lmax, 0, 0) + 63) / 64 * 64;
-      const int64_t irows = (int64_t)mmax * 2 * p->Kh;
-      const size_t fbytes = sizeof(__nv_bfloat16) * (size_t)frows * Kp64;
-      const size_t ibytes = sizeof(__nv_bfloat16) * (size_t)irows * Ip64;
       e = upload(&p->d_roff, roff);
       if (e == cudaSuccess) e = upload(&p->d_soff, soff);
-      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_hi, fbytes);
-      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_hi, ibytes);
-      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_lo, fbytes);
-      if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_lo, ibytes);
-      if (e == cudaSuccess) e = cudaMemset(p->d_tf_hi, 0, fbytes);
-      if (e == cudaSuccess) e = cudaMemset(p->d_ti_hi, 0, ibytes);
-      if (e == cudaSuccess) e = cudaMemset(p->d_tf_lo, 0, fbytes);
-      if (e == cudaSuccess) e = cudaMemset(p->d_ti_lo, 0, ibytes);
-      if (e == cudaSuccess)
-        e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_ti_hi, p->d_ti_lo, p->d_roff, Kp64, Ip64, d_x, d_s,
-                                  d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
-      p->table_bytes = (int64_t)(fbytes + ibytes) * 2;
       TcPlanView &T = p->tc;
+      T.gen = gen;
+      if (!gen) {
+        const int Kp64 = (p->Kh + 63) / 64 * 64;
+        const int Ip64 = (leg_rows(lmax, 0, 0) + 63) / 64 * 64;
+        const int64_t irows = (int64_t)mmax * 2 * p->Kh;
+        const size_t fbytes = sizeof(__nv_bfloat16) * (size_t)frows * Kp64;
+        const size_t ibytes = sizeof(__nv_bfloat16) * (size_t)irows * Ip64;
+        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_hi, fbytes);
+        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_hi, ibytes);
+        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_lo, fbytes);
+        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_lo, ibytes);
+        if (e == cudaSuccess) e = cudaMemset(p->d_tf_hi, 0, fbytes);
+        if (e == cudaSuccess) e = cudaMemset(p->d_ti_hi, 0, ibytes);
+        if (e == cudaSuccess) e = cudaMemset(p->d_tf_lo, 0, fbytes);
+        if (e == cudaSuccess) e = cudaMemset(p->d_ti_lo, 0, ibytes);
+        if (e == cudaSuccess)
+          e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_ti_hi, p->d_ti_lo, p->d_roff, Kp64, Ip64, d_x, d_s,
+                                    d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
+        p->table_bytes = (int64_t)(fbytes + ibytes) * 2;
+        if (e == cudaSuccess &&
+            !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, Kp64, frows, 64, 128) &&
+              tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, Kp64, frows, 64, 128) &&
+              tc_encode_2d(&T.tab_inv_hi, p->d_ti_hi, Ip64, irows, 64, 128) &&
+              tc_encode_2d(&T.tab_inv_lo, p->d_ti_lo, Ip64, irows, 64, 128)))
+          e = cudaErrorInvalidValue;
+      } else {
+        const int NB = (leg_rows(lmax, 0, 0) + 31) / 32 + 1;
+        const int Lc = lmax + 192;
+        const size_t seed_bytes = 16 * (size_t)mmax * 2 * NB * p->Kh;
+        std::vector<float2> coef((size_t)mmax * Lc, make_float2(0.f, 0.f));
+        for (int m = 0; m < mmax; m++)
+          for (int l = m + 2; l < lmax; l++)
+            coef[(size_t)m * Lc + l] = make_float2((float)a[(size_t)l * mmax + m],
+                                                   (float)(a[(size_t)l * mmax + m] * b[(size_t)l * mmax + m]));
+        std::vector<float> xhv(p->Kh), xlv(p->Kh);
+        for (int k = 0; k < p->Kh; k++) {
+          xhv[k] = (float)p->x[k];
+          xlv[k] = (float)(p->x[k] - (double)xhv[k]);
+        }
+        if (e == cudaSuccess) e = upload(&p->d_coef, coef);
+        if (e == cudaSuccess) e = upload(&p->d_xh, xhv);
+        if (e == cudaSuccess) e = upload(&p->d_xl, xlv);
+        if (e == cudaSuccess) e = dev_alloc(&p->d_seeds, seed_bytes);
+        if (e == cudaSuccess) e = cudaMemset(p->d_seeds, 0, seed_bytes);
+        if (e == cudaSuccess)
+          e = launch_seed_gen(p->d_seeds, NB, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
+        p->table_bytes = (int64_t)(seed_bytes + sizeof(float2) * coef.size());
+        T.seeds = p->d_seeds;
+        T.coef = p->d_coef;
+        T.xh = p->d_xh;
+        T.xl = p->d_xl;
+        T.NB = NB;
+        T.Lc = Lc;
+      }
       T.roff = p->d_roff;
       T.soff = p->d_soff;
       T.L = lmax;
@@ -596,12 +644,6 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       T.Kh = p->Kh;
       T.split = split;
       T.err = p->d_err;
-      if (e == cudaSuccess &&
-          !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, Kp64, frows, 64, 128) &&
-            tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, Kp64, frows, 64, 128) &&
-            tc_encode_2d(&T.tab_inv_hi, p->d_ti_hi, Ip64, irows, 64, 128) &&
-            tc_encode_2d(&T.tab_inv_lo, p->d_ti_lo, Ip64, irows, 64, 128)))
-        e = cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_x);

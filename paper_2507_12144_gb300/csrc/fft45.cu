@@ -11,6 +11,8 @@
 // one field are packed into one complex sequence and separated afterwards;
 // a CTA handles 8 fields of 32 / P ring pairs so that the folded output rows
 // are written in contiguous 8-field segments.
+#include <algorithm>
+
 #include "sht_internal.cuh"
 
 namespace shtgb {
@@ -226,13 +228,14 @@ struct OutBF16 {
   }
 };
 
+// One CTA of the analysis: fields bx kFB .. bx kFB + 7, ring pairs
+// by NPAIR .. by NPAIR + NPAIR - 1.
 template <int P, class Out>
-__global__ void __launch_bounds__(kThreads, 2)
-r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int ldc, const float2 *__restrict__ twiddle,
-             const float *__restrict__ ring_scale, int inverse_weights) {
+__device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restrict__ x, Out out, int nlat, int M,
+                                           int B, int ldc, const float2 *__restrict__ twiddle,
+                                           const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
-  constexpr int SEQ = kThreads / P;
   constexpr int BUF = kQ * (P + 1);
   extern __shared__ float2 smem[];
   float2 *tw = smem;
@@ -240,8 +243,8 @@ r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int l
   const int Kh = (nlat + 1) / 2;
   const int s = threadIdx.x / P, t = threadIdx.x % P;
   const int f = s % kFB, pp = s / kFB;
-  const int b = blockIdx.x * kFB + f;
-  const int kp = blockIdx.y * NPAIR + pp;
+  const int b = bx * kFB + f;
+  const int kp = by * NPAIR + pp;
   const int ks = nlat - 1 - kp;
   const bool live = (b < B) && (kp < Kh);
   for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
@@ -261,13 +264,13 @@ r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int l
   seq_fft<P>(v, t, buf, tw);
   __syncthreads();
   // separate the two real transforms, fold by parity, write 8-field segments
-  const int b0 = blockIdx.x * kFB;
+  const int b0 = bx * kFB;
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++)
   for (int e = threadIdx.x; e < M * kFB; e += kThreads) {
     const int ff = e % kFB;
     const int m = e / kFB;
-    const int kq = blockIdx.y * NPAIR + pq;
+    const int kq = by * NPAIR + pq;
     if (b0 + ff >= B || kq >= Kh) continue;
     const int kqs = nlat - 1 - kq;
     const float2 *Z = bufs + (pq * kFB + ff) * BUF;
@@ -292,10 +295,17 @@ r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int l
   }
 }
 
-template <int P>
+template <int P, class Out>
 __global__ void __launch_bounds__(kThreads, 2)
-c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, int ldc,
-             const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights) {
+r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int ldc, const float2 *__restrict__ twiddle,
+             const float *__restrict__ ring_scale, int inverse_weights) {
+  r2c45_body<P, Out>(blockIdx.x, blockIdx.y, x, out, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights);
+}
+
+template <int P>
+__device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restrict__ Gw, float *__restrict__ y,
+                                           int nlat, int M, int B, int ldc, const float2 *__restrict__ twiddle,
+                                           const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
   constexpr int BUF = kQ * (P + 1);
@@ -303,7 +313,7 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
   float2 *tw = smem;
   float2 *bufs = smem + N;
   const int Kh = (nlat + 1) / 2;
-  const int b0 = blockIdx.x * kFB;
+  const int b0 = bx * kFB;
   for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
   // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
   // the southern row (entries M..2M-1) of every sequence buffer
@@ -311,7 +321,7 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
   constexpr int kBatch = 8;
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
-    const int kq = blockIdx.y * NPAIR + pq;
+    const int kq = by * NPAIR + pq;
     if (kq >= Kh) continue;
     const int kqs = nlat - 1 - kq;
     const bool eq = (kq == kqs);
@@ -347,7 +357,7 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
   const int s = threadIdx.x / P, t = threadIdx.x % P;
   const int f = s % kFB, pp = s / kFB;
   const int b = b0 + f;
-  const int kp = blockIdx.y * NPAIR + pp;
+  const int kp = by * NPAIR + pp;
   const int ksth = nlat - 1 - kp;
   const bool live = (b < B) && (kp < Kh);
   float2 *buf = bufs + s * BUF;
@@ -381,6 +391,74 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
     const float2 o = buf[spec_index<P>(j)];
     rn[j] = o.x;
     if (!eq) rs[j] = -o.y;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 2)
+c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, int ldc,
+             const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights) {
+  c2r45_body<P>(blockIdx.x, blockIdx.y, Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights);
+}
+
+// Grouped launches: one grid over several problems (grids and batches) of
+// one batched call.  CTA j belongs to the segment s with blk0[s] <= j <
+// blk0[s + 1]; its (bx, by) follow from gx[s], and the segment's P selects
+// the transform length.
+struct Fft45Seg {
+  const float *in;
+  float *outf;
+  __nv_bfloat16 *hi, *lo;
+  const float2 *tw;
+  const float *ring;
+  int nlat, M, B, ldc, wts, P, gx, blk0;
+};
+struct Fft45Group {
+  Fft45Seg seg[kMaxFftGroup];
+  int nseg;
+};
+
+__device__ __forceinline__ int group_segment(const Fft45Group &g, int blk) {
+  int s = 0;
+  while (s + 1 < g.nseg && blk >= g.seg[s + 1].blk0) s++;
+  return s;
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(kThreads, 2) r2c45_grouped_kernel(const __grid_constant__ Fft45Group g) {
+  const int s = group_segment(g, blockIdx.x);
+  const Fft45Seg &q = g.seg[s];
+  const int local = blockIdx.x - q.blk0;
+  const int bx = local % q.gx, by = local / q.gx;
+  if (kBF16) {
+    const OutBF16 out{q.hi, q.lo};
+    switch (q.P) {
+      case 32: r2c45_body<32>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      case 16: r2c45_body<16>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      case 8: r2c45_body<8>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      default: r2c45_body<4>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+    }
+  } else {
+    const OutF32 out{q.outf};
+    switch (q.P) {
+      case 32: r2c45_body<32>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      case 16: r2c45_body<16>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      case 8: r2c45_body<8>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      default: r2c45_body<4>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) c2r45_grouped_kernel(const __grid_constant__ Fft45Group g) {
+  const int s = group_segment(g, blockIdx.x);
+  const Fft45Seg &q = g.seg[s];
+  const int local = blockIdx.x - q.blk0;
+  const int bx = local % q.gx, by = local / q.gx;
+  switch (q.P) {
+    case 32: c2r45_body<32>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+    case 16: c2r45_body<16>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+    case 8: c2r45_body<8>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+    default: c2r45_body<4>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
   }
 }
 
@@ -428,7 +506,83 @@ cudaError_t r2c45_dispatch(int nlon, const float *x, Out out, int nlat, int M, i
   }
 }
 
+size_t smem45_of(int P) {
+  switch (P) {
+    case 32: return smem45<32>();
+    case 16: return smem45<16>();
+    case 8: return smem45<8>();
+    default: return smem45<4>();
+  }
+}
+
+// Fill the CTA ranges of a group; returns the total CTA count and the
+// largest shared-memory size.
+int64_t group_layout(Fft45Group &g, const Fft45Item *items, int n, size_t &smem) {
+  g.nseg = n;
+  int64_t blk = 0;
+  smem = 0;
+  for (int i = 0; i < n; i++) {
+    const Fft45Item &it = items[i];
+    Fft45Seg &q = g.seg[i];
+    const int P = it.nlon / kQ;
+    const int NPAIR = kThreads / P / kFB;
+    const int Kh = (it.nlat + 1) / 2;
+    q.in = it.in;
+    q.outf = it.outf;
+    q.hi = it.hi;
+    q.lo = it.lo;
+    q.tw = it.twiddle;
+    q.ring = it.ring_scale;
+    q.nlat = it.nlat;
+    q.M = it.M;
+    q.B = it.B;
+    q.ldc = it.ldc;
+    q.wts = it.inverse_weights;
+    q.P = P;
+    q.gx = (it.B + kFB - 1) / kFB;
+    q.blk0 = (int)blk;
+    blk += (int64_t)q.gx * ((Kh + NPAIR - 1) / NPAIR);
+    smem = std::max(smem, smem45_of(P));
+  }
+  return blk;
+}
+
 }  // namespace
+
+cudaError_t launch_r2c45_grouped(const Fft45Item *items, int n, bool bf16, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxFftGroup) return cudaErrorInvalidValue;
+  for (int i = 0; i < n; i++)
+    if (!fft45_supported(items[i].nlon) || items[i].B <= 0) return cudaErrorInvalidValue;
+  Fft45Group g{};
+  size_t smem = 0;
+  const int64_t blocks = group_layout(g, items, n, smem);
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  const void *fn = bf16 ? (const void *)r2c45_grouped_kernel<true> : (const void *)r2c45_grouped_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (bf16)
+    r2c45_grouped_kernel<true><<<(unsigned)blocks, kThreads, smem, st>>>(g);
+  else
+    r2c45_grouped_kernel<false><<<(unsigned)blocks, kThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2r45_grouped(const Fft45Item *items, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxFftGroup) return cudaErrorInvalidValue;
+  for (int i = 0; i < n; i++)
+    if (!fft45_supported(items[i].nlon) || items[i].B <= 0) return cudaErrorInvalidValue;
+  Fft45Group g{};
+  size_t smem = 0;
+  const int64_t blocks = group_layout(g, items, n, smem);
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute((const void *)c2r45_grouped_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  c2r45_grouped_kernel<<<(unsigned)blocks, kThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
 
 bool fft45_supported(int nlon) {
   return nlon == 45 * 32 || nlon == 45 * 16 || nlon == 45 * 8 || nlon == 45 * 4;

@@ -38,7 +38,9 @@ using namespace tc;
 
 constexpr int kRows = 128;    // UMMA M
 constexpr int kKc = 64;       // K per stage (one 128-byte bf16 row)
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;     // filter: TMA, MMA, TMEM, -, 4 epilogue warps
+constexpr int kThreadsGen = 512;  // Legendre: the same + 8 table-generator warps
+constexpr int kSeedRows = 32;     // rows between recurrence seeds
 constexpr int kMaxStages = 6;
 constexpr uint32_t kABytes = kRows * 128;  // one A tile (hi or lo)
 
@@ -87,7 +89,9 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 //   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[soff + i][c]   (A = table, B = data, MN-major)
 //   kFilt: D[m][n]  = sum_k  X[l M + m][b kx + k] WR[l][n][k] (A = data, B = weights, K-major)
 // Table and weights always enter split (hi + lo); data enters split for
-// split BF16 and rounded (hi only) for BF16.
+// split BF16 and rounded (hi only) for BF16.  The Legendre table of kFwd /
+// kInv either streams from a precomputed bf16 table by TMA (kGen = false) or
+// is generated on chip by 8 extra warps from recurrence seeds (kGen = true).
 // ---------------------------------------------------------------------------
 enum Mode { kFwd = 0, kInv = 1, kFilt = 2 };
 
@@ -104,9 +108,25 @@ struct FwdOut {
   int ldo, cin, kx;
 };
 
+// Recurrence seeds of the on-chip Legendre table: for order m, parity p,
+// 32-row block j (rows i = 32 j .. 32 j + 31, l = m + p + 2 i) and latitude
+// k', Phat at l0 = m + p + 64 j and l0 + 1, as FP32 mantissas s0, s1 of a
+// common power of two 2^e (e = kZeroBlock: the block is negligible).
+struct Seed {
+  float s0, s1;
+  int e, pad;
+};
+constexpr int kZeroBlock = -100000;
+
 struct TcArgs {
   // geometry
   int L, M, Kh, B, Nt, nct, stages, ntiles;
+  // on-chip table: seeds [((2m + p) NB + j) Kh + k'], coefficients
+  // coef[m Lc + l] = (a_lm, a_lm b_lm), latitudes x = xh + xl
+  const Seed *seeds;
+  const float2 *coef;
+  const float *xh, *xl;
+  int NB, Lc;
   // forward / inverse
   const LegTile *tiles;
   const int *roff, *soff;
@@ -121,6 +141,7 @@ struct TcArgs {
 };
 
 __host__ __device__ inline int a_count(int mode, bool split) { return (mode == kFilt && !split) ? 1 : 2; }
+__host__ __device__ inline int threads_of(bool gen) { return gen ? kThreadsGen : kThreads; }
 __host__ __device__ inline int b_count(int mode, bool split) { return (mode == kFilt || split) ? 2 : 1; }
 __host__ __device__ inline uint32_t b_bytes_of(int mode, int Nt) {
   return mode == kFilt ? (uint32_t)Nt * 128u : (uint32_t)((Nt + 63) / 64) * 8192u;
@@ -174,7 +195,7 @@ __device__ __forceinline__ TileInfo tile_info(const TcArgs &a, int t) {
   return ti;
 }
 
-template <int kMode, bool kSplit>
+template <int kMode, bool kSplit, bool kGen>
 __device__ __forceinline__ void issue_chunk(unsigned char *st, int Nt, uint32_t tmem, uint32_t idesc, bool first) {
   const int na = a_count(kMode, kSplit);
   const uint32_t bb = b_bytes_of(kMode, Nt);
@@ -191,16 +212,20 @@ __device__ __forceinline__ void issue_chunk(unsigned char *st, int Nt, uint32_t 
       mma_bf16(tmem, ah, bl, idesc, 1u);
       if (kSplit) mma_bf16(tmem, desc_advance(desc_kmajor_sw128(a_lo), ks * 32), bh, idesc, 1u);
     } else {
-      const uint64_t al = desc_advance(desc_kmajor_sw128(a_lo), ks * 32);
+      // A = table: K-major from TMA, or generated (MN-major forward, K-major inverse)
+      constexpr bool kAmn = kGen && kMode == kFwd;
+      const uint64_t ah2 = kAmn ? desc_mnmajor_sw128(a_hi + ks * 2048, 8192, 1024) : ah;
+      const uint64_t al = kAmn ? desc_mnmajor_sw128(a_lo + ks * 2048, 8192, 1024)
+                               : desc_advance(desc_kmajor_sw128(a_lo), ks * 32);
       const uint64_t bh = desc_mnmajor_sw128(b_hi + ks * 2048, 8192, 1024);
-      mma_bf16(tmem, ah, bh, idesc, acc0);
+      mma_bf16(tmem, ah2, bh, idesc, acc0);
       mma_bf16(tmem, al, bh, idesc, 1u);
-      if (kSplit) mma_bf16(tmem, ah, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
+      if (kSplit) mma_bf16(tmem, ah2, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
     }
   }
 }
 
-template <int kMode, bool kSplit>
+template <int kMode, bool kSplit, bool kGen>
 __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti, int kc, int Nt,
                                            const CUtensorMap *ta_hi, const CUtensorMap *ta_lo,
                                            const CUtensorMap *tb_hi, const CUtensorMap *tb_lo, uint64_t *bar) {
@@ -208,8 +233,10 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
   const uint32_t bb = b_bytes_of(kMode, Nt);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
-  tma_load_2d(a_hi, ta_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
-  if (na == 2) tma_load_2d(a_lo, ta_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  if (kMode == kFilt || !kGen) {
+    tma_load_2d(a_hi, ta_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
+    if (na == 2) tma_load_2d(a_lo, ta_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  }
   if (kMode == kFilt) {
     tma_load_2d(b_hi, tb_hi, bar, kc * kKc, ti.b_row0);
     tma_load_2d(b_lo, tb_lo, bar, kc * kKc, ti.b_row0);
@@ -307,8 +334,116 @@ __device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, ui
   }
 }
 
-template <int kMode, bool kSplit>
-__global__ void __launch_bounds__(kThreads, 1)
+// Table generator (warps 8..15 of the Legendre kernels): one thread runs the
+// three-term recurrence, folded as
+//   Phat_{l} = (a_l x) Phat_{l-1} - (a_l b_l) Phat_{l-2},
+// for one latitude over one 32-row block of one parity (63 steps from the
+// block's seeds) in FP32: one FMA per step on the dependency chain, a_l x
+// formed off the chain from x = xh + xl, mantissas carried beside a
+// power-of-two exponent and renormalised every 4 steps when above 2^64.
+// The 32 values go to shared memory as bf16 hi/lo in 16-byte chunks of 8
+// consecutive rows:
+//   forward: A[i][k'] MN-major (rows i contiguous): thread (k' = 64 kc + g mod
+//            64, block r0/32 + g/64) of tile rows r0 .. r0 + 127;
+//   inverse: A[k'][i] K-major (i contiguous): thread (k' = r0 + g mod 128,
+//            block 2 kc + g/128).
+// Seed of the chunk (kc) handled by generator thread g, with its latitude.
+struct GenIn {
+  Seed sd;
+  float xh, xl;
+};
+
+template <int kMode>
+__device__ __forceinline__ void gen_coords(const TileInfo &ti, int kc, int g, int &kp, int &j) {
+  if (kMode == kFwd) {
+    kp = kc * kKc + (g & 63);
+    j = ti.r0 / kSeedRows + (g >> 6);
+  } else {
+    kp = ti.r0 + (g & 127);
+    j = 2 * kc + (g >> 7);
+  }
+}
+
+template <int kMode>
+__device__ __forceinline__ GenIn gen_load(const TcArgs &a, const TileInfo &ti, int kc, int g) {
+  int kp, j;
+  gen_coords<kMode>(ti, kc, g, kp, j);
+  GenIn in{{0.f, 0.f, kZeroBlock, 0}, 0.f, 0.f};
+  if (kc < ti.nk && kp < a.Kh) {
+    if (j < a.NB) in.sd = a.seeds[((int64_t)(ti.m * 2 + ti.p) * a.NB + j) * a.Kh + kp];
+    in.xh = a.xh[kp];
+    in.xl = a.xl[kp];
+  }
+  return in;
+}
+
+// cs: the tile's recurrence coefficients in shared memory, cs[l - lbase].
+template <int kMode>
+__device__ __forceinline__ void generate_chunk(const TcArgs &a, const TileInfo &ti, int kc, int g,
+                                               unsigned char *a_hi, unsigned char *a_lo, const GenIn &in,
+                                               const float2 *cs, int lbase) {
+  int kp, j, row, cbase;
+  gen_coords<kMode>(ti, kc, g, kp, j);
+  if (kMode == kFwd) {
+    row = g & 63;  // column k' inside the tile
+    cbase = 4 * ((g >> 6) & 1);  // 8-row chunk index inside the 64-row M block
+  } else {
+    row = g & 127;
+    cbase = 4 * (g >> 7);
+  }
+  const Seed sd = in.sd;
+  const float xh = in.xh, xl = in.xl;
+  const int l0 = ti.m + ti.p + 2 * kSeedRows * j;
+  const bool zero = sd.e == kZeroBlock || l0 >= a.L;
+  float pa = zero ? 0.f : sd.s0, pb = zero ? 0.f : sd.s1;  // scaled Phat_l, Phat_{l+1}
+  int E = zero ? 0 : sd.e;
+  const float2 *cf = cs + (zero ? 0 : l0 + 2 - lbase);
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    uint32_t h[4], lw[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const float scale = (zero || E < -126) ? 0.f : __int_as_float((E + 127) << 23);
+      const float v0 = pa * scale;
+      float2 c[4];
+#pragma unroll
+      for (int w = 0; w < 4; w++) c[w] = zero ? make_float2(0.f, 0.f) : cf[w];
+      if (!zero) cf += 4;
+      // two outputs (rows l, l + 2): four recurrence steps
+      const float pc = fmaf(fmaf(c[0].x, xh, c[0].x * xl), pb, -c[0].y * pa);
+      const float pd = fmaf(fmaf(c[1].x, xh, c[1].x * xl), pc, -c[1].y * pb);
+      const float v1 = pc * scale;
+      const float pe = fmaf(fmaf(c[2].x, xh, c[2].x * xl), pd, -c[2].y * pc);
+      const float pf = fmaf(fmaf(c[3].x, xh, c[3].x * xl), pe, -c[3].y * pd);
+      pa = pe;
+      pb = pf;
+      if (fabsf(pb) > 1.8446744e19f) {  // 2^64
+        pa *= 5.4210109e-20f;            // 2^-64
+        pb *= 5.4210109e-20f;
+        E += 64;
+      }
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
+      const float2 hf = __bfloat1622float2(hh);
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+      h[u] = *reinterpret_cast<const uint32_t *>(&hh);
+      lw[u] = *reinterpret_cast<const uint32_t *>(&ll);
+    }
+    const int chunk = cbase + q;
+    uint32_t off;
+    if (kMode == kFwd) {
+      const int hb = (g >> 6) >> 1;  // 64-row M block of the 128-row tile
+      off = (uint32_t)hb * 8192u + (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u +
+            ((uint32_t)(chunk ^ (row & 7)) << 4);
+    } else {
+      off = (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
+    }
+    *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+template <int kMode, bool kSplit, bool kGen>
+__global__ void __launch_bounds__(kGen ? kThreadsGen : kThreads, 1)
 tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                      const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                      const TcArgs a) {
@@ -325,7 +460,7 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
   if (warp == 2) tmem_alloc(&tmem_slot, ncols);
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; s++) {
-      mbar_init(&full_bar[s], 1);
+      mbar_init(&full_bar[s], kGen ? 1 + 8 : 1);  // + the 8 generator warps
       mbar_init(&empty_bar[s], 1);
     }
     for (int i = 0; i < 2; i++) {
@@ -353,13 +488,46 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
         const uint32_t use = g / (uint32_t)S;
         if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, a.err);
         unsigned char *st = base + (size_t)s * sbytes;
-        mbar_arrive_expect_tx(&full_bar[s], sbytes);
-        load_chunk<kMode, kSplit>(st, ti, kc, a.Nt, &ta_hi, &ta_lo, &tb_hi, &tb_lo, &full_bar[s]);
+        // with kGen the generator warps fill the A buffers
+        mbar_arrive_expect_tx(&full_bar[s], kGen ? sbytes - 2u * kABytes : sbytes);
+        load_chunk<kMode, kSplit, kGen>(st, ti, kc, a.Nt, &ta_hi, &ta_lo, &tb_hi, &tb_lo, &full_bar[s]);
+      }
+    }
+  } else if (kGen && warp >= 8) {
+    // table generators: the tile's recurrence coefficients are staged in
+    // shared memory (after the stage ring), the next chunk's seed is loaded
+    // while the current chunk is generated
+    const int gtid = threadIdx.x - 256;
+    float2 *cs = reinterpret_cast<float2 *>(base + (size_t)S * sbytes);
+    uint32_t g = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      const TileInfo ti = tile_info<kMode>(a, t);
+      const int lbase = ti.m + ti.p + (kMode == kFwd ? 2 * ti.r0 : 0);
+      const int ncoef = kMode == kFwd ? 4 * kKc + 8 : 2 * kKc * ti.nk + 8;
+      asm volatile("bar.sync 2, 256;" ::: "memory");  // previous tile's coefficients no longer read
+      for (int e = gtid; e < ncoef; e += 256) {
+        const int l = lbase + e;
+        cs[e] = l < a.Lc ? __ldg(a.coef + (int64_t)ti.m * a.Lc + l) : make_float2(0.f, 0.f);
+      }
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      GenIn in = gen_load<kMode>(a, ti, 0, gtid);
+      for (int kc = 0; kc < ti.nk; kc++, g++) {
+        const GenIn next = gen_load<kMode>(a, ti, kc + 1, gtid);
+        const int s = (int)(g % (uint32_t)S);
+        const uint32_t use = g / (uint32_t)S;
+        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, a.err);
+        unsigned char *st = base + (size_t)s * sbytes;
+        generate_chunk<kMode>(a, ti, kc, gtid, st, st + kABytes, in, cs, lbase);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[s]);
+        in = next;
       }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t idesc = idesc_bf16_f32(kRows, a.Nt, kMode != kFilt);
+    uint32_t idesc = idesc_bf16_f32(kRows, a.Nt, kMode != kFilt);
+    if (kGen && kMode == kFwd) idesc |= 1u << 15;  // generated table enters MN-major
     uint32_t g = 0, it = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, it++) {
       const TileInfo ti = tile_info<kMode>(a, t);
@@ -373,7 +541,7 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
         const uint32_t use = g / (uint32_t)S;
         mbar_wait(&full_bar[s], use & 1, a.err);
         tc_fence_after();
-        issue_chunk<kMode, kSplit>(base + (size_t)s * sbytes, a.Nt, tacc, idesc, kc == 0);
+        issue_chunk<kMode, kSplit, kGen>(base + (size_t)s * sbytes, a.Nt, tacc, idesc, kc == 0);
         mma_commit(&empty_bar[s]);
       }
       if (ti.nk > 0)
@@ -495,6 +663,44 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
   }
 }
 
+// FP64 recurrence seeds (one thread per (m, k')): at the start l0 of every
+// 32-row block of both parities, store Phat_{l0} and Phat_{l0+1} as FP32
+// mantissas of a common power of two.
+__global__ void seed_gen_kernel(Seed *__restrict__ seeds, int NB, const double *__restrict__ xk,
+                                const double *__restrict__ sk, const double *__restrict__ a,
+                                const double *__restrict__ bcoef, const double *__restrict__ seedf, int L, int M,
+                                int Kh) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (k >= Kh || m >= M) return;
+  const double x = xk[k], s = sk[k];
+  double pmm = 0.28209479177387814347;  // 1 / sqrt(4 pi)
+  for (int i = 1; i <= m; i++) pmm *= seedf[i] * s;
+  double cur = pmm;
+  double nxt = (m + 1 < L) ? sqrt(2.0 * m + 3.0) * x * pmm : 0.0;
+  for (int l = m; l < L; l++) {
+    const int d = l - m, p = d & 1, i = d >> 1;
+    if ((i % kSeedRows) == 0) {
+      Seed sd{0.f, 0.f, kZeroBlock, 0};
+      const double mx = fmax(fabs(cur), fabs(nxt));
+      if (mx > 0.0) {
+        const int e = ilogb(mx);
+        sd.s0 = (float)scalbn(cur, -e);
+        sd.s1 = (float)scalbn(nxt, -e);
+        sd.e = e;
+      }
+      seeds[((int64_t)(m * 2 + p) * NB + i / kSeedRows) * Kh + k] = sd;
+    }
+    double nn = 0.0;
+    if (l + 2 < L) {
+      const int64_t ci = (int64_t)(l + 2) * M + m;
+      nn = a[ci] * (x * nxt - bcoef[ci] * cur);
+    }
+    cur = nxt;
+    nxt = nn;
+  }
+}
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -512,23 +718,43 @@ void column_tiles(int B, int &Nt, int &nct) {
   Nt = ((C2 + nct - 1) / nct + 15) / 16 * 16;
 }
 
-template <int kMode>
-cudaError_t launch_persistent(bool split, const CUtensorMap &ta_hi, const CUtensorMap &ta_lo,
-                              const CUtensorMap &tb_hi, const CUtensorMap &tb_lo, TcArgs &args, cudaStream_t st) {
-  if (args.ntiles <= 0) return cudaSuccess;
-  const int sb = (int)stage_bytes(kMode, split, args.Nt);
-  const int budget = 220 * 1024 - 1024;
-  args.stages = std::max(2, std::min(kMaxStages, budget / sb));
-  const size_t smem = 1024 + (size_t)args.stages * sb;
-  const void *fn = split ? (const void *)tc_persistent_kernel<kMode, true>
-                         : (const void *)tc_persistent_kernel<kMode, false>;
+template <int kMode, bool kSplit, bool kGen>
+cudaError_t start_persistent(unsigned grid, size_t smem, const CUtensorMap &ta_hi, const CUtensorMap &ta_lo,
+                             const CUtensorMap &tb_hi, const CUtensorMap &tb_lo, const TcArgs &args,
+                             cudaStream_t st) {
+  auto fn = tc_persistent_kernel<kMode, kSplit, kGen>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  fn<<<grid, threads_of(kGen), smem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  return cudaSuccess;
+}
+
+template <int kMode>
+cudaError_t launch_persistent(bool split, bool gen, const CUtensorMap &ta_hi, const CUtensorMap &ta_lo,
+                              const CUtensorMap &tb_hi, const CUtensorMap &tb_lo, TcArgs &args, cudaStream_t st) {
+  if (args.ntiles <= 0) return cudaSuccess;
+  gen = gen && kMode != kFilt;
+  const int sb = (int)stage_bytes(kMode, split, args.Nt);
+  // coefficient staging of the table generators (forward: one 128-row tile,
+  // inverse: every chunk of one (m, p) block)
+  const size_t cbytes =
+      !gen ? 0 : sizeof(float2) * (size_t)(2 * kKc * ((leg_rows(args.L, 0, 0) + kKc - 1) / kKc) + 4 * kKc + 16);
+  const int budget = 220 * 1024 - 1024 - (int)cbytes;
+  args.stages = std::max(2, std::min(kMaxStages, budget / sb));
+  const size_t smem = 1024 + (size_t)args.stages * sb + cbytes;
   const unsigned grid = (unsigned)std::min(args.ntiles, sm_count());
-  if (split)
-    tc_persistent_kernel<kMode, true><<<grid, kThreads, smem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
-  else
-    tc_persistent_kernel<kMode, false><<<grid, kThreads, smem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  cudaError_t e;
+  if constexpr (kMode == kFilt) {
+    e = split ? start_persistent<kMode, true, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st)
+              : start_persistent<kMode, false, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st);
+  } else if (gen) {
+    e = split ? start_persistent<kMode, true, true>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st)
+              : start_persistent<kMode, false, true>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st);
+  } else {
+    e = split ? start_persistent<kMode, true, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st)
+              : start_persistent<kMode, false, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st);
+  }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -565,6 +791,13 @@ cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_b
   return cudaGetLastError();
 }
 
+cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
+                            const double *b, const double *seedf, int L, int M, int Kh, cudaStream_t st) {
+  dim3 grid((Kh + 127) / 128, M);
+  seed_gen_kernel<<<grid, 128, 0, st>>>(reinterpret_cast<Seed *>(seeds), NB, xk, sk, a, b, seedf, L, M, Kh);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
                               __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
                               cudaStream_t st) {
@@ -581,7 +814,13 @@ cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int nti
   a.soff = T.soff;
   a.fout = FwdOut{xhat, rows_hi, rows_lo, ldo, cin > 0 ? cin : 1, kx};
   a.err = T.err;
-  return launch_persistent<kFwd>(T.split, T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.split ? T.f_lo : T.f_hi, a, st);
+  a.seeds = reinterpret_cast<const Seed *>(T.seeds);
+  a.coef = T.coef;
+  a.xh = T.xh;
+  a.xl = T.xl;
+  a.NB = T.NB;
+  a.Lc = T.Lc;
+  return launch_persistent<kFwd>(T.split, T.gen, T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.split ? T.f_lo : T.f_hi, a, st);
 }
 
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
@@ -600,7 +839,14 @@ cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int nti
   a.Gw = Gw;
   a.ldc = ldc;
   a.err = T.err;
-  return launch_persistent<kInv>(T.split, T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.split ? T.s_lo : T.s_hi, a, st);
+  a.seeds = reinterpret_cast<const Seed *>(T.seeds);
+  a.coef = T.coef;
+  a.xh = T.xh;
+  a.xl = T.xl;
+  a.NB = T.NB;
+  a.Lc = T.Lc;
+  return launch_persistent<kInv>(T.split, T.gen, T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.split ? T.s_lo : T.s_hi, a,
+                                 st);
 }
 
 cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
@@ -632,7 +878,7 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   a.s_hi = s_hi;
   a.s_lo = s_lo;
   a.err = T.err;
-  return launch_persistent<kFilt>(T.split, T.x_hi, T.split ? T.x_lo : T.x_hi, tw_hi, tw_lo, a, st);
+  return launch_persistent<kFilt>(T.split, false, T.x_hi, T.split ? T.x_lo : T.x_hi, tw_hi, tw_lo, a, st);
 }
 
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,

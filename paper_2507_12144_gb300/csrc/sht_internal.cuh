@@ -45,20 +45,32 @@ struct TableF32 {
 // Fourier workspace F[(2m+p) Kh + k'][ldcb] (hi, lo) and of the internal
 // coefficient rows S[soff[2m+p] + i][ldcb] (hi, lo), plus the error word.
 struct TcPlanView {
-  CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;
+  CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;  // bf16 table (streamed)
   CUtensorMap f_hi, f_lo, s_hi, s_lo;
   CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
   const int *roff, *soff;
+  // on-chip Legendre table: seeds (16 B each), coefficients [M][Lc],
+  // latitudes as FP32 hi + lo
+  const void *seeds;
+  const float2 *coef;
+  const float *xh, *xl;
+  int NB, Lc;
   int L, M, Kh;
   bool split;
+  bool gen;  // generate the table on chip instead of streaming it
   unsigned *err;
 };
 
 bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows);
+// FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64],
+// transposed layout [(2m + p) Kh + k'][Ip64]).
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
                                   const int *roff, int Kp64, int Ip64, const double *xk, const double *sk,
                                   const double *a, const double *b, const double *seed, int L, int M, int Kh,
                                   cudaStream_t st);
+// FP64 seeds of the on-chip Legendre table (every 32 rows of every (m, p)).
+cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
+                            const double *b, const double *seedf, int L, int M, int Kh, cudaStream_t st);
 // Forward contraction on the tensor cores from the bf16 Fourier workspace;
 // output to the API layout xhat (rows_hi == NULL) or to l-major bf16 rows
 // rows[l M + m][ldo] with member b = f / cin at columns b kx + 2 (f mod cin).
@@ -121,6 +133,22 @@ cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfl
                          cudaStream_t st);
 cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, int ldc,
                          const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st);
+
+// One problem of a grouped longitude launch: the arguments of launch_r2c45
+// (in = x; outf = Fw or hi/lo) or launch_c2r45 (in = Gw, outf = y).
+struct Fft45Item {
+  const float *in;
+  float *outf;
+  __nv_bfloat16 *hi, *lo;
+  const float2 *twiddle;
+  const float *ring_scale;
+  int nlat, nlon, M, B, ldc, inverse_weights;
+};
+constexpr int kMaxFftGroup = 8;
+// Grouped launches of up to kMaxFftGroup problems (every nlon = 45 P, B >= 1)
+// in one grid; bf16 selects the bf16 hi/lo output of the analysis.
+cudaError_t launch_r2c45_grouped(const Fft45Item *items, int n, bool bf16, cudaStream_t st);
+cudaError_t launch_c2r45_grouped(const Fft45Item *items, int n, cudaStream_t st);
 
 // Longitude synthesis from folded Gw[m][p][k'][ldc]:
 //   u_kj = ring_scale[k] * sum_m c_m Re(G_k(m) e^{2 pi i j m / nlon})
@@ -198,6 +226,11 @@ struct sht_plan_s {
   // device memory (all owned)
   unsigned *d_err = nullptr;   // error word of bounded device waits
   shtgb::TcPlanView tc{};      // tensor-core view (bf16 precisions)
+  __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;  // bf16 tables
+  int table_source = 0;        // 0: streamed bf16 table, 1: on-chip recurrence
+  void *d_seeds = nullptr;     // recurrence seeds of the on-chip table
+  float2 *d_coef = nullptr;    // FP32 recurrence coefficients [M][Lc]
+  float *d_xh = nullptr, *d_xl = nullptr;  // latitudes as FP32 hi + lo
   int ldcb = 0;                // bf16 row stride of the workspaces (elements)
   int64_t srows = 0;           // rows of the internal coefficient layout
   int *d_soff = nullptr;       // [2 M] first internal row of block (m, p)
@@ -209,7 +242,6 @@ struct sht_plan_s {
   void *d_ftiles = nullptr;    // filter tiles (l, m0)
   int n_ftiles = 0;
   __nv_bfloat16 *d_s_hi = nullptr, *d_s_lo = nullptr;  // bf16 internal rows [srows][ldcb]
-  __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;
   int *d_roff = nullptr;
   float *d_table = nullptr;
   int64_t *d_tab_off = nullptr;

@@ -88,6 +88,11 @@ def test_reserved_options_must_be_zero(lib):
     o.reserved[3] = 0
     o.max_batch = 0
     assert lib.sht_plan(ctypes.byref(h), 33, 64, 0, 32, 32, ctypes.byref(o)) == 1
+    o.max_batch = 16
+    assert o.table_source == 0
+    o.table_source = 2
+    assert lib.sht_plan(ctypes.byref(h), 33, 64, 0, 32, 32, ctypes.byref(o)) == 1
+    assert b"table_source" in lib.sht_last_error_message()
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -23,7 +23,11 @@ TOL_FP32 = 1e-5
 # fraction bits); for smooth fields the rounding errors of neighbouring rows
 # are alike and do not average out, so the bound is the unit roundoff itself.
 TOL = {"fp32": 1e-5, "split_bf16": 2e-5, "bf16": 2.0 ** -8}
-PRECS = ["fp32", "split_bf16", "bf16"]
+# "+rec": the tensor-core precisions with the Legendre table generated on
+# chip by the recurrence instead of streamed from the precomputed table
+TOL.update({p + "+rec": TOL[p] for p in ("split_bf16", "bf16")})
+PRECS = ["fp32", "split_bf16", "bf16", "split_bf16+rec", "bf16+rec"]
+TC_PRECS = ["split_bf16", "bf16", "split_bf16+rec", "bf16+rec"]
 
 SHAPES = [
     # nlat, nlon, grid, L, M, B
@@ -49,6 +53,10 @@ def shtgb():
 
 
 def _plan(shtgb, nlat, nlon, grid, L, M, **kw):
+    prec = kw.get("precision", "fp32")
+    if prec.endswith("+rec"):
+        kw["precision"] = prec[:-4]
+        kw["table_source"] = "recurrence"
     return shtgb.Plan(nlat, nlon, grid, L, M, **kw)
 
 
@@ -139,12 +147,18 @@ def test_block_and_fused_filter_inverse_match_oracle(shtgb, prec):
     xh = shtgb.sht_forward(plan, x)
     y2 = shtgb.spectral_filter_inverse(plan, xh, Wg).cpu().numpy()
     plan.check()
-    if prec == "bf16":
+    if prec.startswith("bf16"):
         # the data is rounded twice (Fourier rows, filter output) and the
         # channel mixing can shrink single output fields, so the bound is two
         # roundings relative to the whole member
         for out in (y, y2):
             assert rel_l2(out, ref_y) <= 2 * TOL_FP32
+    elif prec.startswith("split_bf16"):
+        # three chained split contractions (forward, filter, inverse), each
+        # within the per-operation tolerance; the whole member within one
+        for out in (y, y2):
+            assert per_field_spatial_err(out, ref_y).max() <= 3 * TOL_FP32
+            assert rel_l2(out, ref_y) <= TOL_FP32
     else:
         assert per_field_spatial_err(y, ref_y).max() <= TOL_FP32
         assert per_field_spatial_err(y2, ref_y).max() <= TOL_FP32
@@ -172,7 +186,7 @@ def test_round_trip_and_ylm_deltas_gauss_33x64(shtgb):
         assert np.abs(out[i] - want).max() < 5e-6
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "bf16"])
+@pytest.mark.parametrize("prec", TC_PRECS)
 def test_tensor_core_column_tiles(shtgb, prec):
     """Batches above 128 fields span several 256-column tiles of the
     tensor-core kernels, with a ragged last tile."""
@@ -317,7 +331,7 @@ def test_adjoint_identities_on_gpu(shtgb):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16", "split_bf16+rec"])
 def test_full_size_block_against_oracle(shtgb, prec):
     nlat, nlon, grid, L, M = 721, 1440, "equiangular_cc", 720, 720
     TOL_FP32 = TOL[prec]
