@@ -107,7 +107,8 @@ typedef enum {
  *   TMA on every call (table bytes re-read per call, no recurrence work).
  * RECURRENCE: only FP64 seeds every 32 degrees are stored; extra warps of
  *   the Legendre kernels run the three-term recurrence in FP32 on chip
- *   (about 1/16 of the table bytes, more instructions per call). */
+ *   (about 1/16 of the table bytes, more instructions per call); lmax <=
+ *   1400, else sht_plan returns UNSUPPORTED. */
 typedef enum {
   SHT_TABLE_STREAMED = 0,
   SHT_TABLE_RECURRENCE = 1

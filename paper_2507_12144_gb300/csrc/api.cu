@@ -178,8 +178,8 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_ti_lo);
   cudaFree(p->d_seeds);
   cudaFree(p->d_coef);
-  cudaFree(p->d_xh);
-  cudaFree(p->d_xl);
+  cudaFree(p->d_x2h);
+  cudaFree(p->d_x2l);
   cudaFree(p->d_roff);
   cudaFree(p->d_soff);
   cudaFree(p->d_x_hi);
@@ -454,6 +454,8 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   if (o.max_channels < 0) return fail(SHT_ERR_INVALID_ARG, "max_channels must be >= 0");
   if (o.table_source != SHT_TABLE_STREAMED && o.table_source != SHT_TABLE_RECURRENCE)
     return fail(SHT_ERR_INVALID_ARG, "unknown table_source");
+  if (o.table_source == SHT_TABLE_RECURRENCE && o.precision != SHT_PREC_FP32 && leg_rows(lmax, 0, 0) > 700)
+    return fail(SHT_ERR_UNSUPPORTED, "the on-chip recurrence supports lmax <= 1400");
   if (nlon > kMaxNlon) return fail(SHT_ERR_UNSUPPORTED, "nlon above 8192 is not supported");
   RadixPlan rp;
   if (!factor_radix(nlon, rp)) return fail(SHT_ERR_UNSUPPORTED, "nlon must factor into 2, 3 and 5");
@@ -610,32 +612,52 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
           e = cudaErrorInvalidValue;
       } else {
         const int NB = (leg_rows(lmax, 0, 0) + 31) / 32 + 1;
-        const int Lc = lmax + 192;
         const size_t seed_bytes = 16 * (size_t)mmax * 2 * NB * p->Kh;
-        std::vector<float2> coef((size_t)mmax * Lc, make_float2(0.f, 0.f));
+        // two-step coefficients of row i (l = m + p + 2 i): the step to the
+        // row after next, zero where that row is past lmax
+        const int ldC = (leg_rows(lmax, 0, 0) + 63) / 64 * 64 + 64;
+        auto A = [](double n, double m) { return std::sqrt((4.0 * n * n - 1.0) / (n * n - m * m)); };
+        auto Bc = [](double n, double m) {
+          return std::sqrt(((n - 1.0) * (n - 1.0) - m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+        };
+        std::vector<float4> coef((size_t)mmax * 2 * ldC, make_float4(0.f, 0.f, 0.f, 0.f));
         for (int m = 0; m < mmax; m++)
-          for (int l = m + 2; l < lmax; l++)
-            coef[(size_t)m * Lc + l] = make_float2((float)a[(size_t)l * mmax + m],
-                                                   (float)(a[(size_t)l * mmax + m] * b[(size_t)l * mmax + m]));
-        std::vector<float> xhv(p->Kh), xlv(p->Kh);
+          for (int q = 0; q < 2; q++)
+            for (int i = 0; i < leg_rows(lmax, m, q); i++) {
+              const int l = m + q + 2 * i;
+              if (l + 2 >= lmax) continue;
+              const double a2 = A(l + 2, m), a1 = A(l + 1, m), b2 = Bc(l + 2, m), b1 = Bc(l + 1, m);
+              double al = a2 * a1, be, ga;
+              if (l == m) {
+                be = -a2 * b2;
+                ga = 0.0;
+              } else {
+                const double a0 = A(l, m), b0 = Bc(l, m);
+                be = -a2 * (b2 + a1 * b1 / a0);
+                ga = -a2 * a1 * b1 * b0;
+              }
+              coef[((size_t)m * 2 + q) * ldC + i] = make_float4((float)al, (float)be, (float)ga, 0.f);
+            }
+        std::vector<float> x2hv(p->Kh), x2lv(p->Kh);
         for (int k = 0; k < p->Kh; k++) {
-          xhv[k] = (float)p->x[k];
-          xlv[k] = (float)(p->x[k] - (double)xhv[k]);
+          const double x2 = p->x[k] * p->x[k];
+          x2hv[k] = (float)x2;
+          x2lv[k] = (float)(x2 - (double)x2hv[k]);
         }
         if (e == cudaSuccess) e = upload(&p->d_coef, coef);
-        if (e == cudaSuccess) e = upload(&p->d_xh, xhv);
-        if (e == cudaSuccess) e = upload(&p->d_xl, xlv);
+        if (e == cudaSuccess) e = upload(&p->d_x2h, x2hv);
+        if (e == cudaSuccess) e = upload(&p->d_x2l, x2lv);
         if (e == cudaSuccess) e = dev_alloc(&p->d_seeds, seed_bytes);
         if (e == cudaSuccess) e = cudaMemset(p->d_seeds, 0, seed_bytes);
         if (e == cudaSuccess)
           e = launch_seed_gen(p->d_seeds, NB, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
-        p->table_bytes = (int64_t)(seed_bytes + sizeof(float2) * coef.size());
+        p->table_bytes = (int64_t)(seed_bytes + sizeof(float4) * coef.size());
         T.seeds = p->d_seeds;
         T.coef = p->d_coef;
-        T.xh = p->d_xh;
-        T.xl = p->d_xl;
+        T.x2h = p->d_x2h;
+        T.x2l = p->d_x2l;
         T.NB = NB;
-        T.Lc = Lc;
+        T.ldC = ldC;
       }
       T.roff = p->d_roff;
       T.soff = p->d_soff;

@@ -41,6 +41,8 @@ constexpr int kKc = 64;       // K per stage (one 128-byte bf16 row)
 constexpr int kThreads = 256;     // filter: TMA, MMA, TMEM, -, 4 epilogue warps
 constexpr int kThreadsGen = 512;  // Legendre: the same + 8 table-generator warps
 constexpr int kSeedRows = 32;     // rows between recurrence seeds
+constexpr int kSeedAhead = 4;     // seed prefetch distance of the generators (chunks)
+constexpr int kCoefPerThread = 3; // coefficient slice per generator thread (<= 768 per tile)
 constexpr int kMaxStages = 6;
 constexpr uint32_t kABytes = kRows * 128;  // one A tile (hi or lo)
 
@@ -110,8 +112,9 @@ struct FwdOut {
 
 // Recurrence seeds of the on-chip Legendre table: for order m, parity p,
 // 32-row block j (rows i = 32 j .. 32 j + 31, l = m + p + 2 i) and latitude
-// k', Phat at l0 = m + p + 64 j and l0 + 1, as FP32 mantissas s0, s1 of a
-// common power of two 2^e (e = kZeroBlock: the block is negligible).
+// k', Phat at l0 = m + p + 64 j and l0 + 2 (the block's first two rows), as
+// FP32 mantissas s0, s1 of a common power of two 2^e (e = kZeroBlock: the
+// block is negligible).
 struct Seed {
   float s0, s1;
   int e, pad;
@@ -121,12 +124,13 @@ constexpr int kZeroBlock = -100000;
 struct TcArgs {
   // geometry
   int L, M, Kh, B, Nt, nct, stages, ntiles;
-  // on-chip table: seeds [((2m + p) NB + j) Kh + k'], coefficients
-  // coef[m Lc + l] = (a_lm, a_lm b_lm), latitudes x = xh + xl
+  // on-chip table: seeds [((2m + p) NB + j) Kh + k'], two-step
+  // coefficients coef[(2m + p) ldC + i] = (alpha, beta, gamma, 0) of row i,
+  // squared latitudes x^2 = x2h + x2l
   const Seed *seeds;
-  const float2 *coef;
-  const float *xh, *xl;
-  int NB, Lc;
+  const float4 *coef;
+  const float *x2h, *x2l;
+  int NB, ldC, ncmax;
   // forward / inverse
   const LegTile *tiles;
   const int *roff, *soff;
@@ -334,25 +338,24 @@ __device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, ui
   }
 }
 
-// Table generator (warps 8..15 of the Legendre kernels): one thread runs the
-// three-term recurrence, folded as
-//   Phat_{l} = (a_l x) Phat_{l-1} - (a_l b_l) Phat_{l-2},
-// for one latitude over one 32-row block of one parity (63 steps from the
-// block's seeds) in FP32: one FMA per step on the dependency chain, a_l x
-// formed off the chain from x = xh + xl, mantissas carried beside a
-// power-of-two exponent and renormalised every 4 steps when above 2^64.
-// The 32 values go to shared memory as bf16 hi/lo in 16-byte chunks of 8
-// consecutive rows:
+// Table generator (warps 8..15 of the Legendre kernels).  Two steps of the
+// three-term recurrence of Eq. sht_legendre_recursion, composed so that
+// only rows of one parity appear,
+//   Phat_{l+2} = (alpha_l x^2 + beta_l) Phat_l + gamma_l Phat_{l-2},
+//   alpha_l = a_{l+2} a_{l+1},
+//   beta_l  = -a_{l+2} (b_{l+2} + a_{l+1} b_{l+1} / a_l),   (beta_m = -a_{m+2} b_{m+2})
+//   gamma_l = -a_{l+2} a_{l+1} b_{l+1} b_l,                  (gamma_m = 0)
+// give one FMA per stored row on the dependency chain.  One thread runs one
+// latitude through one 32-row block of one parity from the block's seeds,
+// in FP32 with x^2 = x2h + x2l, mantissas carried beside a power-of-two
+// exponent and renormalised when above 2^64.  The 32 values go to shared
+// memory as bf16 hi/lo in 16-byte chunks of 8 consecutive rows:
 //   forward: A[i][k'] MN-major (rows i contiguous): thread (k' = 64 kc + g mod
 //            64, block r0/32 + g/64) of tile rows r0 .. r0 + 127;
 //   inverse: A[k'][i] K-major (i contiguous): thread (k' = r0 + g mod 128,
 //            block 2 kc + g/128).
-// Seed of the chunk (kc) handled by generator thread g, with its latitude.
-struct GenIn {
-  Seed sd;
-  float xh, xl;
-};
-
+// Seed of chunk kc of a tile for generator thread g: its latitude k' and
+// seed block j.
 template <int kMode>
 __device__ __forceinline__ void gen_coords(const TileInfo &ti, int kc, int g, int &kp, int &j) {
   if (kMode == kFwd) {
@@ -364,24 +367,24 @@ __device__ __forceinline__ void gen_coords(const TileInfo &ti, int kc, int g, in
   }
 }
 
+// Asynchronous copy of that seed into the thread's slot of the seed ring
+// (zeros where the latitude or the block does not exist).
 template <int kMode>
-__device__ __forceinline__ GenIn gen_load(const TcArgs &a, const TileInfo &ti, int kc, int g) {
+__device__ __forceinline__ void gen_prefetch(const TcArgs &a, const TileInfo &ti, int kc, int g, Seed *slot) {
   int kp, j;
   gen_coords<kMode>(ti, kc, g, kp, j);
-  GenIn in{{0.f, 0.f, kZeroBlock, 0}, 0.f, 0.f};
-  if (kc < ti.nk && kp < a.Kh) {
-    if (j < a.NB) in.sd = a.seeds[((int64_t)(ti.m * 2 + ti.p) * a.NB + j) * a.Kh + kp];
-    in.xh = a.xh[kp];
-    in.xl = a.xl[kp];
-  }
-  return in;
+  const bool ok = kp < a.Kh && j < a.NB;
+  const Seed *src = ok ? a.seeds + ((int64_t)(ti.m * 2 + ti.p) * a.NB + j) * a.Kh + kp : a.seeds;
+  cp_async16(slot, src, ok ? 16u : 0u);
 }
 
-// cs: the tile's recurrence coefficients in shared memory, cs[l - lbase].
+__device__ __forceinline__ float pow2_or_zero(int E) { return E < -126 ? 0.f : __int_as_float((E + 127) << 23); }
+
+// cs: the tile's two-step coefficients in shared memory, cs[i - ibase].
 template <int kMode>
 __device__ __forceinline__ void generate_chunk(const TcArgs &a, const TileInfo &ti, int kc, int g,
-                                               unsigned char *a_hi, unsigned char *a_lo, const GenIn &in,
-                                               const float2 *cs, int lbase) {
+                                               unsigned char *a_hi, unsigned char *a_lo, const Seed &sd,
+                                               const float2 *xs, const float4 *cs, int ibase) {
   int kp, j, row, cbase;
   gen_coords<kMode>(ti, kc, g, kp, j);
   if (kMode == kFwd) {
@@ -391,36 +394,33 @@ __device__ __forceinline__ void generate_chunk(const TcArgs &a, const TileInfo &
     row = g & 127;
     cbase = 4 * (g >> 7);
   }
-  const Seed sd = in.sd;
-  const float xh = in.xh, xl = in.xl;
-  const int l0 = ti.m + ti.p + 2 * kSeedRows * j;
-  const bool zero = sd.e == kZeroBlock || l0 >= a.L;
-  float pa = zero ? 0.f : sd.s0, pb = zero ? 0.f : sd.s1;  // scaled Phat_l, Phat_{l+1}
+  const float2 x2 = kp < a.Kh ? xs[kp] : make_float2(0.f, 0.f);
+  const float x2h = x2.x, x2l = x2.y;
+  const int i0 = kSeedRows * j;
+  const bool zero = sd.e == kZeroBlock || ti.m + ti.p + 2 * i0 >= a.L;
+  float pa = zero ? 0.f : sd.s0, pb = zero ? 0.f : sd.s1;  // scaled rows i, i + 1
   int E = zero ? 0 : sd.e;
-  const float2 *cf = cs + (zero ? 0 : l0 + 2 - lbase);
+  float scale = zero ? 0.f : pow2_or_zero(E);
+  // the step to row i + 2 uses the coefficients of row i + 1
+  const float4 *cf = cs + (zero ? 0 : i0 + 1 - ibase);
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     uint32_t h[4], lw[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const float scale = (zero || E < -126) ? 0.f : __int_as_float((E + 127) << 23);
-      const float v0 = pa * scale;
-      float2 c[4];
-#pragma unroll
-      for (int w = 0; w < 4; w++) c[w] = zero ? make_float2(0.f, 0.f) : cf[w];
-      if (!zero) cf += 4;
-      // two outputs (rows l, l + 2): four recurrence steps
-      const float pc = fmaf(fmaf(c[0].x, xh, c[0].x * xl), pb, -c[0].y * pa);
-      const float pd = fmaf(fmaf(c[1].x, xh, c[1].x * xl), pc, -c[1].y * pb);
-      const float v1 = pc * scale;
-      const float pe = fmaf(fmaf(c[2].x, xh, c[2].x * xl), pd, -c[2].y * pc);
-      const float pf = fmaf(fmaf(c[3].x, xh, c[3].x * xl), pe, -c[3].y * pd);
-      pa = pe;
-      pb = pf;
+      const float v0 = pa * scale, v1 = pb * scale;
+      const float4 c0 = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : cf[0];
+      const float4 c1 = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : cf[1];
+      if (!zero) cf += 2;
+      const float pc = fmaf(fmaf(c0.x, x2h, fmaf(c0.x, x2l, c0.y)), pb, c0.z * pa);
+      const float pd = fmaf(fmaf(c1.x, x2h, fmaf(c1.x, x2l, c1.y)), pc, c1.z * pb);
+      pa = pc;
+      pb = pd;
       if (fabsf(pb) > 1.8446744e19f) {  // 2^64
         pa *= 5.4210109e-20f;            // 2^-64
         pb *= 5.4210109e-20f;
         E += 64;
+        scale = pow2_or_zero(E);
       }
       const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
       const float2 hf = __bfloat1622float2(hh);
@@ -494,36 +494,84 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
       }
     }
   } else if (kGen && warp >= 8) {
-    // table generators: the tile's recurrence coefficients are staged in
-    // shared memory (after the stage ring), the next chunk's seed is loaded
-    // while the current chunk is generated
+    // table generators.  Shared memory after the stage ring: the current
+    // tile's two-step coefficients (the next tile's are loaded into
+    // registers meanwhile), x^2 of every latitude, and a ring of kSeedAhead
+    // seed slots per thread filled by cp.async kSeedAhead chunks ahead.
     const int gtid = threadIdx.x - 256;
-    float2 *cs = reinterpret_cast<float2 *>(base + (size_t)S * sbytes);
+    float4 *cs = reinterpret_cast<float4 *>(base + (size_t)S * sbytes);
+    float2 *xs = reinterpret_cast<float2 *>(cs + a.ncmax);
+    Seed *ring = reinterpret_cast<Seed *>(xs + ((a.Kh + 1) & ~1));
+    for (int k = gtid; k < a.Kh; k += 256) xs[k] = make_float2(__ldg(a.x2h + k), __ldg(a.x2l + k));
+    // prefetch cursor: tile pt (pti), chunk pkc
+    int pt = blockIdx.x, pkc = 0;
+    TileInfo pti{};
+    if (pt < a.ntiles) pti = tile_info<kMode>(a, pt);
+    auto prefetch = [&](uint32_t pg) {
+      while (pt < a.ntiles && pkc >= pti.nk) {
+        pt += gridDim.x;
+        pkc = 0;
+        if (pt < a.ntiles) pti = tile_info<kMode>(a, pt);
+      }
+      if (pt < a.ntiles) {
+        gen_prefetch<kMode>(a, pti, pkc, gtid, ring + (pg % kSeedAhead) * 256 + gtid);
+        pkc++;
+      }
+      cp_async_commit();
+    };
+    for (uint32_t q = 0; q < (uint32_t)kSeedAhead; q++) prefetch(q);
+    // coefficients of the first tile with chunks go through registers too
+    auto coef_range = [&](const TileInfo &ti, int &ibase, int &ncoef) {
+      // forward: the tile's 128 rows (+ 2 past its end), inverse: every row
+      ibase = kMode == kFwd ? ti.r0 : 0;
+      ncoef = kMode == kFwd ? 2 * kKc + 4 : kKc * ti.nk + 4;
+    };
+    auto coef_load = [&](int t, float4 (&cr)[kCoefPerThread]) {
+      while (t < a.ntiles && tile_info<kMode>(a, t).nk == 0) t += gridDim.x;
+#pragma unroll
+      for (int u = 0; u < kCoefPerThread; u++) cr[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (t >= a.ntiles) return;
+      const TileInfo ti = tile_info<kMode>(a, t);
+      int ibase, ncoef;
+      coef_range(ti, ibase, ncoef);
+      const float4 *src = a.coef + (int64_t)(ti.m * 2 + ti.p) * a.ldC;
+#pragma unroll
+      for (int u = 0; u < kCoefPerThread; u++) {
+        const int e = gtid + 256 * u;
+        if (e < ncoef && ibase + e < a.ldC) cr[u] = __ldg(src + ibase + e);
+      }
+    };
+    float4 creg[kCoefPerThread];
+    coef_load(blockIdx.x, creg);
     uint32_t g = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
       const TileInfo ti = tile_info<kMode>(a, t);
-      const int lbase = ti.m + ti.p + (kMode == kFwd ? 2 * ti.r0 : 0);
-      const int ncoef = kMode == kFwd ? 4 * kKc + 8 : 2 * kKc * ti.nk + 8;
+      if (ti.nk == 0) continue;
+      int ibase, ncoef;
+      coef_range(ti, ibase, ncoef);
       asm volatile("bar.sync 2, 256;" ::: "memory");  // previous tile's coefficients no longer read
-      for (int e = gtid; e < ncoef; e += 256) {
-        const int l = lbase + e;
-        cs[e] = l < a.Lc ? __ldg(a.coef + (int64_t)ti.m * a.Lc + l) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kCoefPerThread; u++) {
+        const int e = gtid + 256 * u;
+        if (e < ncoef) cs[e] = creg[u];
       }
-      asm volatile("bar.sync 2, 256;" ::: "memory");
-      GenIn in = gen_load<kMode>(a, ti, 0, gtid);
+      asm volatile("bar.sync 2, 256;" ::: "memory");  // also orders the x^2 stores of the first tile
+      coef_load(t + gridDim.x, creg);
       for (int kc = 0; kc < ti.nk; kc++, g++) {
-        const GenIn next = gen_load<kMode>(a, ti, kc + 1, gtid);
         const int s = (int)(g % (uint32_t)S);
         const uint32_t use = g / (uint32_t)S;
+        cp_async_wait<kSeedAhead - 1>();
+        const Seed sd = ring[(g % kSeedAhead) * 256 + gtid];
         if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, a.err);
         unsigned char *st = base + (size_t)s * sbytes;
-        generate_chunk<kMode>(a, ti, kc, gtid, st, st + kABytes, in, cs, lbase);
+        generate_chunk<kMode>(a, ti, kc, gtid, st, st + kABytes, sd, xs, cs, ibase);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&full_bar[s]);
-        in = next;
+        prefetch(g + kSeedAhead);
       }
     }
+    cp_async_wait<0>();
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     uint32_t idesc = idesc_bf16_f32(kRows, a.Nt, kMode != kFilt);
@@ -663,9 +711,9 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
   }
 }
 
-// FP64 recurrence seeds (one thread per (m, k')): at the start l0 of every
-// 32-row block of both parities, store Phat_{l0} and Phat_{l0+1} as FP32
-// mantissas of a common power of two.
+// FP64 recurrence seeds (one thread per (m, k')): at the first row l0 of
+// every 32-row block of both parities, store Phat_{l0} and Phat_{l0+2} as
+// FP32 mantissas of a common power of two.
 __global__ void seed_gen_kernel(Seed *__restrict__ seeds, int NB, const double *__restrict__ xk,
                                 const double *__restrict__ sk, const double *__restrict__ a,
                                 const double *__restrict__ bcoef, const double *__restrict__ seedf, int L, int M,
@@ -676,28 +724,40 @@ __global__ void seed_gen_kernel(Seed *__restrict__ seeds, int NB, const double *
   const double x = xk[k], s = sk[k];
   double pmm = 0.28209479177387814347;  // 1 / sqrt(4 pi)
   for (int i = 1; i <= m; i++) pmm *= seedf[i] * s;
-  double cur = pmm;
-  double nxt = (m + 1 < L) ? sqrt(2.0 * m + 3.0) * x * pmm : 0.0;
+  // window of Phat_l, Phat_{l+1}, Phat_{l+2}, Phat_{l+3}
+  double w[4];
+  w[0] = pmm;
+  w[1] = (m + 1 < L) ? sqrt(2.0 * m + 3.0) * x * pmm : 0.0;
+  for (int q = 2; q < 4; q++) {
+    const int l = m + q;
+    w[q] = 0.0;
+    if (l < L) {
+      const int64_t ci = (int64_t)l * M + m;
+      w[q] = a[ci] * (x * w[q - 1] - bcoef[ci] * w[q - 2]);
+    }
+  }
   for (int l = m; l < L; l++) {
     const int d = l - m, p = d & 1, i = d >> 1;
     if ((i % kSeedRows) == 0) {
       Seed sd{0.f, 0.f, kZeroBlock, 0};
-      const double mx = fmax(fabs(cur), fabs(nxt));
+      const double mx = fmax(fabs(w[0]), fabs(w[2]));
       if (mx > 0.0) {
         const int e = ilogb(mx);
-        sd.s0 = (float)scalbn(cur, -e);
-        sd.s1 = (float)scalbn(nxt, -e);
+        sd.s0 = (float)scalbn(w[0], -e);
+        sd.s1 = (float)scalbn(w[2], -e);
         sd.e = e;
       }
       seeds[((int64_t)(m * 2 + p) * NB + i / kSeedRows) * Kh + k] = sd;
     }
     double nn = 0.0;
-    if (l + 2 < L) {
-      const int64_t ci = (int64_t)(l + 2) * M + m;
-      nn = a[ci] * (x * nxt - bcoef[ci] * cur);
+    if (l + 4 < L) {
+      const int64_t ci = (int64_t)(l + 4) * M + m;
+      nn = a[ci] * (x * w[3] - bcoef[ci] * w[2]);
     }
-    cur = nxt;
-    nxt = nn;
+    w[0] = w[1];
+    w[1] = w[2];
+    w[2] = w[3];
+    w[3] = nn;
   }
 }
 
@@ -737,8 +797,12 @@ cudaError_t launch_persistent(bool split, bool gen, const CUtensorMap &ta_hi, co
   const int sb = (int)stage_bytes(kMode, split, args.Nt);
   // coefficient staging of the table generators (forward: one 128-row tile,
   // inverse: every chunk of one (m, p) block)
-  const size_t cbytes =
-      !gen ? 0 : sizeof(float2) * (size_t)(2 * kKc * ((leg_rows(args.L, 0, 0) + kKc - 1) / kKc) + 4 * kKc + 16);
+  // generator shared memory: coefficients, x^2 per latitude, seed ring
+  args.ncmax = std::max(2 * kKc + 4, kKc * ((leg_rows(args.L, 0, 0) + kKc - 1) / kKc) + 4);
+  const size_t cbytes = !gen ? 0
+                             : sizeof(float4) * (size_t)args.ncmax + sizeof(float2) * (size_t)((args.Kh + 1) & ~1) +
+                                   sizeof(Seed) * 256 * kSeedAhead;
+  if (gen && args.ncmax > 256 * kCoefPerThread) return cudaErrorInvalidValue;
   const int budget = 220 * 1024 - 1024 - (int)cbytes;
   args.stages = std::max(2, std::min(kMaxStages, budget / sb));
   const size_t smem = 1024 + (size_t)args.stages * sb + cbytes;
@@ -816,10 +880,10 @@ cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int nti
   a.err = T.err;
   a.seeds = reinterpret_cast<const Seed *>(T.seeds);
   a.coef = T.coef;
-  a.xh = T.xh;
-  a.xl = T.xl;
+  a.x2h = T.x2h;
+  a.x2l = T.x2l;
   a.NB = T.NB;
-  a.Lc = T.Lc;
+  a.ldC = T.ldC;
   return launch_persistent<kFwd>(T.split, T.gen, T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.split ? T.f_lo : T.f_hi, a, st);
 }
 
@@ -841,10 +905,10 @@ cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int nti
   a.err = T.err;
   a.seeds = reinterpret_cast<const Seed *>(T.seeds);
   a.coef = T.coef;
-  a.xh = T.xh;
-  a.xl = T.xl;
+  a.x2h = T.x2h;
+  a.x2l = T.x2l;
   a.NB = T.NB;
-  a.Lc = T.Lc;
+  a.ldC = T.ldC;
   return launch_persistent<kInv>(T.split, T.gen, T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.split ? T.s_lo : T.s_hi, a,
                                  st);
 }

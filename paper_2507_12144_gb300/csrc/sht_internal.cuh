@@ -49,12 +49,11 @@ struct TcPlanView {
   CUtensorMap f_hi, f_lo, s_hi, s_lo;
   CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
   const int *roff, *soff;
-  // on-chip Legendre table: seeds (16 B each), coefficients [M][Lc],
-  // latitudes as FP32 hi + lo
+  // on-chip Legendre table: seeds (16 B each) every 32 rows
   const void *seeds;
-  const float2 *coef;
-  const float *xh, *xl;
-  int NB, Lc;
+  const float4 *coef;        // two-step coefficients [(2m + p) ldC + i]
+  const float *x2h, *x2l;    // x^2 = x2h + x2l per latitude
+  int NB, ldC;
   int L, M, Kh;
   bool split;
   bool gen;  // generate the table on chip instead of streaming it
@@ -229,8 +228,8 @@ struct sht_plan_s {
   __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;  // bf16 tables
   int table_source = 0;        // 0: streamed bf16 table, 1: on-chip recurrence
   void *d_seeds = nullptr;     // recurrence seeds of the on-chip table
-  float2 *d_coef = nullptr;    // FP32 recurrence coefficients [M][Lc]
-  float *d_xh = nullptr, *d_xl = nullptr;  // latitudes as FP32 hi + lo
+  float4 *d_coef = nullptr;    // two-step recurrence coefficients [(2m + p) ldC + i]
+  float *d_x2h = nullptr, *d_x2l = nullptr;  // squared latitudes as FP32 hi + lo
   int ldcb = 0;                // bf16 row stride of the workspaces (elements)
   int64_t srows = 0;           // rows of the internal coefficient layout
   int *d_soff = nullptr;       // [2 M] first internal row of block (m, p)
