@@ -511,14 +511,24 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   // block-major order: the row tiles of one (m, p) block run back to back
   // and share its Fourier rows in L2
   std::vector<LegTile> ft, it;
+  int64_t frows_acc = 0, srows_acc = 0;
+  std::vector<int> roff_h(2 * (size_t)mmax), soff_h(2 * (size_t)mmax);
+  for (int m = 0; m < mmax; m++)
+    for (int q = 0; q < 2; q++) {
+      roff_h[2 * m + q] = (int)frows_acc;
+      soff_h[2 * m + q] = (int)srows_acc;
+      frows_acc += leg_rows(lmax, m, q);
+      srows_acc += (leg_rows(lmax, m, q) + 63) / 64 * 64;
+    }
   for (int m = 0; m < mmax; m++)
     for (int q = 0; q < 2; q++)
-      for (int r0 = 0; r0 < leg_rows(lmax, m, q); r0 += trow) ft.push_back(LegTile{m, q, r0});
+      for (int r0 = 0; r0 < leg_rows(lmax, m, q); r0 += trow)
+        ft.push_back(LegTile{m, q, r0, roff_h[2 * m + q] + r0});
   // every (m, p) block gets inverse tiles, also the empty one (m = lmax-1,
   // odd parity): its tiles write the zeros that the synthesis reads
   for (int m = 0; m < mmax; m++)
     for (int q = 0; q < 2; q++)
-      for (int k0 = 0; k0 < p->Kh; k0 += trow) it.push_back(LegTile{m, q, k0});
+      for (int k0 = 0; k0 < p->Kh; k0 += trow) it.push_back(LegTile{m, q, k0, soff_h[2 * m + q]});
   p->n_fwd_tiles = (int)ft.size();
   p->n_inv_tiles = (int)it.size();
 

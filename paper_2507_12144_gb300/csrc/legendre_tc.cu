@@ -121,25 +121,46 @@ struct Seed {
 };
 constexpr int kZeroBlock = -100000;
 
-struct TcArgs {
-  // geometry
-  int L, M, Kh, B, Nt, nct, stages, ntiles;
+// One problem (a plan and its batch) of a Legendre launch.  A launch walks
+// the tiles of up to kMaxSeg problems (grids of different sizes in one
+// batched call); global tile t belongs to problem s with tile0[s] <= t <
+// tile0[s + 1] and splits into row tile (t - tile0) / nct and column tile
+// (t - tile0) % nct.
+constexpr int kMaxSeg = 8;
+
+struct SegArgs {
+  int L, M, Kh, B;        // degrees, orders, ceil(nlat / 2), fields
+  int Nt, nct, tile0;     // column tile width and count, first global tile
+  int xoff;               // offset of this problem's x^2 in shared memory
+  const LegTile *tiles;   // (m, p, first row, TMA row) of the row tiles
+  FwdOut fout;            // forward destination
+  float *Gw;              // inverse destination [(2m + p) Kh + k'][ldc]
+  int ldc;
   // on-chip table: seeds [((2m + p) NB + j) Kh + k'], two-step
   // coefficients coef[(2m + p) ldC + i] = (alpha, beta, gamma, 0) of row i,
   // squared latitudes x^2 = x2h + x2l
   const Seed *seeds;
   const float4 *coef;
   const float *x2h, *x2l;
-  int NB, ldC, ncmax;
-  // forward / inverse
-  const LegTile *tiles;
-  const int *roff, *soff;
-  FwdOut fout;      // forward destination
-  float *Gw;        // inverse destination
-  int ldc;
-  // filter
+  int NB, ldC;
+};
+
+// TMA maps of one problem: A (table hi/lo, or filter data) and B (data, or
+// filter weights).
+struct SegMaps {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+struct TcParams {
+  SegMaps maps[kMaxSeg];
+  SegArgs seg[kMaxSeg];
+  int nseg, ntiles, stages;
+  int Nmax;               // widest column tile: stage layout and TMEM columns
+  int ncmax, xtot;        // generator shared memory: coefficients, x^2 entries
+  // filter (one problem)
   const FiltTile *ftiles;
-  int Bm, ntn, kx, nwr, cin, cout, lds;
+  const int *soff;
+  int L, M, Nt, Bm, ntn, kx, nwr, cin, cout, lds;
   __nv_bfloat16 *s_hi, *s_lo;
   unsigned *err;
 };
@@ -155,6 +176,7 @@ __host__ __device__ inline uint32_t stage_bytes(int mode, bool split, int Nt) {
 }
 
 struct TileInfo {
+  int s, Nt;             // problem, its column tile width
   int nk;                // K chunks
   int a_col0, a_row;     // A: K column of chunk 0, row
   int b_col0, b_row0;    // B: for MN-major (col of box 0, K row of chunk 0); for K-major (K col 0, row)
@@ -162,47 +184,102 @@ struct TileInfo {
   int m, p, r0, c0, l, b, n0;
 };
 
+// A tile as fetched: its problem, index inside the problem and the row
+// tile's descriptor (a pending load until decoded), so that every role can
+// request the next tile one tile ahead.
+struct RawTile {
+  int s, local;
+  int4 d;
+};
+
 template <int kMode>
-__device__ __forceinline__ TileInfo tile_info(const TcArgs &a, int t) {
+__device__ __forceinline__ RawTile tile_fetch(const TcParams &P, int t) {
+  RawTile r{0, t, make_int4(0, 0, 0, 0)};
+  if (t >= P.ntiles) return r;
+  if (kMode == kFilt) {
+    const int per = P.Bm * P.ntn;
+    const int2 ft = __ldg(reinterpret_cast<const int2 *>(P.ftiles) + t / per);
+    r.d = make_int4(ft.x, ft.y, 0, 0);
+  } else {
+    int s = 0;
+    while (s + 1 < P.nseg && t >= P.seg[s + 1].tile0) s++;
+    r.s = s;
+    r.local = t - P.seg[s].tile0;
+    r.d = __ldg(reinterpret_cast<const int4 *>(P.seg[s].tiles) + r.local / P.seg[s].nct);
+  }
+  return r;
+}
+
+template <int kMode>
+__device__ __forceinline__ TileInfo tile_decode(const TcParams &P, const RawTile &r) {
   TileInfo ti{};
   if (kMode == kFilt) {
-    const int per = a.Bm * a.ntn;
-    const FiltTile ft = a.ftiles[t / per];
-    const int rem = t - (t / per) * per;
-    ti.l = ft.l;
-    ti.m = ft.m0;
-    ti.b = rem / a.ntn;
-    ti.n0 = (rem - ti.b * a.ntn) * a.Nt;
-    ti.nk = (2 * a.cin + kKc - 1) / kKc;
-    ti.a_col0 = ti.b * a.kx;
-    ti.a_row = ti.l * a.M + ti.m;
+    const int per = P.Bm * P.ntn;
+    const int rem = r.local - (r.local / per) * per;
+    ti.s = 0;
+    ti.Nt = P.Nt;
+    ti.l = r.d.x;
+    ti.m = r.d.y;
+    ti.b = rem / P.ntn;
+    ti.n0 = (rem - ti.b * P.ntn) * P.Nt;
+    ti.nk = (2 * P.cin + kKc - 1) / kKc;
+    ti.a_col0 = ti.b * P.kx;
+    ti.a_row = ti.l * P.M + ti.m;
     ti.b_col0 = 0;
-    ti.b_row0 = ti.l * a.nwr + ti.n0;
+    ti.b_row0 = ti.l * P.nwr + ti.n0;
   } else {
-    const LegTile tl = a.tiles[t / a.nct];
-    ti.m = tl.m;
-    ti.p = tl.p;
-    ti.r0 = tl.r0;
-    ti.c0 = (t % a.nct) * a.Nt;
+    const SegArgs &g = P.seg[r.s];
+    ti.s = r.s;
+    ti.Nt = g.Nt;
+    ti.m = r.d.x;
+    ti.p = r.d.y;
+    ti.r0 = r.d.z;
+    ti.c0 = (r.local % g.nct) * g.Nt;
     ti.b_col0 = ti.c0;
     ti.a_col0 = 0;
     if (kMode == kFwd) {
-      ti.nk = (a.Kh + kKc - 1) / kKc;
-      ti.a_row = a.roff[2 * ti.m + ti.p] + ti.r0;
-      ti.b_row0 = (ti.m * 2 + ti.p) * a.Kh;
+      ti.nk = (g.Kh + kKc - 1) / kKc;
+      ti.a_row = r.d.w;  // table row of the tile
+      ti.b_row0 = (ti.m * 2 + ti.p) * g.Kh;
     } else {
-      ti.nk = (leg_rows(a.L, ti.m, ti.p) + kKc - 1) / kKc;
-      ti.a_row = (ti.m * 2 + ti.p) * a.Kh + ti.r0;
-      ti.b_row0 = a.soff[2 * ti.m + ti.p];
+      ti.nk = (leg_rows(g.L, ti.m, ti.p) + kKc - 1) / kKc;
+      ti.a_row = (ti.m * 2 + ti.p) * g.Kh + ti.r0;
+      ti.b_row0 = r.d.w;  // first internal coefficient row of (m, p)
     }
   }
   return ti;
 }
 
+// Tiles of this CTA in order, the next one fetched a tile ahead.
+template <int kMode>
+struct TileWalk {
+  int t;
+  RawTile nxt;
+  __device__ __forceinline__ TileWalk(const TcParams &P) : t(blockIdx.x) { nxt = tile_fetch<kMode>(P, t); }
+  __device__ __forceinline__ bool more(const TcParams &P) const { return t < P.ntiles; }
+  // the current tile's info; requests the one after it
+  __device__ __forceinline__ TileInfo take(const TcParams &P) {
+    const TileInfo ti = tile_decode<kMode>(P, nxt);
+    t += gridDim.x;
+    nxt = tile_fetch<kMode>(P, t);
+    return ti;
+  }
+};
+
+// Bytes that the TMA loads of one chunk of the tile deliver.
 template <int kMode, bool kSplit, bool kGen>
-__device__ __forceinline__ void issue_chunk(unsigned char *st, int Nt, uint32_t tmem, uint32_t idesc, bool first) {
+__device__ __forceinline__ uint32_t chunk_tx_bytes(const TileInfo &ti) {
+  const uint32_t abytes = (kMode != kFilt && kGen) ? 0u : (uint32_t)a_count(kMode, kSplit) * kABytes;
+  if (kMode == kFilt) return abytes + 2u * (uint32_t)ti.Nt * 128u;
+  return abytes + (uint32_t)b_count(kMode, kSplit) * (uint32_t)((ti.Nt + 63) / 64) * 8192u;
+}
+
+// MMAs of one K chunk (kKc = 64) of a tile, N = the tile's column width.
+// Stage layout (for the launch's widest tile Nmax): A hi, A lo, B hi, B lo.
+template <int kMode, bool kSplit, bool kGen>
+__device__ __forceinline__ void issue_chunk(unsigned char *st, int Nmax, uint32_t tmem, uint32_t idesc, bool first) {
   const int na = a_count(kMode, kSplit);
-  const uint32_t bb = b_bytes_of(kMode, Nt);
+  const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
 #pragma unroll
@@ -230,41 +307,42 @@ __device__ __forceinline__ void issue_chunk(unsigned char *st, int Nt, uint32_t 
 }
 
 template <int kMode, bool kSplit, bool kGen>
-__device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti, int kc, int Nt,
-                                           const CUtensorMap *ta_hi, const CUtensorMap *ta_lo,
-                                           const CUtensorMap *tb_hi, const CUtensorMap *tb_lo, uint64_t *bar) {
+__device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti, int kc, int Nmax, const SegMaps &mp,
+                                           uint64_t *bar) {
   const int na = a_count(kMode, kSplit);
-  const uint32_t bb = b_bytes_of(kMode, Nt);
+  const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
   if (kMode == kFilt || !kGen) {
-    tma_load_2d(a_hi, ta_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
-    if (na == 2) tma_load_2d(a_lo, ta_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+    tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
+    if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
   }
   if (kMode == kFilt) {
-    tma_load_2d(b_hi, tb_hi, bar, kc * kKc, ti.b_row0);
-    tma_load_2d(b_lo, tb_lo, bar, kc * kKc, ti.b_row0);
+    tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
+    tma_load_2d(b_lo, &mp.b_lo, bar, kc * kKc, ti.b_row0);
   } else {
-    const int nbox = (Nt + 63) / 64;
+    const int nbox = (ti.Nt + 63) / 64;
     for (int j = 0; j < nbox; j++) {
-      tma_load_2d(b_hi + j * 8192, tb_hi, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
-      if (kSplit) tma_load_2d(b_lo + j * 8192, tb_lo, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
+      tma_load_2d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
+      if (kSplit) tma_load_2d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
     }
   }
 }
 
 // Epilogue of one tile for the accumulator at tacc (zero: write zeros).
 template <int kMode>
-__device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, uint32_t tacc, int q4, int lane,
+__device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, uint32_t tacc, int q4, int lane,
                                          bool zero) {
-  const int Nt = a.Nt;
+  const int Nt = ti.Nt;
   const uint32_t tl = tacc + ((uint32_t)(q4 * 32) << 16);
   if (kMode == kFwd) {
+    const SegArgs &g = P.seg[ti.s];
     const int r = ti.r0 + q4 * 32 + lane;
-    const bool row_ok = r < leg_rows(a.L, ti.m, ti.p);
+    const bool row_ok = r < leg_rows(g.L, ti.m, ti.p);
     const int l = ti.m + ti.p + 2 * r;
-    const FwdOut &out = a.fout;
-    const int64_t orow = ((int64_t)l * a.M + ti.m) * out.ldo;
+    const FwdOut out = g.fout;
+    const int B = g.B, L = g.L, M = g.M;
+    const int64_t orow = ((int64_t)l * M + ti.m) * out.ldo;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
       tmem_ld16(tl + (uint32_t)(j * 16), v);
@@ -273,12 +351,12 @@ __device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, ui
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           const int f = (ti.c0 + j * 16) / 2 + 4 * h;  // first of 4 fields
-          if (f >= a.B) continue;
+          if (f >= B) continue;
           const int mb = f / out.cin, ch = f - mb * out.cin;
-          if ((ch & 3) == 0 && ch + 4 <= out.cin && f + 4 <= a.B) {
+          if ((ch & 3) == 0 && ch + 4 <= out.cin && f + 4 <= B) {
             put_bf16x8(out.rows_hi, out.rows_lo, orow + (int64_t)mb * out.kx + 2 * ch, v + 8 * h);
           } else {
-            for (int u = 0; u < 4 && f + u < a.B; u++) {
+            for (int u = 0; u < 4 && f + u < B; u++) {
               const int fu = f + u, mu = fu / out.cin, cu = fu - mu * out.cin;
               put_bf16_pair(out.rows_hi, out.rows_lo, orow + (int64_t)mu * out.kx + 2 * cu, v[8 * h + 2 * u],
                             v[8 * h + 2 * u + 1]);
@@ -289,13 +367,16 @@ __device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, ui
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const int f = (ti.c0 + j * 16) / 2 + u;
-          if (f < a.B) out.xhat[((int64_t)f * a.L + l) * a.M + ti.m] = make_float2(v[2 * u], v[2 * u + 1]);
+          if (f < B) out.xhat[((int64_t)f * L + l) * M + ti.m] = make_float2(v[2 * u], v[2 * u + 1]);
         }
       }
     }
   } else if (kMode == kInv) {
+    const SegArgs &g = P.seg[ti.s];
     const int k = ti.r0 + q4 * 32 + lane;
-    float *G = a.Gw + (((int64_t)ti.m * 2 + ti.p) * a.Kh + k) * a.ldc;
+    const int ldc = g.ldc;
+    float *G = g.Gw + (((int64_t)ti.m * 2 + ti.p) * g.Kh + k) * ldc;
+    const bool k_ok = k < g.Kh;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
       if (!zero) {
@@ -304,21 +385,21 @@ __device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, ui
 #pragma unroll
         for (int u = 0; u < 16; u++) v[u] = 0.f;
       }
-      if (k < a.Kh) {
+      if (k_ok) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           const int c = ti.c0 + j * 16 + 4 * u;
-          if (c < a.ldc)
+          if (c < ldc)
             *reinterpret_cast<float4 *>(G + c) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
         }
       }
     }
   } else {
     const int m = ti.m + q4 * 32 + lane;
-    const bool ok = (m < a.M) && (m <= ti.l);
+    const bool ok = (m < P.M) && (m <= ti.l);
     const int d = ti.l - m;
     const int64_t srow =
-        ok ? (int64_t)(a.soff[2 * m + (d & 1)] + (d >> 1)) * a.lds + 2 * (int64_t)ti.b * a.cout : 0;
+        ok ? (int64_t)(P.soff[2 * m + (d & 1)] + (d >> 1)) * P.lds + 2 * (int64_t)ti.b * P.cout : 0;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
       tmem_ld16(tl + (uint32_t)(j * 16), v);
@@ -326,12 +407,12 @@ __device__ __forceinline__ void epilogue(const TcArgs &a, const TileInfo &ti, ui
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         const int n = ti.n0 + j * 16 + 8 * h;  // 4 output channels
-        if (n + 8 <= 2 * a.cout && ((srow + n) & 7) == 0) {
-          put_bf16x8(a.s_hi, a.s_lo, srow + n, v + 8 * h);
+        if (n + 8 <= 2 * P.cout && ((srow + n) & 7) == 0) {
+          put_bf16x8(P.s_hi, P.s_lo, srow + n, v + 8 * h);
         } else {
           for (int u = 0; u < 4; u++)
-            if (n + 2 * u < 2 * a.cout)
-              put_bf16_pair(a.s_hi, a.s_lo, srow + n + 2 * u, v[8 * h + 2 * u], v[8 * h + 2 * u + 1]);
+            if (n + 2 * u < 2 * P.cout)
+              put_bf16_pair(P.s_hi, P.s_lo, srow + n + 2 * u, v[8 * h + 2 * u], v[8 * h + 2 * u + 1]);
         }
       }
     }
@@ -370,19 +451,20 @@ __device__ __forceinline__ void gen_coords(const TileInfo &ti, int kc, int g, in
 // Asynchronous copy of that seed into the thread's slot of the seed ring
 // (zeros where the latitude or the block does not exist).
 template <int kMode>
-__device__ __forceinline__ void gen_prefetch(const TcArgs &a, const TileInfo &ti, int kc, int g, Seed *slot) {
+__device__ __forceinline__ void gen_prefetch(const SegArgs &sg, const TileInfo &ti, int kc, int g, Seed *slot) {
   int kp, j;
   gen_coords<kMode>(ti, kc, g, kp, j);
-  const bool ok = kp < a.Kh && j < a.NB;
-  const Seed *src = ok ? a.seeds + ((int64_t)(ti.m * 2 + ti.p) * a.NB + j) * a.Kh + kp : a.seeds;
+  const bool ok = kp < sg.Kh && j < sg.NB;
+  const Seed *src = ok ? sg.seeds + ((int64_t)(ti.m * 2 + ti.p) * sg.NB + j) * sg.Kh + kp : sg.seeds;
   cp_async16(slot, src, ok ? 16u : 0u);
 }
 
 __device__ __forceinline__ float pow2_or_zero(int E) { return E < -126 ? 0.f : __int_as_float((E + 127) << 23); }
 
-// cs: the tile's two-step coefficients in shared memory, cs[i - ibase].
+// cs: the tile's two-step coefficients in shared memory, cs[i - ibase];
+// xs: x^2 (hi, lo) of the problem's latitudes.
 template <int kMode>
-__device__ __forceinline__ void generate_chunk(const TcArgs &a, const TileInfo &ti, int kc, int g,
+__device__ __forceinline__ void generate_chunk(const SegArgs &sg, const TileInfo &ti, int kc, int g,
                                                unsigned char *a_hi, unsigned char *a_lo, const Seed &sd,
                                                const float2 *xs, const float4 *cs, int ibase) {
   int kp, j, row, cbase;
@@ -394,10 +476,10 @@ __device__ __forceinline__ void generate_chunk(const TcArgs &a, const TileInfo &
     row = g & 127;
     cbase = 4 * (g >> 7);
   }
-  const float2 x2 = kp < a.Kh ? xs[kp] : make_float2(0.f, 0.f);
+  const float2 x2 = kp < sg.Kh ? xs[kp] : make_float2(0.f, 0.f);
   const float x2h = x2.x, x2l = x2.y;
   const int i0 = kSeedRows * j;
-  const bool zero = sd.e == kZeroBlock || ti.m + ti.p + 2 * i0 >= a.L;
+  const bool zero = sd.e == kZeroBlock || ti.m + ti.p + 2 * i0 >= sg.L;
   float pa = zero ? 0.f : sd.s0, pb = zero ? 0.f : sd.s1;  // scaled rows i, i + 1
   int E = zero ? 0 : sd.e;
   float scale = zero ? 0.f : pow2_or_zero(E);
@@ -444,18 +526,16 @@ __device__ __forceinline__ void generate_chunk(const TcArgs &a, const TileInfo &
 
 template <int kMode, bool kSplit, bool kGen>
 __global__ void __launch_bounds__(kGen ? kThreadsGen : kThreads, 1)
-tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
-                     const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                     const TcArgs a) {
+tc_persistent_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = align1024(smem_raw);
   __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t acc_cols = (uint32_t)tmem_cols_for(a.Nt);
+  const uint32_t acc_cols = (uint32_t)tmem_cols_for(P.Nmax);
   const uint32_t ncols = 2 * acc_cols;
-  const uint32_t sbytes = stage_bytes(kMode, kSplit, a.Nt);
-  const int S = a.stages;
+  const uint32_t sbytes = stage_bytes(kMode, kSplit, P.Nmax);
+  const int S = P.stages;
 
   if (warp == 2) tmem_alloc(&tmem_slot, ncols);
   if (threadIdx.x == 0) {
@@ -476,77 +556,84 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
 
   if (warp == 0 && lane == 0) {
     // TMA producer
-    tma_prefetch_desc(&ta_hi);
-    tma_prefetch_desc(&ta_lo);
-    tma_prefetch_desc(&tb_hi);
-    tma_prefetch_desc(&tb_lo);
+    for (int s = 0; s < P.nseg; s++) {
+      tma_prefetch_desc(&P.maps[s].a_hi);
+      tma_prefetch_desc(&P.maps[s].b_hi);
+    }
     uint32_t g = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      const TileInfo ti = tile_info<kMode>(a, t);
+    for (TileWalk<kMode> w(P); w.more(P);) {
+      const TileInfo ti = w.take(P);
+      const uint32_t tx = chunk_tx_bytes<kMode, kSplit, kGen>(ti);
       for (int kc = 0; kc < ti.nk; kc++, g++) {
         const int s = (int)(g % (uint32_t)S);
         const uint32_t use = g / (uint32_t)S;
-        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, a.err);
+        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, P.err);
         unsigned char *st = base + (size_t)s * sbytes;
-        // with kGen the generator warps fill the A buffers
-        mbar_arrive_expect_tx(&full_bar[s], kGen ? sbytes - 2u * kABytes : sbytes);
-        load_chunk<kMode, kSplit, kGen>(st, ti, kc, a.Nt, &ta_hi, &ta_lo, &tb_hi, &tb_lo, &full_bar[s]);
+        mbar_arrive_expect_tx(&full_bar[s], tx);
+        load_chunk<kMode, kSplit, kGen>(st, ti, kc, P.Nmax, P.maps[ti.s], &full_bar[s]);
       }
     }
   } else if (kGen && warp >= 8) {
     // table generators.  Shared memory after the stage ring: the current
     // tile's two-step coefficients (the next tile's are loaded into
-    // registers meanwhile), x^2 of every latitude, and a ring of kSeedAhead
-    // seed slots per thread filled by cp.async kSeedAhead chunks ahead.
+    // registers meanwhile), x^2 of every problem's latitudes, and a ring of
+    // kSeedAhead seed slots per thread filled by cp.async kSeedAhead chunks
+    // ahead.
     const int gtid = threadIdx.x - 256;
     float4 *cs = reinterpret_cast<float4 *>(base + (size_t)S * sbytes);
-    float2 *xs = reinterpret_cast<float2 *>(cs + a.ncmax);
-    Seed *ring = reinterpret_cast<Seed *>(xs + ((a.Kh + 1) & ~1));
-    for (int k = gtid; k < a.Kh; k += 256) xs[k] = make_float2(__ldg(a.x2h + k), __ldg(a.x2l + k));
-    // prefetch cursor: tile pt (pti), chunk pkc
-    int pt = blockIdx.x, pkc = 0;
+    float2 *xs = reinterpret_cast<float2 *>(cs + P.ncmax);
+    Seed *ring = reinterpret_cast<Seed *>(xs + ((P.xtot + 1) & ~1));
+    for (int s = 0; s < P.nseg; s++)
+      for (int k = gtid; k < P.seg[s].Kh; k += 256)
+        xs[P.seg[s].xoff + k] = make_float2(__ldg(P.seg[s].x2h + k), __ldg(P.seg[s].x2l + k));
+    // prefetch cursor over the same chunk sequence
+    TileWalk<kMode> pw(P);
     TileInfo pti{};
-    if (pt < a.ntiles) pti = tile_info<kMode>(a, pt);
+    pti.nk = 0;
+    int pkc = 0;
     auto prefetch = [&](uint32_t pg) {
-      while (pt < a.ntiles && pkc >= pti.nk) {
-        pt += gridDim.x;
+      while (pkc >= pti.nk && pw.more(P)) {
+        pti = pw.take(P);
         pkc = 0;
-        if (pt < a.ntiles) pti = tile_info<kMode>(a, pt);
       }
-      if (pt < a.ntiles) {
-        gen_prefetch<kMode>(a, pti, pkc, gtid, ring + (pg % kSeedAhead) * 256 + gtid);
+      if (pkc < pti.nk) {
+        gen_prefetch<kMode>(P.seg[pti.s], pti, pkc, gtid, ring + (pg % kSeedAhead) * 256 + gtid);
         pkc++;
       }
       cp_async_commit();
     };
     for (uint32_t q = 0; q < (uint32_t)kSeedAhead; q++) prefetch(q);
-    // coefficients of the first tile with chunks go through registers too
     auto coef_range = [&](const TileInfo &ti, int &ibase, int &ncoef) {
       // forward: the tile's 128 rows (+ 2 past its end), inverse: every row
       ibase = kMode == kFwd ? ti.r0 : 0;
       ncoef = kMode == kFwd ? 2 * kKc + 4 : kKc * ti.nk + 4;
     };
-    auto coef_load = [&](int t, float4 (&cr)[kCoefPerThread]) {
-      while (t < a.ntiles && tile_info<kMode>(a, t).nk == 0) t += gridDim.x;
+    // coefficients of the next tile with chunks (cursor cw) into registers
+    TileWalk<kMode> cw(P);
+    auto coef_load = [&](float4 (&cr)[kCoefPerThread]) {
 #pragma unroll
       for (int u = 0; u < kCoefPerThread; u++) cr[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (t >= a.ntiles) return;
-      const TileInfo ti = tile_info<kMode>(a, t);
+      TileInfo ti{};
+      ti.nk = 0;
+      while (ti.nk == 0 && cw.more(P)) ti = cw.take(P);
+      if (ti.nk == 0) return;
+      const SegArgs &sg = P.seg[ti.s];
       int ibase, ncoef;
       coef_range(ti, ibase, ncoef);
-      const float4 *src = a.coef + (int64_t)(ti.m * 2 + ti.p) * a.ldC;
+      const float4 *src = sg.coef + (int64_t)(ti.m * 2 + ti.p) * sg.ldC;
 #pragma unroll
       for (int u = 0; u < kCoefPerThread; u++) {
         const int e = gtid + 256 * u;
-        if (e < ncoef && ibase + e < a.ldC) cr[u] = __ldg(src + ibase + e);
+        if (e < ncoef && ibase + e < sg.ldC) cr[u] = __ldg(src + ibase + e);
       }
     };
     float4 creg[kCoefPerThread];
-    coef_load(blockIdx.x, creg);
+    coef_load(creg);
     uint32_t g = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      const TileInfo ti = tile_info<kMode>(a, t);
+    for (TileWalk<kMode> w(P); w.more(P);) {
+      const TileInfo ti = w.take(P);
       if (ti.nk == 0) continue;
+      const SegArgs &sg = P.seg[ti.s];
       int ibase, ncoef;
       coef_range(ti, ibase, ncoef);
       asm volatile("bar.sync 2, 256;" ::: "memory");  // previous tile's coefficients no longer read
@@ -556,15 +643,15 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
         if (e < ncoef) cs[e] = creg[u];
       }
       asm volatile("bar.sync 2, 256;" ::: "memory");  // also orders the x^2 stores of the first tile
-      coef_load(t + gridDim.x, creg);
+      coef_load(creg);
       for (int kc = 0; kc < ti.nk; kc++, g++) {
         const int s = (int)(g % (uint32_t)S);
         const uint32_t use = g / (uint32_t)S;
         cp_async_wait<kSeedAhead - 1>();
         const Seed sd = ring[(g % kSeedAhead) * 256 + gtid];
-        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, a.err);
+        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, P.err);
         unsigned char *st = base + (size_t)s * sbytes;
-        generate_chunk<kMode>(a, ti, kc, gtid, st, st + kABytes, sd, xs, cs, ibase);
+        generate_chunk<kMode>(sg, ti, kc, gtid, st, st + kABytes, sd, xs + sg.xoff, cs, ibase);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&full_bar[s]);
@@ -574,22 +661,22 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
     cp_async_wait<0>();
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    uint32_t idesc = idesc_bf16_f32(kRows, a.Nt, kMode != kFilt);
-    if (kGen && kMode == kFwd) idesc |= 1u << 15;  // generated table enters MN-major
     uint32_t g = 0, it = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, it++) {
-      const TileInfo ti = tile_info<kMode>(a, t);
+    for (TileWalk<kMode> w(P); w.more(P); it++) {
+      const TileInfo ti = w.take(P);
+      uint32_t idesc = idesc_bf16_f32(kRows, ti.Nt, kMode != kFilt);
+      if (kGen && kMode == kFwd) idesc |= 1u << 15;  // generated table enters MN-major
       const int acc = (int)(it & 1);
       const uint32_t use_a = it >> 1;
-      if (use_a > 0) mbar_wait(&tempty[acc], (use_a - 1) & 1, a.err);
+      if (use_a > 0) mbar_wait(&tempty[acc], (use_a - 1) & 1, P.err);
       tc_fence_after();
       const uint32_t tacc = tmem + (uint32_t)acc * acc_cols;
       for (int kc = 0; kc < ti.nk; kc++, g++) {
         const int s = (int)(g % (uint32_t)S);
         const uint32_t use = g / (uint32_t)S;
-        mbar_wait(&full_bar[s], use & 1, a.err);
+        mbar_wait(&full_bar[s], use & 1, P.err);
         tc_fence_after();
-        issue_chunk<kMode, kSplit, kGen>(base + (size_t)s * sbytes, a.Nt, tacc, idesc, kc == 0);
+        issue_chunk<kMode, kSplit, kGen>(base + (size_t)s * sbytes, P.Nmax, tacc, idesc, kc == 0);
         mma_commit(&empty_bar[s]);
       }
       if (ti.nk > 0)
@@ -597,16 +684,16 @@ tc_persistent_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_con
       else
         mbar_arrive(&tfull[acc]);
     }
-  } else if (warp >= 4) {
+  } else if (warp >= 4 && warp < 8) {
     // epilogue
     const int q4 = warp - 4;
     uint32_t it = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, it++) {
-      const TileInfo ti = tile_info<kMode>(a, t);
+    for (TileWalk<kMode> w(P); w.more(P); it++) {
+      const TileInfo ti = w.take(P);
       const int acc = (int)(it & 1);
-      mbar_wait(&tfull[acc], (it >> 1) & 1, a.err);
+      mbar_wait(&tfull[acc], (it >> 1) & 1, P.err);
       tc_fence_after();
-      epilogue<kMode>(a, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0);
+      epilogue<kMode>(P, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -779,44 +866,55 @@ void column_tiles(int B, int &Nt, int &nct) {
 }
 
 template <int kMode, bool kSplit, bool kGen>
-cudaError_t start_persistent(unsigned grid, size_t smem, const CUtensorMap &ta_hi, const CUtensorMap &ta_lo,
-                             const CUtensorMap &tb_hi, const CUtensorMap &tb_lo, const TcArgs &args,
-                             cudaStream_t st) {
+cudaError_t start_persistent(unsigned grid, size_t smem, const TcParams &P, cudaStream_t st) {
   auto fn = tc_persistent_kernel<kMode, kSplit, kGen>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, threads_of(kGen), smem, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  fn<<<grid, threads_of(kGen), smem, st>>>(P);
   return cudaSuccess;
 }
 
+// Shared memory of one CTA: 1024 B of alignment slack, the stage ring and
+// the generators' area; at most 227 KB with the static barriers.
+constexpr size_t kSmemLimit = 227 * 1024 - 256;
+
 template <int kMode>
-cudaError_t launch_persistent(bool split, bool gen, const CUtensorMap &ta_hi, const CUtensorMap &ta_lo,
-                              const CUtensorMap &tb_hi, const CUtensorMap &tb_lo, TcArgs &args, cudaStream_t st) {
-  if (args.ntiles <= 0) return cudaSuccess;
+cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch &cfg, cudaStream_t st) {
+  if (P.ntiles <= 0) return cudaSuccess;
   gen = gen && kMode != kFilt;
-  const int sb = (int)stage_bytes(kMode, split, args.Nt);
-  // coefficient staging of the table generators (forward: one 128-row tile,
-  // inverse: every chunk of one (m, p) block)
-  // generator shared memory: coefficients, x^2 per latitude, seed ring
-  args.ncmax = std::max(2 * kKc + 4, kKc * ((leg_rows(args.L, 0, 0) + kKc - 1) / kKc) + 4);
-  const size_t cbytes = !gen ? 0
-                             : sizeof(float4) * (size_t)args.ncmax + sizeof(float2) * (size_t)((args.Kh + 1) & ~1) +
-                                   sizeof(Seed) * 256 * kSeedAhead;
-  if (gen && args.ncmax > 256 * kCoefPerThread) return cudaErrorInvalidValue;
-  const int budget = 220 * 1024 - 1024 - (int)cbytes;
-  args.stages = std::max(2, std::min(kMaxStages, budget / sb));
-  const size_t smem = 1024 + (size_t)args.stages * sb + cbytes;
-  const unsigned grid = (unsigned)std::min(args.ntiles, sm_count());
+  const size_t sb = stage_bytes(kMode, split, P.Nmax);
+  size_t cbytes = 0;
+  if (gen) {
+    // generator shared memory: coefficients of one tile, x^2 of every
+    // problem's latitudes, the seed ring
+    int rows_max = 0;
+    P.xtot = 0;
+    for (int s = 0; s < P.nseg; s++) {
+      rows_max = std::max(rows_max, leg_rows(P.seg[s].L, 0, 0));
+      P.seg[s].xoff = P.xtot;
+      P.xtot += P.seg[s].Kh;
+    }
+    P.ncmax = std::max(2 * kKc + 4, kKc * ((rows_max + kKc - 1) / kKc) + 4);
+    if (P.ncmax > 256 * kCoefPerThread) return cudaErrorInvalidValue;
+    cbytes = sizeof(float4) * (size_t)P.ncmax + sizeof(float2) * (size_t)((P.xtot + 1) & ~1) +
+             sizeof(Seed) * 256 * kSeedAhead;
+  }
+  if (1024 + 2 * sb + cbytes > kSmemLimit) return cudaErrorInvalidValue;
+  int stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 1024 - cbytes) / sb);
+  if (cfg.stages >= 2) stages = std::min(stages, cfg.stages);
+  P.stages = stages;
+  const size_t smem = 1024 + (size_t)stages * sb + cbytes;
+  const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
   if constexpr (kMode == kFilt) {
-    e = split ? start_persistent<kMode, true, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st)
-              : start_persistent<kMode, false, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st);
+    e = split ? start_persistent<kMode, true, false>(grid, smem, P, st)
+              : start_persistent<kMode, false, false>(grid, smem, P, st);
   } else if (gen) {
-    e = split ? start_persistent<kMode, true, true>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st)
-              : start_persistent<kMode, false, true>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st);
+    e = split ? start_persistent<kMode, true, true>(grid, smem, P, st)
+              : start_persistent<kMode, false, true>(grid, smem, P, st);
   } else {
-    e = split ? start_persistent<kMode, true, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st)
-              : start_persistent<kMode, false, false>(grid, smem, ta_hi, ta_lo, tb_hi, tb_lo, args, st);
+    e = split ? start_persistent<kMode, true, false>(grid, smem, P, st)
+              : start_persistent<kMode, false, false>(grid, smem, P, st);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -862,55 +960,90 @@ cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double 
   return cudaGetLastError();
 }
 
+cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, const TcLaunch &cfg, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxSeg) return cudaErrorInvalidValue;
+  TcParams P{};
+  const bool split = items[0].T->split, gen = items[0].T->gen;
+  P.err = items[0].T->err;
+  int nseg = 0, ntiles = 0;
+  for (int i = 0; i < n; i++) {
+    const TcLegItem &it = items[i];
+    const TcPlanView &T = *it.T;
+    if (T.split != split || T.gen != gen) return cudaErrorInvalidValue;
+    if (it.ntiles <= 0 || it.B <= 0) continue;
+    SegArgs &g = P.seg[nseg];
+    g.L = T.L;
+    g.M = T.M;
+    g.Kh = T.Kh;
+    g.B = it.B;
+    if (it.Nt > 0) {
+      if (it.Nt % 16 != 0 || it.Nt > 256) return cudaErrorInvalidValue;
+      g.Nt = it.Nt;
+      g.nct = (2 * it.B + it.Nt - 1) / it.Nt;
+    } else {
+      column_tiles(it.B, g.Nt, g.nct);
+    }
+    g.tile0 = ntiles;
+    g.tiles = it.tiles;
+    g.fout = FwdOut{it.xhat, it.rows_hi, it.rows_lo, it.ldo, it.cin > 0 ? it.cin : 1, it.kx};
+    g.Gw = it.Gw;
+    g.ldc = it.ldc;
+    g.seeds = reinterpret_cast<const Seed *>(T.seeds);
+    g.coef = T.coef;
+    g.x2h = T.x2h;
+    g.x2l = T.x2l;
+    g.NB = T.NB;
+    g.ldC = T.ldC;
+    SegMaps &mp = P.maps[nseg];
+    if (!inverse) {
+      mp.a_hi = T.tab_fwd_hi;
+      mp.a_lo = T.tab_fwd_lo;
+      mp.b_hi = T.f_hi;
+      mp.b_lo = split ? T.f_lo : T.f_hi;
+    } else {
+      mp.a_hi = T.tab_inv_hi;
+      mp.a_lo = T.tab_inv_lo;
+      mp.b_hi = T.s_hi;
+      mp.b_lo = split ? T.s_lo : T.s_hi;
+    }
+    P.Nmax = std::max(P.Nmax, g.Nt);
+    ntiles += it.ntiles * g.nct;
+    nseg++;
+  }
+  if (nseg == 0) return cudaSuccess;
+  P.nseg = nseg;
+  P.ntiles = ntiles;
+  return inverse ? launch_persistent<kInv>(split, gen, P, cfg, st) : launch_persistent<kFwd>(split, gen, P, cfg, st);
+}
+
 cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
                               __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
                               cudaStream_t st) {
-  if (ntiles == 0 || B <= 0) return cudaSuccess;
-  TcArgs a{};
-  a.L = T.L;
-  a.M = T.M;
-  a.Kh = T.Kh;
-  a.B = B;
-  column_tiles(B, a.Nt, a.nct);
-  a.ntiles = ntiles * a.nct;
-  a.tiles = tiles;
-  a.roff = T.roff;
-  a.soff = T.soff;
-  a.fout = FwdOut{xhat, rows_hi, rows_lo, ldo, cin > 0 ? cin : 1, kx};
-  a.err = T.err;
-  a.seeds = reinterpret_cast<const Seed *>(T.seeds);
-  a.coef = T.coef;
-  a.x2h = T.x2h;
-  a.x2l = T.x2l;
-  a.NB = T.NB;
-  a.ldC = T.ldC;
-  return launch_persistent<kFwd>(T.split, T.gen, T.tab_fwd_hi, T.tab_fwd_lo, T.f_hi, T.split ? T.f_lo : T.f_hi, a, st);
+  TcLegItem it{};
+  it.T = &T;
+  it.tiles = tiles;
+  it.ntiles = ntiles;
+  it.B = B;
+  it.xhat = xhat;
+  it.rows_hi = rows_hi;
+  it.rows_lo = rows_lo;
+  it.ldo = ldo;
+  it.cin = cin;
+  it.kx = kx;
+  return launch_leg_tc_group(0, &it, 1, TcLaunch{}, st);
 }
 
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
                               cudaStream_t st) {
-  if (ntiles == 0 || B <= 0) return cudaSuccess;
-  TcArgs a{};
-  a.L = T.L;
-  a.M = T.M;
-  a.Kh = T.Kh;
-  a.B = B;
-  column_tiles(B, a.Nt, a.nct);
-  a.ntiles = ntiles * a.nct;
-  a.tiles = tiles;
-  a.roff = T.roff;
-  a.soff = T.soff;
-  a.Gw = Gw;
-  a.ldc = ldc;
-  a.err = T.err;
-  a.seeds = reinterpret_cast<const Seed *>(T.seeds);
-  a.coef = T.coef;
-  a.x2h = T.x2h;
-  a.x2l = T.x2l;
-  a.NB = T.NB;
-  a.ldC = T.ldC;
-  return launch_persistent<kInv>(T.split, T.gen, T.tab_inv_hi, T.tab_inv_lo, T.s_hi, T.split ? T.s_lo : T.s_hi, a,
-                                 st);
+  TcLegItem it{};
+  it.T = &T;
+  it.tiles = tiles;
+  it.ntiles = ntiles;
+  it.B = B;
+  it.Gw = Gw;
+  it.ldc = ldc;
+  return launch_leg_tc_group(1, &it, 1, TcLaunch{}, st);
 }
 
 cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
@@ -924,25 +1057,30 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
                              const CUtensorMap &tw_lo, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx,
                              int nwr, int Bm, int Cin, int Cout, cudaStream_t st) {
   if (nftiles == 0 || Bm <= 0) return cudaSuccess;
-  TcArgs a{};
-  a.L = T.L;
-  a.M = T.M;
-  a.Kh = T.Kh;
-  a.ntn = (2 * Cout + 255) / 256;
-  a.Nt = ((2 * Cout + a.ntn - 1) / a.ntn + 15) / 16 * 16;
-  a.Bm = Bm;
-  a.ntiles = nftiles * Bm * a.ntn;
-  a.ftiles = reinterpret_cast<const FiltTile *>(ftiles);
-  a.soff = T.soff;
-  a.kx = kx;
-  a.nwr = nwr;
-  a.cin = Cin;
-  a.cout = Cout;
-  a.lds = lds;
-  a.s_hi = s_hi;
-  a.s_lo = s_lo;
-  a.err = T.err;
-  return launch_persistent<kFilt>(T.split, false, T.x_hi, T.split ? T.x_lo : T.x_hi, tw_hi, tw_lo, a, st);
+  TcParams P{};
+  P.nseg = 1;
+  P.L = T.L;
+  P.M = T.M;
+  P.ntn = (2 * Cout + 255) / 256;
+  P.Nt = ((2 * Cout + P.ntn - 1) / P.ntn + 15) / 16 * 16;
+  P.Nmax = P.Nt;
+  P.Bm = Bm;
+  P.ntiles = nftiles * Bm * P.ntn;
+  P.ftiles = reinterpret_cast<const FiltTile *>(ftiles);
+  P.soff = T.soff;
+  P.kx = kx;
+  P.nwr = nwr;
+  P.cin = Cin;
+  P.cout = Cout;
+  P.lds = lds;
+  P.s_hi = s_hi;
+  P.s_lo = s_lo;
+  P.err = T.err;
+  P.maps[0].a_hi = T.x_hi;
+  P.maps[0].a_lo = T.split ? T.x_lo : T.x_hi;
+  P.maps[0].b_hi = tw_hi;
+  P.maps[0].b_lo = tw_lo;
+  return launch_persistent<kFilt>(T.split, false, P, TcLaunch{}, st);
 }
 
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,

@@ -23,11 +23,14 @@ struct RadixPlan {
   int r[kMaxRadices];
 };
 
-// One tile of a Legendre contraction: order m, parity p of l + m, first row.
-struct LegTile {
+// One tile of a Legendre contraction: order m, parity p of l + m, first row
+// (or latitude), and for the tensor-core kernels the row of its first
+// operand (forward: table row roff[2m+p] + r0; inverse: soff[2m+p]).
+struct __align__(16) LegTile {
   int m;
   int p;
   int r0;
+  int row;
 };
 
 // Device-side view of the folded FP32 Legendre table.  For order m and
@@ -88,6 +91,30 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
 // FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
                               cudaStream_t st);
+// One problem of a grouped tensor-core Legendre launch: a plan's view, its
+// tiles, its batch, and the destination of the forward (xhat or rows, as in
+// launch_leg_fwd_tc) or of the inverse (Gw, ldc).  Nt = column tile width
+// (multiple of 16, <= 256; 0 = balanced tiles of at most 256).
+struct TcLegItem {
+  const TcPlanView *T;
+  const LegTile *tiles;
+  int ntiles;
+  int B, Nt;
+  float2 *xhat;
+  __nv_bfloat16 *rows_hi, *rows_lo;
+  int ldo, cin, kx;
+  float *Gw;
+  int ldc;
+};
+// Launch shape of a persistent kernel: CTAs (0 = one per SM) and pipeline
+// stages (0 = as many as fit).
+struct TcLaunch {
+  int grid;
+  int stages;
+};
+// Up to 8 problems of equal precision and table source in one persistent
+// launch (inverse = 0: forward contraction, 1: inverse).
+cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, const TcLaunch &cfg, cudaStream_t st);
 // API-layout coefficients -> internal bf16 hi/lo rows.
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,
                              int M, int ldb, int B, cudaStream_t st);
