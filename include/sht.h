@@ -232,6 +232,99 @@ sht_status_t sht_forward_static_scratch(sht_plan_t plan, const float *x,
                                         void *xhat, int64_t B, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched transforms over several grids.  Ensemble members are independent
+ * of one another (the ensemble-parallel computations of the section on
+ * simultaneous model-, data- and ensemble-parallelism are embarrassingly
+ * parallel), so many fields on grids of different
+ * sizes can be transformed together.  A batch binds up to 8 items, each a
+ * plan (its grid, table and workspace) with a fixed count of fields and
+ * fixed input and output buffers, and records the whole transform of all
+ * items as one CUDA graph: one grouped longitude launch, one persistent
+ * Legendre launch over the tiles of every item, one grouped epilogue launch
+ * (zero fill for the forward; the coefficient repacking precedes the
+ * inverse on the tensor-core precisions).  sht_batch_run replays it.
+ *
+ * Items:
+ *   plan   a plan, at most once per batch; all plans of a batch share the
+ *          device, the precision and the table source.
+ *   count  fields, 1 <= count <= the plan's max_batch.
+ *   in     forward: float [count][nlat][nlon]; inverse: complex64
+ *          [count][lmax][mmax] (same contract as sht_forward / sht_inverse).
+ *   out    forward: complex64 [count][lmax][mmax]; inverse: float
+ *          [count][nlat][nlon].
+ * The buffers stay owned by the caller and must outlive the batch; their
+ * contents are read and written by every run.  The plans' workspaces are
+ * used by the runs: a plan must not execute other calls concurrently.
+ *
+ * Tuning (opts.tune = 1): creation times the Legendre launch for candidate
+ * launch shapes (column tile widths 256, 128 and 64 for the tensor-core
+ * precisions; item orders) on the bound buffers — so it writes the outputs
+ * — and keeps the fastest.  With opts.tune_cache set, the choice is looked
+ * up in that text file by the batch's key first, and appended to it after
+ * tuning.  opts.profile = 1 adds CUDA event nodes between the kernels of
+ * the graph for sht_batch_profile_*.
+ *
+ * Errors: INVALID_ARG (n outside 1..8, NULL or repeated plans, mixed
+ * device, precision or table source, counts outside the range, NULL
+ * buffers); CUDA / OOM from tuning, capture or instantiation.
+ * No paper counterpart as an interface: it serves the batched form.
+ * ------------------------------------------------------------------------- */
+typedef struct sht_batch_s *sht_batch_t;
+
+typedef enum {
+  SHT_BATCH_FORWARD = 0,   /* sht_forward of every item */
+  SHT_BATCH_INVERSE = 1    /* sht_inverse of every item */
+} sht_batch_direction_t;
+
+typedef struct {
+  sht_plan_t plan;
+  int64_t count;
+  const void *in;
+  void *out;
+} sht_batch_item;
+
+typedef struct {
+  int direction;           /* sht_batch_direction_t, default FORWARD     */
+  int tune;                /* 1 (default): time candidate launch shapes  */
+  const char *tune_cache;  /* NULL (default) or a text file of choices   */
+  int profile;             /* 0 (default) or 1: event nodes in the graph */
+  int reserved[8];         /* must be zero                               */
+} sht_batch_opts;
+
+void sht_batch_opts_default(sht_batch_opts *opts);
+
+/* Validate, tune, record and instantiate.  `stream` (may be NULL) orders
+ * the tuning runs after the caller's earlier work on it; creation returns
+ * after they finished. */
+sht_status_t sht_batch_create(sht_batch_t *out, const sht_batch_item *items,
+                              int n, const sht_batch_opts *opts,
+                              void *stream);
+
+/* Launch the recorded graph on `stream` (NULL: the legacy default stream).
+ * Asynchronous; errors of earlier device work surface as SHT_ERR_CUDA. */
+sht_status_t sht_batch_run(sht_batch_t batch, void *stream);
+
+/* NUL-terminated description of the launch shape in use and how it was
+ * chosen, e.g. "legendre: tile<=128, order=cost; tuned 412.3 us". */
+sht_status_t sht_batch_describe(sht_batch_t batch, char *buf, int len);
+
+/* Kernels of the graph, in launch order ("r2c", "leg_fwd", "zero", ...). */
+int sht_batch_stage_count(sht_batch_t batch);
+const char *sht_batch_stage_name(sht_batch_t batch, int stage);
+
+/* Per-stage device time of profiled runs (batches created with
+ * opts.profile = 1).  begin: record the next `capacity` runs; collect: wait
+ * for them and return the number of recorded runs and the summed
+ * milliseconds per stage (array of sht_batch_stage_count entries), then
+ * reset the record. */
+sht_status_t sht_batch_profile_begin(sht_batch_t batch, int capacity);
+sht_status_t sht_batch_profile_collect(sht_batch_t batch, int64_t *runs,
+                                       double *ms);
+
+/* Release the graph and the batch (not the plans or the buffers). */
+sht_status_t sht_batch_destroy(sht_batch_t batch);
+
+/* ---------------------------------------------------------------------------
  * Per-kernel timing.  While profiling is on, every kernel a plan's execute
  * calls launch is bracketed by two CUDA events recorded on the launch
  * stream (up to `capacity` launches; later launches run unrecorded and are

@@ -20,7 +20,7 @@ import torch
 from . import _abi
 from ._abi import ShtError
 
-__all__ = ["Plan", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
+__all__ = ["Plan", "Batch", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
            "SpectralBlock", "spectral_block", "ShtError"]
 
@@ -267,6 +267,98 @@ def spectral_filter_inverse(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> 
 # ---------------------------------------------------------------------------
 # autograd
 # ---------------------------------------------------------------------------
+
+class Batch:
+    """Forward or inverse SHTs of several plans (grids) in one CUDA-graph
+    launch.  ``items`` is a list of (plan, input, output) with the tensors
+    of sht_forward (float32 [count, nlat, nlon] -> complex64 [count, lmax,
+    mmax]) or of sht_inverse (the reverse); the tensors stay bound to the
+    batch and every ``run()`` reads and writes them.  ``tune`` times
+    candidate launch shapes at creation (writing the outputs);
+    ``tune_cache`` names a text file of tuned choices; ``profile`` adds
+    per-kernel events (``profile_begin`` / ``profile_collect``)."""
+
+    def __init__(self, items, direction: str = "forward", tune: bool = True, tune_cache: str | None = None,
+                 profile: bool = False):
+        if direction not in _abi.BATCH_DIRECTIONS:
+            raise ValueError(f"direction must be one of {list(_abi.BATCH_DIRECTIONS)}")
+        arr = (_abi.sht_batch_item * len(items))()
+        keep = []
+        dev = None
+        for k, (plan, inp, out) in enumerate(items):
+            fwd = direction == "forward"
+            in_dtype, out_dtype = (torch.float32, torch.complex64) if fwd else (torch.complex64, torch.float32)
+            sp, sc = (plan.nlat, plan.nlon), (plan.lmax, plan.mmax)
+            in_tail, out_tail = (sp, sc) if fwd else (sc, sp)
+            for name, t, dt, tail in (("input", inp, in_dtype, in_tail), ("output", out, out_dtype, out_tail)):
+                _need(t, dt, f"{name} {k}", plan.device)
+                if t.dim() != 3 or tuple(t.shape[1:]) != tail or not t.is_contiguous():
+                    raise ValueError(f"{name} {k} must be a contiguous (count, {tail[0]}, {tail[1]}) tensor")
+            if out.shape[0] != inp.shape[0]:
+                raise ValueError(f"input {k} and output {k} differ in count")
+            arr[k] = _abi.sht_batch_item(plan.handle, inp.shape[0], _ptr(inp), _ptr(out))
+            keep.append((plan, inp, out))
+            dev = plan.device
+        opts = _abi.sht_batch_opts()
+        _abi.lib().sht_batch_opts_default(ctypes.byref(opts))
+        opts.direction = _abi.BATCH_DIRECTIONS[direction]
+        opts.tune = 1 if tune else 0
+        opts.tune_cache = tune_cache.encode() if tune_cache else None
+        opts.profile = 1 if profile else 0
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            st = torch.cuda.current_stream(dev).cuda_stream
+            _abi.check(_abi.lib().sht_batch_create(ctypes.byref(h), arr, len(items), ctypes.byref(opts),
+                                                   ctypes.c_void_p(st)))
+        self._h = h
+        self._keep = keep
+        self.device = dev
+        self.direction = direction
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("batch has been destroyed")
+        return self._h
+
+    def run(self) -> None:
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        _abi.check(_abi.lib().sht_batch_run(self.handle, ctypes.c_void_p(st)))
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        _abi.check(_abi.lib().sht_batch_describe(self.handle, buf, len(buf)))
+        return buf.value.decode()
+
+    @property
+    def stages(self) -> list:
+        n = _abi.lib().sht_batch_stage_count(self.handle)
+        return [_abi.lib().sht_batch_stage_name(self.handle, k).decode() for k in range(n)]
+
+    def profile_begin(self, capacity: int = 4096) -> None:
+        _abi.check(_abi.lib().sht_batch_profile_begin(self.handle, int(capacity)))
+
+    def profile_collect(self) -> dict:
+        """{stage: total ms} over the recorded runs, and "_runs"."""
+        n = _abi.lib().sht_batch_stage_count(self.handle)
+        runs = ctypes.c_int64()
+        ms = (ctypes.c_double * n)()
+        _abi.check(_abi.lib().sht_batch_profile_collect(self.handle, ctypes.byref(runs), ms))
+        out = {name: float(ms[k]) for k, name in enumerate(self.stages)}
+        out["_runs"] = int(runs.value)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            h, self._h = self._h, None
+            _abi.check(_abi.lib().sht_batch_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class SpectralBlock(torch.autograd.Function):
     """y = ISHT(filter(SHT(x), W)) with hand-written adjoints.

@@ -26,6 +26,18 @@ class sht_plan_opts(ctypes.Structure):
                 ("max_channels", ctypes.c_int), ("table_source", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
+class sht_batch_item(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("count", ctypes.c_int64), ("input", ctypes.c_void_p),
+                ("output", ctypes.c_void_p)]
+
+
+class sht_batch_opts(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_int), ("tune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+BATCH_DIRECTIONS = {"forward": 0, "inverse": 1}
+
 _i, _i64, _p, _d = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
 _ip, _i64p = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)
 
@@ -54,6 +66,16 @@ SIGNATURES = {
     "sht_last_error_message": ([], ctypes.c_char_p),
     "sht_version": ([], ctypes.c_char_p),
     "sht_debug_fail_alloc_after": ([_i], None),
+    "sht_batch_opts_default": ([ctypes.POINTER(sht_batch_opts)], None),
+    "sht_batch_create": ([ctypes.POINTER(_p), ctypes.POINTER(sht_batch_item), _i, ctypes.POINTER(sht_batch_opts), _p],
+                         _i),
+    "sht_batch_run": ([_p, _p], _i),
+    "sht_batch_describe": ([_p, ctypes.c_char_p, _i], _i),
+    "sht_batch_stage_count": ([_p], _i),
+    "sht_batch_stage_name": ([_p, _i], ctypes.c_char_p),
+    "sht_batch_profile_begin": ([_p, _i], _i),
+    "sht_batch_profile_collect": ([_p, _i64p, ctypes.POINTER(ctypes.c_double)], _i),
+    "sht_batch_destroy": ([_p], _i),
 }
 
 _lock = threading.Lock()

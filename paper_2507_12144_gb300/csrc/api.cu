@@ -480,6 +480,7 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   p->L = lmax;
   p->M = mmax;
   p->precision = o.precision;
+  p->table_source = o.precision == SHT_PREC_FP32 ? SHT_TABLE_STREAMED : o.table_source;
   p->max_batch = o.max_batch;
   p->Kh = (nlat + 1) / 2;
   p->Khp = (p->Kh + 15) / 16 * 16;

@@ -26,17 +26,18 @@ constexpr int kTileK = 16;   // reduction chunk
 constexpr int kThreads = 256;
 
 // Forward: C[i][c] = sum_k' T[i][k'] F[k'][c]   (i rows of block (m, p))
-__global__ void __launch_bounds__(kThreads)
-leg_fwd_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float *__restrict__ Fw,
-                   float2 *__restrict__ xhat, int L, int M, int Kh, int ldc, int B, int nct) {
+// CTA bid of the forward contraction of one problem.
+__device__ __forceinline__ void leg_fwd_f32_body(int bid, const TableF32 &T, const LegTile *__restrict__ tiles,
+                                                 const float *__restrict__ Fw, float2 *__restrict__ xhat, int L,
+                                                 int M, int Kh, int ldc, int B, int nct) {
   __shared__ __align__(16) float As[kTileK][kTileR];
   __shared__ __align__(16) float Bs[kTileK][kTileC];
   // column tiles vary fastest so that the CTAs sharing one table tile run
   // back to back and find it in L2
-  const LegTile tile = tiles[blockIdx.x / nct];
+  const LegTile tile = tiles[bid / nct];
   const int m = tile.m, p = tile.p, r0 = tile.r0;
   const int nrows = leg_rows(L, m, p);
-  const int c0 = (blockIdx.x % nct) * kTileC;
+  const int c0 = (bid % nct) * kTileC;
   const float *A = T.data + T.off[2 * m + p];
   const float *Bm = Fw + ((int64_t)m * 2 + p) * Kh * (int64_t)ldc;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -89,15 +90,15 @@ leg_fwd_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float *_
 }
 
 // Inverse: C[k'][c] = sum_i T[i][k'] Y[i][c],  Y[i][2b + {0,1}] = yhat[b][l_i][m]
-__global__ void __launch_bounds__(kThreads)
-leg_inv_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float2 *__restrict__ yhat,
-                   float *__restrict__ Gw, int L, int M, int Kh, int ldc, int B, int nct) {
+__device__ __forceinline__ void leg_inv_f32_body(int bid, const TableF32 &T, const LegTile *__restrict__ tiles,
+                                                 const float2 *__restrict__ yhat, float *__restrict__ Gw, int L,
+                                                 int M, int Kh, int ldc, int B, int nct) {
   __shared__ __align__(16) float As[kTileK][kTileR];
   __shared__ __align__(16) float Bs[kTileK][kTileC];
-  const LegTile tile = tiles[blockIdx.x / nct];
+  const LegTile tile = tiles[bid / nct];
   const int m = tile.m, p = tile.p, k0r = tile.r0;  // r0 = first k'
   const int nrows = leg_rows(L, m, p);              // reduction length
-  const int c0 = (blockIdx.x % nct) * kTileC;
+  const int c0 = (bid % nct) * kTileC;
   const float *A = T.data + T.off[2 * m + p];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float acc[4][4];
@@ -147,6 +148,71 @@ leg_inv_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float2 *
     const int c = c0 + tx * 4;
     if (c < ldc) *reinterpret_cast<float4 *>(G + (int64_t)k * ldc + c) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
   }
+}
+
+// One problem of a grouped FP32 launch; CTA j belongs to the problem s with
+// blk0[s] <= j < blk0[s + 1].
+struct F32Seg {
+  TableF32 T;
+  const LegTile *tiles;
+  const float *Fw;
+  float2 *xhat;
+  const float2 *yhat;
+  float *Gw;
+  int L, M, Kh, ldc, B, nct, blk0;
+};
+struct F32Group {
+  F32Seg seg[kMaxLegGroup];
+  int nseg;
+};
+
+__device__ __forceinline__ int f32_segment(const F32Group &g, int blk) {
+  int s = 0;
+  while (s + 1 < g.nseg && blk >= g.seg[s + 1].blk0) s++;
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+leg_fwd_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float *__restrict__ Fw,
+                   float2 *__restrict__ xhat, int L, int M, int Kh, int ldc, int B, int nct) {
+  leg_fwd_f32_body(blockIdx.x, T, tiles, Fw, xhat, L, M, Kh, ldc, B, nct);
+}
+
+__global__ void __launch_bounds__(kThreads)
+leg_inv_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float2 *__restrict__ yhat,
+                   float *__restrict__ Gw, int L, int M, int Kh, int ldc, int B, int nct) {
+  leg_inv_f32_body(blockIdx.x, T, tiles, yhat, Gw, L, M, Kh, ldc, B, nct);
+}
+
+__global__ void __launch_bounds__(kThreads) leg_fwd_f32_grouped(const __grid_constant__ F32Group g) {
+  const F32Seg &q = g.seg[f32_segment(g, blockIdx.x)];
+  leg_fwd_f32_body(blockIdx.x - q.blk0, q.T, q.tiles, q.Fw, q.xhat, q.L, q.M, q.Kh, q.ldc, q.B, q.nct);
+}
+
+__global__ void __launch_bounds__(kThreads) leg_inv_f32_grouped(const __grid_constant__ F32Group g) {
+  const F32Seg &q = g.seg[f32_segment(g, blockIdx.x)];
+  leg_inv_f32_body(blockIdx.x - q.blk0, q.T, q.tiles, q.yhat, q.Gw, q.L, q.M, q.Kh, q.ldc, q.B, q.nct);
+}
+
+// Zero fill of the l < m entries of several problems: one warp per (b, l)
+// row, rows of problem s from row0[s].
+struct ZeroGroup {
+  float2 *xhat[kMaxLegGroup];
+  int64_t row0[kMaxLegGroup + 1];
+  int L[kMaxLegGroup], M[kMaxLegGroup];
+  int nseg;
+};
+
+__global__ void zero_upper_grouped(const __grid_constant__ ZeroGroup g) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= g.row0[g.nseg]) return;
+  int s = 0;
+  while (s + 1 < g.nseg && row >= g.row0[s + 1]) s++;
+  const int64_t r = row - g.row0[s];
+  const int L = g.L[s], M = g.M[s];
+  const int l = (int)(r % L);
+  float2 *out = g.xhat[s] + r * M;
+  for (int m = l + 1 + (threadIdx.x & 31); m < M; m += 32) out[m] = make_float2(0.f, 0.f);
 }
 
 __global__ void zero_upper_kernel(float2 *__restrict__ xhat, int L, int M, int64_t rows) {
@@ -206,6 +272,61 @@ cudaError_t launch_leg_inv_f32(const TableF32 &T, const LegTile *tiles, int ntil
   if (ntiles == 0 || B <= 0) return cudaSuccess;
   const int nct = (2 * B + kTileC - 1) / kTileC;
   leg_inv_f32_kernel<<<(unsigned)ntiles * nct, kThreads, 0, st>>>(T, tiles, yhat, Gw, L, M, Kh, ldc, B, nct);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leg_f32_group(int inverse, const F32LegItem *items, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxLegGroup) return cudaErrorInvalidValue;
+  F32Group g{};
+  int64_t blk = 0;
+  for (int i = 0; i < n; i++) {
+    const F32LegItem &it = items[i];
+    if (it.ntiles <= 0 || it.B <= 0) continue;
+    F32Seg &q = g.seg[g.nseg++];
+    q.T = it.T;
+    q.tiles = it.tiles;
+    q.Fw = it.Fw;
+    q.xhat = it.xhat;
+    q.yhat = it.yhat;
+    q.Gw = it.Gw;
+    q.L = it.L;
+    q.M = it.M;
+    q.Kh = it.Kh;
+    q.ldc = it.ldc;
+    q.B = it.B;
+    q.nct = (2 * it.B + kTileC - 1) / kTileC;
+    q.blk0 = (int)blk;
+    blk += (int64_t)it.ntiles * q.nct;
+  }
+  if (g.nseg == 0) return cudaSuccess;
+  if (blk > 0x7fffffff) return cudaErrorInvalidValue;
+  if (inverse)
+    leg_inv_f32_grouped<<<(unsigned)blk, kThreads, 0, st>>>(g);
+  else
+    leg_fwd_f32_grouped<<<(unsigned)blk, kThreads, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_upper_group(float2 *const *xhat, const int *L, const int *M, const int64_t *B, int n,
+                                    cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxLegGroup) return cudaErrorInvalidValue;
+  ZeroGroup g{};
+  int64_t rows = 0;
+  for (int i = 0; i < n; i++) {
+    if (B[i] <= 0 || M[i] <= 1) continue;
+    const int s = g.nseg++;
+    g.xhat[s] = xhat[i];
+    g.L[s] = L[i];
+    g.M[s] = M[i];
+    g.row0[s] = rows;
+    rows += B[i] * L[i];
+  }
+  g.row0[g.nseg] = rows;
+  if (rows == 0) return cudaSuccess;
+  const int wpb = 8;
+  zero_upper_grouped<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -710,12 +710,12 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
 // Repack API-layout coefficients yhat[b][l][m] (complex64) into the internal
 // split rows S[soff(m, p) + i][2b + {re, im}] (bf16 hi and lo), l = m + p + 2i.
 // One thread per (row, field).
-__global__ void pack_rows_kernel(const float2 *__restrict__ yhat, __nv_bfloat16 *__restrict__ shi,
-                                 __nv_bfloat16 *__restrict__ slo, const int *__restrict__ soff, int L, int M, int ldb,
-                                 int B) {
-  const int m = blockIdx.y >> 1, p = blockIdx.y & 1;
+__device__ __forceinline__ void pack_rows_body(int bx, int by, const float2 *__restrict__ yhat,
+                                               __nv_bfloat16 *__restrict__ shi, __nv_bfloat16 *__restrict__ slo,
+                                               const int *__restrict__ soff, int L, int M, int ldb, int B) {
+  const int m = by >> 1, p = by & 1;
   const int nrows = leg_rows(L, m, p);
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
   if (e >= (int64_t)nrows * B) return;
   const int i = (int)(e / B), b = (int)(e - (int64_t)i * B);
   const float2 v = yhat[((int64_t)b * L + m + p + 2 * i) * M + m];
@@ -725,6 +725,31 @@ __global__ void pack_rows_kernel(const float2 *__restrict__ yhat, __nv_bfloat16 
   const int64_t o = (int64_t)(soff[2 * m + p] + i) * ldb + 2 * b;
   *reinterpret_cast<uint32_t *>(shi + o) = pack_bf16x2(hr, hi_);
   if (slo) *reinterpret_cast<uint32_t *>(slo + o) = pack_bf16x2(lr, li);
+}
+
+__global__ void pack_rows_kernel(const float2 *__restrict__ yhat, __nv_bfloat16 *__restrict__ shi,
+                                 __nv_bfloat16 *__restrict__ slo, const int *__restrict__ soff, int L, int M, int ldb,
+                                 int B) {
+  pack_rows_body(blockIdx.x, blockIdx.y, yhat, shi, slo, soff, L, M, ldb, B);
+}
+
+// Repacking of several problems in one launch: CTA j belongs to problem s
+// with blk0[s] <= j < blk0[s + 1]; (bx, by) follow from gx[s].
+struct PackGroup {
+  const float2 *yhat[kMaxSeg];
+  __nv_bfloat16 *shi[kMaxSeg], *slo[kMaxSeg];
+  const int *soff[kMaxSeg];
+  int L[kMaxSeg], M[kMaxSeg], ldb[kMaxSeg], B[kMaxSeg], gx[kMaxSeg];
+  int blk0[kMaxSeg + 1];
+  int nseg;
+};
+
+__global__ void pack_rows_grouped(const __grid_constant__ PackGroup g) {
+  int s = 0;
+  while (s + 1 < g.nseg && (int)blockIdx.x >= g.blk0[s + 1]) s++;
+  const int local = blockIdx.x - g.blk0[s];
+  pack_rows_body(local % g.gx[s], local / g.gx[s], g.yhat[s], g.shi[s], g.slo[s], g.soff[s], g.L[s], g.M[s],
+                 g.ldb[s], g.B[s]);
 }
 
 // WR[l][n][k] (bf16 hi/lo), n < nwr rows, k < kx columns, from W[l][o][i]:
@@ -1081,6 +1106,34 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.maps[0].b_hi = tw_hi;
   P.maps[0].b_lo = tw_lo;
   return launch_persistent<kFilt>(T.split, false, P, TcLaunch{}, st);
+}
+
+cudaError_t launch_pack_rows_group(const PackItem *items, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxSeg) return cudaErrorInvalidValue;
+  PackGroup g{};
+  int64_t blk = 0;
+  for (int i = 0; i < n; i++) {
+    const PackItem &it = items[i];
+    if (it.B <= 0) continue;
+    const int s = g.nseg++;
+    g.yhat[s] = it.yhat;
+    g.shi[s] = it.shi;
+    g.slo[s] = it.slo;
+    g.soff[s] = it.soff;
+    g.L[s] = it.L;
+    g.M[s] = it.M;
+    g.ldb[s] = it.ldb;
+    g.B[s] = it.B;
+    g.gx[s] = (int)(((int64_t)leg_rows(it.L, 0, 0) * it.B + 255) / 256);
+    g.blk0[s] = (int)blk;
+    blk += (int64_t)g.gx[s] * 2 * it.M;
+  }
+  g.blk0[g.nseg] = (int)blk;
+  if (blk == 0) return cudaSuccess;
+  if (blk > 0x7fffffff) return cudaErrorInvalidValue;
+  pack_rows_grouped<<<(unsigned)blk, 256, 0, st>>>(g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,

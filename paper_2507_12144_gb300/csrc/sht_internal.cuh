@@ -116,6 +116,13 @@ struct TcLaunch {
 // launch (inverse = 0: forward contraction, 1: inverse).
 cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, const TcLaunch &cfg, cudaStream_t st);
 // API-layout coefficients -> internal bf16 hi/lo rows.
+struct PackItem {
+  const float2 *yhat;
+  __nv_bfloat16 *shi, *slo;
+  const int *soff;
+  int L, M, ldb, B;
+};
+cudaError_t launch_pack_rows_group(const PackItem *items, int n, cudaStream_t st);
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,
                              int M, int ldb, int B, cudaStream_t st);
 // Longitude analysis writing the folded Fourier workspace as bf16 hi/lo
@@ -197,6 +204,25 @@ cudaError_t launch_leg_inv_f32(const TableF32 &T, const LegTile *tiles,
                                int ntiles, const float2 *yhat, float *Gw,
                                int L, int M, int Kh, int ldc, int B,
                                cudaStream_t st);
+
+// One problem of a grouped FP32 Legendre launch (the arguments of
+// launch_leg_fwd_f32: T, tiles, Fw -> xhat; or of launch_leg_inv_f32:
+// T, tiles, yhat -> Gw).
+constexpr int kMaxLegGroup = 8;
+struct F32LegItem {
+  TableF32 T;
+  const LegTile *tiles;
+  int ntiles;
+  const float *Fw;
+  float2 *xhat;
+  const float2 *yhat;
+  float *Gw;
+  int L, M, Kh, ldc, B;
+};
+cudaError_t launch_leg_f32_group(int inverse, const F32LegItem *items, int n, cudaStream_t st);
+// Zero fill of the l < m parts of up to kMaxLegGroup problems in one launch.
+cudaError_t launch_zero_upper_group(float2 *const *xhat, const int *L, const int *M, const int64_t *B, int n,
+                                    cudaStream_t st);
 
 // Zero the l < m part of B dense [L][M] coefficient blocks.
 cudaError_t launch_zero_upper(float2 *xhat, int L, int M, int64_t B,

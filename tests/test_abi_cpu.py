@@ -101,3 +101,26 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _abi.lib()
+
+
+def test_batch_rejects_bad_arguments_before_any_cuda_call(lib):
+    from paper_2507_12144_gb300 import _abi
+    o = _abi.sht_batch_opts()
+    lib.sht_batch_opts_default(ctypes.byref(o))
+    assert o.direction == 0 and o.tune == 1 and o.profile == 0 and not o.tune_cache
+    h = ctypes.c_void_p()
+    items = (_abi.sht_batch_item * 9)()
+    assert lib.sht_batch_create(ctypes.byref(h), items, 0, ctypes.byref(o), None) == 1
+    assert lib.sht_batch_create(ctypes.byref(h), items, 9, ctypes.byref(o), None) == 1
+    assert lib.sht_batch_create(ctypes.byref(h), items, 1, ctypes.byref(o), None) == 1  # NULL plan
+    assert b"plan" in lib.sht_last_error_message()
+    o.direction = 2
+    assert lib.sht_batch_create(ctypes.byref(h), items, 1, ctypes.byref(o), None) == 1
+    assert b"direction" in lib.sht_last_error_message()
+    o.direction = 0
+    o.reserved[0] = 1
+    assert lib.sht_batch_create(ctypes.byref(h), items, 1, ctypes.byref(o), None) == 1
+    assert lib.sht_batch_run(None, None) == 1
+    assert lib.sht_batch_destroy(None) == 1
+    assert lib.sht_batch_stage_count(None) == 0
+    assert lib.sht_batch_stage_name(None, 0) == b"?"
