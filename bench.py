@@ -12,6 +12,8 @@ the dominant kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--table-source S]
   python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+  python bench.py --workload batched ... # forward + inverse SHT of an uneven
+                                         # mix of four grids, one CUDA graph each
 
 Multi-GPU runs (torchrun) are independent replicas: the path has no
 exchange step, so every rank transforms its own batch (weak scaling).
@@ -40,6 +42,11 @@ UNIT = "field-transforms/s"
 NLAT, NLON, GRID, LMAX, MMAX = 721, 1440, "equiangular_cc", 720, 720
 MEMBERS, CHANNELS = 1, 72
 FALLBACK_HBM_GBS = 6800.0
+
+# batched workload: (nlat, nlon, lmax = mmax, fields) on equiangular CC grids
+BATCH_MIX = [(91, 180, 90, 32 * 256), (181, 360, 180, 16 * 128), (361, 720, 360, 4 * 256), (721, 1440, 720, 72)]
+BATCH_METRIC = ("batched SHT+ISHT field-transforms/s over 91x180 (32x256), 181x360 (16x128), "
+                "361x720 (4x256), 721x1440 (1x72), lmax = nlat-1")
 
 
 def workload_config(precision: str, table_source: str = "streamed") -> dict:
@@ -279,11 +286,80 @@ class OracleSampler:
                 f"counts {rows}/721 of a field-transform per field")
 
 
+def batched_config(precision: str, table_source: str) -> dict:
+    return {
+        "workload": "batched forward + inverse SHT (no filter) of an uneven grid mix in one CUDA graph per "
+                    "direction: equiangular Clenshaw-Curtis 91x180 (32 members x 256 channels), 181x360 "
+                    "(16 x 128), 361x720 (4 x 256), 721x1440 (1 x 72), lmax = mmax = nlat - 1",
+        "grids": [f"{a}x{b}" for a, b, _, _ in BATCH_MIX], "fields": [n for *_, n in BATCH_MIX],
+        "precision": precision, "legendre_table": table_source if precision != "fp32" else "streamed",
+        "spectrum": "(l+1)^-3 angular power, seeded",
+        "l2": "inputs larger than L2: 2.43 GB of fields per direction",
+        "parallelism": "replicas",
+    }
+
+
+def batched_bytes(stage: str) -> float:
+    """Algorithmic bytes of one launch of a batched stage over the whole mix."""
+    tot = 0.0
+    for nlat, nlon, L, n in BATCH_MIX:
+        tri = n_tri(L, L) * 8.0
+        four = nlat * L * 8.0
+        grid = nlat * nlon * 4.0
+        upper = (L * L - n_tri(L, L)) * 8.0
+        per = {"r2c": grid + four, "c2r": four + grid, "leg_fwd": four + tri, "leg_inv": tri + four,
+               "zero": upper, "pack": tri + tri, "finalize": tri + tri + upper}.get(stage, float("nan"))
+        tot += n * per
+    return tot
+
+
+def n_tri(L, M):
+    return sum(L - m for m in range(M))
+
+
+class BatchedOracleSampler:
+    """The FP64 oracle on a scaled-down copy of the batched mix: 64, 16 and 4
+    fields of the three smaller grids and latitude rows [0, R) of one
+    721 x 1440 field, forward and inverse."""
+
+    PLAN = [(91, 180, 90, 64), (181, 360, 180, 16), (361, 720, 360, 4)]
+
+    def __init__(self, seed: int = 5):
+        import oracle
+        from paper_2507_12144_gb300 import inputs
+        oracle.build()
+        self.oracle = oracle
+        self.cores = oracle.num_threads()
+        g = inputs.rng(seed)
+        self.x = [g.standard_normal((n, a, b)) for a, b, _, n in self.PLAN]
+        self.c = [inputs.spectral_coeffs(seed + 1 + i, (n,), L, L) for i, (_, _, L, n) in enumerate(self.PLAN)]
+        self.x721 = g.standard_normal((1, 721, 1440))
+        self.c721 = inputs.spectral_coeffs(seed + 9, (1,), 720, 720)
+        self.rows = 24
+
+    def step(self):
+        o = self.oracle
+        for (a, b, L, _), x, c in zip(self.PLAN, self.x, self.c):
+            o.sht_forward(x, a, b, "equiangular_cc", L, L)
+            o.sht_inverse(c, a, b, "equiangular_cc", L, L)
+        o.sht_forward_rows(self.x721, 721, 1440, "equiangular_cc", 720, 720, 0, self.rows)
+        o.sht_inverse_rows(self.c721, 721, 1440, "equiangular_cc", 720, 720, 0, self.rows)
+
+    def fields_per_step(self) -> float:
+        return sum(n for *_, n in self.PLAN) + self.rows / 721
+
+    def describe(self) -> str:
+        return ("64 fields of 91x180, 16 of 181x360, 4 of 361x720 and latitude rows [0,24) of one 721x1440 "
+                "field, forward and inverse")
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args.gpus)
     if rank != 0:
         barrier(world)
         return 0
+    if args.workload == "batched":
+        return run_reference_batched(args, world)
     s = OracleSampler()
     budget = args.ref_seconds / max(1, args.steps + args.warmup)
     rows = s.calibrate(min(budget, 20.0))
@@ -307,6 +383,38 @@ def run_reference(args):
     sys.stdout.flush()
     barrier(world)
     return 0
+
+
+def run_reference_batched(args, world):
+    s = BatchedOracleSampler()
+    for _ in range(args.warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    value = args.steps * s.fields_per_step() / dt
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": batched_config("fp64 oracle", "streamed"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.cores, "kind": "oracle", "sample": s.describe()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    barrier(world)
+    return 0
+
+
+def cpu_baseline_batched() -> dict:
+    s = BatchedOracleSampler()
+    t0 = time.perf_counter()
+    s.step()
+    dt = time.perf_counter() - t0
+    return {"value": s.fields_per_step() / dt, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+            "sample": s.describe() + f"; one pass, {dt:.1f} s"}
 
 
 def cpu_baseline_line(target_s: float = 15.0) -> dict:
@@ -440,12 +548,136 @@ def run_gpu(args):
     return 0
 
 
+def run_gpu_batched(args):
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+
+    import paper_2507_12144_gb300 as shtgb
+    from paper_2507_12144_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    plans, fields, coefs, outs = [], [], [], []
+    for k, (nlat, nlon, L, n) in enumerate(BATCH_MIX):
+        plan = shtgb.Plan(nlat, nlon, "equiangular_cc", L, L, precision=args.precision, device=dev, max_batch=n,
+                          table_source=args.table_source)
+        # seeded (l+1)^-3 coefficients: 16 base draws under random scales, synthesised on the GPU
+        nb = min(n, 16)
+        base = torch.from_numpy(inputs.spectral_coeffs(50 + 10 * rank + k, (nb,), L, L).astype(np.complex64))
+        g = torch.Generator(device=dev).manual_seed(60 + k)
+        scale = torch.rand((n, 1, 1), generator=g, device=dev) + 0.5
+        c = base.to(dev)[torch.arange(n, device=dev) % nb] * scale
+        x = shtgb.sht_inverse(plan, c.contiguous())
+        plans.append(plan)
+        fields.append(x)
+        coefs.append(torch.empty((n, L, L), dtype=torch.complex64, device=dev))
+        outs.append(torch.empty_like(x))
+        del c
+    total = sum(n for *_, n in BATCH_MIX)
+    cache = os.path.join(ROOT, "_build_tune", "batch_tune.txt")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    fb = shtgb.Batch(list(zip(plans, fields, coefs)), "forward", tune_cache=cache, profile=True)
+    ib = shtgb.Batch(list(zip(plans, coefs, outs)), "inverse", tune_cache=cache, profile=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fb.run()
+        ib.run()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    fb.profile_begin(args.steps + 1)
+    ib.profile_begin(args.steps + 1)
+    clocks = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    ms_step = ms_total / args.steps
+    value = world * total / (ms_step * 1e-3)
+    pf, pi = fb.profile_collect(), ib.profile_collect()
+    stages = {}
+    for prof in (pf, pi):
+        runs = prof.pop("_runs")
+        for k, v in prof.items():
+            stages[k] = (runs, v)
+    dom = max(stages, key=lambda k: stages[k][1])
+    runs, dom_ms = stages[dom]
+    per_launch_s = dom_ms / max(runs, 1) * 1e-3
+    alg = batched_bytes(dom)
+    peak, peak_kind = load_peaks()
+    achieved = alg / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth", "traffic": None,
+                "algorithmic_bytes_per_launch": alg, "kernel_ms_per_launch": per_launch_s * 1e3,
+                "share_of_step": dom_ms / ms_total if world == 1 else None}
+    breakdown = {k: {"launches": r, "ms_per_launch": v / max(r, 1), "share": v / ms_total}
+                 for k, (r, v) in stages.items()}
+
+    # end to end: host fields in, host fields out, through the same batches
+    e2e_steps = max(3, min(args.steps, 5))
+    host_in = [f.cpu().pin_memory() for f in fields]
+    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for h, d in zip(host_in, fields):
+            d.copy_(h, non_blocking=True)
+        step()
+        for h, d in zip(host_out, outs):
+            h.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    nbytes = int(sum(f.numel() * 4 for f in fields))
+    if rank == 0:
+        line = {
+            "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+            "data": "synthetic: seeded (l+1)^-3 spectra synthesised on the GPU",
+            "config": batched_config(args.precision, args.table_source),
+            "roofline": roofline, "kernels": breakdown, "gpu_launches": 6 * args.steps,
+            "tuned": {"forward": fb.describe(), "inverse": ib.describe()},
+            "e2e": {"value": world * total * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+            "clocks": clk,
+            "cpu_baseline": cpu_baseline_batched() if world == 1 and not args.no_cpu_baseline else None,
+        }
+        print(json.dumps(line))
+        sys.stdout.flush()
+    fb.close()
+    ib.close()
+    for p in plans:
+        p.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["block", "batched"], default="block",
+                    help="block: SHT -> filter -> ISHT at 721x1440 (the headline); batched: forward + inverse "
+                         "SHT of the uneven four-grid mix")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
     ap.add_argument("--table-source", choices=["streamed", "recurrence"], default="streamed",
                     help="Legendre table of the tensor-core precisions: precomputed and streamed, or "
@@ -460,6 +692,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_gpu_batched(args)
     return run_gpu(args)
 
 

@@ -241,8 +241,10 @@ sht_status_t sht_forward_static_scratch(sht_plan_t plan, const float *x,
  * fixed input and output buffers, and records the whole transform of all
  * items as one CUDA graph: one grouped longitude launch, one persistent
  * Legendre launch over the tiles of every item, one grouped epilogue launch
- * (zero fill for the forward; the coefficient repacking precedes the
- * inverse on the tensor-core precisions).  sht_batch_run replays it.
+ * (for the forward: the transpose of the tensor-core rows into the API
+ * layout, or the zero fill of the FP32 path; before the inverse on the
+ * tensor-core precisions: the transpose into the internal rows).
+ * sht_batch_run replays it.
  *
  * Items:
  *   plan   a plan, at most once per batch; all plans of a batch share the
@@ -342,7 +344,8 @@ typedef enum {
   SHT_KERNEL_C2R = 6,        /* longitude synthesis (inverse FFT)         */
   SHT_KERNEL_PACK = 7,       /* API coefficients -> internal bf16 rows    */
   SHT_KERNEL_FILTER_PREP = 8, /* real bf16 form of the filter weights    */
-  SHT_KERNEL_COUNT = 9
+  SHT_KERNEL_FINALIZE = 9,   /* FP32 l-major rows -> API xhat (+ zeros)   */
+  SHT_KERNEL_COUNT = 10
 } sht_kernel_t;
 
 /* Start recording (capacity >= 1 launches); creates the events on the

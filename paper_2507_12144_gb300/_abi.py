@@ -18,7 +18,7 @@ STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3: "S
 GRIDS = {"gauss": 0, "equiangular_cc": 1, "equiangular_trapz": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "split_bf16": 2}
 TABLE_SOURCES = {"streamed": 0, "recurrence": 1}
-KERNEL_COUNT = 9
+KERNEL_COUNT = 10
 
 
 class sht_plan_opts(ctypes.Structure):

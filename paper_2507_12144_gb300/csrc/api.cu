@@ -182,8 +182,7 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_x2l);
   cudaFree(p->d_roff);
   cudaFree(p->d_soff);
-  cudaFree(p->d_x_hi);
-  cudaFree(p->d_x_lo);
+  cudaFree(p->d_x_hi);  // d_x_lo lies inside the same block
   cudaFree(p->d_wr_hi);
   cudaFree(p->d_wr_lo);
   cudaFree(p->d_ftiles);
@@ -242,6 +241,9 @@ bool is_tc(const sht_plan_s *p) { return p->precision != SHT_PREC_FP32; }
 
 __nv_bfloat16 *f_hi(sht_plan_s *p) { return reinterpret_cast<__nv_bfloat16 *>(p->d_work); }
 __nv_bfloat16 *f_lo(sht_plan_s *p) { return f_hi(p) + (size_t)p->M * 2 * p->Kh * p->ldcb; }
+// FP32 l-major rows of the forward into the API layout (the fused block's
+// bf16 row buffers, used as one FP32 array).
+float *rows_f32(sht_plan_s *p) { return reinterpret_cast<float *>(p->d_x_hi); }
 // The lo half of the data exists only for split precision.
 __nv_bfloat16 *data_lo(sht_plan_s *p, __nv_bfloat16 *lo) { return p->precision == SHT_PREC_SPLIT_BF16 ? lo : nullptr; }
 
@@ -286,12 +288,32 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
       });
       if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
       e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
-        if (rows_out)
-          return launch_leg_fwd_tc(p->tc, p->d_fwd_tiles, p->n_fwd_tiles, nullptr, rows_out->hi, rows_out->lo,
-                                   rows_out->ldo, rows_out->cin, rows_out->kx, nb, st);
-        return launch_leg_fwd_tc(p->tc, p->d_fwd_tiles, p->n_fwd_tiles, xhat + b0 * LM, nullptr, nullptr, 0, 1, 0,
-                                 nb, st);
+        TcLegItem it{};
+        it.T = &p->tc;
+        it.tiles = p->d_fwd_tiles;
+        it.ntiles = p->n_fwd_tiles;
+        it.B = nb;
+        if (rows_out) {
+          it.rows_hi = rows_out->hi;
+          it.rows_lo = rows_out->lo;
+          it.ldo = rows_out->ldo;
+          it.cin = rows_out->cin;
+          it.kx = rows_out->kx;
+        } else {
+          // FP32 l-major rows, turned into the API layout below
+          it.rowsf = rows_f32(p);
+          it.ldr = p->ldx;
+        }
+        return launch_leg_tc_group(0, &it, 1, TcLaunch{}, st);
       });
+      if (e == cudaSuccess && !rows_out) {
+        e = traced(p, SHT_KERNEL_FINALIZE, st, [&] {
+          RowsItem r{rows_f32(p), xhat + b0 * LM, nullptr, nullptr, nullptr, p->L, p->M, nb, p->ldx};
+          return launch_rows_transpose(false, &r, 1, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "coefficient transpose launch");
+        continue;
+      }
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward Legendre launch");
     if (zero_upper && !rows_out) {
@@ -331,8 +353,9 @@ sht_status_t synthesis(sht_plan_s *p, const float2 *yhat, float *y, int64_t B, c
     float *yb = y + b0 * p->nlat * (int64_t)p->nlon;
     if (is_tc(p)) {
       cudaError_t e = traced(p, SHT_KERNEL_PACK, st, [&] {
-        return launch_pack_rows(yhat + b0 * LM, p->d_s_hi, data_lo(p, p->d_s_lo), p->d_soff, p->L, p->M, p->ldcb, nb,
-                                st);
+        RowsItem r{nullptr, const_cast<float2 *>(yhat + b0 * LM), p->d_s_hi, data_lo(p, p->d_s_lo), p->d_soff,
+                   p->L, p->M, nb, p->ldcb};
+        return launch_rows_transpose(true, &r, 1, st);
       });
       if (e != cudaSuccess) return cuda_fail(e, "coefficient repack launch");
       SHT_TRY(synthesis_rows(p, yb, nb, st, adjoint));
@@ -715,13 +738,14 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     for (int l = 0; l < lmax; l++)
       for (int m0 = 0; m0 < std::min(l + 1, mmax); m0 += 128) ftl.push_back(make_int2(l, m0));
     p->n_ftiles = (int)ftl.size();
-    if ((e = dev_alloc((void **)&p->d_x_hi, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
-    if ((e = dev_alloc((void **)&p->d_x_lo, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    // one block: the bf16 hi and lo rows of the fused block, or the FP32
+    // rows (row stride ldx floats) of the forward into the API layout
+    if ((e = dev_alloc((void **)&p->d_x_hi, 2 * xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    p->d_x_lo = p->d_x_hi + (size_t)lmax * mmax * p->ldx;
     if ((e = dev_alloc((void **)&p->d_wr_hi, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_wr_lo, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = upload((int2 **)&p->d_ftiles, ftl)) != cudaSuccess) return bail(e, "tile upload");
-    if ((e = cudaMemset(p->d_x_hi, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
-    if ((e = cudaMemset(p->d_x_lo, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    if ((e = cudaMemset(p->d_x_hi, 0, 2 * xbytes)) != cudaSuccess) return bail(e, "workspace memset");
     extra = 2 * sbytes + 2 * xbytes + 2 * wbytes;
     TcPlanView &T = p->tc;
     if (!(tc_encode_2d(&T.x_hi, p->d_x_hi, p->ldx, (int64_t)lmax * mmax, 64, 128) &&
@@ -983,7 +1007,7 @@ sht_status_t sht_profile_end(sht_plan_t p) {
 
 const char *sht_kernel_name(int k) {
   static const char *names[SHT_KERNEL_COUNT] = {"r2c", "leg_fwd", "zero_upper", "filter", "filter_dw", "leg_inv",
-                                                "c2r", "pack", "filter_prep"};
+                                                "c2r", "pack", "filter_prep", "finalize"};
   return (k >= 0 && k < SHT_KERNEL_COUNT) ? names[k] : "?";
 }
 

@@ -184,7 +184,8 @@ cudaError_t stage_legendre(sht_batch_s *b, const Shape &sh, cudaStream_t st) {
       q.B = (int)b->items[i].count;
       q.Nt = column_tile(q.B, sh.nt_cap);
       if (!inverse) {
-        q.xhat = static_cast<float2 *>(b->items[i].out);
+        q.rowsf = reinterpret_cast<float *>(p->d_x_hi);
+        q.ldr = p->ldx;
         q.cin = 1;
       } else {
         q.Gw = p->d_work;
@@ -234,19 +235,31 @@ cudaError_t stage_zero(sht_batch_s *b, cudaStream_t st) {
 
 cudaError_t stage_pack(sht_batch_s *b, cudaStream_t st) {
   const int n = (int)b->items.size();
-  PackItem it[kMaxItems];
+  RowsItem it[kMaxItems];
   for (int i = 0; i < n; i++) {
     sht_plan_s *p = b->plans[i];
-    it[i] = PackItem{static_cast<const float2 *>(b->items[i].in), p->d_s_hi, srow_lo(p), p->d_soff, p->L, p->M,
-                     p->ldcb, (int)b->items[i].count};
+    it[i] = RowsItem{nullptr, static_cast<float2 *>(const_cast<void *>(b->items[i].in)), p->d_s_hi, srow_lo(p),
+                     p->d_soff, p->L, p->M, (int)b->items[i].count, p->ldcb};
   }
-  return launch_pack_rows_group(it, n, st);
+  return launch_rows_transpose(true, it, n, st);
+}
+
+// FP32 rows of the tensor-core forward -> API layout, zeros included.
+cudaError_t stage_finalize(sht_batch_s *b, cudaStream_t st) {
+  const int n = (int)b->items.size();
+  RowsItem it[kMaxItems];
+  for (int i = 0; i < n; i++) {
+    sht_plan_s *p = b->plans[i];
+    it[i] = RowsItem{reinterpret_cast<const float *>(p->d_x_hi), static_cast<float2 *>(b->items[i].out), nullptr,
+                     nullptr, nullptr, p->L, p->M, (int)b->items[i].count, p->ldx};
+  }
+  return launch_rows_transpose(false, it, n, st);
 }
 
 void stage_names(sht_batch_s *b) {
   b->stages.clear();
   if (b->direction == SHT_BATCH_FORWARD) {
-    b->stages = {"r2c", "leg_fwd", "zero"};
+    b->stages = {"r2c", "leg_fwd", b->tc ? "finalize" : "zero"};
   } else if (b->tc) {
     b->stages = {"pack", "leg_inv", "c2r"};
   } else {
@@ -259,6 +272,7 @@ cudaError_t run_stage(sht_batch_s *b, int k, const Shape &sh, cudaStream_t st) {
   if (!strcmp(name, "r2c")) return stage_r2c(b, st);
   if (!strcmp(name, "leg_fwd") || !strcmp(name, "leg_inv")) return stage_legendre(b, sh, st);
   if (!strcmp(name, "zero")) return stage_zero(b, st);
+  if (!strcmp(name, "finalize")) return stage_finalize(b, st);
   if (!strcmp(name, "pack")) return stage_pack(b, st);
   return stage_c2r(b, st);
 }

@@ -104,10 +104,14 @@ struct FiltTile {
 // Destination of the forward contraction: the API layout xhat[b][l][m], or
 // l-major bf16 rows (row l M + m, member b's channel ch at column
 // b kx + 2 ch + {re, im}) for the tensor-core filter.
+// Or FP32 l-major rows (row l M + m, field f at columns 2 f + {re, im},
+// row stride ldr floats), which a transpose kernel turns into xhat.
 struct FwdOut {
   float2 *xhat;
   __nv_bfloat16 *rows_hi, *rows_lo;
   int ldo, cin, kx;
+  float *rowsf;
+  int ldr;
 };
 
 // Recurrence seeds of the on-chip Legendre table: for order m, parity p,
@@ -347,7 +351,17 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       float v[16];
       tmem_ld16(tl + (uint32_t)(j * 16), v);
       if (!row_ok) continue;
-      if (out.rows_hi) {
+      if (out.rowsf) {
+        float *dst = out.rowsf + ((int64_t)l * M + ti.m) * out.ldr;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int c = ti.c0 + j * 16 + 4 * u;
+          if (c + 4 <= 2 * B)
+            *reinterpret_cast<float4 *>(dst + c) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+          else if (c + 2 <= 2 * B)
+            *reinterpret_cast<float2 *>(dst + c) = make_float2(v[4 * u], v[4 * u + 1]);
+        }
+      } else if (out.rows_hi) {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           const int f = (ti.c0 + j * 16) / 2 + 4 * h;  // first of 4 fields
@@ -752,6 +766,87 @@ __global__ void pack_rows_grouped(const __grid_constant__ PackGroup g) {
                  g.ldb[s], g.B[s]);
 }
 
+// Transposes between the API layout xhat[b][l][m] (complex64) and the
+// l-major forms of the tensor-core path, through 32 x 32 shared tiles so
+// that both sides are read and written in contiguous runs.  One CTA (32 x 8
+// threads) per (32 orders m, degree l, 32 fields b).
+struct RowsT {
+  const float *rows;   // finalize: FP32 rows [l M + m][ldr]
+  float2 *xhat;        // finalize: destination; pack: source
+  __nv_bfloat16 *shi, *slo;  // pack: split rows [soff[2m + p] + i][ldb]
+  const int *soff;
+  int L, M, B, ld;     // ld = ldr (finalize) or ldb (pack)
+};
+
+// xhat[b][l][m] = rows[l M + m][2b, 2b + 1] for m <= l, zero for m > l.
+__device__ __forceinline__ void finalize_tile(const RowsT &a, int mt, int l, int bt, float2 (*T)[33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int m0 = mt * 32, b0 = bt * 32;
+  for (int mm = ty; mm < 32; mm += 8) {
+    const int m = m0 + mm, b = b0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (m <= l && m < a.M && b < a.B)
+      v = *reinterpret_cast<const float2 *>(a.rows + ((int64_t)l * a.M + m) * a.ld + 2 * b);
+    T[mm][tx] = v;
+  }
+  __syncthreads();
+  for (int bb = ty; bb < 32; bb += 8) {
+    const int b = b0 + bb, m = m0 + tx;
+    if (b < a.B && m < a.M) a.xhat[((int64_t)b * a.L + l) * a.M + m] = T[tx][bb];
+  }
+}
+
+// split rows S[soff[2m + p] + i][2b, 2b + 1] = hi/lo of xhat[b][l][m], m <= l.
+__device__ __forceinline__ void pack_tile(const RowsT &a, int mt, int l, int bt, float2 (*T)[33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int m0 = mt * 32, b0 = bt * 32;
+  for (int bb = ty; bb < 32; bb += 8) {
+    const int b = b0 + bb, m = m0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (b < a.B && m < a.M && m <= l) v = a.xhat[((int64_t)b * a.L + l) * a.M + m];
+    T[tx][bb] = v;
+  }
+  __syncthreads();
+  for (int mm = ty; mm < 32; mm += 8) {
+    const int m = m0 + mm, b = b0 + tx;
+    if (m > l || m >= a.M || b >= a.B) continue;
+    const int d = l - m;
+    const int64_t o = (int64_t)(a.soff[2 * m + (d & 1)] + (d >> 1)) * a.ld + 2 * b;
+    const float2 v = T[mm][tx];
+    __nv_bfloat16 hr, lr, hi_, li;
+    split_bf16(v.x, hr, lr);
+    split_bf16(v.y, hi_, li);
+    *reinterpret_cast<uint32_t *>(a.shi + o) = pack_bf16x2(hr, hi_);
+    if (a.slo) *reinterpret_cast<uint32_t *>(a.slo + o) = pack_bf16x2(lr, li);
+  }
+}
+
+// Several problems per launch: CTA j belongs to problem s with blk0[s] <= j
+// < blk0[s + 1]; mt, then l, then bt vary slowest.
+struct RowsTGroup {
+  RowsT seg[kMaxSeg];
+  int blk0[kMaxSeg + 1];
+  int nseg;
+};
+
+template <bool kPack>
+__global__ void __launch_bounds__(256) rows_transpose_kernel(const __grid_constant__ RowsTGroup g) {
+  __shared__ float2 T[32][33];
+  int s = 0;
+  while (s + 1 < g.nseg && (int)blockIdx.x >= g.blk0[s + 1]) s++;
+  const RowsT &a = g.seg[s];
+  const int mtiles = (a.M + 31) / 32;
+  int local = blockIdx.x - g.blk0[s];
+  const int mt = local % mtiles;
+  local /= mtiles;
+  const int l = local % a.L;
+  const int bt = local / a.L;
+  if (kPack)
+    pack_tile(a, mt, l, bt, T);
+  else
+    finalize_tile(a, mt, l, bt, T);
+}
+
 // WR[l][n][k] (bf16 hi/lo), n < nwr rows, k < kx columns, from W[l][o][i]:
 // n = 2 o + a, k = 2 i + c: (a, c) = (0, 0) Re W, (0, 1) -Im W, (1, 0) Im W,
 // (1, 1) Re W; zero outside 2 Cout x 2 Cin.
@@ -883,10 +978,11 @@ int sm_count() {
   return n;
 }
 
-// Column tiling of the 2B real columns: tiles of at most 256, multiple of 16.
-void column_tiles(int B, int &Nt, int &nct) {
+// Column tiling of the 2B real columns: balanced tiles of at most `cap`
+// (a multiple of 16) columns, each a multiple of 16.
+void column_tiles(int B, int cap, int &Nt, int &nct) {
   const int C2 = 2 * B;
-  nct = (C2 + 255) / 256;
+  nct = (C2 + cap - 1) / cap;
   Nt = ((C2 + nct - 1) / nct + 15) / 16 * 16;
 }
 
@@ -903,13 +999,13 @@ cudaError_t start_persistent(unsigned grid, size_t smem, const TcParams &P, cuda
 // the generators' area; at most 227 KB with the static barriers.
 constexpr size_t kSmemLimit = 227 * 1024 - 256;
 
+// Shared memory beyond the stage ring (the generators' area); fills the
+// generators' layout fields of P.  SIZE_MAX when the problems cannot be
+// served.
 template <int kMode>
-cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch &cfg, cudaStream_t st) {
-  if (P.ntiles <= 0) return cudaSuccess;
-  gen = gen && kMode != kFilt;
-  const size_t sb = stage_bytes(kMode, split, P.Nmax);
+size_t extra_smem(bool gen, TcParams &P) {
   size_t cbytes = 0;
-  if (gen) {
+  if (gen && kMode != kFilt) {
     // generator shared memory: coefficients of one tile, x^2 of every
     // problem's latitudes, the seed ring
     int rows_max = 0;
@@ -920,15 +1016,31 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
       P.xtot += P.seg[s].Kh;
     }
     P.ncmax = std::max(2 * kKc + 4, kKc * ((rows_max + kKc - 1) / kKc) + 4);
-    if (P.ncmax > 256 * kCoefPerThread) return cudaErrorInvalidValue;
+    if (P.ncmax > 256 * kCoefPerThread) return SIZE_MAX;
     cbytes = sizeof(float4) * (size_t)P.ncmax + sizeof(float2) * (size_t)((P.xtot + 1) & ~1) +
              sizeof(Seed) * 256 * kSeedAhead;
   }
-  if (1024 + 2 * sb + cbytes > kSmemLimit) return cudaErrorInvalidValue;
-  int stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 1024 - cbytes) / sb);
+  return (cbytes + 15) / 16 * 16;
+}
+
+// Whether two pipeline stages and the extra areas fit one CTA.
+template <int kMode>
+bool persistent_fits(bool split, bool gen, TcParams &P) {
+  const size_t extra = extra_smem<kMode>(gen, P);
+  return extra != SIZE_MAX && 1024 + 2 * (size_t)stage_bytes(kMode, split, P.Nmax) + extra <= kSmemLimit;
+}
+
+template <int kMode>
+cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch &cfg, cudaStream_t st) {
+  if (P.ntiles <= 0) return cudaSuccess;
+  gen = gen && kMode != kFilt;
+  const size_t sb = stage_bytes(kMode, split, P.Nmax);
+  const size_t extra = extra_smem<kMode>(gen, P);
+  if (extra == SIZE_MAX || 1024 + 2 * sb + extra > kSmemLimit) return cudaErrorInvalidValue;
+  int stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 1024 - extra) / sb);
   if (cfg.stages >= 2) stages = std::min(stages, cfg.stages);
   P.stages = stages;
-  const size_t smem = 1024 + (size_t)stages * sb + cbytes;
+  const size_t smem = 1024 + (size_t)stages * sb + extra;
   const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
   if constexpr (kMode == kFilt) {
@@ -988,58 +1100,64 @@ cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double 
 cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, const TcLaunch &cfg, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSeg) return cudaErrorInvalidValue;
-  TcParams P{};
   const bool split = items[0].T->split, gen = items[0].T->gen;
-  P.err = items[0].T->err;
-  int nseg = 0, ntiles = 0;
   for (int i = 0; i < n; i++) {
-    const TcLegItem &it = items[i];
-    const TcPlanView &T = *it.T;
-    if (T.split != split || T.gen != gen) return cudaErrorInvalidValue;
-    if (it.ntiles <= 0 || it.B <= 0) continue;
-    SegArgs &g = P.seg[nseg];
-    g.L = T.L;
-    g.M = T.M;
-    g.Kh = T.Kh;
-    g.B = it.B;
-    if (it.Nt > 0) {
-      if (it.Nt % 16 != 0 || it.Nt > 256) return cudaErrorInvalidValue;
-      g.Nt = it.Nt;
-      g.nct = (2 * it.B + it.Nt - 1) / it.Nt;
-    } else {
-      column_tiles(it.B, g.Nt, g.nct);
-    }
-    g.tile0 = ntiles;
-    g.tiles = it.tiles;
-    g.fout = FwdOut{it.xhat, it.rows_hi, it.rows_lo, it.ldo, it.cin > 0 ? it.cin : 1, it.kx};
-    g.Gw = it.Gw;
-    g.ldc = it.ldc;
-    g.seeds = reinterpret_cast<const Seed *>(T.seeds);
-    g.coef = T.coef;
-    g.x2h = T.x2h;
-    g.x2l = T.x2l;
-    g.NB = T.NB;
-    g.ldC = T.ldC;
-    SegMaps &mp = P.maps[nseg];
-    if (!inverse) {
-      mp.a_hi = T.tab_fwd_hi;
-      mp.a_lo = T.tab_fwd_lo;
-      mp.b_hi = T.f_hi;
-      mp.b_lo = split ? T.f_lo : T.f_hi;
-    } else {
-      mp.a_hi = T.tab_inv_hi;
-      mp.a_lo = T.tab_inv_lo;
-      mp.b_hi = T.s_hi;
-      mp.b_lo = split ? T.s_lo : T.s_hi;
-    }
-    P.Nmax = std::max(P.Nmax, g.Nt);
-    ntiles += it.ntiles * g.nct;
-    nseg++;
+    if (items[i].T->split != split || items[i].T->gen != gen) return cudaErrorInvalidValue;
+    if (items[i].Nt < 0 || items[i].Nt % 16 != 0 || items[i].Nt > 256) return cudaErrorInvalidValue;
   }
-  if (nseg == 0) return cudaSuccess;
-  P.nseg = nseg;
-  P.ntiles = ntiles;
-  return inverse ? launch_persistent<kInv>(split, gen, P, cfg, st) : launch_persistent<kFwd>(split, gen, P, cfg, st);
+  // column tiles: the requested widths (or 256), narrowed until two
+  // pipeline stages fit in shared memory
+  const int caps[4] = {256, 192, 128, 64};
+  for (int cap : caps) {
+    TcParams P{};
+    P.err = items[0].T->err;
+    int nseg = 0, ntiles = 0;
+    for (int i = 0; i < n; i++) {
+      const TcLegItem &it = items[i];
+      const TcPlanView &T = *it.T;
+      if (it.ntiles <= 0 || it.B <= 0) continue;
+      SegArgs &g = P.seg[nseg];
+      g.L = T.L;
+      g.M = T.M;
+      g.Kh = T.Kh;
+      g.B = it.B;
+      column_tiles(it.B, std::min(it.Nt > 0 ? it.Nt : 256, cap), g.Nt, g.nct);
+      g.tile0 = ntiles;
+      g.tiles = it.tiles;
+      g.fout = FwdOut{it.xhat, it.rows_hi, it.rows_lo, it.ldo, it.cin > 0 ? it.cin : 1, it.kx, it.rowsf, it.ldr};
+      g.Gw = it.Gw;
+      g.ldc = it.ldc;
+      g.seeds = reinterpret_cast<const Seed *>(T.seeds);
+      g.coef = T.coef;
+      g.x2h = T.x2h;
+      g.x2l = T.x2l;
+      g.NB = T.NB;
+      g.ldC = T.ldC;
+      SegMaps &mp = P.maps[nseg];
+      if (!inverse) {
+        mp.a_hi = T.tab_fwd_hi;
+        mp.a_lo = T.tab_fwd_lo;
+        mp.b_hi = T.f_hi;
+        mp.b_lo = split ? T.f_lo : T.f_hi;
+      } else {
+        mp.a_hi = T.tab_inv_hi;
+        mp.a_lo = T.tab_inv_lo;
+        mp.b_hi = T.s_hi;
+        mp.b_lo = split ? T.s_lo : T.s_hi;
+      }
+      P.Nmax = std::max(P.Nmax, g.Nt);
+      ntiles += it.ntiles * g.nct;
+      nseg++;
+    }
+    if (nseg == 0) return cudaSuccess;
+    P.nseg = nseg;
+    P.ntiles = ntiles;
+    const bool fits = inverse ? persistent_fits<kInv>(split, gen, P) : persistent_fits<kFwd>(split, gen, P);
+    if (!fits) continue;
+    return inverse ? launch_persistent<kInv>(split, gen, P, cfg, st)
+                   : launch_persistent<kFwd>(split, gen, P, cfg, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
@@ -1106,6 +1224,29 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.maps[0].b_hi = tw_hi;
   P.maps[0].b_lo = tw_lo;
   return launch_persistent<kFilt>(T.split, false, P, TcLaunch{}, st);
+}
+
+cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kMaxSeg) return cudaErrorInvalidValue;
+  RowsTGroup g{};
+  int64_t blk = 0;
+  for (int i = 0; i < n; i++) {
+    const RowsItem &it = items[i];
+    if (it.B <= 0) continue;
+    const int s = g.nseg++;
+    g.seg[s] = RowsT{it.rows, it.xhat, it.shi, it.slo, it.soff, it.L, it.M, it.B, it.ld};
+    g.blk0[s] = (int)blk;
+    blk += (int64_t)((it.M + 31) / 32) * it.L * ((it.B + 31) / 32);
+  }
+  g.blk0[g.nseg] = (int)blk;
+  if (blk == 0) return cudaSuccess;
+  if (blk > 0x7fffffff) return cudaErrorInvalidValue;
+  if (pack)
+    rows_transpose_kernel<true><<<(unsigned)blk, 256, 0, st>>>(g);
+  else
+    rows_transpose_kernel<false><<<(unsigned)blk, 256, 0, st>>>(g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_rows_group(const PackItem *items, int n, cudaStream_t st) {

@@ -103,6 +103,8 @@ struct TcLegItem {
   float2 *xhat;
   __nv_bfloat16 *rows_hi, *rows_lo;
   int ldo, cin, kx;
+  float *rowsf;  // FP32 l-major rows (row l M + m, field f at 2f), stride ldr
+  int ldr;
   float *Gw;
   int ldc;
 };
@@ -123,6 +125,19 @@ struct PackItem {
   int L, M, ldb, B;
 };
 cudaError_t launch_pack_rows_group(const PackItem *items, int n, cudaStream_t st);
+// Coalesced transposes of up to 8 problems per launch.
+//   pack = false: xhat[b][l][m] = rows[l M + m][2b + {re, im}] (m <= l; zero
+//                 for m > l), rows FP32 with row stride ld floats;
+//   pack = true:  split bf16 rows S[soff[2m + p] + i][2b + {re, im}] (row
+//                 stride ld) from xhat, m <= l (l = m + p + 2 i).
+struct RowsItem {
+  const float *rows;
+  float2 *xhat;
+  __nv_bfloat16 *shi, *slo;
+  const int *soff;
+  int L, M, B, ld;
+};
+cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaStream_t st);
 cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,
                              int M, int ldb, int B, cudaStream_t st);
 // Longitude analysis writing the folded Fourier workspace as bf16 hi/lo

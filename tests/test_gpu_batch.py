@@ -100,7 +100,7 @@ def test_batched_forward_matches_oracle(shtgb, mix, prec):
         assert err.max() <= TOL[prec], (plan.nlat, err.max())
         assert np.all(out[:, ~triangle_mask(plan.lmax, plan.mmax)] == 0)
         assert np.all(out[..., 0].imag == 0)
-    assert batch.stages == ["r2c", "leg_fwd", "zero"]
+    assert batch.stages == ["r2c", "leg_fwd", "zero" if prec == "fp32" else "finalize"]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -154,7 +154,7 @@ def test_batch_tuning_cache_and_profile(shtgb, tmp_path):
         b2.run()
     prof = b2.profile_collect()
     assert prof["_runs"] == 5
-    assert all(prof[s] > 0 for s in ("r2c", "leg_fwd", "zero"))
+    assert all(prof[s] > 0 for s in ("r2c", "leg_fwd", "finalize"))
     torch.cuda.synchronize()
     for (_, _, y), ref in zip(items, refs):
         assert per_field_spec_err(y.cpu().numpy(), ref).max() <= TOL["split_bf16"]
