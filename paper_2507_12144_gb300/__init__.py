@@ -265,7 +265,7 @@ def spectral_filter_inverse(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> 
 
 
 # ---------------------------------------------------------------------------
-# autograd
+# batched transforms over several grids
 # ---------------------------------------------------------------------------
 
 class Batch:
@@ -359,6 +359,10 @@ class Batch:
         except Exception:
             pass
 
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
 
 class SpectralBlock(torch.autograd.Function):
     """y = ISHT(filter(SHT(x), W)) with hand-written adjoints.

@@ -182,7 +182,8 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_x2l);
   cudaFree(p->d_roff);
   cudaFree(p->d_soff);
-  cudaFree(p->d_x_hi);  // d_x_lo lies inside the same block
+  cudaFree(p->d_x_hi);
+  cudaFree(p->d_x_lo);
   cudaFree(p->d_wr_hi);
   cudaFree(p->d_wr_lo);
   cudaFree(p->d_ftiles);
@@ -241,9 +242,9 @@ bool is_tc(const sht_plan_s *p) { return p->precision != SHT_PREC_FP32; }
 
 __nv_bfloat16 *f_hi(sht_plan_s *p) { return reinterpret_cast<__nv_bfloat16 *>(p->d_work); }
 __nv_bfloat16 *f_lo(sht_plan_s *p) { return f_hi(p) + (size_t)p->M * 2 * p->Kh * p->ldcb; }
-// FP32 l-major rows of the forward into the API layout (the fused block's
-// bf16 row buffers, used as one FP32 array).
-float *rows_f32(sht_plan_s *p) { return reinterpret_cast<float *>(p->d_x_hi); }
+// FP32 l-major rows of the forward into the API layout (in the spec_b
+// workspace, row stride ldr floats).
+float *rows_f32(sht_plan_s *p) { return reinterpret_cast<float *>(p->d_spec_b); }
 // The lo half of the data exists only for split precision.
 __nv_bfloat16 *data_lo(sht_plan_s *p, __nv_bfloat16 *lo) { return p->precision == SHT_PREC_SPLIT_BF16 ? lo : nullptr; }
 
@@ -302,13 +303,13 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
         } else {
           // FP32 l-major rows, turned into the API layout below
           it.rowsf = rows_f32(p);
-          it.ldr = p->ldx;
+          it.ldr = p->ldr;
         }
         return launch_leg_tc_group(0, &it, 1, TcLaunch{}, st);
       });
       if (e == cudaSuccess && !rows_out) {
         e = traced(p, SHT_KERNEL_FINALIZE, st, [&] {
-          RowsItem r{rows_f32(p), xhat + b0 * LM, nullptr, nullptr, nullptr, p->L, p->M, nb, p->ldx};
+          RowsItem r{rows_f32(p), xhat + b0 * LM, nullptr, nullptr, nullptr, p->L, p->M, nb, p->ldr};
           return launch_rows_transpose(false, &r, 1, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "coefficient transpose launch");
@@ -714,7 +715,11 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   p->ldcb = (int)std::max<int64_t>(64, (2 * o.max_batch + 7) / 8 * 8);
   const size_t frow = (size_t)mmax * 2 * p->Kh;
   const size_t work = std::max(sizeof(float) * frow * p->ldc, tc ? 2 * sizeof(__nv_bfloat16) * frow * p->ldcb : 0);
-  const size_t spec = sizeof(float2) * (size_t)o.max_batch * lmax * mmax;
+  // spec_b also holds the FP32 l-major rows of the tensor-core forward into
+  // the API layout: [lmax mmax][ldr] floats, ldr = 2 max_batch rounded to 4
+  p->ldr = (int)((2 * o.max_batch + 3) / 4 * 4);
+  const size_t spec = std::max(sizeof(float2) * (size_t)o.max_batch * lmax * mmax,
+                               tc ? sizeof(float) * (size_t)lmax * mmax * p->ldr : 0);
   size_t extra = 0;
   if ((e = dev_alloc((void **)&p->d_work, work)) != cudaSuccess) return bail(e, "workspace allocation");
   if (!tc && (e = dev_alloc((void **)&p->d_spec_a, spec)) != cudaSuccess) return bail(e, "workspace allocation");
@@ -738,14 +743,14 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     for (int l = 0; l < lmax; l++)
       for (int m0 = 0; m0 < std::min(l + 1, mmax); m0 += 128) ftl.push_back(make_int2(l, m0));
     p->n_ftiles = (int)ftl.size();
-    // one block: the bf16 hi and lo rows of the fused block, or the FP32
-    // rows (row stride ldx floats) of the forward into the API layout
-    if ((e = dev_alloc((void **)&p->d_x_hi, 2 * xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
-    p->d_x_lo = p->d_x_hi + (size_t)lmax * mmax * p->ldx;
+    if ((e = dev_alloc((void **)&p->d_x_hi, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
+    if ((e = dev_alloc((void **)&p->d_x_lo, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_wr_hi, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_wr_lo, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = upload((int2 **)&p->d_ftiles, ftl)) != cudaSuccess) return bail(e, "tile upload");
-    if ((e = cudaMemset(p->d_x_hi, 0, 2 * xbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    // the padding columns stay zero: the filter's K chunks read them
+    if ((e = cudaMemset(p->d_x_hi, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
+    if ((e = cudaMemset(p->d_x_lo, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
     extra = 2 * sbytes + 2 * xbytes + 2 * wbytes;
     TcPlanView &T = p->tc;
     if (!(tc_encode_2d(&T.x_hi, p->d_x_hi, p->ldx, (int64_t)lmax * mmax, 64, 128) &&

@@ -184,8 +184,8 @@ cudaError_t stage_legendre(sht_batch_s *b, const Shape &sh, cudaStream_t st) {
       q.B = (int)b->items[i].count;
       q.Nt = column_tile(q.B, sh.nt_cap);
       if (!inverse) {
-        q.rowsf = reinterpret_cast<float *>(p->d_x_hi);
-        q.ldr = p->ldx;
+        q.rowsf = reinterpret_cast<float *>(p->d_spec_b);
+        q.ldr = p->ldr;
         q.cin = 1;
       } else {
         q.Gw = p->d_work;
@@ -250,8 +250,8 @@ cudaError_t stage_finalize(sht_batch_s *b, cudaStream_t st) {
   RowsItem it[kMaxItems];
   for (int i = 0; i < n; i++) {
     sht_plan_s *p = b->plans[i];
-    it[i] = RowsItem{reinterpret_cast<const float *>(p->d_x_hi), static_cast<float2 *>(b->items[i].out), nullptr,
-                     nullptr, nullptr, p->L, p->M, (int)b->items[i].count, p->ldx};
+    it[i] = RowsItem{reinterpret_cast<const float *>(p->d_spec_b), static_cast<float2 *>(b->items[i].out), nullptr,
+                     nullptr, nullptr, p->L, p->M, (int)b->items[i].count, p->ldr};
   }
   return launch_rows_transpose(false, it, n, st);
 }

@@ -178,6 +178,31 @@ struct RegDFT<4> {
 
 // Buffer of one sequence: rows k2 < 45 of P + 1 entries (padding against
 // bank conflicts).  After seq_fft, X[k2 + 45 k1] sits at row k2, column k1.
+// Sequence buffer pitch (float2 entries): 45 rows of P + 1, padded to 2 mod
+// 16 so that the 8 fields of a CTA fall on distinct bank pairs.
+template <int P>
+__host__ __device__ constexpr int seq_pitch() {
+  return (kQ * (P + 1) + 15 - 2) / 16 * 16 + 2;
+}
+
+// Twiddle table w_N^{t k2} (t < P, k2 < 45, lane-major) into shared memory
+// from the plan's table w_N^q; indices walked without divisions.
+template <int P>
+__device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ twiddle) {
+  constexpr int N = kQ * P;
+  int d = threadIdx.x / kQ, r = threadIdx.x - (threadIdx.x / kQ) * kQ;  // q = 45 d + r
+  constexpr int kStepD = kThreads / kQ, kStepR = kThreads % kQ;
+  for (int q = threadIdx.x; q < N; q += kThreads) {
+    tw[q] = twiddle[d * r];
+    r += kStepR;
+    d += kStepD;
+    if (r >= kQ) {
+      r -= kQ;
+      d++;
+    }
+  }
+}
+
 template <int P>
 __device__ __forceinline__ int spec_index(int k) {
   return (k % kQ) * (P + 1) + k / kQ;
@@ -205,13 +230,6 @@ __device__ __forceinline__ void seq_fft(float2 (&v)[kQ], int t, float2 *buf, con
   __syncwarp();
 }
 
-__device__ __forceinline__ float mode_weight(int m, int n, int inverse_weights) {
-  if (!inverse_weights) return 1.0f;
-  if (m == 0) return 1.0f;
-  if ((n & 1) == 0 && 2 * m == n) return 1.0f;
-  return 2.0f;
-}
-
 struct OutF32 {
   float *F;
   __device__ __forceinline__ void put(int64_t idx, float2 v) const { *reinterpret_cast<float2 *>(F + idx) = v; }
@@ -236,7 +254,7 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
                                            const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
-  constexpr int BUF = kQ * (P + 1);
+  constexpr int BUF = seq_pitch<P>();
   extern __shared__ float2 smem[];
   float2 *tw = smem;
   float2 *bufs = smem + N;
@@ -247,7 +265,7 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
   const int kp = by * NPAIR + pp;
   const int ks = nlat - 1 - kp;
   const bool live = (b < B) && (kp < Kh);
-  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
+  load_twiddles<P>(tw, twiddle);
   float2 v[kQ];
   if (live) {
     const float *rn = x + ((int64_t)b * nlat + kp) * N;
@@ -263,35 +281,49 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
   float2 *buf = bufs + s * BUF;
   seq_fft<P>(v, t, buf, tw);
   __syncthreads();
-  // separate the two real transforms, fold by parity, write 8-field segments
+  // separate the two real transforms, fold by parity, write 8-field
+  // segments: thread (ff, m0) handles field ff and orders m0, m0 + 32, ...
+  // (m = 45 q + r tracked without divisions)
+  constexpr int kMStep = kThreads / kFB;
+  static_assert(kMStep < kQ, "one wrap of r per step");
   const int b0 = bx * kFB;
+  const int ff = threadIdx.x % kFB, m0 = threadIdx.x / kFB;
+  if (b0 + ff >= B) return;
+  const int64_t col = 2 * (int64_t)(b0 + ff);
+  const int64_t pstride = (int64_t)Kh * ldc;  // E row -> O row
 #pragma unroll 1
-  for (int pq = 0; pq < NPAIR; pq++)
-  for (int e = threadIdx.x; e < M * kFB; e += kThreads) {
-    const int ff = e % kFB;
-    const int m = e / kFB;
+  for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
-    if (b0 + ff >= B || kq >= Kh) continue;
+    if (kq >= Kh) continue;
     const int kqs = nlat - 1 - kq;
+    const bool eqr = kq == kqs;
+    const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
+    const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
     const float2 *Z = bufs + (pq * kFB + ff) * BUF;
-    const float2 zm = Z[spec_index<P>(m)];
-    const float2 zc = conjf2(Z[spec_index<P>((N - m) % N)]);
-    const float c = 0.5f * mode_weight(m, N, inverse_weights);
-    const float sn = ring_scale ? ring_scale[kq] : 1.0f;
-    const float ss = ring_scale ? ring_scale[kqs] : 1.0f;
-    const float2 Fk = cscale(cadd(zm, zc), c * sn);
-    const float2 Fs = cscale(mul_mi(csub(zm, zc)), c * ss);
-    float2 E, O;
-    if (kq == kqs) {
-      E = Fk;
-      O = make_float2(0.f, 0.f);
-    } else {
-      E = cadd(Fk, Fs);
-      O = csub(Fk, Fs);
+    int r = m0, q = 0;
+    int64_t o = ((int64_t)m0 * 2 * Kh + kq) * ldc + col;
+    for (int m = m0; m < M; m += kMStep, o += 2 * kMStep * pstride) {
+      // X[m] sits at spec_index(m); X[N - m] at spec_index(N - m)
+      const int im = r * (P + 1) + q;
+      const int ic = m == 0 ? 0 : (r > 0 ? (kQ - r) * (P + 1) + (P - 1 - q) : P - q);
+      const float2 zm = Z[im];
+      const float2 zc = conjf2(Z[ic]);
+      const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
+      const float2 Fk = cscale(cadd(zm, zc), w * sn);
+      const float2 Fs = cscale(mul_mi(csub(zm, zc)), w * ss);
+      if (eqr) {
+        out.put(o, Fk);
+        out.put(o + pstride, make_float2(0.f, 0.f));
+      } else {
+        out.put(o, cadd(Fk, Fs));
+        out.put(o + pstride, csub(Fk, Fs));
+      }
+      r += kMStep;
+      if (r >= kQ) {
+        r -= kQ;
+        q++;
+      }
     }
-    const int64_t col = 2 * (int64_t)(b0 + ff);
-    out.put((((int64_t)m * 2 + 0) * Kh + kq) * ldc + col, E);
-    out.put((((int64_t)m * 2 + 1) * Kh + kq) * ldc + col, O);
   }
 }
 
@@ -308,48 +340,51 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
                                            const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
-  constexpr int BUF = kQ * (P + 1);
+  constexpr int BUF = seq_pitch<P>();
   extern __shared__ float2 smem[];
   float2 *tw = smem;
   float2 *bufs = smem + N;
   const int Kh = (nlat + 1) / 2;
   const int b0 = bx * kFB;
-  for (int q = threadIdx.x; q < N; q += kThreads) tw[q] = twiddle[(q / kQ) * (q % kQ)];
+  load_twiddles<P>(tw, twiddle);
   // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
   // the southern row (entries M..2M-1) of every sequence buffer
   // loads are issued in batches of 8 iterations so that many are in flight
+  // thread (ff, m0) stages field ff, orders m0, m0 + 32, ...
   constexpr int kBatch = 8;
+  constexpr int kMStep = kThreads / kFB;
+  const int ff = threadIdx.x % kFB, m0 = threadIdx.x / kFB;
+  const bool field_ok = b0 + ff < B;
+  const int64_t col = 2 * (int64_t)(b0 + ff);
+  const int64_t pstride = (int64_t)Kh * ldc;  // E row -> O row
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
-    if (kq >= Kh) continue;
+    if (kq >= Kh || !field_ok) continue;
     const int kqs = nlat - 1 - kq;
     const bool eq = (kq == kqs);
-    const float sn = ring_scale ? ring_scale[kq] : 1.0f;
-    const float ss = ring_scale ? ring_scale[kqs] : 1.0f;
-    const float *ge_row = Gw + ((int64_t)0 * Kh + kq) * ldc;
-    for (int e0 = threadIdx.x; e0 < M * kFB; e0 += kThreads * kBatch) {
+    const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
+    const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
+    const float *g0 = Gw + ((int64_t)m0 * 2 * Kh + kq) * ldc + col;
+    float2 *Bq = bufs + (pq * kFB + ff) * BUF;
+    for (int mb = m0; mb < M; mb += kMStep * kBatch, g0 += (int64_t)2 * kMStep * kBatch * pstride) {
       float2 ge[kBatch], go[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; u++) {
-        const int e = e0 + u * kThreads;
-        const int ff = e % kFB, m = e / kFB;
         ge[u] = go[u] = make_float2(0.f, 0.f);
-        if (e < M * kFB && b0 + ff < B) {
-          const int64_t col = 2 * (int64_t)(b0 + ff);
-          ge[u] = *reinterpret_cast<const float2 *>(ge_row + ((int64_t)m * 2 + 0) * Kh * ldc + col);
-          go[u] = *reinterpret_cast<const float2 *>(ge_row + ((int64_t)m * 2 + 1) * Kh * ldc + col);
+        if (mb + u * kMStep < M) {
+          const float *g = g0 + (int64_t)2 * u * kMStep * pstride;
+          ge[u] = *reinterpret_cast<const float2 *>(g);
+          go[u] = *reinterpret_cast<const float2 *>(g + pstride);
         }
       }
 #pragma unroll
       for (int u = 0; u < kBatch; u++) {
-        const int e = e0 + u * kThreads;
-        const int ff = e % kFB, m = e / kFB;
-        if (e >= M * kFB || b0 + ff >= B) continue;
-        const float c = 0.5f * mode_weight(m, N, inverse_weights);
-        float2 *Bq = bufs + (pq * kFB + ff) * BUF;
-        Bq[m] = cscale(eq ? ge[u] : cadd(ge[u], go[u]), c * sn);
-        Bq[M + m] = eq ? make_float2(0.f, 0.f) : cscale(csub(ge[u], go[u]), c * ss);
+        const int m = mb + u * kMStep;
+        if (m >= M) break;
+        const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
+        Bq[m] = cscale(eq ? ge[u] : cadd(ge[u], go[u]), w * sn);
+        Bq[M + m] = eq ? make_float2(0.f, 0.f) : cscale(csub(ge[u], go[u]), w * ss);
       }
     }
   }
@@ -373,7 +408,7 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
         hn = buf[q];
         hs = buf[M + q];
       }
-      const int qm = (N - q) % N;
+      const int qm = q == 0 ? 0 : N - q;
       if (qm < M) {
         hn = cadd(hn, conjf2(buf[qm]));
         hs = cadd(hs, conjf2(buf[M + qm]));
@@ -387,10 +422,17 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   const bool eq = (kp == ksth);
   float *rn = y + ((int64_t)b * nlat + kp) * N;
   float *rs = y + ((int64_t)b * nlat + ksth) * N;
+  int r = t, q = 0;  // j = 45 q + r
+#pragma unroll 5
   for (int j = t; j < N; j += P) {
-    const float2 o = buf[spec_index<P>(j)];
+    const float2 o = buf[r * (P + 1) + q];
     rn[j] = o.x;
     if (!eq) rs[j] = -o.y;
+    r += P;
+    if (r >= kQ) {
+      r -= kQ;
+      q++;
+    }
   }
 }
 
@@ -464,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 2) c2r45_grouped_kernel(const __grid
 
 template <int P>
 size_t smem45() {
-  return sizeof(float2) * ((size_t)kQ * P + (size_t)(kThreads / P) * kQ * (P + 1));
+  return sizeof(float2) * ((size_t)kQ * P + (size_t)(kThreads / P) * seq_pitch<P>());
 }
 
 template <int P, class Out>

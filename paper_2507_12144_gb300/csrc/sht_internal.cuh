@@ -302,6 +302,7 @@ struct sht_plan_s {
   int64_t srows = 0;           // rows of the internal coefficient layout
   int *d_soff = nullptr;       // [2 M] first internal row of block (m, p)
   int ldx = 0;                 // columns of the l-major forward rows
+  int ldr = 0;                 // columns of the FP32 forward rows (in spec_b)
   int max_channels = 0;        // capacity of the real filter weights
   __nv_bfloat16 *d_x_hi = nullptr, *d_x_lo = nullptr;  // l-major forward rows [L M][ldx]
   __nv_bfloat16 *d_wr_hi = nullptr, *d_wr_lo = nullptr;  // real filter weights

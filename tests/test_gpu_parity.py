@@ -164,6 +164,25 @@ def test_block_and_fused_filter_inverse_match_oracle(shtgb, prec):
         assert per_field_spatial_err(y2, ref_y).max() <= TOL_FP32
 
 
+@pytest.mark.parametrize("prec", TC_PRECS)
+def test_forward_then_block_on_one_plan(shtgb, prec):
+    """The forward into the API layout and the fused block share a plan's
+    workspaces; neither may leave values the other reads."""
+    nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
+    Bm, C = 2, 6
+    fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, Bm * C, 3, 520)
+    W = inputs.filter_weights(521, L, C, C).astype(np.complex64)
+    ref_y = oracle.sht_inverse(oracle.spectral_filter(ref_x.reshape(Bm, C, L, M), W), nlat, nlon, grid, L, M)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=Bm * C, precision=prec)
+    x = _to_gpu(fields, torch.float32)
+    for _ in range(2):
+        xh = shtgb.sht_forward(plan, x).cpu().numpy()
+        assert per_field_spec_err(xh, ref_x).max() <= TOL[prec]
+        y = shtgb.sht_spectral_block(plan, x.reshape(Bm, C, nlat, nlon), _to_gpu(W, torch.complex64)).cpu().numpy()
+        assert np.isfinite(y).all()
+        assert rel_l2(y, ref_y) <= 2 * TOL[prec]
+
+
 def test_round_trip_and_ylm_deltas_gauss_33x64(shtgb):
     """33 x 64 Gaussian grid, lmax = mmax = 32, batch 4, (l+1)^-1.5 spectra."""
     nlat, nlon, L = 33, 64, 32
