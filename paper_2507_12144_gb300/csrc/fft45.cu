@@ -69,6 +69,8 @@ __device__ __forceinline__ float2 root(int k);
 template <>
 __device__ __forceinline__ float2 root<45>(int k) { return kRoot45[k % 45]; }
 template <>
+__device__ __forceinline__ float2 root<9>(int k) { return kRoot45[(5 * k) % 45]; }
+template <>
 __device__ __forceinline__ float2 root<32>(int k) { return kRoot32[k & 31]; }
 template <>
 __device__ __forceinline__ float2 root<16>(int k) { return kRoot32[(k & 15) * 2]; }
@@ -142,11 +144,37 @@ __device__ __forceinline__ void reg_stage(float2 (&a)[N]) {
 template <int N>
 struct RegDFT;
 template <>
+struct RegDFT<9> {
+  static __device__ __forceinline__ void run(float2 (&a)[9]) {
+    reg_stage<9, 1, 3>(a);
+    reg_stage<9, 3, 3>(a);
+  }
+};
+// 45 = 9 x 5 with coprime factors (Good-Thomas): inputs n = (5 n1 + 9 n2)
+// mod 45, outputs k = (10 k1 + 36 k2) mod 45 (k = k1 mod 9, k = k2 mod 5),
+// 9-point DFTs along n1 and 5-point DFTs along n2, no twiddles between them.
+template <>
 struct RegDFT<45> {
   static __device__ __forceinline__ void run(float2 (&a)[45]) {
-    reg_stage<45, 1, 5>(a);
-    reg_stage<45, 5, 3>(a);
-    reg_stage<45, 15, 3>(a);
+    float2 b[9][5];
+#pragma unroll
+    for (int n2 = 0; n2 < 5; n2++) {
+      float2 c[9];
+#pragma unroll
+      for (int n1 = 0; n1 < 9; n1++) c[n1] = a[(5 * n1 + 9 * n2) % 45];
+      RegDFT<9>::run(c);
+#pragma unroll
+      for (int k1 = 0; k1 < 9; k1++) b[k1][n2] = c[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 9; k1++) {
+      float2 c[5];
+#pragma unroll
+      for (int n2 = 0; n2 < 5; n2++) c[n2] = b[k1][n2];
+      butterfly<5>(c);
+#pragma unroll
+      for (int k2 = 0; k2 < 5; k2++) a[(10 * k1 + 36 * k2) % 45] = c[k2];
+    }
   }
 };
 template <>
@@ -383,10 +411,22 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
         const int m = mb + u * kMStep;
         if (m >= M) break;
         const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
-        Bq[m] = cscale(eq ? ge[u] : cadd(ge[u], go[u]), w * sn);
-        Bq[M + m] = eq ? make_float2(0.f, 0.f) : cscale(csub(ge[u], go[u]), w * ss);
+        const float2 gn = cscale(eq ? ge[u] : cadd(ge[u], go[u]), w * sn);
+        const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(ge[u], go[u]), w * ss);
+        // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
+        // G_m enters Z[m], conj(G_m) enters Z[N - m]
+        const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
+        const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
+        const int mq = m == 0 ? 0 : N - m;
+        if (mq == m) {
+          Bq[m] = cadd(za, zb);
+        } else {
+          Bq[m] = za;
+          Bq[mq] = zb;
+        }
       }
     }
+    for (int q = M + m0; q <= N - M; q += kMStep) Bq[q] = make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int s = threadIdx.x / P, t = threadIdx.x % P;
@@ -396,26 +436,11 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   const int ksth = nlat - 1 - kp;
   const bool live = (b < B) && (kp < Kh);
   float2 *buf = bufs + s * BUF;
-  // Hermitian extension of both rows, packed Z = H_n + i H_s; the synthesis
-  // is an inverse DFT, evaluated as conj(FFT(conj Z)).
+  // the staged conj(Z); the synthesis is an inverse DFT, evaluated as
+  // conj(FFT(conj Z))
   float2 v[kQ];
 #pragma unroll
-  for (int j = 0; j < kQ; j++) {
-    const int q = t + P * j;
-    float2 hn = make_float2(0.f, 0.f), hs = make_float2(0.f, 0.f);
-    if (live) {
-      if (q < M) {
-        hn = buf[q];
-        hs = buf[M + q];
-      }
-      const int qm = q == 0 ? 0 : N - q;
-      if (qm < M) {
-        hn = cadd(hn, conjf2(buf[qm]));
-        hs = cadd(hs, conjf2(buf[M + qm]));
-      }
-    }
-    v[j] = conjf2(make_float2(hn.x - hs.y, hn.y + hs.x));
-  }
+  for (int j = 0; j < kQ; j++) v[j] = live ? buf[t + P * j] : make_float2(0.f, 0.f);
   __syncwarp();
   seq_fft<P>(v, t, buf, tw);
   if (!live) return;
