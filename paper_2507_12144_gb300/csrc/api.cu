@@ -758,6 +758,13 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       free_plan(p);
       return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
     }
+    T.gw = p->d_work;
+    T.gw_ldc = p->ldc;
+    if (!(tc_encode_rows_f32(&T.g32, p->d_work, p->ldc, p->Kh, 2 * mmax, 32) &&
+          tc_encode_rows_f32(&T.g16, p->d_work, p->ldc, p->Kh, 2 * mmax, 16))) {
+      free_plan(p);
+      return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the inverse output");
+    }
     if (!(tc_encode_2d(&T.f_hi, f_hi(p), p->ldcb, (int64_t)frow, 64, 64) &&
           tc_encode_2d(&T.f_lo, f_lo(p), p->ldcb, (int64_t)frow, 64, 64) &&
           tc_encode_2d(&T.s_hi, p->d_s_hi, p->ldcb, p->srows, 64, 64) &&

@@ -67,8 +67,6 @@ __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.
 template <int N>
 __device__ __forceinline__ float2 root(int k);
 template <>
-__device__ __forceinline__ float2 root<45>(int k) { return kRoot45[k % 45]; }
-template <>
 __device__ __forceinline__ float2 root<9>(int k) { return kRoot45[(5 * k) % 45]; }
 template <>
 __device__ __forceinline__ float2 root<32>(int k) { return kRoot32[k & 31]; }

@@ -149,10 +149,11 @@ struct SegArgs {
   int NB, ldC;
 };
 
-// TMA maps of one problem: A (table hi/lo, or filter data) and B (data, or
-// filter weights).
+// TMA maps of one problem: A (table hi/lo, or filter data), B (data, or
+// filter weights), and for the inverse the FP32 output rows viewed as
+// [2M][Kh][ldc] with 32 x 32 and 16 x 32 store boxes.
 struct SegMaps {
-  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  CUtensorMap a_hi, a_lo, b_hi, b_lo, g32, g16;
 };
 
 struct TcParams {
@@ -161,6 +162,7 @@ struct TcParams {
   int nseg, ntiles, stages;
   int Nmax;               // widest column tile: stage layout and TMEM columns
   int ncmax, xtot;        // generator shared memory: coefficients, x^2 entries
+  int epi_off;            // byte offset of the epilogue staging (inverse)
   // filter (one problem)
   const FiltTile *ftiles;
   const int *soff;
@@ -336,7 +338,7 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
 // Epilogue of one tile for the accumulator at tacc (zero: write zeros).
 template <int kMode>
 __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, uint32_t tacc, int q4, int lane,
-                                         bool zero) {
+                                         bool zero, unsigned char *stg) {
   const int Nt = ti.Nt;
   const uint32_t tl = tacc + ((uint32_t)(q4 * 32) << 16);
   if (kMode == kFwd) {
@@ -386,28 +388,48 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       }
     }
   } else if (kMode == kInv) {
-    const SegArgs &g = P.seg[ti.s];
-    const int k = ti.r0 + q4 * 32 + lane;
-    const int ldc = g.ldc;
-    float *G = g.Gw + (((int64_t)ti.m * 2 + ti.p) * g.Kh + k) * ldc;
-    const bool k_ok = k < g.Kh;
-    for (int j = 0; j < Nt / 16; j++) {
-      float v[16];
+    // FP32 rows G[(2m + p) Kh + k'][ldc] through the warp's two swizzled
+    // 32 x 32 staging buffers and TMA stores; rows k' >= Kh fall outside
+    // the map's extents and are not written
+    const SegMaps &mp = P.maps[ti.s];
+    const int k0 = ti.r0 + q4 * 32;
+    for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
+      const bool half = Nt - j0 == 16;
+      unsigned char *buf = stg + (c & 1) * 4096;
+      if (c >= 2) {
+        if (lane == 0) bulk_wait_read<1>();
+        __syncwarp();
+      }
+      float v[32];
       if (!zero) {
-        tmem_ld16(tl + (uint32_t)(j * 16), v);
+        tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+        if (!half) tmem_ld16(tl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
       } else {
 #pragma unroll
-        for (int u = 0; u < 16; u++) v[u] = 0.f;
+        for (int u = 0; u < 32; u++) v[u] = 0.f;
       }
-      if (k_ok) {
+      if (!half) {
+        // 128-byte rows, 16-byte chunk u at u ^ (row mod 8)
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int c = ti.c0 + j * 16 + 4 * u;
-          if (c < ldc)
-            *reinterpret_cast<float4 *>(G + c) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-        }
+        for (int u = 0; u < 8; u++)
+          *reinterpret_cast<float4 *>(buf + lane * 128 + ((u ^ (lane & 7)) << 4)) =
+              make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+      } else {
+        // 64-byte rows, 16-byte chunk u at u ^ ((row / 2) mod 4)
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          *reinterpret_cast<float4 *>(buf + lane * 64 + ((u ^ ((lane >> 1) & 3)) << 4)) =
+              make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_3d(half ? &mp.g16 : &mp.g32, buf, ti.c0 + j0, k0, 2 * ti.m + ti.p);
+        bulk_commit();
       }
     }
+    if (lane == 0) bulk_wait_read<0>();
+    __syncwarp();
   } else {
     const int m = ti.m + q4 * 32 + lane;
     const bool ok = (m < P.M) && (m <= ti.l);
@@ -699,19 +721,21 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
         mbar_arrive(&tfull[acc]);
     }
   } else if (warp >= 4 && warp < 8) {
-    // epilogue
+    // epilogue (the inverse's staging buffers: 8 KB per warp, 1024-aligned)
     const int q4 = warp - 4;
+    unsigned char *stg = base + P.epi_off + q4 * 8192;
     uint32_t it = 0;
     for (TileWalk<kMode> w(P); w.more(P); it++) {
       const TileInfo ti = w.take(P);
       const int acc = (int)(it & 1);
       mbar_wait(&tfull[acc], (it >> 1) & 1, P.err);
       tc_fence_after();
-      epilogue<kMode>(P, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0);
+      epilogue<kMode>(P, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0, stg);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
+    if (kMode == kInv && lane == 0) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
@@ -1020,7 +1044,9 @@ size_t extra_smem(bool gen, TcParams &P) {
     cbytes = sizeof(float4) * (size_t)P.ncmax + sizeof(float2) * (size_t)((P.xtot + 1) & ~1) +
              sizeof(Seed) * 256 * kSeedAhead;
   }
-  return (cbytes + 15) / 16 * 16;
+  cbytes = (cbytes + 1023) / 1024 * 1024;
+  if (kMode == kInv) cbytes += 4 * 8192;  // epilogue staging
+  return cbytes;
 }
 
 // Whether two pipeline stages and the extra areas fit one CTA.
@@ -1040,6 +1066,9 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
   int stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 1024 - extra) / sb);
   if (cfg.stages >= 2) stages = std::min(stages, cfg.stages);
   P.stages = stages;
+  // the inverse's staging follows the generators' area (stage sizes and the
+  // generators' area are multiples of 1024 bytes)
+  P.epi_off = (int)((size_t)stages * sb + extra - (kMode == kInv ? 4 * 8192 : 0));
   const size_t smem = 1024 + (size_t)stages * sb + extra;
   const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
@@ -1079,6 +1108,25 @@ bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, 
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_encode_rows_f32(CUtensorMap *tm, const float *ptr, int ldc, int Kh, int nblocks, int box_cols) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&enc, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !enc)
+      return false;
+  }
+  if (box_cols != 32 && box_cols != 16) return false;
+  cuuint64_t gdim[3] = {(cuuint64_t)ldc, (cuuint64_t)Kh, (cuuint64_t)nblocks};
+  cuuint64_t gstr[2] = {(cuuint64_t)ldc * 4, (cuuint64_t)ldc * 4 * Kh};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, 32, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
@@ -1144,6 +1192,10 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
         mp.a_lo = T.tab_inv_lo;
         mp.b_hi = T.s_hi;
         mp.b_lo = split ? T.s_lo : T.s_hi;
+        // the output maps describe the plan's FP32 workspace
+        if (it.Gw != T.gw || it.ldc != T.gw_ldc) return cudaErrorInvalidValue;
+        mp.g32 = T.g32;
+        mp.g16 = T.g16;
       }
       P.Nmax = std::max(P.Nmax, g.Nt);
       ntiles += it.ntiles * g.nct;

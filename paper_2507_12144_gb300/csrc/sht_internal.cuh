@@ -51,6 +51,9 @@ struct TcPlanView {
   CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;  // bf16 table (streamed)
   CUtensorMap f_hi, f_lo, s_hi, s_lo;
   CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
+  CUtensorMap g32, g16;    // FP32 inverse output rows [2M][Kh][ldc], store boxes 32 x 32, 16 x 32
+  const float *gw;         // their base (the FP32 workspace) and row stride
+  int gw_ldc;
   const int *roff, *soff;
   // on-chip Legendre table: seeds (16 B each) every 32 rows
   const void *seeds;
@@ -64,6 +67,9 @@ struct TcPlanView {
 };
 
 bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows);
+// FP32 rows [nblocks][Kh][ldc] as a 3-D map with store boxes box_cols x 32
+// (box_cols 32: 128-byte swizzle; 16: 64-byte swizzle).
+bool tc_encode_rows_f32(CUtensorMap *tm, const float *ptr, int ldc, int Kh, int nblocks, int box_cols);
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64],
 // transposed layout [(2m + p) Kh + k'][Ip64]).
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
