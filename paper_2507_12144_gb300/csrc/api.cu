@@ -760,6 +760,15 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     }
     T.gw = p->d_work;
     T.gw_ldc = p->ldc;
+    T.xrows_hi = p->d_x_hi;
+    T.ldx = p->ldx;
+    if (!(tc_encode_lrows_bf16(&T.xo32_hi, p->d_x_hi, p->ldx, mmax, lmax, 32) &&
+          tc_encode_lrows_bf16(&T.xo32_lo, p->d_x_lo, p->ldx, mmax, lmax, 32) &&
+          tc_encode_lrows_bf16(&T.xo16_hi, p->d_x_hi, p->ldx, mmax, lmax, 16) &&
+          tc_encode_lrows_bf16(&T.xo16_lo, p->d_x_lo, p->ldx, mmax, lmax, 16))) {
+      free_plan(p);
+      return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
+    }
     if (!(tc_encode_rows_f32(&T.g32, p->d_work, p->ldc, p->Kh, 2 * mmax, 32) &&
           tc_encode_rows_f32(&T.g16, p->d_work, p->ldc, p->Kh, 2 * mmax, 16))) {
       free_plan(p);

@@ -150,10 +150,12 @@ struct SegArgs {
 };
 
 // TMA maps of one problem: A (table hi/lo, or filter data), B (data, or
-// filter weights), and for the inverse the FP32 output rows viewed as
-// [2M][Kh][ldc] with 32 x 32 and 16 x 32 store boxes.
+// filter weights), and store maps of the output with 32- and 16-column
+// boxes of 32 rows: for the inverse the FP32 rows viewed as [2M][Kh][ldc]
+// (o32_hi, o16_hi); for the forward into l-major bf16 rows those rows
+// viewed as [L][M][ldx] with every second l (hi and lo).
 struct SegMaps {
-  CUtensorMap a_hi, a_lo, b_hi, b_lo, g32, g16;
+  CUtensorMap a_hi, a_lo, b_hi, b_lo, o32_hi, o32_lo, o16_hi, o16_lo;
 };
 
 struct TcParams {
@@ -343,6 +345,58 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
   const uint32_t tl = tacc + ((uint32_t)(q4 * 32) << 16);
   if (kMode == kFwd) {
     const SegArgs &g = P.seg[ti.s];
+    // l-major bf16 rows of one member through TMA stores: the tile's
+    // columns must lie in one member and start on a 16-byte boundary
+    {
+      const FwdOut &out = g.fout;
+      const int mb = (ti.c0 / 2) / out.cin;
+      const bool one_member = out.rows_hi && (out.cin & 3) == 0 && ((ti.c0 + Nt) / 2 - 1) / out.cin == mb;
+      if (one_member) {
+        const SegMaps &mp = P.maps[ti.s];
+        const int x0 = mb * out.kx + (ti.c0 - 2 * mb * out.cin);  // output column of accumulator column c0
+        const int l0 = ti.m + ti.p + 2 * (ti.r0 + q4 * 32);
+        const bool lo = out.rows_lo != nullptr;
+        for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
+          const bool half = Nt - j0 == 16;
+          unsigned char *bh = stg + (c & 1) * 4096, *bl = bh + 2048;
+          if (c >= 2) {
+            if (lane == 0) bulk_wait_read<1>();
+            __syncwarp();
+          }
+          float v[32];
+          tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+          if (!half) tmem_ld16(tl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
+          const int nchunk = half ? 2 : 4;  // 16-byte chunks of 8 values
+          for (int u = 0; u < nchunk; u++) {
+            uint32_t h[4], r4[4];
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+              const __nv_bfloat162 hh = __floats2bfloat162_rn(v[8 * u + 2 * w], v[8 * u + 2 * w + 1]);
+              const float2 hf = __bfloat1622float2(hh);
+              const __nv_bfloat162 ll =
+                  __floats2bfloat162_rn(v[8 * u + 2 * w] - hf.x, v[8 * u + 2 * w + 1] - hf.y);
+              h[w] = *reinterpret_cast<const uint32_t *>(&hh);
+              r4[w] = *reinterpret_cast<const uint32_t *>(&ll);
+            }
+            // 64-byte rows swizzled (chunk u at u ^ ((row / 2) mod 4)), or
+            // 32-byte rows unswizzled for the 16-column tail
+            const uint32_t off = half ? lane * 32 + u * 16 : lane * 64 + ((u ^ ((lane >> 1) & 3)) << 4);
+            *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            if (lo) *reinterpret_cast<uint4 *>(bl + off) = make_uint4(r4[0], r4[1], r4[2], r4[3]);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, bh, x0 + j0, ti.m, l0);
+            if (lo) tma_store_3d(half ? &mp.o16_lo : &mp.o32_lo, bl, x0 + j0, ti.m, l0);
+            bulk_commit();
+          }
+        }
+        if (lane == 0) bulk_wait_read<0>();
+        __syncwarp();
+        return;
+      }
+    }
     const int r = ti.r0 + q4 * 32 + lane;
     const bool row_ok = r < leg_rows(g.L, ti.m, ti.p);
     const int l = ti.m + ti.p + 2 * r;
@@ -424,7 +478,7 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        tma_store_3d(half ? &mp.g16 : &mp.g32, buf, ti.c0 + j0, k0, 2 * ti.m + ti.p);
+        tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, buf, ti.c0 + j0, k0, 2 * ti.m + ti.p);
         bulk_commit();
       }
     }
@@ -735,7 +789,7 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
-    if (kMode == kInv && lane == 0) bulk_wait<0>();
+    if (kMode != kFilt && lane == 0) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
@@ -1045,7 +1099,7 @@ size_t extra_smem(bool gen, TcParams &P) {
              sizeof(Seed) * 256 * kSeedAhead;
   }
   cbytes = (cbytes + 1023) / 1024 * 1024;
-  if (kMode == kInv) cbytes += 4 * 8192;  // epilogue staging
+  if (kMode != kFilt) cbytes += 4 * 8192;  // epilogue staging
   return cbytes;
 }
 
@@ -1068,7 +1122,7 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
   P.stages = stages;
   // the inverse's staging follows the generators' area (stage sizes and the
   // generators' area are multiples of 1024 bytes)
-  P.epi_off = (int)((size_t)stages * sb + extra - (kMode == kInv ? 4 * 8192 : 0));
+  P.epi_off = (int)((size_t)stages * sb + extra - (kMode != kFilt ? 4 * 8192 : 0));
   const size_t smem = 1024 + (size_t)stages * sb + extra;
   const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
@@ -1126,6 +1180,30 @@ bool tc_encode_rows_f32(CUtensorMap *tm, const float *ptr, int ldc, int Kh, int 
   cuuint32_t es[3] = {1, 1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&enc, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !enc)
+      return false;
+  }
+  if (box_cols != 32 && box_cols != 16) return false;
+  if (!ptr) {
+    *tm = CUtensorMap{};
+    return true;
+  }
+  // dims (column, m, l); every second l, 32 of them per box
+  cuuint64_t gdim[3] = {(cuuint64_t)ldx, (cuuint64_t)M, (cuuint64_t)L};
+  cuuint64_t gstr[2] = {(cuuint64_t)ldx * 2, (cuuint64_t)ldx * 2 * M};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, 1, 64};
+  cuuint32_t es[3] = {1, 1, 2};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1187,6 +1265,13 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
         mp.a_lo = T.tab_fwd_lo;
         mp.b_hi = T.f_hi;
         mp.b_lo = split ? T.f_lo : T.f_hi;
+        // store maps of the plan's l-major rows (used when the destination
+        // is those rows)
+        if (it.rows_hi && (it.rows_hi != T.xrows_hi || it.ldo != T.ldx)) return cudaErrorInvalidValue;
+        mp.o32_hi = T.xo32_hi;
+        mp.o32_lo = T.xo32_lo;
+        mp.o16_hi = T.xo16_hi;
+        mp.o16_lo = T.xo16_lo;
       } else {
         mp.a_hi = T.tab_inv_hi;
         mp.a_lo = T.tab_inv_lo;
@@ -1194,8 +1279,8 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
         mp.b_lo = split ? T.s_lo : T.s_hi;
         // the output maps describe the plan's FP32 workspace
         if (it.Gw != T.gw || it.ldc != T.gw_ldc) return cudaErrorInvalidValue;
-        mp.g32 = T.g32;
-        mp.g16 = T.g16;
+        mp.o32_hi = T.g32;
+        mp.o16_hi = T.g16;
       }
       P.Nmax = std::max(P.Nmax, g.Nt);
       ntiles += it.ntiles * g.nct;

@@ -54,6 +54,9 @@ struct TcPlanView {
   CUtensorMap g32, g16;    // FP32 inverse output rows [2M][Kh][ldc], store boxes 32 x 32, 16 x 32
   const float *gw;         // their base (the FP32 workspace) and row stride
   int gw_ldc;
+  CUtensorMap xo32_hi, xo32_lo, xo16_hi, xo16_lo;  // l-major rows [L][M][ldx], every second l, store boxes
+  const __nv_bfloat16 *xrows_hi;                    // their base and row stride
+  int ldx;
   const int *roff, *soff;
   // on-chip Legendre table: seeds (16 B each) every 32 rows
   const void *seeds;
@@ -70,6 +73,9 @@ bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, 
 // FP32 rows [nblocks][Kh][ldc] as a 3-D map with store boxes box_cols x 32
 // (box_cols 32: 128-byte swizzle; 16: 64-byte swizzle).
 bool tc_encode_rows_f32(CUtensorMap *tm, const float *ptr, int ldc, int Kh, int nblocks, int box_cols);
+// bf16 l-major rows [L][M][ldx] as a 3-D map whose store boxes take box_cols
+// columns of 32 rows l, l + 2, ..., l + 62 (element stride 2 along l).
+bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols);
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64],
 // transposed layout [(2m + p) Kh + k'][Ip64]).
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,

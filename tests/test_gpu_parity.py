@@ -165,15 +165,18 @@ def test_block_and_fused_filter_inverse_match_oracle(shtgb, prec):
 
 
 @pytest.mark.parametrize("prec", TC_PRECS)
-def test_forward_then_block_on_one_plan(shtgb, prec):
+@pytest.mark.parametrize("BmC", [(2, 6), (1, 24), (2, 128)])
+def test_forward_then_block_on_one_plan(shtgb, prec, BmC):
     """The forward into the API layout and the fused block share a plan's
-    workspaces; neither may leave values the other reads."""
+    workspaces; neither may leave values the other reads.  (1, 24) and
+    (2, 128) take the forward rows through TMA stores (column tiles inside
+    one member), (2, 6) through per-lane stores."""
     nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
-    Bm, C = 2, 6
+    Bm, C = BmC
     fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, Bm * C, 3, 520)
     W = inputs.filter_weights(521, L, C, C).astype(np.complex64)
     ref_y = oracle.sht_inverse(oracle.spectral_filter(ref_x.reshape(Bm, C, L, M), W), nlat, nlon, grid, L, M)
-    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=Bm * C, precision=prec)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=Bm * C, precision=prec, max_channels=C)
     x = _to_gpu(fields, torch.float32)
     for _ in range(2):
         xh = shtgb.sht_forward(plan, x).cpu().numpy()
