@@ -249,6 +249,9 @@ float *rows_f32(sht_plan_s *p) { return reinterpret_cast<float *>(p->d_spec_b); 
 __nv_bfloat16 *data_lo(sht_plan_s *p, __nv_bfloat16 *lo) { return p->precision == SHT_PREC_SPLIT_BF16 ? lo : nullptr; }
 
 // Destination of the forward contraction in the tensor-core block path: the
+// Column block of one member in the l-major rows of the fused block.
+int block_kx(int Cin) { return (2 * Cin + 7) / 8 * 8; }
+
 // l-major bf16 rows with members of cin channels in blocks of kx columns.
 struct RowsOut {
   __nv_bfloat16 *hi, *lo;
@@ -270,9 +273,9 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
     if (!is_tc(p)) {
       e = traced(p, SHT_KERNEL_R2C, st, [&] {
         if (fft45_supported(p->nlon))
-          return launch_r2c45(xb, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle,
+          return launch_r2c45(xb, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
                               ring, wts, st);
-        return launch_r2c(xb, p->d_work, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, p->radix, ring, wts, st);
+        return launch_r2c(xb, p->d_work, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle, p->radix, ring, wts, st);
       });
       if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
       e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
@@ -282,9 +285,9 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
     } else {
       e = traced(p, SHT_KERNEL_R2C, st, [&] {
         if (fft45_supported(p->nlon))
-          return launch_r2c45(xb, nullptr, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->ldcb,
+          return launch_r2c45(xb, nullptr, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->lay_f,
                               p->d_twiddle, ring, wts, st);
-        return launch_r2c_bf16(xb, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->ldcb, p->d_twiddle,
+        return launch_r2c_bf16(xb, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
                                p->radix, ring, wts, st);
       });
       if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
@@ -331,8 +334,8 @@ cudaError_t c2r_any(sht_plan_s *p, float *y, int nb, bool adjoint, cudaStream_t 
   const float *ring = adjoint ? p->d_ring_w : nullptr;
   const int wts = adjoint ? 0 : 1;
   if (fft45_supported(p->nlon))
-    return launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, ring, wts, st);
-  return launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, p->radix, ring, wts, st);
+    return launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, ring, wts, st);
+  return launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, p->radix, ring, wts, st);
 }
 
 // Inverse Legendre + longitude synthesis of B fields whose coefficients are
@@ -393,25 +396,36 @@ sht_status_t filter_body(sht_plan_s *p, const float2 *x, const float2 *W, float2
 // rows of the inverse, inverse + synthesis.
 sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, int64_t nb, int Cin, int Cout,
                       cudaStream_t st) {
-  const int kx = (2 * Cin + 63) / 64 * 64;
+  // members' columns packed at kx = 2 Cin rounded to 8: the 64-column K
+  // chunks of one member run into the next member's columns, which meet
+  // zero weight columns, or past the last member outside the map (read as
+  // zero without memory traffic)
+  const int kx = block_kx(Cin);
   const int nwr = (2 * Cout + 15) / 16 * 16;
   const bool split = p->precision == SHT_PREC_SPLIT_BF16;
   RowsOut ro{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, kx};
   SHT_TRY(analysis(p, x, nullptr, nb * Cin, st, false, false, &ro));
-  // real weights: [L][nwr][kx] bf16 hi/lo, TMA boxes of 64 columns x Nt rows
+  CUtensorMap ta_hi, ta_lo;
+  const int64_t width = std::max<int64_t>(64, nb * (int64_t)kx);
+  if (!tc_encode_2d(&ta_hi, p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx) ||
+      !tc_encode_2d(&ta_lo, split ? p->d_x_lo : p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx))
+    return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
+  // real weights: [L][nwr][kw] bf16 hi/lo (kw = 2 Cin rounded to 64, zero
+  // past 2 Cin), TMA boxes of 64 columns x Nt rows
+  const int kw = (2 * Cin + 63) / 64 * 64;
   const int ntile_n = (2 * Cout + 255) / 256;
   const int Nt = ((2 * Cout + ntile_n - 1) / ntile_n + 15) / 16 * 16;
   CUtensorMap tw_hi, tw_lo;
-  if (!tc_encode_2d(&tw_hi, p->d_wr_hi, kx, (int64_t)p->L * nwr, 64, Nt) ||
-      !tc_encode_2d(&tw_lo, p->d_wr_lo, kx, (int64_t)p->L * nwr, 64, Nt))
+  if (!tc_encode_2d(&tw_hi, p->d_wr_hi, kw, (int64_t)p->L * nwr, 64, Nt) ||
+      !tc_encode_2d(&tw_lo, p->d_wr_lo, kw, (int64_t)p->L * nwr, 64, Nt))
     return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the filter weights");
   cudaError_t e = traced(p, SHT_KERNEL_FILTER_PREP, st, [&] {
-    return launch_filter_prep((const float2 *)W, p->d_wr_hi, p->d_wr_lo, p->L, Cout, Cin, nwr, kx, st);
+    return launch_filter_prep((const float2 *)W, p->d_wr_hi, p->d_wr_lo, p->L, Cout, Cin, nwr, kw, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "filter weight preparation launch");
   e = traced(p, SHT_KERNEL_FILTER, st, [&] {
-    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, tw_hi, tw_lo, p->d_s_hi, data_lo(p, p->d_s_lo), p->ldcb,
-                            kx, nwr, (int)nb, Cin, Cout, st);
+    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, ta_hi, ta_lo, tw_hi, tw_lo, p->d_s_hi,
+                            data_lo(p, p->d_s_lo), p->ldcb, kx, nwr, (int)nb, Cin, Cout, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "filter launch");
   return synthesis_rows(p, y, (int)(nb * Cout), st, false);
@@ -713,6 +727,12 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
 
   // workspaces
   p->ldcb = (int)std::max<int64_t>(64, (2 * o.max_batch + 7) / 8 * 8);
+  // folded Fourier workspaces, (m, p)-major: the Legendre kernels read and
+  // write whole (m, p) blocks of contiguous rows.  (A ring-major layout,
+  // which gives the longitude kernels adjacent rows, measured no faster for
+  // them and slower for the tensor-core gathers at 721 x 1440.)
+  p->lay_f = classic_layout(p->Kh, tc ? p->ldcb : p->ldc);
+  p->lay_g = classic_layout(p->Kh, p->ldc);
   const size_t frow = (size_t)mmax * 2 * p->Kh;
   const size_t work = std::max(sizeof(float) * frow * p->ldc, tc ? 2 * sizeof(__nv_bfloat16) * frow * p->ldcb : 0);
   // spec_b also holds the FP32 l-major rows of the tensor-core forward into
@@ -769,13 +789,13 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       free_plan(p);
       return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
     }
-    if (!(tc_encode_rows_f32(&T.g32, p->d_work, p->ldc, p->Kh, 2 * mmax, 32) &&
-          tc_encode_rows_f32(&T.g16, p->d_work, p->ldc, p->Kh, 2 * mmax, 16))) {
+    if (!(tc_encode_fold_f32(&T.g32, p->d_work, p->lay_g, p->ldc, 2 * mmax, p->Kh, 32) &&
+          tc_encode_fold_f32(&T.g16, p->d_work, p->lay_g, p->ldc, 2 * mmax, p->Kh, 16))) {
       free_plan(p);
       return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the inverse output");
     }
-    if (!(tc_encode_2d(&T.f_hi, f_hi(p), p->ldcb, (int64_t)frow, 64, 64) &&
-          tc_encode_2d(&T.f_lo, f_lo(p), p->ldcb, (int64_t)frow, 64, 64) &&
+    if (!(tc_encode_fold_bf16(&T.f_hi, f_hi(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh) &&
+          tc_encode_fold_bf16(&T.f_lo, f_lo(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh) &&
           tc_encode_2d(&T.s_hi, p->d_s_hi, p->ldcb, p->srows, 64, 64) &&
           tc_encode_2d(&T.s_lo, p->d_s_lo, p->ldcb, p->srows, 64, 64))) {
       free_plan(p);
@@ -913,7 +933,7 @@ sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, flo
   if (is_tc(p)) {
     if (std::max(Cin, Cout) > p->max_channels)
       return fail(SHT_ERR_INVALID_ARG, "max(Cin, Cout) exceeds the plan's max_channels");
-    per = std::min<int64_t>(per, p->ldx / ((2 * Cin + 63) / 64 * 64));
+    per = std::min<int64_t>(per, p->ldx / block_kx(Cin));
   }
   const int64_t npix = (int64_t)p->nlat * p->nlon;
   for (int64_t b0 = 0; b0 < Bm; b0 += per) {

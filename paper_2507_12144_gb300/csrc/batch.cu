@@ -114,11 +114,11 @@ cudaError_t stage_r2c(sht_batch_s *b, cudaStream_t st) {
                         b->tc ? work_lo(p) : nullptr,
                         p->d_twiddle,
                         p->d_ring_w,
+                        p->lay_f,
                         p->nlat,
                         p->nlon,
                         p->M,
                         (int)b->items[i].count,
-                        b->tc ? p->ldcb : p->ldc,
                         0};
     }
     return launch_r2c45_grouped(it, n, b->tc, st);
@@ -129,14 +129,14 @@ cudaError_t stage_r2c(sht_batch_s *b, cudaStream_t st) {
     const int nb = (int)b->items[i].count;
     cudaError_t e;
     if (fft45_supported(p->nlon))
-      e = b->tc ? launch_r2c45(x, nullptr, work_hi(p), work_lo(p), p->nlat, p->nlon, p->M, nb, p->ldcb,
+      e = b->tc ? launch_r2c45(x, nullptr, work_hi(p), work_lo(p), p->nlat, p->nlon, p->M, nb, p->lay_f,
                                p->d_twiddle, p->d_ring_w, 0, st)
-                : launch_r2c45(x, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle,
+                : launch_r2c45(x, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
                                p->d_ring_w, 0, st);
     else
-      e = b->tc ? launch_r2c_bf16(x, work_hi(p), work_lo(p), p->nlat, p->nlon, p->M, nb, p->ldcb, p->d_twiddle,
+      e = b->tc ? launch_r2c_bf16(x, work_hi(p), work_lo(p), p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
                                   p->radix, p->d_ring_w, 0, st)
-                : launch_r2c(x, p->d_work, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, p->radix, p->d_ring_w,
+                : launch_r2c(x, p->d_work, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle, p->radix, p->d_ring_w,
                              0, st);
     if (e != cudaSuccess) return e;
   }
@@ -150,7 +150,7 @@ cudaError_t stage_c2r(sht_batch_s *b, cudaStream_t st) {
     for (int i = 0; i < n; i++) {
       sht_plan_s *p = b->plans[i];
       it[i] = Fft45Item{p->d_work, static_cast<float *>(b->items[i].out), nullptr, nullptr, p->d_twiddle, nullptr,
-                        p->nlat, p->nlon, p->M, (int)b->items[i].count, p->ldc, 1};
+                        p->lay_g, p->nlat, p->nlon, p->M, (int)b->items[i].count, 1};
     }
     return launch_c2r45_grouped(it, n, st);
   }
@@ -160,8 +160,8 @@ cudaError_t stage_c2r(sht_batch_s *b, cudaStream_t st) {
     const int nb = (int)b->items[i].count;
     cudaError_t e =
         fft45_supported(p->nlon)
-            ? launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, nullptr, 1, st)
-            : launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->ldc, p->d_twiddle, p->radix, nullptr, 1, st);
+            ? launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, nullptr, 1, st)
+            : launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, p->radix, nullptr, 1, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -132,7 +132,7 @@ struct OutBF16 {
 
 template <class Out>
 __global__ void __launch_bounds__(kThreads)
-r2c_pairs_kernel(const float *__restrict__ x, Out out, int nlat, int nlon, int M, int B, int ldc,
+r2c_pairs_kernel(const float *__restrict__ x, Out out, int nlat, int nlon, int M, int B, FoldLayout fl,
                  const float2 *__restrict__ twiddle, RadixPlan rp, const float *__restrict__ ring_scale,
                  int inverse_weights) {
   extern __shared__ float2 smem[];
@@ -140,7 +140,6 @@ r2c_pairs_kernel(const float *__restrict__ x, Out out, int nlat, int nlon, int M
   float2 *tw = smem;
   float2 *bufA = tw + n;
   float2 *bufB = bufA + kFields * n;
-  const int Kh = (nlat + 1) / 2;
   const int kp = blockIdx.y;          // northern row k'
   const int ks = nlat - 1 - kp;       // mirrored southern row
   const bool equator = (kp == ks);
@@ -180,13 +179,13 @@ r2c_pairs_kernel(const float *__restrict__ x, Out out, int nlat, int nlon, int M
       O = csub(Fk, Fs);
     }
     const int64_t col = 2 * (int64_t)(b0 + f);
-    out.put((((int64_t)m * 2 + 0) * Kh + kp) * ldc + col, E);
-    out.put((((int64_t)m * 2 + 1) * Kh + kp) * ldc + col, O);
+    out.put(fold_row(fl, m, 0, kp) + col, E);
+    out.put(fold_row(fl, m, 1, kp) + col, O);
   }
 }
 
 __global__ void __launch_bounds__(kThreads)
-c2r_pairs_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int nlon, int M, int B, int ldc,
+c2r_pairs_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int nlon, int M, int B, FoldLayout fl,
                  const float2 *__restrict__ twiddle, RadixPlan rp, const float *__restrict__ ring_scale,
                  int inverse_weights) {
   extern __shared__ float2 smem[];
@@ -194,7 +193,6 @@ c2r_pairs_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, 
   float2 *tw = smem;
   float2 *bufA = tw + n;
   float2 *bufB = bufA + kFields * n;
-  const int Kh = (nlat + 1) / 2;
   const int kp = blockIdx.y;
   const int ks = nlat - 1 - kp;
   const bool equator = (kp == ks);
@@ -210,8 +208,8 @@ c2r_pairs_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, 
     const int f = t / M;
     const int m = t - f * M;
     const int64_t col = 2 * (int64_t)(b0 + f);
-    const float2 ge = *reinterpret_cast<const float2 *>(Gw + (((int64_t)m * 2 + 0) * Kh + kp) * ldc + col);
-    const float2 go = *reinterpret_cast<const float2 *>(Gw + (((int64_t)m * 2 + 1) * Kh + kp) * ldc + col);
+    const float2 ge = *reinterpret_cast<const float2 *>(Gw + fold_row(fl, m, 0, kp) + col);
+    const float2 go = *reinterpret_cast<const float2 *>(Gw + fold_row(fl, m, 1, kp) + col);
     const float c = 0.5f * mode_weight(m, n, inverse_weights);
     float2 gn = equator ? ge : cadd(ge, go);
     float2 gs = equator ? make_float2(0.f, 0.f) : csub(ge, go);
@@ -268,7 +266,7 @@ static cudaError_t set_smem(const void *fn, size_t bytes) {
   return cudaSuccess;
 }
 
-cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M, int B, int ldc,
+cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M, int B, FoldLayout fl,
                        const float2 *twiddle, const RadixPlan &rp, const float *ring_scale, int inverse_weights,
                        cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
@@ -277,13 +275,13 @@ cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M, int
   size_t smem = fft_smem_bytes(nlon, 2);
   cudaError_t e = set_smem((const void *)r2c_pairs_kernel<OutF32>, smem);
   if (e != cudaSuccess) return e;
-  r2c_pairs_kernel<OutF32><<<grid, kThreads, smem, st>>>(x, OutF32{Fw}, nlat, nlon, M, B, ldc, twiddle, rp,
+  r2c_pairs_kernel<OutF32><<<grid, kThreads, smem, st>>>(x, OutF32{Fw}, nlat, nlon, M, B, fl, twiddle, rp,
                                                          ring_scale, inverse_weights);
   return cudaGetLastError();
 }
 
 cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,
-                            int ldb, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
+                            FoldLayout fl, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
                             int inverse_weights, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   const int Kh = (nlat + 1) / 2;
@@ -291,12 +289,12 @@ cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *F
   size_t smem = fft_smem_bytes(nlon, 2);
   cudaError_t e = set_smem((const void *)r2c_pairs_kernel<OutBF16>, smem);
   if (e != cudaSuccess) return e;
-  r2c_pairs_kernel<OutBF16><<<grid, kThreads, smem, st>>>(x, OutBF16{Fhi, Flo}, nlat, nlon, M, B, ldb, twiddle, rp,
+  r2c_pairs_kernel<OutBF16><<<grid, kThreads, smem, st>>>(x, OutBF16{Fhi, Flo}, nlat, nlon, M, B, fl, twiddle, rp,
                                                           ring_scale, inverse_weights);
   return cudaGetLastError();
 }
 
-cudaError_t launch_c2r(const float *Gw, float *y, int nlat, int nlon, int M, int B, int ldc,
+cudaError_t launch_c2r(const float *Gw, float *y, int nlat, int nlon, int M, int B, FoldLayout fl,
                        const float2 *twiddle, const RadixPlan &rp, const float *ring_scale, int inverse_weights,
                        cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
@@ -305,7 +303,7 @@ cudaError_t launch_c2r(const float *Gw, float *y, int nlat, int nlon, int M, int
   size_t smem = fft_smem_bytes(nlon, 3);
   cudaError_t e = set_smem((const void *)c2r_pairs_kernel, smem);
   if (e != cudaSuccess) return e;
-  c2r_pairs_kernel<<<grid, kThreads, smem, st>>>(Gw, y, nlat, nlon, M, B, ldc, twiddle, rp, ring_scale,
+  c2r_pairs_kernel<<<grid, kThreads, smem, st>>>(Gw, y, nlat, nlon, M, B, fl, twiddle, rp, ring_scale,
                                                  inverse_weights);
   return cudaGetLastError();
 }

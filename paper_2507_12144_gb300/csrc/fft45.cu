@@ -256,9 +256,14 @@ __device__ __forceinline__ void seq_fft(float2 (&v)[kQ], int t, float2 *buf, con
   __syncwarp();
 }
 
+// Destinations of the analysis: `put` writes one complex value, `put2` the
+// values of two adjacent fields (idx a multiple of 4 elements).
 struct OutF32 {
   float *F;
   __device__ __forceinline__ void put(int64_t idx, float2 v) const { *reinterpret_cast<float2 *>(F + idx) = v; }
+  __device__ __forceinline__ void put2(int64_t idx, float2 a, float2 b) const {
+    *reinterpret_cast<float4 *>(F + idx) = make_float4(a.x, a.y, b.x, b.y);
+  }
 };
 struct OutBF16 {
   __nv_bfloat16 *hi, *lo;
@@ -270,13 +275,25 @@ struct OutBF16 {
       *reinterpret_cast<__nv_bfloat162 *>(lo + idx) = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
     }
   }
+  __device__ __forceinline__ void put2(int64_t idx, float2 a, float2 b) const {
+    const __nv_bfloat162 ha = __floats2bfloat162_rn(a.x, a.y), hb = __floats2bfloat162_rn(b.x, b.y);
+    *reinterpret_cast<uint2 *>(hi + idx) =
+        make_uint2(*reinterpret_cast<const uint32_t *>(&ha), *reinterpret_cast<const uint32_t *>(&hb));
+    if (lo) {
+      const float2 fa = __bfloat1622float2(ha), fb = __bfloat1622float2(hb);
+      const __nv_bfloat162 la = __floats2bfloat162_rn(a.x - fa.x, a.y - fa.y);
+      const __nv_bfloat162 lb = __floats2bfloat162_rn(b.x - fb.x, b.y - fb.y);
+      *reinterpret_cast<uint2 *>(lo + idx) =
+          make_uint2(*reinterpret_cast<const uint32_t *>(&la), *reinterpret_cast<const uint32_t *>(&lb));
+    }
+  }
 };
 
 // One CTA of the analysis: fields bx kFB .. bx kFB + 7, ring pairs
 // by NPAIR .. by NPAIR + NPAIR - 1.
 template <int P, class Out>
 __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restrict__ x, Out out, int nlat, int M,
-                                           int B, int ldc, const float2 *__restrict__ twiddle,
+                                           int B, FoldLayout fl, const float2 *__restrict__ twiddle,
                                            const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
@@ -308,15 +325,17 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
   seq_fft<P>(v, t, buf, tw);
   __syncthreads();
   // separate the two real transforms, fold by parity, write 8-field
-  // segments: thread (ff, m0) handles field ff and orders m0, m0 + 32, ...
-  // (m = 45 q + r tracked without divisions)
-  constexpr int kMStep = kThreads / kFB;
-  static_assert(kMStep < kQ, "one wrap of r per step");
+  // segments: thread (f2, m0) handles fields 2 f2, 2 f2 + 1 and orders m0,
+  // m0 + 64, ... (m = 45 q + r tracked without divisions)
+  constexpr int kPairs = kFB / 2;
+  constexpr int kMStep = kThreads / kPairs;  // 64
   const int b0 = bx * kFB;
-  const int ff = threadIdx.x % kFB, m0 = threadIdx.x / kFB;
-  if (b0 + ff >= B) return;
-  const int64_t col = 2 * (int64_t)(b0 + ff);
-  const int64_t pstride = (int64_t)Kh * ldc;  // E row -> O row
+  const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+  const int fa = 2 * f2;
+  if (b0 + fa >= B) return;
+  const bool two = b0 + fa + 1 < B;
+  const int64_t col = 2 * (int64_t)(b0 + fa);
+  const int64_t pstride = fl.smp;  // E row -> O row
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
@@ -325,26 +344,37 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
     const bool eqr = kq == kqs;
     const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
     const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
-    const float2 *Z = bufs + (pq * kFB + ff) * BUF;
-    int r = m0, q = 0;
-    int64_t o = ((int64_t)m0 * 2 * Kh + kq) * ldc + col;
+    const float2 *Za = bufs + (pq * kFB + fa) * BUF;
+    const float2 *Zb = Za + BUF;
+    int r = m0 % kQ, q = m0 / kQ;
+    int64_t o = fold_row(fl, m0, 0, kq) + col;
     for (int m = m0; m < M; m += kMStep, o += 2 * kMStep * pstride) {
       // X[m] sits at spec_index(m); X[N - m] at spec_index(N - m)
       const int im = r * (P + 1) + q;
       const int ic = m == 0 ? 0 : (r > 0 ? (kQ - r) * (P + 1) + (P - 1 - q) : P - q);
-      const float2 zm = Z[im];
-      const float2 zc = conjf2(Z[ic]);
       const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
-      const float2 Fk = cscale(cadd(zm, zc), w * sn);
-      const float2 Fs = cscale(mul_mi(csub(zm, zc)), w * ss);
-      if (eqr) {
-        out.put(o, Fk);
-        out.put(o + pstride, make_float2(0.f, 0.f));
-      } else {
-        out.put(o, cadd(Fk, Fs));
-        out.put(o + pstride, csub(Fk, Fs));
+      const float wn = w * sn, ws = w * ss;
+      float2 e[2], od[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const float2 *Z = h ? Zb : Za;
+        const float2 zm = Z[im];
+        const float2 zc = conjf2(Z[ic]);
+        const float2 Fk = cscale(cadd(zm, zc), wn);
+        const float2 Fs = cscale(mul_mi(csub(zm, zc)), ws);
+        e[h] = eqr ? Fk : cadd(Fk, Fs);
+        od[h] = eqr ? make_float2(0.f, 0.f) : csub(Fk, Fs);
       }
-      r += kMStep;
+      if (two) {
+        out.put2(o, e[0], e[1]);
+        out.put2(o + pstride, od[0], od[1]);
+      } else {
+        out.put(o, e[0]);
+        out.put(o + pstride, od[0]);
+      }
+      // m += 64 = 45 + 19
+      r += kMStep - kQ;
+      q++;
       if (r >= kQ) {
         r -= kQ;
         q++;
@@ -355,14 +385,14 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
 
 template <int P, class Out>
 __global__ void __launch_bounds__(kThreads, 2)
-r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, int ldc, const float2 *__restrict__ twiddle,
+r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, FoldLayout fl, const float2 *__restrict__ twiddle,
              const float *__restrict__ ring_scale, int inverse_weights) {
-  r2c45_body<P, Out>(blockIdx.x, blockIdx.y, x, out, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights);
+  r2c45_body<P, Out>(blockIdx.x, blockIdx.y, x, out, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
 }
 
 template <int P>
 __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restrict__ Gw, float *__restrict__ y,
-                                           int nlat, int M, int B, int ldc, const float2 *__restrict__ twiddle,
+                                           int nlat, int M, int B, FoldLayout fl, const float2 *__restrict__ twiddle,
                                            const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
@@ -376,13 +406,18 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
   // the southern row (entries M..2M-1) of every sequence buffer
   // loads are issued in batches of 8 iterations so that many are in flight
-  // thread (ff, m0) stages field ff, orders m0, m0 + 32, ...
-  constexpr int kBatch = 8;
-  constexpr int kMStep = kThreads / kFB;
-  const int ff = threadIdx.x % kFB, m0 = threadIdx.x / kFB;
-  const bool field_ok = b0 + ff < B;
-  const int64_t col = 2 * (int64_t)(b0 + ff);
-  const int64_t pstride = (int64_t)Kh * ldc;  // E row -> O row
+  // thread (f2, m0) stages fields 2 f2 and 2 f2 + 1 (one 16-byte load per
+  // row), orders m0, m0 + 64, ...
+  constexpr int kBatch = 6;
+  constexpr int kPairs = kFB / 2;
+  constexpr int kMStep = kThreads / kPairs;  // 64
+  const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+  const int fa = 2 * f2;
+  // fields past B stage zeros (their sequences are not synthesised)
+  const bool field_ok = b0 + fa < B;
+  const bool two = b0 + fa + 1 < B;
+  const int64_t col = 2 * (int64_t)(b0 + fa);
+  const int64_t pstride = fl.smp;  // E row -> O row
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
@@ -391,17 +426,23 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
     const bool eq = (kq == kqs);
     const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
     const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
-    const float *g0 = Gw + ((int64_t)m0 * 2 * Kh + kq) * ldc + col;
-    float2 *Bq = bufs + (pq * kFB + ff) * BUF;
+    const float *g0 = Gw + fold_row(fl, m0, 0, kq) + col;
+    float2 *Ba = bufs + (pq * kFB + fa) * BUF;
     for (int mb = m0; mb < M; mb += kMStep * kBatch, g0 += (int64_t)2 * kMStep * kBatch * pstride) {
-      float2 ge[kBatch], go[kBatch];
+      float4 ge[kBatch], go[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; u++) {
-        ge[u] = go[u] = make_float2(0.f, 0.f);
+        ge[u] = go[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (mb + u * kMStep < M) {
           const float *g = g0 + (int64_t)2 * u * kMStep * pstride;
-          ge[u] = *reinterpret_cast<const float2 *>(g);
-          go[u] = *reinterpret_cast<const float2 *>(g + pstride);
+          if (two) {
+            ge[u] = *reinterpret_cast<const float4 *>(g);
+            go[u] = *reinterpret_cast<const float4 *>(g + pstride);
+          } else {
+            const float2 a = *reinterpret_cast<const float2 *>(g), c = *reinterpret_cast<const float2 *>(g + pstride);
+            ge[u] = make_float4(a.x, a.y, 0.f, 0.f);
+            go[u] = make_float4(c.x, c.y, 0.f, 0.f);
+          }
         }
       }
 #pragma unroll
@@ -409,22 +450,31 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
         const int m = mb + u * kMStep;
         if (m >= M) break;
         const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
-        const float2 gn = cscale(eq ? ge[u] : cadd(ge[u], go[u]), w * sn);
-        const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(ge[u], go[u]), w * ss);
-        // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
-        // G_m enters Z[m], conj(G_m) enters Z[N - m]
-        const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
-        const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
         const int mq = m == 0 ? 0 : N - m;
-        if (mq == m) {
-          Bq[m] = cadd(za, zb);
-        } else {
-          Bq[m] = za;
-          Bq[mq] = zb;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const float2 e = h ? make_float2(ge[u].z, ge[u].w) : make_float2(ge[u].x, ge[u].y);
+          const float2 o = h ? make_float2(go[u].z, go[u].w) : make_float2(go[u].x, go[u].y);
+          const float2 gn = cscale(eq ? e : cadd(e, o), w * sn);
+          const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(e, o), w * ss);
+          // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
+          // G_m enters Z[m], conj(G_m) enters Z[N - m]
+          const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
+          const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
+          float2 *Bq = Ba + h * BUF;
+          if (mq == m) {
+            Bq[m] = cadd(za, zb);
+          } else {
+            Bq[m] = za;
+            Bq[mq] = zb;
+          }
         }
       }
     }
-    for (int q = M + m0; q <= N - M; q += kMStep) Bq[q] = make_float2(0.f, 0.f);
+    for (int q = M + m0; q <= N - M; q += kMStep) {
+      Ba[q] = make_float2(0.f, 0.f);
+      Ba[BUF + q] = make_float2(0.f, 0.f);
+    }
   }
   __syncthreads();
   const int s = threadIdx.x / P, t = threadIdx.x % P;
@@ -461,9 +511,9 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, 2)
-c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, int ldc,
+c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, FoldLayout fl,
              const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights) {
-  c2r45_body<P>(blockIdx.x, blockIdx.y, Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights);
+  c2r45_body<P>(blockIdx.x, blockIdx.y, Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
 }
 
 // Grouped launches: one grid over several problems (grids and batches) of
@@ -476,7 +526,8 @@ struct Fft45Seg {
   __nv_bfloat16 *hi, *lo;
   const float2 *tw;
   const float *ring;
-  int nlat, M, B, ldc, wts, P, gx, blk0;
+  FoldLayout fl;
+  int nlat, M, B, wts, P, gx, blk0;
 };
 struct Fft45Group {
   Fft45Seg seg[kMaxFftGroup];
@@ -498,18 +549,18 @@ __global__ void __launch_bounds__(kThreads, 2) r2c45_grouped_kernel(const __grid
   if (kBF16) {
     const OutBF16 out{q.hi, q.lo};
     switch (q.P) {
-      case 32: r2c45_body<32>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-      case 16: r2c45_body<16>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-      case 8: r2c45_body<8>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-      default: r2c45_body<4>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      case 32: r2c45_body<32>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+      case 16: r2c45_body<16>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+      case 8: r2c45_body<8>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+      default: r2c45_body<4>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
     }
   } else {
     const OutF32 out{q.outf};
     switch (q.P) {
-      case 32: r2c45_body<32>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-      case 16: r2c45_body<16>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-      case 8: r2c45_body<8>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-      default: r2c45_body<4>(bx, by, q.in, out, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+      case 32: r2c45_body<32>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+      case 16: r2c45_body<16>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+      case 8: r2c45_body<8>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+      default: r2c45_body<4>(bx, by, q.in, out, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
     }
   }
 }
@@ -520,10 +571,10 @@ __global__ void __launch_bounds__(kThreads, 2) c2r45_grouped_kernel(const __grid
   const int local = blockIdx.x - q.blk0;
   const int bx = local % q.gx, by = local / q.gx;
   switch (q.P) {
-    case 32: c2r45_body<32>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-    case 16: c2r45_body<16>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-    case 8: c2r45_body<8>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
-    default: c2r45_body<4>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.ldc, q.tw, q.ring, q.wts); break;
+    case 32: c2r45_body<32>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    case 16: c2r45_body<16>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    case 8: c2r45_body<8>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    default: c2r45_body<4>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
   }
 }
 
@@ -533,7 +584,7 @@ size_t smem45() {
 }
 
 template <int P, class Out>
-cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, int ldc, const float2 *tw, const float *ring,
+cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl, const float2 *tw, const float *ring,
                   int wts, cudaStream_t st) {
   const int Kh = (nlat + 1) / 2;
   constexpr int NPAIR = kThreads / P / kFB;
@@ -542,12 +593,12 @@ cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, int ldc, cons
   cudaError_t e = cudaFuncSetAttribute((const void *)r2c45_kernel<P, Out>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  r2c45_kernel<P, Out><<<grid, kThreads, smem, st>>>(x, out, nlat, M, B, ldc, tw, ring, wts);
+  r2c45_kernel<P, Out><<<grid, kThreads, smem, st>>>(x, out, nlat, M, B, fl, tw, ring, wts);
   return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, int ldc, const float2 *tw, const float *ring,
+cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, FoldLayout fl, const float2 *tw, const float *ring,
                   int wts, cudaStream_t st) {
   const int Kh = (nlat + 1) / 2;
   constexpr int NPAIR = kThreads / P / kFB;
@@ -556,18 +607,18 @@ cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, int ldc, con
   cudaError_t e = cudaFuncSetAttribute((const void *)c2r45_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  c2r45_kernel<P><<<grid, kThreads, smem, st>>>(G, y, nlat, M, B, ldc, tw, ring, wts);
+  c2r45_kernel<P><<<grid, kThreads, smem, st>>>(G, y, nlat, M, B, fl, tw, ring, wts);
   return cudaGetLastError();
 }
 
 template <class Out>
-cudaError_t r2c45_dispatch(int nlon, const float *x, Out out, int nlat, int M, int B, int ldc, const float2 *tw,
+cudaError_t r2c45_dispatch(int nlon, const float *x, Out out, int nlat, int M, int B, FoldLayout fl, const float2 *tw,
                            const float *ring, int wts, cudaStream_t st) {
   switch (nlon / kQ) {
-    case 32: return r2c45<32>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
-    case 16: return r2c45<16>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
-    case 8: return r2c45<8>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
-    default: return r2c45<4>(x, out, nlat, M, B, ldc, tw, ring, wts, st);
+    case 32: return r2c45<32>(x, out, nlat, M, B, fl, tw, ring, wts, st);
+    case 16: return r2c45<16>(x, out, nlat, M, B, fl, tw, ring, wts, st);
+    case 8: return r2c45<8>(x, out, nlat, M, B, fl, tw, ring, wts, st);
+    default: return r2c45<4>(x, out, nlat, M, B, fl, tw, ring, wts, st);
   }
 }
 
@@ -601,7 +652,7 @@ int64_t group_layout(Fft45Group &g, const Fft45Item *items, int n, size_t &smem)
     q.nlat = it.nlat;
     q.M = it.M;
     q.B = it.B;
-    q.ldc = it.ldc;
+    q.fl = it.fl;
     q.wts = it.inverse_weights;
     q.P = P;
     q.gx = (it.B + kFB - 1) / kFB;
@@ -654,21 +705,21 @@ bool fft45_supported(int nlon) {
 }
 
 cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon,
-                         int M, int B, int ldc, const float2 *twiddle, const float *ring_scale, int inverse_weights,
+                         int M, int B, FoldLayout fl, const float2 *twiddle, const float *ring_scale, int inverse_weights,
                          cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  if (Fw) return r2c45_dispatch(nlon, x, OutF32{Fw}, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
-  return r2c45_dispatch(nlon, x, OutBF16{Fhi, Flo}, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+  if (Fw) return r2c45_dispatch(nlon, x, OutF32{Fw}, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
+  return r2c45_dispatch(nlon, x, OutBF16{Fhi, Flo}, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
 }
 
-cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, int ldc,
+cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, FoldLayout fl,
                          const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   switch (nlon / kQ) {
-    case 32: return c2r45<32>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
-    case 16: return c2r45<16>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
-    case 8: return c2r45<8>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
-    default: return c2r45<4>(Gw, y, nlat, M, B, ldc, twiddle, ring_scale, inverse_weights, st);
+    case 32: return c2r45<32>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
+    case 16: return c2r45<16>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
+    case 8: return c2r45<8>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
+    default: return c2r45<4>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
   }
 }
 

@@ -247,8 +247,8 @@ __device__ __forceinline__ TileInfo tile_decode(const TcParams &P, const RawTile
     ti.a_col0 = 0;
     if (kMode == kFwd) {
       ti.nk = (g.Kh + kKc - 1) / kKc;
-      ti.a_row = r.d.w;  // table row of the tile
-      ti.b_row0 = (ti.m * 2 + ti.p) * g.Kh;
+      ti.a_row = r.d.w;         // table row of the tile
+      ti.b_row0 = 2 * ti.m + ti.p;  // (2m + p) coordinate of the folded data map
     } else {
       ti.nk = (leg_rows(g.L, ti.m, ti.p) + kKc - 1) / kKc;
       ti.a_row = (ti.m * 2 + ti.p) * g.Kh + ti.r0;
@@ -328,6 +328,13 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
   if (kMode == kFilt) {
     tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
     tma_load_2d(b_lo, &mp.b_lo, bar, kc * kKc, ti.b_row0);
+  } else if (kMode == kFwd) {
+    // the folded data as (column, 2m + p, k'): 64 rows k' of one (m, p)
+    const int nbox = (ti.Nt + 63) / 64;
+    for (int j = 0; j < nbox; j++) {
+      tma_load_3d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.b_row0, kc * kKc);
+      if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0, kc * kKc);
+    }
   } else {
     const int nbox = (ti.Nt + 63) / 64;
     for (int j = 0; j < nbox; j++) {
@@ -442,7 +449,7 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       }
     }
   } else if (kMode == kInv) {
-    // FP32 rows G[(2m + p) Kh + k'][ldc] through the warp's two swizzled
+    // FP32 folded rows (column, 2m + p, k') through the warp's two swizzled
     // 32 x 32 staging buffers and TMA stores; rows k' >= Kh fall outside
     // the map's extents and are not written
     const SegMaps &mp = P.maps[ti.s];
@@ -478,7 +485,7 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, buf, ti.c0 + j0, k0, 2 * ti.m + ti.p);
+        tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, buf, ti.c0 + j0, 2 * ti.m + ti.p, k0);
         bulk_commit();
       }
     }
@@ -1142,7 +1149,8 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
 
 }  // namespace
 
-bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows) {
+bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows,
+                  int64_t ld) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     cudaDriverEntryPointQueryResult q;
@@ -1156,7 +1164,7 @@ bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, 
     return true;
   }
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstr[1] = {(cuuint64_t)cols * 2};
+  cuuint64_t gstr[1] = {(cuuint64_t)(ld > 0 ? ld : cols) * 2};
   cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), gdim, gstr, box, es,
@@ -1164,23 +1172,47 @@ bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_encode_rows_f32(CUtensorMap *tm, const float *ptr, int ldc, int Kh, int nblocks, int box_cols) {
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&enc, 12000, cudaEnableDefault, &q) !=
             cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !enc)
-      return false;
+        q != cudaDriverEntryPointSuccess)
+      enc = nullptr;
   }
-  if (box_cols != 32 && box_cols != 16) return false;
-  cuuint64_t gdim[3] = {(cuuint64_t)ldc, (cuuint64_t)Kh, (cuuint64_t)nblocks};
-  cuuint64_t gstr[2] = {(cuuint64_t)ldc * 4, (cuuint64_t)ldc * 4 * Kh};
-  cuuint32_t box[3] = {(cuuint32_t)box_cols, 32, 1};
+  return enc;
+}
+}  // namespace
+
+bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int ld, int nmp, int Kh,
+                        int box_cols) {
+  auto enc = encoder();
+  if (!enc || (box_cols != 32 && box_cols != 16)) return false;
+  cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)nmp, (cuuint64_t)Kh};
+  cuuint64_t gstr[2] = {(cuuint64_t)fl.smp * 4, (cuuint64_t)fl.sk * 4};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, 1, 32};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh) {
+  auto enc = encoder();
+  if (!enc) return false;
+  if (!ptr) {
+    *tm = CUtensorMap{};
+    return true;
+  }
+  cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)nmp, (cuuint64_t)Kh};
+  cuuint64_t gstr[2] = {(cuuint64_t)fl.smp * 2, (cuuint64_t)fl.sk * 2};
+  cuuint32_t box[3] = {64, 1, 64};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols) {
@@ -1333,9 +1365,10 @@ cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat1
   return cudaGetLastError();
 }
 
-cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &tw_hi,
-                             const CUtensorMap &tw_lo, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx,
-                             int nwr, int Bm, int Cin, int Cout, cudaStream_t st) {
+cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &ta_hi,
+                             const CUtensorMap &ta_lo, const CUtensorMap &tw_hi, const CUtensorMap &tw_lo,
+                             __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx, int nwr, int Bm, int Cin,
+                             int Cout, cudaStream_t st) {
   if (nftiles == 0 || Bm <= 0) return cudaSuccess;
   TcParams P{};
   P.nseg = 1;
@@ -1356,8 +1389,8 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.s_hi = s_hi;
   P.s_lo = s_lo;
   P.err = T.err;
-  P.maps[0].a_hi = T.x_hi;
-  P.maps[0].a_lo = T.split ? T.x_lo : T.x_hi;
+  P.maps[0].a_hi = ta_hi;
+  P.maps[0].a_lo = ta_lo;
   P.maps[0].b_hi = tw_hi;
   P.maps[0].b_lo = tw_lo;
   return launch_persistent<kFilt>(T.split, false, P, TcLaunch{}, st);

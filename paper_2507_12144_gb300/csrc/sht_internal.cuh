@@ -33,6 +33,21 @@ struct __align__(16) LegTile {
   int row;
 };
 
+// Layout of a folded Fourier workspace (longitude coefficients E / O of
+// ring pair k' for order m, parity p, fields as columns): row (m, p, k')
+// starts at (2m + p) smp + k' sk elements.  (m, p)-major: smp = Kh ld,
+// sk = ld (what the plans use); ring-major: smp = ld, sk = 2 mmax ld.  The
+// longitude kernels take any layout; the tensor-core contractions address
+// it through 3-D TMA maps built from the same strides.
+struct FoldLayout {
+  int64_t smp, sk;
+};
+__host__ __device__ inline int64_t fold_row(const FoldLayout &fl, int m, int p, int k) {
+  return (2 * (int64_t)m + p) * fl.smp + (int64_t)k * fl.sk;
+}
+inline FoldLayout classic_layout(int Kh, int ld) { return FoldLayout{(int64_t)Kh * ld, (int64_t)ld}; }
+inline FoldLayout ring_layout(int M, int ld) { return FoldLayout{(int64_t)ld, 2 * (int64_t)M * ld}; }
+
 // Device-side view of the folded FP32 Legendre table.  For order m and
 // parity p the rows are l = m + p + 2 i (i < nrows(m, p)), the columns are
 // the northern half-rows k' = 0 .. Kh-1 (Kh = ceil(nlat / 2)), padded to Khp.
@@ -69,10 +84,20 @@ struct TcPlanView {
   unsigned *err;
 };
 
-bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows);
+// 2-D bf16 map of rows x cols (row stride ld elements, default cols) with
+// SWIZZLE_128B boxes box_cols x box_rows; columns past `cols` read as zero.
+bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, int box_cols, int box_rows,
+                  int64_t ld = 0);
 // FP32 rows [nblocks][Kh][ldc] as a 3-D map with store boxes box_cols x 32
 // (box_cols 32: 128-byte swizzle; 16: 64-byte swizzle).
-bool tc_encode_rows_f32(CUtensorMap *tm, const float *ptr, int ldc, int Kh, int nblocks, int box_cols);
+// FP32 folded rows (layout fl, row length ld) as a 3-D map (column, 2m + p,
+// k') with store boxes box_cols x 1 x 32 (box_cols 32: 128-byte swizzle;
+// 16: 64-byte swizzle).
+bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int ld, int nmp, int Kh,
+                        int box_cols);
+// bf16 folded rows (layout fl, row length ld) as a 3-D map (column, 2m + p,
+// k') with load boxes 64 x 1 x 64 (128-byte swizzle).
+bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh);
 // bf16 l-major rows [L][M][ldx] as a 3-D map whose store boxes take box_cols
 // columns of 32 rows l, l + 2, ..., l + 62 (element stride 2 along l).
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols);
@@ -96,9 +121,11 @@ cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat1
                                int nwr, int kx, cudaStream_t st);
 // Tensor-core filter from the l-major rows to the inverse's split rows.
 // ftiles: (l, m0) pairs covering m <= l, m < M in steps of 128.
-cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &tw_hi,
-                             const CUtensorMap &tw_lo, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx,
-                             int nwr, int Bm, int Cin, int Cout, cudaStream_t st);
+// ta: the forward rows (width = members x kx, row stride ldx); tw: W_R.
+cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &ta_hi,
+                             const CUtensorMap &ta_lo, const CUtensorMap &tw_hi, const CUtensorMap &tw_lo,
+                             __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx, int nwr, int Bm, int Cin,
+                             int Cout, cudaStream_t st);
 // Inverse contraction on the tensor cores from the bf16 internal rows to the
 // FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
@@ -155,7 +182,7 @@ cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat
 // Longitude analysis writing the folded Fourier workspace as bf16 hi/lo
 // (same contract as launch_r2c).
 cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,
-                            int ldb, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
+                            FoldLayout fl, const float2 *twiddle, const RadixPlan &rp, const float *ring_scale,
                             int inverse_weights, cudaStream_t st);
 
 
@@ -180,7 +207,7 @@ __host__ __device__ inline int leg_rows(int L, int m, int p) {
 // when inverse_weights == 0, else the weight of the real inverse (1 for
 // m = 0 and the Nyquist mode, 2 otherwise).  ring_scale may be NULL (= 1).
 cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M,
-                       int B, int ldc, const float2 *twiddle,
+                       int B, FoldLayout fl, const float2 *twiddle,
                        const RadixPlan &rp, const float *ring_scale,
                        int inverse_weights, cudaStream_t st);
 
@@ -189,9 +216,9 @@ cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M,
 // (and lo when Flo != NULL) with row stride ldc elements.
 bool fft45_supported(int nlon);
 cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon,
-                         int M, int B, int ldc, const float2 *twiddle, const float *ring_scale, int inverse_weights,
+                         int M, int B, FoldLayout fl, const float2 *twiddle, const float *ring_scale, int inverse_weights,
                          cudaStream_t st);
-cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, int ldc,
+cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, FoldLayout fl,
                          const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st);
 
 // One problem of a grouped longitude launch: the arguments of launch_r2c45
@@ -202,7 +229,8 @@ struct Fft45Item {
   __nv_bfloat16 *hi, *lo;
   const float2 *twiddle;
   const float *ring_scale;
-  int nlat, nlon, M, B, ldc, inverse_weights;
+  FoldLayout fl;
+  int nlat, nlon, M, B, inverse_weights;
 };
 constexpr int kMaxFftGroup = 8;
 // Grouped launches of up to kMaxFftGroup problems (every nlon = 45 P, B >= 1)
@@ -214,7 +242,7 @@ cudaError_t launch_c2r45_grouped(const Fft45Item *items, int n, cudaStream_t st)
 //   u_kj = ring_scale[k] * sum_m c_m Re(G_k(m) e^{2 pi i j m / nlon})
 // with G_k = G_even + G_odd (north row k'), G_kbar = G_even - G_odd.
 cudaError_t launch_c2r(const float *Gw, float *y, int nlat, int nlon, int M,
-                       int B, int ldc, const float2 *twiddle,
+                       int B, FoldLayout fl, const float2 *twiddle,
                        const RadixPlan &rp, const float *ring_scale,
                        int inverse_weights, cudaStream_t st);
 
@@ -296,6 +324,8 @@ struct sht_plan_s {
   int Kh = 0;    // ceil(nlat / 2)
   int Khp = 0;   // Kh padded to a multiple of 16
   int ldc = 0;   // row stride (floats) of the folded Fourier workspace
+  shtgb::FoldLayout lay_f{};  // layout of the workspace the analysis writes (FP32 ldc or bf16 ldcb rows)
+  shtgb::FoldLayout lay_g{};  // layout of the FP32 workspace the synthesis reads
   shtgb::RadixPlan radix{};
   std::vector<double> x, s, w;  // nodes, sin(theta), latitude weights
   std::vector<int64_t> tab_off;  // host copy of the table offsets

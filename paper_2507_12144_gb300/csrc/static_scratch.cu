@@ -89,7 +89,8 @@ extern "C" sht_status_t sht_forward_static_scratch(sht_plan_t p, const float *x,
   for (int64_t b0 = 0; b0 < B; b0 += chunk) {
     const int nb = (int)std::min<int64_t>(chunk, B - b0);
     const int ldc = (2 * nb + 3) / 4 * 4;
-    cudaError_t e = launch_r2c(x + b0 * p->nlat * (int64_t)p->nlon, Fw, p->nlat, p->nlon, p->M, nb, ldc,
+    cudaError_t e = launch_r2c(x + b0 * p->nlat * (int64_t)p->nlon, Fw, p->nlat, p->nlon, p->M, nb,
+                               classic_layout(p->Kh, ldc),
                                p->d_twiddle, p->radix, p->d_ring_w, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
     e = launch_leg_fwd_f32(T, p->d_fwd_tiles, p->n_fwd_tiles, Fw, (float2 *)xhat + b0 * LM, p->L, p->M, p->Kh, ldc,

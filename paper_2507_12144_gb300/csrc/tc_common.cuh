@@ -108,6 +108,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_
       : "memory");
 }
 
+// 3-D tiled load of a box into shared memory, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, uint64_t *bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 // 3-D tiled store of a shared-memory box to global memory (bulk async
 // group); elements outside the tensor's extents are not written.
 __device__ __forceinline__ void tma_store_3d(const void *tmap, const void *src, int x, int y, int z) {
