@@ -181,7 +181,6 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_x2h);
   cudaFree(p->d_x2l);
   cudaFree(p->d_roff);
-  cudaFree(p->d_soff);
   cudaFree(p->d_x_hi);
   cudaFree(p->d_x_lo);
   cudaFree(p->d_wr_hi);
@@ -312,7 +311,7 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
       });
       if (e == cudaSuccess && !rows_out) {
         e = traced(p, SHT_KERNEL_FINALIZE, st, [&] {
-          RowsItem r{rows_f32(p), xhat + b0 * LM, nullptr, nullptr, nullptr, p->L, p->M, nb, p->ldr};
+          RowsItem r{rows_f32(p), xhat + b0 * LM, nullptr, nullptr, p->L, p->M, nb, p->ldr};
           return launch_rows_transpose(false, &r, 1, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "coefficient transpose launch");
@@ -357,8 +356,7 @@ sht_status_t synthesis(sht_plan_s *p, const float2 *yhat, float *y, int64_t B, c
     float *yb = y + b0 * p->nlat * (int64_t)p->nlon;
     if (is_tc(p)) {
       cudaError_t e = traced(p, SHT_KERNEL_PACK, st, [&] {
-        RowsItem r{nullptr, const_cast<float2 *>(yhat + b0 * LM), p->d_s_hi, data_lo(p, p->d_s_lo), p->d_soff,
-                   p->L, p->M, nb, p->ldcb};
+        RowsItem r{nullptr, const_cast<float2 *>(yhat + b0 * LM), p->d_s_hi, data_lo(p, p->d_s_lo), p->L, p->M, nb, p->ldcb};
         return launch_rows_transpose(true, &r, 1, st);
       });
       if (e != cudaSuccess) return cuda_fail(e, "coefficient repack launch");
@@ -550,14 +548,12 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   // block-major order: the row tiles of one (m, p) block run back to back
   // and share its Fourier rows in L2
   std::vector<LegTile> ft, it;
-  int64_t frows_acc = 0, srows_acc = 0;
-  std::vector<int> roff_h(2 * (size_t)mmax), soff_h(2 * (size_t)mmax);
+  int64_t frows_acc = 0;
+  std::vector<int> roff_h(2 * (size_t)mmax);
   for (int m = 0; m < mmax; m++)
     for (int q = 0; q < 2; q++) {
       roff_h[2 * m + q] = (int)frows_acc;
-      soff_h[2 * m + q] = (int)srows_acc;
       frows_acc += leg_rows(lmax, m, q);
-      srows_acc += (leg_rows(lmax, m, q) + 63) / 64 * 64;
     }
   for (int m = 0; m < mmax; m++)
     for (int q = 0; q < 2; q++)
@@ -567,7 +563,7 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   // odd parity): its tiles write the zeros that the synthesis reads
   for (int m = 0; m < mmax; m++)
     for (int q = 0; q < 2; q++)
-      for (int k0 = 0; k0 < p->Kh; k0 += trow) it.push_back(LegTile{m, q, k0, soff_h[2 * m + q]});
+      for (int k0 = 0; k0 < p->Kh; k0 += trow) it.push_back(LegTile{m, q, k0, m + q});
   p->n_fwd_tiles = (int)ft.size();
   p->n_inv_tiles = (int)it.size();
 
@@ -621,18 +617,14 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       // lmax) and the latitudes as hi + lo
       const bool split = o.precision == SHT_PREC_SPLIT_BF16;
       const bool gen = o.table_source == SHT_TABLE_RECURRENCE;
-      std::vector<int> roff(2 * (size_t)mmax), soff(2 * (size_t)mmax);
-      int64_t frows = 0, srows = 0;
+      std::vector<int> roff(2 * (size_t)mmax);
+      int64_t frows = 0;
       for (int m = 0; m < mmax; m++)
         for (int q = 0; q < 2; q++) {
           roff[2 * m + q] = (int)frows;
-          soff[2 * m + q] = (int)srows;
           frows += leg_rows(lmax, m, q);
-          srows += (leg_rows(lmax, m, q) + 63) / 64 * 64;
         }
-      p->srows = srows;
       e = upload(&p->d_roff, roff);
-      if (e == cudaSuccess) e = upload(&p->d_soff, soff);
       TcPlanView &T = p->tc;
       T.gen = gen;
       if (!gen) {
@@ -709,7 +701,6 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
         T.ldC = ldC;
       }
       T.roff = p->d_roff;
-      T.soff = p->d_soff;
       T.L = lmax;
       T.M = mmax;
       T.Kh = p->Kh;
@@ -746,6 +737,8 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   if ((e = dev_alloc((void **)&p->d_spec_b, spec)) != cudaSuccess) return bail(e, "workspace allocation");
   if ((e = cudaMemset(p->d_work, 0, work)) != cudaSuccess) return bail(e, "workspace memset");
   if (tc) {
+    // internal coefficient rows S, l-major [lmax][mmax][ldcb] (rows m > l unused)
+    p->srows = (int64_t)lmax * mmax;
     const size_t sbytes = sizeof(__nv_bfloat16) * (size_t)p->srows * p->ldcb;
     if ((e = dev_alloc((void **)&p->d_s_hi, sbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_s_lo, sbytes)) != cudaSuccess) return bail(e, "workspace allocation");
@@ -782,6 +775,8 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     T.gw_ldc = p->ldc;
     T.xrows_hi = p->d_x_hi;
     T.ldx = p->ldx;
+    T.srows_hi = p->d_s_hi;
+    T.lds = p->ldcb;
     if (!(tc_encode_lrows_bf16(&T.xo32_hi, p->d_x_hi, p->ldx, mmax, lmax, 32) &&
           tc_encode_lrows_bf16(&T.xo32_lo, p->d_x_lo, p->ldx, mmax, lmax, 32) &&
           tc_encode_lrows_bf16(&T.xo16_hi, p->d_x_hi, p->ldx, mmax, lmax, 16) &&
@@ -796,8 +791,12 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     }
     if (!(tc_encode_fold_bf16(&T.f_hi, f_hi(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh) &&
           tc_encode_fold_bf16(&T.f_lo, f_lo(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh) &&
-          tc_encode_2d(&T.s_hi, p->d_s_hi, p->ldcb, p->srows, 64, 64) &&
-          tc_encode_2d(&T.s_lo, p->d_s_lo, p->ldcb, p->srows, 64, 64))) {
+          tc_encode_srows_bf16(&T.s_hi, p->d_s_hi, p->ldcb, mmax, lmax, true, 64) &&
+          tc_encode_srows_bf16(&T.s_lo, p->d_s_lo, p->ldcb, mmax, lmax, true, 64) &&
+          tc_encode_srows_bf16(&T.so32_hi, p->d_s_hi, p->ldcb, mmax, lmax, false, 32) &&
+          tc_encode_srows_bf16(&T.so32_lo, p->d_s_lo, p->ldcb, mmax, lmax, false, 32) &&
+          tc_encode_srows_bf16(&T.so16_hi, p->d_s_hi, p->ldcb, mmax, lmax, false, 16) &&
+          tc_encode_srows_bf16(&T.so16_lo, p->d_s_lo, p->ldcb, mmax, lmax, false, 16))) {
       free_plan(p);
       return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspaces");
     }

@@ -238,8 +238,7 @@ cudaError_t stage_pack(sht_batch_s *b, cudaStream_t st) {
   RowsItem it[kMaxItems];
   for (int i = 0; i < n; i++) {
     sht_plan_s *p = b->plans[i];
-    it[i] = RowsItem{nullptr, static_cast<float2 *>(const_cast<void *>(b->items[i].in)), p->d_s_hi, srow_lo(p),
-                     p->d_soff, p->L, p->M, (int)b->items[i].count, p->ldcb};
+    it[i] = RowsItem{nullptr, static_cast<float2 *>(const_cast<void *>(b->items[i].in)), p->d_s_hi, srow_lo(p), p->L, p->M, (int)b->items[i].count, p->ldcb};
   }
   return launch_rows_transpose(true, it, n, st);
 }
@@ -251,7 +250,7 @@ cudaError_t stage_finalize(sht_batch_s *b, cudaStream_t st) {
   for (int i = 0; i < n; i++) {
     sht_plan_s *p = b->plans[i];
     it[i] = RowsItem{reinterpret_cast<const float *>(p->d_spec_b), static_cast<float2 *>(b->items[i].out), nullptr,
-                     nullptr, nullptr, p->L, p->M, (int)b->items[i].count, p->ldr};
+                     nullptr, p->L, p->M, (int)b->items[i].count, p->ldr};
   }
   return launch_rows_transpose(false, it, n, st);
 }

@@ -88,7 +88,7 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 // across tiles; the accumulator is double-buffered in tensor memory so that
 // the epilogue warps drain tile i while the MMAs of tile i + 1 run.
 //   kFwd:  D[i][c]  = sum_k' T[m][p][i][k'] F[m][p][k'][c]   (A = table, B = data, MN-major)
-//   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[soff + i][c]   (A = table, B = data, MN-major)
+//   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[(m + p + 2i) M + m][c]   (A = table, B = data, MN-major)
 //   kFilt: D[m][n]  = sum_k  X[l M + m][b kx + k] WR[l][n][k] (A = data, B = weights, K-major)
 // Table and weights always enter split (hi + lo); data enters split for
 // split BF16 and rounded (hi only) for BF16.  The Legendre table of kFwd /
@@ -153,7 +153,8 @@ struct SegArgs {
 // filter weights), and store maps of the output with 32- and 16-column
 // boxes of 32 rows: for the inverse the FP32 rows viewed as [2M][Kh][ldc]
 // (o32_hi, o16_hi); for the forward into l-major bf16 rows those rows
-// viewed as [L][M][ldx] with every second l (hi and lo).
+// viewed as [L][M][ldx] with every second l (hi and lo); for the filter the
+// internal rows S viewed as [L][M][ldcb], boxes of 32 m of one l.
 struct SegMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo, o32_hi, o32_lo, o16_hi, o16_lo;
 };
@@ -167,7 +168,6 @@ struct TcParams {
   int epi_off;            // byte offset of the epilogue staging (inverse)
   // filter (one problem)
   const FiltTile *ftiles;
-  const int *soff;
   int L, M, Nt, Bm, ntn, kx, nwr, cin, cout, lds;
   __nv_bfloat16 *s_hi, *s_lo;
   unsigned *err;
@@ -252,7 +252,7 @@ __device__ __forceinline__ TileInfo tile_decode(const TcParams &P, const RawTile
     } else {
       ti.nk = (leg_rows(g.L, ti.m, ti.p) + kKc - 1) / kKc;
       ti.a_row = (ti.m * 2 + ti.p) * g.Kh + ti.r0;
-      ti.b_row0 = r.d.w;  // first internal coefficient row of (m, p)
+      ti.b_row0 = r.d.w;  // first degree m + p of the (m, p) block
     }
   }
   return ti;
@@ -336,12 +336,66 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
       if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0, kc * kKc);
     }
   } else {
+    // the internal rows as (column, m, l) with every second l: 64 rows
+    // l = m + p + 2 i of one (m, p) block per box
     const int nbox = (ti.Nt + 63) / 64;
     for (int j = 0; j < nbox; j++) {
-      tma_load_2d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
-      if (kSplit) tma_load_2d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0 + kc * kKc);
+      tma_load_3d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * kc * kKc);
+      if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * kc * kKc);
     }
   }
+}
+
+// Write accumulator columns [0, ncols) (a multiple of 16) of this warp's 32
+// TMEM lanes as bf16 hi (and lo) through TMA stores: the 32-column chunk
+// at j0 goes to (x + j0, y, z) of the 32-column maps, a 16-column tail to
+// the 16-column maps.  nbuf (1 or 2) staging buffers of 4 KB (hi 2 KB, lo
+// 2 KB) at stg; 64-byte rows swizzled for the 32-column box, 32-byte rows
+// for the tail.
+__device__ __forceinline__ void store_rows_bf16_tma(uint32_t tl, int ncols, const CUtensorMap *m32h,
+                                                    const CUtensorMap *m32l, const CUtensorMap *m16h,
+                                                    const CUtensorMap *m16l, bool lo, int x, int y, int z,
+                                                    unsigned char *stg, int nbuf, int lane) {
+  for (int j0 = 0, c = 0; j0 < ncols; j0 += 32, c++) {
+    const bool half = ncols - j0 == 16;
+    unsigned char *bh = stg + (c % nbuf) * 4096, *bl = bh + 2048;
+    if (c >= nbuf) {
+      if (lane == 0) {
+        if (nbuf == 2)
+          bulk_wait_read<1>();
+        else
+          bulk_wait_read<0>();
+      }
+      __syncwarp();
+    }
+    float v[32];
+    tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+    if (!half) tmem_ld16(tl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
+    const int nchunk = half ? 2 : 4;  // 16-byte chunks of 8 values
+    for (int u = 0; u < nchunk; u++) {
+      uint32_t h[4], r4[4];
+#pragma unroll
+      for (int w = 0; w < 4; w++) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v[8 * u + 2 * w], v[8 * u + 2 * w + 1]);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v[8 * u + 2 * w] - hf.x, v[8 * u + 2 * w + 1] - hf.y);
+        h[w] = *reinterpret_cast<const uint32_t *>(&hh);
+        r4[w] = *reinterpret_cast<const uint32_t *>(&ll);
+      }
+      const uint32_t off = half ? lane * 32 + u * 16 : lane * 64 + ((u ^ ((lane >> 1) & 3)) << 4);
+      *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      if (lo) *reinterpret_cast<uint4 *>(bl + off) = make_uint4(r4[0], r4[1], r4[2], r4[3]);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_3d(half ? m16h : m32h, bh, x + j0, y, z);
+      if (lo) tma_store_3d(half ? m16l : m32l, bl, x + j0, y, z);
+      bulk_commit();
+    }
+  }
+  if (lane == 0) bulk_wait_read<0>();
+  __syncwarp();
 }
 
 // Epilogue of one tile for the accumulator at tacc (zero: write zeros).
@@ -362,45 +416,8 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
         const SegMaps &mp = P.maps[ti.s];
         const int x0 = mb * out.kx + (ti.c0 - 2 * mb * out.cin);  // output column of accumulator column c0
         const int l0 = ti.m + ti.p + 2 * (ti.r0 + q4 * 32);
-        const bool lo = out.rows_lo != nullptr;
-        for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
-          const bool half = Nt - j0 == 16;
-          unsigned char *bh = stg + (c & 1) * 4096, *bl = bh + 2048;
-          if (c >= 2) {
-            if (lane == 0) bulk_wait_read<1>();
-            __syncwarp();
-          }
-          float v[32];
-          tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
-          if (!half) tmem_ld16(tl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
-          const int nchunk = half ? 2 : 4;  // 16-byte chunks of 8 values
-          for (int u = 0; u < nchunk; u++) {
-            uint32_t h[4], r4[4];
-#pragma unroll
-            for (int w = 0; w < 4; w++) {
-              const __nv_bfloat162 hh = __floats2bfloat162_rn(v[8 * u + 2 * w], v[8 * u + 2 * w + 1]);
-              const float2 hf = __bfloat1622float2(hh);
-              const __nv_bfloat162 ll =
-                  __floats2bfloat162_rn(v[8 * u + 2 * w] - hf.x, v[8 * u + 2 * w + 1] - hf.y);
-              h[w] = *reinterpret_cast<const uint32_t *>(&hh);
-              r4[w] = *reinterpret_cast<const uint32_t *>(&ll);
-            }
-            // 64-byte rows swizzled (chunk u at u ^ ((row / 2) mod 4)), or
-            // 32-byte rows unswizzled for the 16-column tail
-            const uint32_t off = half ? lane * 32 + u * 16 : lane * 64 + ((u ^ ((lane >> 1) & 3)) << 4);
-            *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            if (lo) *reinterpret_cast<uint4 *>(bl + off) = make_uint4(r4[0], r4[1], r4[2], r4[3]);
-          }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, bh, x0 + j0, ti.m, l0);
-            if (lo) tma_store_3d(half ? &mp.o16_lo : &mp.o32_lo, bl, x0 + j0, ti.m, l0);
-            bulk_commit();
-          }
-        }
-        if (lane == 0) bulk_wait_read<0>();
-        __syncwarp();
+        store_rows_bf16_tma(tl, Nt, &mp.o32_hi, &mp.o32_lo, &mp.o16_hi, &mp.o16_lo, out.rows_lo != nullptr, x0,
+                            ti.m, l0, stg, 2, lane);
         return;
       }
     }
@@ -492,11 +509,20 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
     if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
   } else {
+    // internal rows S, l-major (row l M + m), member b's outputs at columns
+    // 2 b cout + n; through TMA stores when the tile's columns are whole
+    // 16-column chunks of one member (rows m > l receive values nothing
+    // reads, rows m >= M are outside the map)
+    const int ncol = min(Nt, 2 * P.cout - ti.n0);
+    if ((P.cout & 3) == 0 && (ncol & 15) == 0) {
+      const SegMaps &mp = P.maps[0];
+      store_rows_bf16_tma(tl, ncol, &mp.o32_hi, &mp.o32_lo, &mp.o16_hi, &mp.o16_lo, P.s_lo != nullptr,
+                          2 * ti.b * P.cout + ti.n0, ti.m + 32 * q4, ti.l, stg, 1, lane);
+      return;
+    }
     const int m = ti.m + q4 * 32 + lane;
     const bool ok = (m < P.M) && (m <= ti.l);
-    const int d = ti.l - m;
-    const int64_t srow =
-        ok ? (int64_t)(P.soff[2 * m + (d & 1)] + (d >> 1)) * P.lds + 2 * (int64_t)ti.b * P.cout : 0;
+    const int64_t srow = ok ? ((int64_t)ti.l * P.M + m) * P.lds + 2 * (int64_t)ti.b * P.cout : 0;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
       tmem_ld16(tl + (uint32_t)(j * 16), v);
@@ -784,7 +810,7 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
   } else if (warp >= 4 && warp < 8) {
     // epilogue (the inverse's staging buffers: 8 KB per warp, 1024-aligned)
     const int q4 = warp - 4;
-    unsigned char *stg = base + P.epi_off + q4 * 8192;
+    unsigned char *stg = base + P.epi_off + q4 * (kMode == kFilt ? 4096 : 8192);
     uint32_t it = 0;
     for (TileWalk<kMode> w(P); w.more(P); it++) {
       const TileInfo ti = w.take(P);
@@ -796,7 +822,7 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
-    if (kMode != kFilt && lane == 0) bulk_wait<0>();
+    if (lane == 0) bulk_wait<0>();
   }
   tc_fence_before();
   __syncthreads();
@@ -806,51 +832,6 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
   }
 }
 
-// Repack API-layout coefficients yhat[b][l][m] (complex64) into the internal
-// split rows S[soff(m, p) + i][2b + {re, im}] (bf16 hi and lo), l = m + p + 2i.
-// One thread per (row, field).
-__device__ __forceinline__ void pack_rows_body(int bx, int by, const float2 *__restrict__ yhat,
-                                               __nv_bfloat16 *__restrict__ shi, __nv_bfloat16 *__restrict__ slo,
-                                               const int *__restrict__ soff, int L, int M, int ldb, int B) {
-  const int m = by >> 1, p = by & 1;
-  const int nrows = leg_rows(L, m, p);
-  const int64_t e = (int64_t)bx * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)nrows * B) return;
-  const int i = (int)(e / B), b = (int)(e - (int64_t)i * B);
-  const float2 v = yhat[((int64_t)b * L + m + p + 2 * i) * M + m];
-  __nv_bfloat16 hr, lr, hi_, li;
-  split_bf16(v.x, hr, lr);
-  split_bf16(v.y, hi_, li);
-  const int64_t o = (int64_t)(soff[2 * m + p] + i) * ldb + 2 * b;
-  *reinterpret_cast<uint32_t *>(shi + o) = pack_bf16x2(hr, hi_);
-  if (slo) *reinterpret_cast<uint32_t *>(slo + o) = pack_bf16x2(lr, li);
-}
-
-__global__ void pack_rows_kernel(const float2 *__restrict__ yhat, __nv_bfloat16 *__restrict__ shi,
-                                 __nv_bfloat16 *__restrict__ slo, const int *__restrict__ soff, int L, int M, int ldb,
-                                 int B) {
-  pack_rows_body(blockIdx.x, blockIdx.y, yhat, shi, slo, soff, L, M, ldb, B);
-}
-
-// Repacking of several problems in one launch: CTA j belongs to problem s
-// with blk0[s] <= j < blk0[s + 1]; (bx, by) follow from gx[s].
-struct PackGroup {
-  const float2 *yhat[kMaxSeg];
-  __nv_bfloat16 *shi[kMaxSeg], *slo[kMaxSeg];
-  const int *soff[kMaxSeg];
-  int L[kMaxSeg], M[kMaxSeg], ldb[kMaxSeg], B[kMaxSeg], gx[kMaxSeg];
-  int blk0[kMaxSeg + 1];
-  int nseg;
-};
-
-__global__ void pack_rows_grouped(const __grid_constant__ PackGroup g) {
-  int s = 0;
-  while (s + 1 < g.nseg && (int)blockIdx.x >= g.blk0[s + 1]) s++;
-  const int local = blockIdx.x - g.blk0[s];
-  pack_rows_body(local % g.gx[s], local / g.gx[s], g.yhat[s], g.shi[s], g.slo[s], g.soff[s], g.L[s], g.M[s],
-                 g.ldb[s], g.B[s]);
-}
-
 // Transposes between the API layout xhat[b][l][m] (complex64) and the
 // l-major forms of the tensor-core path, through 32 x 32 shared tiles so
 // that both sides are read and written in contiguous runs.  One CTA (32 x 8
@@ -858,8 +839,7 @@ __global__ void pack_rows_grouped(const __grid_constant__ PackGroup g) {
 struct RowsT {
   const float *rows;   // finalize: FP32 rows [l M + m][ldr]
   float2 *xhat;        // finalize: destination; pack: source
-  __nv_bfloat16 *shi, *slo;  // pack: split rows [soff[2m + p] + i][ldb]
-  const int *soff;
+  __nv_bfloat16 *shi, *slo;  // pack: split rows [l M + m][ldb]
   int L, M, B, ld;     // ld = ldr (finalize) or ldb (pack)
 };
 
@@ -881,7 +861,7 @@ __device__ __forceinline__ void finalize_tile(const RowsT &a, int mt, int l, int
   }
 }
 
-// split rows S[soff[2m + p] + i][2b, 2b + 1] = hi/lo of xhat[b][l][m], m <= l.
+// split rows S[l M + m][2b, 2b + 1] = hi/lo of xhat[b][l][m], m <= l.
 __device__ __forceinline__ void pack_tile(const RowsT &a, int mt, int l, int bt, float2 (*T)[33]) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int m0 = mt * 32, b0 = bt * 32;
@@ -895,8 +875,7 @@ __device__ __forceinline__ void pack_tile(const RowsT &a, int mt, int l, int bt,
   for (int mm = ty; mm < 32; mm += 8) {
     const int m = m0 + mm, b = b0 + tx;
     if (m > l || m >= a.M || b >= a.B) continue;
-    const int d = l - m;
-    const int64_t o = (int64_t)(a.soff[2 * m + (d & 1)] + (d >> 1)) * a.ld + 2 * b;
+    const int64_t o = ((int64_t)l * a.M + m) * a.ld + 2 * b;
     const float2 v = T[mm][tx];
     __nv_bfloat16 hr, lr, hi_, li;
     split_bf16(v.x, hr, lr);
@@ -1106,7 +1085,7 @@ size_t extra_smem(bool gen, TcParams &P) {
              sizeof(Seed) * 256 * kSeedAhead;
   }
   cbytes = (cbytes + 1023) / 1024 * 1024;
-  if (kMode != kFilt) cbytes += 4 * 8192;  // epilogue staging
+  cbytes += kMode != kFilt ? 4 * 8192 : 4 * 4096;  // epilogue staging
   return cbytes;
 }
 
@@ -1129,7 +1108,7 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
   P.stages = stages;
   // the inverse's staging follows the generators' area (stage sizes and the
   // generators' area are multiples of 1024 bytes)
-  P.epi_off = (int)((size_t)stages * sb + extra - (kMode != kFilt ? 4 * 8192 : 0));
+  P.epi_off = (int)((size_t)stages * sb + extra - (kMode != kFilt ? 4 * 8192 : 4 * 4096));
   const size_t smem = 1024 + (size_t)stages * sb + extra;
   const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
@@ -1213,6 +1192,28 @@ bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLa
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int M, int L, bool load,
+                          int box_cols) {
+  auto enc = encoder();
+  if (!enc) return false;
+  if (!load && box_cols != 32 && box_cols != 16) return false;
+  if (!ptr) {
+    *tm = CUtensorMap{};
+    return true;
+  }
+  // dims (column, m, l); loads: 64 columns x every second l (64 of them),
+  // stores: box_cols columns x 32 m of one l
+  cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)M, (cuuint64_t)L};
+  cuuint64_t gstr[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * M};
+  cuuint32_t box_l[3] = {64, 1, 128}, box_s[3] = {(cuuint32_t)box_cols, 32, 1};
+  cuuint32_t es_l[3] = {1, 1, 2}, es_s[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = load ? CU_TENSOR_MAP_SWIZZLE_128B
+                                     : (box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE);
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), gdim, gstr,
+             load ? box_l : box_s, load ? es_l : es_s, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols) {
@@ -1369,6 +1370,7 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
                              const CUtensorMap &ta_lo, const CUtensorMap &tw_hi, const CUtensorMap &tw_lo,
                              __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx, int nwr, int Bm, int Cin,
                              int Cout, cudaStream_t st) {
+  if (s_hi != T.srows_hi || lds != T.lds) return cudaErrorInvalidValue;  // the store maps describe these rows
   if (nftiles == 0 || Bm <= 0) return cudaSuccess;
   TcParams P{};
   P.nseg = 1;
@@ -1380,7 +1382,6 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.Bm = Bm;
   P.ntiles = nftiles * Bm * P.ntn;
   P.ftiles = reinterpret_cast<const FiltTile *>(ftiles);
-  P.soff = T.soff;
   P.kx = kx;
   P.nwr = nwr;
   P.cin = Cin;
@@ -1391,6 +1392,10 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.err = T.err;
   P.maps[0].a_hi = ta_hi;
   P.maps[0].a_lo = ta_lo;
+  P.maps[0].o32_hi = T.so32_hi;
+  P.maps[0].o32_lo = T.so32_lo;
+  P.maps[0].o16_hi = T.so16_hi;
+  P.maps[0].o16_lo = T.so16_lo;
   P.maps[0].b_hi = tw_hi;
   P.maps[0].b_lo = tw_lo;
   return launch_persistent<kFilt>(T.split, false, P, TcLaunch{}, st);
@@ -1405,7 +1410,7 @@ cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaS
     const RowsItem &it = items[i];
     if (it.B <= 0) continue;
     const int s = g.nseg++;
-    g.seg[s] = RowsT{it.rows, it.xhat, it.shi, it.slo, it.soff, it.L, it.M, it.B, it.ld};
+    g.seg[s] = RowsT{it.rows, it.xhat, it.shi, it.slo, it.L, it.M, it.B, it.ld};
     g.blk0[s] = (int)blk;
     blk += (int64_t)((it.M + 31) / 32) * it.L * ((it.B + 31) / 32);
   }
@@ -1416,43 +1421,6 @@ cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaS
     rows_transpose_kernel<true><<<(unsigned)blk, 256, 0, st>>>(g);
   else
     rows_transpose_kernel<false><<<(unsigned)blk, 256, 0, st>>>(g);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pack_rows_group(const PackItem *items, int n, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  if (n > kMaxSeg) return cudaErrorInvalidValue;
-  PackGroup g{};
-  int64_t blk = 0;
-  for (int i = 0; i < n; i++) {
-    const PackItem &it = items[i];
-    if (it.B <= 0) continue;
-    const int s = g.nseg++;
-    g.yhat[s] = it.yhat;
-    g.shi[s] = it.shi;
-    g.slo[s] = it.slo;
-    g.soff[s] = it.soff;
-    g.L[s] = it.L;
-    g.M[s] = it.M;
-    g.ldb[s] = it.ldb;
-    g.B[s] = it.B;
-    g.gx[s] = (int)(((int64_t)leg_rows(it.L, 0, 0) * it.B + 255) / 256);
-    g.blk0[s] = (int)blk;
-    blk += (int64_t)g.gx[s] * 2 * it.M;
-  }
-  g.blk0[g.nseg] = (int)blk;
-  if (blk == 0) return cudaSuccess;
-  if (blk > 0x7fffffff) return cudaErrorInvalidValue;
-  pack_rows_grouped<<<(unsigned)blk, 256, 0, st>>>(g);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,
-                             int M, int ldb, int B, cudaStream_t st) {
-  if (B <= 0) return cudaSuccess;
-  const int64_t maxrows = (int64_t)leg_rows(L, 0, 0) * B;
-  dim3 grid((unsigned)((maxrows + 255) / 256), 2 * M);
-  pack_rows_kernel<<<grid, 256, 0, st>>>(yhat, shi, slo, soff, L, M, ldb, B);
   return cudaGetLastError();
 }
 

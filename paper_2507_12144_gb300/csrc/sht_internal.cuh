@@ -25,7 +25,8 @@ struct RadixPlan {
 
 // One tile of a Legendre contraction: order m, parity p of l + m, first row
 // (or latitude), and for the tensor-core kernels the row of its first
-// operand (forward: table row roff[2m+p] + r0; inverse: soff[2m+p]).
+// operand (forward: table row roff[2m+p] + r0; inverse: the first degree
+// m + p of the block).
 struct __align__(16) LegTile {
   int m;
   int p;
@@ -61,18 +62,21 @@ struct TableF32 {
 // of the bf16 hi/lo Legendre tables (forward layout [rows][Kp64] with block
 // (m, p) at row roff[2m+p]; transposed layout [(2m+p) Kh + k'][Ip64]), of the
 // Fourier workspace F[(2m+p) Kh + k'][ldcb] (hi, lo) and of the internal
-// coefficient rows S[soff[2m+p] + i][ldcb] (hi, lo), plus the error word.
+// coefficient rows S[l M + m][ldcb] (hi, lo, l-major), plus the error word.
 struct TcPlanView {
   CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;  // bf16 table (streamed)
-  CUtensorMap f_hi, f_lo, s_hi, s_lo;
+  CUtensorMap f_hi, f_lo, s_hi, s_lo;  // s: 3-D (column, m, l) loads of every second l
   CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
   CUtensorMap g32, g16;    // FP32 inverse output rows [2M][Kh][ldc], store boxes 32 x 32, 16 x 32
   const float *gw;         // their base (the FP32 workspace) and row stride
   int gw_ldc;
   CUtensorMap xo32_hi, xo32_lo, xo16_hi, xo16_lo;  // l-major rows [L][M][ldx], every second l, store boxes
+  CUtensorMap so32_hi, so32_lo, so16_hi, so16_lo;  // internal rows S [L][M][ldcb], store boxes of 32 m
+  const __nv_bfloat16 *srows_hi;                    // their base and row stride
+  int lds;
   const __nv_bfloat16 *xrows_hi;                    // their base and row stride
   int ldx;
-  const int *roff, *soff;
+  const int *roff;
   // on-chip Legendre table: seeds (16 B each) every 32 rows
   const void *seeds;
   const float4 *coef;        // two-step coefficients [(2m + p) ldC + i]
@@ -101,6 +105,12 @@ bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLa
 // bf16 l-major rows [L][M][ldx] as a 3-D map whose store boxes take box_cols
 // columns of 32 rows l, l + 2, ..., l + 62 (element stride 2 along l).
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols);
+// The internal coefficient rows S [L][M][ld] (bf16, l-major) as a 3-D map
+// (column, m, l): load = true: boxes of 64 columns x every second l (64 of
+// them, 128-byte swizzle) for the inverse contraction; load = false: store
+// boxes of box_cols columns x 32 m of one l (the filter's epilogue).
+bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int M, int L, bool load,
+                          int box_cols);
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64],
 // transposed layout [(2m + p) Kh + k'][Ip64]).
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
@@ -156,29 +166,18 @@ struct TcLaunch {
 // Up to 8 problems of equal precision and table source in one persistent
 // launch (inverse = 0: forward contraction, 1: inverse).
 cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, const TcLaunch &cfg, cudaStream_t st);
-// API-layout coefficients -> internal bf16 hi/lo rows.
-struct PackItem {
-  const float2 *yhat;
-  __nv_bfloat16 *shi, *slo;
-  const int *soff;
-  int L, M, ldb, B;
-};
-cudaError_t launch_pack_rows_group(const PackItem *items, int n, cudaStream_t st);
 // Coalesced transposes of up to 8 problems per launch.
 //   pack = false: xhat[b][l][m] = rows[l M + m][2b + {re, im}] (m <= l; zero
 //                 for m > l), rows FP32 with row stride ld floats;
-//   pack = true:  split bf16 rows S[soff[2m + p] + i][2b + {re, im}] (row
-//                 stride ld) from xhat, m <= l (l = m + p + 2 i).
+//   pack = true:  split bf16 rows S[l M + m][2b + {re, im}] (row stride ld)
+//                 from xhat, m <= l.
 struct RowsItem {
   const float *rows;
   float2 *xhat;
   __nv_bfloat16 *shi, *slo;
-  const int *soff;
   int L, M, B, ld;
 };
 cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaStream_t st);
-cudaError_t launch_pack_rows(const float2 *yhat, __nv_bfloat16 *shi, __nv_bfloat16 *slo, const int *soff, int L,
-                             int M, int ldb, int B, cudaStream_t st);
 // Longitude analysis writing the folded Fourier workspace as bf16 hi/lo
 // (same contract as launch_r2c).
 cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,
@@ -342,7 +341,6 @@ struct sht_plan_s {
   float *d_x2h = nullptr, *d_x2l = nullptr;  // squared latitudes as FP32 hi + lo
   int ldcb = 0;                // bf16 row stride of the workspaces (elements)
   int64_t srows = 0;           // rows of the internal coefficient layout
-  int *d_soff = nullptr;       // [2 M] first internal row of block (m, p)
   int ldx = 0;                 // columns of the l-major forward rows
   int ldr = 0;                 // columns of the FP32 forward rows (in spec_b)
   int max_channels = 0;        // capacity of the real filter weights
