@@ -520,7 +520,10 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   p->max_batch = o.max_batch;
   p->Kh = (nlat + 1) / 2;
   p->Khp = (p->Kh + 15) / 16 * 16;
-  p->ldc = (int)((2 * o.max_batch + 3) / 4 * 4);
+  // FP32 workspace row: 2 max_batch columns, rounded to 4 (FP32 plans) or to
+  // the 16-column groups of the parity-paired layout (tensor-core plans)
+  p->ldc = o.precision == SHT_PREC_FP32 ? (int)((2 * o.max_batch + 3) / 4 * 4)
+                                        : (int)((2 * o.max_batch + 15) / 16 * 16);
   p->radix = rp;
   make_grid(grid, nlat, p->x, p->s, p->w);
 
@@ -718,12 +721,16 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
 
   // workspaces
   p->ldcb = (int)std::max<int64_t>(64, (2 * o.max_batch + 7) / 8 * 8);
-  // folded Fourier workspaces, (m, p)-major: the Legendre kernels read and
-  // write whole (m, p) blocks of contiguous rows.  (A ring-major layout,
-  // which gives the longitude kernels adjacent rows, measured no faster for
-  // them and slower for the tensor-core gathers at 721 x 1440.)
+  // folded Fourier workspaces.  The analysis output is (m, p)-major: the
+  // forward contraction reads whole (m, p) blocks of contiguous rows.  The
+  // synthesis input of the tensor-core plans is parity-paired, so that the
+  // longitude synthesis reads E and O of 8 fields as one 128-byte line
+  // (the inverse contraction stores whole 16-column groups through TMA);
+  // the FP32 contraction writes (m, p)-major rows.  (A ring-major layout
+  // measured no faster for the longitude kernels at 721 x 1440 and slower
+  // for the tensor-core gathers.)
   p->lay_f = classic_layout(p->Kh, tc ? p->ldcb : p->ldc);
-  p->lay_g = classic_layout(p->Kh, p->ldc);
+  p->lay_g = tc ? pair_layout(p->Kh, p->ldc) : classic_layout(p->Kh, p->ldc);
   const size_t frow = (size_t)mmax * 2 * p->Kh;
   const size_t work = std::max(sizeof(float) * frow * p->ldc, tc ? 2 * sizeof(__nv_bfloat16) * frow * p->ldcb : 0);
   // spec_b also holds the FP32 l-major rows of the tensor-core forward into
@@ -773,6 +780,7 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     }
     T.gw = p->d_work;
     T.gw_ldc = p->ldc;
+    T.gpair = p->lay_g.cg;
     T.xrows_hi = p->d_x_hi;
     T.ldx = p->ldx;
     T.srows_hi = p->d_s_hi;

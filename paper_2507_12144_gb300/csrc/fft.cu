@@ -178,7 +178,7 @@ r2c_pairs_kernel(const float *__restrict__ x, Out out, int nlat, int nlon, int M
       E = cadd(Fk, Fs);
       O = csub(Fk, Fs);
     }
-    const int64_t col = 2 * (int64_t)(b0 + f);
+    const int64_t col = fold_col(fl, 2 * (int64_t)(b0 + f));
     out.put(fold_row(fl, m, 0, kp) + col, E);
     out.put(fold_row(fl, m, 1, kp) + col, O);
   }
@@ -207,7 +207,7 @@ c2r_pairs_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, 
   for (int t = threadIdx.x; t < nf * M; t += blockDim.x) {
     const int f = t / M;
     const int m = t - f * M;
-    const int64_t col = 2 * (int64_t)(b0 + f);
+    const int64_t col = fold_col(fl, 2 * (int64_t)(b0 + f));
     const float2 ge = *reinterpret_cast<const float2 *>(Gw + fold_row(fl, m, 0, kp) + col);
     const float2 go = *reinterpret_cast<const float2 *>(Gw + fold_row(fl, m, 1, kp) + col);
     const float c = 0.5f * mode_weight(m, n, inverse_weights);

@@ -334,8 +334,8 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
   const int fa = 2 * f2;
   if (b0 + fa >= B) return;
   const bool two = b0 + fa + 1 < B;
-  const int64_t col = 2 * (int64_t)(b0 + fa);
-  const int64_t pstride = fl.smp;  // E row -> O row
+  const int64_t col = fold_col(fl, 2 * (int64_t)(b0 + fa));  // 4 columns of one 16-column group
+  const int64_t pstride = fl.sp;                            // E row -> O row
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
@@ -348,7 +348,7 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
     const float2 *Zb = Za + BUF;
     int r = m0 % kQ, q = m0 / kQ;
     int64_t o = fold_row(fl, m0, 0, kq) + col;
-    for (int m = m0; m < M; m += kMStep, o += 2 * kMStep * pstride) {
+    for (int m = m0; m < M; m += kMStep, o += kMStep * fl.sm) {
       // X[m] sits at spec_index(m); X[N - m] at spec_index(N - m)
       const int im = r * (P + 1) + q;
       const int ic = m == 0 ? 0 : (r > 0 ? (kQ - r) * (P + 1) + (P - 1 - q) : P - q);
@@ -416,8 +416,8 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   // fields past B stage zeros (their sequences are not synthesised)
   const bool field_ok = b0 + fa < B;
   const bool two = b0 + fa + 1 < B;
-  const int64_t col = 2 * (int64_t)(b0 + fa);
-  const int64_t pstride = fl.smp;  // E row -> O row
+  const int64_t col = fold_col(fl, 2 * (int64_t)(b0 + fa));  // 4 columns of one 16-column group
+  const int64_t pstride = fl.sp;                            // E row -> O row
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
@@ -428,13 +428,13 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
     const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
     const float *g0 = Gw + fold_row(fl, m0, 0, kq) + col;
     float2 *Ba = bufs + (pq * kFB + fa) * BUF;
-    for (int mb = m0; mb < M; mb += kMStep * kBatch, g0 += (int64_t)2 * kMStep * kBatch * pstride) {
+    for (int mb = m0; mb < M; mb += kMStep * kBatch, g0 += (int64_t)kMStep * kBatch * fl.sm) {
       float4 ge[kBatch], go[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; u++) {
         ge[u] = go[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (mb + u * kMStep < M) {
-          const float *g = g0 + (int64_t)2 * u * kMStep * pstride;
+          const float *g = g0 + (int64_t)u * kMStep * fl.sm;
           if (two) {
             ge[u] = *reinterpret_cast<const float4 *>(g);
             go[u] = *reinterpret_cast<const float4 *>(g + pstride);

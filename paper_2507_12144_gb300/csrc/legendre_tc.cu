@@ -138,8 +138,9 @@ struct SegArgs {
   int xoff;               // offset of this problem's x^2 in shared memory
   const LegTile *tiles;   // (m, p, first row, TMA row) of the row tiles
   FwdOut fout;            // forward destination
-  float *Gw;              // inverse destination [(2m + p) Kh + k'][ldc]
+  float *Gw;              // inverse destination (folded FP32 workspace)
   int ldc;
+  int gpair;              // its layout: parity-paired (1) or (m, p)-major (0)
   // on-chip table: seeds [((2m + p) NB + j) Kh + k'], two-step
   // coefficients coef[(2m + p) ldC + i] = (alpha, beta, gamma, 0) of row i,
   // squared latitudes x^2 = x2h + x2l
@@ -466,9 +467,10 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       }
     }
   } else if (kMode == kInv) {
-    // FP32 folded rows (column, 2m + p, k') through the warp's two swizzled
-    // 32 x 32 staging buffers and TMA stores; rows k' >= Kh fall outside
-    // the map's extents and are not written
+    // FP32 folded rows through the warp's two swizzled 32 x 32 staging
+    // buffers and TMA stores of whole 16-column groups (the 5-D map of the
+    // workspace's layout); rows k' >= Kh fall outside the map's extents and
+    // are not written
     const SegMaps &mp = P.maps[ti.s];
     const int k0 = ti.r0 + q4 * 32;
     for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
@@ -487,10 +489,11 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
         for (int u = 0; u < 32; u++) v[u] = 0.f;
       }
       if (!half) {
-        // 128-byte rows, 16-byte chunk u at u ^ (row mod 8)
+        // two 64-byte rows (one per 16-column group) per k', 16-byte chunk
+        // q of a row at q ^ (k' mod 4) (the 64-byte swizzle of row 2 k' + g)
 #pragma unroll
         for (int u = 0; u < 8; u++)
-          *reinterpret_cast<float4 *>(buf + lane * 128 + ((u ^ (lane & 7)) << 4)) =
+          *reinterpret_cast<float4 *>(buf + lane * 128 + (u >> 2) * 64 + (((u & 3) ^ (lane & 3)) << 4)) =
               make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
       } else {
         // 64-byte rows, 16-byte chunk u at u ^ ((row / 2) mod 4)
@@ -502,7 +505,11 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, buf, ti.c0 + j0, 2 * ti.m + ti.p, k0);
+        const int g = (ti.c0 + j0) >> 4;
+        if (P.seg[ti.s].gpair)
+          tma_store_5d(half ? &mp.o16_hi : &mp.o32_hi, buf, 0, ti.p, g, k0, ti.m);
+        else
+          tma_store_5d(half ? &mp.o16_hi : &mp.o32_hi, buf, 0, g, k0, ti.p, ti.m);
         bulk_commit();
       }
     }
@@ -1168,14 +1175,36 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int ld, int nmp, int Kh,
                         int box_cols) {
   auto enc = encoder();
-  if (!enc || (box_cols != 32 && box_cols != 16)) return false;
-  cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)nmp, (cuuint64_t)Kh};
-  cuuint64_t gstr[2] = {(cuuint64_t)fl.smp * 4, (cuuint64_t)fl.sk * 4};
-  cuuint32_t box[3] = {(cuuint32_t)box_cols, 1, 32};
-  cuuint32_t es[3] = {1, 1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), gdim, gstr, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  if (!enc || (box_cols != 32 && box_cols != 16) || ld % 16 != 0 || nmp % 2 != 0) return false;
+  // 5-D view, strides increasing: (column in group, group, k', p, m) for
+  // the (m, p)-major layouts, (column in group, p, group, k', m) for the
+  // parity-paired one; a box is box_cols / 16 groups x 32 rows k' of one
+  // (m, p), laid out in shared memory as 64-byte rows (k', group) with the
+  // 64-byte swizzle (the box's inner extent equals the swizzle span)
+  const cuuint64_t ng = (cuuint64_t)ld / 16, M = (cuuint64_t)nmp / 2;
+  cuuint64_t gdim[5], gstr[4];
+  cuuint32_t box[5];
+  if (fl.cg) {
+    if (fl.sp != 16 || fl.sk != 2 * (int64_t)ld || fl.sm != fl.sk * Kh) return false;
+    const cuuint64_t d[5] = {16, 2, ng, (cuuint64_t)Kh, M};
+    const cuuint64_t st[4] = {16 * 4, 32 * 4, (cuuint64_t)fl.sk * 4, (cuuint64_t)fl.sm * 4};
+    const cuuint32_t b[5] = {16, 1, (cuuint32_t)box_cols / 16, 32, 1};
+    std::copy(d, d + 5, gdim);
+    std::copy(st, st + 4, gstr);
+    std::copy(b, b + 5, box);
+  } else {
+    if (fl.sk != ld || fl.sp != fl.sk * Kh || fl.sm != 2 * fl.sp) return false;  // (m, p)-major
+    const cuuint64_t d[5] = {16, ng, (cuuint64_t)Kh, 2, M};
+    const cuuint64_t st[4] = {16 * 4, (cuuint64_t)fl.sk * 4, (cuuint64_t)fl.sp * 4, (cuuint64_t)fl.sm * 4};
+    const cuuint32_t b[5] = {16, (cuuint32_t)box_cols / 16, 32, 1, 1};
+    std::copy(d, d + 5, gdim);
+    std::copy(st, st + 4, gstr);
+    std::copy(b, b + 5, box);
+  }
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float *>(ptr), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh) {
@@ -1185,8 +1214,9 @@ bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLa
     *tm = CUtensorMap{};
     return true;
   }
+  if (fl.cg || fl.sm != 2 * fl.sp) return false;  // rows (2m + p) at stride sp
   cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)nmp, (cuuint64_t)Kh};
-  cuuint64_t gstr[2] = {(cuuint64_t)fl.smp * 2, (cuuint64_t)fl.sk * 2};
+  cuuint64_t gstr[2] = {(cuuint64_t)fl.sp * 2, (cuuint64_t)fl.sk * 2};
   cuuint32_t box[3] = {64, 1, 64};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), gdim, gstr, box, es,
@@ -1286,6 +1316,7 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       g.fout = FwdOut{it.xhat, it.rows_hi, it.rows_lo, it.ldo, it.cin > 0 ? it.cin : 1, it.kx, it.rowsf, it.ldr};
       g.Gw = it.Gw;
       g.ldc = it.ldc;
+      g.gpair = T.gpair;
       g.seeds = reinterpret_cast<const Seed *>(T.seeds);
       g.coef = T.coef;
       g.x2h = T.x2h;

@@ -36,18 +36,31 @@ struct __align__(16) LegTile {
 
 // Layout of a folded Fourier workspace (longitude coefficients E / O of
 // ring pair k' for order m, parity p, fields as columns): row (m, p, k')
-// starts at (2m + p) smp + k' sk elements.  (m, p)-major: smp = Kh ld,
-// sk = ld (what the plans use); ring-major: smp = ld, sk = 2 mmax ld.  The
-// longitude kernels take any layout; the tensor-core contractions address
-// it through 3-D TMA maps built from the same strides.
+// starts at m sm + p sp + k' sk elements, and column n of a row sits at
+// n + cg (n & ~15).
+//   (m, p)-major ("classic"): sm = 2 Kh ld, sp = Kh ld, sk = ld, cg = 0;
+//   ring-major: sm = 2 ld, sp = ld, sk = 2 mmax ld, cg = 0;
+//   parity-paired: rows (m, k') of 2 ld elements in which 16-column groups
+//     of the two parities alternate (sm = 2 Kh ld, sp = 16, sk = 2 ld,
+//     cg = 1), so that E and O of 16 columns share one 128-byte line
+//     (FP32).
+// The longitude kernels take any layout whose 16-column groups hold the
+// columns they access together; the tensor-core contractions address it
+// through TMA maps built from the same strides.
 struct FoldLayout {
-  int64_t smp, sk;
+  int64_t sm, sp, sk;
+  int cg;
 };
 __host__ __device__ inline int64_t fold_row(const FoldLayout &fl, int m, int p, int k) {
-  return (2 * (int64_t)m + p) * fl.smp + (int64_t)k * fl.sk;
+  return (int64_t)m * fl.sm + p * fl.sp + (int64_t)k * fl.sk;
 }
-inline FoldLayout classic_layout(int Kh, int ld) { return FoldLayout{(int64_t)Kh * ld, (int64_t)ld}; }
-inline FoldLayout ring_layout(int M, int ld) { return FoldLayout{(int64_t)ld, 2 * (int64_t)M * ld}; }
+__host__ __device__ inline int64_t fold_col(const FoldLayout &fl, int64_t n) { return fl.cg ? n + (n & ~15) : n; }
+inline FoldLayout classic_layout(int Kh, int ld) {
+  return FoldLayout{2 * (int64_t)Kh * ld, (int64_t)Kh * ld, (int64_t)ld, 0};
+}
+inline FoldLayout ring_layout(int M, int ld) { return FoldLayout{2 * (int64_t)ld, (int64_t)ld, 2 * (int64_t)M * ld, 0}; }
+// ld a multiple of 16
+inline FoldLayout pair_layout(int Kh, int ld) { return FoldLayout{2 * (int64_t)Kh * ld, 16, 2 * (int64_t)ld, 1}; }
 
 // Device-side view of the folded FP32 Legendre table.  For order m and
 // parity p the rows are l = m + p + 2 i (i < nrows(m, p)), the columns are
@@ -67,9 +80,10 @@ struct TcPlanView {
   CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;  // bf16 table (streamed)
   CUtensorMap f_hi, f_lo, s_hi, s_lo;  // s: 3-D (column, m, l) loads of every second l
   CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
-  CUtensorMap g32, g16;    // FP32 inverse output rows [2M][Kh][ldc], store boxes 32 x 32, 16 x 32
-  const float *gw;         // their base (the FP32 workspace) and row stride
+  CUtensorMap g32, g16;    // FP32 inverse output (folded workspace), store boxes 32 x 32, 16 x 32
+  const float *gw;         // their base (the FP32 workspace), row stride and layout
   int gw_ldc;
+  int gpair;               // 1: parity-paired layout (else (m, p)-major)
   CUtensorMap xo32_hi, xo32_lo, xo16_hi, xo16_lo;  // l-major rows [L][M][ldx], every second l, store boxes
   CUtensorMap so32_hi, so32_lo, so16_hi, so16_lo;  // internal rows S [L][M][ldcb], store boxes of 32 m
   const __nv_bfloat16 *srows_hi;                    // their base and row stride

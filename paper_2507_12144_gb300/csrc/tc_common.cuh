@@ -125,6 +125,16 @@ __device__ __forceinline__ void tma_store_3d(const void *tmap, const void *src, 
                "r"(smem_addr(src)), "r"(x), "r"(y), "r"(z)
                : "memory");
 }
+// 5-D tiled store of a shared-memory box to global memory (bulk async
+// group); elements outside the tensor's extents are not written.
+__device__ __forceinline__ void tma_store_5d(const void *tmap, const void *src, int c0, int c1, int c2, int c3,
+                                             int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(tmap)),
+      "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Wait until at most N bulk groups of this thread still read shared memory.
 template <int N>
