@@ -232,6 +232,40 @@ sht_status_t sht_forward_static_scratch(sht_plan_t plan, const float *x,
                                         void *xhat, int64_t B, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Host-resident fields through the spectral block.  A pipe owns `depth`
+ * device staging slots (one input and one output array of the block's
+ * shape each) and two copy streams.  sht_pipe_block(x_host -> y_host) is
+ * asynchronous: it queues the host-to-device copy of x_host on the pipe's
+ * input stream, sht_spectral_block on `stream` once that copy landed, and
+ * the device-to-host copy into y_host on the pipe's output stream, with
+ * events so that successive calls overlap (the next input copy and the
+ * previous output copy run while a block computes) and a slot is reused
+ * only after its previous input was consumed and its output drained.
+ *   - x_host: float32 [Bm][Cin][nlat][nlon], y_host: float32
+ *     [Bm][Cout][nlat][nlon], host memory, 16-byte aligned; page-locked
+ *     (cudaHostAlloc / pinned) memory is needed for the copies to overlap.
+ *     The caller keeps x_host unchanged, and reads y_host only, after
+ *     sht_pipe_wait.  W: device complex64 [lmax][Cout][Cin], read when
+ *     the block runs.
+ *   - Errors: argument errors before anything is queued; CUDA errors as
+ *     SHT_ERR_CUDA; the block's own conditions as sht_spectral_block.
+ *   - The paper has no counterpart (it trains from data already on the
+ *     GPU); this is the serving path for fields held by the host. */
+typedef struct sht_pipe_s *sht_pipe_t;
+
+/* depth: 1 .. 4 slots (2 overlaps input copy, block and output copy of
+ * neighbouring calls).  Allocates depth * (in + out) bytes of device
+ * memory on the plan's device.  The plan must outlive the pipe. */
+sht_status_t sht_pipe_create(sht_pipe_t *out, sht_plan_t plan, int64_t Bm,
+                             int Cin, int Cout, int depth);
+sht_status_t sht_pipe_block(sht_pipe_t pipe, const float *x_host,
+                            const void *W, float *y_host, void *stream);
+/* Block the calling thread until every queued output copy has finished. */
+sht_status_t sht_pipe_wait(sht_pipe_t pipe);
+/* Wait for the pipe's copies, then free its slots, streams and events. */
+sht_status_t sht_pipe_destroy(sht_pipe_t pipe);
+
+/* ---------------------------------------------------------------------------
  * Batched transforms over several grids.  Ensemble members are independent
  * of one another (the ensemble-parallel computations of the section on
  * simultaneous model-, data- and ensemble-parallelism are embarrassingly

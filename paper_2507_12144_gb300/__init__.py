@@ -20,7 +20,7 @@ import torch
 from . import _abi
 from ._abi import ShtError
 
-__all__ = ["Plan", "Batch", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
+__all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
            "SpectralBlock", "spectral_block", "ShtError"]
 
@@ -352,6 +352,57 @@ class Batch:
         if getattr(self, "_h", None) is not None:
             h, self._h = self._h, None
             _abi.check(_abi.lib().sht_batch_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipe:
+    """Spectral blocks of host-resident fields: ``block(x_host, W, y_host)``
+    queues the copy of x_host (float32 [Bm, Cin, nlat, nlon], CPU, pinned
+    for overlap) into one of ``depth`` device slots, the block on the
+    current CUDA stream, and the copy of the result into y_host (float32
+    [Bm, Cout, nlat, nlon], CPU); successive calls overlap.  ``wait()``
+    blocks until every queued result is in host memory."""
+
+    def __init__(self, plan: "Plan", Bm: int, Cin: int, Cout: int, depth: int = 2):
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().sht_pipe_create(ctypes.byref(h), plan.handle, int(Bm), int(Cin), int(Cout), int(depth)))
+        self._h = h
+        self.plan = plan
+        self.shape_in = (int(Bm), int(Cin), plan.nlat, plan.nlon)
+        self.shape_out = (int(Bm), int(Cout), plan.nlat, plan.nlon)
+        self._inflight = []
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("pipe has been destroyed")
+        return self._h
+
+    def block(self, x_host: torch.Tensor, W: torch.Tensor, y_host: torch.Tensor) -> None:
+        for name, t, shape in (("x_host", x_host, self.shape_in), ("y_host", y_host, self.shape_out)):
+            if not isinstance(t, torch.Tensor) or t.device.type != "cpu" or t.dtype != torch.float32:
+                raise TypeError(f"{name} must be a float32 CPU tensor")
+            if tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous {shape} tensor")
+        W = _need(W, torch.complex64, "W", self.plan.device)
+        st = torch.cuda.current_stream(self.plan.device).cuda_stream
+        _abi.check(_abi.lib().sht_pipe_block(self.handle, _ptr(x_host), _ptr(W), _ptr(y_host), ctypes.c_void_p(st)))
+        self._inflight.append((x_host, W, y_host))
+
+    def wait(self) -> None:
+        _abi.check(_abi.lib().sht_pipe_wait(self.handle))
+        self._inflight.clear()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            h, self._h = self._h, None
+            _abi.check(_abi.lib().sht_pipe_destroy(h))
+            self._inflight.clear()
 
     def __del__(self):
         try:

@@ -76,6 +76,10 @@ SIGNATURES = {
     "sht_batch_profile_begin": ([_p, _i], _i),
     "sht_batch_profile_collect": ([_p, _i64p, ctypes.POINTER(ctypes.c_double)], _i),
     "sht_batch_destroy": ([_p], _i),
+    "sht_pipe_create": ([ctypes.POINTER(_p), _p, _i64, _i, _i, _i], _i),
+    "sht_pipe_block": ([_p, _p, _p, _p, _p], _i),
+    "sht_pipe_wait": ([_p], _i),
+    "sht_pipe_destroy": ([_p], _i),
 }
 
 _lock = threading.Lock()

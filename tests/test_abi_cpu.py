@@ -124,3 +124,14 @@ def test_batch_rejects_bad_arguments_before_any_cuda_call(lib):
     assert lib.sht_batch_destroy(None) == 1
     assert lib.sht_batch_stage_count(None) == 0
     assert lib.sht_batch_stage_name(None, 0) == b"?"
+
+
+def test_pipe_rejects_bad_arguments_before_any_cuda_call(lib):
+    h = ctypes.c_void_p()
+    assert lib.sht_pipe_create(None, None, 1, 1, 1, 2) == 1
+    assert lib.sht_pipe_create(ctypes.byref(h), None, 1, 1, 1, 2) == 1  # NULL plan
+    assert b"plan" in lib.sht_last_error_message() and not h.value
+    assert lib.sht_pipe_block(None, None, None, None, None) == 1
+    assert b"pipe" in lib.sht_last_error_message()
+    assert lib.sht_pipe_wait(None) == 1
+    assert lib.sht_pipe_destroy(None) == 0
