@@ -118,9 +118,8 @@ typedef struct {
   int precision;      /* sht_precision_t, default SHT_PREC_FP32            */
   int device;         /* CUDA device ordinal, default: the current device  */
   int64_t max_batch;  /* fields per internal chunk, default 256            */
-  int max_channels;   /* tensor-core plans: largest Cin / Cout of the
-                         fused block (sizes the real filter weights);
-                         0 = min(max_batch, 128)                            */
+  int max_channels;   /* tensor-core plans: largest Cin / Cout accepted
+                         by the fused block; 0 = min(max_batch, 128)        */
   int table_source;   /* sht_table_source_t, default SHT_TABLE_STREAMED    */
   int reserved[6];    /* must be zero                                      */
 } sht_plan_opts;
@@ -377,7 +376,8 @@ typedef enum {
   SHT_KERNEL_LEG_INV = 5,    /* inverse Legendre contraction              */
   SHT_KERNEL_C2R = 6,        /* longitude synthesis (inverse FFT)         */
   SHT_KERNEL_PACK = 7,       /* API coefficients -> internal bf16 rows    */
-  SHT_KERNEL_FILTER_PREP = 8, /* real bf16 form of the filter weights    */
+  SHT_KERNEL_FILTER_PREP = 8, /* unused (the filter forms its weights on
+                                 chip); kept so the numbering is stable   */
   SHT_KERNEL_FINALIZE = 9,   /* FP32 l-major rows -> API xhat (+ zeros)   */
   SHT_KERNEL_COUNT = 10
 } sht_kernel_t;

@@ -183,8 +183,6 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_roff);
   cudaFree(p->d_x_hi);
   cudaFree(p->d_x_lo);
-  cudaFree(p->d_wr_hi);
-  cudaFree(p->d_wr_lo);
   cudaFree(p->d_ftiles);
   cudaFree(p->d_s_hi);
   cudaFree(p->d_s_lo);
@@ -408,21 +406,9 @@ sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, in
   if (!tc_encode_2d(&ta_hi, p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx) ||
       !tc_encode_2d(&ta_lo, split ? p->d_x_lo : p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx))
     return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
-  // real weights: [L][nwr][kw] bf16 hi/lo (kw = 2 Cin rounded to 64, zero
-  // past 2 Cin), TMA boxes of 64 columns x Nt rows
-  const int kw = (2 * Cin + 63) / 64 * 64;
-  const int ntile_n = (2 * Cout + 255) / 256;
-  const int Nt = ((2 * Cout + ntile_n - 1) / ntile_n + 15) / 16 * 16;
-  CUtensorMap tw_hi, tw_lo;
-  if (!tc_encode_2d(&tw_hi, p->d_wr_hi, kw, (int64_t)p->L * nwr, 64, Nt) ||
-      !tc_encode_2d(&tw_lo, p->d_wr_lo, kw, (int64_t)p->L * nwr, 64, Nt))
-    return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the filter weights");
-  cudaError_t e = traced(p, SHT_KERNEL_FILTER_PREP, st, [&] {
-    return launch_filter_prep((const float2 *)W, p->d_wr_hi, p->d_wr_lo, p->L, Cout, Cin, nwr, kw, st);
-  });
-  if (e != cudaSuccess) return cuda_fail(e, "filter weight preparation launch");
+  cudaError_t e;
   e = traced(p, SHT_KERNEL_FILTER, st, [&] {
-    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, ta_hi, ta_lo, tw_hi, tw_lo, p->d_s_hi,
+    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, ta_hi, ta_lo, (const float2 *)W, p->d_s_hi,
                             data_lo(p, p->d_s_lo), p->ldcb, kx, nwr, (int)nb, Cin, Cout, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "filter launch");
@@ -756,22 +742,17 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     p->max_channels = o.max_channels > 0 ? o.max_channels : (int)std::min<int64_t>(o.max_batch, 128);
     p->ldx = (int)std::max<int64_t>(64, (2 * o.max_batch + 63) / 64 * 64);
     const size_t xbytes = sizeof(__nv_bfloat16) * (size_t)lmax * mmax * p->ldx;
-    const int cm = p->max_channels;
-    p->wr_capacity = (int64_t)lmax * ((2 * cm + 15) / 16 * 16) * ((2 * cm + 63) / 64 * 64);
-    const size_t wbytes = sizeof(__nv_bfloat16) * (size_t)p->wr_capacity;
     std::vector<int2> ftl;
     for (int l = 0; l < lmax; l++)
       for (int m0 = 0; m0 < std::min(l + 1, mmax); m0 += 128) ftl.push_back(make_int2(l, m0));
     p->n_ftiles = (int)ftl.size();
     if ((e = dev_alloc((void **)&p->d_x_hi, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = dev_alloc((void **)&p->d_x_lo, xbytes)) != cudaSuccess) return bail(e, "workspace allocation");
-    if ((e = dev_alloc((void **)&p->d_wr_hi, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
-    if ((e = dev_alloc((void **)&p->d_wr_lo, wbytes)) != cudaSuccess) return bail(e, "workspace allocation");
     if ((e = upload((int2 **)&p->d_ftiles, ftl)) != cudaSuccess) return bail(e, "tile upload");
     // the padding columns stay zero: the filter's K chunks read them
     if ((e = cudaMemset(p->d_x_hi, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
     if ((e = cudaMemset(p->d_x_lo, 0, xbytes)) != cudaSuccess) return bail(e, "workspace memset");
-    extra = 2 * sbytes + 2 * xbytes + 2 * wbytes;
+    extra = 2 * sbytes + 2 * xbytes;
     TcPlanView &T = p->tc;
     if (!(tc_encode_2d(&T.x_hi, p->d_x_hi, p->ldx, (int64_t)lmax * mmax, 64, 128) &&
           tc_encode_2d(&T.x_lo, p->d_x_lo, p->ldx, (int64_t)lmax * mmax, 64, 128))) {

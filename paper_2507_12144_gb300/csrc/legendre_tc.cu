@@ -170,6 +170,7 @@ struct TcParams {
   // filter (one problem)
   const FiltTile *ftiles;
   int L, M, Nt, Bm, ntn, kx, nwr, cin, cout, lds;
+  const float2 *W;        // complex weights [L][cout][cin] (B generated on chip)
   __nv_bfloat16 *s_hi, *s_lo;
   unsigned *err;
 };
@@ -279,7 +280,7 @@ struct TileWalk {
 template <int kMode, bool kSplit, bool kGen>
 __device__ __forceinline__ uint32_t chunk_tx_bytes(const TileInfo &ti) {
   const uint32_t abytes = (kMode != kFilt && kGen) ? 0u : (uint32_t)a_count(kMode, kSplit) * kABytes;
-  if (kMode == kFilt) return abytes + 2u * (uint32_t)ti.Nt * 128u;
+  if (kMode == kFilt) return abytes + (kGen ? 0u : 2u * (uint32_t)ti.Nt * 128u);
   return abytes + (uint32_t)b_count(kMode, kSplit) * (uint32_t)((ti.Nt + 63) / 64) * 8192u;
 }
 
@@ -327,8 +328,10 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
     if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
   }
   if (kMode == kFilt) {
-    tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
-    tma_load_2d(b_lo, &mp.b_lo, bar, kc * kKc, ti.b_row0);
+    if (!kGen) {
+      tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
+      tma_load_2d(b_lo, &mp.b_lo, bar, kc * kKc, ti.b_row0);
+    }
   } else if (kMode == kFwd) {
     // the folded data as (column, 2m + p, k'): 64 rows k' of one (m, p)
     const int nbox = (ti.Nt + 63) / 64;
@@ -703,7 +706,95 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
         load_chunk<kMode, kSplit, kGen>(st, ti, kc, P.Nmax, P.maps[ti.s], &full_bar[s]);
       }
     }
-  } else if (kGen && warp >= 8) {
+  } else if (kMode == kFilt && kGen && warp >= 8) {
+    // filter weights in their real form, generated per K chunk from the
+    // complex W[l][o][i]: row n = 2 o + a of the B operand multiplies
+    // (Re x_i, Im x_i) by (Re W, -Im W) (a = 0) or (Im W, Re W) (a = 1);
+    // zero past Cout and Cin.  bf16 hi/lo in the TMA SWIZZLE_128B K-major
+    // layout (row n at 128 n bytes, 16-byte chunk q at q ^ (n mod 8)).
+    // Thread item (o, q): 4 input channels of output channel o, both rows.
+    // The next chunk's weights are loaded before waiting for its stage.
+    constexpr int kItems = 4;  // (Nt / 2) x 8 items <= 1024 over 256 threads
+    const int gtid = threadIdx.x - 256;
+    const int na = a_count(kMode, kSplit);
+    const uint32_t bb = b_bytes_of(kMode, P.Nmax);
+    TileWalk<kMode> w(P);
+    TileInfo ti{};
+    ti.nk = 0;
+    int kc = 0;
+    auto next = [&]() {
+      kc++;
+      while (kc >= ti.nk) {
+        if (!w.more(P)) return false;
+        ti = w.take(P);
+        kc = 0;
+      }
+      return true;
+    };
+    float4 wv[kItems][2];
+    auto fetch = [&]() {
+      const float2 *Wl = P.W + (int64_t)ti.l * P.cout * P.cin;
+#pragma unroll
+      for (int u = 0; u < kItems; u++) {
+        const int e = gtid + 256 * u;
+        const int o = (ti.n0 >> 1) + (e >> 3), i0 = kc * (kKc / 2) + 4 * (e & 7);
+        wv[u][0] = wv[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < ti.Nt * 4 && o < P.cout) {
+          const float2 *src = Wl + (int64_t)o * P.cin + i0;
+          if (i0 + 4 <= P.cin && (P.cin & 1) == 0) {
+            wv[u][0] = __ldg(reinterpret_cast<const float4 *>(src));
+            wv[u][1] = __ldg(reinterpret_cast<const float4 *>(src) + 1);
+          } else {
+            float2 t4[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) t4[c] = i0 + c < P.cin ? __ldg(src + c) : make_float2(0.f, 0.f);
+            wv[u][0] = make_float4(t4[0].x, t4[0].y, t4[1].x, t4[1].y);
+            wv[u][1] = make_float4(t4[2].x, t4[2].y, t4[3].x, t4[3].y);
+          }
+        }
+      }
+    };
+    kc = -1;
+    bool have = next();
+    if (have) fetch();
+    for (uint32_t g = 0; have; g++) {
+      const int s = (int)(g % (uint32_t)S);
+      const uint32_t use = g / (uint32_t)S;
+      if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, P.err);
+      unsigned char *bh = base + (size_t)s * sbytes + na * kABytes, *bl = bh + bb;
+#pragma unroll
+      for (int u = 0; u < kItems; u++) {
+        const int e = gtid + 256 * u;
+        if (e >= ti.Nt * 4) continue;
+        const int q = e & 7;
+        const float wr[4] = {wv[u][0].x, wv[u][0].z, wv[u][1].x, wv[u][1].z};
+        const float wi[4] = {wv[u][0].y, wv[u][0].w, wv[u][1].y, wv[u][1].w};
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+          const int n = 2 * (e >> 3) + a;
+          uint32_t h[4], r[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            const float v0 = a ? wi[c] : wr[c];   // multiplies Re x_i
+            const float v1 = a ? wr[c] : -wi[c];  // multiplies Im x_i
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
+            const float2 hf = __bfloat1622float2(hh);
+            const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+            h[c] = *reinterpret_cast<const uint32_t *>(&hh);
+            r[c] = *reinterpret_cast<const uint32_t *>(&ll);
+          }
+          const uint32_t off = (uint32_t)n * 128u + ((uint32_t)(q ^ (n & 7)) << 4);
+          *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4 *>(bl + off) = make_uint4(r[0], r[1], r[2], r[3]);
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[s]);
+      have = next();
+      if (have) fetch();
+    }
+  } else if (kMode != kFilt && kGen && warp >= 8) {
     // table generators.  Shared memory after the stage ring: the current
     // tile's two-step coefficients (the next tile's are loaded into
     // registers meanwhile), x^2 of every problem's latitudes, and a ring of
@@ -921,33 +1012,6 @@ __global__ void __launch_bounds__(256) rows_transpose_kernel(const __grid_consta
 // WR[l][n][k] (bf16 hi/lo), n < nwr rows, k < kx columns, from W[l][o][i]:
 // n = 2 o + a, k = 2 i + c: (a, c) = (0, 0) Re W, (0, 1) -Im W, (1, 0) Im W,
 // (1, 1) Re W; zero outside 2 Cout x 2 Cin.
-__global__ void filter_prep_kernel(const float2 *__restrict__ W, __nv_bfloat16 *__restrict__ whi,
-                                   __nv_bfloat16 *__restrict__ wlo, int L, int Cout, int Cin, int nwr, int kx) {
-  // one thread per (l, n, 4 input channels): 8 columns, one 16-byte store each
-  const int kq = kx / 8;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)L * nwr * kq) return;
-  const int iq = (int)(e % kq);
-  const int64_t ln = e / kq;
-  const int n = (int)(ln % nwr);
-  const int l = (int)(ln / nwr);
-  const int o = n >> 1, a = n & 1;
-  float v[8];
-#pragma unroll
-  for (int u = 0; u < 4; u++) {
-    const int i = 4 * iq + u;
-    float v0 = 0.f, v1 = 0.f;
-    if (o < Cout && i < Cin) {
-      const float2 w = W[((int64_t)l * Cout + o) * Cin + i];
-      v0 = a ? w.y : w.x;   // multiplies Re x_i
-      v1 = a ? w.x : -w.y;  // multiplies Im x_i
-    }
-    v[2 * u] = v0;
-    v[2 * u + 1] = v1;
-  }
-  put_bf16x8(whi, wlo, ln * kx + 8 * iq, v);
-}
-
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and
 // transposed layout [(m, p, k')][Ip64]); same recurrence as the FP32 table.
 __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bfloat16 *__restrict__ flo,
@@ -1106,7 +1170,6 @@ bool persistent_fits(bool split, bool gen, TcParams &P) {
 template <int kMode>
 cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch &cfg, cudaStream_t st) {
   if (P.ntiles <= 0) return cudaSuccess;
-  gen = gen && kMode != kFilt;
   const size_t sb = stage_bytes(kMode, split, P.Nmax);
   const size_t extra = extra_smem<kMode>(gen, P);
   if (extra == SIZE_MAX || 1024 + 2 * sb + extra > kSmemLimit) return cudaErrorInvalidValue;
@@ -1119,10 +1182,7 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
   const size_t smem = 1024 + (size_t)stages * sb + extra;
   const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
-  if constexpr (kMode == kFilt) {
-    e = split ? start_persistent<kMode, true, false>(grid, smem, P, st)
-              : start_persistent<kMode, false, false>(grid, smem, P, st);
-  } else if (gen) {
+  if (gen) {
     e = split ? start_persistent<kMode, true, true>(grid, smem, P, st)
               : start_persistent<kMode, false, true>(grid, smem, P, st);
   } else {
@@ -1390,17 +1450,9 @@ cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int nti
   return launch_leg_tc_group(1, &it, 1, TcLaunch{}, st);
 }
 
-cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
-                               int nwr, int kx, cudaStream_t st) {
-  const int64_t n = (int64_t)L * nwr * (kx / 8);
-  filter_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, whi, wlo, L, Cout, Cin, nwr, kx);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &ta_hi,
-                             const CUtensorMap &ta_lo, const CUtensorMap &tw_hi, const CUtensorMap &tw_lo,
-                             __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx, int nwr, int Bm, int Cin,
-                             int Cout, cudaStream_t st) {
+                             const CUtensorMap &ta_lo, const float2 *W, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo,
+                             int lds, int kx, int nwr, int Bm, int Cin, int Cout, cudaStream_t st) {
   if (s_hi != T.srows_hi || lds != T.lds) return cudaErrorInvalidValue;  // the store maps describe these rows
   if (nftiles == 0 || Bm <= 0) return cudaSuccess;
   TcParams P{};
@@ -1427,9 +1479,8 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.maps[0].o32_lo = T.so32_lo;
   P.maps[0].o16_hi = T.so16_hi;
   P.maps[0].o16_lo = T.so16_lo;
-  P.maps[0].b_hi = tw_hi;
-  P.maps[0].b_lo = tw_lo;
-  return launch_persistent<kFilt>(T.split, false, P, TcLaunch{}, st);
+  P.W = W;
+  return launch_persistent<kFilt>(T.split, true, P, TcLaunch{}, st);
 }
 
 cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaStream_t st) {

@@ -140,16 +140,14 @@ cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double 
 cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
                               __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
                               cudaStream_t st);
-// Real form WR of the filter weights (bf16 hi/lo, [L][nwr][kx]).
-cudaError_t launch_filter_prep(const float2 *W, __nv_bfloat16 *whi, __nv_bfloat16 *wlo, int L, int Cout, int Cin,
-                               int nwr, int kx, cudaStream_t st);
 // Tensor-core filter from the l-major rows to the inverse's split rows.
 // ftiles: (l, m0) pairs covering m <= l, m < M in steps of 128.
-// ta: the forward rows (width = members x kx, row stride ldx); tw: W_R.
+// ta: the forward rows (width = members x kx, row stride ldx); W: the
+// complex weights [L][Cout][Cin] (device), turned into the real bf16 hi/lo
+// form of each K chunk on chip; nwr = 2 Cout rounded to 16.
 cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &ta_hi,
-                             const CUtensorMap &ta_lo, const CUtensorMap &tw_hi, const CUtensorMap &tw_lo,
-                             __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, int lds, int kx, int nwr, int Bm, int Cin,
-                             int Cout, cudaStream_t st);
+                             const CUtensorMap &ta_lo, const float2 *W, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo,
+                             int lds, int kx, int nwr, int Bm, int Cin, int Cout, cudaStream_t st);
 // Inverse contraction on the tensor cores from the bf16 internal rows to the
 // FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
@@ -359,8 +357,6 @@ struct sht_plan_s {
   int ldr = 0;                 // columns of the FP32 forward rows (in spec_b)
   int max_channels = 0;        // capacity of the real filter weights
   __nv_bfloat16 *d_x_hi = nullptr, *d_x_lo = nullptr;  // l-major forward rows [L M][ldx]
-  __nv_bfloat16 *d_wr_hi = nullptr, *d_wr_lo = nullptr;  // real filter weights
-  int64_t wr_capacity = 0;     // elements of each of d_wr_hi / d_wr_lo
   void *d_ftiles = nullptr;    // filter tiles (l, m0)
   int n_ftiles = 0;
   __nv_bfloat16 *d_s_hi = nullptr, *d_s_lo = nullptr;  // bf16 internal rows [srows][ldcb]
