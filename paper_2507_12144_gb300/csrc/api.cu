@@ -766,10 +766,14 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     T.ldx = p->ldx;
     T.srows_hi = p->d_s_hi;
     T.lds = p->ldcb;
+    T.frows = reinterpret_cast<const float *>(p->d_spec_b);
+    T.ldr = p->ldr;
     if (!(tc_encode_lrows_bf16(&T.xo32_hi, p->d_x_hi, p->ldx, mmax, lmax, 32) &&
           tc_encode_lrows_bf16(&T.xo32_lo, p->d_x_lo, p->ldx, mmax, lmax, 32) &&
           tc_encode_lrows_bf16(&T.xo16_hi, p->d_x_hi, p->ldx, mmax, lmax, 16) &&
-          tc_encode_lrows_bf16(&T.xo16_lo, p->d_x_lo, p->ldx, mmax, lmax, 16))) {
+          tc_encode_lrows_bf16(&T.xo16_lo, p->d_x_lo, p->ldx, mmax, lmax, 16) &&
+          tc_encode_lrows_f32(&T.ro32, T.frows, p->ldr, mmax, lmax, 32) &&
+          tc_encode_lrows_f32(&T.ro16, T.frows, p->ldr, mmax, lmax, 16))) {
       free_plan(p);
       return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
     }

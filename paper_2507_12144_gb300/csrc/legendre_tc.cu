@@ -425,6 +425,46 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
         return;
       }
     }
+    if (g.fout.rowsf) {
+      // FP32 l-major rows [L][M][ldr]: 32 x 32 boxes of every second l
+      // through the warp's two swizzled staging buffers; rows past lmax and
+      // columns past ldr fall outside the map
+      const SegMaps &mp = P.maps[ti.s];
+      const int l0 = ti.m + ti.p + 2 * (ti.r0 + q4 * 32);
+      for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
+        const bool half = Nt - j0 == 16;
+        unsigned char *buf = stg + (c & 1) * 4096;
+        if (c >= 2) {
+          if (lane == 0) bulk_wait_read<1>();
+          __syncwarp();
+        }
+        float v[32];
+        tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+        if (!half) tmem_ld16(tl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
+        if (!half) {
+          // 128-byte rows, 16-byte chunk u at u ^ (row mod 8)
+#pragma unroll
+          for (int u = 0; u < 8; u++)
+            *reinterpret_cast<float4 *>(buf + lane * 128 + ((u ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        } else {
+          // 64-byte rows, 16-byte chunk u at u ^ ((row / 2) mod 4)
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            *reinterpret_cast<float4 *>(buf + lane * 64 + ((u ^ ((lane >> 1) & 3)) << 4)) =
+                make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_3d(half ? &mp.o16_hi : &mp.o32_hi, buf, ti.c0 + j0, ti.m, l0);
+          bulk_commit();
+        }
+      }
+      if (lane == 0) bulk_wait_read<0>();
+      __syncwarp();
+      return;
+    }
     const int r = ti.r0 + q4 * 32 + lane;
     const bool row_ok = r < leg_rows(g.L, ti.m, ti.p);
     const int l = ti.m + ti.p + 2 * r;
@@ -524,6 +564,7 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
     // 16-column chunks of one member (rows m > l receive values nothing
     // reads, rows m >= M are outside the map)
     const int ncol = min(Nt, 2 * P.cout - ti.n0);
+    if (ti.m + 32 * q4 > ti.l) return;  // this warp's 32 orders are all above l: nothing reads them
     if ((P.cout & 3) == 0 && (ncol & 15) == 0) {
       const SegMaps &mp = P.maps[0];
       store_rows_bf16_tma(tl, ncol, &mp.o32_hi, &mp.o32_lo, &mp.o16_hi, &mp.o16_lo, P.s_lo != nullptr,
@@ -1306,6 +1347,24 @@ bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tc_encode_lrows_f32(CUtensorMap *tm, const float *ptr, int ldr, int M, int L, int box_cols) {
+  auto enc = encoder();
+  if (!enc || (box_cols != 32 && box_cols != 16) || ldr % 4 != 0) return false;
+  if (!ptr) {
+    *tm = CUtensorMap{};
+    return true;
+  }
+  // dims (column, m, l); every second l, 32 of them per box; the box's
+  // inner extent (128 or 64 bytes) equals its swizzle span
+  cuuint64_t gdim[3] = {(cuuint64_t)ldr, (cuuint64_t)M, (cuuint64_t)L};
+  cuuint64_t gstr[2] = {(cuuint64_t)ldr * 4, (cuuint64_t)ldr * 4 * M};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, 1, 64};
+  cuuint32_t es[3] = {1, 1, 2};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
@@ -1392,9 +1451,10 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
         // store maps of the plan's l-major rows (used when the destination
         // is those rows)
         if (it.rows_hi && (it.rows_hi != T.xrows_hi || it.ldo != T.ldx)) return cudaErrorInvalidValue;
-        mp.o32_hi = T.xo32_hi;
+        if (it.rowsf && (it.rowsf != T.frows || it.ldr != T.ldr)) return cudaErrorInvalidValue;
+        mp.o32_hi = it.rowsf ? T.ro32 : T.xo32_hi;
         mp.o32_lo = T.xo32_lo;
-        mp.o16_hi = T.xo16_hi;
+        mp.o16_hi = it.rowsf ? T.ro16 : T.xo16_hi;
         mp.o16_lo = T.xo16_lo;
       } else {
         mp.a_hi = T.tab_inv_hi;

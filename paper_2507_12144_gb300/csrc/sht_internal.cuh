@@ -86,6 +86,9 @@ struct TcPlanView {
   int gpair;               // 1: parity-paired layout (else (m, p)-major)
   CUtensorMap xo32_hi, xo32_lo, xo16_hi, xo16_lo;  // l-major rows [L][M][ldx], every second l, store boxes
   CUtensorMap so32_hi, so32_lo, so16_hi, so16_lo;  // internal rows S [L][M][ldcb], store boxes of 32 m
+  CUtensorMap ro32, ro16;  // FP32 l-major rows of the API forward [L][M][ldr], every second l, store boxes
+  const float *frows;      // their base and row stride (floats)
+  int ldr;
   const __nv_bfloat16 *srows_hi;                    // their base and row stride
   int lds;
   const __nv_bfloat16 *xrows_hi;                    // their base and row stride
@@ -119,6 +122,9 @@ bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLa
 // bf16 l-major rows [L][M][ldx] as a 3-D map whose store boxes take box_cols
 // columns of 32 rows l, l + 2, ..., l + 62 (element stride 2 along l).
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols);
+// FP32 l-major rows [L][M][ldr] as the same 3-D store view (32- or
+// 16-column boxes, 128- or 64-byte swizzle).
+bool tc_encode_lrows_f32(CUtensorMap *tm, const float *ptr, int ldr, int M, int L, int box_cols);
 // The internal coefficient rows S [L][M][ld] (bf16, l-major) as a 3-D map
 // (column, m, l): load = true: boxes of 64 columns x every second l (64 of
 // them, 128-byte swizzle) for the inverse contraction; load = false: store
