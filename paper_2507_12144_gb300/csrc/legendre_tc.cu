@@ -982,50 +982,85 @@ struct RowsT {
   int L, M, B, ld;     // ld = ldr (finalize) or ldb (pack)
 };
 
+// A CTA moves kRowsL consecutive degrees of one (32 orders, 32 fields)
+// tile, so that each thread has 16 loads in flight before the exchange.
+constexpr int kRowsL = 4;
+using RowsTile = float2[kRowsL][32][33];
+
 // xhat[b][l][m] = rows[l M + m][2b, 2b + 1] for m <= l, zero for m > l.
-__device__ __forceinline__ void finalize_tile(const RowsT &a, int mt, int l, int bt, float2 (*T)[33]) {
+__device__ __forceinline__ void finalize_tile(const RowsT &a, int mt, int lg, int bt, RowsTile &T) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int m0 = mt * 32, b0 = bt * 32;
-  for (int mm = ty; mm < 32; mm += 8) {
-    const int m = m0 + mm, b = b0 + tx;
-    float2 v = make_float2(0.f, 0.f);
-    if (m <= l && m < a.M && b < a.B)
-      v = *reinterpret_cast<const float2 *>(a.rows + ((int64_t)l * a.M + m) * a.ld + 2 * b);
-    T[mm][tx] = v;
+  float2 v[kRowsL][4];
+#pragma unroll
+  for (int q = 0; q < kRowsL; q++) {
+    const int l = lg * kRowsL + q;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int m = m0 + ty + 8 * k, b = b0 + tx;
+      v[q][k] = make_float2(0.f, 0.f);
+      if (l < a.L && m <= l && m < a.M && b < a.B)
+        v[q][k] = *reinterpret_cast<const float2 *>(a.rows + ((int64_t)l * a.M + m) * a.ld + 2 * b);
+    }
   }
+#pragma unroll
+  for (int q = 0; q < kRowsL; q++)
+#pragma unroll
+    for (int k = 0; k < 4; k++) T[q][ty + 8 * k][tx] = v[q][k];
   __syncthreads();
-  for (int bb = ty; bb < 32; bb += 8) {
-    const int b = b0 + bb, m = m0 + tx;
-    if (b < a.B && m < a.M) a.xhat[((int64_t)b * a.L + l) * a.M + m] = T[tx][bb];
+#pragma unroll
+  for (int q = 0; q < kRowsL; q++) {
+    const int l = lg * kRowsL + q;
+    if (l >= a.L) break;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int b = b0 + ty + 8 * k, m = m0 + tx;
+      if (b < a.B && m < a.M) a.xhat[((int64_t)b * a.L + l) * a.M + m] = T[q][tx][ty + 8 * k];
+    }
   }
 }
 
 // split rows S[l M + m][2b, 2b + 1] = hi/lo of xhat[b][l][m], m <= l.
-__device__ __forceinline__ void pack_tile(const RowsT &a, int mt, int l, int bt, float2 (*T)[33]) {
+__device__ __forceinline__ void pack_tile(const RowsT &a, int mt, int lg, int bt, RowsTile &T) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int m0 = mt * 32, b0 = bt * 32;
-  for (int bb = ty; bb < 32; bb += 8) {
-    const int b = b0 + bb, m = m0 + tx;
-    float2 v = make_float2(0.f, 0.f);
-    if (b < a.B && m < a.M && m <= l) v = a.xhat[((int64_t)b * a.L + l) * a.M + m];
-    T[tx][bb] = v;
+  float2 v[kRowsL][4];
+#pragma unroll
+  for (int q = 0; q < kRowsL; q++) {
+    const int l = lg * kRowsL + q;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int b = b0 + ty + 8 * k, m = m0 + tx;
+      v[q][k] = make_float2(0.f, 0.f);
+      if (l < a.L && b < a.B && m < a.M && m <= l) v[q][k] = a.xhat[((int64_t)b * a.L + l) * a.M + m];
+    }
   }
+#pragma unroll
+  for (int q = 0; q < kRowsL; q++)
+#pragma unroll
+    for (int k = 0; k < 4; k++) T[q][tx][ty + 8 * k] = v[q][k];
   __syncthreads();
-  for (int mm = ty; mm < 32; mm += 8) {
-    const int m = m0 + mm, b = b0 + tx;
-    if (m > l || m >= a.M || b >= a.B) continue;
-    const int64_t o = ((int64_t)l * a.M + m) * a.ld + 2 * b;
-    const float2 v = T[mm][tx];
-    __nv_bfloat16 hr, lr, hi_, li;
-    split_bf16(v.x, hr, lr);
-    split_bf16(v.y, hi_, li);
-    *reinterpret_cast<uint32_t *>(a.shi + o) = pack_bf16x2(hr, hi_);
-    if (a.slo) *reinterpret_cast<uint32_t *>(a.slo + o) = pack_bf16x2(lr, li);
+#pragma unroll
+  for (int q = 0; q < kRowsL; q++) {
+    const int l = lg * kRowsL + q;
+    if (l >= a.L) break;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int m = m0 + ty + 8 * k, b = b0 + tx;
+      if (m > l || m >= a.M || b >= a.B) continue;
+      const int64_t o = ((int64_t)l * a.M + m) * a.ld + 2 * b;
+      const float2 w = T[q][ty + 8 * k][tx];
+      __nv_bfloat16 hr, lr, hi_, li;
+      split_bf16(w.x, hr, lr);
+      split_bf16(w.y, hi_, li);
+      *reinterpret_cast<uint32_t *>(a.shi + o) = pack_bf16x2(hr, hi_);
+      if (a.slo) *reinterpret_cast<uint32_t *>(a.slo + o) = pack_bf16x2(lr, li);
+    }
   }
 }
 
 // Several problems per launch: CTA j belongs to problem s with blk0[s] <= j
-// < blk0[s + 1]; mt, then l, then bt vary slowest.
+// < blk0[s + 1]; mt, then the degree group, then bt vary slowest.
 struct RowsTGroup {
   RowsT seg[kMaxSeg];
   int blk0[kMaxSeg + 1];
@@ -1034,25 +1069,22 @@ struct RowsTGroup {
 
 template <bool kPack>
 __global__ void __launch_bounds__(256) rows_transpose_kernel(const __grid_constant__ RowsTGroup g) {
-  __shared__ float2 T[32][33];
+  __shared__ RowsTile T;
   int s = 0;
   while (s + 1 < g.nseg && (int)blockIdx.x >= g.blk0[s + 1]) s++;
   const RowsT &a = g.seg[s];
-  const int mtiles = (a.M + 31) / 32;
+  const int mtiles = (a.M + 31) / 32, lgroups = (a.L + kRowsL - 1) / kRowsL;
   int local = blockIdx.x - g.blk0[s];
   const int mt = local % mtiles;
   local /= mtiles;
-  const int l = local % a.L;
-  const int bt = local / a.L;
+  const int lg = local % lgroups;
+  const int bt = local / lgroups;
   if (kPack)
-    pack_tile(a, mt, l, bt, T);
+    pack_tile(a, mt, lg, bt, T);
   else
-    finalize_tile(a, mt, l, bt, T);
+    finalize_tile(a, mt, lg, bt, T);
 }
 
-// WR[l][n][k] (bf16 hi/lo), n < nwr rows, k < kx columns, from W[l][o][i]:
-// n = 2 o + a, k = 2 i + c: (a, c) = (0, 0) Re W, (0, 1) -Im W, (1, 0) Im W,
-// (1, 1) Re W; zero outside 2 Cout x 2 Cin.
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and
 // transposed layout [(m, p, k')][Ip64]); same recurrence as the FP32 table.
 __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bfloat16 *__restrict__ flo,
@@ -1554,7 +1586,7 @@ cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaS
     const int s = g.nseg++;
     g.seg[s] = RowsT{it.rows, it.xhat, it.shi, it.slo, it.L, it.M, it.B, it.ld};
     g.blk0[s] = (int)blk;
-    blk += (int64_t)((it.M + 31) / 32) * it.L * ((it.B + 31) / 32);
+    blk += (int64_t)((it.M + 31) / 32) * ((it.L + kRowsL - 1) / kRowsL) * ((it.B + 31) / 32);
   }
   g.blk0[g.nseg] = (int)blk;
   if (blk == 0) return cudaSuccess;
