@@ -202,13 +202,19 @@ struct RegDFT<4> {
   static __device__ __forceinline__ void run(float2 (&a)[4]) { reg_stage<4, 1, 4>(a); }
 };
 
-// Buffer of one sequence: rows k2 < 45 of P + 1 entries (padding against
-// bank conflicts).  After seq_fft, X[k2 + 45 k1] sits at row k2, column k1.
-// Sequence buffer pitch (float2 entries): 45 rows of P + 1, padded to 2 mod
-// 16 so that the 8 fields of a CTA fall on distinct bank pairs.
+// Buffer of one sequence: rows k2 < 45 of rpitch entries, P + 1 (padding
+// against bank conflicts) except for P = 4, whose 4 lanes per sequence meet
+// distinct banks unpadded and whose 64 sequences per CTA must fit twice per
+// SM.  After seq_fft, X[k2 + 45 k1] sits at row k2, column k1.
+template <int P>
+__host__ __device__ constexpr int rpitch() {
+  return P == 4 ? P : P + 1;
+}
+// Sequence buffer pitch (float2 entries): 45 rows, padded to 2 mod 16 so
+// that the 8 fields of a CTA fall on distinct bank pairs.
 template <int P>
 __host__ __device__ constexpr int seq_pitch() {
-  return (kQ * (P + 1) + 15 - 2) / 16 * 16 + 2;
+  return (kQ * rpitch<P>() + 15 - 2) / 16 * 16 + 2;
 }
 
 // Twiddle table w_N^{t k2} (t < P, k2 < 45, lane-major) into shared memory
@@ -231,7 +237,7 @@ __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restri
 
 template <int P>
 __device__ __forceinline__ int spec_index(int k) {
-  return (k % kQ) * (P + 1) + k / kQ;
+  return (k % kQ) * rpitch<P>() + k / kQ;
 }
 
 // Forward DFT of the sequence held as v[j] = z[t + P j] by lane t.
@@ -243,15 +249,15 @@ __device__ __forceinline__ void seq_fft(float2 (&v)[kQ], int t, float2 *buf, con
 #pragma unroll
   for (int k2 = 1; k2 < kQ; k2++) v[k2] = cmul(v[k2], twT[t * kQ + k2]);
 #pragma unroll
-  for (int k2 = 0; k2 < kQ; k2++) buf[k2 * (P + 1) + t] = v[k2];
+  for (int k2 = 0; k2 < kQ; k2++) buf[k2 * rpitch<P>() + t] = v[k2];
   __syncwarp();
   for (int k2 = t; k2 < kQ; k2 += P) {
     float2 u[P];
 #pragma unroll
-    for (int n = 0; n < P; n++) u[n] = buf[k2 * (P + 1) + n];
+    for (int n = 0; n < P; n++) u[n] = buf[k2 * rpitch<P>() + n];
     RegDFT<P>::run(u);
 #pragma unroll
-    for (int n = 0; n < P; n++) buf[k2 * (P + 1) + n] = u[n];
+    for (int n = 0; n < P; n++) buf[k2 * rpitch<P>() + n] = u[n];
   }
   __syncwarp();
 }
@@ -350,8 +356,8 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
     int64_t o = fold_row(fl, m0, 0, kq) + col;
     for (int m = m0; m < M; m += kMStep, o += kMStep * fl.sm) {
       // X[m] sits at spec_index(m); X[N - m] at spec_index(N - m)
-      const int im = r * (P + 1) + q;
-      const int ic = m == 0 ? 0 : (r > 0 ? (kQ - r) * (P + 1) + (P - 1 - q) : P - q);
+      const int im = r * rpitch<P>() + q;
+      const int ic = m == 0 ? 0 : (r > 0 ? (kQ - r) * rpitch<P>() + (P - 1 - q) : P - q);
       const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
       const float wn = w * sn, ws = w * ss;
       float2 e[2], od[2];
@@ -403,11 +409,10 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   const int Kh = (nlat + 1) / 2;
   const int b0 = bx * kFB;
   load_twiddles<P>(tw, twiddle);
-  // stage c_m / 2 * ring scale * G for the northern row (entries 0..M-1) and
-  // the southern row (entries M..2M-1) of every sequence buffer
-  // loads are issued in batches of 8 iterations so that many are in flight
-  // thread (f2, m0) stages fields 2 f2 and 2 f2 + 1 (one 16-byte load per
-  // row), orders m0, m0 + 64, ...
+  // stage conj(Z) (c_m / 2 * ring scale * G of the northern and southern
+  // rows, as the Hermitian sequences' Z = H_n + i H_s) in every sequence
+  // buffer; thread (f2, m0) stages fields 2 f2 and 2 f2 + 1 (one 16-byte
+  // load per row), orders m0, m0 + 64, ..., kBatch loads in flight
   constexpr int kBatch = 6;
   constexpr int kPairs = kFB / 2;
   constexpr int kMStep = kThreads / kPairs;  // 64
@@ -418,59 +423,71 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   const bool two = b0 + fa + 1 < B;
   const int64_t col = fold_col(fl, 2 * (int64_t)(b0 + fa));  // 4 columns of one 16-column group
   const int64_t pstride = fl.sp;                            // E row -> O row
+  // the thread's items (ring pair pq, order m0 + i kMStep) in batches that
+  // may span ring pairs, so that short rows (small grids, several ring
+  // pairs per CTA) still keep kBatch loads in flight
+  const int per = m0 < M ? (M - m0 + kMStep - 1) / kMStep : 0;
+  const int total = field_ok ? NPAIR * per : 0;
+  for (int it0 = 0; it0 < total; it0 += kBatch) {
+    float4 ge[kBatch], go[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      ge[u] = go[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int it = it0 + u;
+      if (it >= total) continue;
+      const int pq = NPAIR == 1 ? 0 : it / per;
+      const int m = m0 + (it - pq * per) * kMStep, kq = by * NPAIR + pq;
+      if (kq >= Kh) continue;
+      const float *g = Gw + fold_row(fl, m, 0, kq) + col;
+      if (two) {
+        ge[u] = *reinterpret_cast<const float4 *>(g);
+        go[u] = *reinterpret_cast<const float4 *>(g + pstride);
+      } else {
+        const float2 a = *reinterpret_cast<const float2 *>(g), c = *reinterpret_cast<const float2 *>(g + pstride);
+        ge[u] = make_float4(a.x, a.y, 0.f, 0.f);
+        go[u] = make_float4(c.x, c.y, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; u++) {
+      const int it = it0 + u;
+      if (it >= total) break;
+      const int pq = NPAIR == 1 ? 0 : it / per;
+      const int m = m0 + (it - pq * per) * kMStep, kq = by * NPAIR + pq;
+      if (kq >= Kh) continue;
+      const int kqs = nlat - 1 - kq;
+      const bool eq = (kq == kqs);
+      const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
+      const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
+      float2 *Ba = bufs + (pq * kFB + fa) * BUF;
+      const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
+      const int mq = m == 0 ? 0 : N - m;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const float2 e = h ? make_float2(ge[u].z, ge[u].w) : make_float2(ge[u].x, ge[u].y);
+        const float2 o = h ? make_float2(go[u].z, go[u].w) : make_float2(go[u].x, go[u].y);
+        const float2 gn = cscale(eq ? e : cadd(e, o), w * sn);
+        const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(e, o), w * ss);
+        // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
+        // G_m enters Z[m], conj(G_m) enters Z[N - m]
+        const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
+        const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
+        float2 *Bq = Ba + h * BUF;
+        if (mq == m) {
+          Bq[m] = cadd(za, zb);
+        } else {
+          Bq[m] = za;
+          Bq[mq] = zb;
+        }
+      }
+    }
+  }
+  // zeros between the two halves of every staged sequence
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
     const int kq = by * NPAIR + pq;
     if (kq >= Kh || !field_ok) continue;
-    const int kqs = nlat - 1 - kq;
-    const bool eq = (kq == kqs);
-    const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
-    const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
-    const float *g0 = Gw + fold_row(fl, m0, 0, kq) + col;
     float2 *Ba = bufs + (pq * kFB + fa) * BUF;
-    for (int mb = m0; mb < M; mb += kMStep * kBatch, g0 += (int64_t)kMStep * kBatch * fl.sm) {
-      float4 ge[kBatch], go[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; u++) {
-        ge[u] = go[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (mb + u * kMStep < M) {
-          const float *g = g0 + (int64_t)u * kMStep * fl.sm;
-          if (two) {
-            ge[u] = *reinterpret_cast<const float4 *>(g);
-            go[u] = *reinterpret_cast<const float4 *>(g + pstride);
-          } else {
-            const float2 a = *reinterpret_cast<const float2 *>(g), c = *reinterpret_cast<const float2 *>(g + pstride);
-            ge[u] = make_float4(a.x, a.y, 0.f, 0.f);
-            go[u] = make_float4(c.x, c.y, 0.f, 0.f);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; u++) {
-        const int m = mb + u * kMStep;
-        if (m >= M) break;
-        const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
-        const int mq = m == 0 ? 0 : N - m;
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const float2 e = h ? make_float2(ge[u].z, ge[u].w) : make_float2(ge[u].x, ge[u].y);
-          const float2 o = h ? make_float2(go[u].z, go[u].w) : make_float2(go[u].x, go[u].y);
-          const float2 gn = cscale(eq ? e : cadd(e, o), w * sn);
-          const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(e, o), w * ss);
-          // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
-          // G_m enters Z[m], conj(G_m) enters Z[N - m]
-          const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
-          const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
-          float2 *Bq = Ba + h * BUF;
-          if (mq == m) {
-            Bq[m] = cadd(za, zb);
-          } else {
-            Bq[m] = za;
-            Bq[mq] = zb;
-          }
-        }
-      }
-    }
     for (int q = M + m0; q <= N - M; q += kMStep) {
       Ba[q] = make_float2(0.f, 0.f);
       Ba[BUF + q] = make_float2(0.f, 0.f);
@@ -498,7 +515,7 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   int r = t, q = 0;  // j = 45 q + r
 #pragma unroll 5
   for (int j = t; j < N; j += P) {
-    const float2 o = buf[r * (P + 1) + q];
+    const float2 o = buf[r * rpitch<P>() + q];
     rn[j] = o.x;
     if (!eq) rs[j] = -o.y;
     r += P;
