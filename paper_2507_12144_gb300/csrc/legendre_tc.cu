@@ -657,7 +657,10 @@ __device__ __forceinline__ void generate_chunk(const SegArgs &sg, const TileInfo
   float pa = zero ? 0.f : sd.s0, pb = zero ? 0.f : sd.s1;  // scaled rows i, i + 1
   int E = zero ? 0 : sd.e;
   float scale = zero ? 0.f : pow2_or_zero(E);
-  // the step to row i + 2 uses the coefficients of row i + 1
+  // the step to row i + 2 uses the coefficients of row i + 1.  A zero
+  // block runs the same steps from zero rows (and zero scale) over the
+  // first coefficients of the tile, which stay in bounds, so that the loop
+  // has no per-step selects.
   const float4 *cf = cs + (zero ? 0 : i0 + 1 - ibase);
 #pragma unroll
   for (int q = 0; q < 4; q++) {
@@ -665,24 +668,26 @@ __device__ __forceinline__ void generate_chunk(const SegArgs &sg, const TileInfo
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       const float v0 = pa * scale, v1 = pb * scale;
-      const float4 c0 = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : cf[0];
-      const float4 c1 = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : cf[1];
-      if (!zero) cf += 2;
+      const float4 c0 = cf[2 * u], c1 = cf[2 * u + 1];
       const float pc = fmaf(fmaf(c0.x, x2h, fmaf(c0.x, x2l, c0.y)), pb, c0.z * pa);
       const float pd = fmaf(fmaf(c1.x, x2h, fmaf(c1.x, x2l, c1.y)), pc, c1.z * pb);
       pa = pc;
       pb = pd;
-      if (fabsf(pb) > 1.8446744e19f) {  // 2^64
-        pa *= 5.4210109e-20f;            // 2^-64
-        pb *= 5.4210109e-20f;
-        E += 64;
-        scale = pow2_or_zero(E);
-      }
       const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
       const float2 hf = __bfloat1622float2(hh);
       const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
       h[u] = *reinterpret_cast<const uint32_t *>(&hh);
       lw[u] = *reinterpret_cast<const uint32_t *>(&ll);
+    }
+    cf += 8;
+    // renormalise once per 8 rows: a row grows by less than 2^12 per step
+    // here, so 2^64 plus four steps stays far inside the FP32 range, and the
+    // power-of-two rescaling is exact whenever it happens
+    if (fabsf(pb) > 1.8446744e19f) {  // 2^64
+      pa *= 5.4210109e-20f;            // 2^-64
+      pb *= 5.4210109e-20f;
+      E += 64;
+      scale = pow2_or_zero(E);
     }
     const int chunk = cbase + q;
     uint32_t off;

@@ -165,12 +165,14 @@ def test_block_and_fused_filter_inverse_match_oracle(shtgb, prec):
 
 
 @pytest.mark.parametrize("prec", TC_PRECS)
-@pytest.mark.parametrize("BmC", [(2, 6), (1, 24), (2, 128)])
+@pytest.mark.parametrize("BmC", [(2, 6), (1, 24), (2, 128), (3, 7)])
 def test_forward_then_block_on_one_plan(shtgb, prec, BmC):
     """The forward into the API layout and the fused block share a plan's
     workspaces; neither may leave values the other reads.  (1, 24) and
-    (2, 128) take the forward rows through TMA stores (column tiles inside
-    one member), (2, 6) through per-lane stores."""
+    (2, 128) take the forward rows and the filter's rows through TMA stores
+    (column tiles inside one member, channels a multiple of 4), (2, 6) and
+    (3, 7) through per-lane stores; (3, 7) also has an odd channel count
+    (the filter's weight chunks load W element by element)."""
     nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
     Bm, C = BmC
     fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, Bm * C, 3, 520)
