@@ -55,12 +55,19 @@ __constant__ float2 kRoot32[32] = {
     {9.238795325e-01f, 3.826834324e-01f}, {9.807852804e-01f, 1.950903220e-01f},
 };
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex additions and real scalings on the packed two-lane FP32
+// instructions (one instruction for the real and imaginary parts; each lane
+// rounds as the scalar operation does; a - b as b (-1) + a, exact up to the
+// one rounding).  The complex product stays scalar: its packed forms need
+// operand swaps that cost as much as they save (timed on the 45 P grids).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+// a + s b
+__device__ __forceinline__ float2 caxpy(float s, float2 b, float2 a) { return __ffma2_rn(make_float2(s, s), b, a); }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
 
@@ -87,7 +94,7 @@ __device__ __forceinline__ void butterfly(float2 (&v)[R]) {
   } else if (R == 3) {
     const float h = 0.86602540378443864676f;
     const float2 t1 = cadd(v[1], v[2]);
-    const float2 t2 = csub(v[0], cscale(t1, 0.5f));
+    const float2 t2 = caxpy(-0.5f, t1, v[0]);
     const float2 t3 = mul_mi(cscale(csub(v[1], v[2]), h));
     v[0] = cadd(v[0], t1);
     v[1] = cadd(t2, t3);
@@ -104,10 +111,10 @@ __device__ __forceinline__ void butterfly(float2 (&v)[R]) {
     const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
     const float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
     const float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
-    const float2 r1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
-    const float2 r2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
-    const float2 q1 = mul_mi(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
-    const float2 q2 = mul_mi(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    const float2 r1 = caxpy(c2, a2, caxpy(c1, a1, v[0]));
+    const float2 r2 = caxpy(c1, a2, caxpy(c2, a1, v[0]));
+    const float2 q1 = mul_mi(caxpy(s2, b2, cscale(b1, s1)));
+    const float2 q2 = mul_mi(caxpy(-s1, b2, cscale(b1, s2)));
     v[0] = cadd(v[0], cadd(a1, a2));
     v[1] = cadd(r1, q1);
     v[4] = csub(r1, q1);
