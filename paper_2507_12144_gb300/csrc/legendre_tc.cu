@@ -101,13 +101,12 @@ struct FiltTile {
   int l, m0;
 };
 
-// Destination of the forward contraction: the API layout xhat[b][l][m], or
-// l-major bf16 rows (row l M + m, member b's channel ch at column
-// b kx + 2 ch + {re, im}) for the tensor-core filter.
-// Or FP32 l-major rows (row l M + m, field f at columns 2 f + {re, im},
-// row stride ldr floats), which a transpose kernel turns into xhat.
+// Destination of the forward contraction: l-major bf16 rows (row l M + m,
+// member b's channel ch at column b kx + 2 ch + {re, im}) for the
+// tensor-core filter, or FP32 l-major rows (row l M + m, field f at columns
+// 2 f + {re, im}, row stride ldr floats), which a transpose kernel turns
+// into the API layout xhat[b][l][m].
 struct FwdOut {
-  float2 *xhat;
   __nv_bfloat16 *rows_hi, *rows_lo;
   int ldo, cin, kx;
   float *rowsf;
@@ -469,23 +468,13 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
     const bool row_ok = r < leg_rows(g.L, ti.m, ti.p);
     const int l = ti.m + ti.p + 2 * r;
     const FwdOut out = g.fout;
-    const int B = g.B, L = g.L, M = g.M;
+    const int B = g.B, M = g.M;
     const int64_t orow = ((int64_t)l * M + ti.m) * out.ldo;
     for (int j = 0; j < Nt / 16; j++) {
       float v[16];
       tmem_ld16(tl + (uint32_t)(j * 16), v);
       if (!row_ok) continue;
-      if (out.rowsf) {
-        float *dst = out.rowsf + ((int64_t)l * M + ti.m) * out.ldr;
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int c = ti.c0 + j * 16 + 4 * u;
-          if (c + 4 <= 2 * B)
-            *reinterpret_cast<float4 *>(dst + c) = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-          else if (c + 2 <= 2 * B)
-            *reinterpret_cast<float2 *>(dst + c) = make_float2(v[4 * u], v[4 * u + 1]);
-        }
-      } else if (out.rows_hi) {
+      {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           const int f = (ti.c0 + j * 16) / 2 + 4 * h;  // first of 4 fields
@@ -500,12 +489,6 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
                             v[8 * h + 2 * u + 1]);
             }
           }
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-          const int f = (ti.c0 + j * 16) / 2 + u;
-          if (f < B) out.xhat[((int64_t)f * L + l) * M + ti.m] = make_float2(v[2 * u], v[2 * u + 1]);
         }
       }
     }
@@ -1469,7 +1452,7 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       column_tiles(it.B, std::min(it.Nt > 0 ? it.Nt : 256, cap), g.Nt, g.nct);
       g.tile0 = ntiles;
       g.tiles = it.tiles;
-      g.fout = FwdOut{it.xhat, it.rows_hi, it.rows_lo, it.ldo, it.cin > 0 ? it.cin : 1, it.kx, it.rowsf, it.ldr};
+      g.fout = FwdOut{it.rows_hi, it.rows_lo, it.ldo, it.cin > 0 ? it.cin : 1, it.kx, it.rowsf, it.ldr};
       g.Gw = it.Gw;
       g.ldc = it.ldc;
       g.gpair = T.gpair;
@@ -1487,6 +1470,7 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
         mp.b_lo = split ? T.f_lo : T.f_hi;
         // store maps of the plan's l-major rows (used when the destination
         // is those rows)
+        if (!it.rows_hi == !it.rowsf) return cudaErrorInvalidValue;  // exactly one destination
         if (it.rows_hi && (it.rows_hi != T.xrows_hi || it.ldo != T.ldx)) return cudaErrorInvalidValue;
         if (it.rowsf && (it.rowsf != T.frows || it.ldr != T.ldr)) return cudaErrorInvalidValue;
         mp.o32_hi = it.rowsf ? T.ro32 : T.xo32_hi;
@@ -1516,23 +1500,6 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
                    : launch_persistent<kFwd>(split, gen, P, cfg, st);
   }
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
-                              __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
-                              cudaStream_t st) {
-  TcLegItem it{};
-  it.T = &T;
-  it.tiles = tiles;
-  it.ntiles = ntiles;
-  it.B = B;
-  it.xhat = xhat;
-  it.rows_hi = rows_hi;
-  it.rows_lo = rows_lo;
-  it.ldo = ldo;
-  it.cin = cin;
-  it.kx = kx;
-  return launch_leg_tc_group(0, &it, 1, TcLaunch{}, st);
 }
 
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,

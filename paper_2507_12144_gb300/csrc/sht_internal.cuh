@@ -140,12 +140,6 @@ cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_b
 // FP64 seeds of the on-chip Legendre table (every 32 rows of every (m, p)).
 cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
                             const double *b, const double *seedf, int L, int M, int Kh, cudaStream_t st);
-// Forward contraction on the tensor cores from the bf16 Fourier workspace;
-// output to the API layout xhat (rows_hi == NULL) or to l-major bf16 rows
-// rows[l M + m][ldo] with member b = f / cin at columns b kx + 2 (f mod cin).
-cudaError_t launch_leg_fwd_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float2 *xhat,
-                              __nv_bfloat16 *rows_hi, __nv_bfloat16 *rows_lo, int ldo, int cin, int kx, int B,
-                              cudaStream_t st);
 // Tensor-core filter from the l-major rows to the inverse's split rows.
 // ftiles: (l, m0) pairs covering m <= l, m < M in steps of 128.
 // ta: the forward rows (width = members x kx, row stride ldx); W: the
@@ -159,15 +153,16 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
                               cudaStream_t st);
 // One problem of a grouped tensor-core Legendre launch: a plan's view, its
-// tiles, its batch, and the destination of the forward (xhat or rows, as in
-// launch_leg_fwd_tc) or of the inverse (Gw, ldc).  Nt = column tile width
-// (multiple of 16, <= 256; 0 = balanced tiles of at most 256).
+// tiles, its batch, and the destination of the forward (the plan's l-major
+// bf16 rows, rows[l M + m][ldo] with member b = f / cin at columns
+// b kx + 2 (f mod cin), or its FP32 l-major rows rowsf) or of the inverse
+// (Gw, ldc).  Nt = column tile width (multiple of 16, <= 256; 0 = balanced
+// tiles of at most 256).
 struct TcLegItem {
   const TcPlanView *T;
   const LegTile *tiles;
   int ntiles;
   int B, Nt;
-  float2 *xhat;
   __nv_bfloat16 *rows_hi, *rows_lo;
   int ldo, cin, kx;
   float *rowsf;  // FP32 l-major rows (row l M + m, field f at 2f), stride ldr
