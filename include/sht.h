@@ -411,6 +411,15 @@ const char *sht_version(void);
  * it had allocated.  Not thread-safe; for tests only. */
 void sht_debug_fail_alloc_after(int n);
 
+/* Test hook for device-side failure detection: queue on `stream` one kernel
+ * that waits on a shared-memory barrier nothing ever completes, through the
+ * same bounded wait the tensor-core kernels use, with a limit of
+ * timeout_ns (1 .. 2e9).  The wait gives up, records the timeout in the
+ * plan's error word and the kernel returns normally; sht_plan_check then
+ * reports SHT_ERR_TIMEOUT (and clears the word), and the plan stays usable.
+ * For tests only. */
+sht_status_t sht_debug_stall(sht_plan_t plan, int64_t timeout_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

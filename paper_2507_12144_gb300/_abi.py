@@ -66,6 +66,7 @@ SIGNATURES = {
     "sht_last_error_message": ([], ctypes.c_char_p),
     "sht_version": ([], ctypes.c_char_p),
     "sht_debug_fail_alloc_after": ([_i], None),
+    "sht_debug_stall": ([_p, _i64, _p], _i),
     "sht_batch_opts_default": ([ctypes.POINTER(sht_batch_opts)], None),
     "sht_batch_create": ([ctypes.POINTER(_p), ctypes.POINTER(sht_batch_item), _i, ctypes.POINTER(sht_batch_opts), _p],
                          _i),

@@ -1065,4 +1065,13 @@ const char *sht_version(void) { return "0.1.0"; }
  * (n = 0 fails the next one; n < 0 disables). */
 void sht_debug_fail_alloc_after(int n) { g_fail_alloc_after = n; }
 
+sht_status_t sht_debug_stall(sht_plan_t p, int64_t timeout_ns, void *stream) {
+  SHT_TRY(check_plan(p));
+  if (timeout_ns < 1 || timeout_ns > 2000000000ll) return fail(SHT_ERR_INVALID_ARG, "timeout_ns must be 1 .. 2e9");
+  DeviceGuard g(p->device);
+  const cudaError_t e = launch_debug_stall(p->d_err, timeout_ns, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stall launch");
+  return SHT_OK;
+}
+
 }  // extern "C"

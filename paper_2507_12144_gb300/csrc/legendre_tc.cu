@@ -1547,6 +1547,22 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   return launch_persistent<kFilt>(T.split, true, P, TcLaunch{}, st);
 }
 
+// A wait that nothing satisfies: one thread initialises a barrier for one
+// arrival that never comes and waits on it with the given limit.
+__global__ void stall_kernel(unsigned *err, uint64_t timeout_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  mbar_wait(&bar, 0, err, timeout_ns);
+}
+
+cudaError_t launch_debug_stall(unsigned *err, int64_t timeout_ns, cudaStream_t st) {
+  if (timeout_ns < 1 || timeout_ns > 2000000000ll) return cudaErrorInvalidValue;
+  stall_kernel<<<1, 32, 0, st>>>(err, (uint64_t)timeout_ns);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSeg) return cudaErrorInvalidValue;

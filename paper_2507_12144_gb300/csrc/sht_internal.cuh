@@ -191,6 +191,8 @@ struct RowsItem {
   int L, M, B, ld;
 };
 cudaError_t launch_rows_transpose(bool pack, const RowsItem *items, int n, cudaStream_t st);
+// One kernel whose bounded barrier wait runs out (test hook).
+cudaError_t launch_debug_stall(unsigned *err, int64_t timeout_ns, cudaStream_t st);
 // Longitude analysis writing the folded Fourier workspace as bf16 hi/lo
 // (same contract as launch_r2c).
 cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon, int M, int B,

@@ -135,3 +135,7 @@ def test_pipe_rejects_bad_arguments_before_any_cuda_call(lib):
     assert b"pipe" in lib.sht_last_error_message()
     assert lib.sht_pipe_wait(None) == 1
     assert lib.sht_pipe_destroy(None) == 0
+
+
+def test_stall_hook_rejects_null_plan(lib):
+    assert lib.sht_debug_stall(None, 1000, None) == 1
