@@ -455,6 +455,7 @@ void sht_plan_opts_default(sht_plan_opts *opts) {
 }
 
 sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, int mmax, const sht_plan_opts *opts) {
+  NvtxRange nvtx_range("sht_plan");
   if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   sht_plan_opts o;
@@ -835,6 +836,7 @@ sht_status_t sht_plan_grid(sht_plan_t p, double *x, double *w) {
 }
 
 sht_status_t sht_forward(sht_plan_t p, const float *x, void *xhat, int64_t B, void *stream) {
+  NvtxRange nvtx_range("sht_forward");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(B));
   if (B == 0) return SHT_OK;
@@ -845,6 +847,7 @@ sht_status_t sht_forward(sht_plan_t p, const float *x, void *xhat, int64_t B, vo
 }
 
 sht_status_t sht_inverse_adjoint(sht_plan_t p, const float *gx, void *gxhat, int64_t B, void *stream) {
+  NvtxRange nvtx_range("sht_inverse_adjoint");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(B));
   if (B == 0) return SHT_OK;
@@ -855,6 +858,7 @@ sht_status_t sht_inverse_adjoint(sht_plan_t p, const float *gx, void *gxhat, int
 }
 
 sht_status_t sht_inverse(sht_plan_t p, const void *xhat, float *x, int64_t B, void *stream) {
+  NvtxRange nvtx_range("sht_inverse");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(B));
   if (B == 0) return SHT_OK;
@@ -865,6 +869,7 @@ sht_status_t sht_inverse(sht_plan_t p, const void *xhat, float *x, int64_t B, vo
 }
 
 sht_status_t sht_forward_adjoint(sht_plan_t p, const void *gxhat, float *gx, int64_t B, void *stream) {
+  NvtxRange nvtx_range("sht_forward_adjoint");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(B));
   if (B == 0) return SHT_OK;
@@ -876,6 +881,7 @@ sht_status_t sht_forward_adjoint(sht_plan_t p, const void *gxhat, float *gx, int
 
 sht_status_t spectral_filter(sht_plan_t p, const void *xhat, const void *W, void *yhat, int64_t Bm, int Cin, int Cout,
                              void *stream) {
+  NvtxRange nvtx_range("spectral_filter");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(Bm));
   SHT_TRY(check_channels(p, Cin, Cout, false));
@@ -890,6 +896,7 @@ sht_status_t spectral_filter(sht_plan_t p, const void *xhat, const void *W, void
 
 sht_status_t spectral_filter_adjoint(sht_plan_t p, const void *gy, const void *W, const void *xhat, void *gx, void *gW,
                                      int64_t Bm, int Cin, int Cout, void *stream) {
+  NvtxRange nvtx_range("spectral_filter_adjoint");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(Bm));
   SHT_TRY(check_channels(p, Cin, Cout, false));
@@ -912,6 +919,7 @@ sht_status_t spectral_filter_adjoint(sht_plan_t p, const void *gy, const void *W
 
 sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, float *y, int64_t Bm, int Cin, int Cout,
                                 void *stream) {
+  NvtxRange nvtx_range("sht_spectral_block");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(Bm));
   SHT_TRY(check_channels(p, Cin, Cout, true));
@@ -943,6 +951,7 @@ sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, flo
 
 sht_status_t spectral_filter_inverse(sht_plan_t p, const void *xhat, const void *W, float *y, int64_t Bm, int Cin,
                                      int Cout, void *stream) {
+  NvtxRange nvtx_range("spectral_filter_inverse");
   SHT_TRY(check_plan(p));
   SHT_TRY(check_batch(Bm));
   SHT_TRY(check_channels(p, Cin, Cout, true));

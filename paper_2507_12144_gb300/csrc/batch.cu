@@ -389,6 +389,7 @@ void sht_batch_opts_default(sht_batch_opts *opts) {
 
 sht_status_t sht_batch_create(sht_batch_t *out, const sht_batch_item *items, int n, const sht_batch_opts *opts,
                               void *stream) {
+  NvtxRange nvtx_range("sht_batch_create");
   if (!out) return fail(SHT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   sht_batch_opts o;
@@ -539,6 +540,7 @@ sht_status_t sht_batch_create(sht_batch_t *out, const sht_batch_item *items, int
 }
 
 sht_status_t sht_batch_run(sht_batch_t b, void *stream) {
+  NvtxRange nvtx_range("sht_batch_run");
   if (!b || !b->exec) return fail(SHT_ERR_INVALID_ARG, "batch is NULL");
   DevGuard guard(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

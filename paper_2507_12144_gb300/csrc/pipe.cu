@@ -112,6 +112,7 @@ sht_status_t sht_pipe_create(sht_pipe_t *out, sht_plan_t plan, int64_t Bm, int C
 }
 
 sht_status_t sht_pipe_block(sht_pipe_t q, const float *x_host, const void *W, float *y_host, void *stream) {
+  NvtxRange nvtx_range("sht_pipe_block");
   if (!q) return fail(SHT_ERR_INVALID_ARG, "pipe is NULL");
   if (!x_host || !W || !y_host) return fail(SHT_ERR_INVALID_ARG, "x_host, W and y_host must not be NULL");
   if ((((uintptr_t)x_host) | ((uintptr_t)y_host)) & 15)

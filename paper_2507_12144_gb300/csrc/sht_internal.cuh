@@ -9,9 +9,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sht.h"
 
 namespace shtgb {
+
+// NVTX range around a public entry point (host timeline of the enqueue;
+// free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxRadices = 16;
 constexpr int kMaxNlon = 8192;

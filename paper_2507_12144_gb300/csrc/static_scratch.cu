@@ -61,6 +61,7 @@ using namespace shtgb;
 
 extern "C" sht_status_t sht_forward_static_scratch(sht_plan_t p, const float *x, void *xhat, int64_t B,
                                                    void *stream) {
+  shtgb::NvtxRange nvtx_range("sht_forward_static_scratch");
   if (!p) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
   if (p->precision != SHT_PREC_FP32) return fail(SHT_ERR_UNSUPPORTED, "static-scratch forward is FP32 only");
   if (B < 0) return fail(SHT_ERR_INVALID_ARG, "batch must be >= 0");
