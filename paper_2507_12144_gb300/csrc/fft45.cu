@@ -293,9 +293,9 @@ struct OutBF16 {
     *reinterpret_cast<uint2 *>(hi + idx) =
         make_uint2(*reinterpret_cast<const uint32_t *>(&ha), *reinterpret_cast<const uint32_t *>(&hb));
     if (lo) {
-      const float2 fa = __bfloat1622float2(ha), fb = __bfloat1622float2(hb);
-      const __nv_bfloat162 la = __floats2bfloat162_rn(a.x - fa.x, a.y - fa.y);
-      const __nv_bfloat162 lb = __floats2bfloat162_rn(b.x - fb.x, b.y - fb.y);
+      const float2 da = csub(a, __bfloat1622float2(ha)), db = csub(b, __bfloat1622float2(hb));
+      const __nv_bfloat162 la = __floats2bfloat162_rn(da.x, da.y);
+      const __nv_bfloat162 lb = __floats2bfloat162_rn(db.x, db.y);
       *reinterpret_cast<uint2 *>(lo + idx) =
           make_uint2(*reinterpret_cast<const uint32_t *>(&la), *reinterpret_cast<const uint32_t *>(&lb));
     }
