@@ -526,6 +526,32 @@ def run_gpu(args):
     e2e_value = world * fields * e2e_steps / e2e_s
     pipe.close()
 
+    # the plain FP32 form (CUDA cores, FP32 table) on the same workload, for
+    # comparison with the tensor-core precision forms
+    fp32_side = None
+    if world == 1 and args.precision != "fp32" and not args.no_fp32_side:
+        p32 = shtgb.Plan(NLAT, NLON, GRID, LMAX, MMAX, precision="fp32", device=dev, max_batch=fields)
+        y32 = torch.empty_like(x)
+
+        def step32():
+            shtgb._abi.check(lib.sht_spectral_block(p32.handle, shtgb._ptr(x), shtgb._ptr(W), shtgb._ptr(y32),
+                                                    MEMBERS, CHANNELS, CHANNELS, shtgb._stream(x)))
+
+        for _ in range(3):
+            step32()
+        n32 = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n32):
+            step32()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / n32
+        fp32_side = {"value": fields / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "steps": n32,
+                     "dtype": "f32"}
+        p32.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -541,6 +567,8 @@ def run_gpu(args):
                     "path": "sht_pipe_block, 2 staging slots, pinned host buffers"},
             "clocks": clk,
         }
+        if fp32_side is not None:
+            line["fp32_form"] = fp32_side
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_line(args.cpu_seconds)
         else:
@@ -685,6 +713,8 @@ def main(argv=None):
                     help="block: SHT -> filter -> ISHT at 721x1440 (the headline); batched: forward + inverse "
                          "SHT of the uneven four-grid mix")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
+    ap.add_argument("--no-fp32-side", action="store_true",
+                    help="skip timing the plain FP32 form beside a tensor-core precision")
     ap.add_argument("--table-source", choices=["streamed", "recurrence"], default="streamed",
                     help="Legendre table of the tensor-core precisions: precomputed and streamed, or "
                          "generated on chip by the recurrence")
