@@ -14,14 +14,16 @@
 // average out in the sum over latitudes.  The paper trains in bf16 mixed
 // precision (Sec. E.3); the split form recovers FP32-level accuracy.
 //
-// CTA layout (256 threads):
-//   warp 0      TMA producer of the table tiles (A operand)
-//   warp 1      MMA issuer (one thread)
-//   warp 2      tensor-memory allocation
-//   warps 4..7  converters of the data tiles (B operand: FP32 -> bf16 hi/lo
-//               written in the K-major 128-byte-swizzled layout) and, after
-//               the K loop, the epilogue (tensor memory -> registers ->
-//               global), one 32-lane quarter of the accumulator each.
+// One persistent CTA per SM (256 threads, 512 when an operand is built on
+// chip):
+//   warp 0       TMA producer of the operand tiles (table or data rows, and
+//                the data / weights) into a ring of pipeline stages
+//   warp 1       MMA issuer (one thread)
+//   warp 2       tensor-memory allocation (two accumulators)
+//   warps 4..7   epilogue: tensor memory -> registers -> swizzled shared
+//                staging -> TMA stores, one 32-lane quarter each
+//   warps 8..15  only with kGen: the Legendre table generators (recurrence)
+//                or the filter's weight builders
 // Stages are guarded by mbarriers; every wait is bounded and records a
 // timeout in the plan's error word instead of hanging.
 #include <cudaTypedefs.h>
@@ -93,7 +95,9 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 // Table and weights always enter split (hi + lo); data enters split for
 // split BF16 and rounded (hi only) for BF16.  The Legendre table of kFwd /
 // kInv either streams from a precomputed bf16 table by TMA (kGen = false) or
-// is generated on chip by 8 extra warps from recurrence seeds (kGen = true).
+// is generated on chip by 8 extra warps from recurrence seeds (kGen = true);
+// the filter's real-form weights WR are always built on chip by those warps
+// from the complex W (kFilt with kGen = true).
 // ---------------------------------------------------------------------------
 enum Mode { kFwd = 0, kInv = 1, kFilt = 2 };
 
