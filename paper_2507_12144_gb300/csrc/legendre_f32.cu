@@ -23,15 +23,35 @@ namespace {
 constexpr int kTileR = 64;   // rows (l in the forward, k' in the inverse)
 constexpr int kTileC = 64;   // real columns (2 per field)
 constexpr int kTileK = 16;   // reduction chunk
-constexpr int kThreads = 256;
+// Legendre GEMMs: 64 threads per 64 x 64 tile, 8 x 8 outputs per thread
+// (thread (ty, tx) owns rows 8 ty .. 8 ty + 7 and columns 8 tx .. 8 tx + 7),
+// so that each K step reads 16 values from shared memory for 64 FMAs; the
+// products run as packed two-lane FMAs along the columns; shared memory is
+// double-buffered with the next K chunk loaded into registers meanwhile.
+constexpr int kLegThreads = 64;
+constexpr int kApad = kTileR + 4;  // A rows padded against bank conflicts of the transposed stores
+
+__device__ __forceinline__ void mma8x8(float2 (&acc)[8][4], const float *a8, const float *b8) {
+  const float4 a0 = *reinterpret_cast<const float4 *>(a8), a1 = *reinterpret_cast<const float4 *>(a8 + 4);
+  const float4 b0 = *reinterpret_cast<const float4 *>(b8), b1 = *reinterpret_cast<const float4 *>(b8 + 4);
+  const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                        make_float2(b1.z, b1.w)};
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const float2 ai = make_float2(av[i], av[i]);
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = __ffma2_rn(ai, bv[j], acc[i][j]);
+  }
+}
 
 // Forward: C[i][c] = sum_k' T[i][k'] F[k'][c]   (i rows of block (m, p))
 // CTA bid of the forward contraction of one problem.
 __device__ __forceinline__ void leg_fwd_f32_body(int bid, const TableF32 &T, const LegTile *__restrict__ tiles,
                                                  const float *__restrict__ Fw, float2 *__restrict__ xhat, int L,
                                                  int M, int Kh, int ldc, int B, int nct) {
-  __shared__ __align__(16) float As[kTileK][kTileR];
-  __shared__ __align__(16) float Bs[kTileK][kTileC];
+  __shared__ __align__(16) float As[2][kTileK][kApad];
+  __shared__ __align__(16) float Bs[2][kTileK][kTileC];
   // column tiles vary fastest so that the CTAs sharing one table tile run
   // back to back and find it in L2
   const LegTile tile = tiles[bid / nct];
@@ -40,51 +60,61 @@ __device__ __forceinline__ void leg_fwd_f32_body(int bid, const TableF32 &T, con
   const int c0 = (bid % nct) * kTileC;
   const float *A = T.data + T.off[2 * m + p];
   const float *Bm = Fw + ((int64_t)m * 2 + p) * Kh * (int64_t)ldc;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4];
+  const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
+  float2 acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < 8; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
 
-  // loader coordinates
-  const int ar = threadIdx.x >> 2, ak = (threadIdx.x & 3) * 4;    // A: 64 rows x 16 k
-  const int bk = threadIdx.x >> 4, bc = (threadIdx.x & 15) * 4;   // B: 16 k x 64 c
-  for (int k0 = 0; k0 < Kh; k0 += kTileK) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r0 + ar < nrows) a = *reinterpret_cast<const float4 *>(A + (int64_t)(r0 + ar) * T.Khp + k0 + ak);
-    As[ak + 0][ar] = a.x;
-    As[ak + 1][ar] = a.y;
-    As[ak + 2][ar] = a.z;
-    As[ak + 3][ar] = a.w;
-    float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k0 + bk < Kh && c0 + bc < ldc) bv = *reinterpret_cast<const float4 *>(Bm + (int64_t)(k0 + bk) * ldc + c0 + bc);
-    *reinterpret_cast<float4 *>(&Bs[bk][bc]) = bv;
-    __syncthreads();
+  // loaders: A rows (t >> 2) + 16 q, k (t & 3) 4 .. + 3; B k (t >> 4) + 4 q,
+  // columns (t & 15) 4 .. + 3
+  const int ar = t >> 2, ak = (t & 3) * 4, bk = t >> 4, bc = (t & 15) * 4;
+  float4 an[4], bn[4];
+  auto gload = [&](int k0) {
 #pragma unroll
-    for (int kk = 0; kk < kTileK; kk++) {
-      const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-      const float4 bw = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-      const float ar4[4] = {av.x, av.y, av.z, av.w};
-      const float br4[4] = {bw.x, bw.y, bw.z, bw.w};
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(ar4[i], br4[j], acc[i][j]);
+    for (int q = 0; q < 4; q++) {
+      const int r = ar + 16 * q, k = bk + 4 * q;
+      an[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 + r < nrows) an[q] = *reinterpret_cast<const float4 *>(A + (int64_t)(r0 + r) * T.Khp + k0 + ak);
+      bn[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k0 + k < Kh && c0 + bc < ldc) bn[q] = *reinterpret_cast<const float4 *>(Bm + (int64_t)(k0 + k) * ldc + c0 + bc);
     }
+  };
+  auto sstore = [&](int u) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int r = ar + 16 * q;
+      As[u][ak + 0][r] = an[q].x;
+      As[u][ak + 1][r] = an[q].y;
+      As[u][ak + 2][r] = an[q].z;
+      As[u][ak + 3][r] = an[q].w;
+      *reinterpret_cast<float4 *>(&Bs[u][bk + 4 * q][bc]) = bn[q];
+    }
+  };
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int u = 0;
+  for (int k0 = 0; k0 < Kh; k0 += kTileK) {
+    const bool more = k0 + kTileK < Kh;
+    if (more) gload(k0 + kTileK);
+#pragma unroll
+    for (int kk = 0; kk < kTileK; kk++) mma8x8(acc, &As[u][kk][ty * 8], &Bs[u][kk][tx * 8]);
+    if (more) sstore(u ^ 1);
     __syncthreads();
+    u ^= 1;
   }
   // write: columns (c, c+1) are (re, im) of field c / 2
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const int r = r0 + ty * 4 + i;
+  for (int i = 0; i < 8; i++) {
+    const int r = r0 + ty * 8 + i;
     if (r >= nrows) continue;
     const int l = m + p + 2 * r;
 #pragma unroll
-    for (int j = 0; j < 4; j += 2) {
-      const int c = c0 + tx * 4 + j;
-      const int b = c >> 1;
-      if (b < B) xhat[((int64_t)b * L + l) * M + m] = make_float2(acc[i][j], acc[i][j + 1]);
+    for (int j = 0; j < 4; j++) {
+      const int b = (c0 + tx * 8 + 2 * j) >> 1;
+      if (b < B) xhat[((int64_t)b * L + l) * M + m] = acc[i][j];
     }
   }
 }
@@ -93,60 +123,79 @@ __device__ __forceinline__ void leg_fwd_f32_body(int bid, const TableF32 &T, con
 __device__ __forceinline__ void leg_inv_f32_body(int bid, const TableF32 &T, const LegTile *__restrict__ tiles,
                                                  const float2 *__restrict__ yhat, float *__restrict__ Gw, int L,
                                                  int M, int Kh, int ldc, int B, int nct) {
-  __shared__ __align__(16) float As[kTileK][kTileR];
-  __shared__ __align__(16) float Bs[kTileK][kTileC];
+  __shared__ __align__(16) float As[2][kTileK][kApad];
+  __shared__ __align__(16) float Bs[2][kTileK][kTileC];
   const LegTile tile = tiles[bid / nct];
   const int m = tile.m, p = tile.p, k0r = tile.r0;  // r0 = first k'
   const int nrows = leg_rows(L, m, p);              // reduction length
   const int c0 = (bid % nct) * kTileC;
   const float *A = T.data + T.off[2 * m + p];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4];
+  const int t = threadIdx.x, tx = t & 7, ty = t >> 3;
+  float2 acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < 8; i++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
 
-  const int ai = threadIdx.x >> 4, ak = (threadIdx.x & 15) * 4;   // A: 16 i x 64 k'
-  for (int i0 = 0; i0 < nrows; i0 += kTileK) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i0 + ai < nrows && k0r + ak < T.Khp)
-      a = *reinterpret_cast<const float4 *>(A + (int64_t)(i0 + ai) * T.Khp + k0r + ak);
-    *reinterpret_cast<float4 *>(&As[ai][ak]) = a;
-    // B: 16 i x 32 fields, two float2 per thread
+  // loaders: A rows i (t >> 4) + 4 q, k' (t & 15) 4 .. + 3; B: 16 i x 32
+  // fields, element e = t + 64 q: row e >> 5, field e & 31
+  const int ai = t >> 4, ak = (t & 15) * 4;
+  float4 an[4];
+  float2 bn[8];
+  auto gload = [&](int i0) {
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int e = threadIdx.x + h * kThreads;  // 0 .. 511
+    for (int q = 0; q < 4; q++) {
+      const int i = ai + 4 * q;
+      an[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + i < nrows && k0r + ak < T.Khp)
+        an[q] = *reinterpret_cast<const float4 *>(A + (int64_t)(i0 + i) * T.Khp + k0r + ak);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int e = t + kLegThreads * q;  // 0 .. 511
       const int ii = e >> 5, f = e & 31;
       const int b = (c0 >> 1) + f;
-      float2 v = make_float2(0.f, 0.f);
+      bn[q] = make_float2(0.f, 0.f);
       if (i0 + ii < nrows && b < B) {
         const int l = m + p + 2 * (i0 + ii);
-        v = yhat[((int64_t)b * L + l) * M + m];
+        bn[q] = yhat[((int64_t)b * L + l) * M + m];
       }
-      *reinterpret_cast<float2 *>(&Bs[ii][2 * f]) = v;
     }
-    __syncthreads();
+  };
+  auto sstore = [&](int u) {
 #pragma unroll
-    for (int kk = 0; kk < kTileK; kk++) {
-      const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-      const float4 bw = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-      const float ar4[4] = {av.x, av.y, av.z, av.w};
-      const float br4[4] = {bw.x, bw.y, bw.z, bw.w};
+    for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(&As[u][ai + 4 * q][ak]) = an[q];
 #pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(ar4[i], br4[j], acc[i][j]);
+    for (int q = 0; q < 8; q++) {
+      const int e = t + kLegThreads * q;
+      *reinterpret_cast<float2 *>(&Bs[u][e >> 5][2 * (e & 31)]) = bn[q];
     }
+  };
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int u = 0;
+  for (int i0 = 0; i0 < nrows; i0 += kTileK) {
+    const bool more = i0 + kTileK < nrows;
+    if (more) gload(i0 + kTileK);
+#pragma unroll
+    for (int kk = 0; kk < kTileK; kk++) mma8x8(acc, &As[u][kk][ty * 8], &Bs[u][kk][tx * 8]);
+    if (more) sstore(u ^ 1);
     __syncthreads();
+    u ^= 1;
   }
   float *G = Gw + ((int64_t)m * 2 + p) * Kh * (int64_t)ldc;
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const int k = k0r + ty * 4 + i;
+  for (int i = 0; i < 8; i++) {
+    const int k = k0r + ty * 8 + i;
     if (k >= Kh) continue;
-    const int c = c0 + tx * 4;
-    if (c < ldc) *reinterpret_cast<float4 *>(G + (int64_t)k * ldc + c) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int c = c0 + tx * 8 + 4 * h;
+      if (c < ldc)
+        *reinterpret_cast<float4 *>(G + (int64_t)k * ldc + c) =
+            make_float4(acc[i][2 * h].x, acc[i][2 * h].y, acc[i][2 * h + 1].x, acc[i][2 * h + 1].y);
+    }
   }
 }
 
@@ -172,24 +221,24 @@ __device__ __forceinline__ int f32_segment(const F32Group &g, int blk) {
   return s;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kLegThreads)
 leg_fwd_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float *__restrict__ Fw,
                    float2 *__restrict__ xhat, int L, int M, int Kh, int ldc, int B, int nct) {
   leg_fwd_f32_body(blockIdx.x, T, tiles, Fw, xhat, L, M, Kh, ldc, B, nct);
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kLegThreads)
 leg_inv_f32_kernel(TableF32 T, const LegTile *__restrict__ tiles, const float2 *__restrict__ yhat,
                    float *__restrict__ Gw, int L, int M, int Kh, int ldc, int B, int nct) {
   leg_inv_f32_body(blockIdx.x, T, tiles, yhat, Gw, L, M, Kh, ldc, B, nct);
 }
 
-__global__ void __launch_bounds__(kThreads) leg_fwd_f32_grouped(const __grid_constant__ F32Group g) {
+__global__ void __launch_bounds__(kLegThreads) leg_fwd_f32_grouped(const __grid_constant__ F32Group g) {
   const F32Seg &q = g.seg[f32_segment(g, blockIdx.x)];
   leg_fwd_f32_body(blockIdx.x - q.blk0, q.T, q.tiles, q.Fw, q.xhat, q.L, q.M, q.Kh, q.ldc, q.B, q.nct);
 }
 
-__global__ void __launch_bounds__(kThreads) leg_inv_f32_grouped(const __grid_constant__ F32Group g) {
+__global__ void __launch_bounds__(kLegThreads) leg_inv_f32_grouped(const __grid_constant__ F32Group g) {
   const F32Seg &q = g.seg[f32_segment(g, blockIdx.x)];
   leg_inv_f32_body(blockIdx.x - q.blk0, q.T, q.tiles, q.yhat, q.Gw, q.L, q.M, q.Kh, q.ldc, q.B, q.nct);
 }
@@ -263,7 +312,7 @@ cudaError_t launch_leg_fwd_f32(const TableF32 &T, const LegTile *tiles, int ntil
                                int L, int M, int Kh, int ldc, int B, cudaStream_t st) {
   if (ntiles == 0 || B <= 0) return cudaSuccess;
   const int nct = (2 * B + kTileC - 1) / kTileC;
-  leg_fwd_f32_kernel<<<(unsigned)ntiles * nct, kThreads, 0, st>>>(T, tiles, Fw, xhat, L, M, Kh, ldc, B, nct);
+  leg_fwd_f32_kernel<<<(unsigned)ntiles * nct, kLegThreads, 0, st>>>(T, tiles, Fw, xhat, L, M, Kh, ldc, B, nct);
   return cudaGetLastError();
 }
 
@@ -271,7 +320,7 @@ cudaError_t launch_leg_inv_f32(const TableF32 &T, const LegTile *tiles, int ntil
                                int L, int M, int Kh, int ldc, int B, cudaStream_t st) {
   if (ntiles == 0 || B <= 0) return cudaSuccess;
   const int nct = (2 * B + kTileC - 1) / kTileC;
-  leg_inv_f32_kernel<<<(unsigned)ntiles * nct, kThreads, 0, st>>>(T, tiles, yhat, Gw, L, M, Kh, ldc, B, nct);
+  leg_inv_f32_kernel<<<(unsigned)ntiles * nct, kLegThreads, 0, st>>>(T, tiles, yhat, Gw, L, M, Kh, ldc, B, nct);
   return cudaGetLastError();
 }
 
@@ -302,9 +351,9 @@ cudaError_t launch_leg_f32_group(int inverse, const F32LegItem *items, int n, cu
   if (g.nseg == 0) return cudaSuccess;
   if (blk > 0x7fffffff) return cudaErrorInvalidValue;
   if (inverse)
-    leg_inv_f32_grouped<<<(unsigned)blk, kThreads, 0, st>>>(g);
+    leg_inv_f32_grouped<<<(unsigned)blk, kLegThreads, 0, st>>>(g);
   else
-    leg_fwd_f32_grouped<<<(unsigned)blk, kThreads, 0, st>>>(g);
+    leg_fwd_f32_grouped<<<(unsigned)blk, kLegThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 
