@@ -15,18 +15,17 @@ constexpr int kTO = 32;   // output channels per CTA
 constexpr int kTM = 64;   // orders m per CTA
 constexpr int kTK = 16;   // reduction chunk (input channels)
 constexpr int kThreads = 256;
+constexpr int kFThreads = 128;  // filter: 4 outputs x 4 orders per thread
 
-__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
-  c.x = fmaf(a.x, b.x, c.x);
-  c.x = fmaf(-a.y, b.y, c.x);
-  c.y = fmaf(a.x, b.y, c.y);
-  c.y = fmaf(a.y, b.x, c.y);
-  return c;
+// c + a b (complex) on packed two-lane FMAs, with a given as its broadcast
+// pairs ar = (Re a, Re a), ai = (-Im a, Im a) and b as b, bs = (Im b, Re b).
+__device__ __forceinline__ float2 cfma2(float2 ar, float2 ai, float2 b, float2 bs, float2 c) {
+  return __ffma2_rn(ai, bs, __ffma2_rn(ar, b, c));
 }
 
 // grid: x = l * mtiles + mt, y = output-channel tile, z = member b
 template <bool kAdjoint>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFThreads)
 filter_kernel(const float2 *__restrict__ x, const float2 *__restrict__ W, float2 *__restrict__ y, int L, int M,
               int Cin, int Cout) {
   __shared__ __align__(16) float2 Ws[kTK][kTO];
@@ -42,24 +41,24 @@ filter_kernel(const float2 *__restrict__ x, const float2 *__restrict__ W, float2
   const int64_t LM = (int64_t)L * M;
   const float2 *xb = x + b * Cred * LM + (int64_t)l * M;
   float2 *yb = y + b * Cout_ * LM + (int64_t)l * M;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty: 2 outputs, tx: 4 orders
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // ty: 4 outputs, tx: 4 orders
   if (m0 > l) {
     // whole tile above the diagonal: zeros
-    for (int e = threadIdx.x; e < kTO * kTM; e += kThreads) {
+    for (int e = threadIdx.x; e < kTO * kTM; e += kFThreads) {
       const int oo = e / kTM, mm = e - oo * kTM;
       if (o0 + oo < Cout_ && m0 + mm < M) yb[(int64_t)(o0 + oo) * LM + m0 + mm] = make_float2(0.f, 0.f);
     }
     return;
   }
-  float2 acc[2][4];
+  float2 acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 2; i++)
+  for (int i = 0; i < 4; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
   const int mlim = min(M, l + 1);
   for (int k0 = 0; k0 < Cred; k0 += kTK) {
     // W tile: Ws[kk][oo] = Wmat(o0 + oo, k0 + kk)
-    for (int e = threadIdx.x; e < kTK * kTO; e += kThreads) {
+    for (int e = threadIdx.x; e < kTK * kTO; e += kFThreads) {
       int kk, oo;
       float2 w = make_float2(0.f, 0.f);
       if (!kAdjoint) {
@@ -76,7 +75,7 @@ filter_kernel(const float2 *__restrict__ x, const float2 *__restrict__ W, float2
       }
       Ws[kk][oo] = w;
     }
-    for (int e = threadIdx.x; e < kTK * kTM; e += kThreads) {
+    for (int e = threadIdx.x; e < kTK * kTM; e += kFThreads) {
       const int kk = e / kTM, mm = e - kk * kTM;
       float2 v = make_float2(0.f, 0.f);
       if (k0 + kk < Cred && m0 + mm < mlim) v = xb[(int64_t)(k0 + kk) * LM + m0 + mm];
@@ -85,19 +84,28 @@ filter_kernel(const float2 *__restrict__ x, const float2 *__restrict__ W, float2
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kTK; kk++) {
-      const float2 w0 = Ws[kk][ty * 2 + 0], w1 = Ws[kk][ty * 2 + 1];
+      float2 wr[4], wi[4], xv[4], xs[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const float2 w = Ws[kk][ty * 4 + i];
+        wr[i] = make_float2(w.x, w.x);
+        wi[i] = make_float2(-w.y, w.y);
+      }
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        const float2 xv = Xs[kk][tx + 16 * j];
-        acc[0][j] = cfma(w0, xv, acc[0][j]);
-        acc[1][j] = cfma(w1, xv, acc[1][j]);
+        xv[j] = Xs[kk][tx + 16 * j];
+        xs[j] = make_float2(xv[j].y, xv[j].x);
       }
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = cfma2(wr[i], wi[i], xv[j], xs[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; i++) {
-    const int o = o0 + ty * 2 + i;
+  for (int i = 0; i < 4; i++) {
+    const int o = o0 + ty * 4 + i;
     if (o >= Cout_) continue;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -177,9 +185,9 @@ cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L, in
   const int cout = adjoint ? Cin : Cout;
   dim3 grid(L * mtiles, (cout + kTO - 1) / kTO, (unsigned)Bm);
   if (adjoint)
-    filter_kernel<true><<<grid, kThreads, 0, st>>>(x, W, y, L, M, Cin, Cout);
+    filter_kernel<true><<<grid, kFThreads, 0, st>>>(x, W, y, L, M, Cin, Cout);
   else
-    filter_kernel<false><<<grid, kThreads, 0, st>>>(x, W, y, L, M, Cin, Cout);
+    filter_kernel<false><<<grid, kFThreads, 0, st>>>(x, W, y, L, M, Cin, Cout);
   return cudaGetLastError();
 }
 
