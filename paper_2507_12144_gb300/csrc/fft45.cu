@@ -361,6 +361,7 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
     const float2 *Zb = Za + BUF;
     int r = m0 % kQ, q = m0 / kQ;
     int64_t o = fold_row(fl, m0, 0, kq) + col;
+#pragma unroll 2
     for (int m = m0; m < M; m += kMStep, o += kMStep * fl.sm) {
       // X[m] sits at spec_index(m); X[N - m] at spec_index(N - m)
       const int im = r * rpitch<P>() + q;
@@ -403,7 +404,7 @@ r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, FoldL
   r2c45_body<P, Out>(blockIdx.x, blockIdx.y, x, out, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
 }
 
-template <int P>
+template <int P, int kBatch>
 __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restrict__ Gw, float *__restrict__ y,
                                            int nlat, int M, int B, FoldLayout fl, const float2 *__restrict__ twiddle,
                                            const float *__restrict__ ring_scale, int inverse_weights) {
@@ -419,8 +420,9 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   // stage conj(Z) (c_m / 2 * ring scale * G of the northern and southern
   // rows, as the Hermitian sequences' Z = H_n + i H_s) in every sequence
   // buffer; thread (f2, m0) stages fields 2 f2 and 2 f2 + 1 (one 16-byte
-  // load per row), orders m0, m0 + 64, ..., kBatch loads in flight
-  constexpr int kBatch = 6;
+  // load per row), orders m0, m0 + 64, ..., kBatch loads in flight (12:
+  // all of a thread's orders at nlon = 1440 in one memory round trip; the
+  // grouped kernel, which holds every P's body, keeps 6 to stay unspilled)
   constexpr int kPairs = kFB / 2;
   constexpr int kMStep = kThreads / kPairs;  // 64
   const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
@@ -537,7 +539,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, 2)
 c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, FoldLayout fl,
              const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights) {
-  c2r45_body<P>(blockIdx.x, blockIdx.y, Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
+  c2r45_body<P, 12>(blockIdx.x, blockIdx.y, Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
 }
 
 // Grouped launches: one grid over several problems (grids and batches) of
@@ -595,10 +597,10 @@ __global__ void __launch_bounds__(kThreads, 2) c2r45_grouped_kernel(const __grid
   const int local = blockIdx.x - q.blk0;
   const int bx = local % q.gx, by = local / q.gx;
   switch (q.P) {
-    case 32: c2r45_body<32>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
-    case 16: c2r45_body<16>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
-    case 8: c2r45_body<8>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
-    default: c2r45_body<4>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    case 32: c2r45_body<32, 6>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    case 16: c2r45_body<16, 6>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    case 8: c2r45_body<8, 6>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
+    default: c2r45_body<4, 6>(bx, by, q.in, q.outf, q.nlat, q.M, q.B, q.fl, q.tw, q.ring, q.wts); break;
   }
 }
 
