@@ -8,7 +8,7 @@
  *   forward SHT   xhat_lm = int u conj(Y_lm) dmu                       Eq. (sht)
  *                 = sum_k w_k (2 pi / nlon) Phat_l^m(x_k) sum_j u_kj e^{-i m phi_j}
  *                 (longitude FFT, then a Legendre contraction whose
- *                 quadrature weights are folded in: Sec. B.3, Sec. F.2.2
+ *                 quadrature weights are folded in: Sec. B.3, Sec. G.2.2
  *                 Algorithm 1)
  *   filter        yhat[b][o][l][m] = sum_i W[l][o][i] xhat[b][i][l][m]
  *                 (the convolution theorem Eq. (s2_spectral_conv), with the

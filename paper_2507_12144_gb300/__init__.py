@@ -1,7 +1,7 @@
 """shtgb: GB300-native spherical harmonic transforms and spectral filtering.
 
 The global operation of FourCastNet 3's spherical neural-operator blocks
-(arXiv 2507.12144, Sec. B.3 and Sec. F.2.2): forward SHT (longitude FFT +
+(arXiv 2507.12144, Sec. B.3 and Sec. G.2.2): forward SHT (longitude FFT +
 quadrature-weighted Legendre contraction), a per-degree complex
 channel-mixing filter (Eq. s2_spectral_conv generalised), and the inverse
 SHT, with their adjoints.

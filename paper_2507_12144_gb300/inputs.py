@@ -10,12 +10,16 @@ Recipes (stand-ins for ERA5, which is not available here):
 * ``spectral_coeffs(..., spectrum="l-3")``: complex Gaussian coefficients with
   per-coefficient variance (l+1)^-3 / (2l+1), so that the angular power
   spectrum sum_{|m|<=l} |u_lm|^2 of Eq. (psd) falls off like (l+1)^-3, the
-  slope atmospheric fields show (Sec. E.7).  Band-limited to l < L, zero for
+  slope atmospheric fields show (Sec. F.7).  Band-limited to l < L, zero for
   l < m, Im of m = 0 set to zero (real field).
 * ``spectrum="l-1.5"``: re, im ~ N(0, 1) scaled by (l+1)^-1.5 (the small
   round-trip case on a 33 x 64 Gaussian grid).
 * ``filter_weights``: W[l][o][i] with Re, Im i.i.d. N(0, 1/(2 Cin)), so that
   E|W|^2 = 1/Cin.
+* ``ensemble_coefficients``: an ensemble of E members and one observation
+  per channel that are exchangeable (an ideal ensemble): a shared draw s
+  plus an independent draw per member and for the observation, all with the
+  (l+1)^-3 spectrum, the independent ones scaled by ``spread``.
 """
 from __future__ import annotations
 
@@ -70,3 +74,13 @@ def scales_and_rolls(seed: int, n: int, nlon: int):
     """Per-field amplitude scale in [0.5, 2) and longitude roll in [0, nlon)."""
     g = rng(seed)
     return g.uniform(0.5, 2.0, size=n), g.integers(0, nlon, size=n)
+
+
+def ensemble_coefficients(seed: int, E: int, C: int, L: int, M: int, spread: float = 0.5,
+                          spectrum: str = "l-3"):
+    """(ens complex128 [E, C, L, M], obs complex128 [C, L, M]) drawn as
+    s + spread * n_e and s + spread * n_obs, all of them real-field
+    coefficients (zero for l < m, Im(m = 0) = 0)."""
+    s = spectral_coeffs(seed, (C,), L, M, spectrum=spectrum)
+    n = spectral_coeffs(seed + 1, (E + 1, C), L, M, spectrum=spectrum)
+    return s[None] + spread * n[:E], s + spread * n[E]
