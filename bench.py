@@ -14,6 +14,9 @@ the dominant kernel.
   python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
   python bench.py --workload batched ... # forward + inverse SHT of an uneven
                                          # mix of four grids, one CUDA graph each
+  python bench.py --workload scores ...  # angular power spectrum + spectral
+                                         # CRPS of a 16-member x 72-channel
+                                         # ensemble of 720 x 720 coefficients
 
 Multi-GPU runs (torchrun) are independent replicas: the path has no
 exchange step, so every rank transforms its own batch (weak scaling).
@@ -47,6 +50,26 @@ FALLBACK_HBM_GBS = 6800.0
 BATCH_MIX = [(91, 180, 90, 32 * 256), (181, 360, 180, 16 * 128), (361, 720, 360, 4 * 256), (721, 1440, 720, 72)]
 BATCH_METRIC = ("batched SHT+ISHT field-transforms/s over 91x180 (32x256), 181x360 (16x128), "
                 "361x720 (4x256), 721x1440 (1x72), lmax = nlat-1")
+
+
+# ensemble-scores workload: the training ensemble (16 members) of the 72
+# channels, coefficients of lmax = mmax = 720
+SCORE_E, SCORE_C, SCORE_L = 16, 72, 720
+SCORE_LO = 1  # Eq. (spectral_loss) sums the degrees from 1
+SCORE_METRIC = ("ensemble-scored member fields/s: angular PSD + spectral CRPS, 16 members x 72 channels, "
+                "lmax=mmax=720; roofline fraction")
+SCORE_UNIT = "member fields/s"
+
+
+def scores_config() -> dict:
+    return {
+        "workload": "angular PSD (Eq. psd) of every member + spectral CRPS (Eq. spectral_loss, biased form, "
+                    "degrees 1..719) of a 16-member x 72-channel ensemble, lmax=mmax=720",
+        "members": SCORE_E, "channels": SCORE_C, "lmax": SCORE_L, "mmax": SCORE_L, "fair": False,
+        "spectrum": "(l+1)^-3, exchangeable members and observation, seeded",
+        "l2": "inputs larger than L2: 4.9 GB of coefficients read per step",
+        "parallelism": "replicas",
+    }
 
 
 def workload_config(precision: str, table_source: str = "streamed") -> dict:
@@ -107,6 +130,8 @@ def kernel_sources(kernel: str, precision: str):
         "leg_inv": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/legendre_f32.cu"],
         "filter": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/filter.cu"],
         "filter_prep": ["paper_2507_12144_gb300/csrc/legendre_tc.cu"],
+        "crps": ["paper_2507_12144_gb300/csrc/scores.cu"],
+        "psd": ["paper_2507_12144_gb300/csrc/scores.cu"],
     }
     return table.get(kernel, [])
 
@@ -353,6 +378,44 @@ class BatchedOracleSampler:
                 "field, forward and inverse")
 
 
+class ScoresOracleSampler:
+    """The FP64 oracle (oracle/scores.py), as it stands, on a slab of the
+    scores workload: one channel of the 16-member ensemble, degrees [0, R)
+    (the angular PSD of every member and the spectral CRPS on those rows).
+    A slab counts its share of the l >= m coefficients of a member field."""
+
+    def __init__(self, seed: int = 7):
+        from oracle import scores
+        from paper_2507_12144_gb300 import inputs
+        self.scores = scores
+        e, o = inputs.ensemble_coefficients(seed, SCORE_E, 1, SCORE_L, SCORE_L)
+        self.ens = e.astype(np.complex64).astype(np.complex128)
+        self.obs = o.astype(np.complex64).astype(np.complex128)
+        self.tri_cum = np.cumsum([l + 1 for l in range(SCORE_L)])
+        self.cores = 1  # elementwise numpy on one thread
+
+    def step(self, rows: int):
+        self.scores.angular_psd(self.ens[:, :, :rows])
+        _, crps_l = self.scores.spectral_crps(self.ens[:, :, :rows], self.obs[:, :rows])
+        self.scores.spectral_crps_loss(crps_l, SCORE_LO, rows)
+
+    def fields_per_step(self, rows: int) -> float:
+        return SCORE_E * self.tri_cum[rows - 1] / self.tri_cum[-1]
+
+    def calibrate(self, target_s: float) -> int:
+        """Degree rows per step so that one step takes about target_s seconds."""
+        r = 90
+        t0 = time.perf_counter()
+        self.step(r)
+        dt = max(time.perf_counter() - t0, 1e-3)
+        return int(min(SCORE_L, max(1, round(r * target_s / dt))))
+
+    def describe(self, rows: int) -> str:
+        return (f"1 channel x {SCORE_E} members, degrees [0,{rows}) of 720: angular PSD of every member and the "
+                f"spectral CRPS (numpy FP64 oracle); counts {self.tri_cum[rows - 1]}/{self.tri_cum[-1]} of the "
+                "coefficients per member field")
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args.gpus)
     if rank != 0:
@@ -360,6 +423,8 @@ def run_reference(args):
         return 0
     if args.workload == "batched":
         return run_reference_batched(args, world)
+    if args.workload == "scores":
+        return run_reference_scores(args, world)
     s = OracleSampler()
     budget = args.ref_seconds / max(1, args.steps + args.warmup)
     rows = s.calibrate(min(budget, 20.0))
@@ -406,6 +471,41 @@ def run_reference_batched(args, world):
     sys.stdout.flush()
     barrier(world)
     return 0
+
+
+def run_reference_scores(args, world):
+    s = ScoresOracleSampler()
+    rows = s.calibrate(min(args.ref_seconds / max(1, args.steps + args.warmup), 20.0))
+    for _ in range(args.warmup):
+        s.step(rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(rows)
+    dt = time.perf_counter() - t0
+    value = args.steps * s.fields_per_step(rows) / dt
+    line = {
+        "impl": "reference", "metric": SCORE_METRIC, "value": value, "unit": SCORE_UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": scores_config(),
+        "cpu_baseline": {"value": value, "unit": SCORE_UNIT, "cores": s.cores, "kind": "oracle",
+                         "sample": s.describe(rows)},
+        "e2e": {"value": value, "unit": SCORE_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    barrier(world)
+    return 0
+
+
+def cpu_baseline_scores(target_s: float = 10.0) -> dict:
+    s = ScoresOracleSampler()
+    rows = s.calibrate(target_s)
+    t0 = time.perf_counter()
+    s.step(rows)
+    dt = time.perf_counter() - t0
+    return {"value": s.fields_per_step(rows) / dt, "unit": SCORE_UNIT, "cores": s.cores, "kind": "oracle",
+            "sample": s.describe(rows) + f"; one slab, {dt:.1f} s"}
 
 
 def cpu_baseline_batched() -> dict:
@@ -703,15 +803,135 @@ def run_gpu_batched(args):
     return 0
 
 
+def run_gpu_scores(args):
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+
+    import paper_2507_12144_gb300 as shtgb
+    from paper_2507_12144_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E, C, L = SCORE_E, SCORE_C, SCORE_L
+    # 4 seeded base channels under power-of-two scales (exact in FP32)
+    nb = 4
+    eb, ob = inputs.ensemble_coefficients(70 + rank, E, nb, L, L)
+    eb = torch.from_numpy(eb.astype(np.complex64)).to(dev)
+    ob = torch.from_numpy(ob.astype(np.complex64)).to(dev)
+    ens = torch.empty((E, C, L, L), dtype=torch.complex64, device=dev)
+    obs = torch.empty((C, L, L), dtype=torch.complex64, device=dev)
+    for c in range(C):
+        sc = float(2.0 ** (c % 5 - 2))
+        ens[:, c] = eb[:, c % nb] * sc
+        obs[c] = ob[c % nb] * sc
+    del eb, ob
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step(timed=None):
+        if timed is not None:
+            timed[0].record(stream)
+        psd = shtgb.angular_psd(ens)
+        if timed is not None:
+            timed[1].record(stream)
+        crps_l, loss = shtgb.spectral_crps(ens, obs, fair=False, l_range=(SCORE_LO, L))
+        if timed is not None:
+            timed[2].record(stream)
+        return psd, crps_l, loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # per-kernel durations (events around each call), then the timed region
+    kt = {"psd": 0.0, "crps": 0.0}
+    nk = max(3, min(args.steps, 50))
+    for _ in range(nk):
+        step(ev)
+        ev[2].synchronize()
+        kt["psd"] += ev[0].elapsed_time(ev[1])
+        kt["crps"] += ev[1].elapsed_time(ev[2])
+    clocks = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    value = world * E * C / (ms_step * 1e-3)
+    T = n_triangle(L, L)
+    alg = {"crps": (E + 1) * C * T * 8.0 + C * L * 4.0 + C * 4.0, "psd": E * C * T * 8.0 + E * C * L * 4.0}
+    dom = max(kt, key=kt.get)
+    per_launch_s = kt[dom] / nk * 1e-3
+    peak, peak_kind = load_peaks()
+    achieved = alg[dom] / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "traffic": measured_traffic(dom, "scores"),
+                "algorithmic_bytes_per_launch": alg[dom], "kernel_ms_per_launch": per_launch_s * 1e3}
+    kernels = {k: {"ms_per_launch": v / nk, "GB_per_s": alg[k] / (v / nk * 1e-3) / 1e9} for k, v in kt.items()}
+
+    # end to end: the ensemble and observation copied in from pinned host
+    # memory, the per-degree scores and losses read back, every step
+    e2e_steps = 3
+    h_ens = ens.cpu().pin_memory()
+    h_obs = obs.cpu().pin_memory()
+    h_psd = torch.empty((E, C, L), dtype=torch.float32, pin_memory=True)
+    h_crps = torch.empty((C, L), dtype=torch.float32, pin_memory=True)
+    h_loss = torch.empty((C,), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ens.copy_(h_ens, non_blocking=True)
+        obs.copy_(h_obs, non_blocking=True)
+        psd, crps_l, loss = step()
+        h_psd.copy_(psd, non_blocking=True)
+        h_crps.copy_(crps_l, non_blocking=True)
+        h_loss.copy_(loss, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    if rank == 0:
+        line = {
+            "metric": SCORE_METRIC, "value": value, "unit": SCORE_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded (l+1)^-3 ensembles, 4 base channels under power-of-two scales",
+            "config": scores_config(), "roofline": roofline, "kernels": kernels,
+            "gpu_launches": 3 * args.steps,
+            "e2e": {"value": world * E * C * e2e_steps / e2e_s, "unit": SCORE_UNIT,
+                    "h2d_bytes_per_step": int(ens.numel() * 8 + obs.numel() * 8),
+                    "d2h_bytes_per_step": int((E * C * L + C * L + C) * 4), "steps": e2e_steps},
+            "clocks": clk,
+            "cpu_baseline": cpu_baseline_scores(args.cpu_seconds) if world == 1 and not args.no_cpu_baseline else None,
+        }
+        print(json.dumps(line))
+        sys.stdout.flush()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["block", "batched"], default="block",
+    ap.add_argument("--workload", choices=["block", "batched", "scores"], default="block",
                     help="block: SHT -> filter -> ISHT at 721x1440 (the headline); batched: forward + inverse "
-                         "SHT of the uneven four-grid mix")
+                         "SHT of the uneven four-grid mix; scores: angular PSD + spectral CRPS of a "
+                         "16-member ensemble")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
     ap.add_argument("--no-fp32-side", action="store_true",
                     help="skip timing the plain FP32 form beside a tensor-core precision")
@@ -730,6 +950,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batched":
         return run_gpu_batched(args)
+    if args.workload == "scores":
+        return run_gpu_scores(args)
     return run_gpu(args)
 
 

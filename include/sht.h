@@ -359,6 +359,74 @@ sht_status_t sht_batch_profile_collect(sht_batch_t batch, int64_t *runs,
 /* Release the graph and the batch (not the plans or the buffers). */
 sht_status_t sht_batch_destroy(sht_batch_t batch);
 
+/* ------------------------------------------------------------------------
+ * Ensemble scores (Sec. D.4, Sec. E.1, Sec. F.7)
+ *
+ * Scores of E-member ensembles against one observation, computed on the
+ * coefficients a forward transform produces (or on the grid).  They need no
+ * plan except the spatial CRPS, which takes the grid's quadrature weights
+ * from one.  Every result is summed in a fixed order (deterministic).
+ * FP32 arithmetic.  Pointers as everywhere else: device, 16-byte aligned,
+ * contiguous, on the current device (the plan's for sht_spatial_crps).
+ * ------------------------------------------------------------------------ */
+
+/* Angular power spectrum, Eq. (psd), of B coefficient arrays:
+ *   psd[b][l] = |xhat[b][l][0]|^2 + 2 sum_{m = 1}^{min(l, mmax - 1)} |xhat[b][l][m]|^2
+ * (the sum over |m| <= l of a real field, whose m < 0 coefficients have the
+ * moduli of m > 0).  xhat: complex64 [B][lmax][mmax], read at l >= m only;
+ * psd: float32 [B][lmax].  Needs 1 <= mmax <= lmax; B = 0 is a no-op. */
+sht_status_t sht_angular_psd(const void *xhat, float *psd, int64_t B, int lmax,
+                             int mmax, void *stream);
+
+/* Spectral CRPS, Eq. (spectral_loss): for every channel c and degree l
+ *   crps_l[c][l] = sum_{|m| <= l} CRPS(u_l^m) = c_l0 + 2 sum_{m >= 1} c_lm,
+ *   c_lm = CRPS(Re ens[.][c][l][m], Re obs[c][l][m])
+ *        + CRPS(Im ens[.][c][l][m], Im obs[c][l][m]),
+ * with the ensemble CRPS of Eq. (spread_skill_crps) (fair = 0) or the fair
+ * CRPS of Eq. (fair_spread_skill_crps) (fair = 1), computed on the sorted
+ * members.
+ *   ens:     complex64 [E][C][lmax][mmax], members first (the layout of
+ *            sht_forward applied to E x C fields), read at l >= m only;
+ *   obs:     complex64 [C][lmax][mmax];
+ *   crps_l:  float32 [C][lmax], required;
+ *   crps_lm: float32 [C][lmax][mmax] or NULL: c_lm, 0 at l < m;
+ *   loss:    float32 [C] or NULL: sum_{l_lo <= l < l_hi} crps_l[c][l].
+ * 1 <= E <= 64 (E >= 2 for the fair form), 0 <= l_lo <= l_hi <= lmax,
+ * C >= 0 (C = 0 is a no-op). */
+sht_status_t sht_spectral_crps(const void *ens, const void *obs, float *crps_l,
+                               float *crps_lm, float *loss, int E, int64_t C,
+                               int lmax, int mmax, int fair, int l_lo,
+                               int l_hi, void *stream);
+
+/* Gradient of the loss output of sht_spectral_crps, for training with it:
+ *   gens[e][c][l][m] = gloss[c] d loss[c] / d ens[e][c][l][m],
+ *   gobs[c][l][m]    = gloss[c] d loss[c] / d obs[c][l][m]   (gobs NULL: skipped),
+ * complex64, each entry d/dRe + i d/dIm (PyTorch's convention for a real
+ * function of complex values).  Per real value with members u_e and
+ * observation u*,
+ *   d CRPS / d u_e = sign(u_e - u*) / E - (1/D) sum_i sign(u_e - u_i),
+ *   d CRPS / d u*  = -(1/E) sum_e sign(u_e - u*),       sign(0) = 0
+ * (at ties the subgradient that averages the tied ranks), D = E^2
+ * (fair = 0) or E (E - 1) (fair = 1); m > 0 counts twice.  Both
+ * outputs are written everywhere: zero outside l_lo <= l < l_hi and at
+ * l < m.  gloss: float32 [C]; other arguments as for sht_spectral_crps. */
+sht_status_t sht_spectral_crps_backward(const void *ens, const void *obs,
+                                        const float *gloss, void *gens, void *gobs,
+                                        int E, int64_t C, int lmax, int mmax,
+                                        int fair, int l_lo, int l_hi,
+                                        void *stream);
+
+/* Spatial CRPS, Eq. (spatial_loss): the point-wise CRPS averaged over the
+ * sphere with the plan's grid and quadrature,
+ *   crps_k[c][k] = (1 / (4 pi)) w_k (2 pi / nlon) sum_j CRPS(ens[.][c][k][j], obs[c][k][j]),
+ *   loss[c]      = sum_k crps_k[c][k].
+ * ens: float32 [E][C][nlat][nlon], obs: float32 [C][nlat][nlon], crps_k:
+ * float32 [C][nlat] (required), loss: float32 [C] or NULL.  E and fair as
+ * for sht_spectral_crps. */
+sht_status_t sht_spatial_crps(sht_plan_t plan, const float *ens, const float *obs,
+                              float *crps_k, float *loss, int E, int64_t C,
+                              int fair, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Per-kernel timing.  While profiling is on, every kernel a plan's execute
  * calls launch is bracketed by two CUDA events recorded on the launch

@@ -18,6 +18,8 @@ E.1 and Sec. F.7):
   every coefficient u_l^m over |m| <= l;
 * ``spatial_crps``: the point-wise CRPS averaged over the sphere with the
   grid's quadrature, Eq. (spatial_loss);
+* ``crps_grad`` and ``spectral_crps_loss_grad``: the derivatives of the
+  spread-skill form (for training with the loss);
 * ``angular_psd``: Eq. (psd).
 
 Readings where the paper leaves the form open:
@@ -127,6 +129,44 @@ def spectral_crps_loss(crps_l, l_lo: int, l_hi: int):
     """sum_{l_lo <= l < l_hi} of the per-degree spectral CRPS, per channel."""
     crps_l = np.asarray(crps_l, dtype=np.float64)
     return np.sum(crps_l[..., l_lo:l_hi], axis=-1)
+
+
+def crps_grad(u, obs, fair: bool = False, axis: int = 0):
+    """Derivatives of the CRPS of Eq. (spread_skill_crps) / Eq.
+    (fair_spread_skill_crps) with respect to the members and the observation,
+    vectorised like ``crps_spread_skill``:
+      d/du_e = (1/N) sign(u_e - obs) - (1/D) sum_i sign(u_e - u_i)
+      d/dobs = -(1/N) sum_e sign(u_e - obs)
+    (the double sum holds u_e in both places), D = N^2 or N (N - 1), with
+    sign(0) = 0: at ties this is the subgradient that averages the ranks."""
+    u = np.moveaxis(np.asarray(u, dtype=np.float64), axis, 0)
+    obs = np.asarray(obs, dtype=np.float64)
+    n = u.shape[0]
+    D = n * (n - 1) if fair else n * n
+    s_obs = np.sign(u - obs[None])
+    pair = np.zeros_like(u)
+    for i in range(n):
+        pair = pair + np.sign(u - u[i][None])
+    gu = s_obs / n - pair / D
+    gobs = -np.sum(s_obs, axis=0) / n
+    return np.moveaxis(gu, 0, axis), gobs
+
+
+def spectral_crps_loss_grad(ens, obs, gloss, l_lo: int, l_hi: int, fair: bool = False):
+    """Gradient of loss[c] = sum_{l_lo <= l < l_hi} crps_l[c][l] (Eq.
+    (spectral_loss)) weighted by gloss[c]: complex arrays d/dRe + i d/dIm,
+    (gens [E, C, L, M], gobs [C, L, M]), zero outside the degree range and
+    at l < m."""
+    ens = np.asarray(ens, dtype=np.complex128)
+    obs = np.asarray(obs, dtype=np.complex128)
+    E, C, L, M = ens.shape
+    gr, gor = crps_grad(ens.real, obs.real, fair)
+    gi, goi = crps_grad(ens.imag, obs.imag, fair)
+    l = np.arange(L)[:, None]
+    w = np.where((l >= np.arange(M)[None, :]) & (l >= l_lo) & (l < l_hi),
+                 np.where(np.arange(M) == 0, 1.0, 2.0)[None, :], 0.0)
+    w = np.asarray(gloss, dtype=np.float64)[:, None, None] * w[None]
+    return (gr + 1j * gi) * w[None], (gor + 1j * goi) * w
 
 
 def angular_psd(xhat):

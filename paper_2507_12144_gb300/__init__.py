@@ -22,7 +22,8 @@ from ._abi import ShtError
 
 __all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
-           "SpectralBlock", "spectral_block", "ShtError"]
+           "SpectralBlock", "spectral_block", "angular_psd", "spectral_crps", "spectral_crps_backward",
+           "spectral_crps_loss", "SpectralCRPSLoss", "sht_forward_ad", "SHTForward", "spatial_crps", "ShtError"]
 
 
 def _stream(t: torch.Tensor):
@@ -443,3 +444,127 @@ class SpectralBlock(torch.autograd.Function):
 
 def spectral_block(x: torch.Tensor, W: torch.Tensor, plan: Plan) -> torch.Tensor:
     return SpectralBlock.apply(x, W, plan)
+
+
+# ---------------------------------------------------------------------------
+# ensemble scores (Sec. D.4, Sec. E.1, Sec. F.7)
+# ---------------------------------------------------------------------------
+
+def angular_psd(xhat: torch.Tensor) -> torch.Tensor:
+    """Eq. (psd) of complex64 coefficients [..., lmax, mmax] -> float32
+    [..., lmax]: |u_l0|^2 + 2 sum_{1 <= m <= l} |u_lm|^2."""
+    x = _need(xhat, torch.complex64, "xhat", None)
+    if x.dim() < 2:
+        raise ValueError("xhat must end in (lmax, mmax)")
+    L, M = int(x.shape[-2]), int(x.shape[-1])
+    lead = tuple(x.shape[:-2])
+    B = int(torch.tensor(lead).prod().item()) if lead else 1
+    out = torch.empty(lead + (L,), dtype=torch.float32, device=x.device)
+    with torch.cuda.device(x.device):
+        _abi.check(_abi.lib().sht_angular_psd(_ptr(x), _ptr(out), B, L, M, _stream(x)))
+    return out
+
+
+def spectral_crps(ens: torch.Tensor, obs: torch.Tensor, fair: bool = False, l_range=None,
+                  per_coefficient: bool = False):
+    """Spectral CRPS, Eq. (spectral_loss), of an ensemble of coefficients.
+
+    ens: complex64 [E, C, lmax, mmax] (members first), obs: complex64
+    [C, lmax, mmax].  Returns (crps_l [C, lmax], loss [C]) and, with
+    ``per_coefficient``, crps_lm [C, lmax, mmax] as a third item.  ``loss``
+    sums the degrees in ``l_range`` = (l_lo, l_hi) (default: all).
+    ``fair`` selects Eq. (fair_spread_skill_crps)."""
+    ens = _need(ens, torch.complex64, "ens", None)
+    obs = _need(obs, torch.complex64, "obs", ens.device)
+    if ens.dim() != 4 or obs.shape != ens.shape[1:]:
+        raise ValueError("ens must be [E, C, lmax, mmax] and obs [C, lmax, mmax]")
+    E, C, L, M = (int(v) for v in ens.shape)
+    l_lo, l_hi = (0, L) if l_range is None else (int(l_range[0]), int(l_range[1]))
+    crps_l = torch.empty((C, L), dtype=torch.float32, device=ens.device)
+    loss = torch.empty((C,), dtype=torch.float32, device=ens.device)
+    crps_lm = torch.empty((C, L, M), dtype=torch.float32, device=ens.device) if per_coefficient else None
+    with torch.cuda.device(ens.device):
+        _abi.check(_abi.lib().sht_spectral_crps(_ptr(ens), _ptr(obs), _ptr(crps_l), _ptr(crps_lm), _ptr(loss), E, C,
+                                                L, M, int(bool(fair)), l_lo, l_hi, _stream(ens)))
+    return (crps_l, loss, crps_lm) if per_coefficient else (crps_l, loss)
+
+
+def spectral_crps_backward(ens: torch.Tensor, obs: torch.Tensor, gloss: torch.Tensor, fair: bool = False,
+                           l_range=None, need_obs: bool = False):
+    """Gradient of the ``loss`` of :func:`spectral_crps` weighted by gloss [C]:
+    (gens [E, C, lmax, mmax], gobs [C, lmax, mmax] or None), complex64."""
+    ens = _need(ens, torch.complex64, "ens", None)
+    obs = _need(obs, torch.complex64, "obs", ens.device)
+    gloss = _need(gloss, torch.float32, "gloss", ens.device)
+    E, C, L, M = (int(v) for v in ens.shape)
+    if obs.shape != ens.shape[1:] or gloss.shape != (C,):
+        raise ValueError("need ens [E, C, lmax, mmax], obs [C, lmax, mmax] and gloss [C]")
+    l_lo, l_hi = (0, L) if l_range is None else (int(l_range[0]), int(l_range[1]))
+    gens = torch.empty_like(ens)
+    gobs = torch.empty_like(obs) if need_obs else None
+    with torch.cuda.device(ens.device):
+        _abi.check(_abi.lib().sht_spectral_crps_backward(_ptr(ens), _ptr(obs), _ptr(gloss), _ptr(gens), _ptr(gobs),
+                                                         E, C, L, M, int(bool(fair)), l_lo, l_hi, _stream(ens)))
+    return gens, gobs
+
+
+class SpectralCRPSLoss(torch.autograd.Function):
+    """loss[c] of Eq. (spectral_loss) with its gradient from
+    ``sht_spectral_crps_backward`` (the inputs are kept, nothing else)."""
+
+    @staticmethod
+    def forward(ctx, ens, obs, fair, l_lo, l_hi):
+        _, loss = spectral_crps(ens, obs, fair=fair, l_range=(l_lo, l_hi))
+        ctx.save_for_backward(ens, obs)
+        ctx.args = (fair, l_lo, l_hi)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gloss):
+        ens, obs = ctx.saved_tensors
+        fair, l_lo, l_hi = ctx.args
+        gens, gobs = spectral_crps_backward(ens.detach(), obs.detach(), gloss.contiguous().float(), fair,
+                                            (l_lo, l_hi), need_obs=ctx.needs_input_grad[1])
+        return (gens if ctx.needs_input_grad[0] else None), gobs, None, None, None
+
+
+def spectral_crps_loss(ens: torch.Tensor, obs: torch.Tensor, fair: bool = False, l_range=None) -> torch.Tensor:
+    """Differentiable per-channel spectral CRPS loss [C] (Eq. spectral_loss);
+    ``l_range`` = (l_lo, l_hi), default all degrees."""
+    L = int(ens.shape[-2])
+    l_lo, l_hi = (0, L) if l_range is None else (int(l_range[0]), int(l_range[1]))
+    return SpectralCRPSLoss.apply(ens, obs, bool(fair), l_lo, l_hi)
+
+
+class SHTForward(torch.autograd.Function):
+    """Forward SHT whose backward is the adjoint transform (real inner
+    product), so that losses on coefficients reach the spatial fields."""
+
+    @staticmethod
+    def forward(ctx, x, plan):
+        ctx.plan = plan
+        return sht_forward(plan, x)
+
+    @staticmethod
+    def backward(ctx, g):
+        return sht_forward_adjoint(ctx.plan, g.contiguous()), None
+
+
+def sht_forward_ad(x: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return SHTForward.apply(x, plan)
+
+
+def spatial_crps(plan: Plan, ens: torch.Tensor, obs: torch.Tensor, fair: bool = False):
+    """Spatial CRPS, Eq. (spatial_loss), on the plan's grid: ens float32
+    [E, C, nlat, nlon], obs float32 [C, nlat, nlon] -> (crps_k [C, nlat],
+    loss [C]), crps_k being each latitude row's share of the loss."""
+    ens = _need(ens, torch.float32, "ens", plan.device)
+    obs = _need(obs, torch.float32, "obs", plan.device)
+    if ens.dim() != 4 or ens.shape[2:] != (plan.nlat, plan.nlon) or obs.shape != ens.shape[1:]:
+        raise ValueError(f"ens must be [E, C, {plan.nlat}, {plan.nlon}] and obs [C, {plan.nlat}, {plan.nlon}]")
+    E, C = int(ens.shape[0]), int(ens.shape[1])
+    crps_k = torch.empty((C, plan.nlat), dtype=torch.float32, device=ens.device)
+    loss = torch.empty((C,), dtype=torch.float32, device=ens.device)
+    _abi.check(_abi.lib().sht_spatial_crps(plan.handle, _ptr(ens), _ptr(obs), _ptr(crps_k), _ptr(loss), E, C,
+                                           int(bool(fair)), _stream(ens)))
+    return crps_k, loss

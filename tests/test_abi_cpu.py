@@ -139,3 +139,32 @@ def test_pipe_rejects_bad_arguments_before_any_cuda_call(lib):
 
 def test_stall_hook_rejects_null_plan(lib):
     assert lib.sht_debug_stall(None, 1000, None) == 1
+
+
+def test_scores_reject_bad_arguments_before_any_cuda_call(lib):
+    p16, p8 = ctypes.c_void_p(64), ctypes.c_void_p(72)  # never dereferenced: validation fails first
+    # angular PSD: sizes, NULL and misaligned pointers; B = 0 is a no-op
+    assert lib.sht_angular_psd(p16, p16, -1, 4, 4, None) == 1
+    assert lib.sht_angular_psd(p16, p16, 1, 4, 5, None) == 1
+    assert b"mmax" in lib.sht_last_error_message()
+    assert lib.sht_angular_psd(None, p16, 1, 4, 4, None) == 1
+    assert lib.sht_angular_psd(p8, p16, 1, 4, 4, None) == 1
+    assert b"aligned" in lib.sht_last_error_message()
+    assert lib.sht_angular_psd(None, None, 0, 4, 4, None) == 0
+    # spectral CRPS: member counts, the fair form's E >= 2, the degree range
+    args = lambda E, fair=0, lo=0, hi=4, C=1: (p16, p16, p16, None, None, E, C, 4, 4, fair, lo, hi, None)
+    assert lib.sht_spectral_crps(*args(0)) == 1
+    assert lib.sht_spectral_crps(*args(65)) == 1
+    assert b"1 .. 64" in lib.sht_last_error_message()
+    assert lib.sht_spectral_crps(*args(1, fair=1)) == 1
+    assert b"fair" in lib.sht_last_error_message()
+    assert lib.sht_spectral_crps(*args(4, lo=3, hi=2)) == 1
+    assert lib.sht_spectral_crps(*args(4, hi=5)) == 1
+    assert lib.sht_spectral_crps(*args(4, C=-1)) == 1
+    assert lib.sht_spectral_crps(*args(4, C=0)) == 0
+    assert lib.sht_spectral_crps(None, p16, p16, None, None, 4, 1, 4, 4, 0, 0, 4, None) == 1
+    assert lib.sht_spectral_crps(p16, p16, p16, p8, None, 4, 1, 4, 4, 0, 0, 4, None) == 1
+    assert b"crps_lm" in lib.sht_last_error_message()
+    # spatial CRPS needs a plan
+    assert lib.sht_spatial_crps(None, p16, p16, p16, None, 4, 1, 0, None) == 1
+    assert b"plan" in lib.sht_last_error_message()

@@ -192,3 +192,50 @@ def test_spatial_crps_of_a_constant_score_is_that_score(grid):
 def test_spectral_crps_loss_sums_the_degree_range():
     crps_l = np.arange(12, dtype=np.float64).reshape(2, 6)
     np.testing.assert_array_equal(scores.spectral_crps_loss(crps_l, 1, 4), [1 + 2 + 3, 7 + 8 + 9])
+
+
+def test_crps_gradient_against_finite_differences():
+    """The CRPS is piecewise linear: away from ties, central differences of
+    the spread-skill form reproduce its derivative to rounding."""
+    g = _rng(60)
+    for E, fair in [(1, False), (2, True), (5, False), (16, True), (16, False)]:
+        u = g.standard_normal(E)
+        obs = g.standard_normal()
+        gu, gobs = scores.crps_grad(u, np.array(obs), fair=fair)
+        h = 1e-7
+        f = lambda uu, oo: float(scores.crps_spread_skill(uu, np.array(oo), fair=fair))
+        for e in range(E):
+            up, um = u.copy(), u.copy()
+            up[e] += h
+            um[e] -= h
+            assert gu[e] == pytest.approx((f(up, obs) - f(um, obs)) / (2 * h), abs=1e-7)
+        assert float(gobs) == pytest.approx((f(u, obs + h) - f(u, obs - h)) / (2 * h), abs=1e-7)
+        # translation invariance: moving everything together changes nothing
+        assert float(np.sum(gu) + gobs) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_spectral_crps_loss_gradient_against_finite_differences():
+    E, C, L, M = 3, 2, 5, 4
+    ens, obs = inputs.ensemble_coefficients(61, E, C, L, M)
+    gloss = np.array([0.7, -1.3])
+    lo, hi = 1, 4
+    gens, gobs = scores.spectral_crps_loss_grad(ens, obs, gloss, lo, hi)
+
+    def total(en, ob):
+        _, crps_l = scores.spectral_crps(en, ob)
+        return float(np.dot(gloss, scores.spectral_crps_loss(crps_l, lo, hi)))
+
+    h = 1e-7
+    for idx in [(0, 0, 2, 1), (2, 1, 3, 3), (1, 0, 1, 0), (0, 1, 4, 2), (1, 1, 0, 0)]:
+        for part in (1.0, 1j):
+            ep, em = ens.copy(), ens.copy()
+            ep[idx] += h * part
+            em[idx] -= h * part
+            fd = (total(ep, obs) - total(em, obs)) / (2 * h)
+            want = gens[idx].real if part == 1.0 else gens[idx].imag
+            assert want == pytest.approx(fd, abs=1e-6), (idx, part)
+    for idx in [(0, 2, 1), (1, 3, 0)]:
+        op, om = obs.copy(), obs.copy()
+        op[idx] += h
+        om[idx] -= h
+        assert gobs[idx].real == pytest.approx((total(ens, op) - total(ens, om)) / (2 * h), abs=1e-6)
