@@ -20,7 +20,8 @@ E.1 and Sec. F.7):
   grid's quadrature, Eq. (spatial_loss);
 * ``crps_grad`` and ``spectral_crps_loss_grad``: the derivatives of the
   spread-skill form (for training with the loss);
-* ``angular_psd``: Eq. (psd).
+* ``angular_psd``: Eq. (psd);
+* ``zonal_psd``: Eq. (zonal_psd), the power at each latitude and order.
 
 Readings where the paper leaves the form open:
 
@@ -33,6 +34,9 @@ Readings where the paper leaves the form open:
   |m| <= l counts m = 0 once and every m > 0 twice.  The same holds for
   |u_l^{-m}|^2 in the angular power spectrum.
 * The degree range of Eq. (spectral_loss) is an argument [l_lo, l_hi).
+* Eq. (zonal_psd) multiplies by the circumference 2 pi sin(theta) (the text
+  says "normalized by" it): the formula is followed, for each m >= 0
+  without folding in m < 0.
 """
 from __future__ import annotations
 
@@ -177,6 +181,25 @@ def angular_psd(xhat):
     p = np.where(_triangle(L, M), np.abs(x) ** 2, 0.0)
     mult = np.where(np.arange(M) == 0, 1.0, 2.0)
     return np.sum(p * mult, axis=-1)
+
+
+def zonal_psd(u, grid: str, M: int):
+    """Eq. (zonal_psd) on a grid: zonalPSD[k][m] = 2 pi sin(theta_k)
+    |(2 pi / nlon) sum_j u_kj e^{-i m phi_j}|^2 for m < M, the longitude
+    integral taken with the grid's uniform longitude quadrature.  u: real
+    [..., nlat, nlon]; returns [..., nlat, M].  The longitude sums are the
+    oracle's direct DFT."""
+    import oracle
+    u = np.asarray(u, dtype=np.float64)
+    nlat, nlon = u.shape[-2:]
+    _, sin_t, _ = oracle.grid(nlat, grid)
+    flat = u.reshape(-1, nlat, nlon)
+    out = np.zeros((flat.shape[0], nlat, M))
+    for b in range(flat.shape[0]):
+        for k in range(nlat):
+            F = (2.0 * np.pi / nlon) * oracle.dft(flat[b, k], M)
+            out[b, k] = 2.0 * np.pi * sin_t[k] * np.abs(F) ** 2
+    return out.reshape(u.shape[:-2] + (nlat, M))
 
 
 def spatial_crps(ens, obs, w_lat, fair: bool = False):

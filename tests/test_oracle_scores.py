@@ -239,3 +239,30 @@ def test_spectral_crps_loss_gradient_against_finite_differences():
         op[idx] += h
         om[idx] -= h
         assert gobs[idx].real == pytest.approx((total(ens, op) - total(ens, om)) / (2 * h), abs=1e-6)
+
+
+@pytest.mark.parametrize("grid", ["gauss", "equiangular_cc"])
+def test_zonal_psd_of_a_zonal_wave_and_parseval(grid):
+    """u = a cos(m0 phi + c) on every ring: the longitude integral is pi a e^{i c}
+    at m0, so the zonal spectrum is 2 pi sin(theta) pi^2 a^2 there and 0 at
+    other m; and for any field the sum over the full spectrum (m and -m) is
+    2 pi sin(theta) (2 pi)^2 / nlon sum_j u^2 (Parseval of the DFT), checked
+    with numpy's FFT."""
+    nlat, nlon, M, m0 = 9, 16, 9, 3
+    x, s, _ = oracle.grid(nlat, grid)
+    phi = 2.0 * np.pi * np.arange(nlon) / nlon
+    a = 1.0 + 0.1 * np.arange(nlat)
+    u = a[:, None] * np.cos(m0 * phi[None, :] + 0.4)
+    z = scores.zonal_psd(u, grid, M)
+    want = np.zeros((nlat, M))
+    want[:, m0] = 2.0 * np.pi * s * np.pi ** 2 * a ** 2
+    np.testing.assert_allclose(z, want, rtol=1e-12, atol=1e-12)
+    g = _rng(70)
+    v = g.standard_normal((2, nlat, nlon))
+    zz = scores.zonal_psd(v, grid, nlon // 2 + 1)
+    full = zz[..., 0] + 2.0 * zz[..., 1:nlon // 2].sum(-1) + zz[..., nlon // 2]
+    rhs = 2.0 * np.pi * s * (2.0 * np.pi) ** 2 / nlon * np.sum(v ** 2, axis=-1)
+    np.testing.assert_allclose(full, rhs, rtol=1e-12)
+    X = np.fft.rfft(v, axis=-1)
+    np.testing.assert_allclose(zz, 2.0 * np.pi * s[:, None] * np.abs(2.0 * np.pi / nlon * X) ** 2, rtol=1e-11,
+                               atol=1e-14)
