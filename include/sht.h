@@ -378,6 +378,18 @@ sht_status_t sht_batch_destroy(sht_batch_t batch);
 sht_status_t sht_angular_psd(const void *xhat, float *psd, int64_t B, int lmax,
                              int mmax, void *stream);
 
+/* Zonal power spectrum, Eq. (zonal_psd), of B fields on the plan's grid:
+ *   zpsd[b][k][m] = 2 pi sin(theta_k) |(2 pi / nlon) sum_j x[b][k][j] e^{-i m phi_j}|^2
+ * for m < mmax (each m >= 0 once; the longitude integral by the grid's
+ * uniform longitude quadrature).  x: float32 [B][nlat][nlon], zpsd: float32
+ * [B][nlat][mmax].  Runs the plan's longitude FFT in FP32 whatever the
+ * plan's precision, with an FP32 buffer of the plan as scratch (the
+ * analysis workspace of FP32 plans, the spectral buffer of tensor-core
+ * plans); SHT_ERR_UNSUPPORTED when a tensor-core plan's buffer cannot hold
+ * one field (lmax < nlat / 2).  B = 0 is a no-op. */
+sht_status_t sht_zonal_psd(sht_plan_t plan, const float *x, float *zpsd,
+                           int64_t B, void *stream);
+
 /* Spectral CRPS, Eq. (spectral_loss): for every channel c and degree l
  *   crps_l[c][l] = sum_{|m| <= l} CRPS(u_l^m) = c_l0 + 2 sum_{m >= 1} c_lm,
  *   c_lm = CRPS(Re ens[.][c][l][m], Re obs[c][l][m])

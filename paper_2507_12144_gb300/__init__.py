@@ -22,7 +22,7 @@ from ._abi import ShtError
 
 __all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
-           "SpectralBlock", "spectral_block", "angular_psd", "spectral_crps", "spectral_crps_backward",
+           "SpectralBlock", "spectral_block", "angular_psd", "zonal_psd", "spectral_crps", "spectral_crps_backward",
            "spectral_crps_loss", "SpectralCRPSLoss", "sht_forward_ad", "SHTForward", "spatial_crps", "ShtError"]
 
 
@@ -462,6 +462,15 @@ def angular_psd(xhat: torch.Tensor) -> torch.Tensor:
     out = torch.empty(lead + (L,), dtype=torch.float32, device=x.device)
     with torch.cuda.device(x.device):
         _abi.check(_abi.lib().sht_angular_psd(_ptr(x), _ptr(out), B, L, M, _stream(x)))
+    return out
+
+
+def zonal_psd(plan: Plan, x: torch.Tensor) -> torch.Tensor:
+    """Eq. (zonal_psd) of float32 fields [..., nlat, nlon] on the plan's grid
+    -> float32 [..., nlat, mmax]."""
+    x, lead, B = _spatial_in(plan, x)
+    out = torch.empty(lead + (plan.nlat, plan.mmax), dtype=torch.float32, device=x.device)
+    _abi.check(_abi.lib().sht_zonal_psd(plan.handle, _ptr(x), _ptr(out), B, _stream(x)))
     return out
 
 

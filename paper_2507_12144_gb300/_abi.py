@@ -83,6 +83,7 @@ SIGNATURES = {
     "sht_pipe_destroy": ([_p], _i),
     "sht_angular_psd": ([_p, _p, _i64, _i, _i, _p], _i),
     "sht_spectral_crps": ([_p, _p, _p, _p, _p, _i, _i64, _i, _i, _i, _i, _i, _p], _i),
+    "sht_zonal_psd": ([_p, _p, _p, _i64, _p], _i),
     "sht_spectral_crps_backward": ([_p, _p, _p, _p, _p, _i, _i64, _i, _i, _i, _i, _i, _p], _i),
     "sht_spatial_crps": ([_p, _p, _p, _p, _p, _i, _i64, _i, _p], _i),
 }

@@ -190,6 +190,7 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_tab_off);
   cudaFree(p->d_twiddle);
   cudaFree(p->d_ring_w);
+  cudaFree(p->d_zonal_c);
   cudaFree(p->d_fwd_tiles);
   cudaFree(p->d_inv_tiles);
   cudaFree(p->d_work);
@@ -579,6 +580,12 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   std::vector<float> ringw(nlat);
   for (int k = 0; k < nlat; k++) ringw[k] = (float)(p->w[k] * 2.0 * kPi / (double)nlon);
   if ((e = upload(&p->d_ring_w, ringw)) != cudaSuccess) return bail(e, "weight upload");
+  std::vector<float> zonal(nlat);
+  for (int k = 0; k < nlat; k++) {
+    const double d = 2.0 * kPi / (double)nlon;
+    zonal[k] = (float)(2.0 * kPi * p->s[k] * d * d);
+  }
+  if ((e = upload(&p->d_zonal_c, zonal)) != cudaSuccess) return bail(e, "weight upload");
 
   // FP64 generation of the table on the device
   {

@@ -22,6 +22,7 @@
 // sum is taken over the differences to the observation, which it does not
 // change (the weights 2 i + 1 - E sum to zero), so that a common offset of
 // the members does not cancel in FP32.
+#include <algorithm>
 #include <cmath>
 
 #include "sht_internal.cuh"
@@ -264,6 +265,52 @@ __global__ void __launch_bounds__(256) angular_psd_kernel(const float2 *__restri
   if (lane == 0) psd[row] = acc;
 }
 
+// Zonal power spectrum, Eq. (zonal_psd), from the plan's longitude FFT of
+// ring pairs (no weights, FP32): E = X_k + X_kbar, O = X_k - X_kbar with
+// X_k(m) = sum_j u_kj e^{-i m phi_j} (the equator ring of odd nlat: E = X_k),
+//   zpsd[b][k][m] = zc[k] |X_k(m)|^2,  zc[k] = 2 pi sin(theta_k) (2 pi / nlon)^2.
+// A block takes 32 orders x 32 fields of one ring pair through shared memory,
+// so that it reads the folded rows along the fields and writes the output
+// rows along the orders.
+__global__ void __launch_bounds__(256) zonal_psd_kernel(const float *__restrict__ F, float *__restrict__ zpsd,
+                                                        const float *__restrict__ zc, int nlat, int M, int nb,
+                                                        FoldLayout fl) {
+  __shared__ float tn[32][33], ts[32][33];
+  const int kq = blockIdx.y, ks = nlat - 1 - kq;
+  const int m0 = blockIdx.x * 32, b0 = blockIdx.z * 32;
+  const bool eq = kq == ks;
+  const float cn = zc[kq], cs = zc[ks];
+  {
+    const int b = threadIdx.x & 31;
+    for (int mi = threadIdx.x >> 5; mi < 32; mi += 8) {
+      const int m = m0 + mi;
+      float vn = 0.f, vs = 0.f;
+      if (m < M && b0 + b < nb) {
+        const float2 E = *reinterpret_cast<const float2 *>(F + fold_row(fl, m, 0, kq) + 2 * (b0 + b));
+        if (eq) {
+          vn = cn * (E.x * E.x + E.y * E.y);
+        } else {
+          const float2 O = *reinterpret_cast<const float2 *>(F + fold_row(fl, m, 1, kq) + 2 * (b0 + b));
+          const float nr = 0.5f * (E.x + O.x), ni = 0.5f * (E.y + O.y);
+          const float sr = 0.5f * (E.x - O.x), si = 0.5f * (E.y - O.y);
+          vn = cn * (nr * nr + ni * ni);
+          vs = cs * (sr * sr + si * si);
+        }
+      }
+      tn[mi][b] = vn;
+      ts[mi][b] = vs;
+    }
+  }
+  __syncthreads();
+  const int mi = threadIdx.x & 31;
+  if (m0 + mi >= M) return;
+  for (int b = threadIdx.x >> 5; b < 32 && b0 + b < nb; b += 8) {
+    float *out = zpsd + (int64_t)(b0 + b) * nlat * M + m0 + mi;
+    out[(int64_t)kq * M] = tn[mi][b];
+    if (!eq) out[(int64_t)ks * M] = ts[mi][b];
+  }
+}
+
 int members_bucket(int E) {
   int np = 1;
   while (np < E) np <<= 1;
@@ -404,6 +451,56 @@ sht_status_t sht_spectral_crps_backward(const void *ens, const void *obs, const 
                                 (const float *)obs, gloss, (float *)gens, (float *)gobs, E, C, lmax, mmax, l_lo, l_hi,
                                 inv_e, inv_d);
   return e == cudaSuccess ? SHT_OK : cuda_fail(e, "spectral_crps_grad_kernel");
+}
+
+sht_status_t sht_zonal_psd(sht_plan_t plan, const float *x, float *zpsd, int64_t B, void *stream) {
+  NvtxRange nvtx_range("sht_zonal_psd");
+  if (!plan) return fail(SHT_ERR_INVALID_ARG, "plan is NULL");
+  if (B < 0) return fail(SHT_ERR_INVALID_ARG, "batch must be >= 0");
+  if (B == 0) return SHT_OK;
+  SCORE_TRY(check_dev_ptr(x, "x", false));
+  SCORE_TRY(check_dev_ptr(zpsd, "zpsd", false));
+  sht_plan_s *p = plan;
+  // The FP32 folded FFT of a chunk of fields needs M x 2 x Kh rows of ld
+  // floats (ld = 2 for one field, else 2 n rounded up to 4).  FP32 plans
+  // use their analysis workspace (FP32 in every call, sized for max_batch
+  // fields); tensor-core plans use their FP32 spectral buffer, never the
+  // bf16 workspace, and take as many fields per chunk as it holds.
+  const bool fp32 = p->precision == SHT_PREC_FP32;
+  const size_t scratch = fp32 ? sizeof(float) * (size_t)p->M * 2 * p->Kh * p->ldc
+                              : std::max(sizeof(float2) * (size_t)p->max_batch * p->L * p->M,
+                                         sizeof(float) * (size_t)p->L * p->M * p->ldr);
+  const size_t row_bytes = sizeof(float) * (size_t)p->M * 2 * p->Kh;
+  auto ld_of = [](int64_t n) { return n == 1 ? (int64_t)2 : (2 * n + 3) / 4 * 4; };
+  int64_t nb = std::min<int64_t>(p->max_batch, B);
+  while (nb > 1 && row_bytes * (size_t)ld_of(nb) > scratch) nb--;
+  if (row_bytes * (size_t)ld_of(nb) > scratch)
+    return fail(SHT_ERR_UNSUPPORTED, "the plan's FP32 buffer is too small for one field's longitude FFT (lmax < nlat / 2 "
+                                     "on a tensor-core plan); use an FP32 plan");
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != p->device && cudaSetDevice(p->device) != cudaSuccess)
+    return fail(SHT_ERR_CUDA, "cannot select the plan's device");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  float *F = fp32 ? p->d_work : reinterpret_cast<float *>(p->d_spec_b);
+  const int64_t npix = (int64_t)p->nlat * p->nlon;
+  for (int64_t b0 = 0; b0 < B && e == cudaSuccess; b0 += nb) {
+    const int n = (int)std::min<int64_t>(nb, B - b0);
+    const FoldLayout fl = classic_layout(p->Kh, (int)ld_of(n));
+    if (fft45_supported(p->nlon))
+      e = launch_r2c45(x + b0 * npix, F, nullptr, nullptr, p->nlat, p->nlon, p->M, n, fl, p->d_twiddle, nullptr, 0,
+                       st);
+    else
+      e = launch_r2c(x + b0 * npix, F, p->nlat, p->nlon, p->M, n, fl, p->d_twiddle, p->radix, nullptr, 0, st);
+    if (e != cudaSuccess) break;
+    const dim3 grid((unsigned)((p->M + 31) / 32), (unsigned)p->Kh, (unsigned)((n + 31) / 32));
+    zonal_psd_kernel<<<grid, 256, 0, st>>>(F, zpsd + b0 * p->nlat * (int64_t)p->M, p->d_zonal_c, p->nlat, p->M, n,
+                                           fl);
+    e = cudaGetLastError();
+  }
+  if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
+  return e == cudaSuccess ? SHT_OK : cuda_fail(e, "zonal power spectrum");
 }
 
 sht_status_t sht_spatial_crps(sht_plan_t plan, const float *ens, const float *obs, float *crps_k, float *loss, int E,

@@ -379,6 +379,7 @@ struct sht_plan_s {
   int64_t *d_tab_off = nullptr;
   float2 *d_twiddle = nullptr;
   float *d_ring_w = nullptr;  // w_k * 2 pi / nlon
+  float *d_zonal_c = nullptr; // 2 pi sin(theta_k) (2 pi / nlon)^2 (zonal power spectrum)
   shtgb::LegTile *d_fwd_tiles = nullptr;
   int n_fwd_tiles = 0;
   shtgb::LegTile *d_inv_tiles = nullptr;

@@ -168,3 +168,9 @@ def test_scores_reject_bad_arguments_before_any_cuda_call(lib):
     # spatial CRPS needs a plan
     assert lib.sht_spatial_crps(None, p16, p16, p16, None, 4, 1, 0, None) == 1
     assert b"plan" in lib.sht_last_error_message()
+    assert lib.sht_zonal_psd(None, p16, p16, 1, None) == 1
+    assert b"plan" in lib.sht_last_error_message()
+    assert lib.sht_spectral_crps_backward(p16, p16, p16, p16, None, 1, 1, 4, 4, 1, 0, 4, None) == 1
+    assert b"fair" in lib.sht_last_error_message()
+    assert lib.sht_spectral_crps_backward(p16, p16, None, p16, None, 4, 1, 4, 4, 0, 0, 4, None) == 1
+    assert b"gloss" in lib.sht_last_error_message()

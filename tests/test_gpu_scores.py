@@ -251,3 +251,33 @@ def test_spectral_crps_loss_autograd_through_the_forward_transform():
         ey = np.linalg.norm(y.grad.cpu().numpy() - gy) / np.linalg.norm(gy)
         assert ex < 1e-5 and ey < 1e-5, (fair, ex, ey)
     plan.close()
+
+
+@pytest.mark.parametrize("nlat,nlon,grid,M,B,prec,mb", [
+    (17, 32, "gauss", 16, 3, "fp32", 8),             # generic longitude FFT
+    (33, 64, "equiangular_cc", 32, 5, "fp32", 2),    # chunks of 2 fields, ragged
+    (91, 180, "equiangular_cc", 90, 37, "fp32", 40), # four-step FFT (nlon = 45 x 4), >32 fields (two field tiles)
+    (91, 180, "equiangular_trapz", 60, 4, "split_bf16", 4),  # tensor-core plan: its FP32 spectral buffer as scratch
+    (20, 40, "gauss", 12, 2, "fp32", 4),             # even nlat (no equator ring)
+])
+def test_zonal_psd_matches_oracle(nlat, nlon, grid, M, B, prec, mb):
+    sht = _sht()
+    L = nlat if grid == "gauss" else nlat - 1
+    plan = sht.Plan(nlat, nlon, grid, L, M, precision=prec, max_batch=mb, max_channels=mb)
+    u = inputs.rng(800 + nlat).standard_normal((B, nlat, nlon)).astype(np.float32)
+    got = sht.zonal_psd(plan, torch.from_numpy(u).cuda()).cpu().numpy()
+    want = scores.zonal_psd(u.astype(np.float64), grid, M)
+    # relative error 1e-5 with an absolute floor of 1e-6 of the field's largest
+    # value: at the poles sin(theta) is 0 (the plan) or a rounding residue of
+    # 1e-16 (the oracle's sin(pi)), and the FP32 FFT of nlon points errs by
+    # about 1e-7 of the ring's norm in every order
+    floor = 1e-6 * np.max(want, axis=(-2, -1), keepdims=True)
+    err = np.abs(got - want)
+    assert np.all(err <= 1e-5 * np.abs(want) + floor), float(np.max(err / (np.abs(want) + floor)))
+    # the plan still transforms correctly after using its buffer as scratch
+    x = torch.from_numpy(u).cuda()
+    xh = sht.sht_forward(plan, x).cpu().numpy()
+    ref = oracle.sht_forward(u.astype(np.float64), nlat, nlon, grid, L, M)
+    err = np.linalg.norm(xh - ref) / np.linalg.norm(ref)
+    assert err < (1e-5 if prec == "fp32" else 2e-5)
+    plan.close()
