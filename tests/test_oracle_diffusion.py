@@ -1,0 +1,64 @@
+"""Pins of the diffusion-process oracle (oracle/diffusion.py) against what
+Eq. (spherical_diffusion) fixes: the process variance is sigma^2 ("the
+variance of the process is determined by sigma", Sec. B.7) and the same at
+every latitude, the lag-one correlation is phi = exp(-lambda), and the
+spatial length scale shrinks with kT.  Checked by Monte Carlo through the
+oracle's inverse SHT on a Gauss grid, not by restating the formulas."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import diffusion
+
+
+def _eta(g, shape):
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+@pytest.mark.parametrize("kT", [0.0, 4.93e-4 * 200, 7.89e-3 * 20])
+def test_stationary_variance_is_sigma_squared_at_every_latitude(kT):
+    nlat, nlon, L = 24, 48, 24
+    lam, sig = 0.5, 1.7
+    g = np.random.Generator(np.random.PCG64(5))
+    n = 400
+    # a draw from the stationary distribution: z = sigma_l xi / sqrt(1 - phi^2)
+    phi = np.exp(-lam)
+    z0 = np.zeros((n, L, L), dtype=np.complex128)
+    z = diffusion.diffusion_step(z0, _eta(g, (n, L, L)), np.full(n, kT), lam, sig) / np.sqrt(1.0 - phi * phi)
+    u = oracle.sht_inverse(z, nlat, nlon, "gauss", L, L)
+    var_lat = np.mean(u ** 2, axis=(0, 2))  # per latitude row
+    # 400 fields x 48 longitudes, correlated along the ring: a loose but decisive bound
+    assert np.all(np.abs(var_lat / sig ** 2 - 1.0) < 0.15), var_lat / sig ** 2
+    assert abs(np.mean(var_lat) / sig ** 2 - 1.0) < 0.06
+    # a reading without the sqrt(2) at m = 0 would put less variance at the
+    # poles (only m = 0 reaches them) than at the equator
+    x, _, _ = oracle.grid(nlat, "gauss")
+    pole = var_lat[np.abs(x) > 0.9].mean()
+    eq = var_lat[np.abs(x) < 0.3].mean()
+    assert abs(pole / eq - 1.0) < 0.15
+
+
+def test_lag_one_correlation_is_phi():
+    L, n = 16, 3000
+    lam, sig, kT = 0.7, 1.0, 0.01
+    g = np.random.Generator(np.random.PCG64(6))
+    phi = np.exp(-lam)
+    z = diffusion.diffusion_step(np.zeros((n, L, L), complex), _eta(g, (n, L, L)), np.full(n, kT), lam, sig)
+    z = z / np.sqrt(1.0 - phi * phi)
+    z1 = diffusion.diffusion_step(z, _eta(g, (n, L, L)), np.full(n, kT), lam, sig)
+    a, b = z[:, 1:].ravel(), z1[:, 1:].ravel()
+    mask = np.abs(a) > 0
+    c = np.real(np.vdot(a[mask], b[mask])) / np.real(np.vdot(a[mask], a[mask]))
+    assert abs(c - phi) < 0.01
+
+
+def test_length_scale_and_no_mean():
+    """l = 0 carries no noise; a larger kT moves the power to low degrees."""
+    L = 40
+    s_small = diffusion.sigma_l(1e-4, 1.0, 1.0, L)
+    s_large = diffusion.sigma_l(1e-2, 1.0, 1.0, L)
+    assert s_large[1] > s_small[1] and s_large[-1] < s_small[-1]
+    g = np.random.Generator(np.random.PCG64(7))
+    z = diffusion.diffusion_step(np.ones((2, L, L), complex), _eta(g, (2, L, L)), np.array([1e-3, 1e-2]), 1.0, 1.0)
+    assert np.all(z[:, 0, :] == 0) and np.all(z[:, np.arange(L)[:, None] < np.arange(L)[None, :]] == 0)
+    assert np.all(z[:, :, 0].imag == 0)
