@@ -14,6 +14,8 @@ the dominant kernel.
   python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
   python bench.py --workload batched ... # forward + inverse SHT of an uneven
                                          # mix of four grids, one CUDA graph each
+  python bench.py --workload noise ...   # spherical diffusion noise: 16 members
+                                         # x 8 length scales at 721x1440
   python bench.py --workload scores ...  # angular power spectrum + spectral
                                          # CRPS of a 16-member x 72-channel
                                          # ensemble of 720 x 720 coefficients
@@ -59,6 +61,27 @@ SCORE_LO = 1  # Eq. (spectral_loss) sums the degrees from 1
 SCORE_METRIC = ("ensemble-scored member fields/s: angular PSD + spectral CRPS, 16 members x 72 channels, "
                 "lmax=mmax=720; roofline fraction")
 SCORE_UNIT = "member fields/s"
+
+
+# noise workload: the paper's 8 noise channels (kT values of its table of
+# input variables, lambda = 1, sigma = 1) for a 16-member ensemble
+NOISE_KT = [3.08e-5, 1.23e-4, 4.93e-4, 1.97e-3, 7.89e-3, 3.16e-2, 1.26e-1, 5.05e-1]
+NOISE_E = 16
+NOISE_METRIC = ("spherical diffusion noise fields/s at 721x1440, lmax=720 (16 members x 8 length scales, "
+                "step + inverse SHT); roofline fraction")
+NOISE_UNIT = "noise fields/s"
+
+
+def noise_config(precision: str) -> dict:
+    return {
+        "workload": "spherical diffusion process (Eq. spherical_diffusion): one AR(1) step of 16 members x 8 noise "
+                    "channels (kT of the paper's table, lambda=1, sigma=1) with on-GPU Philox normals, then the "
+                    "inverse SHT to 721x1440 equiangular (Clenshaw-Curtis), lmax=mmax=720",
+        "members": NOISE_E, "channels": len(NOISE_KT), "nlat": NLAT, "nlon": NLON, "lmax": LMAX, "mmax": MMAX,
+        "precision": precision,
+        "l2": "inputs larger than L2: 531 MB of coefficients read and written, 531 MB of fields written per step",
+        "parallelism": "replicas",
+    }
 
 
 def scores_config() -> dict:
@@ -131,6 +154,7 @@ def kernel_sources(kernel: str, precision: str):
         "filter": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/filter.cu"],
         "filter_prep": ["paper_2507_12144_gb300/csrc/legendre_tc.cu"],
         "crps": ["paper_2507_12144_gb300/csrc/scores.cu"],
+        "diffusion": ["paper_2507_12144_gb300/csrc/diffusion.cu"],
         "psd": ["paper_2507_12144_gb300/csrc/scores.cu"],
     }
     return table.get(kernel, [])
@@ -425,6 +449,8 @@ def run_reference(args):
         return run_reference_batched(args, world)
     if args.workload == "scores":
         return run_reference_scores(args, world)
+    if args.workload == "noise":
+        return run_reference_noise(args, world)
     s = OracleSampler()
     budget = args.ref_seconds / max(1, args.steps + args.warmup)
     rows = s.calibrate(min(budget, 20.0))
@@ -922,13 +948,159 @@ def run_gpu_scores(args):
     return 0
 
 
+def run_gpu_noise(args):
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+
+    import paper_2507_12144_gb300 as shtgb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    C, E = len(NOISE_KT), NOISE_E
+    B = E * C
+    plan = shtgb.Plan(NLAT, NLON, GRID, LMAX, MMAX, precision=args.precision, device=dev, max_batch=B,
+                      table_source=args.table_source)
+    proc = shtgb.SphericalDiffusion(plan, NOISE_KT, members=E, lam=1.0, sigma=1.0, seed=1234 + rank)
+    out = torch.empty((E, C, NLAT, NLON), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        shtgb.diffusion_step(proc.z, NOISE_KT, 1.0, 1.0, proc.seed, proc.step)
+        proc.step += 1
+        return shtgb.sht_inverse(plan, proc.z)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # per-kernel durations: the plan's profiler for the inverse SHT's
+    # kernels, events around the diffusion step
+    nk = max(3, min(args.steps, 50))
+    plan.profile_begin(capacity=8 * (nk + 1))
+    plan.profile_collect()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_diff = 0.0
+    for _ in range(nk):
+        e0.record(stream)
+        shtgb.diffusion_step(proc.z, NOISE_KT, 1.0, 1.0, proc.seed, proc.step)
+        e1.record(stream)
+        proc.step += 1
+        shtgb.sht_inverse(plan, proc.z)
+        e1.synchronize()
+        t_diff += e0.elapsed_time(e1)
+    prof = plan.profile_collect()
+    plan.profile_end()
+    clocks = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    value = world * B / (ms_step * 1e-3)
+    tri = n_triangle(LMAX, MMAX) * 8.0
+    kernels = {k: v[1] / max(v[0], 1) for k, v in prof.items() if not k.startswith("_") and v[0] > 0}
+    kernels["diffusion"] = t_diff / nk
+    alg = {"diffusion": B * 2 * tri, "c2r": algorithmic_bytes("c2r", B, 1, 1, 1),
+           "leg_inv": algorithmic_bytes("leg_inv", B, 1, 1, 1)}
+    dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k])
+    per_launch_s = kernels[dom] * 1e-3
+    peak, peak_kind = load_peaks()
+    achieved = alg[dom] / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "traffic": measured_traffic(dom, "noise"),
+                "algorithmic_bytes_per_launch": alg[dom], "kernel_ms_per_launch": kernels[dom]}
+    # end to end: the noise fields read back to pinned host memory every step
+    # (the state stays on the GPU: the process runs there)
+    e2e_steps = 10
+    host = torch.empty((E, C, NLAT, NLON), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host.copy_(step(), non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    if rank == 0:
+        line = {
+            "metric": NOISE_METRIC, "value": value, "unit": NOISE_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+            "data": "synthetic: the process's own normals (Philox4x32-10 on the GPU)",
+            "config": noise_config(args.precision), "roofline": roofline,
+            "kernels": {k: {"ms_per_launch": v} for k, v in kernels.items()},
+            "gpu_launches": None,
+            "e2e": {"value": world * B * e2e_steps / e2e_s, "unit": NOISE_UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(B * NLAT * NLON * 4), "steps": e2e_steps},
+            "clocks": clk,
+            "cpu_baseline": cpu_baseline_noise() if world == 1 and not args.no_cpu_baseline else None,
+        }
+        line["gpu_launches"] = args.steps * (1 + sum(v[0] for k, v in prof.items() if not k.startswith("_")) // nk)
+        print(json.dumps(line))
+        sys.stdout.flush()
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference_noise(args, world):
+    runs = [cpu_baseline_noise() for _ in range(args.warmup + args.steps)][args.warmup:]
+    value = statistics.median(r["value"] for r in runs)
+    line = {
+        "impl": "reference", "metric": NOISE_METRIC, "value": value, "unit": NOISE_UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 2 * 240 / NLAT / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": noise_config("fp64 oracle"),
+        "cpu_baseline": {"value": value, "unit": NOISE_UNIT, "cores": runs[0]["cores"], "kind": "oracle",
+                         "sample": runs[0]["sample"]},
+        "e2e": {"value": value, "unit": NOISE_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    barrier(world)
+    return 0
+
+
+def cpu_baseline_noise() -> dict:
+    """The FP64 oracles on a slab: one step of the process for 2 fields
+    and their inverse SHT on latitude rows [0, R)."""
+    import oracle
+    from oracle import diffusion
+    from paper_2507_12144_gb300 import inputs
+    oracle.build()
+    g = inputs.rng(3)
+    n = 2
+    z = np.zeros((n, LMAX, MMAX), dtype=np.complex128)
+    eta = g.standard_normal((n, LMAX, MMAX)) + 1j * g.standard_normal((n, LMAX, MMAX))
+    rows = 240
+    t0 = time.perf_counter()
+    z = diffusion.diffusion_step(z, eta, np.array(NOISE_KT[:n]), 1.0, 1.0)
+    oracle.sht_inverse_rows(z, NLAT, NLON, GRID, LMAX, MMAX, 0, rows)
+    dt = time.perf_counter() - t0
+    return {"value": n * rows / NLAT / dt, "unit": NOISE_UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} fields: one process step (numpy FP64) and the C oracle's inverse SHT on latitude rows "
+                      f"[0,{rows}) of 721; counts {rows}/721 of a noise field per field; {dt:.1f} s"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["block", "batched", "scores"], default="block",
+    ap.add_argument("--workload", choices=["block", "batched", "scores", "noise"], default="block",
                     help="block: SHT -> filter -> ISHT at 721x1440 (the headline); batched: forward + inverse "
                          "SHT of the uneven four-grid mix; scores: angular PSD + spectral CRPS of a "
                          "16-member ensemble")
@@ -952,6 +1124,8 @@ def main(argv=None):
         return run_gpu_batched(args)
     if args.workload == "scores":
         return run_gpu_scores(args)
+    if args.workload == "noise":
+        return run_gpu_noise(args)
     return run_gpu(args)
 
 

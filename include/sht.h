@@ -439,6 +439,33 @@ sht_status_t sht_spatial_crps(sht_plan_t plan, const float *ens, const float *ob
                               float *crps_k, float *loss, int E, int64_t C,
                               int fair, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Spherical diffusion process (Sec. B.7)
+ * ------------------------------------------------------------------------ */
+
+/* One step of Eq. (spherical_diffusion) for B noise fields, in place on
+ * their coefficients:
+ *   zhat[b][l][m] = phi zhat[b][l][m] + sigma_l xi[b][l][m],
+ *   phi = exp(-lambda), sigma_l = F0 exp(-(kT / 2) l (l + 1)),
+ *   F0 = sigma sqrt(2 pi (1 - phi^2) / sum_{l=1}^{lmax-1} (2l+1) exp(-kT l (l+1))),
+ * for 1 <= l < lmax and m <= l; the l = 0 entry is set to 0 (no l = 0
+ * term) and entries with m > l are neither read nor written (the inverse
+ * transform ignores them).  xi = eta for m > 0 (real and imaginary part standard normal) and
+ * sqrt(2) Re(eta) at m = 0, so that the real field (sht_inverse of zhat)
+ * has the stationary variance sigma^2 at every point.
+ *   zhat: complex64 [B][lmax][mmax] device, updated in place;
+ *   eta:  complex64 [B][lmax][mmax] device standard normals, or NULL: drawn
+ *         on the GPU from Philox4x32-10 with key = seed and counter =
+ *         (flat coefficient index b lmax mmax + l mmax + m, step), then the
+ *         Box-Muller transform of its first two words, u1 = ((w0 >> 8) + 1)
+ *         2^-24, u2 = (w1 >> 8) 2^-24, eta = sqrt(-2 ln u1) e^{2 pi i u2};
+ *   kT:   HOST array of nk (1 .. 16) length scales; field b uses kT[b % nk].
+ * lambda > 0, sigma >= 0, lmax >= 2, 1 <= mmax <= lmax; B = 0 is a no-op. */
+sht_status_t sht_diffusion_step(void *zhat, const void *eta, int64_t B, int lmax,
+                                int mmax, const double *kT, int nk,
+                                double lambda, double sigma, uint64_t seed,
+                                uint64_t step, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Per-kernel timing.  While profiling is on, every kernel a plan's execute
  * calls launch is bracketed by two CUDA events recorded on the launch

@@ -54,3 +54,42 @@ def diffusion_step(z, eta, kT, lam: float, sigma: float):
         s = sigma_l(float(kT[b]), lam, sigma, L)[:, None]
         out[b] = np.where(live, phi * z[b] + s * xi[b], 0.0)
     return out
+
+
+# ----------------------------------------------------------------------------
+# The counter-based generator, from its published definition: Philox4x32
+# with 10 rounds (Salmon, Moraes, Dror and Shaw, SC 2011), and the
+# Box-Muller transform of its first two words, in FP64.
+# ----------------------------------------------------------------------------
+
+_M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+_W0, _W1 = np.uint64(0x9E3779B9), np.uint64(0xBB67AE85)
+_MASK = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Vectorised Philox4x32-10 of counters (c0, c1, c2, c3) under the key
+    (k0, k1), all uint32 values held in uint64 arrays; returns 4 words."""
+    c = [np.asarray(v, dtype=np.uint64) & _MASK for v in (c0, c1, c2, c3)]
+    k = [np.asarray(v, dtype=np.uint64) & _MASK for v in (k0, k1)]
+    for _ in range(10):
+        p0 = _M0 * c[0]
+        p1 = _M1 * c[2]
+        c = [((p1 >> np.uint64(32)) ^ c[1] ^ k[0]) & _MASK, p1 & _MASK,
+             ((p0 >> np.uint64(32)) ^ c[3] ^ k[1]) & _MASK, p0 & _MASK]
+        k = [(k[0] + _W0) & _MASK, (k[1] + _W1) & _MASK]
+    return c
+
+
+def philox_normals(seed: int, step: int, idx):
+    """Standard complex normals of flat coefficient indices ``idx`` (the
+    generator's counter is (idx, step), its key the seed):
+    u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8) 2^-24,
+    eta = sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    w = philox4x32_10(idx & _MASK, idx >> np.uint64(32), np.uint64(step) & _MASK, np.uint64(step) >> np.uint64(32),
+                      np.uint64(seed) & _MASK, np.uint64(seed) >> np.uint64(32))
+    u1 = ((w[0] >> np.uint64(8)) + np.uint64(1)).astype(np.float64) * 2.0 ** -24
+    u2 = (w[1] >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(2.0 * np.pi * u2) + 1j * r * np.sin(2.0 * np.pi * u2)

@@ -22,7 +22,8 @@ from ._abi import ShtError
 
 __all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
-           "SpectralBlock", "spectral_block", "angular_psd", "zonal_psd", "spectral_crps", "spectral_crps_backward",
+           "SpectralBlock", "spectral_block", "diffusion_step", "SphericalDiffusion", "angular_psd", "zonal_psd",
+           "spectral_crps", "spectral_crps_backward",
            "spectral_crps_loss", "SpectralCRPSLoss", "sht_forward_ad", "SHTForward", "spatial_crps", "ShtError"]
 
 
@@ -577,3 +578,52 @@ def spatial_crps(plan: Plan, ens: torch.Tensor, obs: torch.Tensor, fair: bool = 
     _abi.check(_abi.lib().sht_spatial_crps(plan.handle, _ptr(ens), _ptr(obs), _ptr(crps_k), _ptr(loss), E, C,
                                            int(bool(fair)), _stream(ens)))
     return crps_k, loss
+
+
+# ---------------------------------------------------------------------------
+# spherical diffusion process (Sec. B.7)
+# ---------------------------------------------------------------------------
+
+def diffusion_step(zhat: torch.Tensor, kT, lam: float = 1.0, sigma: float = 1.0, seed: int = 0, step: int = 0,
+                   eta: torch.Tensor | None = None) -> torch.Tensor:
+    """One step of Eq. (spherical_diffusion), in place on complex64 state
+    [..., lmax, mmax]; field b (flattened leading index) uses kT[b % len(kT)].
+    ``eta`` (standard normals, same shape) or None: drawn on the GPU."""
+    z = zhat
+    if not isinstance(z, torch.Tensor) or z.dtype != torch.complex64 or z.device.type != "cuda":
+        raise TypeError("zhat must be a complex64 CUDA tensor")
+    if not z.is_contiguous():
+        raise ValueError("zhat must be contiguous (it is updated in place)")
+    L, M = int(z.shape[-2]), int(z.shape[-1])
+    B = z.numel() // (L * M)
+    if eta is not None:
+        eta = _need(eta, torch.complex64, "eta", z.device)
+        if eta.shape != z.shape:
+            raise ValueError("eta must have the shape of zhat")
+    ks = [float(k) for k in (kT if hasattr(kT, "__len__") else [kT])]
+    arr = (ctypes.c_double * len(ks))(*ks)
+    with torch.cuda.device(z.device):
+        _abi.check(_abi.lib().sht_diffusion_step(_ptr(z), _ptr(eta), B, L, M, arr, len(ks), float(lam), float(sigma),
+                                                 int(seed) & (2 ** 64 - 1), int(step) & (2 ** 64 - 1), _stream(z)))
+    return z
+
+
+class SphericalDiffusion:
+    """Noise fields of Eq. (spherical_diffusion) on a plan's grid: ``fields``
+    channels x ``members``, channel c with length scale kT[c]; each call of
+    :meth:`next` advances the state one step (on the GPU generator) and
+    returns the fields [members, channels, nlat, nlon] through the plan's
+    inverse SHT."""
+
+    def __init__(self, plan: Plan, kT, members: int = 1, lam: float = 1.0, sigma: float = 1.0, seed: int = 0):
+        self.plan = plan
+        self.kT = [float(k) for k in kT]
+        self.lam, self.sigma, self.seed = float(lam), float(sigma), int(seed)
+        self.step = 0
+        self.z = torch.zeros((int(members), len(self.kT), plan.lmax, plan.mmax), dtype=torch.complex64,
+                             device=plan.device)
+
+    def next(self) -> torch.Tensor:
+        diffusion_step(self.z, self.kT, self.lam, self.sigma, self.seed, self.step)
+        self.step += 1
+        return sht_inverse(self.plan, self.z)

@@ -84,6 +84,8 @@ SIGNATURES = {
     "sht_angular_psd": ([_p, _p, _i64, _i, _i, _p], _i),
     "sht_spectral_crps": ([_p, _p, _p, _p, _p, _i, _i64, _i, _i, _i, _i, _i, _p], _i),
     "sht_zonal_psd": ([_p, _p, _p, _i64, _p], _i),
+    "sht_diffusion_step": ([_p, _p, _i64, _i, _i, _d, _i, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                            ctypes.c_uint64, _p], _i),
     "sht_spectral_crps_backward": ([_p, _p, _p, _p, _p, _i, _i64, _i, _i, _i, _i, _i, _p], _i),
     "sht_spatial_crps": ([_p, _p, _p, _p, _p, _i, _i64, _i, _p], _i),
 }

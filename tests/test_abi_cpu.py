@@ -174,3 +174,22 @@ def test_scores_reject_bad_arguments_before_any_cuda_call(lib):
     assert b"fair" in lib.sht_last_error_message()
     assert lib.sht_spectral_crps_backward(p16, p16, None, p16, None, 4, 1, 4, 4, 0, 0, 4, None) == 1
     assert b"gloss" in lib.sht_last_error_message()
+
+
+def test_diffusion_step_rejects_bad_arguments_before_any_cuda_call(lib):
+    p16, p8 = ctypes.c_void_p(64), ctypes.c_void_p(72)
+    kT = (ctypes.c_double * 2)(1e-3, 2e-3)
+    f = lib.sht_diffusion_step
+    assert f(p16, None, -1, 8, 8, kT, 2, 1.0, 1.0, 0, 0, None) == 1
+    assert f(p16, None, 1, 1, 1, kT, 2, 1.0, 1.0, 0, 0, None) == 1          # lmax < 2
+    assert f(p16, None, 1, 8, 9, kT, 2, 1.0, 1.0, 0, 0, None) == 1          # mmax > lmax
+    assert f(p16, None, 1, 8, 8, None, 2, 1.0, 1.0, 0, 0, None) == 1
+    assert f(p16, None, 1, 8, 8, kT, 17, 1.0, 1.0, 0, 0, None) == 1
+    assert b"length scales" in lib.sht_last_error_message()
+    assert f(p16, None, 1, 8, 8, kT, 2, 0.0, 1.0, 0, 0, None) == 1          # lambda = 0
+    neg = (ctypes.c_double * 1)(-1.0)
+    assert f(p16, None, 1, 8, 8, neg, 1, 1.0, 1.0, 0, 0, None) == 1
+    assert f(None, None, 1, 8, 8, kT, 2, 1.0, 1.0, 0, 0, None) == 1
+    assert f(p8, None, 1, 8, 8, kT, 2, 1.0, 1.0, 0, 0, None) == 1
+    assert b"aligned" in lib.sht_last_error_message()
+    assert f(None, None, 0, 8, 8, kT, 2, 1.0, 1.0, 0, 0, None) == 0       # B = 0: no-op

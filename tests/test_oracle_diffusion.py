@@ -62,3 +62,24 @@ def test_length_scale_and_no_mean():
     z = diffusion.diffusion_step(np.ones((2, L, L), complex), _eta(g, (2, L, L)), np.array([1e-3, 1e-2]), 1.0, 1.0)
     assert np.all(z[:, 0, :] == 0) and np.all(z[:, np.arange(L)[:, None] < np.arange(L)[None, :]] == 0)
     assert np.all(z[:, :, 0].imag == 0)
+
+
+def test_philox_normals_are_standard_normal():
+    """The generator's normals: mean 0, variance 1 per part, uncorrelated
+    parts and steps, and a Kolmogorov-Smirnov distance to N(0, 1) within
+    its 0.1 % critical value."""
+    from math import erf, sqrt
+    n = 200_000
+    e0 = diffusion.philox_normals(12345, 0, np.arange(n))
+    e1 = diffusion.philox_normals(12345, 1, np.arange(n))
+    for v in (e0.real, e0.imag, e1.real):
+        assert abs(v.mean()) < 4.5 / sqrt(n)
+        assert abs(v.var() - 1.0) < 4.5 * sqrt(2.0 / n)
+        x = np.sort(v)
+        cdf = 0.5 * (1.0 + np.vectorize(erf)(x / sqrt(2.0)))
+        d = np.max(np.maximum(np.arange(1, n + 1) / n - cdf, cdf - np.arange(n) / n))
+        assert d < 1.95 / sqrt(n)
+    assert abs(np.mean(e0.real * e0.imag)) < 4.5 / sqrt(n)
+    assert abs(np.mean(e0.real * e1.real)) < 4.5 / sqrt(n)
+    # another seed gives other numbers
+    assert not np.allclose(diffusion.philox_normals(1, 0, np.arange(8)), e0[:8])
