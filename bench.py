@@ -84,6 +84,27 @@ def noise_config(precision: str) -> dict:
     }
 
 
+# DISCO workload: the contraction of the model's internal 360 x 720
+# Gaussian grid with the Morlet-type basis (basis_n = 3, K = 17) on a cap of
+# 4 grid spacings, 64 channels, forward and backward
+DISCO_GRID = (360, 720, "gauss")
+DISCO_N, DISCO_CUTOFF, DISCO_C = 3, 4 * math.pi / 360, 64
+DISCO_METRIC = ("DISCO contraction fields/s (forward + backward) on the 360x720 Gaussian grid, 17 basis functions, "
+                "cap of 4 grid spacings; roofline fraction")
+DISCO_UNIT = "fields/s"
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+
+
+def disco_config() -> dict:
+    return {
+        "workload": "DISCO contraction (Eq. disco_convolution_formula), forward and its transpose, 360x720 Gaussian "
+                    "grid in and out, Morlet-type basis basis_n=3 (K=17), theta_cutoff = 4 pi / 360, 64 channels",
+        "nlat": 360, "nlon": 720, "grid": "gauss", "basis": 17, "theta_cutoff": DISCO_CUTOFF, "channels": DISCO_C,
+        "l2": "outputs larger than L2: 1.13 GB of basis outputs written and read per step",
+        "parallelism": "replicas",
+    }
+
+
 def scores_config() -> dict:
     return {
         "workload": "angular PSD (Eq. psd) of every member + spectral CRPS (Eq. spectral_loss, biased form, "
@@ -451,6 +472,19 @@ def run_reference(args):
         return run_reference_scores(args, world)
     if args.workload == "noise":
         return run_reference_noise(args, world)
+    if args.workload == "disco":
+        runs = [cpu_baseline_disco() for _ in range(args.warmup + args.steps)][args.warmup:]
+        value = statistics.median(r["value"] for r in runs)
+        print(json.dumps({
+            "impl": "reference", "metric": DISCO_METRIC, "value": value, "unit": DISCO_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": disco_config(),
+            "cpu_baseline": {"value": value, "unit": DISCO_UNIT, "cores": 1, "kind": "oracle",
+                             "sample": runs[0]["sample"]},
+            "e2e": {"value": value, "unit": DISCO_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        sys.stdout.flush()
+        barrier(world)
+        return 0
     s = OracleSampler()
     budget = args.ref_seconds / max(1, args.steps + args.warmup)
     rows = s.calibrate(min(budget, 20.0))
@@ -1094,13 +1128,126 @@ def cpu_baseline_noise() -> dict:
                       f"[0,{rows}) of 721; counts {rows}/721 of a noise field per field; {dt:.1f} s"}
 
 
+def run_gpu_disco(args):
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+
+    import paper_2507_12144_gb300 as shtgb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H, W, grid = DISCO_GRID
+    d = shtgb.Disco(H, W, grid, H, W, grid, basis_n=DISCO_N, theta_cutoff=DISCO_CUTOFF, device=dev)
+    g = torch.Generator(device=dev).manual_seed(77 + rank)
+    x = torch.randn((DISCO_C, H, W), generator=g, device=dev)
+    gy = torch.randn((DISCO_C, d.nbasis, H, W), generator=g, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(args.warmup):
+        d.forward(x)
+        d.backward(gy)
+    torch.cuda.synchronize()
+    nk = max(3, min(args.steps, 20))
+    tf = tb = 0.0
+    for _ in range(nk):
+        ev[0].record(stream)
+        d.forward(x)
+        ev[1].record(stream)
+        d.backward(gy)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        tf += ev[0].elapsed_time(ev[1])
+        tb += ev[1].elapsed_time(ev[2])
+    clocks = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d.forward(x)
+        d.backward(gy)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    ms_step = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+    value = world * DISCO_C / (ms_step * 1e-3)
+    flops = 2.0 * d.nbasis * DISCO_C * d.nnz * W  # every entry: K FMAs per channel and output longitude
+    kern = {"disco_fwd": tf / nk, "disco_bwd": tb / nk}
+    dom = max(kern, key=kern.get)
+    achieved = flops / (kern[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
+                "peak_source": "FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops x 2070 MHz)",
+                "traffic": None, "algorithmic_flops_per_launch": flops, "kernel_ms_per_launch": kern[dom]}
+    # end to end: fields in from pinned host memory, gradients back, every step
+    e2e_steps = 5
+    hx = x.cpu().pin_memory()
+    hg = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(hx, non_blocking=True)
+        d.forward(x)
+        hg.copy_(d.backward(gy), non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    if rank == 0:
+        line = {
+            "metric": DISCO_METRIC, "value": value, "unit": DISCO_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic: seeded Gaussian fields and cotangents",
+            "config": disco_config(), "roofline": roofline,
+            "kernels": {k: {"ms_per_launch": v} for k, v in kern.items()}, "nnz": d.nnz,
+            "gpu_launches": 2 * args.steps,
+            "e2e": {"value": world * DISCO_C * e2e_steps / e2e_s, "unit": DISCO_UNIT,
+                    "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(x.numel() * 4),
+                    "steps": e2e_steps},
+            "clocks": clk,
+            "cpu_baseline": cpu_baseline_disco() if world == 1 and not args.no_cpu_baseline else None,
+        }
+        print(json.dumps(line))
+        sys.stdout.flush()
+    d.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_disco() -> dict:
+    """The FP64 oracle on a slab: psi of one output latitude (the 90th of
+    360) and the forward contraction of one channel at 16 output longitudes."""
+    import oracle
+    from oracle import disco
+    H, W, grid = DISCO_GRID
+    x, _, w = oracle.grid(H, grid)
+    th = np.arccos(x)
+    u = np.random.Generator(np.random.PCG64(5)).standard_normal((1, H, W))
+    t0 = time.perf_counter()
+    psi = disco.psi_dense(th[[90]], th, w, W, DISCO_CUTOFF, DISCO_N)
+    npts = 16
+    for wo in range(npts):
+        np.einsum("khiv,biv->bkh", psi, np.roll(u, -wo, axis=-1))
+    dt = time.perf_counter() - t0
+    return {"value": npts / (H * W) / dt, "unit": DISCO_UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one channel, output latitude 90 of 360, {npts} output longitudes (psi built for that "
+                      f"latitude, dense contraction, numpy FP64, forward only); counts {npts}/{H * W} of a field; "
+                      f"{dt:.1f} s"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["block", "batched", "scores", "noise"], default="block",
+    ap.add_argument("--workload", choices=["block", "batched", "scores", "noise", "disco"], default="block",
                     help="block: SHT -> filter -> ISHT at 721x1440 (the headline); batched: forward + inverse "
                          "SHT of the uneven four-grid mix; scores: angular PSD + spectral CRPS of a "
                          "16-member ensemble")
@@ -1126,6 +1273,8 @@ def main(argv=None):
         return run_gpu_scores(args)
     if args.workload == "noise":
         return run_gpu_noise(args)
+    if args.workload == "disco":
+        return run_gpu_disco(args)
     return run_gpu(args)
 
 

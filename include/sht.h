@@ -466,6 +466,49 @@ sht_status_t sht_diffusion_step(void *zhat, const void *eta, int64_t B, int lmax
                                 double lambda, double sigma, uint64_t seed,
                                 uint64_t step, void *stream);
 
+/* ------------------------------------------------------------------------
+ * DISCO convolution (Sec. B.5, Eq. disco_convolution_formula)
+ *
+ * The contraction of a field with the sparse convolution tensor psi of a
+ * locally supported filter basis, for every shift in longitude:
+ *   y[c][k][h][w] = sum_{h', w'} psi[k][h][h'][w'] x[c][h'][(w' + s w) mod nlon_in],
+ *   psi[k][h][h'][w'] = kb_k(R_h^{-1} x_{h', w'}) w_{h'} 2 pi / nlon_in,
+ * nlon_in = s nlon_out, R_h the rotation taking the north pole to the
+ * output point (theta_h, longitude 0), and the basis kb_k of Sec. B.5.1 on
+ * the cap of radius theta_cutoff: with vartheta' = vartheta / theta_cutoff
+ * <= 1 and the azimuth varphi of the rotated input point,
+ * cos^2(pi vartheta' / 2) times cos or sin of pi (l vartheta' sin varphi +
+ * m vartheta' cos varphi), 0 <= l, m < basis_n: the cosines for all (l, m),
+ * then the sines without l = m = 0, K = 2 basis_n^2 - 1 functions.  The
+ * mixing of channels and basis functions with learnable weights, a dense
+ * GEMM over (c, k), is left to the caller.
+ * ------------------------------------------------------------------------ */
+typedef struct sht_disco_s *sht_disco_t;
+
+/* Build psi (FP64 on the host, FP32 on the device) for an input grid
+ * (nlat_in, nlon_in, grid_in) and an output grid (nlat_out, nlon_out,
+ * grid_out); nlon_in a multiple of nlon_out, basis_n 1 .. 4,
+ * 0 < theta_cutoff <= pi (radians), on CUDA device `device`. */
+sht_status_t sht_disco_create(sht_disco_t *out, int nlat_in, int nlon_in,
+                              int grid_in, int nlat_out, int nlon_out,
+                              int grid_out, int basis_n, double theta_cutoff,
+                              int device);
+
+/* K and the number of (output latitude, input point) entries of psi. */
+sht_status_t sht_disco_info(sht_disco_t disco, int *nbasis, int64_t *nnz);
+
+/* x: float32 [C][nlat_in][nlon_in] -> y: float32 [C][K][nlat_out][nlon_out]. */
+sht_status_t sht_disco_forward(sht_disco_t disco, const float *x, float *y,
+                               int64_t C, void *stream);
+
+/* The transpose of sht_disco_forward (its backward): gy: float32
+ * [C][K][nlat_out][nlon_out] -> gx: float32 [C][nlat_in][nlon_in]
+ * (overwritten). */
+sht_status_t sht_disco_backward(sht_disco_t disco, const float *gy, float *gx,
+                                int64_t C, void *stream);
+
+sht_status_t sht_disco_destroy(sht_disco_t disco);
+
 /* ---------------------------------------------------------------------------
  * Per-kernel timing.  While profiling is on, every kernel a plan's execute
  * calls launch is bracketed by two CUDA events recorded on the launch

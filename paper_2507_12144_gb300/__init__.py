@@ -22,7 +22,7 @@ from ._abi import ShtError
 
 __all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
-           "SpectralBlock", "spectral_block", "diffusion_step", "SphericalDiffusion", "angular_psd", "zonal_psd",
+           "SpectralBlock", "spectral_block", "Disco", "DiscoContraction", "disco_contraction", "diffusion_step", "SphericalDiffusion", "angular_psd", "zonal_psd",
            "spectral_crps", "spectral_crps_backward",
            "spectral_crps_loss", "SpectralCRPSLoss", "sht_forward_ad", "SHTForward", "spatial_crps", "ShtError"]
 
@@ -627,3 +627,81 @@ class SphericalDiffusion:
         diffusion_step(self.z, self.kT, self.lam, self.sigma, self.seed, self.step)
         self.step += 1
         return sht_inverse(self.plan, self.z)
+
+
+# ---------------------------------------------------------------------------
+# DISCO convolution (Sec. B.5, Eq. disco_convolution_formula)
+# ---------------------------------------------------------------------------
+
+class Disco:
+    """The sparse convolution tensor psi of the Morlet-type basis (basis_n,
+    theta_cutoff in radians) from an input grid to an output grid (nlon_in
+    a multiple of nlon_out), and its contraction with fields."""
+
+    def __init__(self, nlat_in: int, nlon_in: int, grid_in: str, nlat_out: int, nlon_out: int, grid_out: str,
+                 basis_n: int = 3, theta_cutoff: float = 0.1, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().sht_disco_create(ctypes.byref(h), int(nlat_in), int(nlon_in), _abi.GRIDS[grid_in],
+                                               int(nlat_out), int(nlon_out), _abi.GRIDS[grid_out], int(basis_n),
+                                               float(theta_cutoff), dev.index))
+        self._h = h
+        self.device = dev
+        self.nlat_in, self.nlon_in, self.nlat_out, self.nlon_out = int(nlat_in), int(nlon_in), int(nlat_out), int(nlon_out)
+        k = ctypes.c_int()
+        nnz = ctypes.c_int64()
+        _abi.check(_abi.lib().sht_disco_info(h, ctypes.byref(k), ctypes.byref(nnz)))
+        self.nbasis, self.nnz = int(k.value), int(nnz.value)
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        """float32 [..., nlat_in, nlon_in] -> [..., K, nlat_out, nlon_out]."""
+        x = _need(x, torch.float32, "x", self.device)
+        if x.shape[-2:] != (self.nlat_in, self.nlon_in):
+            raise ValueError(f"x must end in ({self.nlat_in}, {self.nlon_in})")
+        lead = tuple(x.shape[:-2])
+        C = x.numel() // (self.nlat_in * self.nlon_in)
+        y = torch.empty(lead + (self.nbasis, self.nlat_out, self.nlon_out), dtype=torch.float32, device=x.device)
+        _abi.check(_abi.lib().sht_disco_forward(self._h, _ptr(x), _ptr(y), C, _stream(x)))
+        return y
+
+    def backward(self, gy: torch.Tensor) -> torch.Tensor:
+        """The transpose: float32 [..., K, nlat_out, nlon_out] -> [..., nlat_in, nlon_in]."""
+        gy = _need(gy, torch.float32, "gy", self.device)
+        if gy.shape[-3:] != (self.nbasis, self.nlat_out, self.nlon_out):
+            raise ValueError(f"gy must end in ({self.nbasis}, {self.nlat_out}, {self.nlon_out})")
+        lead = tuple(gy.shape[:-3])
+        C = gy.numel() // (self.nbasis * self.nlat_out * self.nlon_out)
+        gx = torch.empty(lead + (self.nlat_in, self.nlon_in), dtype=torch.float32, device=gy.device)
+        _abi.check(_abi.lib().sht_disco_backward(self._h, _ptr(gy), _ptr(gx), C, _stream(gy)))
+        return gx
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            h, self._h = self._h, None
+            _abi.check(_abi.lib().sht_disco_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DiscoContraction(torch.autograd.Function):
+    """y = contraction with psi (Eq. disco_convolution_formula); the backward
+    is the transposed contraction kernel."""
+
+    @staticmethod
+    def forward(ctx, x, disco):
+        ctx.disco = disco
+        return disco.forward(x)
+
+    @staticmethod
+    def backward(ctx, gy):
+        return ctx.disco.backward(gy.contiguous()), None
+
+
+def disco_contraction(x: torch.Tensor, disco: Disco) -> torch.Tensor:
+    return DiscoContraction.apply(x, disco)

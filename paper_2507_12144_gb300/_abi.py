@@ -84,6 +84,11 @@ SIGNATURES = {
     "sht_angular_psd": ([_p, _p, _i64, _i, _i, _p], _i),
     "sht_spectral_crps": ([_p, _p, _p, _p, _p, _i, _i64, _i, _i, _i, _i, _i, _p], _i),
     "sht_zonal_psd": ([_p, _p, _p, _i64, _p], _i),
+    "sht_disco_create": ([ctypes.POINTER(_p), _i, _i, _i, _i, _i, _i, _i, ctypes.c_double, _i], _i),
+    "sht_disco_info": ([_p, _ip, _i64p], _i),
+    "sht_disco_forward": ([_p, _p, _p, _i64, _p], _i),
+    "sht_disco_backward": ([_p, _p, _p, _i64, _p], _i),
+    "sht_disco_destroy": ([_p], _i),
     "sht_diffusion_step": ([_p, _p, _i64, _i, _i, _d, _i, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                             ctypes.c_uint64, _p], _i),
     "sht_spectral_crps_backward": ([_p, _p, _p, _p, _p, _i, _i64, _i, _i, _i, _i, _i, _p], _i),

@@ -441,6 +441,11 @@ sht_status_t check_channels(sht_plan_s *p, int Cin, int Cout, bool block) {
 
 
 }  // namespace
+
+void grid_nodes(int grid, int nlat, std::vector<double> &x, std::vector<double> &s, std::vector<double> &w) {
+  make_grid(grid, nlat, x, s, w);
+}
+
 }  // namespace shtgb
 
 using namespace shtgb;

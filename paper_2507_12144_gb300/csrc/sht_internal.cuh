@@ -213,6 +213,9 @@ cudaError_t launch_r2c_bf16(const float *x, __nv_bfloat16 *Fhi, __nv_bfloat16 *F
 
 // Record a failure message for sht_last_error_message() and return status.
 sht_status_t fail(sht_status_t st, const std::string &msg);
+// latitude nodes x = cos(theta_k), sin(theta_k) and weights w_k of a grid
+// (the plan's grids; k = 0 is the northernmost row)
+void grid_nodes(int grid, int nlat, std::vector<double> &x, std::vector<double> &s, std::vector<double> &w);
 sht_status_t cuda_fail(cudaError_t err, const char *what);
 
 // Number of l in parity class p at order m for lmax L.

@@ -193,3 +193,21 @@ def test_diffusion_step_rejects_bad_arguments_before_any_cuda_call(lib):
     assert f(p8, None, 1, 8, 8, kT, 2, 1.0, 1.0, 0, 0, None) == 1
     assert b"aligned" in lib.sht_last_error_message()
     assert f(None, None, 0, 8, 8, kT, 2, 1.0, 1.0, 0, 0, None) == 0       # B = 0: no-op
+
+
+def test_disco_rejects_bad_arguments_before_any_cuda_call(lib):
+    h = ctypes.c_void_p()
+    f = lib.sht_disco_create
+    assert f(None, 9, 16, 0, 9, 16, 0, 2, 0.5, 0) == 1
+    assert f(ctypes.byref(h), 1, 16, 0, 9, 16, 0, 2, 0.5, 0) == 1           # nlat < 2
+    assert f(ctypes.byref(h), 9, 16, 0, 9, 6, 0, 2, 0.5, 0) == 1            # 16 not a multiple of 6
+    assert b"multiple" in lib.sht_last_error_message()
+    assert f(ctypes.byref(h), 9, 16, 7, 9, 16, 0, 2, 0.5, 0) == 1           # unknown grid
+    assert f(ctypes.byref(h), 9, 16, 0, 9, 16, 0, 5, 0.5, 0) == 1           # basis_n > 4
+    assert f(ctypes.byref(h), 9, 16, 0, 9, 16, 0, 2, 0.0, 0) == 1           # cutoff 0
+    assert f(ctypes.byref(h), 9, 16, 0, 9, 16, 0, 2, 4.0, 0) == 1           # cutoff > pi
+    assert not h.value
+    assert lib.sht_disco_forward(None, None, None, 1, None) == 1
+    assert lib.sht_disco_backward(None, None, None, 1, None) == 1
+    assert lib.sht_disco_info(None, None, None) == 1
+    assert lib.sht_disco_destroy(None) == 0
