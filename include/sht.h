@@ -20,6 +20,12 @@
  * Y_l^m(theta, phi) = Phat_l^m(cos theta) e^{i m phi} with the orthonormal
  * normalisation and one factor (-1)^m (Eq. spherical_harmonics).
  *
+ * Around the transforms (sections further down): ensemble scores of the
+ * coefficients and the grid (power spectra, spectral and spatial CRPS with
+ * the loss gradient; Sec. D.4, E.1, F.7), the DISCO convolution's sparse
+ * contraction and its transpose (Sec. B.5), and one step of the spherical
+ * diffusion process that makes the noise channels (Sec. B.7).
+ *
  * Conventions
  *   - lmax and mmax are COUNTS: 0 <= l < lmax, 0 <= m < mmax, and
  *     1 <= mmax <= lmax, mmax <= nlon/2 + 1.  Gaussian grids need
