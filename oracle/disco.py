@@ -138,3 +138,21 @@ def disco_direct(u, theta_out, nlon_out, theta_in, w_in, theta_cutoff, n):
             kb = _basis_values(vt, vp, theta_cutoff, n)
             y[..., :, h, w] = np.einsum("kiv,...iv->...k", kb * omega[None], u)
     return y
+
+
+def transposed_direct(g, theta_out, w_out, nlon_out, theta_in, nlon_in, theta_cutoff, n):
+    """Eq. (transposed_disco_convolution) evaluated point by point at the
+    input-grid points x: sum_k sum_i conj(k_k(R_{x_i}^{-1} x)) g_k(x_i) omega_i
+    over the output-grid points x_i (weights w_out 2 pi / nlon_out), for
+    g [..., K, nlat_out, nlon_out]; returns [..., nlat_in, nlon_in]."""
+    g = np.asarray(g, dtype=np.float64)
+    phi_in = 2.0 * np.pi * np.arange(nlon_in) / nlon_in
+    TI, PI = np.meshgrid(theta_in, phi_in, indexing="ij")
+    out = np.zeros(g.shape[:-3] + (len(theta_in), nlon_in))
+    for h, to in enumerate(theta_out):
+        om = w_out[h] * 2.0 * np.pi / nlon_out
+        for w in range(nlon_out):
+            vt, vp = local_coords(to, 2.0 * np.pi * w / nlon_out, TI, PI)
+            kb = _basis_values(vt, vp, theta_cutoff, n)  # [K, nlat_in, nlon_in]
+            out += np.einsum("kiv,...k->...iv", kb, g[..., :, h, w]) * om
+    return out

@@ -73,3 +73,22 @@ def test_basis_is_compact_and_counted():
     vt, _ = disco.local_coords(th[16], 0.0, *np.meshgrid(th, 2 * np.pi * np.arange(64) / 64, indexing="ij"))
     assert np.all(psi[:, 0][:, vt > tc] == 0.0)
     assert np.count_nonzero(psi[0, 0]) == np.count_nonzero(vt < tc)
+
+
+def test_backward_is_the_papers_transposed_convolution():
+    """Eq. (transposed_disco_convolution) sums over the rotations of the
+    output points with their quadrature weights; the transpose of the
+    contraction carries the input weights instead:
+    backward(omega_out g) = omega_in transposed(g)."""
+    nlat_i, nlon_i, nlat_o, s = 11, 16, 9, 2
+    th_i, w_i = _theta(nlat_i, "equiangular_cc")
+    th_o, w_o = _theta(nlat_o, "gauss")
+    n, tc = 2, 0.7
+    nlon_o = nlon_i // s
+    psi = disco.psi_dense(th_o, th_i, w_i, nlon_i, tc, n)
+    g = np.random.Generator(np.random.PCG64(3)).standard_normal((2, disco.basis_count(n), nlat_o, nlon_o))
+    om_o = (w_o * 2.0 * np.pi / nlon_o)[:, None]
+    om_i = (w_i * 2.0 * np.pi / nlon_i)[:, None]
+    a = disco.disco_backward(g * om_o, psi, s)
+    b = om_i * disco.transposed_direct(g, th_o, w_o, nlon_o, th_i, nlon_i, tc, n)
+    np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-12 * np.max(np.abs(b)))
