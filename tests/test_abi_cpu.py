@@ -211,3 +211,21 @@ def test_disco_rejects_bad_arguments_before_any_cuda_call(lib):
     assert lib.sht_disco_backward(None, None, None, 1, None) == 1
     assert lib.sht_disco_info(None, None, None) == 1
     assert lib.sht_disco_destroy(None) == 0
+
+
+def test_python_bindings_reject_host_tensors_and_wrong_dtypes():
+    """The binding checks device and dtype before any library call: a host
+    tensor or a wrong dtype is a Python error, never a CPU computation."""
+    torch = pytest.importorskip("torch")
+    import paper_2507_12144_gb300 as sht
+    c = torch.zeros((2, 4, 4), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="CUDA"):
+        sht.angular_psd(c)
+    with pytest.raises(ValueError, match="CUDA"):
+        sht.spectral_crps(torch.zeros((3, 2, 4, 4), dtype=torch.complex64), c)
+    with pytest.raises(ValueError, match="CUDA"):
+        sht.spectral_crps_backward(torch.zeros((3, 2, 4, 4), dtype=torch.complex64), c, torch.zeros(2))
+    with pytest.raises(TypeError):
+        sht.diffusion_step(c, [1e-3])
+    with pytest.raises(TypeError, match="torch.Tensor"):
+        sht.angular_psd([[0.0]])
