@@ -229,3 +229,20 @@ def test_python_bindings_reject_host_tensors_and_wrong_dtypes():
         sht.diffusion_step(c, [1e-3])
     with pytest.raises(TypeError, match="torch.Tensor"):
         sht.angular_psd([[0.0]])
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/sht.h is a C ABI: it compiles as C99 with warnings on, and a
+    C program can take the address of every declared function."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    names = _declared_functions()
+    src = tmp_path / "use.c"
+    src.write_text('#include "sht.h"\nvoid *table[] = {' + ", ".join(f"(void *){n}" for n in names) + "};\n"
+                   "int main(void) { return table[0] == 0; }\n")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-c", str(src), "-o",
+                        str(tmp_path / "use.o"), "-I", os.path.join(ROOT, "include")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
