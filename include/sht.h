@@ -223,16 +223,21 @@ sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,
  * device memory through their own pool and forbid cudaMalloc in plug-ins,
  * or services held to a fixed memory budget.  The plan itself must have
  * been made beforehand (sht_plan allocates its tables).
- *   - Limit: one field of the plan's grid must fit, i.e. 16 * mmax *
- *     ceil(nlat/2) bytes <= 16 MiB; larger grids get SHT_ERR_INVALID_ARG.
- *     Larger batches are processed in chunks that fit.
+ *   - Limit: the smallest chunk must fit.  A chunk row holds 4 floats
+ *     (the re and im parts of two fields; the kernel loads them 16 bytes at
+ *     a time) for every (order, parity, latitude), so the grid needs
+ *     32 * mmax * ceil(nlat/2) bytes <= 16 MiB, also for a single field;
+ *     larger grids get SHT_ERR_INVALID_ARG.  Larger batches are processed
+ *     in chunks that fit.
  *   - FP32 plans only (SHT_ERR_UNSUPPORTED otherwise).
  *   - The array exists once per GPU that loads the library and stays until
  *     the process exits.  Every call on a device shares it: calls whose
  *     work overlaps on the GPU (two streams, or two host threads) race.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream
- *     capture. */
+ *     capture.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset of that device, do not call this entry point again.
+ *   - SHT_ERR_CUDA if the plan's device cannot be made current. */
 sht_status_t sht_forward_static_scratch(sht_plan_t plan, const float *x,
                                         void *xhat, int64_t B, void *stream);
 

@@ -11,6 +11,16 @@
 // The array is 16 MiB and lives on every GPU that loads the library until
 // the process exits.  Calls share it, so calls whose work overlaps on the
 // GPU (different streams, or different host threads on one device) race.
+//
+// Size limit: the Legendre kernel reads the coefficients of two fields per
+// 16-byte load, so a chunk row holds at least 4 floats (two fields' re and
+// im) for every (order, parity, latitude): 32 * mmax * ceil(nlat/2) bytes
+// must fit in the 16 MiB, even when a single field is transformed.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process.  A cudaDeviceReset of that device ends the validity
+// of this address together with every plan made on the device before the
+// reset; plans made afterwards must not be used with this entry point.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -43,11 +53,20 @@ sht_status_t scratch_address(int device, void **out) {
   return SHT_OK;
 }
 
+// Makes `dev` the current device for the life of the object and restores
+// the previous one afterwards; `ok` is false when the switch failed, so
+// that nothing is looked up or launched on another device.
 struct DeviceSwitch {
   int prev = -1;
-  bool changed = false;
+  bool changed = false, ok = false;
   explicit DeviceSwitch(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    if (prev != dev) {
+      if (cudaSetDevice(dev) != cudaSuccess) return;
+      changed = true;
+    }
+    int now = -1;
+    ok = cudaGetDevice(&now) == cudaSuccess && now == dev;
   }
   ~DeviceSwitch() {
     if (changed) cudaSetDevice(prev);
@@ -73,13 +92,17 @@ extern "C" sht_status_t sht_forward_static_scratch(sht_plan_t p, const float *x,
   // Nothing in it needs clearing: the analysis kernel writes every entry the
   // Legendre kernel reads for live fields; padding columns may keep an
   // earlier call's values and only feed outputs that are discarded.
+  // A chunk row is at least 4 floats wide (the kernel's 16-byte loads take
+  // two fields), so the smallest chunk needs 4 columns whatever B is.
   const size_t column_bytes = (size_t)p->M * 2 * p->Kh * sizeof(float);
   const size_t ldc_max = (kStaticScratchBytes / column_bytes) / 4 * 4;
   if (ldc_max < 4)
-    return fail(SHT_ERR_INVALID_ARG, "grid too large for the 16 MiB static scratch: one field needs " +
-                                         std::to_string(column_bytes * 4) + " bytes");
+    return fail(SHT_ERR_INVALID_ARG,
+                "grid too large for the 16 MiB static scratch: the smallest chunk (4 columns, two fields) needs "
+                "32 * mmax * ceil(nlat/2) = " + std::to_string(column_bytes * 4) + " bytes");
   const int64_t chunk = (int64_t)(ldc_max / 2);  // fields per chunk
   DeviceSwitch g(p->device);
+  if (!g.ok) return fail(SHT_ERR_CUDA, "could not make the plan's device current");
   void *scratch = nullptr;
   sht_status_t st = scratch_address(p->device, &scratch);
   if (st != SHT_OK) return st;
