@@ -1,7 +1,10 @@
 """GPU parity: every call of the C ABI against the FP64 oracle.
 
 Tolerances (relative L2 per field over the stored values, the l >= m
-triangle for spectral results): 1e-5 for the FP32 path.  Grids cover
+triangle for spectral results) for one operation: 1e-5 FP32, 2e-5 split
+BF16, 2e-3 BF16; the spectral block chains three operations and is held to
+the same per-field numbers, except BF16, which is held to three BF16
+roundings and misses 2e-3 (a strict expected failure).  Grids cover
 Gaussian and both equiangular weightings, odd and even nlat, mmax < lmax,
 the Nyquist column, ragged batches and several row/column tiles.
 """
@@ -11,21 +14,13 @@ import pytest
 import oracle
 from paper_2507_12144_gb300 import inputs
 
-from _fixtures import (batch_from_bases, base_fields, per_field_spatial_err, per_field_spec_err, rel_l2,
-                       triangle_mask)
+from _fixtures import (BF16_STAGE, TOL, assert_op_err, batch_from_bases, base_fields, chain_bound,
+                       per_field_spatial_err, per_field_spec_err, rel_l2, triangle_mask)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
-# relative L2 tolerances per precision of the Legendre contractions.  BF16
-# rounds the input data to bf16, whose unit roundoff is 2^-8 (7 stored
-# fraction bits); for smooth fields the rounding errors of neighbouring rows
-# are alike and do not average out, so the bound is the unit roundoff itself.
-TOL = {"fp32": 1e-5, "split_bf16": 2e-5, "bf16": 2.0 ** -8}
-# "+rec": the tensor-core precisions with the Legendre table generated on
-# chip by the recurrence instead of streamed from the precomputed table
-TOL.update({p + "+rec": TOL[p] for p in ("split_bf16", "bf16")})
 PRECS = ["fp32", "split_bf16", "bf16", "split_bf16+rec", "bf16+rec"]
 TC_PRECS = ["split_bf16", "bf16", "split_bf16+rec", "bf16+rec"]
 
@@ -72,8 +67,7 @@ def test_forward_matches_oracle(shtgb, shape, prec):
     plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     out = shtgb.sht_forward(plan, _to_gpu(fields, torch.float32)).cpu().numpy()
     plan.check()
-    err = per_field_spec_err(out, ref)
-    assert err.max() <= TOL[prec], err
+    assert_op_err(per_field_spec_err(out, ref), prec)
     # exact zeros above the diagonal, exactly real m = 0
     assert np.all(out[:, ~triangle_mask(L, M)] == 0)
     assert np.all(out[..., 0].imag == 0)
@@ -90,15 +84,26 @@ def test_inverse_matches_oracle(shtgb, shape, prec):
     plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     out = shtgb.sht_inverse(plan, _to_gpu(c, torch.complex64)).cpu().numpy()
     plan.check()
-    err = per_field_spatial_err(out, ref)
-    assert err.max() <= TOL[prec], err
+    assert_op_err(per_field_spatial_err(out, ref), prec)
+
+
+@pytest.mark.xfail(strict=True, reason="documented miss: plain BF16 rounds each coefficient once; a field carried by "
+                                       "a few coefficients reaches up to 2^-8, above the 2e-3 stated for BF16")
+@pytest.mark.parametrize("prec", ["bf16", "bf16+rec"])
+def test_bf16_inverse_max_over_fields_at_2e3(shtgb, prec):
+    nlat, nlon, grid, L, M, B = SHAPES[2]
+    c = inputs.spectral_coeffs(200, (B,), L, M, nyquist_nlon=nlon).astype(np.complex64)
+    c[:, ~triangle_mask(L, M)] = 0
+    ref = oracle.sht_inverse(c, nlat, nlon, grid, L, M)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
+    out = shtgb.sht_inverse(plan, _to_gpu(c, torch.complex64)).cpu().numpy()
+    assert per_field_spatial_err(out, ref).max() <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES[:6])
 def test_adjoints_match_oracle(shtgb, shape, prec):
     nlat, nlon, grid, L, M, B = shape
-    TOL_FP32 = TOL[prec]
     plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     gy = inputs.spectral_coeffs(300, (B,), L, M, spectrum="flat").astype(np.complex64)
     gx = inputs.spatial_noise(301, (B, nlat, nlon)).astype(np.float32)
@@ -106,8 +111,8 @@ def test_adjoints_match_oracle(shtgb, shape, prec):
     ref_ia = oracle.sht_inverse_adjoint(gx.astype(np.float64), nlat, nlon, grid, L, M)
     out_fa = shtgb.sht_forward_adjoint(plan, _to_gpu(gy, torch.complex64)).cpu().numpy()
     out_ia = shtgb.sht_inverse_adjoint(plan, _to_gpu(gx, torch.float32)).cpu().numpy()
-    assert per_field_spatial_err(out_fa, ref_fa).max() <= TOL_FP32
-    assert per_field_spec_err(out_ia, ref_ia).max() <= TOL_FP32
+    assert_op_err(per_field_spatial_err(out_fa, ref_fa), prec)
+    assert_op_err(per_field_spec_err(out_ia, ref_ia), prec)
     assert np.all(out_ia[:, ~triangle_mask(L, M)] == 0)
 
 
@@ -147,21 +152,25 @@ def test_block_and_fused_filter_inverse_match_oracle(shtgb, prec):
     xh = shtgb.sht_forward(plan, x)
     y2 = shtgb.spectral_filter_inverse(plan, xh, Wg).cpu().numpy()
     plan.check()
-    if prec.startswith("bf16"):
-        # the data is rounded twice (Fourier rows, filter output) and the
-        # channel mixing can shrink single output fields, so the bound is two
-        # roundings relative to the whole member
-        for out in (y, y2):
-            assert rel_l2(out, ref_y) <= 2 * TOL_FP32
-    elif prec.startswith("split_bf16"):
-        # three chained split contractions (forward, filter, inverse), each
-        # within the per-operation tolerance; the whole member within one
-        for out in (y, y2):
-            assert per_field_spatial_err(out, ref_y).max() <= 3 * TOL_FP32
-            assert rel_l2(out, ref_y) <= TOL_FP32
-    else:
-        assert per_field_spatial_err(y, ref_y).max() <= TOL_FP32
-        assert per_field_spatial_err(y2, ref_y).max() <= TOL_FP32
+    bound = 3 * BF16_STAGE if prec.startswith("bf16") else TOL_FP32
+    for out in (y, y2):
+        err = per_field_spatial_err(out, ref_y)
+        assert err.max() <= bound, err
+
+
+@pytest.mark.xfail(strict=True, reason="documented miss: the BF16 block rounds its data three times; 2e-3 is the "
+                                       "tolerance of one BF16 operation")
+@pytest.mark.parametrize("prec", ["bf16", "bf16+rec"])
+def test_bf16_block_at_one_operation_tolerance(shtgb, prec):
+    nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
+    Bm, Cin, Cout = 3, 5, 4
+    fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, Bm * Cin, 3, 500)
+    W = inputs.filter_weights(501, L, Cout, Cin).astype(np.complex64)
+    ref_y = oracle.sht_inverse(oracle.spectral_filter(ref_x.reshape(Bm, Cin, L, M), W), nlat, nlon, grid, L, M)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=10, precision=prec)
+    y = shtgb.sht_spectral_block(plan, _to_gpu(fields.reshape(Bm, Cin, nlat, nlon), torch.float32),
+                                 _to_gpu(W, torch.complex64)).cpu().numpy()
+    assert per_field_spatial_err(y, ref_y).max() <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", TC_PRECS)
@@ -182,10 +191,26 @@ def test_forward_then_block_on_one_plan(shtgb, prec, BmC):
     x = _to_gpu(fields, torch.float32)
     for _ in range(2):
         xh = shtgb.sht_forward(plan, x).cpu().numpy()
-        assert per_field_spec_err(xh, ref_x).max() <= TOL[prec]
+        assert_op_err(per_field_spec_err(xh, ref_x), prec)
         y = shtgb.sht_spectral_block(plan, x.reshape(Bm, C, nlat, nlon), _to_gpu(W, torch.complex64)).cpu().numpy()
         assert np.isfinite(y).all()
-        assert rel_l2(y, ref_y) <= 2 * TOL[prec]
+        assert per_field_spatial_err(y, ref_y).max() <= chain_bound(prec, 3)
+        if not prec.startswith("bf16"):
+            assert rel_l2(y, ref_y) <= TOL[prec]
+
+
+@pytest.mark.xfail(strict=True, reason="documented miss: the three chained split-BF16 operations of the block reach "
+                                       "2.46e-5 per field on this small grid (each operation alone is within 2e-5)")
+def test_split_bf16_chain_per_field_at_one_operation_tolerance(shtgb):
+    nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
+    Bm, C = 2, 128
+    fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, Bm * C, 3, 520)
+    W = inputs.filter_weights(521, L, C, C).astype(np.complex64)
+    ref_y = oracle.sht_inverse(oracle.spectral_filter(ref_x.reshape(Bm, C, L, M), W), nlat, nlon, grid, L, M)
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=Bm * C, precision="split_bf16", max_channels=C)
+    y = shtgb.sht_spectral_block(plan, _to_gpu(fields, torch.float32).reshape(Bm, C, nlat, nlon),
+                                 _to_gpu(W, torch.complex64)).cpu().numpy()
+    assert per_field_spatial_err(y, ref_y).max() <= TOL["split_bf16"]
 
 
 def test_round_trip_and_ylm_deltas_gauss_33x64(shtgb):
@@ -220,12 +245,12 @@ def test_tensor_core_column_tiles(shtgb, prec):
     plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec, max_batch=512)
     x = _to_gpu(fields, torch.float32)
     out = shtgb.sht_forward(plan, x).cpu().numpy()
-    assert per_field_spec_err(out, ref).max() <= TOL[prec]
+    assert_op_err(per_field_spec_err(out, ref), prec)
     c = inputs.spectral_coeffs(661, (B,), L, M).astype(np.complex64)
     ref_u = oracle.sht_inverse(c[:7], nlat, nlon, grid, L, M)
     u = shtgb.sht_inverse(plan, _to_gpu(c, torch.complex64)).cpu().numpy()
     plan.check()
-    assert per_field_spatial_err(u[:7], ref_u).max() <= TOL[prec]
+    assert_op_err(per_field_spatial_err(u[:7], ref_u), prec)
 
 
 def test_batch_chunking_and_empty_batch(shtgb):
@@ -244,7 +269,6 @@ def test_plan_reuse_across_calls(shtgb, shape, prec):
     """One plan serves forward, inverse and both adjoints in any order: no
     call may read workspace left behind by another."""
     nlat, nlon, grid, L, M, B = shape
-    TOL_FP32 = TOL[prec]
     plan = _plan(shtgb, nlat, nlon, grid, L, M, precision=prec)
     x = inputs.spatial_noise(650, (B, nlat, nlon)).astype(np.float32)
     y = inputs.spectral_coeffs(651, (B,), L, M, spectrum="flat").astype(np.complex64)
@@ -263,9 +287,9 @@ def test_plan_reuse_across_calls(shtgb, shape, prec):
         for name in order:
             out = calls[name]().cpu().numpy()
             if name in ("fwd", "iadj"):
-                assert per_field_spec_err(out, refs[name]).max() <= TOL_FP32, name
+                assert_op_err(per_field_spec_err(out, refs[name]), prec)
             else:
-                assert per_field_spatial_err(out, refs[name]).max() <= TOL_FP32, name
+                assert_op_err(per_field_spatial_err(out, refs[name]), prec)
 
 
 def test_streams_are_respected(shtgb):
@@ -301,13 +325,15 @@ def test_plan_oom_injection_and_bad_pointers(shtgb):
     assert lib.sht_forward(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), -1, None) == 1
 
 
-def test_autograd_matches_oracle_finite_differences(shtgb):
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16", "split_bf16+rec"])
+def test_autograd_matches_oracle_finite_differences(shtgb, prec):
     """SHT -> W[l] (complex, N(0, 1/C)) -> ISHT on a 17 x 32 Gaussian copy of
     the differentiation case: GPU gradients vs FP64 central differences of
-    the oracle composition, and the adjoint identity on the GPU."""
+    the oracle composition, for the FP32 and the split-BF16 plans."""
     nlat, nlon, L, C, Bm = 17, 32, 16, 4, 2
     grid = "gauss"
-    plan = _plan(shtgb, nlat, nlon, grid, L, L)
+    tol = TOL[prec]
+    plan = _plan(shtgb, nlat, nlon, grid, L, L, precision=prec, max_batch=Bm * C, max_channels=C)
     x64 = inputs.spatial_noise(800, (Bm, C, nlat, nlon)).astype(np.float32).astype(np.float64)
     W64 = inputs.filter_weights(801, L, C, C).astype(np.complex64).astype(np.complex128)
     v64 = inputs.spatial_noise(802, (Bm, C, nlat, nlon)).astype(np.float32).astype(np.float64)
@@ -326,10 +352,10 @@ def test_autograd_matches_oracle_finite_differences(shtgb):
     for seed in (803, 804):
         d = inputs.spatial_noise(seed, x64.shape)
         fd = (loss(x64 + eps * d, W64) - loss(x64 - eps * d, W64)) / (2 * eps)
-        assert abs(fd - np.sum(gx * d)) <= 1e-5 * (abs(fd) + np.linalg.norm(gx) * np.linalg.norm(d))
+        assert abs(fd - np.sum(gx * d)) <= tol * (abs(fd) + np.linalg.norm(gx) * np.linalg.norm(d))
         D = inputs.filter_weights(seed + 10, L, C, C)
         fdw = (loss(x64, W64 + eps * D) - loss(x64, W64 - eps * D)) / (2 * eps)
-        assert abs(fdw - np.real(np.vdot(D, gW))) <= 1e-5 * (abs(fdw) + np.linalg.norm(gW) * np.linalg.norm(D))
+        assert abs(fdw - np.real(np.vdot(D, gW))) <= tol * (abs(fdw) + np.linalg.norm(gW) * np.linalg.norm(D))
 
 
 def test_adjoint_identities_on_gpu(shtgb):
@@ -358,18 +384,18 @@ def test_adjoint_identities_on_gpu(shtgb):
 @pytest.mark.parametrize("prec", ["fp32", "split_bf16", "split_bf16+rec"])
 def test_full_size_block_against_oracle(shtgb, prec):
     nlat, nlon, grid, L, M = 721, 1440, "equiangular_cc", 720, 720
-    TOL_FP32 = TOL[prec]
+    tol = TOL[prec]
     C = 72
     fields, ref_x = batch_from_bases(nlat, nlon, grid, L, M, C, 4, 1000)
     plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=C, precision=prec)
     x = _to_gpu(fields, torch.float32)
     xh = shtgb.sht_forward(plan, x).cpu().numpy()
     err = per_field_spec_err(xh, ref_x)
-    assert err.max() <= TOL_FP32, err.max()
+    assert err.max() <= tol, err.max()
     W = inputs.filter_weights(1001, L, C, C).astype(np.complex64)
     y = shtgb.sht_spectral_block(plan, x.reshape(1, C, nlat, nlon), _to_gpu(W, torch.complex64)).cpu().numpy()[0]
     # oracle: filter all channels, inverse for a few output channels
     yh = oracle.spectral_filter(ref_x.reshape(1, C, L, M), W)[0]
     for o in (0, 37, 71):
         ref_y = oracle.sht_inverse(yh[o], nlat, nlon, grid, L, M)
-        assert rel_l2(y[o], ref_y) <= TOL_FP32
+        assert rel_l2(y[o], ref_y) <= tol
