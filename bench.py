@@ -1254,9 +1254,9 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
     ap.add_argument("--no-fp32-side", action="store_true",
                     help="skip timing the plain FP32 form beside a tensor-core precision")
-    ap.add_argument("--table-source", choices=["streamed", "recurrence"], default="streamed",
-                    help="Legendre table of the tensor-core precisions: precomputed and streamed, or "
-                         "generated on chip by the recurrence")
+    ap.add_argument("--table-source", choices=["streamed", "recurrence", "mixed"], default="streamed",
+                    help="Legendre table of the tensor-core precisions: precomputed and streamed, "
+                         "generated on chip by the recurrence, or streamed forward and generated inverse")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

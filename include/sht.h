@@ -111,13 +111,19 @@ typedef enum {
  * for the tensor-core precisions; FP32 plans always stream an FP32 table.
  * STREAMED: bf16 hi/lo tables built once in FP64 at plan time and read by
  *   TMA on every call (table bytes re-read per call, no recurrence work).
- * RECURRENCE: only FP64 seeds every 32 degrees are stored; extra warps of
- *   the Legendre kernels run the three-term recurrence in FP32 on chip
- *   (about 1/16 of the table bytes, more instructions per call); lmax <=
- *   1400, else sht_plan returns UNSUPPORTED. */
+ * RECURRENCE: only seeds every 32 degrees are stored (FP64-computed, kept
+ *   as FP32 pairs); extra warps of the Legendre kernels run the three-term
+ *   recurrence in FP32 on chip (about 1/16 of the table bytes, more
+ *   instructions per call).  The inverse keeps its generated table in
+ *   tensor memory and, for split BF16, in three bf16 parts.
+ * MIXED: the forward contraction streams the table (forward layout only),
+ *   the inverse generates it on chip as RECURRENCE does.
+ * RECURRENCE and MIXED need lmax <= 1400, else sht_plan returns
+ * UNSUPPORTED. */
 typedef enum {
   SHT_TABLE_STREAMED = 0,
-  SHT_TABLE_RECURRENCE = 1
+  SHT_TABLE_RECURRENCE = 1,
+  SHT_TABLE_MIXED = 2
 } sht_table_source_t;
 
 typedef struct {
@@ -240,6 +246,53 @@ sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,
  *   - SHT_ERR_CUDA if the plan's device cannot be made current. */
 sht_status_t sht_forward_static_scratch(sht_plan_t plan, const float *x,
                                         void *xhat, int64_t B, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Partial transforms: the local steps of the distributed (pencil) transform
+ * of Algorithm 1 (appendix, "Distributed spherical Harmonic transforms").
+ * A rank of a pencil decomposition holds a block of latitude rows for the
+ * longitude steps and a block of orders over all latitudes for the Legendre
+ * steps; the exchanges between the steps (all-to-alls over the polar and
+ * azimuth groups) are the caller's.  The forward SHT is
+ * legendre_orders(forward) of analysis_rows of every row, the inverse SHT
+ * is synthesis_rows of legendre_orders(inverse).  All data on the plan's
+ * device, 16-byte aligned, caller-owned; stream-ordered, no allocation.
+ * Longitude steps use the generic mixed-radix FFT in FP32 on any plan;
+ * the Legendre steps use the FP32 plan's table (SHT_ERR_UNSUPPORTED on
+ * tensor-core plans).
+ *
+ * sht_analysis_rows: F[b][r][m] = w_k (2 pi / nlon) sum_j x[b][r][j]
+ *   e^{-2 pi i j m / nlon} for m < mmax, k = k0 + r (Algorithm 1's
+ *   2 pi FFT_1D_R2C and truncation; w_k the latitude weight of Sec. B.1).
+ *   x: float32 [B][nrows][nlon], F: complex64 [B][nrows][mmax];
+ *   0 <= k0, k0 + nrows <= nlat, else SHT_ERR_INVALID_ARG. */
+sht_status_t sht_analysis_rows(sht_plan_t plan, const float *x, void *F,
+                               int64_t B, int k0, int nrows, void *stream);
+
+/* sht_synthesis_rows: y[b][r][j] = sum_{m < mmax} c_m Re(G[b][r][m]
+ *   e^{2 pi i j m / nlon}), c_0 = 1, c_m = 2, c_{nlon/2} = 1 (Eq. isht for a
+ *   real field; the imaginary parts of m = 0 and of the Nyquist mode are
+ *   ignored).  G: complex64 [B][nrows][mmax], y: float32 [B][nrows][nlon];
+ *   k0 and nrows as for sht_analysis_rows (the rows carry no weight). */
+sht_status_t sht_synthesis_rows(sht_plan_t plan, const void *G, float *y,
+                                int64_t B, int k0, int nrows, void *stream);
+
+/* sht_legendre_orders: the Legendre step for orders m0 .. m0 + mcount - 1
+ *   over all latitudes (Algorithm 1's "Legendre-Gauss quadrature via tensor
+ *   contraction" on an order block; Eq. isht's sum over l for the inverse).
+ *   inverse = 0: in = F complex64 [B][nlat][mcount] (weights applied, as
+ *     sht_analysis_rows gives them), out = xhat complex64 [B][lmax][mcount],
+ *     xhat[b][l][j] = sum_k Phat_l^m(x_k) F[b][k][j], m = m0 + j, zero for
+ *     l < m.
+ *   inverse = 1: in = yhat complex64 [B][lmax][mcount] (entries l < m are
+ *     ignored), out = G complex64 [B][nlat][mcount], G[b][k][j] =
+ *     sum_l Phat_l^m(x_k) yhat[b][l][j].
+ *   0 <= m0, m0 + mcount <= mmax, else SHT_ERR_INVALID_ARG; FP32 plans only
+ *   (SHT_ERR_UNSUPPORTED).  Uses the plan's workspaces: one stream at a
+ *   time per plan, like the other execute calls. */
+sht_status_t sht_legendre_orders(sht_plan_t plan, int inverse, const void *in,
+                                 void *out, int64_t B, int m0, int mcount,
+                                 void *stream);
 
 /* ---------------------------------------------------------------------------
  * Host-resident fields through the spectral block.  A pipe owns `depth`

@@ -53,9 +53,10 @@ class Plan:
     ``grid`` is "gauss", "equiangular_cc" or "equiangular_trapz"; ``lmax``
     and ``mmax`` are counts (l < lmax, m < mmax); ``precision`` is "fp32",
     "bf16" or "split_bf16" for the Legendre contractions.  ``table_source``
-    ("streamed" or "recurrence") selects how the tensor-core precisions get
-    the Legendre table: read from a precomputed bf16 table, or generated on
-    chip by the three-term recurrence from stored seeds.  ``max_channels``
+    ("streamed", "recurrence" or "mixed") selects how the tensor-core
+    precisions get the Legendre table: read from a precomputed bf16 table,
+    generated on chip by the three-term recurrence from stored seeds, or
+    streamed for the forward and generated for the inverse.  ``max_channels``
     bounds Cin / Cout of the fused spectral block (0: min(max_batch, 128)).
     """
 
@@ -178,6 +179,54 @@ def sht_forward(plan: Plan, x: torch.Tensor) -> torch.Tensor:
     x, lead, B = _spatial_in(plan, x)
     out = torch.empty(lead + (plan.lmax, plan.mmax), dtype=torch.complex64, device=x.device)
     _abi.check(_abi.lib().sht_forward(plan.handle, _ptr(x), _ptr(out), B, _stream(x)))
+    return out
+
+
+def _lead(t: torch.Tensor, keep: int):
+    lead = tuple(t.shape[:-keep])
+    return lead, int(torch.tensor(lead).prod().item()) if lead else 1
+
+
+def analysis_rows(plan: Plan, x: torch.Tensor, k0: int) -> torch.Tensor:
+    """Longitude step of latitude rows k0 .. k0 + n - 1 (a rank's block in the
+    distributed transform): float32 [..., n, nlon] -> complex64 [..., n, mmax],
+    w_k (2 pi / nlon) FFT_R2C truncated to mmax."""
+    x = _need(x, torch.float32, "x", plan.device)
+    if x.dim() < 2 or x.shape[-1] != plan.nlon:
+        raise ValueError(f"x must end in (rows, {plan.nlon}), got {tuple(x.shape)}")
+    n = int(x.shape[-2])
+    lead, B = _lead(x, 2)
+    out = torch.empty(lead + (n, plan.mmax), dtype=torch.complex64, device=x.device)
+    _abi.check(_abi.lib().sht_analysis_rows(plan.handle, _ptr(x), _ptr(out), B, int(k0), n, _stream(x)))
+    return out
+
+
+def synthesis_rows(plan: Plan, G: torch.Tensor, k0: int) -> torch.Tensor:
+    """Real synthesis of latitude rows: complex64 [..., n, mmax] -> float32
+    [..., n, nlon], sum_m c_m Re(G_m e^{i m phi})."""
+    G = _need(G, torch.complex64, "G", plan.device)
+    if G.dim() < 2 or G.shape[-1] != plan.mmax:
+        raise ValueError(f"G must end in (rows, {plan.mmax}), got {tuple(G.shape)}")
+    n = int(G.shape[-2])
+    lead, B = _lead(G, 2)
+    out = torch.empty(lead + (n, plan.nlon), dtype=torch.float32, device=G.device)
+    _abi.check(_abi.lib().sht_synthesis_rows(plan.handle, _ptr(G), _ptr(out), B, int(k0), n, _stream(G)))
+    return out
+
+
+def legendre_orders(plan: Plan, t: torch.Tensor, m0: int, inverse: bool = False) -> torch.Tensor:
+    """Legendre step of orders m0 .. m0 + mc - 1 over all latitudes (FP32
+    plans): forward complex64 [..., nlat, mc] -> [..., lmax, mc]; inverse
+    [..., lmax, mc] -> [..., nlat, mc]."""
+    t = _need(t, torch.complex64, "t", plan.device)
+    rows_in, rows_out = (plan.lmax, plan.nlat) if inverse else (plan.nlat, plan.lmax)
+    if t.dim() < 2 or t.shape[-2] != rows_in:
+        raise ValueError(f"input must end in ({rows_in}, orders), got {tuple(t.shape)}")
+    mc = int(t.shape[-1])
+    lead, B = _lead(t, 2)
+    out = torch.empty(lead + (rows_out, mc), dtype=torch.complex64, device=t.device)
+    _abi.check(_abi.lib().sht_legendre_orders(plan.handle, int(bool(inverse)), _ptr(t), _ptr(out), B, int(m0), mc,
+                                              _stream(t)))
     return out
 
 

@@ -17,7 +17,7 @@ STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3: "S
           4: "SHT_ERR_CUDA", 5: "SHT_ERR_TIMEOUT", 6: "SHT_ERR_INTERNAL"}
 GRIDS = {"gauss": 0, "equiangular_cc": 1, "equiangular_trapz": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "split_bf16": 2}
-TABLE_SOURCES = {"streamed": 0, "recurrence": 1}
+TABLE_SOURCES = {"streamed": 0, "recurrence": 1, "mixed": 2}
 KERNEL_COUNT = 10
 
 
@@ -58,6 +58,9 @@ SIGNATURES = {
     "sht_spectral_block": ([_p, _p, _p, _p, _i64, _i, _i, _p], _i),
     "spectral_filter_inverse": ([_p, _p, _p, _p, _i64, _i, _i, _p], _i),
     "sht_forward_static_scratch": ([_p, _p, _p, _i64, _p], _i),
+    "sht_analysis_rows": ([_p, _p, _p, _i64, _i, _i, _p], _i),
+    "sht_synthesis_rows": ([_p, _p, _p, _i64, _i, _i, _p], _i),
+    "sht_legendre_orders": ([_p, _i, _p, _p, _i64, _i, _i, _p], _i),
     "sht_profile_begin": ([_p, _i], _i),
     "sht_profile_collect": ([_p, _i64p, ctypes.POINTER(ctypes.c_double), _i64p], _i),
     "sht_profile_end": ([_p], _i),

@@ -481,9 +481,10 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
   for (int r : o.reserved)
     if (r != 0) return fail(SHT_ERR_INVALID_ARG, "reserved option fields must be zero");
   if (o.max_channels < 0) return fail(SHT_ERR_INVALID_ARG, "max_channels must be >= 0");
-  if (o.table_source != SHT_TABLE_STREAMED && o.table_source != SHT_TABLE_RECURRENCE)
+  if (o.table_source != SHT_TABLE_STREAMED && o.table_source != SHT_TABLE_RECURRENCE &&
+      o.table_source != SHT_TABLE_MIXED)
     return fail(SHT_ERR_INVALID_ARG, "unknown table_source");
-  if (o.table_source == SHT_TABLE_RECURRENCE && o.precision != SHT_PREC_FP32 && leg_rows(lmax, 0, 0) > 700)
+  if (o.table_source != SHT_TABLE_STREAMED && o.precision != SHT_PREC_FP32 && leg_rows(lmax, 0, 0) > 700)
     return fail(SHT_ERR_UNSUPPORTED, "the on-chip recurrence supports lmax <= 1400");
   if (nlon > kMaxNlon) return fail(SHT_ERR_UNSUPPORTED, "nlon above 8192 is not supported");
   RadixPlan rp;
@@ -562,6 +563,15 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       for (int k0 = 0; k0 < p->Kh; k0 += trow) it.push_back(LegTile{m, q, k0, m + q});
   p->n_fwd_tiles = (int)ft.size();
   p->n_inv_tiles = (int)it.size();
+  // the tiles of one order are consecutive: first tile of each m
+  p->fwd_tile_m.assign(mmax + 1, (int)ft.size());
+  p->inv_tile_m.assign(mmax + 1, (int)it.size());
+  for (int t = (int)ft.size() - 1; t >= 0; t--) p->fwd_tile_m[ft[t].m] = t;
+  for (int t = (int)it.size() - 1; t >= 0; t--) p->inv_tile_m[it[t].m] = t;
+  for (int m = mmax - 1; m >= 0; m--) {
+    p->fwd_tile_m[m] = std::min(p->fwd_tile_m[m], p->fwd_tile_m[m + 1]);
+    p->inv_tile_m[m] = std::min(p->inv_tile_m[m], p->inv_tile_m[m + 1]);
+  }
 
   // device tables
   if ((e = dev_alloc((void **)&p->d_err, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
@@ -614,11 +624,14 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
     if (e == cudaSuccess && tc) {
       // tensor-core plans: the Legendre table either as bf16 hi/lo tables
       // streamed by TMA (forward [rows][Kp64], transposed
-      // [(2m + p) Kh + k'][Ip64]), or generated on chip from FP64 seeds every
-      // 32 rows of every (m, p), FP32 recurrence coefficients (zero past
+      // [(2m + p) Kh + k'][Ip64]), or generated on chip from seeds every 32
+      // rows of every (m, p) (FP64, stored as FP32), FP32 recurrence coefficients (zero past
       // lmax) and the latitudes as hi + lo
       const bool split = o.precision == SHT_PREC_SPLIT_BF16;
-      const bool gen = o.table_source == SHT_TABLE_RECURRENCE;
+      // the forward streams the table unless it is generated everywhere;
+      // the inverse generates it unless it is streamed everywhere
+      const bool gen_fwd = o.table_source == SHT_TABLE_RECURRENCE;
+      const bool gen_inv = o.table_source != SHT_TABLE_STREAMED;
       std::vector<int> roff(2 * (size_t)mmax);
       int64_t frows = 0;
       for (int m = 0; m < mmax; m++)
@@ -628,34 +641,41 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
         }
       e = upload(&p->d_roff, roff);
       TcPlanView &T = p->tc;
-      T.gen = gen;
-      if (!gen) {
+      T.gen_fwd = gen_fwd;
+      T.gen_inv = gen_inv;
+      p->table_bytes = 0;
+      if (!gen_fwd) {
+        // streamed tables: the forward layout, and the transposed layout
+        // when the inverse streams too
         const int Kp64 = (p->Kh + 63) / 64 * 64;
         const int Ip64 = (leg_rows(lmax, 0, 0) + 63) / 64 * 64;
         const int64_t irows = (int64_t)mmax * 2 * p->Kh;
         const size_t fbytes = sizeof(__nv_bfloat16) * (size_t)frows * Kp64;
-        const size_t ibytes = sizeof(__nv_bfloat16) * (size_t)irows * Ip64;
+        const size_t ibytes = gen_inv ? 0 : sizeof(__nv_bfloat16) * (size_t)irows * Ip64;
         if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_hi, fbytes);
-        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_hi, ibytes);
         if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_lo, fbytes);
-        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_lo, ibytes);
         if (e == cudaSuccess) e = cudaMemset(p->d_tf_hi, 0, fbytes);
-        if (e == cudaSuccess) e = cudaMemset(p->d_ti_hi, 0, ibytes);
         if (e == cudaSuccess) e = cudaMemset(p->d_tf_lo, 0, fbytes);
-        if (e == cudaSuccess) e = cudaMemset(p->d_ti_lo, 0, ibytes);
+        if (!gen_inv) {
+          if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_hi, ibytes);
+          if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_lo, ibytes);
+          if (e == cudaSuccess) e = cudaMemset(p->d_ti_hi, 0, ibytes);
+          if (e == cudaSuccess) e = cudaMemset(p->d_ti_lo, 0, ibytes);
+        }
         if (e == cudaSuccess)
           e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_ti_hi, p->d_ti_lo, p->d_roff, Kp64, Ip64, d_x, d_s,
                                     d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
-        p->table_bytes = (int64_t)(fbytes + ibytes) * 2;
+        p->table_bytes += (int64_t)(fbytes + ibytes) * 2;
         if (e == cudaSuccess &&
             !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, Kp64, frows, 64, 128) &&
               tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, Kp64, frows, 64, 128) &&
               tc_encode_2d(&T.tab_inv_hi, p->d_ti_hi, Ip64, irows, 64, 128) &&
               tc_encode_2d(&T.tab_inv_lo, p->d_ti_lo, Ip64, irows, 64, 128)))
           e = cudaErrorInvalidValue;
-      } else {
+      }
+      if (gen_inv) {
         const int NB = (leg_rows(lmax, 0, 0) + 31) / 32 + 1;
-        const size_t seed_bytes = 16 * (size_t)mmax * 2 * NB * p->Kh;
+        const size_t seed_bytes = sizeof(float2) * (size_t)mmax * 2 * NB * p->Kh;
         // two-step coefficients of row i (l = m + p + 2 i): the step to the
         // row after next, zero where that row is past lmax
         const int ldC = (leg_rows(lmax, 0, 0) + 63) / 64 * 64 + 64;
@@ -694,7 +714,7 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
         if (e == cudaSuccess) e = cudaMemset(p->d_seeds, 0, seed_bytes);
         if (e == cudaSuccess)
           e = launch_seed_gen(p->d_seeds, NB, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
-        p->table_bytes = (int64_t)(seed_bytes + sizeof(float4) * coef.size());
+        p->table_bytes += (int64_t)(seed_bytes + sizeof(float4) * coef.size());
         T.seeds = p->d_seeds;
         T.coef = p->d_coef;
         T.x2h = p->d_x2h;
@@ -795,10 +815,14 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       free_plan(p);
       return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the inverse output");
     }
-    if (!(tc_encode_fold_bf16(&T.f_hi, f_hi(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh) &&
-          tc_encode_fold_bf16(&T.f_lo, f_lo(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh) &&
+    if (!(tc_encode_fold_bf16(&T.f_hi, f_hi(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh, 64) &&
+          tc_encode_fold_bf16(&T.f_lo, f_lo(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh, 64) &&
+          tc_encode_fold_bf16(&T.fh_hi, f_hi(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh, 32) &&
+          tc_encode_fold_bf16(&T.fh_lo, f_lo(p), p->lay_f, p->ldcb, 2 * mmax, p->Kh, 32) &&
           tc_encode_srows_bf16(&T.s_hi, p->d_s_hi, p->ldcb, mmax, lmax, true, 64) &&
           tc_encode_srows_bf16(&T.s_lo, p->d_s_lo, p->ldcb, mmax, lmax, true, 64) &&
+          tc_encode_srows_bf16(&T.sh_hi, p->d_s_hi, p->ldcb, mmax, lmax, true, 64, 32) &&
+          tc_encode_srows_bf16(&T.sh_lo, p->d_s_lo, p->ldcb, mmax, lmax, true, 64, 32) &&
           tc_encode_srows_bf16(&T.so32_hi, p->d_s_hi, p->ldcb, mmax, lmax, false, 32) &&
           tc_encode_srows_bf16(&T.so32_lo, p->d_s_lo, p->ldcb, mmax, lmax, false, 32) &&
           tc_encode_srows_bf16(&T.so16_hi, p->d_s_hi, p->ldcb, mmax, lmax, false, 16) &&

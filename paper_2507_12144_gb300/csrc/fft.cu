@@ -254,6 +254,104 @@ c2r_pairs_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, 
   }
 }
 
+// Longitude analysis of arbitrary latitude rows (the local step of the
+// distributed transform, where a rank holds a block of latitudes and no
+// mirror pairs): rows r = 0 .. R-1 of x[R][nlon], row r on latitude
+// k0 + (r mod nrows) of the grid; rows 2q and 2q + 1 share one complex
+// sequence z = u_2q + i u_2q+1, separated after the FFT.  F[r][m], m < M,
+// times ring_scale of the row's latitude; no parity fold.
+__global__ void __launch_bounds__(kThreads)
+r2c_rows_kernel(const float *__restrict__ x, float2 *__restrict__ F, int64_t R, int nrows, int k0, int nlon, int M,
+                const float2 *__restrict__ twiddle, RadixPlan rp, const float *__restrict__ ring_scale) {
+  extern __shared__ float2 smem[];
+  const int n = nlon;
+  float2 *tw = smem;
+  float2 *bufA = tw + n;
+  float2 *bufB = bufA + kFields * n;
+  const int64_t r0 = (int64_t)blockIdx.x * 2 * kFields;
+  const int64_t pending = (R - r0 + 1) / 2;
+  const int nf = pending < kFields ? (int)pending : kFields;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) tw[q] = twiddle[q];
+  for (int f = 0; f < nf; f++) {
+    const int64_t ra = r0 + 2 * f, rb = ra + 1;
+    const float *xa = x + ra * n;
+    const float *xb = x + rb * n;
+    float2 *z = bufA + f * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) z[j] = make_float2(xa[j], rb < R ? xb[j] : 0.f);
+  }
+  __syncthreads();
+  float2 *Z = fft_forward(bufA, bufB, tw, rp, nf);
+  for (int t = threadIdx.x; t < nf * M; t += blockDim.x) {
+    const int f = t / M;
+    const int m = t - f * M;
+    const int64_t ra = r0 + 2 * f, rb = ra + 1;
+    const float2 *zf = Z + f * n;
+    const float2 zm = zf[m];
+    const float2 zc = conjf2(zf[(n - m) % n]);
+    const float sa = ring_scale[k0 + (int)(ra % nrows)];
+    F[ra * M + m] = cscale(cadd(zm, zc), 0.5f * sa);
+    if (rb < R) {
+      const float sb = ring_scale[k0 + (int)(rb % nrows)];
+      F[rb * M + m] = cscale(mul_mi(csub(zm, zc)), 0.5f * sb);
+    }
+  }
+}
+
+// Longitude synthesis of arbitrary rows: y[r][j] = sum_{m < M} c_m Re(G[r][m]
+// e^{2 pi i j m / nlon}) (c_0 = 1, c_{nlon/2} = 1, c_m = 2 otherwise; the
+// imaginary parts of m = 0 and of the Nyquist mode are ignored), two rows
+// per complex sequence.
+__global__ void __launch_bounds__(kThreads)
+c2r_rows_kernel(const float2 *__restrict__ G, float *__restrict__ y, int64_t R, int nlon, int M,
+                const float2 *__restrict__ twiddle, RadixPlan rp) {
+  extern __shared__ float2 smem[];
+  const int n = nlon;
+  float2 *tw = smem;
+  float2 *bufA = tw + n;
+  float2 *bufB = bufA + kFields * n;
+  float2 *Zc = bufB + kFields * n;
+  const int64_t r0 = (int64_t)blockIdx.x * 2 * kFields;
+  const int64_t pending = (R - r0 + 1) / 2;
+  const int nf = pending < kFields ? (int)pending : kFields;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) tw[q] = twiddle[q];
+  for (int t = threadIdx.x; t < nf * M; t += blockDim.x) {
+    const int f = t / M;
+    const int m = t - f * M;
+    const int64_t ra = r0 + 2 * f, rb = ra + 1;
+    const float c = 0.5f * mode_weight(m, n, 1);
+    bufA[f * n + m] = cscale(G[ra * M + m], c);
+    bufB[f * n + m] = rb < R ? cscale(G[rb * M + m], c) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nf * n; t += blockDim.x) {
+    const int f = t / n;
+    const int q = t - f * n;
+    float2 ha = make_float2(0.f, 0.f), hb = make_float2(0.f, 0.f);
+    if (q < M) {
+      ha = cadd(ha, bufA[f * n + q]);
+      hb = cadd(hb, bufB[f * n + q]);
+    }
+    const int qm = (n - q) % n;
+    if (qm < M) {
+      ha = cadd(ha, conjf2(bufA[f * n + qm]));
+      hb = cadd(hb, conjf2(bufB[f * n + qm]));
+    }
+    const float2 z = make_float2(ha.x - hb.y, ha.y + hb.x);  // Z = ha + i hb
+    Zc[f * n + q] = conjf2(z);
+  }
+  __syncthreads();
+  float2 *out = fft_forward(Zc, bufA, tw, rp, nf);
+  for (int f = 0; f < nf; f++) {
+    const int64_t ra = r0 + 2 * f, rb = ra + 1;
+    const float2 *of = out + f * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const float2 v = of[j];
+      y[ra * n + j] = v.x;
+      if (rb < R) y[rb * n + j] = -v.y;
+    }
+  }
+}
+
 }  // namespace
 
 static size_t fft_smem_bytes(int nlon, int nbuf) {
@@ -305,6 +403,30 @@ cudaError_t launch_c2r(const float *Gw, float *y, int nlat, int nlon, int M, int
   if (e != cudaSuccess) return e;
   c2r_pairs_kernel<<<grid, kThreads, smem, st>>>(Gw, y, nlat, nlon, M, B, fl, twiddle, rp, ring_scale,
                                                  inverse_weights);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_r2c_rows(const float *x, float2 *F, int64_t R, int nrows, int k0, int nlon, int M,
+                            const float2 *twiddle, const RadixPlan &rp, const float *ring_scale, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  const int64_t nblk = (R + 2 * kFields - 1) / (2 * kFields);
+  if (nblk > 0x7fffffff) return cudaErrorInvalidValue;
+  const size_t smem = fft_smem_bytes(nlon, 2);
+  cudaError_t e = set_smem((const void *)r2c_rows_kernel, smem);
+  if (e != cudaSuccess) return e;
+  r2c_rows_kernel<<<(unsigned)nblk, kThreads, smem, st>>>(x, F, R, nrows, k0, nlon, M, twiddle, rp, ring_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2r_rows(const float2 *G, float *y, int64_t R, int nlon, int M, const float2 *twiddle,
+                            const RadixPlan &rp, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  const int64_t nblk = (R + 2 * kFields - 1) / (2 * kFields);
+  if (nblk > 0x7fffffff) return cudaErrorInvalidValue;
+  const size_t smem = fft_smem_bytes(nlon, 3);
+  cudaError_t e = set_smem((const void *)c2r_rows_kernel, smem);
+  if (e != cudaSuccess) return e;
+  c2r_rows_kernel<<<(unsigned)nblk, kThreads, smem, st>>>(G, y, R, nlon, M, twiddle, rp);
   return cudaGetLastError();
 }
 

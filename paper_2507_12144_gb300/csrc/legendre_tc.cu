@@ -6,24 +6,32 @@
 // rows of the folded table by the 2B real columns of the data.  Precision
 // forms, with x = x_hi + x_lo, x_hi = bf16(x), x_lo = bf16(x - x_hi):
 //   split BF16: table and data split, T_hi D_hi + T_hi D_lo + T_lo D_hi (the
-//               lo*lo term is below the FP32 accumulation error);
-//   BF16:       data rounded to bf16, table split, T_hi D_hi + T_lo D_hi.
-// The table keeps its lo part in both: a bf16-rounded table carries one
-// systematic error per (l, m, k) shared by every field (up to the bf16 unit
-// roundoff 2^-8), whereas rounding errors of the data are independent and
-// average out in the sum over latitudes.  The paper trains in bf16 mixed
+//               lo*lo term is below the FP32 accumulation error); the table
+//               generated in tensor memory for the inverse is split in three
+//               (T = T_hi + T_lo + T_lo2, x_lo2 = bf16(x - x_hi - x_lo)) and
+//               adds T_lo2 D_hi;
+//   BF16:       data rounded to bf16, table split in two, T_hi D_hi + T_lo D_hi.
+// The table keeps its lo part in both: its representation error is one
+// systematic error per (l, m, k) shared by every field, and the sum over
+// latitudes of oscillating Phat against smooth data cancels (the terms are
+// about 8x the result at l^-3 spectra), which amplifies it; with two terms
+// the table's error is 2.5x the data's, with three it is negligible.  The paper trains in bf16 mixed
 // precision (Sec. E.3); the split form recovers FP32-level accuracy.
 //
-// One persistent CTA per SM (256 threads, 512 when an operand is built on
-// chip):
-//   warp 0       TMA producer of the operand tiles (table or data rows, and
-//                the data / weights) into a ring of pipeline stages
-//   warp 1       MMA issuer (one thread)
-//   warp 2       tensor-memory allocation (two accumulators)
-//   warps 4..7   epilogue: tensor memory -> registers -> swizzled shared
-//                staging -> TMA stores, one 32-lane quarter each
-//   warps 8..15  only with kGen: the Legendre table generators (recurrence)
-//                or the filter's weight builders
+// Persistent kernels, one CTA per SM:
+//   tc_persistent_kernel  streamed Legendre table (TMA) or the filter
+//     (256 threads; the filter's weights are built on chip by 8 more warps):
+//     warp 0 TMA producer, warp 1 MMA issuer (one thread), warp 2 tensor
+//     memory allocation, warps 4..7 epilogue (tensor memory -> registers ->
+//     swizzled shared staging -> TMA stores), warps 8..15 weight builders.
+//   tc_gen_kernel  Legendre table generated on chip by the recurrence
+//     (512 threads): the same roles, warps 8..15 generate the table chunks.
+//     The generated table (A) and the TMA-loaded data (B) have separate
+//     rings: two table slots of 64 K, and data stages of 32 K, as many as
+//     fit.  The inverse writes its table slots into tensor memory, from
+//     where the MMAs read A: the tcgen05 MMAs of 128 x 144 tiles are bound
+//     by the shared-memory bandwidth of their operands (A 4 KB + B 4.6 KB
+//     per K step of 16), so A out of shared memory is A off that bound.
 // Stages are guarded by mbarriers; every wait is bounded and records a
 // timeout in the plan's error word instead of hanging.
 #include <cudaTypedefs.h>
@@ -43,10 +51,24 @@ constexpr int kKc = 64;       // K per stage (one 128-byte bf16 row)
 constexpr int kThreads = 256;     // filter: TMA, MMA, TMEM, -, 4 epilogue warps
 constexpr int kThreadsGen = 512;  // Legendre: the same + 8 table-generator warps
 constexpr int kSeedRows = 32;     // rows between recurrence seeds
-constexpr int kSeedAhead = 4;     // seed prefetch distance of the generators (chunks)
 constexpr int kCoefPerThread = 3; // coefficient slice per generator thread (<= 768 per tile)
 constexpr int kMaxStages = 6;
 constexpr uint32_t kABytes = kRows * 128;  // one A tile (hi or lo)
+// generated-table kernel: K rows per data stage (a divisor of kKc), table
+// slots, data stages
+constexpr int kKb = 32;
+constexpr int kBPerA = kKc / kKb;  // data stages per table chunk
+constexpr int kASlots = 2;
+constexpr int kMaxBStages = 8;
+// one shared-memory table slot of the generated-table forward: 128 rows x
+// 64 K as hi and lo
+constexpr uint32_t kASlotBytes = 2 * kABytes;
+// the inverse's table slots in tensor memory (accumulators at columns 0 and
+// 256, at most 160 wide): slot s at column 160 + 256 s, parts hi, lo, lo2
+// 32 columns apart (64 K as bf16 pairs)
+constexpr uint32_t kTmemAccStride = 256;
+constexpr int kTmemMaxN = 160;
+__host__ __device__ constexpr uint32_t a_tmem_col(int slot) { return 160u + 256u * (uint32_t)slot; }
 
 __host__ __device__ inline int tmem_cols_for(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256; }
 
@@ -93,11 +115,11 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 //   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[(m + p + 2i) M + m][c]   (A = table, B = data, MN-major)
 //   kFilt: D[m][n]  = sum_k  X[l M + m][b kx + k] WR[l][n][k] (A = data, B = weights, K-major)
 // Table and weights always enter split (hi + lo); data enters split for
-// split BF16 and rounded (hi only) for BF16.  The Legendre table of kFwd /
-// kInv either streams from a precomputed bf16 table by TMA (kGen = false) or
-// is generated on chip by 8 extra warps from recurrence seeds (kGen = true);
-// the filter's real-form weights WR are always built on chip by those warps
-// from the complex W (kFilt with kGen = true).
+// split BF16 and rounded (hi only) for BF16.  Here the Legendre table of
+// kFwd / kInv streams from a precomputed bf16 table by TMA (kGen = false;
+// the table generated on chip is tc_gen_kernel's); the filter's real-form
+// weights WR are built on chip by 8 extra warps from the complex W (kFilt
+// with kGen = true).
 // ---------------------------------------------------------------------------
 enum Mode { kFwd = 0, kInv = 1, kFilt = 2 };
 
@@ -119,14 +141,12 @@ struct FwdOut {
 
 // Recurrence seeds of the on-chip Legendre table: for order m, parity p,
 // 32-row block j (rows i = 32 j .. 32 j + 31, l = m + p + 2 i) and latitude
-// k', Phat at l0 = m + p + 64 j and l0 + 2 (the block's first two rows), as
-// FP32 mantissas s0, s1 of a common power of two 2^e (e = kZeroBlock: the
-// block is negligible).
-struct Seed {
-  float s0, s1;
-  int e, pad;
-};
-constexpr int kZeroBlock = -100000;
+// k', Phat at l0 = m + p + 64 j and l0 + 2 (the block's first two rows) in
+// FP32, as float2 at [((2m + p) NB + j) Kh + k'].  Values below the FP32
+// normal range are stored as zero: inside one block a row grows by at most
+// about 10^32 over the previous 32 rows (the evanescent region just above
+// l = m), so what such a seed would have grown into stays below 10^-6 and
+// contributes nothing the FP32 accumulation keeps.
 
 // One problem (a plan and its batch) of a Legendre launch.  A launch walks
 // the tiles of up to kMaxSeg problems (grids of different sizes in one
@@ -147,7 +167,7 @@ struct SegArgs {
   // on-chip table: seeds [((2m + p) NB + j) Kh + k'], two-step
   // coefficients coef[(2m + p) ldC + i] = (alpha, beta, gamma, 0) of row i,
   // squared latitudes x^2 = x2h + x2l
-  const Seed *seeds;
+  const float2 *seeds;
   const float4 *coef;
   const float *x2h, *x2l;
   int NB, ldC;
@@ -169,7 +189,8 @@ struct TcParams {
   int nseg, ntiles, stages;
   int Nmax;               // widest column tile: stage layout and TMEM columns
   int ncmax, xtot;        // generator shared memory: coefficients, x^2 entries
-  int epi_off;            // byte offset of the epilogue staging (inverse)
+  int epi_off;            // byte offset of the epilogue staging
+  int epi_nbuf;           // its buffers per warp (generated-table kernel)
   // filter (one problem)
   const FiltTile *ftiles;
   int L, M, Nt, Bm, ntn, kx, nwr, cin, cout, lds;
@@ -178,7 +199,8 @@ struct TcParams {
   unsigned *err;
 };
 
-__host__ __device__ inline int a_count(int mode, bool split) { return (mode == kFilt && !split) ? 1 : 2; }
+// A tiles per stage: filter data (hi, lo when split); Legendre table (hi, lo)
+__host__ __device__ inline int a_count(int mode, bool split) { return mode == kFilt ? (split ? 2 : 1) : 2; }
 __host__ __device__ inline int threads_of(bool gen) { return gen ? kThreadsGen : kThreads; }
 __host__ __device__ inline int b_count(int mode, bool split) { return (mode == kFilt || split) ? 2 : 1; }
 __host__ __device__ inline uint32_t b_bytes_of(int mode, int Nt) {
@@ -282,7 +304,7 @@ struct TileWalk {
 // Bytes that the TMA loads of one chunk of the tile deliver.
 template <int kMode, bool kSplit, bool kGen>
 __device__ __forceinline__ uint32_t chunk_tx_bytes(const TileInfo &ti) {
-  const uint32_t abytes = (kMode != kFilt && kGen) ? 0u : (uint32_t)a_count(kMode, kSplit) * kABytes;
+  const uint32_t abytes = (uint32_t)a_count(kMode, kSplit) * kABytes;
   if (kMode == kFilt) return abytes + (kGen ? 0u : 2u * (uint32_t)ti.Nt * 128u);
   return abytes + (uint32_t)b_count(kMode, kSplit) * (uint32_t)((ti.Nt + 63) / 64) * 8192u;
 }
@@ -306,15 +328,12 @@ __device__ __forceinline__ void issue_chunk(unsigned char *st, int Nmax, uint32_
       mma_bf16(tmem, ah, bl, idesc, 1u);
       if (kSplit) mma_bf16(tmem, desc_advance(desc_kmajor_sw128(a_lo), ks * 32), bh, idesc, 1u);
     } else {
-      // A = table: K-major from TMA, or generated (MN-major forward, K-major inverse)
-      constexpr bool kAmn = kGen && kMode == kFwd;
-      const uint64_t ah2 = kAmn ? desc_mnmajor_sw128(a_hi + ks * 2048, 8192, 1024) : ah;
-      const uint64_t al = kAmn ? desc_mnmajor_sw128(a_lo + ks * 2048, 8192, 1024)
-                               : desc_advance(desc_kmajor_sw128(a_lo), ks * 32);
+      // A = table, K-major from TMA
+      const uint64_t al = desc_advance(desc_kmajor_sw128(a_lo), ks * 32);
       const uint64_t bh = desc_mnmajor_sw128(b_hi + ks * 2048, 8192, 1024);
-      mma_bf16(tmem, ah2, bh, idesc, acc0);
+      mma_bf16(tmem, ah, bh, idesc, acc0);
       mma_bf16(tmem, al, bh, idesc, 1u);
-      if (kSplit) mma_bf16(tmem, ah2, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
+      if (kSplit) mma_bf16(tmem, ah, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
     }
   }
 }
@@ -326,10 +345,8 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
   const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
-  if (kMode == kFilt || !kGen) {
-    tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
-    if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
-  }
+  tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
   if (kMode == kFilt) {
     if (!kGen) {
       tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
@@ -405,10 +422,23 @@ __device__ __forceinline__ void store_rows_bf16_tma(uint32_t tl, int ncols, cons
   __syncwarp();
 }
 
-// Epilogue of one tile for the accumulator at tacc (zero: write zeros).
+// Wait until at most nbuf - 1 of this warp's bulk stores still read their
+// staging buffer (lane 0 issues them), before the next buffer is written.
+__device__ __forceinline__ void staging_wait(int nbuf, int lane) {
+  if (lane == 0) {
+    if (nbuf == 2)
+      bulk_wait_read<1>();
+    else
+      bulk_wait_read<0>();
+  }
+  __syncwarp();
+}
+
+// Epilogue of one tile for the accumulator at tacc (zero: write zeros),
+// through nbuf (1 or 2) staging buffers of 4 KB per warp at stg.
 template <int kMode>
 __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, uint32_t tacc, int q4, int lane,
-                                         bool zero, unsigned char *stg) {
+                                         bool zero, unsigned char *stg, int nbuf) {
   const int Nt = ti.Nt;
   const uint32_t tl = tacc + ((uint32_t)(q4 * 32) << 16);
   if (kMode == kFwd) {
@@ -424,7 +454,7 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
         const int x0 = mb * out.kx + (ti.c0 - 2 * mb * out.cin);  // output column of accumulator column c0
         const int l0 = ti.m + ti.p + 2 * (ti.r0 + q4 * 32);
         store_rows_bf16_tma(tl, Nt, &mp.o32_hi, &mp.o32_lo, &mp.o16_hi, &mp.o16_lo, out.rows_lo != nullptr, x0,
-                            ti.m, l0, stg, 2, lane);
+                            ti.m, l0, stg, nbuf, lane);
         return;
       }
     }
@@ -436,11 +466,8 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
       const int l0 = ti.m + ti.p + 2 * (ti.r0 + q4 * 32);
       for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
         const bool half = Nt - j0 == 16;
-        unsigned char *buf = stg + (c & 1) * 4096;
-        if (c >= 2) {
-          if (lane == 0) bulk_wait_read<1>();
-          __syncwarp();
-        }
+        unsigned char *buf = stg + (c % nbuf) * 4096;
+        if (c >= nbuf) staging_wait(nbuf, lane);
         float v[32];
         tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
         if (!half) tmem_ld16(tl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
@@ -505,11 +532,8 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
     const int k0 = ti.r0 + q4 * 32;
     for (int j0 = 0, c = 0; j0 < Nt; j0 += 32, c++) {
       const bool half = Nt - j0 == 16;
-      unsigned char *buf = stg + (c & 1) * 4096;
-      if (c >= 2) {
-        if (lane == 0) bulk_wait_read<1>();
-        __syncwarp();
-      }
+      unsigned char *buf = stg + (c % nbuf) * 4096;
+      if (c >= nbuf) staging_wait(nbuf, lane);
       float v[32];
       if (!zero) {
         tmem_ld16(tl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
@@ -580,7 +604,7 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
   }
 }
 
-// Table generator (warps 8..15 of the Legendre kernels).  Two steps of the
+// Table generator (warps 8..15 of tc_gen_kernel).  Two steps of the
 // three-term recurrence of Eq. sht_legendre_recursion, composed so that
 // only rows of one parity appear,
 //   Phat_{l+2} = (alpha_l x^2 + beta_l) Phat_l + gamma_l Phat_{l-2},
@@ -588,16 +612,14 @@ __device__ __forceinline__ void epilogue(const TcParams &P, const TileInfo &ti, 
 //   beta_l  = -a_{l+2} (b_{l+2} + a_{l+1} b_{l+1} / a_l),   (beta_m = -a_{m+2} b_{m+2})
 //   gamma_l = -a_{l+2} a_{l+1} b_{l+1} b_l,                  (gamma_m = 0)
 // give one FMA per stored row on the dependency chain.  One thread runs one
-// latitude through one 32-row block of one parity from the block's seeds,
-// in FP32 with x^2 = x2h + x2l, mantissas carried beside a power-of-two
-// exponent and renormalised when above 2^64.  The 32 values go to shared
-// memory as bf16 hi/lo in 16-byte chunks of 8 consecutive rows:
+// latitude through one 32-row block of one parity from the block's FP32
+// seeds, with x^2 = x2h + x2l.  The 32 values go to shared memory as bf16
+// hi/lo in 16-byte chunks of 8 consecutive rows:
 //   forward: A[i][k'] MN-major (rows i contiguous): thread (k' = 64 kc + g mod
 //            64, block r0/32 + g/64) of tile rows r0 .. r0 + 127;
 //   inverse: A[k'][i] K-major (i contiguous): thread (k' = r0 + g mod 128,
 //            block 2 kc + g/128).
-// Seed of chunk kc of a tile for generator thread g: its latitude k' and
-// seed block j.
+// Latitude k' and seed block j of table chunk kc (64 K) for thread g.
 template <int kMode>
 __device__ __forceinline__ void gen_coords(const TileInfo &ti, int kc, int g, int &kp, int &j) {
   if (kMode == kFwd) {
@@ -609,84 +631,64 @@ __device__ __forceinline__ void gen_coords(const TileInfo &ti, int kc, int g, in
   }
 }
 
-// Asynchronous copy of that seed into the thread's slot of the seed ring
-// (zeros where the latitude or the block does not exist).
+// The seed of that chunk (zero where the latitude or the block does not exist).
 template <int kMode>
-__device__ __forceinline__ void gen_prefetch(const SegArgs &sg, const TileInfo &ti, int kc, int g, Seed *slot) {
+__device__ __forceinline__ float2 gen_seed(const SegArgs &sg, const TileInfo &ti, int kc, int g) {
   int kp, j;
   gen_coords<kMode>(ti, kc, g, kp, j);
-  const bool ok = kp < sg.Kh && j < sg.NB;
-  const Seed *src = ok ? sg.seeds + ((int64_t)(ti.m * 2 + ti.p) * sg.NB + j) * sg.Kh + kp : sg.seeds;
-  cp_async16(slot, src, ok ? 16u : 0u);
+  if (kp >= sg.Kh || j >= sg.NB) return make_float2(0.f, 0.f);
+  return __ldg(sg.seeds + ((int64_t)(ti.m * 2 + ti.p) * sg.NB + j) * sg.Kh + kp);
 }
 
-__device__ __forceinline__ float pow2_or_zero(int E) { return E < -126 ? 0.f : __int_as_float((E + 127) << 23); }
-
-// cs: the tile's two-step coefficients in shared memory, cs[i - ibase];
-// xs: x^2 (hi, lo) of the problem's latitudes.
-template <int kMode>
-__device__ __forceinline__ void generate_chunk(const SegArgs &sg, const TileInfo &ti, int kc, int g,
-                                               unsigned char *a_hi, unsigned char *a_lo, const Seed &sd,
-                                               const float2 *xs, const float4 *cs, int ibase) {
-  int kp, j, row, cbase;
-  gen_coords<kMode>(ti, kc, g, kp, j);
-  if (kMode == kFwd) {
-    row = g & 63;  // column k' inside the tile
-    cbase = 4 * ((g >> 6) & 1);  // 8-row chunk index inside the 64-row M block
-  } else {
-    row = g & 127;
-    cbase = 4 * (g >> 7);
-  }
-  const float2 x2 = kp < sg.Kh ? xs[kp] : make_float2(0.f, 0.f);
+// The 32 rows of one thread's block, from its seeds sd and x^2 = (x2h,
+// x2l), as bf16 pairs (row 2q in the lower half): h = hi, lw = lo and, when
+// kLo2, l2 = lo2 (v - hi and (v - hi) - lo are exact in FP32).  cf: the
+// coefficients of the block's second row onwards (the step to row i + 2
+// uses those of row i + 1).  Blocks past the last row run the same steps
+// over zero seeds and zero coefficients (the coefficient array is zero past
+// lmax and the index stays inside the tile's slice), so the loop has no
+// per-step selects.
+// NQ row pairs per call; (pa, pb) carry rows i, i + 1 from call to call.
+template <bool kLo2, int NQ>
+__device__ __forceinline__ void recur_rows(float &pa, float &pb, float2 x2, const float4 *cf, uint32_t (&h)[NQ],
+                                           uint32_t (&lw)[NQ], uint32_t (&l2)[NQ]) {
   const float x2h = x2.x, x2l = x2.y;
-  const int i0 = kSeedRows * j;
-  const bool zero = sd.e == kZeroBlock || ti.m + ti.p + 2 * i0 >= sg.L;
-  float pa = zero ? 0.f : sd.s0, pb = zero ? 0.f : sd.s1;  // scaled rows i, i + 1
-  int E = zero ? 0 : sd.e;
-  float scale = zero ? 0.f : pow2_or_zero(E);
-  // the step to row i + 2 uses the coefficients of row i + 1.  A zero
-  // block runs the same steps from zero rows (and zero scale) over the
-  // first coefficients of the tile, which stay in bounds, so that the loop
-  // has no per-step selects.
-  const float4 *cf = cs + (zero ? 0 : i0 + 1 - ibase);
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    uint32_t h[4], lw[4];
+  for (int q = 0; q < NQ; q++) {
+    const float v0 = pa, v1 = pb;
+    const float4 c0 = cf[2 * q], c1 = cf[2 * q + 1];
+    const float pc = fmaf(fmaf(c0.x, x2h, fmaf(c0.x, x2l, c0.y)), pb, c0.z * pa);
+    const float pd = fmaf(fmaf(c1.x, x2h, fmaf(c1.x, x2l, c1.y)), pc, c1.z * pb);
+    pa = pc;
+    pb = pd;
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
+    const float2 hf = __bfloat1622float2(hh);
+    const float r0 = v0 - hf.x, r1 = v1 - hf.y;
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(r0, r1);
+    h[q] = *reinterpret_cast<const uint32_t *>(&hh);
+    lw[q] = *reinterpret_cast<const uint32_t *>(&ll);
+    if (kLo2) {
+      const float2 lf = __bfloat1622float2(ll);
+      const __nv_bfloat162 l22 = __floats2bfloat162_rn(r0 - lf.x, r1 - lf.y);
+      l2[q] = *reinterpret_cast<const uint32_t *>(&l22);
+    }
+  }
+}
+
+// Forward table rows into a shared-memory slot (MN-major, 128-byte
+// swizzle): thread g writes 16 rows (half hf of its 32) of latitude k' =
+// 64 kc + g mod 64 as two 16-byte chunks of 8 rows per part.
+__device__ __forceinline__ void store_rows_smem(int g, int hf, unsigned char *a_hi, unsigned char *a_lo,
+                                                const uint32_t (&h)[8], const uint32_t (&lw)[8]) {
+  const int row = g & 63;                         // column k' inside the chunk
+  const int cbase = 4 * ((g >> 6) & 1) + 2 * hf;  // 8-row chunk index inside the 64-row M block
+  const int hb = (g >> 6) >> 1;                   // 64-row M block of the 128-row tile
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const float v0 = pa * scale, v1 = pb * scale;
-      const float4 c0 = cf[2 * u], c1 = cf[2 * u + 1];
-      const float pc = fmaf(fmaf(c0.x, x2h, fmaf(c0.x, x2l, c0.y)), pb, c0.z * pa);
-      const float pd = fmaf(fmaf(c1.x, x2h, fmaf(c1.x, x2l, c1.y)), pc, c1.z * pb);
-      pa = pc;
-      pb = pd;
-      const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
-      const float2 hf = __bfloat1622float2(hh);
-      const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-      h[u] = *reinterpret_cast<const uint32_t *>(&hh);
-      lw[u] = *reinterpret_cast<const uint32_t *>(&ll);
-    }
-    cf += 8;
-    // renormalise once per 8 rows: a row grows by less than 2^12 per step
-    // here, so 2^64 plus four steps stays far inside the FP32 range, and the
-    // power-of-two rescaling is exact whenever it happens
-    if (fabsf(pb) > 1.8446744e19f) {  // 2^64
-      pa *= 5.4210109e-20f;            // 2^-64
-      pb *= 5.4210109e-20f;
-      E += 64;
-      scale = pow2_or_zero(E);
-    }
-    const int chunk = cbase + q;
-    uint32_t off;
-    if (kMode == kFwd) {
-      const int hb = (g >> 6) >> 1;  // 64-row M block of the 128-row tile
-      off = (uint32_t)hb * 8192u + (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u +
-            ((uint32_t)(chunk ^ (row & 7)) << 4);
-    } else {
-      off = (uint32_t)row * 128u + ((uint32_t)(chunk ^ (row & 7)) << 4);
-    }
-    *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  for (int q = 0; q < 2; q++) {
+    const uint32_t off = (uint32_t)hb * 8192u + (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u +
+                         ((uint32_t)((cbase + q) ^ (row & 7)) << 4);
+    *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+    *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
   }
 }
 
@@ -827,99 +829,12 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       have = next();
       if (have) fetch();
     }
-  } else if (kMode != kFilt && kGen && warp >= 8) {
-    // table generators.  Shared memory after the stage ring: the current
-    // tile's two-step coefficients (the next tile's are loaded into
-    // registers meanwhile), x^2 of every problem's latitudes, and a ring of
-    // kSeedAhead seed slots per thread filled by cp.async kSeedAhead chunks
-    // ahead.
-    const int gtid = threadIdx.x - 256;
-    float4 *cs = reinterpret_cast<float4 *>(base + (size_t)S * sbytes);
-    float2 *xs = reinterpret_cast<float2 *>(cs + P.ncmax);
-    Seed *ring = reinterpret_cast<Seed *>(xs + ((P.xtot + 1) & ~1));
-    for (int s = 0; s < P.nseg; s++)
-      for (int k = gtid; k < P.seg[s].Kh; k += 256)
-        xs[P.seg[s].xoff + k] = make_float2(__ldg(P.seg[s].x2h + k), __ldg(P.seg[s].x2l + k));
-    // prefetch cursor over the same chunk sequence
-    TileWalk<kMode> pw(P);
-    TileInfo pti{};
-    pti.nk = 0;
-    int pkc = 0;
-    auto prefetch = [&](uint32_t pg) {
-      while (pkc >= pti.nk && pw.more(P)) {
-        pti = pw.take(P);
-        pkc = 0;
-      }
-      if (pkc < pti.nk) {
-        gen_prefetch<kMode>(P.seg[pti.s], pti, pkc, gtid, ring + (pg % kSeedAhead) * 256 + gtid);
-        pkc++;
-      }
-      cp_async_commit();
-    };
-    for (uint32_t q = 0; q < (uint32_t)kSeedAhead; q++) prefetch(q);
-    auto coef_range = [&](const TileInfo &ti, int &ibase, int &ncoef) {
-      // forward: the tile's 128 rows (+ 2 past its end), inverse: every row
-      ibase = kMode == kFwd ? ti.r0 : 0;
-      ncoef = kMode == kFwd ? 2 * kKc + 4 : kKc * ti.nk + 4;
-    };
-    // coefficients of the next tile with chunks (cursor cw) into registers
-    TileWalk<kMode> cw(P);
-    auto coef_load = [&](float4 (&cr)[kCoefPerThread]) {
-#pragma unroll
-      for (int u = 0; u < kCoefPerThread; u++) cr[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      TileInfo ti{};
-      ti.nk = 0;
-      while (ti.nk == 0 && cw.more(P)) ti = cw.take(P);
-      if (ti.nk == 0) return;
-      const SegArgs &sg = P.seg[ti.s];
-      int ibase, ncoef;
-      coef_range(ti, ibase, ncoef);
-      const float4 *src = sg.coef + (int64_t)(ti.m * 2 + ti.p) * sg.ldC;
-#pragma unroll
-      for (int u = 0; u < kCoefPerThread; u++) {
-        const int e = gtid + 256 * u;
-        if (e < ncoef && ibase + e < sg.ldC) cr[u] = __ldg(src + ibase + e);
-      }
-    };
-    float4 creg[kCoefPerThread];
-    coef_load(creg);
-    uint32_t g = 0;
-    for (TileWalk<kMode> w(P); w.more(P);) {
-      const TileInfo ti = w.take(P);
-      if (ti.nk == 0) continue;
-      const SegArgs &sg = P.seg[ti.s];
-      int ibase, ncoef;
-      coef_range(ti, ibase, ncoef);
-      asm volatile("bar.sync 2, 256;" ::: "memory");  // previous tile's coefficients no longer read
-#pragma unroll
-      for (int u = 0; u < kCoefPerThread; u++) {
-        const int e = gtid + 256 * u;
-        if (e < ncoef) cs[e] = creg[u];
-      }
-      asm volatile("bar.sync 2, 256;" ::: "memory");  // also orders the x^2 stores of the first tile
-      coef_load(creg);
-      for (int kc = 0; kc < ti.nk; kc++, g++) {
-        const int s = (int)(g % (uint32_t)S);
-        const uint32_t use = g / (uint32_t)S;
-        cp_async_wait<kSeedAhead - 1>();
-        const Seed sd = ring[(g % kSeedAhead) * 256 + gtid];
-        if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, P.err);
-        unsigned char *st = base + (size_t)s * sbytes;
-        generate_chunk<kMode>(sg, ti, kc, gtid, st, st + kABytes, sd, xs + sg.xoff, cs, ibase);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full_bar[s]);
-        prefetch(g + kSeedAhead);
-      }
-    }
-    cp_async_wait<0>();
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     uint32_t g = 0, it = 0;
     for (TileWalk<kMode> w(P); w.more(P); it++) {
       const TileInfo ti = w.take(P);
-      uint32_t idesc = idesc_bf16_f32(kRows, ti.Nt, kMode != kFilt);
-      if (kGen && kMode == kFwd) idesc |= 1u << 15;  // generated table enters MN-major
+      const uint32_t idesc = idesc_bf16_f32(kRows, ti.Nt, kMode != kFilt);
       const int acc = (int)(it & 1);
       const uint32_t use_a = it >> 1;
       if (use_a > 0) mbar_wait(&tempty[acc], (use_a - 1) & 1, P.err);
@@ -948,12 +863,316 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       const int acc = (int)(it & 1);
       mbar_wait(&tfull[acc], (it >> 1) & 1, P.err);
       tc_fence_after();
-      epilogue<kMode>(P, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0, stg);
+      epilogue<kMode>(P, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, ti.nk == 0, stg, 2);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
     if (lane == 0) bulk_wait<0>();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Legendre contractions with the table generated on chip.  The K dimension
+// of a tile (latitudes k' for the forward, rows i of the (m, p) block for
+// the inverse) runs in table chunks of 64 (A, built by the generator warps
+// into one of two slots) and data stages of 32 (B, loaded by TMA into a
+// ring of as many stages as shared memory holds); each table chunk meets
+// the two data stages of its K range (one when the range ends inside it).
+//   kFwd:  D[i][c]  = sum_k' T[m][p][i][k'] F[m][p][k'][c]   (A MN-major)
+//   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[(m + p + 2i) M + m][c]   (A K-major)
+// B is MN-major (64-column boxes of 32 K rows, 128-byte swizzle).
+// ---------------------------------------------------------------------------
+
+// Data stages (32 K rows each) of a tile: those that hold rows of its K range.
+template <int kMode>
+__device__ __forceinline__ int gen_halves(const TcParams &P, const TileInfo &ti) {
+  const int kext = kMode == kFwd ? P.seg[ti.s].Kh : leg_rows(P.seg[ti.s].L, ti.m, ti.p);
+  return (kext + kKb - 1) / kKb;
+}
+
+__host__ __device__ inline uint32_t gen_box_bytes() { return 64u * kKb * 2u; }  // 64 columns x kKb rows, bf16
+__host__ __device__ inline uint32_t gen_stage_bytes(bool split, int Nt) {
+  return (uint32_t)(split ? 2 : 1) * (uint32_t)((Nt + 63) / 64) * gen_box_bytes();
+}
+
+// TMA loads of data stage h (K rows kKb h .. kKb h + kKb - 1) of a tile.
+template <int kMode, bool kSplit>
+__device__ __forceinline__ void gen_load_half(unsigned char *st, const TileInfo &ti, int h, int Nmax,
+                                              const SegMaps &mp, uint64_t *bar) {
+  const uint32_t bx = gen_box_bytes();
+  const uint32_t half_b = (uint32_t)((Nmax + 63) / 64) * bx;
+  unsigned char *b_hi = st, *b_lo = st + half_b;
+  const int nbox = (ti.Nt + 63) / 64;
+  for (int j = 0; j < nbox; j++) {
+    if (kMode == kFwd) {
+      // folded data as (column, 2m + p, k'): kKb rows k' of one (m, p)
+      tma_load_3d(b_hi + j * bx, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.b_row0, h * kKb);
+      if (kSplit) tma_load_3d(b_lo + j * bx, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0, h * kKb);
+    } else {
+      // internal rows as (column, m, l) with every second l: rows
+      // l = m + p + 2 i, i = kKb h .. kKb h + kKb - 1, of one (m, p) block
+      tma_load_3d(b_hi + j * bx, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * h * kKb);
+      if (kSplit) tma_load_3d(b_lo + j * bx, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * h * kKb);
+    }
+  }
+}
+
+// MMAs of one data stage against part hh (K kKb hh .. kKb hh + kKb - 1) of
+// the table slot, K steps of 16.  Forward: A from the shared-memory slot a
+// (MN-major), T_hi D_hi + T_lo D_hi (+ T_hi D_lo when split).  Inverse: A
+// from tensor memory at column a_col, T_hi D_hi + T_lo D_hi (+ T_lo2 D_hi +
+// T_hi D_lo when split).
+template <int kMode, bool kSplit>
+__device__ __forceinline__ void gen_issue_half(const unsigned char *a, uint32_t a_col, int hh, const unsigned char *b,
+                                               int Nmax, uint32_t tmem, uint32_t idesc, bool first) {
+  const uint32_t half_b = (uint32_t)((Nmax + 63) / 64) * gen_box_bytes();
+  const unsigned char *b_hi = b, *b_lo = b + half_b;
+#pragma unroll
+  for (int s = 0; s < kKb / 16; s++) {
+    const int ks = (kKb / 16) * hh + s;  // K step of 16 inside the 64-K table chunk
+    const uint32_t acc = (first && s == 0) ? 0u : 1u;
+    const uint64_t bh = desc_mnmajor_sw128(b_hi + s * 2048, gen_box_bytes(), 1024);
+    if (kMode == kFwd) {
+      const uint64_t ah = desc_mnmajor_sw128(a + ks * 2048, 8192, 1024);
+      const uint64_t al = desc_mnmajor_sw128(a + kABytes + ks * 2048, 8192, 1024);
+      mma_bf16(tmem, ah, bh, idesc, acc);
+      mma_bf16(tmem, al, bh, idesc, 1u);
+      if (kSplit) mma_bf16(tmem, ah, desc_mnmajor_sw128(b_lo + s * 2048, gen_box_bytes(), 1024), idesc, 1u);
+    } else {
+      // 8 columns (16 bf16 of K) per step; parts 32 columns apart
+      const uint32_t ah = a_col + (uint32_t)ks * 8u;
+      mma_bf16_ta(tmem, ah, bh, idesc, acc);
+      mma_bf16_ta(tmem, ah + 32u, bh, idesc, 1u);
+      if (kSplit) {
+        mma_bf16_ta(tmem, ah + 64u, bh, idesc, 1u);
+        mma_bf16_ta(tmem, ah, desc_mnmajor_sw128(b_lo + s * 2048, gen_box_bytes(), 1024), idesc, 1u);
+      }
+    }
+  }
+}
+
+template <int kMode, bool kSplit>
+__global__ void __launch_bounds__(kThreadsGen, 1) tc_gen_kernel(const __grid_constant__ TcParams P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = align1024(smem_raw);
+  __shared__ uint64_t a_full[kASlots], a_empty[kASlots], b_full[kMaxBStages], b_empty[kMaxBStages], tfull[2],
+      tempty[2];
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the inverse holds its table slots in tensor memory beside the two
+  // accumulators; the forward's slots are in shared memory
+  constexpr bool kTA = kMode == kInv;
+  const uint32_t acc_cols = kTA ? kTmemAccStride : (uint32_t)tmem_cols_for(P.Nmax);
+  const uint32_t ncols = kTA ? 512u : 2 * acc_cols;
+  const uint32_t bsb = gen_stage_bytes(kSplit, P.Nmax);
+  const int SB = P.stages;
+  unsigned char *abase = base;
+  unsigned char *bbase = base + (kTA ? 0u : kASlots * kASlotBytes);
+
+  if (warp == 2) tmem_alloc(&tmem_slot, ncols);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kASlots; s++) {
+      mbar_init(&a_full[s], 8);  // the 8 generator warps
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < SB; s++) {
+      mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_fence_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer of the data stages
+    for (int s = 0; s < P.nseg; s++) tma_prefetch_desc(&P.maps[s].b_hi);
+    uint32_t g = 0;
+    for (TileWalk<kMode> w(P); w.more(P);) {
+      const TileInfo ti = w.take(P);
+      const int nh = gen_halves<kMode>(P, ti);
+      const uint32_t tx = gen_stage_bytes(kSplit, ti.Nt);
+      for (int h = 0; h < nh; h++, g++) {
+        const int s = (int)(g % (uint32_t)SB);
+        const uint32_t use = g / (uint32_t)SB;
+        if (use > 0) mbar_wait(&b_empty[s], (use - 1) & 1, P.err);
+        mbar_arrive_expect_tx(&b_full[s], tx);
+        gen_load_half<kMode, kSplit>(bbase + (size_t)s * bsb, ti, h, P.Nmax, P.maps[ti.s], &b_full[s]);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    uint32_t ga = 0, gb = 0, it = 0;
+    for (TileWalk<kMode> w(P); w.more(P); it++) {
+      const TileInfo ti = w.take(P);
+      uint32_t idesc = idesc_bf16_f32(kRows, ti.Nt, true);
+      if (kMode == kFwd) idesc |= 1u << 15;  // the generated forward table enters MN-major
+      const int acc = (int)(it & 1);
+      const uint32_t use_a = it >> 1;
+      if (use_a > 0) mbar_wait(&tempty[acc], (use_a - 1) & 1, P.err);
+      tc_fence_after();
+      const uint32_t tacc = tmem + (uint32_t)acc * acc_cols;
+      const int nh = gen_halves<kMode>(P, ti);
+      for (int c = 0; c < (nh + kBPerA - 1) / kBPerA; c++, ga++) {
+        const int sa = (int)(ga % kASlots);
+        mbar_wait(&a_full[sa], (ga / kASlots) & 1, P.err);
+        tc_fence_after();
+        for (int hh = 0; hh < kBPerA && kBPerA * c + hh < nh; hh++, gb++) {
+          const int sb = (int)(gb % (uint32_t)SB);
+          mbar_wait(&b_full[sb], (gb / (uint32_t)SB) & 1, P.err);
+          tc_fence_after();
+          gen_issue_half<kMode, kSplit>(abase + (size_t)sa * kASlotBytes, tmem + a_tmem_col(sa), hh,
+                                        bbase + (size_t)sb * bsb, P.Nmax, tacc, idesc, c == 0 && hh == 0);
+          mma_commit(&b_empty[sb]);
+        }
+        mma_commit(&a_empty[sa]);
+      }
+      if (nh > 0)
+        mma_commit(&tfull[acc]);
+      else
+        mbar_arrive(&tfull[acc]);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // epilogue (4 KB of staging per buffer and warp, 1024-aligned)
+    const int q4 = warp - 4;
+    unsigned char *stg = base + P.epi_off + q4 * 4096 * P.epi_nbuf;
+    uint32_t it = 0;
+    for (TileWalk<kMode> w(P); w.more(P); it++) {
+      const TileInfo ti = w.take(P);
+      const int acc = (int)(it & 1);
+      mbar_wait(&tfull[acc], (it >> 1) & 1, P.err);
+      tc_fence_after();
+      epilogue<kMode>(P, ti, tmem + (uint32_t)acc * acc_cols, q4, lane, gen_halves<kMode>(P, ti) == 0, stg,
+                      P.epi_nbuf);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+    if (lane == 0) bulk_wait<0>();
+  } else if (warp >= 8) {
+    // table generators.  Shared memory after the data ring: the current
+    // tile's two-step coefficients (the next tile's are loaded into
+    // registers meanwhile) and x^2 of every problem's latitudes.  Each
+    // thread's seeds are loaded two table chunks ahead.
+    const int gtid = threadIdx.x - 256;
+    float4 *cs = reinterpret_cast<float4 *>(bbase + (size_t)SB * bsb);
+    float2 *xs = reinterpret_cast<float2 *>(cs + P.ncmax);
+    for (int s = 0; s < P.nseg; s++)
+      for (int k = gtid; k < P.seg[s].Kh; k += 256)
+        xs[P.seg[s].xoff + k] = make_float2(__ldg(P.seg[s].x2h + k), __ldg(P.seg[s].x2l + k));
+    // seed cursor over the same chunk sequence
+    TileWalk<kMode> pw(P);
+    TileInfo pti{};
+    int pkc = 0, pnk = 0;
+    auto next_seed = [&]() {
+      while (pkc >= pnk && pw.more(P)) {
+        pti = pw.take(P);
+        pkc = 0;
+        pnk = (gen_halves<kMode>(P, pti) + kBPerA - 1) / kBPerA;
+      }
+      if (pkc >= pnk) return make_float2(0.f, 0.f);
+      return gen_seed<kMode>(P.seg[pti.s], pti, pkc++, gtid);
+    };
+    float2 sd0 = next_seed(), sd1 = next_seed();
+    auto coef_range = [&](const TileInfo &ti, int &ibase, int &ncoef) {
+      // forward: the tile's 128 rows (+ 4 past its end), inverse: every row
+      ibase = kMode == kFwd ? ti.r0 : 0;
+      ncoef = kMode == kFwd ? 2 * kKc + 4 : kKc * ((gen_halves<kMode>(P, ti) + kBPerA - 1) / kBPerA) + 4;
+    };
+    // coefficients of the next tile with chunks (cursor cw) into registers
+    TileWalk<kMode> cw(P);
+    auto coef_load = [&](float4 (&cr)[kCoefPerThread]) {
+#pragma unroll
+      for (int u = 0; u < kCoefPerThread; u++) cr[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      TileInfo ti{};
+      bool got = false;
+      while (!got && cw.more(P)) {
+        ti = cw.take(P);
+        got = gen_halves<kMode>(P, ti) > 0;
+      }
+      if (!got) return;
+      const SegArgs &sg = P.seg[ti.s];
+      int ibase, ncoef;
+      coef_range(ti, ibase, ncoef);
+      const float4 *src = sg.coef + (int64_t)(ti.m * 2 + ti.p) * sg.ldC;
+#pragma unroll
+      for (int u = 0; u < kCoefPerThread; u++) {
+        const int e = gtid + 256 * u;
+        if (e < ncoef && ibase + e < sg.ldC) cr[u] = __ldg(src + ibase + e);
+      }
+    };
+    float4 creg[kCoefPerThread];
+    coef_load(creg);
+    uint32_t ga = 0;
+    for (TileWalk<kMode> w(P); w.more(P);) {
+      const TileInfo ti = w.take(P);
+      const int nka = (gen_halves<kMode>(P, ti) + kBPerA - 1) / kBPerA;
+      if (nka == 0) continue;
+      const SegArgs &sg = P.seg[ti.s];
+      int ibase, ncoef;
+      coef_range(ti, ibase, ncoef);
+      asm volatile("bar.sync 2, 256;" ::: "memory");  // previous tile's coefficients no longer read
+#pragma unroll
+      for (int u = 0; u < kCoefPerThread; u++) {
+        const int e = gtid + 256 * u;
+        if (e < ncoef) cs[e] = creg[u];
+      }
+      asm volatile("bar.sync 2, 256;" ::: "memory");  // also orders the x^2 stores of the first tile
+      coef_load(creg);
+      for (int kc = 0; kc < nka; kc++, ga++) {
+        const int sa = (int)(ga % kASlots);
+        const uint32_t use = ga / kASlots;
+        const float2 sd = sd0;
+        sd0 = sd1;
+        sd1 = next_seed();
+        int kp, j;
+        gen_coords<kMode>(ti, kc, gtid, kp, j);
+        const float2 x2 = kp < sg.Kh ? xs[sg.xoff + kp] : make_float2(0.f, 0.f);
+        if (use > 0) mbar_wait(&a_empty[sa], (use - 1) & 1, P.err);
+        if (kTA) tc_fence_after();
+        // the thread's 32 rows in two halves of 16
+        float pa = sd.x, pb = sd.y;
+        const float4 *cf = cs + (kSeedRows * j + 1 - ibase);
+#pragma unroll 1
+        for (int hf = 0; hf < 2; hf++) {
+          uint32_t h[8], lw[8], l2[8];
+          recur_rows<kTA && kSplit, 8>(pa, pb, x2, cf + 16 * hf, h, lw, l2);
+          if constexpr (kTA) {
+            // rows i = 64 kc + 32 (g / 128) + 16 hf + 0 .. 15 of lane
+            // k' - r0 (this warp's quarter of the 128 lanes): 8 columns per part
+            const uint32_t t = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a_tmem_col(sa) +
+                               16u * (uint32_t)(gtid >> 7) + 8u * (uint32_t)hf;
+            tmem_st8(t, h);
+            tmem_st8(t + 32u, lw);
+            if (kSplit) tmem_st8(t + 64u, l2);
+          } else {
+            unsigned char *st = abase + (size_t)sa * kASlotBytes;
+            store_rows_smem(gtid, hf, st, st + kABytes, h, lw);
+          }
+        }
+        if constexpr (kTA) {
+          tmem_wait_st();
+          tc_fence_before();
+        } else {
+          fence_proxy_async_smem();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[sa]);
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -1077,8 +1296,9 @@ __global__ void __launch_bounds__(256) rows_transpose_kernel(const __grid_consta
     finalize_tile(a, mt, lg, bt, T);
 }
 
-// FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and
-// transposed layout [(m, p, k')][Ip64]); same recurrence as the FP32 table.
+// FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and,
+// when ihi is given, transposed layout [(m, p, k')][Ip64]); same recurrence
+// as the FP32 table.
 __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bfloat16 *__restrict__ flo,
                                       __nv_bfloat16 *__restrict__ ihi, __nv_bfloat16 *__restrict__ ilo,
                                       const int *__restrict__ roff, int Kp64, int Ip64, const double *__restrict__ xk,
@@ -1094,11 +1314,11 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
     const __nv_bfloat16 h = __double2bfloat16(v);
     const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(h));
     const int64_t fo = (int64_t)(roff[2 * m + p] + i) * Kp64 + k;
-    const int64_t io = ((int64_t)(m * 2 + p) * Kh + k) * Ip64 + i;
     fhi[fo] = h;
-    ihi[io] = h;
-    if (flo) {
-      flo[fo] = lo;
+    flo[fo] = lo;
+    if (ihi) {
+      const int64_t io = ((int64_t)(m * 2 + p) * Kh + k) * Ip64 + i;
+      ihi[io] = h;
       ilo[io] = lo;
     }
   };
@@ -1119,9 +1339,13 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
 }
 
 // FP64 recurrence seeds (one thread per (m, k')): at the first row l0 of
-// every 32-row block of both parities, store Phat_{l0} and Phat_{l0+2} as
-// FP32 mantissas of a common power of two.
-__global__ void seed_gen_kernel(Seed *__restrict__ seeds, int NB, const double *__restrict__ xk,
+// every 32-row block of both parities, Phat_{l0} and Phat_{l0+2} rounded to
+// FP32 (zero below the FP32 normal range).
+__device__ __forceinline__ float seed_f32(double v) {
+  return fabs(v) < 1.1754943508222875e-38 ? 0.f : (float)v;
+}
+
+__global__ void seed_gen_kernel(float2 *__restrict__ seeds, int NB, const double *__restrict__ xk,
                                 const double *__restrict__ sk, const double *__restrict__ a,
                                 const double *__restrict__ bcoef, const double *__restrict__ seedf, int L, int M,
                                 int Kh) {
@@ -1145,17 +1369,8 @@ __global__ void seed_gen_kernel(Seed *__restrict__ seeds, int NB, const double *
   }
   for (int l = m; l < L; l++) {
     const int d = l - m, p = d & 1, i = d >> 1;
-    if ((i % kSeedRows) == 0) {
-      Seed sd{0.f, 0.f, kZeroBlock, 0};
-      const double mx = fmax(fabs(w[0]), fabs(w[2]));
-      if (mx > 0.0) {
-        const int e = ilogb(mx);
-        sd.s0 = (float)scalbn(w[0], -e);
-        sd.s1 = (float)scalbn(w[2], -e);
-        sd.e = e;
-      }
-      seeds[((int64_t)(m * 2 + p) * NB + i / kSeedRows) * Kh + k] = sd;
-    }
+    if ((i % kSeedRows) == 0)
+      seeds[((int64_t)(m * 2 + p) * NB + i / kSeedRows) * Kh + k] = make_float2(seed_f32(w[0]), seed_f32(w[2]));
     double nn = 0.0;
     if (l + 4 < L) {
       const int64_t ci = (int64_t)(l + 4) * M + m;
@@ -1199,60 +1414,100 @@ cudaError_t start_persistent(unsigned grid, size_t smem, const TcParams &P, cuda
 // the generators' area; at most 227 KB with the static barriers.
 constexpr size_t kSmemLimit = 227 * 1024 - 256;
 
-// Shared memory beyond the stage ring (the generators' area); fills the
-// generators' layout fields of P.  SIZE_MAX when the problems cannot be
-// served.
+// Shared memory of tc_persistent_kernel beyond its stage ring: the
+// epilogue staging.
 template <int kMode>
-size_t extra_smem(bool gen, TcParams &P) {
-  size_t cbytes = 0;
-  if (gen && kMode != kFilt) {
-    // generator shared memory: coefficients of one tile, x^2 of every
-    // problem's latitudes, the seed ring
-    int rows_max = 0;
-    P.xtot = 0;
-    for (int s = 0; s < P.nseg; s++) {
-      rows_max = std::max(rows_max, leg_rows(P.seg[s].L, 0, 0));
-      P.seg[s].xoff = P.xtot;
-      P.xtot += P.seg[s].Kh;
-    }
-    P.ncmax = std::max(2 * kKc + 4, kKc * ((rows_max + kKc - 1) / kKc) + 4);
-    if (P.ncmax > 256 * kCoefPerThread) return SIZE_MAX;
-    cbytes = sizeof(float4) * (size_t)P.ncmax + sizeof(float2) * (size_t)((P.xtot + 1) & ~1) +
-             sizeof(Seed) * 256 * kSeedAhead;
-  }
-  cbytes = (cbytes + 1023) / 1024 * 1024;
-  cbytes += kMode != kFilt ? 4 * 8192 : 4 * 4096;  // epilogue staging
-  return cbytes;
+size_t extra_smem() {
+  return kMode != kFilt ? 4 * 8192 : 4 * 4096;
 }
 
-// Whether two pipeline stages and the extra areas fit one CTA.
+// Shared memory of tc_gen_kernel beyond the table slots and the data ring,
+// without the epilogue staging: the coefficients of one tile and x^2 of
+// every problem's latitudes (whole KB); fills the generators' layout fields
+// of P.  SIZE_MAX when the problems cannot be served.
+size_t gen_extra_smem(TcParams &P) {
+  int rows_max = 0;
+  P.xtot = 0;
+  for (int s = 0; s < P.nseg; s++) {
+    rows_max = std::max(rows_max, leg_rows(P.seg[s].L, 0, 0));
+    P.seg[s].xoff = P.xtot;
+    P.xtot += P.seg[s].Kh;
+  }
+  P.ncmax = std::max(2 * kKc + 4, kKc * ((rows_max + kKc - 1) / kKc) + 4);
+  if (P.ncmax > 256 * kCoefPerThread) return SIZE_MAX;
+  size_t cbytes = sizeof(float4) * (size_t)P.ncmax + sizeof(float2) * (size_t)((P.xtot + 1) & ~1);
+  return (cbytes + 1023) / 1024 * 1024;
+}
+
+// Whether the launch fits one CTA: two pipeline stages and the extra areas
+// (streamed table and filter), or the two table slots, two data stages and
+// the generators' areas (generated table).
 template <int kMode>
 bool persistent_fits(bool split, bool gen, TcParams &P) {
-  const size_t extra = extra_smem<kMode>(gen, P);
-  return extra != SIZE_MAX && 1024 + 2 * (size_t)stage_bytes(kMode, split, P.Nmax) + extra <= kSmemLimit;
+  if (gen && kMode != kFilt) {
+    const size_t extra = gen_extra_smem(P);
+    const size_t aslots = kMode == kInv ? 0 : kASlots * (size_t)kASlotBytes;
+    if (kMode == kInv && P.Nmax > kTmemMaxN) return false;
+    return extra != SIZE_MAX &&
+           1024 + aslots + 2 * (size_t)gen_stage_bytes(split, P.Nmax) + extra + 4 * 4096 <= kSmemLimit;
+  }
+  return 1024 + 2 * (size_t)stage_bytes(kMode, split, P.Nmax) + extra_smem<kMode>() <= kSmemLimit;
+}
+
+template <bool kSplit>
+cudaError_t start_gen(int mode, unsigned grid, size_t smem, const TcParams &P, cudaStream_t st) {
+  auto fn = mode == kFwd ? tc_gen_kernel<kFwd, kSplit> : tc_gen_kernel<kInv, kSplit>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, kThreadsGen, smem, st>>>(P);
+  return cudaSuccess;
 }
 
 template <int kMode>
 cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch &cfg, cudaStream_t st) {
   if (P.ntiles <= 0) return cudaSuccess;
-  const size_t sb = stage_bytes(kMode, split, P.Nmax);
-  const size_t extra = extra_smem<kMode>(gen, P);
-  if (extra == SIZE_MAX || 1024 + 2 * sb + extra > kSmemLimit) return cudaErrorInvalidValue;
-  int stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 1024 - extra) / sb);
-  if (cfg.stages >= 2) stages = std::min(stages, cfg.stages);
-  P.stages = stages;
-  // the inverse's staging follows the generators' area (stage sizes and the
-  // generators' area are multiples of 1024 bytes)
-  P.epi_off = (int)((size_t)stages * sb + extra - (kMode != kFilt ? 4 * 8192 : 4 * 4096));
-  const size_t smem = 1024 + (size_t)stages * sb + extra;
   const unsigned grid = (unsigned)std::min(P.ntiles, cfg.grid > 0 ? cfg.grid : sm_count());
   cudaError_t e;
-  if (gen) {
-    e = split ? start_persistent<kMode, true, true>(grid, smem, P, st)
-              : start_persistent<kMode, false, true>(grid, smem, P, st);
+  if (gen && kMode != kFilt) {
+    const size_t sb = gen_stage_bytes(split, P.Nmax);
+    const size_t extra = gen_extra_smem(P);
+    if (extra == SIZE_MAX || (kMode == kInv && P.Nmax > kTmemMaxN)) return cudaErrorInvalidValue;
+    // the forward's table slots are in shared memory, the inverse's in
+    // tensor memory; two staging buffers per epilogue warp unless that
+    // leaves fewer than four data stages, then one
+    const size_t aslots = kMode == kInv ? 0 : kASlots * (size_t)kASlotBytes;
+    size_t fixed = 1024 + aslots + extra;
+    P.epi_nbuf = fixed + 4 * 8192 + 4 * sb <= kSmemLimit ? 2 : 1;
+    fixed += 4 * 4096 * (size_t)P.epi_nbuf;
+    if (fixed + 2 * sb > kSmemLimit) return cudaErrorInvalidValue;
+    int stages = (int)std::min<size_t>(kMaxBStages, (kSmemLimit - fixed) / sb);
+    if (cfg.stages >= 2) stages = std::min(stages, cfg.stages);
+    P.stages = stages;
+    // the epilogue staging follows the generators' area (all parts are whole KB)
+    P.epi_off = (int)(aslots + (size_t)stages * sb + extra);
+    const size_t smem = fixed + (size_t)stages * sb;
+    e = split ? start_gen<true>(kMode, grid, smem, P, st) : start_gen<false>(kMode, grid, smem, P, st);
   } else {
-    e = split ? start_persistent<kMode, true, false>(grid, smem, P, st)
-              : start_persistent<kMode, false, false>(grid, smem, P, st);
+    const size_t sb = stage_bytes(kMode, split, P.Nmax);
+    const size_t extra = extra_smem<kMode>();
+    if (1024 + 2 * sb + extra > kSmemLimit) return cudaErrorInvalidValue;
+    int stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - 1024 - extra) / sb);
+    if (cfg.stages >= 2) stages = std::min(stages, cfg.stages);
+    P.stages = stages;
+    // the epilogue staging follows the stage ring (stages are whole KB)
+    P.epi_off = (int)((size_t)stages * sb);
+    const size_t smem = 1024 + (size_t)stages * sb + extra;
+    if constexpr (kMode == kFilt) {
+      if (gen)
+        e = split ? start_persistent<kFilt, true, true>(grid, smem, P, st)
+                  : start_persistent<kFilt, false, true>(grid, smem, P, st);
+      else
+        e = split ? start_persistent<kFilt, true, false>(grid, smem, P, st)
+                  : start_persistent<kFilt, false, false>(grid, smem, P, st);
+    } else {
+      e = split ? start_persistent<kMode, true, false>(grid, smem, P, st)
+                : start_persistent<kMode, false, false>(grid, smem, P, st);
+    }
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1332,7 +1587,8 @@ bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh) {
+bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh,
+                         int box_rows) {
   auto enc = encoder();
   if (!enc) return false;
   if (!ptr) {
@@ -1342,7 +1598,8 @@ bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLa
   if (fl.cg || fl.sm != 2 * fl.sp) return false;  // rows (2m + p) at stride sp
   cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)nmp, (cuuint64_t)Kh};
   cuuint64_t gstr[2] = {(cuuint64_t)fl.sp * 2, (cuuint64_t)fl.sk * 2};
-  cuuint32_t box[3] = {64, 1, 64};
+  if (box_rows != 64 && box_rows != 32) return false;
+  cuuint32_t box[3] = {64, 1, (cuuint32_t)box_rows};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1350,19 +1607,20 @@ bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLa
 }
 
 bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int M, int L, bool load,
-                          int box_cols) {
+                          int box_cols, int load_rows) {
   auto enc = encoder();
   if (!enc) return false;
   if (!load && box_cols != 32 && box_cols != 16) return false;
+  if (load && load_rows != 64 && load_rows != 32) return false;
   if (!ptr) {
     *tm = CUtensorMap{};
     return true;
   }
-  // dims (column, m, l); loads: 64 columns x every second l (64 of them),
-  // stores: box_cols columns x 32 m of one l
+  // dims (column, m, l); loads: 64 columns x every second l (load_rows of
+  // them), stores: box_cols columns x 32 m of one l
   cuuint64_t gdim[3] = {(cuuint64_t)ld, (cuuint64_t)M, (cuuint64_t)L};
   cuuint64_t gstr[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * M};
-  cuuint32_t box_l[3] = {64, 1, 128}, box_s[3] = {(cuuint32_t)box_cols, 32, 1};
+  cuuint32_t box_l[3] = {64, 1, 2 * (cuuint32_t)load_rows}, box_s[3] = {(cuuint32_t)box_cols, 32, 1};
   cuuint32_t es_l[3] = {1, 1, 2}, es_s[3] = {1, 1, 1};
   const CUtensorMapSwizzle sw = load ? CU_TENSOR_MAP_SWIZZLE_128B
                                      : (box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -1425,22 +1683,25 @@ cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_b
 cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
                             const double *b, const double *seedf, int L, int M, int Kh, cudaStream_t st) {
   dim3 grid((Kh + 127) / 128, M);
-  seed_gen_kernel<<<grid, 128, 0, st>>>(reinterpret_cast<Seed *>(seeds), NB, xk, sk, a, b, seedf, L, M, Kh);
+  seed_gen_kernel<<<grid, 128, 0, st>>>(reinterpret_cast<float2 *>(seeds), NB, xk, sk, a, b, seedf, L, M, Kh);
   return cudaGetLastError();
 }
 
 cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, const TcLaunch &cfg, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (n > kMaxSeg) return cudaErrorInvalidValue;
-  const bool split = items[0].T->split, gen = items[0].T->gen;
+  const bool split = items[0].T->split;
+  const bool gen = inverse ? items[0].T->gen_inv : items[0].T->gen_fwd;
   for (int i = 0; i < n; i++) {
-    if (items[i].T->split != split || items[i].T->gen != gen) return cudaErrorInvalidValue;
+    if (items[i].T->split != split || (inverse ? items[i].T->gen_inv : items[i].T->gen_fwd) != gen)
+      return cudaErrorInvalidValue;
     if (items[i].Nt < 0 || items[i].Nt % 16 != 0 || items[i].Nt > 256) return cudaErrorInvalidValue;
   }
   // column tiles: the requested widths (or 256), narrowed until two
   // pipeline stages fit in shared memory
   const int caps[4] = {256, 192, 128, 64};
-  for (int cap : caps) {
+  for (int cap0 : caps) {
+    const int cap = (gen && inverse) ? std::min(cap0, kTmemMaxN / 16 * 16) : cap0;
     TcParams P{};
     P.err = items[0].T->err;
     int nseg = 0, ntiles = 0;
@@ -1460,7 +1721,7 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       g.Gw = it.Gw;
       g.ldc = it.ldc;
       g.gpair = T.gpair;
-      g.seeds = reinterpret_cast<const Seed *>(T.seeds);
+      g.seeds = reinterpret_cast<const float2 *>(T.seeds);
       g.coef = T.coef;
       g.x2h = T.x2h;
       g.x2l = T.x2l;
@@ -1470,8 +1731,11 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       if (!inverse) {
         mp.a_hi = T.tab_fwd_hi;
         mp.a_lo = T.tab_fwd_lo;
-        mp.b_hi = T.f_hi;
-        mp.b_lo = split ? T.f_lo : T.f_hi;
+        // data: 64-row boxes for the streamed table's stages, 32-row boxes
+        // for the generated table's data stages
+        const bool box32 = gen && kKb == 32;
+        mp.b_hi = box32 ? T.fh_hi : T.f_hi;
+        mp.b_lo = split ? (box32 ? T.fh_lo : T.f_lo) : mp.b_hi;
         // store maps of the plan's l-major rows (used when the destination
         // is those rows)
         if (!it.rows_hi == !it.rowsf) return cudaErrorInvalidValue;  // exactly one destination
@@ -1484,8 +1748,9 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       } else {
         mp.a_hi = T.tab_inv_hi;
         mp.a_lo = T.tab_inv_lo;
-        mp.b_hi = T.s_hi;
-        mp.b_lo = split ? T.s_lo : T.s_hi;
+        const bool box32 = gen && kKb == 32;
+        mp.b_hi = box32 ? T.sh_hi : T.s_hi;
+        mp.b_lo = split ? (box32 ? T.sh_lo : T.s_lo) : mp.b_hi;
         // the output maps describe the plan's FP32 workspace
         if (it.Gw != T.gw || it.ldc != T.gw_ldc) return cudaErrorInvalidValue;
         mp.o32_hi = T.g32;

@@ -90,6 +90,7 @@ struct TableF32 {
 struct TcPlanView {
   CUtensorMap tab_fwd_hi, tab_fwd_lo, tab_inv_hi, tab_inv_lo;  // bf16 table (streamed)
   CUtensorMap f_hi, f_lo, s_hi, s_lo;  // s: 3-D (column, m, l) loads of every second l
+  CUtensorMap fh_hi, fh_lo, sh_hi, sh_lo;  // the same with 32-row boxes (generated-table kernel)
   CUtensorMap x_hi, x_lo;  // l-major forward output rows [L M][ldx] (bf16)
   CUtensorMap g32, g16;    // FP32 inverse output (folded workspace), store boxes 32 x 32, 16 x 32
   const float *gw;         // their base (the FP32 workspace), row stride and layout
@@ -105,14 +106,14 @@ struct TcPlanView {
   const __nv_bfloat16 *xrows_hi;                    // their base and row stride
   int ldx;
   const int *roff;
-  // on-chip Legendre table: seeds (16 B each) every 32 rows
+  // on-chip Legendre table: FP32 seed pairs (float2) every 32 rows
   const void *seeds;
   const float4 *coef;        // two-step coefficients [(2m + p) ldC + i]
   const float *x2h, *x2l;    // x^2 = x2h + x2l per latitude
   int NB, ldC;
   int L, M, Kh;
   bool split;
-  bool gen;  // generate the table on chip instead of streaming it
+  bool gen_fwd, gen_inv;  // generate the table on chip (per direction) instead of streaming it
   unsigned *err;
 };
 
@@ -128,8 +129,9 @@ bool tc_encode_2d(CUtensorMap *tm, const void *ptr, int64_t cols, int64_t rows, 
 bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int ld, int nmp, int Kh,
                         int box_cols);
 // bf16 folded rows (layout fl, row length ld) as a 3-D map (column, 2m + p,
-// k') with load boxes 64 x 1 x 64 (128-byte swizzle).
-bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh);
+// k') with load boxes 64 x 1 x box_rows (box_rows 64 or 32; 128-byte swizzle).
+bool tc_encode_fold_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, const FoldLayout &fl, int ld, int nmp, int Kh,
+                         int box_rows);
 // bf16 l-major rows [L][M][ldx] as a 3-D map whose store boxes take box_cols
 // columns of 32 rows l, l + 2, ..., l + 62 (element stride 2 along l).
 bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_cols);
@@ -137,18 +139,20 @@ bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, in
 // 16-column boxes, 128- or 64-byte swizzle).
 bool tc_encode_lrows_f32(CUtensorMap *tm, const float *ptr, int ldr, int M, int L, int box_cols);
 // The internal coefficient rows S [L][M][ld] (bf16, l-major) as a 3-D map
-// (column, m, l): load = true: boxes of 64 columns x every second l (64 of
-// them, 128-byte swizzle) for the inverse contraction; load = false: store
-// boxes of box_cols columns x 32 m of one l (the filter's epilogue).
+// (column, m, l): load = true: boxes of 64 columns x every second l
+// (load_rows = 64 or 32 of them, 128-byte swizzle) for the inverse
+// contraction; load = false: store boxes of box_cols columns x 32 m of one
+// l (the filter's epilogue).
 bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int M, int L, bool load,
-                          int box_cols);
+                          int box_cols, int load_rows = 64);
 // FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64],
-// transposed layout [(2m + p) Kh + k'][Ip64]).
+// transposed layout [(2m + p) Kh + k'][Ip64]; ihi / ilo NULL: forward only).
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
                                   const int *roff, int Kp64, int Ip64, const double *xk, const double *sk,
                                   const double *a, const double *b, const double *seed, int L, int M, int Kh,
                                   cudaStream_t st);
-// FP64 seeds of the on-chip Legendre table (every 32 rows of every (m, p)).
+// Seeds of the on-chip Legendre table (every 32 rows of every (m, p)),
+// computed in FP64 and stored as FP32 pairs.
 cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
                             const double *b, const double *seedf, int L, int M, int Kh, cudaStream_t st);
 // Tensor-core filter from the l-major rows to the inverse's split rows.
@@ -266,6 +270,15 @@ constexpr int kMaxFftGroup = 8;
 cudaError_t launch_r2c45_grouped(const Fft45Item *items, int n, bool bf16, cudaStream_t st);
 cudaError_t launch_c2r45_grouped(const Fft45Item *items, int n, cudaStream_t st);
 
+// Longitude transforms of arbitrary latitude rows (distributed transform):
+// F[r][m] = ring_scale[k0 + r mod nrows] sum_j x[r][j] e^{-2 pi i j m / nlon}
+// for rows r < R, m < M; and y[r][j] = sum_m c_m Re(G[r][m] e^{2 pi i j m /
+// nlon}).  Generic mixed-radix FFT (nlon factoring into 2, 3, 5).
+cudaError_t launch_r2c_rows(const float *x, float2 *F, int64_t R, int nrows, int k0, int nlon, int M,
+                            const float2 *twiddle, const RadixPlan &rp, const float *ring_scale, cudaStream_t st);
+cudaError_t launch_c2r_rows(const float2 *G, float *y, int64_t R, int nlon, int M, const float2 *twiddle,
+                            const RadixPlan &rp, cudaStream_t st);
+
 // Longitude synthesis from folded Gw[m][p][k'][ldc]:
 //   u_kj = ring_scale[k] * sum_m c_m Re(G_k(m) e^{2 pi i j m / nlon})
 // with G_k = G_even + G_odd (north row k'), G_kbar = G_even - G_odd.
@@ -364,7 +377,7 @@ struct sht_plan_s {
   unsigned *d_err = nullptr;   // error word of bounded device waits
   shtgb::TcPlanView tc{};      // tensor-core view (bf16 precisions)
   __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;  // bf16 tables
-  int table_source = 0;        // 0: streamed bf16 table, 1: on-chip recurrence
+  int table_source = 0;        // 0: streamed bf16 table, 1: on-chip recurrence, 2: forward streamed, inverse on chip
   void *d_seeds = nullptr;     // recurrence seeds of the on-chip table
   float4 *d_coef = nullptr;    // two-step recurrence coefficients [(2m + p) ldC + i]
   float *d_x2h = nullptr, *d_x2l = nullptr;  // squared latitudes as FP32 hi + lo
@@ -387,6 +400,7 @@ struct sht_plan_s {
   int n_fwd_tiles = 0;
   shtgb::LegTile *d_inv_tiles = nullptr;
   int n_inv_tiles = 0;
+  std::vector<int> fwd_tile_m, inv_tile_m;  // first tile of each order m (M + 1 entries)
   float *d_work = nullptr;    // folded Fourier workspace [M][2][Kh][ldc]
   float2 *d_spec_a = nullptr;  // [max_batch][L][M] spectral buffer
   float2 *d_spec_b = nullptr;  // [max_batch][L][M] spectral buffer
