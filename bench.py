@@ -19,6 +19,9 @@ the dominant kernel.
   python bench.py --workload scores ...  # angular power spectrum + spectral
                                          # CRPS of a 16-member x 72-channel
                                          # ensemble of 720 x 720 coefficients
+  python bench.py --workload block_grad ... # the block's training step at
+                                         # 360x720 Gauss, 4 x 256 channels:
+                                         # forward, input and weight gradients
 
 Multi-GPU runs (torchrun) are independent replicas: the path has no
 exchange step, so every rank transforms its own batch (weak scaling).
@@ -70,6 +73,28 @@ NOISE_E = 16
 NOISE_METRIC = ("spherical diffusion noise fields/s at 721x1440, lmax=720 (16 members x 8 length scales, "
                 "step + inverse SHT); roofline fraction")
 NOISE_UNIT = "noise fields/s"
+
+
+# training-step workload of the spectral block (the differentiation
+# configuration): 360 x 720 Gaussian grid, lmax = mmax = 360, 4 members x
+# 256 channels, W[360][256][256]; one step = forward block, the input
+# gradient (the adjoint block) and the weight gradient
+GRAD_NLAT, GRAD_NLON, GRAD_GRID, GRAD_L = 360, 720, "gauss", 360
+GRAD_MEMBERS, GRAD_CHANNELS = 4, 256
+GRAD_METRIC = ("spectral-block training field-transforms/s (forward + input and weight gradients) at 360x720 "
+               "Gauss, lmax=360, 4 members x 256 channels; roofline fraction")
+
+
+def grad_config(precision: str) -> dict:
+    return {
+        "workload": "spectral block forward + input gradient (adjoint block) + weight gradient, 360x720 Gauss, "
+                    "lmax=mmax=360, 4 members x 256 channels, W[360][256][256] complex",
+        "nlat": GRAD_NLAT, "nlon": GRAD_NLON, "grid": GRAD_GRID, "lmax": GRAD_L, "mmax": GRAD_L,
+        "members": GRAD_MEMBERS, "channels": GRAD_CHANNELS, "precision": precision,
+        "spectrum": "(l+1)^-3 angular power, seeded; cotangent: the block output",
+        "l2": "inputs larger than L2: 1.06 GB of fields in per step",
+        "parallelism": "replicas",
+    }
 
 
 def noise_config(precision: str) -> dict:
@@ -137,10 +162,12 @@ def n_triangle(L, M):
     return sum(L - m for m in range(M))
 
 
-def algorithmic_bytes(kernel: str, fields: int, members: int, cin: int, cout: int) -> float:
-    tri = n_triangle(LMAX, MMAX) * 8.0          # complex64 l >= m coefficients of one field
-    four = NLAT * MMAX * 8.0                      # complex64 Fourier rows of one field
-    grid = NLAT * NLON * 4.0                      # float32 field
+def algorithmic_bytes(kernel: str, fields: int, members: int, cin: int, cout: int, shape=None) -> float:
+    nlat, nlon, L, M = shape if shape else (NLAT, NLON, LMAX, MMAX)
+    tri = n_triangle(L, M) * 8.0                  # complex64 l >= m coefficients of one field
+    four = nlat * M * 8.0                         # complex64 Fourier rows of one field
+    grid = nlat * nlon * 4.0                      # float32 field
+    LMAX_, MMAX_ = L, M
     if kernel == "r2c":
         return fields * (grid + four)
     if kernel == "c2r":
@@ -148,10 +175,20 @@ def algorithmic_bytes(kernel: str, fields: int, members: int, cin: int, cout: in
     if kernel in ("leg_fwd", "leg_inv"):
         return fields * (four + tri)
     if kernel == "filter":
-        return members * (cin + cout) * tri + LMAX * cout * cin * 8.0
+        return members * (cin + cout) * tri + LMAX_ * cout * cin * 8.0
     if kernel == "filter_prep":
-        return LMAX * cout * cin * 8.0
+        return LMAX_ * cout * cin * 8.0
+    if kernel == "filter_dw":
+        return members * (cin + cout) * tri + LMAX_ * cout * cin * 8.0
+    if kernel == "finalize":
+        return fields * (tri + L * M * 8.0)  # FP32 rows in, API layout (with zeros) out
     return float("nan")
+
+
+def filter_dw_flops(members: int, cin: int, cout: int, L: int, M: int) -> float:
+    """Real flops of the weight gradient: one complex multiply-add (8 flops)
+    per (member, output, input, l >= m) coefficient."""
+    return 8.0 * members * cin * cout * n_triangle(L, M)
 
 
 def source_hash(paths) -> str:
@@ -177,6 +214,8 @@ def kernel_sources(kernel: str, precision: str):
         "crps": ["paper_2507_12144_gb300/csrc/scores.cu"],
         "diffusion": ["paper_2507_12144_gb300/csrc/diffusion.cu"],
         "psd": ["paper_2507_12144_gb300/csrc/scores.cu"],
+        "disco_fwd": ["paper_2507_12144_gb300/csrc/disco.cu"],
+        "disco_bwd": ["paper_2507_12144_gb300/csrc/disco.cu"],
     }
     return table.get(kernel, [])
 
@@ -472,6 +511,21 @@ def run_reference(args):
         return run_reference_scores(args, world)
     if args.workload == "noise":
         return run_reference_noise(args, world)
+    if args.workload == "block_grad":
+        runs = [cpu_baseline_grad() for _ in range(min(args.warmup + args.steps, 6))]
+        runs = runs[min(args.warmup, len(runs) - 1):]
+        value = statistics.median(r["value"] for r in runs)
+        print(json.dumps({
+            "impl": "reference", "metric": GRAD_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * GRAD_MEMBERS * GRAD_CHANNELS / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": grad_config("fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": runs[0]["cores"], "kind": "oracle",
+                             "sample": runs[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        sys.stdout.flush()
+        barrier(world)
+        return 0
     if args.workload == "disco":
         runs = [cpu_baseline_disco() for _ in range(args.warmup + args.steps)][args.warmup:]
         value = statistics.median(r["value"] for r in runs)
@@ -740,6 +794,180 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def run_gpu_block_grad(args):
+    """Training step of the spectral block through the C ABI: y =
+    sht_spectral_block(x, W), gx = sht_spectral_block_adjoint(gy, W), and
+    gW = spectral_filter_adjoint(ISHT^T(gy), W, SHT(x)) (xhat recomputed)."""
+    world, rank, local = dist_setup(args.gpus)
+    import torch
+
+    import paper_2507_12144_gb300 as shtgb
+    from paper_2507_12144_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    Bm, C, L = GRAD_MEMBERS, GRAD_CHANNELS, GRAD_L
+    fields = Bm * C
+    plan = shtgb.Plan(GRAD_NLAT, GRAD_NLON, GRAD_GRID, L, L, precision=args.precision, device=dev,
+                      max_batch=fields, max_channels=C, table_source=args.table_source)
+    c = inputs.spectral_coeffs(4 + rank, (fields,), L, L)
+    x = shtgb.sht_inverse(plan, torch.from_numpy(c.astype(np.complex64)).to(dev))
+    x = x.reshape(Bm, C, GRAD_NLAT, GRAD_NLON).contiguous()
+    W = torch.from_numpy(inputs.filter_weights(5, L, C, C).astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    gx = torch.empty_like(x)
+    gyhat = torch.empty((Bm, C, L, L), dtype=torch.complex64, device=dev)
+    xhat = torch.empty_like(gyhat)
+    gW = torch.empty_like(W)
+    lib = shtgb._abi.lib()
+    P = shtgb._ptr
+    stream = torch.cuda.current_stream(dev)
+    st = shtgb._stream(x)
+    check = shtgb._abi.check
+
+    def step(gy):
+        check(lib.sht_spectral_block(plan.handle, P(x), P(W), P(y), Bm, C, C, st))
+        check(lib.sht_spectral_block_adjoint(plan.handle, P(gy), P(W), P(gx), Bm, C, C, st))
+        check(lib.sht_inverse_adjoint(plan.handle, P(gy), P(gyhat), fields, st))
+        check(lib.sht_forward(plan.handle, P(x), P(xhat), fields, st))
+        check(lib.spectral_filter_adjoint(plan.handle, P(gyhat), P(W), P(xhat), None, P(gW), Bm, C, C, st))
+
+    # the cotangent: the block's own output (a field with the data's spectrum)
+    check(lib.sht_spectral_block(plan.handle, P(x), P(W), P(y), Bm, C, C, st))
+    gy = y.clone()
+    for _ in range(args.warmup):
+        step(gy)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    plan.profile_begin(capacity=64 * (args.steps + 1))
+    plan.profile_collect()
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(gy)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank == 0 else None
+    ms_total = ev0.elapsed_time(ev1)
+    prof = plan.profile_collect()
+    plan.profile_end()
+    plan.check()
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+    value = world * fields / (ms_step * 1e-3)
+    kernels = {k: v for k, v in prof.items() if not k.startswith("_") and v[0] > 0}
+    launches = sum(v[0] for v in kernels.values())
+    breakdown = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0], "share": v[1] / ms_total}
+                 for k, v in kernels.items()}
+    dom = max(kernels, key=lambda k: kernels[k][1])
+    dom_launches, dom_ms = kernels[dom]
+    per_launch_s = dom_ms / dom_launches * 1e-3
+    shape = (GRAD_NLAT, GRAD_NLON, L, L)
+    if dom == "filter_dw":
+        flops = filter_dw_flops(Bm, C, C, L, L)
+        achieved = flops / per_launch_s / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
+                    "peak_source": "FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops x 2070 MHz)",
+                    "traffic": None, "algorithmic_flops_per_launch": flops,
+                    "kernel_ms_per_launch": per_launch_s * 1e3, "share_of_step": dom_ms / ms_total}
+    else:
+        # per launch: the kernel's launches process different batches
+        # (blocks of Bm members, API calls of all fields), all of the same size
+        alg = algorithmic_bytes(dom, fields, Bm, C, C, shape)
+        achieved = alg / per_launch_s / 1e9
+        peak, peak_kind = load_peaks()
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth", "traffic": None,
+                    "algorithmic_bytes_per_launch": alg, "kernel_ms_per_launch": per_launch_s * 1e3,
+                    "share_of_step": dom_ms / ms_total}
+
+    # end to end: x and gy in from pinned host memory, gx and gW back, every step
+    e2e_steps = max(2, min(args.steps, 5))
+    hx = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    hg = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    hgx = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+    hgW = torch.empty(W.shape, dtype=torch.complex64, pin_memory=True)
+    hx.copy_(x)
+    hg.copy_(gy)
+    dgy = torch.empty_like(gy)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(hx, non_blocking=True)
+        dgy.copy_(hg, non_blocking=True)
+        step(dgy)
+        hgx.copy_(gx, non_blocking=True)
+        hgW.copy_(gW, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    if rank == 0:
+        line = {
+            "metric": GRAD_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+            "data": "synthetic: seeded (l+1)^-3 spectra synthesised on the GPU, random-init filter",
+            "config": grad_config(args.precision), "roofline": roofline, "kernels": breakdown,
+            "gpu_launches": launches,
+            "e2e": {"value": world * fields * e2e_steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * x.numel() * 4),
+                    "d2h_bytes_per_step": int(x.numel() * 4 + W.numel() * 8), "steps": e2e_steps,
+                    "path": "the step's five C-ABI calls, x and gy copied in, gx and gW copied out"},
+            "clocks": clk,
+            "cpu_baseline": cpu_baseline_grad() if world == 1 and not args.no_cpu_baseline else None,
+        }
+        print(json.dumps(line))
+        sys.stdout.flush()
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_grad(target_s: float = 12.0) -> dict:
+    """The FP64 oracle on a slab of the training step: the transforms of one
+    field on a band of latitude rows (forward, inverse, and each adjoint),
+    and the filter with its adjoint and weight gradient on a band of
+    degrees for one member, scaled to whole fields: a step has per field 3
+    forward-type transforms (SHT, ISHT^T twice), 2 synthesis-type (ISHT,
+    SHT^T), and per member 2 filters and 1 weight gradient."""
+    import oracle
+    from paper_2507_12144_gb300 import inputs
+    nlat, nlon, grid, L = GRAD_NLAT, GRAD_NLON, GRAD_GRID, GRAD_L
+    C = GRAD_CHANNELS
+    u = inputs.spatial_noise(31, (1, nlat, nlon))
+    c = inputs.spectral_coeffs(32, (1,), L, L)
+    k1 = 24
+    t0 = time.perf_counter()
+    oracle.sht_forward_rows(u, nlat, nlon, grid, L, L, 0, k1)
+    oracle.sht_inverse_rows(c, nlat, nlon, grid, L, L, 0, k1)
+    t_tr = time.perf_counter() - t0
+    xh = inputs.spectral_coeffs(33, (1, C), L, L)
+    Wt = inputs.filter_weights(34, L, C, C)
+    l1 = 8
+    t1 = time.perf_counter()
+    oracle.spectral_filter_degrees(xh, Wt, 0, l1)
+    t_f = time.perf_counter() - t1
+    frac_rows = k1 / nlat
+    # degrees 0 .. l1-1 carry n_triangle(l1, l1) of the n_triangle(L, L) coefficients
+    frac_deg = n_triangle(l1, l1) / n_triangle(L, L)
+    per_field_s = (5.0 / 2.0) * t_tr / frac_rows + 3.0 * t_f / frac_deg / C
+    return {"value": 1.0 / per_field_s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one field on latitude rows [0,{k1}) of {nlat} through the forward and inverse transforms "
+                      f"(each adjoint costs as one of them), the filter of one member on degrees [0,{l1}) "
+                      f"(its adjoint and weight gradient cost as one filter each); scaled to a field's share "
+                      f"of the step; {t_tr + t_f:.1f} s"}
 
 
 def run_gpu_batched(args):
@@ -1182,7 +1410,8 @@ def run_gpu_disco(args):
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
                 "peak_source": "FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops x 2070 MHz)",
-                "traffic": None, "algorithmic_flops_per_launch": flops, "kernel_ms_per_launch": kern[dom]}
+                "traffic": measured_traffic(dom, "disco"), "algorithmic_flops_per_launch": flops,
+                "kernel_ms_per_launch": kern[dom]}
     # end to end: fields in from pinned host memory, gradients back, every step
     e2e_steps = 5
     hx = x.cpu().pin_memory()
@@ -1247,10 +1476,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["block", "batched", "scores", "noise", "disco"], default="block",
+    ap.add_argument("--workload", choices=["block", "batched", "scores", "noise", "disco", "block_grad"],
+                    default="block",
                     help="block: SHT -> filter -> ISHT at 721x1440 (the headline); batched: forward + inverse "
                          "SHT of the uneven four-grid mix; scores: angular PSD + spectral CRPS of a "
-                         "16-member ensemble")
+                         "16-member ensemble; block_grad: the block's training step (forward, input and "
+                         "weight gradients) at 360x720 Gauss with 4 x 256 channels")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
     ap.add_argument("--no-fp32-side", action="store_true",
                     help="skip timing the plain FP32 form beside a tensor-core precision")
@@ -1275,6 +1506,8 @@ def main(argv=None):
         return run_gpu_noise(args)
     if args.workload == "disco":
         return run_gpu_disco(args)
+    if args.workload == "block_grad":
+        return run_gpu_block_grad(args)
     return run_gpu(args)
 
 

@@ -215,6 +215,19 @@ sht_status_t sht_spectral_block(sht_plan_t plan, const float *x,
                                 const void *W, float *y, int64_t Bm, int Cin,
                                 int Cout, void *stream);
 
+/* Adjoint of the spectral block in x (Sec. B.8, the differentiable SHT):
+ * gx = SHT^T(W^H ISHT^T(gy)), the gradient of <gy, y> with y =
+ * sht_spectral_block(x).  gy: float32 [Bm][Cout][nlat][nlon], W: complex64
+ * [lmax][Cout][Cin] (the forward's weights), gx: float32
+ * [Bm][Cin][nlat][nlon].  Tensor-core plans run it on the block's kernels
+ * (the analysis with the inverse's mode weights, the filter with
+ * conj(W[l][o][i]) built on chip, the synthesis with the latitude weights);
+ * FP32 plans on the CUDA-core kernels.  Limits and errors as
+ * sht_spectral_block. */
+sht_status_t sht_spectral_block_adjoint(sht_plan_t plan, const float *gy,
+                                        const void *W, float *gx, int64_t Bm,
+                                        int Cin, int Cout, void *stream);
+
 /* Fused filter + inverse SHT: y = ISHT(filter(xhat, W)).  xhat: complex64
  * [Bm][Cin][lmax][mmax], y: float32 [Bm][Cout][nlat][nlon]. */
 sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,

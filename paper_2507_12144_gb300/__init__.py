@@ -304,6 +304,23 @@ def sht_spectral_block(plan: Plan, x: torch.Tensor, W: torch.Tensor) -> torch.Te
     return out
 
 
+def sht_spectral_block_adjoint(plan: Plan, gy: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
+    """gx = SHT^T(W^H ISHT^T(gy)), the block's adjoint in x; gy [Bm, Cout, nlat,
+    nlon], W [lmax, Cout, Cin] -> gx [Bm, Cin, nlat, nlon]."""
+    gy, lead, _ = _spatial_in(plan, gy, "gy")
+    if len(lead) != 2:
+        raise ValueError("gy must be [Bm, Cout, nlat, nlon]")
+    W = _need(W, torch.complex64, "W", plan.device)
+    Bm, Cout = lead
+    if W.dim() != 3 or W.shape[0] != plan.lmax or W.shape[1] != Cout:
+        raise ValueError("W must be [lmax, Cout, Cin]")
+    Cin = int(W.shape[2])
+    out = torch.empty((Bm, Cin, plan.nlat, plan.nlon), dtype=torch.float32, device=gy.device)
+    _abi.check(_abi.lib().sht_spectral_block_adjoint(plan.handle, _ptr(gy), _ptr(W), _ptr(out), Bm, Cin, Cout,
+                                                     _stream(gy)))
+    return out
+
+
 def spectral_filter_inverse(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
     """y = ISHT(filter(xhat, W)); xhat [Bm, Cin, lmax, mmax] -> y [Bm, Cout, nlat, nlon]."""
     xhat, _, _ = _spectral_in(plan, xhat)
@@ -472,7 +489,9 @@ class SpectralBlock(torch.autograd.Function):
     The backward pass recomputes xhat = SHT(x) instead of storing the
     spectral activations:
       gyhat = ISHT^T(gy);  (gxhat, gW) = filter^T(gyhat);  gx = SHT^T(gxhat).
-    """
+    The input gradient runs as one adjoint block (sht_spectral_block_adjoint:
+    on the tensor cores for tensor-core plans); the weight gradient, when it
+    is needed, reduces gyhat against the recomputed xhat."""
 
     @staticmethod
     def forward(ctx, x, W, plan):
@@ -485,10 +504,13 @@ class SpectralBlock(torch.autograd.Function):
         x, W = ctx.saved_tensors
         plan = ctx.plan
         need_x, need_W = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        gyhat = sht_inverse_adjoint(plan, gy.contiguous())
-        xhat = sht_forward(plan, x) if need_W else None
-        gxhat, gW = spectral_filter_adjoint(plan, gyhat, W, xhat, need_gx=need_x, need_gW=need_W)
-        gx = sht_forward_adjoint(plan, gxhat) if need_x else None
+        gy = gy.contiguous()
+        gx = sht_spectral_block_adjoint(plan, gy, W) if need_x else None
+        gW = None
+        if need_W:
+            gyhat = sht_inverse_adjoint(plan, gy)
+            xhat = sht_forward(plan, x)
+            _, gW = spectral_filter_adjoint(plan, gyhat, W, xhat, need_gx=False, need_gW=True)
         return gx, gW, None
 
 

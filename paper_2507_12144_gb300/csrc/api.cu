@@ -390,9 +390,13 @@ sht_status_t filter_body(sht_plan_s *p, const float2 *x, const float2 *W, float2
 
 // One chunk of nb members through the tensor-core block path: forward into
 // the l-major rows, real filter weights, tensor-core filter into the split
-// rows of the inverse, inverse + synthesis.
+// rows of the inverse, inverse + synthesis.  adjoint: the block's adjoint in
+// x, ISHT^T -> W^H -> SHT^T on the same kernels (the analysis with the
+// inverse's mode weights and no latitude weights, the filter with
+// conj(W[l][i][o]), the synthesis with the latitude weights); x then has
+// Cin = the forward's Cout channels, W is the forward's [L][Cin][Cout].
 sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, int64_t nb, int Cin, int Cout,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool adjoint = false) {
   // members' columns packed at kx = 2 Cin rounded to 8: the 64-column K
   // chunks of one member run into the next member's columns, which meet
   // zero weight columns, or past the last member outside the map (read as
@@ -401,7 +405,7 @@ sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, in
   const int nwr = (2 * Cout + 15) / 16 * 16;
   const bool split = p->precision == SHT_PREC_SPLIT_BF16;
   RowsOut ro{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, kx};
-  SHT_TRY(analysis(p, x, nullptr, nb * Cin, st, false, false, &ro));
+  SHT_TRY(analysis(p, x, nullptr, nb * Cin, st, adjoint, false, &ro));
   CUtensorMap ta_hi, ta_lo;
   const int64_t width = std::max<int64_t>(64, nb * (int64_t)kx);
   if (!tc_encode_2d(&ta_hi, p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx) ||
@@ -410,10 +414,10 @@ sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, in
   cudaError_t e;
   e = traced(p, SHT_KERNEL_FILTER, st, [&] {
     return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, ta_hi, ta_lo, (const float2 *)W, p->d_s_hi,
-                            data_lo(p, p->d_s_lo), p->ldcb, kx, nwr, (int)nb, Cin, Cout, st);
+                            data_lo(p, p->d_s_lo), p->ldcb, kx, nwr, (int)nb, Cin, Cout, adjoint ? 1 : 0, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "filter launch");
-  return synthesis_rows(p, y, (int)(nb * Cout), st, false);
+  return synthesis_rows(p, y, (int)(nb * Cout), st, adjoint);
 }
 
 sht_status_t check_plan(sht_plan_t plan) {
@@ -981,6 +985,40 @@ sht_status_t sht_spectral_block(sht_plan_t p, const float *x, const void *W, flo
     SHT_TRY(analysis(p, x + b0 * Cin * npix, p->d_spec_a, nb * Cin, st, false, false));
     SHT_TRY(filter_body(p, p->d_spec_a, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 0, st));
     SHT_TRY(synthesis(p, p->d_spec_b, y + b0 * Cout * npix, nb * Cout, st, false));
+  }
+  return SHT_OK;
+}
+
+sht_status_t sht_spectral_block_adjoint(sht_plan_t p, const float *gy, const void *W, float *gx, int64_t Bm, int Cin,
+                                        int Cout, void *stream) {
+  NvtxRange nvtx_range("sht_spectral_block_adjoint");
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, true));
+  if (Bm == 0) return SHT_OK;
+  SHT_TRY(check_ptr(gy, "gy"));
+  SHT_TRY(check_ptr(W, "W"));
+  SHT_TRY(check_ptr(gx, "gx"));
+  DeviceGuard g(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t per = p->max_batch / std::max(Cin, Cout);
+  if (is_tc(p)) {
+    if (std::max(Cin, Cout) > p->max_channels)
+      return fail(SHT_ERR_INVALID_ARG, "max(Cin, Cout) exceeds the plan's max_channels");
+    per = std::min<int64_t>(per, p->ldx / block_kx(Cout));
+  }
+  const int64_t npix = (int64_t)p->nlat * p->nlon;
+  for (int64_t b0 = 0; b0 < Bm; b0 += per) {
+    const int64_t nb = std::min(per, Bm - b0);
+    const float *gyb = gy + b0 * Cout * npix;
+    float *gxb = gx + b0 * Cin * npix;
+    if (is_tc(p)) {
+      SHT_TRY(block_tc(p, gyb, W, gxb, nb, Cout, Cin, st, true));
+      continue;
+    }
+    SHT_TRY(analysis(p, gyb, p->d_spec_a, nb * Cout, st, true, true));
+    SHT_TRY(filter_body(p, p->d_spec_a, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 1, st));
+    SHT_TRY(synthesis(p, p->d_spec_b, gxb, nb * Cin, st, true));
   }
   return SHT_OK;
 }

@@ -195,6 +195,8 @@ struct TcParams {
   const FiltTile *ftiles;
   int L, M, Nt, Bm, ntn, kx, nwr, cin, cout, lds;
   const float2 *W;        // complex weights [L][cout][cin] (B generated on chip)
+  int wadj;               // 1: the weights of (output o, input i) are conj(W[l][i][o]), W [L][cin][cout]
+                          // (selects the kernel instance; read on the host)
   __nv_bfloat16 *s_hi, *s_lo;
   unsigned *err;
 };
@@ -692,7 +694,7 @@ __device__ __forceinline__ void store_rows_smem(int g, int hf, unsigned char *a_
   }
 }
 
-template <int kMode, bool kSplit, bool kGen>
+template <int kMode, bool kSplit, bool kGen, bool kWAdj = false>
 __global__ void __launch_bounds__(kGen ? kThreadsGen : kThreads, 1)
 tc_persistent_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ unsigned char smem_raw[];
@@ -774,6 +776,20 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
         const int e = gtid + 256 * u;
         const int o = (ti.n0 >> 1) + (e >> 3), i0 = kc * (kKc / 2) + 4 * (e & 7);
         wv[u][0] = wv[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kWAdj) {
+          // the adjoint filter: conj(W[l][i][o]), input channels i0 .. i0 + 3
+          if (e < ti.Nt * 4 && o < P.cout) {
+            float2 t4[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+              const float2 w = i0 + c < P.cin ? __ldg(Wl + (int64_t)(i0 + c) * P.cout + o) : make_float2(0.f, 0.f);
+              t4[c] = make_float2(w.x, -w.y);
+            }
+            wv[u][0] = make_float4(t4[0].x, t4[0].y, t4[1].x, t4[1].y);
+            wv[u][1] = make_float4(t4[2].x, t4[2].y, t4[3].x, t4[3].y);
+          }
+          continue;
+        }
         if (e < ti.Nt * 4 && o < P.cout) {
           const float2 *src = Wl + (int64_t)o * P.cin + i0;
           if (i0 + 4 <= P.cin && (P.cin & 1) == 0) {
@@ -1401,9 +1417,9 @@ void column_tiles(int B, int cap, int &Nt, int &nct) {
   Nt = ((C2 + nct - 1) / nct + 15) / 16 * 16;
 }
 
-template <int kMode, bool kSplit, bool kGen>
+template <int kMode, bool kSplit, bool kGen, bool kWAdj = false>
 cudaError_t start_persistent(unsigned grid, size_t smem, const TcParams &P, cudaStream_t st) {
-  auto fn = tc_persistent_kernel<kMode, kSplit, kGen>;
+  auto fn = tc_persistent_kernel<kMode, kSplit, kGen, kWAdj>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, threads_of(kGen), smem, st>>>(P);
@@ -1498,7 +1514,10 @@ cudaError_t launch_persistent(bool split, bool gen, TcParams &P, const TcLaunch 
     P.epi_off = (int)((size_t)stages * sb);
     const size_t smem = 1024 + (size_t)stages * sb + extra;
     if constexpr (kMode == kFilt) {
-      if (gen)
+      if (gen && P.wadj)
+        e = split ? start_persistent<kFilt, true, true, true>(grid, smem, P, st)
+                  : start_persistent<kFilt, false, true, true>(grid, smem, P, st);
+      else if (gen)
         e = split ? start_persistent<kFilt, true, true>(grid, smem, P, st)
                   : start_persistent<kFilt, false, true>(grid, smem, P, st);
       else
@@ -1785,7 +1804,7 @@ cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int nti
 
 cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &ta_hi,
                              const CUtensorMap &ta_lo, const float2 *W, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo,
-                             int lds, int kx, int nwr, int Bm, int Cin, int Cout, cudaStream_t st) {
+                             int lds, int kx, int nwr, int Bm, int Cin, int Cout, int wadj, cudaStream_t st) {
   if (s_hi != T.srows_hi || lds != T.lds) return cudaErrorInvalidValue;  // the store maps describe these rows
   if (nftiles == 0 || Bm <= 0) return cudaSuccess;
   TcParams P{};
@@ -1813,6 +1832,7 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
   P.maps[0].o16_hi = T.so16_hi;
   P.maps[0].o16_lo = T.so16_lo;
   P.W = W;
+  P.wadj = wadj;
   return launch_persistent<kFilt>(T.split, true, P, TcLaunch{}, st);
 }
 

@@ -159,10 +159,12 @@ cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double 
 // ftiles: (l, m0) pairs covering m <= l, m < M in steps of 128.
 // ta: the forward rows (width = members x kx, row stride ldx); W: the
 // complex weights [L][Cout][Cin] (device), turned into the real bf16 hi/lo
-// form of each K chunk on chip; nwr = 2 Cout rounded to 16.
+// form of each K chunk on chip; nwr = 2 Cout rounded to 16.  wadj = 1: the
+// adjoint filter, output o from input i by conj(W[l][i][o]) with W
+// [L][Cin][Cout].
 cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftiles, const CUtensorMap &ta_hi,
                              const CUtensorMap &ta_lo, const float2 *W, __nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo,
-                             int lds, int kx, int nwr, int Bm, int Cin, int Cout, cudaStream_t st);
+                             int lds, int kx, int nwr, int Bm, int Cin, int Cout, int wadj, cudaStream_t st);
 // Inverse contraction on the tensor cores from the bf16 internal rows to the
 // FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
 cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,

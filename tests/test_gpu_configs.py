@@ -214,12 +214,12 @@ def test_block_360x720_256_channels_with_autograd(shtgb, prec):
 @pytest.mark.slow
 def test_block_360x720_bf16_within_its_stage_bounds(shtgb):
     """BF16: the block rounds data three times (Fourier rows, forward rows,
-    filter output), the input gradient twice (ISHT^T and SHT^T inputs), the
+    filter output), so does the input gradient (the adjoint block), the
     weight gradient twice (its two factors); each chain stays within its
     count of BF16 stage bounds."""
     ey, ex, ew = _cached_errors(shtgb, "bf16")
     assert ey.max() <= 3 * BF16_STAGE, ey
-    assert ex.max() <= 2 * BF16_STAGE, ex
+    assert ex.max() <= 3 * BF16_STAGE, ex
     assert ew.max() <= 2 * BF16_STAGE, ew
 
 
