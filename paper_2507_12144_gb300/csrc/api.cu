@@ -272,7 +272,7 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
       e = traced(p, SHT_KERNEL_R2C, st, [&] {
         if (fft45_supported(p->nlon))
           return launch_r2c45(xb, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
-                              ring, wts, st);
+                              ring, wts, st, p->d_err);
         return launch_r2c(xb, p->d_work, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle, p->radix, ring, wts, st);
       });
       if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
@@ -284,7 +284,7 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
       e = traced(p, SHT_KERNEL_R2C, st, [&] {
         if (fft45_supported(p->nlon))
           return launch_r2c45(xb, nullptr, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->lay_f,
-                              p->d_twiddle, ring, wts, st);
+                              p->d_twiddle, ring, wts, st, p->d_err);
         return launch_r2c_bf16(xb, f_hi(p), data_lo(p, f_lo(p)), p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
                                p->radix, ring, wts, st);
       });
@@ -332,7 +332,7 @@ cudaError_t c2r_any(sht_plan_s *p, float *y, int nb, bool adjoint, cudaStream_t 
   const float *ring = adjoint ? p->d_ring_w : nullptr;
   const int wts = adjoint ? 0 : 1;
   if (fft45_supported(p->nlon))
-    return launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, ring, wts, st);
+    return launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, ring, wts, st, p->d_err);
   return launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, p->radix, ring, wts, st);
 }
 

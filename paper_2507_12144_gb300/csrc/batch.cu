@@ -130,9 +130,9 @@ cudaError_t stage_r2c(sht_batch_s *b, cudaStream_t st) {
     cudaError_t e;
     if (fft45_supported(p->nlon))
       e = b->tc ? launch_r2c45(x, nullptr, work_hi(p), work_lo(p), p->nlat, p->nlon, p->M, nb, p->lay_f,
-                               p->d_twiddle, p->d_ring_w, 0, st)
+                               p->d_twiddle, p->d_ring_w, 0, st, p->d_err)
                 : launch_r2c45(x, p->d_work, nullptr, nullptr, p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
-                               p->d_ring_w, 0, st);
+                               p->d_ring_w, 0, st, p->d_err);
     else
       e = b->tc ? launch_r2c_bf16(x, work_hi(p), work_lo(p), p->nlat, p->nlon, p->M, nb, p->lay_f, p->d_twiddle,
                                   p->radix, p->d_ring_w, 0, st)
@@ -160,7 +160,7 @@ cudaError_t stage_c2r(sht_batch_s *b, cudaStream_t st) {
     const int nb = (int)b->items[i].count;
     cudaError_t e =
         fft45_supported(p->nlon)
-            ? launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, nullptr, 1, st)
+            ? launch_c2r45(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, nullptr, 1, st, p->d_err)
             : launch_c2r(p->d_work, y, p->nlat, p->nlon, p->M, nb, p->lay_g, p->d_twiddle, p->radix, nullptr, 1, st);
     if (e != cudaSuccess) return e;
   }

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "sht_internal.cuh"
+#include "tc_common.cuh"
 
 namespace shtgb {
 namespace {
@@ -302,46 +303,19 @@ struct OutBF16 {
   }
 };
 
-// One CTA of the analysis: fields bx kFB .. bx kFB + 7, ring pairs
-// by NPAIR .. by NPAIR + NPAIR - 1.
+// Output stage of the analysis: separate the two real transforms of every
+// sequence buffer in `bufs`, fold by parity, write 8-field segments: thread
+// (f2, m0) handles fields 2 f2, 2 f2 + 1 and orders m0, m0 + 64, ... (m =
+// 45 q + r tracked without divisions).
 template <int P, class Out>
-__device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restrict__ x, Out out, int nlat, int M,
-                                           int B, FoldLayout fl, const float2 *__restrict__ twiddle,
-                                           const float *__restrict__ ring_scale, int inverse_weights) {
+__device__ __forceinline__ void r2c45_emit(int bx, int by, const float2 *bufs, Out out, int nlat, int M, int B,
+                                           FoldLayout fl, const float *__restrict__ ring_scale, int inverse_weights) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
   constexpr int BUF = seq_pitch<P>();
-  extern __shared__ float2 smem[];
-  float2 *tw = smem;
-  float2 *bufs = smem + N;
-  const int Kh = (nlat + 1) / 2;
-  const int s = threadIdx.x / P, t = threadIdx.x % P;
-  const int f = s % kFB, pp = s / kFB;
-  const int b = bx * kFB + f;
-  const int kp = by * NPAIR + pp;
-  const int ks = nlat - 1 - kp;
-  const bool live = (b < B) && (kp < Kh);
-  load_twiddles<P>(tw, twiddle);
-  float2 v[kQ];
-  if (live) {
-    const float *rn = x + ((int64_t)b * nlat + kp) * N;
-    const float *rs = x + ((int64_t)b * nlat + ks) * N;
-    const bool eq = (kp == ks);
-#pragma unroll
-    for (int j = 0; j < kQ; j++) v[j] = make_float2(__ldg(rn + t + P * j), eq ? 0.f : __ldg(rs + t + P * j));
-  } else {
-#pragma unroll
-    for (int j = 0; j < kQ; j++) v[j] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  float2 *buf = bufs + s * BUF;
-  seq_fft<P>(v, t, buf, tw);
-  __syncthreads();
-  // separate the two real transforms, fold by parity, write 8-field
-  // segments: thread (f2, m0) handles fields 2 f2, 2 f2 + 1 and orders m0,
-  // m0 + 64, ... (m = 45 q + r tracked without divisions)
   constexpr int kPairs = kFB / 2;
   constexpr int kMStep = kThreads / kPairs;  // 64
+  const int Kh = (nlat + 1) / 2;
   const int b0 = bx * kFB;
   const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
   const int fa = 2 * f2;
@@ -397,11 +371,149 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
   }
 }
 
+// One CTA of the analysis: fields bx kFB .. bx kFB + 7, ring pairs
+// by NPAIR .. by NPAIR + NPAIR - 1.
+template <int P, class Out>
+__device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restrict__ x, Out out, int nlat, int M,
+                                           int B, FoldLayout fl, const float2 *__restrict__ twiddle,
+                                           const float *__restrict__ ring_scale, int inverse_weights) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = seq_pitch<P>();
+  extern __shared__ float2 smem[];
+  float2 *tw = smem;
+  float2 *bufs = smem + N;
+  const int Kh = (nlat + 1) / 2;
+  const int s = threadIdx.x / P, t = threadIdx.x % P;
+  const int f = s % kFB, pp = s / kFB;
+  const int b = bx * kFB + f;
+  const int kp = by * NPAIR + pp;
+  const int ks = nlat - 1 - kp;
+  const bool live = (b < B) && (kp < Kh);
+  load_twiddles<P>(tw, twiddle);
+  float2 v[kQ];
+  if (live) {
+    const float *rn = x + ((int64_t)b * nlat + kp) * N;
+    const float *rs = x + ((int64_t)b * nlat + ks) * N;
+    const bool eq = (kp == ks);
+#pragma unroll
+    for (int j = 0; j < kQ; j++) v[j] = make_float2(__ldg(rn + t + P * j), eq ? 0.f : __ldg(rs + t + P * j));
+  } else {
+#pragma unroll
+    for (int j = 0; j < kQ; j++) v[j] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 *buf = bufs + s * BUF;
+  seq_fft<P>(v, t, buf, tw);
+  __syncthreads();
+  r2c45_emit<P, Out>(bx, by, bufs, out, nlat, M, B, fl, ring_scale, inverse_weights);
+}
+
 template <int P, class Out>
 __global__ void __launch_bounds__(kThreads, 2)
 r2c45_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, FoldLayout fl, const float2 *__restrict__ twiddle,
              const float *__restrict__ ring_scale, int inverse_weights) {
   r2c45_body<P, Out>(blockIdx.x, blockIdx.y, x, out, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
+}
+
+// Synthesis staging of one item: conj(Z) (c_m / 2 * ring scale * G of the
+// northern and southern rows, as the Hermitian sequences' Z = H_n + i H_s)
+// of fields fa, fa + 1 at order m of ring pair kq, from their E and O
+// values ge, go (two fields' complex values each), into the two sequence
+// buffers at Ba.
+template <int P>
+__device__ __forceinline__ void c2r45_put(float2 *Ba, float4 ge, float4 go, int m, int kq, int nlat,
+                                          const float *__restrict__ ring_scale, int inverse_weights) {
+  constexpr int N = kQ * P;
+  constexpr int BUF = seq_pitch<P>();
+  const int kqs = nlat - 1 - kq;
+  const bool eq = (kq == kqs);
+  const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
+  const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
+  const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
+  const int mq = m == 0 ? 0 : N - m;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const float2 e = h ? make_float2(ge.z, ge.w) : make_float2(ge.x, ge.y);
+    const float2 o = h ? make_float2(go.z, go.w) : make_float2(go.x, go.y);
+    const float2 gn = cscale(eq ? e : cadd(e, o), w * sn);
+    const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(e, o), w * ss);
+    // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
+    // G_m enters Z[m], conj(G_m) enters Z[N - m]
+    const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
+    const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
+    float2 *Bq = Ba + h * BUF;
+    if (mq == m) {
+      Bq[m] = cadd(za, zb);
+    } else {
+      Bq[m] = za;
+      Bq[mq] = zb;
+    }
+  }
+}
+
+// Zeros between the two halves of every staged sequence of the thread's
+// fields (orders M .. N - M).
+template <int P>
+__device__ __forceinline__ void c2r45_zero_gap(float2 *bufs, int by, int nlat, int M, bool field_ok) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = seq_pitch<P>();
+  constexpr int kPairs = kFB / 2;
+  constexpr int kMStep = kThreads / kPairs;
+  const int Kh = (nlat + 1) / 2;
+  const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+  const int fa = 2 * f2;
+#pragma unroll 1
+  for (int pq = 0; pq < NPAIR; pq++) {
+    const int kq = by * NPAIR + pq;
+    if (kq >= Kh || !field_ok) continue;
+    float2 *Ba = bufs + (pq * kFB + fa) * BUF;
+    for (int q = M + m0; q <= N - M; q += kMStep) {
+      Ba[q] = make_float2(0.f, 0.f);
+      Ba[BUF + q] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// The synthesis proper, after staging (and a CTA barrier): every sequence
+// buffer of `bufs` holds conj(Z); the inverse DFT is evaluated as
+// conj(FFT(conj Z)), and the two real rows are written.
+template <int P>
+__device__ __forceinline__ void c2r45_synth(int bx, int by, float2 *bufs, const float2 *tw, float *__restrict__ y,
+                                            int nlat, int B) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = seq_pitch<P>();
+  const int Kh = (nlat + 1) / 2;
+  const int s = threadIdx.x / P, t = threadIdx.x % P;
+  const int f = s % kFB, pp = s / kFB;
+  const int b = bx * kFB + f;
+  const int kp = by * NPAIR + pp;
+  const int ksth = nlat - 1 - kp;
+  const bool live = (b < B) && (kp < Kh);
+  float2 *buf = bufs + s * BUF;
+  float2 v[kQ];
+#pragma unroll
+  for (int j = 0; j < kQ; j++) v[j] = live ? buf[t + P * j] : make_float2(0.f, 0.f);
+  __syncwarp();
+  seq_fft<P>(v, t, buf, tw);
+  if (!live) return;
+  const bool eq = (kp == ksth);
+  float *rn = y + ((int64_t)b * nlat + kp) * N;
+  float *rs = y + ((int64_t)b * nlat + ksth) * N;
+  int r = t, q = 0;  // j = 45 q + r
+#pragma unroll 5
+  for (int j = t; j < N; j += P) {
+    const float2 o = buf[r * rpitch<P>() + q];
+    rn[j] = o.x;
+    if (!eq) rs[j] = -o.y;
+    r += P;
+    if (r >= kQ) {
+      r -= kQ;
+      q++;
+    }
+  }
 }
 
 template <int P, int kBatch>
@@ -417,12 +529,11 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
   const int Kh = (nlat + 1) / 2;
   const int b0 = bx * kFB;
   load_twiddles<P>(tw, twiddle);
-  // stage conj(Z) (c_m / 2 * ring scale * G of the northern and southern
-  // rows, as the Hermitian sequences' Z = H_n + i H_s) in every sequence
-  // buffer; thread (f2, m0) stages fields 2 f2 and 2 f2 + 1 (one 16-byte
-  // load per row), orders m0, m0 + 64, ..., kBatch loads in flight (12:
-  // all of a thread's orders at nlon = 1440 in one memory round trip; the
-  // grouped kernel, which holds every P's body, keeps 6 to stay unspilled)
+  // stage conj(Z) in every sequence buffer; thread (f2, m0) stages fields
+  // 2 f2 and 2 f2 + 1 (one 16-byte load per row), orders m0, m0 + 64, ...,
+  // kBatch loads in flight (12: all of a thread's orders at nlon = 1440 in
+  // one memory round trip; the grouped kernel, which holds every P's body,
+  // keeps 6 to stay unspilled)
   constexpr int kPairs = kFB / 2;
   constexpr int kMStep = kThreads / kPairs;  // 64
   const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
@@ -464,75 +575,12 @@ __device__ __forceinline__ void c2r45_body(int bx, int by, const float *__restri
       const int pq = NPAIR == 1 ? 0 : it / per;
       const int m = m0 + (it - pq * per) * kMStep, kq = by * NPAIR + pq;
       if (kq >= Kh) continue;
-      const int kqs = nlat - 1 - kq;
-      const bool eq = (kq == kqs);
-      const float sn = 0.5f * (ring_scale ? ring_scale[kq] : 1.0f);
-      const float ss = 0.5f * (ring_scale ? ring_scale[kqs] : 1.0f);
-      float2 *Ba = bufs + (pq * kFB + fa) * BUF;
-      const float w = (inverse_weights && m != 0 && 2 * m != N) ? 2.0f : 1.0f;
-      const int mq = m == 0 ? 0 : N - m;
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const float2 e = h ? make_float2(ge[u].z, ge[u].w) : make_float2(ge[u].x, ge[u].y);
-        const float2 o = h ? make_float2(go[u].z, go[u].w) : make_float2(go[u].x, go[u].y);
-        const float2 gn = cscale(eq ? e : cadd(e, o), w * sn);
-        const float2 gs = eq ? make_float2(0.f, 0.f) : cscale(csub(e, o), w * ss);
-        // Z = H_n + i H_s of the Hermitian extensions, stored conjugated:
-        // G_m enters Z[m], conj(G_m) enters Z[N - m]
-        const float2 za = make_float2(gn.x - gs.y, -(gn.y + gs.x));
-        const float2 zb = make_float2(gn.x + gs.y, gn.y - gs.x);
-        float2 *Bq = Ba + h * BUF;
-        if (mq == m) {
-          Bq[m] = cadd(za, zb);
-        } else {
-          Bq[m] = za;
-          Bq[mq] = zb;
-        }
-      }
+      c2r45_put<P>(bufs + (pq * kFB + fa) * BUF, ge[u], go[u], m, kq, nlat, ring_scale, inverse_weights);
     }
   }
-  // zeros between the two halves of every staged sequence
-#pragma unroll 1
-  for (int pq = 0; pq < NPAIR; pq++) {
-    const int kq = by * NPAIR + pq;
-    if (kq >= Kh || !field_ok) continue;
-    float2 *Ba = bufs + (pq * kFB + fa) * BUF;
-    for (int q = M + m0; q <= N - M; q += kMStep) {
-      Ba[q] = make_float2(0.f, 0.f);
-      Ba[BUF + q] = make_float2(0.f, 0.f);
-    }
-  }
+  c2r45_zero_gap<P>(bufs, by, nlat, M, field_ok);
   __syncthreads();
-  const int s = threadIdx.x / P, t = threadIdx.x % P;
-  const int f = s % kFB, pp = s / kFB;
-  const int b = b0 + f;
-  const int kp = by * NPAIR + pp;
-  const int ksth = nlat - 1 - kp;
-  const bool live = (b < B) && (kp < Kh);
-  float2 *buf = bufs + s * BUF;
-  // the staged conj(Z); the synthesis is an inverse DFT, evaluated as
-  // conj(FFT(conj Z))
-  float2 v[kQ];
-#pragma unroll
-  for (int j = 0; j < kQ; j++) v[j] = live ? buf[t + P * j] : make_float2(0.f, 0.f);
-  __syncwarp();
-  seq_fft<P>(v, t, buf, tw);
-  if (!live) return;
-  const bool eq = (kp == ksth);
-  float *rn = y + ((int64_t)b * nlat + kp) * N;
-  float *rs = y + ((int64_t)b * nlat + ksth) * N;
-  int r = t, q = 0;  // j = 45 q + r
-#pragma unroll 5
-  for (int j = t; j < N; j += P) {
-    const float2 o = buf[r * rpitch<P>() + q];
-    rn[j] = o.x;
-    if (!eq) rs[j] = -o.y;
-    r += P;
-    if (r >= kQ) {
-      r -= kQ;
-      q++;
-    }
-  }
+  c2r45_synth<P>(bx, by, bufs, tw, y, nlat, B);
 }
 
 template <int P>
@@ -540,6 +588,202 @@ __global__ void __launch_bounds__(kThreads, 2)
 c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int M, int B, FoldLayout fl,
              const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights) {
   c2r45_body<P, 12>(blockIdx.x, blockIdx.y, Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent forms, one CTA per SM: the CTA walks the tiles (bx, by) of the
+// grid above (tile = by gx + bx) in steps of the grid size, and the input of
+// its next tile arrives in shared memory by asynchronous bulk copies while
+// the current tile is transformed, so that DRAM and the FFT's instruction
+// stream overlap inside every SM.  Every wait is bounded: a copy that does
+// not arrive within the limit records SHT's timeout code in *err, and the
+// CTA waits a little longer for what it still has in flight and returns.
+
+// Analysis: two stages of NSEQ sequence buffers.  A stage first receives the
+// tile's rows by bulk copies (sequence s: its northern row at float 0, its
+// southern row at float N of the buffer; 2 N floats = N float2 <= BUF), is
+// then read into registers by the sequence's lanes, and serves as the
+// sequence buffers of that tile's FFT and output stage.  The copies of tile
+// i + 2 go into the stage of tile i once the CTA is done with it.
+template <int P>
+__host__ __device__ constexpr size_t r2c_pipe_smem() {
+  return 16 + sizeof(float2) * ((size_t)kQ * P + 2 * (size_t)(kThreads / P) * seq_pitch<P>());
+}
+
+template <int P, class Out>
+__global__ void __launch_bounds__(kThreads, 1)
+r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, FoldLayout fl,
+                  const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights,
+                  unsigned *err) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = seq_pitch<P>();
+  constexpr int NSEQ = kThreads / P;
+  constexpr int SPW = 32 / P;  // sequences per warp
+  constexpr uint32_t kRowBytes = 4u * N;
+  extern __shared__ __align__(1024) unsigned char pipe_smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(pipe_smem);
+  float2 *tw = reinterpret_cast<float2 *>(pipe_smem + 16);
+  float2 *stage0 = tw + N;
+  const int Kh = (nlat + 1) / 2;
+  const int gx = (B + kFB - 1) / kFB;
+  const int ntiles = gx * ((Kh + NPAIR - 1) / NPAIR);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar[0], kThreads / 32);
+    tc::mbar_init(&bar[1], kThreads / 32);
+    tc::mbar_fence_init();
+  }
+  load_twiddles<P>(tw, twiddle);
+  __syncthreads();
+  // the copies of tile `tile` into stage `st`: lane j < 2 SPW of warp w
+  // copies row j % 2 of sequence w SPW + j / 2; lane 0 announces the warp's
+  // bytes (every warp arrives once per phase)
+  auto issue = [&](int tile, int st) {
+    const int bx = tile % gx, by = tile / gx;
+    float2 *sb = stage0 + st * NSEQ * BUF;
+    const int seq = warp * SPW + (lane >> 1), row = lane & 1;
+    const int f = seq % kFB, pp = seq / kFB;
+    const int b = bx * kFB + f, kp = by * NPAIR + pp, ks = nlat - 1 - kp;
+    const bool copy = lane < 2 * SPW && b < B && kp < Kh && (row == 0 || kp != ks);
+    const uint32_t bytes = __reduce_add_sync(0xffffffffu, copy ? kRowBytes : 0u);
+    if (lane == 0) tc::mbar_arrive_expect_tx(&bar[st], bytes);
+    __syncwarp();
+    if (copy)
+      tc::bulk_load(reinterpret_cast<float *>(sb + seq * BUF) + row * N,
+                    x + ((int64_t)b * nlat + (row ? ks : kp)) * N, kRowBytes, &bar[st]);
+  };
+  if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1);
+  const int s = threadIdx.x / P, t = threadIdx.x % P;
+  const int f = s % kFB, pp = s / kFB;
+  int i = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
+    const int st = i & 1;
+    const bool ok = tc::mbar_wait(&bar[st], (i >> 1) & 1, err);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        tc::mbar_wait(&bar[st], (i >> 1) & 1, nullptr, 100000000ull);
+        if (tile + G < ntiles) tc::mbar_wait(&bar[st ^ 1], ((i + 1) >> 1) & 1, nullptr, 100000000ull);
+      }
+      __syncthreads();
+      return;
+    }
+    const int bx = tile % gx, by = tile / gx;
+    float2 *sb = stage0 + st * NSEQ * BUF;
+    const int b = bx * kFB + f, kp = by * NPAIR + pp;
+    const bool live = (b < B) && (kp < Kh);
+    const bool eq = kp == nlat - 1 - kp;
+    float2 *buf = sb + s * BUF;
+    const float *rn = reinterpret_cast<const float *>(buf), *rs = rn + N;
+    float2 v[kQ];
+#pragma unroll
+    for (int j = 0; j < kQ; j++)
+      v[j] = live ? make_float2(rn[t + P * j], eq ? 0.f : rs[t + P * j]) : make_float2(0.f, 0.f);
+    __syncwarp();
+    seq_fft<P>(v, t, buf, tw);
+    __syncthreads();
+    r2c45_emit<P, Out>(bx, by, sb, out, nlat, M, B, fl, ring_scale, inverse_weights);
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (tile + 2 * G < ntiles) issue(tile + 2 * G, st);
+  }
+}
+
+// Synthesis: one staging buffer of the tile's folded rows, [NPAIR][nrows]
+// rows of 32 floats (E and O of the tile's 8 fields at one order m: the
+// parity-paired layout keeps them in one 128-byte segment), filled by TMA
+// boxes of box_rows orders.  The CTA turns it into conj(Z) in the sequence
+// buffers, after which the next tile's boxes are issued into it while this
+// tile's FFTs and row stores run.
+template <int P>
+size_t c2r_pipe_smem(int nrows) {
+  return (size_t)(kThreads / P / kFB) * nrows * 128 + 16 + sizeof(float2) * ((size_t)kQ * P +
+                                                                            (size_t)(kThreads / P) * seq_pitch<P>());
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+c2r45_pipe_kernel(const __grid_constant__ CUtensorMap gmap, float *__restrict__ y, int nlat, int M, int B,
+                  int box_rows, int nbox, const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale,
+                  int inverse_weights, unsigned *err) {
+  constexpr int N = kQ * P;
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = seq_pitch<P>();
+  constexpr int kPairs = kFB / 2;
+  constexpr int kMStep = kThreads / kPairs;  // 64
+  extern __shared__ __align__(1024) unsigned char pipe_smem[];
+  const int nrows = nbox * box_rows;
+  float *stg = reinterpret_cast<float *>(pipe_smem);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(pipe_smem + (size_t)NPAIR * nrows * 128);
+  float2 *tw = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(bar) + 16);
+  float2 *bufs = tw + N;
+  const int Kh = (nlat + 1) / 2;
+  const int gx = (B + kFB - 1) / kFB;
+  const int ntiles = gx * ((Kh + NPAIR - 1) / NPAIR);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    tc::tma_prefetch_desc(&gmap);
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  load_twiddles<P>(tw, twiddle);
+  __syncthreads();
+  auto issue = [&](int tile) {
+    const int bx = tile % gx, by = tile / gx;
+    int live = 0;
+    for (int pq = 0; pq < NPAIR; pq++) live += (by * NPAIR + pq < Kh);
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)(live * nrows * 128));
+    for (int pq = 0; pq < NPAIR; pq++) {
+      const int kq = by * NPAIR + pq;
+      if (kq >= Kh) continue;
+      for (int j = 0; j < nbox; j++)
+        tc::tma_load_3d(stg + ((size_t)pq * nrows + (size_t)j * box_rows) * 32, &gmap, bar, 32 * bx, kq,
+                        j * box_rows);
+    }
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+  const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+  const int fa = 2 * f2;
+  int i = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
+    const bool ok = tc::mbar_wait(bar, i & 1, err);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) tc::mbar_wait(bar, i & 1, nullptr, 100000000ull);
+      __syncthreads();
+      return;
+    }
+    const int bx = tile % gx, by = tile / gx;
+    const int b0 = bx * kFB;
+    const bool field_ok = b0 + fa < B;
+    const bool two = b0 + fa + 1 < B;
+    if (field_ok) {
+#pragma unroll 1
+      for (int pq = 0; pq < NPAIR; pq++) {
+        const int kq = by * NPAIR + pq;
+        if (kq >= Kh) continue;
+        const float *row = stg + (size_t)pq * nrows * 32 + 4 * f2;
+        float2 *Ba = bufs + (pq * kFB + fa) * BUF;
+#pragma unroll 4
+        for (int m = m0; m < M; m += kMStep) {
+          float4 ge = *reinterpret_cast<const float4 *>(row + m * 32);
+          float4 go = *reinterpret_cast<const float4 *>(row + m * 32 + 16);
+          if (!two) {
+            ge.z = ge.w = 0.f;
+            go.z = go.w = 0.f;
+          }
+          c2r45_put<P>(Ba, ge, go, m, kq, nlat, ring_scale, inverse_weights);
+        }
+      }
+    }
+    c2r45_zero_gap<P>(bufs, by, nlat, M, field_ok);
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && tile + G < ntiles) issue(tile + G);
+    c2r45_synth<P>(bx, by, bufs, tw, y, nlat, B);
+    __syncthreads();
+  }
 }
 
 // Grouped launches: one grid over several problems (grids and batches) of
@@ -609,15 +853,39 @@ size_t smem45() {
   return sizeof(float2) * ((size_t)kQ * P + (size_t)(kThreads / P) * seq_pitch<P>());
 }
 
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int max_smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 0;
+  }
+  return v;
+}
+
 template <int P, class Out>
 cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl, const float2 *tw, const float *ring,
-                  int wts, cudaStream_t st) {
+                  int wts, cudaStream_t st, unsigned *err) {
   const int Kh = (nlat + 1) / 2;
   constexpr int NPAIR = kThreads / P / kFB;
   dim3 grid((B + kFB - 1) / kFB, (Kh + NPAIR - 1) / NPAIR);
+  cudaError_t e;
+  constexpr size_t psmem = r2c_pipe_smem<P>();
+  if (aligned16(x) && psmem <= (size_t)max_smem_optin()) {
+    // persistent form: the rows arrive by 16-byte-aligned bulk copies
+    e = cudaFuncSetAttribute((const void *)r2c45_pipe_kernel<P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)psmem);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (int64_t)grid.x * grid.y;
+    const unsigned g = (unsigned)std::min<int64_t>(ntiles, sm_count());
+    r2c45_pipe_kernel<P, Out><<<g, kThreads, psmem, st>>>(x, out, nlat, M, B, fl, tw, ring, wts, err);
+    return cudaGetLastError();
+  }
   const size_t smem = smem45<P>();
-  cudaError_t e = cudaFuncSetAttribute((const void *)r2c45_kernel<P, Out>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute((const void *)r2c45_kernel<P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
   r2c45_kernel<P, Out><<<grid, kThreads, smem, st>>>(x, out, nlat, M, B, fl, tw, ring, wts);
   return cudaGetLastError();
@@ -625,13 +893,29 @@ cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl
 
 template <int P>
 cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, FoldLayout fl, const float2 *tw, const float *ring,
-                  int wts, cudaStream_t st) {
+                  int wts, cudaStream_t st, unsigned *err) {
   const int Kh = (nlat + 1) / 2;
   constexpr int NPAIR = kThreads / P / kFB;
   dim3 grid((B + kFB - 1) / kFB, (Kh + NPAIR - 1) / NPAIR);
+  cudaError_t e;
+  if (fl.cg && aligned16(G) && M >= 1) {
+    // persistent form on the parity-paired layout: TMA boxes of box_rows
+    // orders of one ring pair and one 8-field group (128 bytes per order)
+    const int nbox = (M + 255) / 256, box_rows = (M + nbox - 1) / nbox;
+    const size_t psmem = c2r_pipe_smem<P>(nbox * box_rows);
+    CUtensorMap gm;
+    if (psmem <= (size_t)max_smem_optin() && tc_encode_pair_rows_f32(&gm, G, fl, Kh, M, box_rows)) {
+      e = cudaFuncSetAttribute((const void *)c2r45_pipe_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem);
+      if (e != cudaSuccess) return e;
+      const int64_t ntiles = (int64_t)grid.x * grid.y;
+      const unsigned g = (unsigned)std::min<int64_t>(ntiles, sm_count());
+      c2r45_pipe_kernel<P><<<g, kThreads, psmem, st>>>(gm, y, nlat, M, B, box_rows, nbox, tw, ring, wts, err);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = smem45<P>();
-  cudaError_t e = cudaFuncSetAttribute((const void *)c2r45_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  e = cudaFuncSetAttribute((const void *)c2r45_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   c2r45_kernel<P><<<grid, kThreads, smem, st>>>(G, y, nlat, M, B, fl, tw, ring, wts);
   return cudaGetLastError();
@@ -639,12 +923,12 @@ cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, FoldLayout f
 
 template <class Out>
 cudaError_t r2c45_dispatch(int nlon, const float *x, Out out, int nlat, int M, int B, FoldLayout fl, const float2 *tw,
-                           const float *ring, int wts, cudaStream_t st) {
+                           const float *ring, int wts, cudaStream_t st, unsigned *err) {
   switch (nlon / kQ) {
-    case 32: return r2c45<32>(x, out, nlat, M, B, fl, tw, ring, wts, st);
-    case 16: return r2c45<16>(x, out, nlat, M, B, fl, tw, ring, wts, st);
-    case 8: return r2c45<8>(x, out, nlat, M, B, fl, tw, ring, wts, st);
-    default: return r2c45<4>(x, out, nlat, M, B, fl, tw, ring, wts, st);
+    case 32: return r2c45<32>(x, out, nlat, M, B, fl, tw, ring, wts, st, err);
+    case 16: return r2c45<16>(x, out, nlat, M, B, fl, tw, ring, wts, st, err);
+    case 8: return r2c45<8>(x, out, nlat, M, B, fl, tw, ring, wts, st, err);
+    default: return r2c45<4>(x, out, nlat, M, B, fl, tw, ring, wts, st, err);
   }
 }
 
@@ -732,20 +1016,21 @@ bool fft45_supported(int nlon) {
 
 cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon,
                          int M, int B, FoldLayout fl, const float2 *twiddle, const float *ring_scale, int inverse_weights,
-                         cudaStream_t st) {
+                         cudaStream_t st, unsigned *err) {
   if (B <= 0) return cudaSuccess;
-  if (Fw) return r2c45_dispatch(nlon, x, OutF32{Fw}, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
-  return r2c45_dispatch(nlon, x, OutBF16{Fhi, Flo}, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
+  if (Fw) return r2c45_dispatch(nlon, x, OutF32{Fw}, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st, err);
+  return r2c45_dispatch(nlon, x, OutBF16{Fhi, Flo}, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st, err);
 }
 
 cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, FoldLayout fl,
-                         const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st) {
+                         const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st,
+                         unsigned *err) {
   if (B <= 0) return cudaSuccess;
   switch (nlon / kQ) {
-    case 32: return c2r45<32>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
-    case 16: return c2r45<16>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
-    case 8: return c2r45<8>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
-    default: return c2r45<4>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st);
+    case 32: return c2r45<32>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st, err);
+    case 16: return c2r45<16>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st, err);
+    case 8: return c2r45<8>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st, err);
+    default: return c2r45<4>(Gw, y, nlat, M, B, fl, twiddle, ring_scale, inverse_weights, st, err);
   }
 }
 

@@ -1399,6 +1399,8 @@ __global__ void seed_gen_kernel(float2 *__restrict__ seeds, int NB, const double
   }
 }
 
+}  // namespace
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -1408,6 +1410,8 @@ int sm_count() {
   }
   return n;
 }
+
+namespace {
 
 // Column tiling of the 2B real columns: balanced tiles of at most `cap`
 // (a multiple of 16) columns, each a multiple of 16.
@@ -1603,6 +1607,20 @@ bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl,
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float *>(ptr), gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_encode_pair_rows_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int Kh, int M, int box_rows) {
+  auto enc = encoder();
+  if (!enc || !fl.cg || fl.sp != 16 || fl.sk % 4 != 0 || fl.sm != fl.sk * Kh || box_rows < 1 || box_rows > 256)
+    return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)fl.sk, (cuuint64_t)Kh, (cuuint64_t)M};
+  const cuuint64_t gstr[2] = {(cuuint64_t)fl.sk * 4, (cuuint64_t)fl.sm * 4};
+  const cuuint32_t box[3] = {32, 1, (cuuint32_t)box_rows};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), const_cast<cuuint64_t *>(gdim),
+             const_cast<cuuint64_t *>(gstr), const_cast<cuuint32_t *>(box), const_cast<cuuint32_t *>(es),
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -249,11 +249,21 @@ cudaError_t launch_r2c(const float *x, float *Fw, int nlat, int nlon, int M,
 // P in {4, 8, 16, 32}.  The analysis writes FP32 (Fw != NULL) or bf16 hi
 // (and lo when Flo != NULL) with row stride ldc elements.
 bool fft45_supported(int nlon);
+// SMs of the current device (queried once).
+int sm_count();
+// Both run as persistent kernels with bulk-copy staging when the input is
+// 16-byte aligned (and, for the synthesis, in the parity-paired layout);
+// err (may be NULL) receives the timeout code of their bounded waits.
 cudaError_t launch_r2c45(const float *x, float *Fw, __nv_bfloat16 *Fhi, __nv_bfloat16 *Flo, int nlat, int nlon,
                          int M, int B, FoldLayout fl, const float2 *twiddle, const float *ring_scale, int inverse_weights,
-                         cudaStream_t st);
+                         cudaStream_t st, unsigned *err = nullptr);
 cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, int B, FoldLayout fl,
-                         const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st);
+                         const float2 *twiddle, const float *ring_scale, int inverse_weights, cudaStream_t st,
+                         unsigned *err = nullptr);
+// FP32 parity-paired folded rows (layout fl, fl.cg set) as a 3-D map
+// (column, k', m) whose load boxes take 32 columns (one 8-field group's E
+// and O) of box_rows orders m of one ring pair, unswizzled.
+bool tc_encode_pair_rows_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int Kh, int M, int box_rows);
 
 // One problem of a grouped longitude launch: the arguments of launch_r2c45
 // (in = x; outf = Fw or hi/lo) or launch_c2r45 (in = Gw, outf = y).
