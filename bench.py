@@ -254,6 +254,18 @@ def load_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def load_bf16_peak(sustained: bool):
+    """Dense bf16 tensor throughput (TFLOP/s): the burst figure for a kernel
+    timed alone, the sustained one for a kernel inside a long step."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained" if sustained else "bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return (1700.0 if sustained else 1900.0), "fallback"
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -799,7 +811,8 @@ def run_gpu(args):
 def run_gpu_block_grad(args):
     """Training step of the spectral block through the C ABI: y =
     sht_spectral_block(x, W), gx = sht_spectral_block_adjoint(gy, W), and
-    gW = spectral_filter_adjoint(ISHT^T(gy), W, SHT(x)) (xhat recomputed)."""
+    gW = sht_spectral_block_weight_grad(x, gy) (ISHT^T(gy) against the
+    recomputed SHT(x), per degree)."""
     world, rank, local = dist_setup(args.gpus)
     import torch
 
@@ -818,8 +831,6 @@ def run_gpu_block_grad(args):
     W = torch.from_numpy(inputs.filter_weights(5, L, C, C).astype(np.complex64)).to(dev)
     y = torch.empty_like(x)
     gx = torch.empty_like(x)
-    gyhat = torch.empty((Bm, C, L, L), dtype=torch.complex64, device=dev)
-    xhat = torch.empty_like(gyhat)
     gW = torch.empty_like(W)
     lib = shtgb._abi.lib()
     P = shtgb._ptr
@@ -830,9 +841,7 @@ def run_gpu_block_grad(args):
     def step(gy):
         check(lib.sht_spectral_block(plan.handle, P(x), P(W), P(y), Bm, C, C, st))
         check(lib.sht_spectral_block_adjoint(plan.handle, P(gy), P(W), P(gx), Bm, C, C, st))
-        check(lib.sht_inverse_adjoint(plan.handle, P(gy), P(gyhat), fields, st))
-        check(lib.sht_forward(plan.handle, P(x), P(xhat), fields, st))
-        check(lib.spectral_filter_adjoint(plan.handle, P(gyhat), P(W), P(xhat), None, P(gW), Bm, C, C, st))
+        check(lib.sht_spectral_block_weight_grad(plan.handle, P(x), P(gy), P(gW), Bm, C, C, st))
 
     # the cotangent: the block's own output (a field with the data's spectrum)
     check(lib.sht_spectral_block(plan.handle, P(x), P(W), P(y), Bm, C, C, st))
@@ -874,11 +883,18 @@ def run_gpu_block_grad(args):
     if dom == "filter_dw":
         flops = filter_dw_flops(Bm, C, C, L, L)
         achieved = flops / per_launch_s / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
-                    "peak_source": "FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops x 2070 MHz)",
-                    "traffic": None, "algorithmic_flops_per_launch": flops,
-                    "kernel_ms_per_launch": per_launch_s * 1e3, "share_of_step": dom_ms / ms_total}
+        if args.precision == "fp32":
+            roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
+                        "peak_source": "FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 flops x 2070 MHz)"}
+        else:
+            # bf16 MMAs (three per product in the split form); algorithmic
+            # flops count each complex multiply-add once
+            peak, kind = load_bf16_peak(sustained=True)
+            roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "peak_source": f"{kind} dense bf16 tensor throughput (sustained)"}
+        roofline.update({"traffic": None, "algorithmic_flops_per_launch": flops,
+                         "kernel_ms_per_launch": per_launch_s * 1e3, "share_of_step": dom_ms / ms_total})
     else:
         # per launch: the kernel's launches process different batches
         # (blocks of Bm members, API calls of all fields), all of the same size
@@ -922,7 +938,7 @@ def run_gpu_block_grad(args):
             "e2e": {"value": world * fields * e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * x.numel() * 4),
                     "d2h_bytes_per_step": int(x.numel() * 4 + W.numel() * 8), "steps": e2e_steps,
-                    "path": "the step's five C-ABI calls, x and gy copied in, gx and gW copied out"},
+                    "path": "the step's three C-ABI calls, x and gy copied in, gx and gW copied out"},
             "clocks": clk,
             "cpu_baseline": cpu_baseline_grad() if world == 1 and not args.no_cpu_baseline else None,
         }

@@ -228,6 +228,21 @@ sht_status_t sht_spectral_block_adjoint(sht_plan_t plan, const float *gy,
                                         const void *W, float *gx, int64_t Bm,
                                         int Cin, int Cout, void *stream);
 
+/* Weight gradient of the spectral block (Sec. B.8): the gradient of
+ * <gy, y> with respect to W for y = sht_spectral_block(x, W),
+ *   gW[l][o][i] = sum_{b, m <= l} ISHT^T(gy)[b][o][l][m] conj(SHT(x)[b][i][l][m]).
+ * x: float32 [Bm][Cin][nlat][nlon], gy: float32 [Bm][Cout][nlat][nlon],
+ * gW: complex64 [lmax][Cout][Cin] (overwritten; device memory).  Tensor-
+ * core plans compute both transforms into split (or single) bf16 l-major
+ * rows and contract them per degree on the tensor cores (the first call
+ * allocates a second rows buffer of the size of the plan's forward rows);
+ * FP32 plans run the API transforms and an FP32 CUDA-core contraction.
+ * Limits and errors as sht_spectral_block. */
+sht_status_t sht_spectral_block_weight_grad(sht_plan_t plan, const float *x,
+                                            const float *gy, void *gW,
+                                            int64_t Bm, int Cin, int Cout,
+                                            void *stream);
+
 /* Fused filter + inverse SHT: y = ISHT(filter(xhat, W)).  xhat: complex64
  * [Bm][Cin][lmax][mmax], y: float32 [Bm][Cout][nlat][nlon]. */
 sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,

@@ -21,7 +21,8 @@ from . import _abi
 from ._abi import ShtError
 
 __all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
-           "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "spectral_filter_inverse",
+           "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "sht_spectral_block_adjoint",
+           "sht_spectral_block_weight_grad", "spectral_filter_inverse",
            "SpectralBlock", "spectral_block", "Disco", "DiscoContraction", "disco_contraction", "diffusion_step", "SphericalDiffusion", "angular_psd", "zonal_psd",
            "spectral_crps", "spectral_crps_backward",
            "spectral_crps_loss", "SpectralCRPSLoss", "sht_forward_ad", "SHTForward", "spatial_crps", "ShtError"]
@@ -321,6 +322,22 @@ def sht_spectral_block_adjoint(plan: Plan, gy: torch.Tensor, W: torch.Tensor) ->
     return out
 
 
+def sht_spectral_block_weight_grad(plan: Plan, x: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
+    """The block's gradient in W: gW[l][o][i] = sum_{b, m <= l} ISHT^T(gy)[b][o][l][m]
+    conj(SHT(x)[b][i][l][m]); x [Bm, Cin, nlat, nlon], gy [Bm, Cout, nlat, nlon]
+    -> gW [lmax, Cout, Cin] complex64."""
+    x, lead, _ = _spatial_in(plan, x)
+    gy, glead, _ = _spatial_in(plan, gy, "gy")
+    if len(lead) != 2 or len(glead) != 2 or lead[0] != glead[0]:
+        raise ValueError("x must be [Bm, Cin, nlat, nlon] and gy [Bm, Cout, nlat, nlon]")
+    Bm, Cin = lead
+    Cout = glead[1]
+    gW = torch.empty((plan.lmax, Cout, Cin), dtype=torch.complex64, device=x.device)
+    _abi.check(_abi.lib().sht_spectral_block_weight_grad(plan.handle, _ptr(x), _ptr(gy), _ptr(gW), Bm, Cin, Cout,
+                                                         _stream(x)))
+    return gW
+
+
 def spectral_filter_inverse(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
     """y = ISHT(filter(xhat, W)); xhat [Bm, Cin, lmax, mmax] -> y [Bm, Cout, nlat, nlon]."""
     xhat, _, _ = _spectral_in(plan, xhat)
@@ -489,9 +506,10 @@ class SpectralBlock(torch.autograd.Function):
     The backward pass recomputes xhat = SHT(x) instead of storing the
     spectral activations:
       gyhat = ISHT^T(gy);  (gxhat, gW) = filter^T(gyhat);  gx = SHT^T(gxhat).
-    The input gradient runs as one adjoint block (sht_spectral_block_adjoint:
-    on the tensor cores for tensor-core plans); the weight gradient, when it
-    is needed, reduces gyhat against the recomputed xhat."""
+    The input gradient runs as one adjoint block (sht_spectral_block_adjoint)
+    and the weight gradient as one call that reduces gyhat against the
+    recomputed xhat per degree (sht_spectral_block_weight_grad); both on the
+    tensor cores for tensor-core plans."""
 
     @staticmethod
     def forward(ctx, x, W, plan):
@@ -506,11 +524,7 @@ class SpectralBlock(torch.autograd.Function):
         need_x, need_W = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         gy = gy.contiguous()
         gx = sht_spectral_block_adjoint(plan, gy, W) if need_x else None
-        gW = None
-        if need_W:
-            gyhat = sht_inverse_adjoint(plan, gy)
-            xhat = sht_forward(plan, x)
-            _, gW = spectral_filter_adjoint(plan, gyhat, W, xhat, need_gx=False, need_gW=True)
+        gW = sht_spectral_block_weight_grad(plan, x, gy) if need_W else None
         return gx, gW, None
 
 

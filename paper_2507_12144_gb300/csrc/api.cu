@@ -183,6 +183,8 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_roff);
   cudaFree(p->d_x_hi);
   cudaFree(p->d_x_lo);
+  cudaFree(p->d_g_hi);
+  cudaFree(p->d_g_lo);
   cudaFree(p->d_ftiles);
   cudaFree(p->d_s_hi);
   cudaFree(p->d_s_lo);
@@ -250,10 +252,13 @@ __nv_bfloat16 *data_lo(sht_plan_s *p, __nv_bfloat16 *lo) { return p->precision =
 // Column block of one member in the l-major rows of the fused block.
 int block_kx(int Cin) { return (2 * Cin + 7) / 8 * 8; }
 
-// l-major bf16 rows with members of cin channels in blocks of kx columns.
+// l-major bf16 rows with members of cin channels in blocks of kx columns;
+// T: the tensor-core view whose forward-row maps describe these rows (NULL:
+// the plan's own view and rows).
 struct RowsOut {
   __nv_bfloat16 *hi, *lo;
   int ldo, cin, kx;
+  const TcPlanView *T = nullptr;
 };
 
 // Forward transform (or the inverse adjoint) of B fields; the coefficients
@@ -291,7 +296,7 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
       if (e != cudaSuccess) return cuda_fail(e, "longitude analysis launch");
       e = traced(p, SHT_KERNEL_LEG_FWD, st, [&] {
         TcLegItem it{};
-        it.T = &p->tc;
+        it.T = rows_out && rows_out->T ? rows_out->T : &p->tc;
         it.tiles = p->d_fwd_tiles;
         it.ntiles = p->n_fwd_tiles;
         it.B = nb;
@@ -1020,6 +1025,93 @@ sht_status_t sht_spectral_block_adjoint(sht_plan_t p, const float *gy, const voi
     SHT_TRY(filter_body(p, p->d_spec_a, (const float2 *)W, p->d_spec_b, nb, Cin, Cout, 1, st));
     SHT_TRY(synthesis(p, p->d_spec_b, gxb, nb * Cin, st, true));
   }
+  return SHT_OK;
+}
+
+namespace {
+// The weight gradient's second rows buffer (ISHT^T(gy) rows) and its view:
+// a copy of the plan's tensor-core view with the forward-row maps re-encoded
+// for it.  Rows m > l stay zero (the forward writes l >= m only), as the
+// contraction requires.
+sht_status_t ensure_grad_rows(sht_plan_s *p, cudaStream_t st) {
+  if (p->d_g_hi) return SHT_OK;
+  const size_t xbytes = sizeof(__nv_bfloat16) * (size_t)p->L * p->M * p->ldx;
+  cudaError_t e;
+  if ((e = dev_alloc((void **)&p->d_g_hi, xbytes)) != cudaSuccess) return cuda_fail(e, "gradient rows allocation");
+  if ((e = dev_alloc((void **)&p->d_g_lo, xbytes)) != cudaSuccess) {
+    cudaFree(p->d_g_hi);
+    p->d_g_hi = nullptr;
+    return cuda_fail(e, "gradient rows allocation");
+  }
+  if ((e = cudaMemsetAsync(p->d_g_hi, 0, xbytes, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(p->d_g_lo, 0, xbytes, st)) != cudaSuccess)
+    return cuda_fail(e, "gradient rows memset");
+  TcPlanView &T = p->tc_g;
+  T = p->tc;
+  T.xrows_hi = p->d_g_hi;
+  if (!(tc_encode_2d(&T.x_hi, p->d_g_hi, p->ldx, (int64_t)p->L * p->M, 64, 128) &&
+        tc_encode_2d(&T.x_lo, p->d_g_lo, p->ldx, (int64_t)p->L * p->M, 64, 128) &&
+        tc_encode_lrows_bf16(&T.xo32_hi, p->d_g_hi, p->ldx, p->M, p->L, 32) &&
+        tc_encode_lrows_bf16(&T.xo32_lo, p->d_g_lo, p->ldx, p->M, p->L, 32) &&
+        tc_encode_lrows_bf16(&T.xo16_hi, p->d_g_hi, p->ldx, p->M, p->L, 16) &&
+        tc_encode_lrows_bf16(&T.xo16_lo, p->d_g_lo, p->ldx, p->M, p->L, 16)))
+    return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the gradient rows");
+  p->workspace_bytes += (int64_t)(2 * xbytes);
+  return SHT_OK;
+}
+}  // namespace
+
+sht_status_t sht_spectral_block_weight_grad(sht_plan_t p, const float *x, const float *gy, void *gW, int64_t Bm,
+                                            int Cin, int Cout, void *stream) {
+  NvtxRange nvtx_range("sht_spectral_block_weight_grad");
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, true));
+  SHT_TRY(check_ptr(gW, "gW"));
+  DeviceGuard g(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t LM = (int64_t)p->L * p->M;
+  if (Bm == 0) {
+    const cudaError_t e = cudaMemsetAsync(gW, 0, sizeof(float2) * (size_t)p->L * Cout * Cin, st);
+    return e == cudaSuccess ? SHT_OK : cuda_fail(e, "gradient memset");
+  }
+  SHT_TRY(check_ptr(x, "x"));
+  SHT_TRY(check_ptr(gy, "gy"));
+  const int64_t npix = (int64_t)p->nlat * p->nlon;
+  int64_t per = p->max_batch / std::max(Cin, Cout);
+  if (is_tc(p)) {
+    if (std::max(Cin, Cout) > p->max_channels)
+      return fail(SHT_ERR_INVALID_ARG, "max(Cin, Cout) exceeds the plan's max_channels");
+    SHT_TRY(ensure_grad_rows(p, st));
+    const int kxa = block_kx(Cout), kxb = block_kx(Cin);
+    per = std::min<int64_t>(per, p->ldx / std::max(kxa, kxb));
+    const bool split = p->precision == SHT_PREC_SPLIT_BF16;
+    for (int64_t b0 = 0; b0 < Bm; b0 += per) {
+      const int64_t nb = std::min(per, Bm - b0);
+      RowsOut rx{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, kxb, &p->tc};
+      SHT_TRY(analysis(p, x + b0 * Cin * npix, nullptr, nb * Cin, st, false, false, &rx));
+      RowsOut rg{p->d_g_hi, split ? p->d_g_lo : nullptr, p->ldx, Cout, kxa, &p->tc_g};
+      SHT_TRY(analysis(p, gy + b0 * Cout * npix, nullptr, nb * Cout, st, true, false, &rg));
+      const cudaError_t e = traced(p, SHT_KERNEL_FILTER_DW, st, [&] {
+        return launch_dw_tc(p->d_g_hi, split ? p->d_g_lo : nullptr, p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx,
+                            (float2 *)gW, p->L, p->M, (int)nb, Cin, Cout, kxa, kxb, b0 > 0 ? 1 : 0, p->d_err, st);
+      });
+      if (e != cudaSuccess) return cuda_fail(e, "weight gradient launch");
+    }
+    return SHT_OK;
+  }
+  // FP32 plans: the API transforms into the spectral buffers and the FP32
+  // contraction, accumulated over member chunks
+  for (int64_t b0 = 0; b0 < Bm; b0 += per) {
+    const int64_t nb = std::min(per, Bm - b0);
+    SHT_TRY(analysis(p, x + b0 * Cin * npix, p->d_spec_a, nb * Cin, st, false, true));
+    SHT_TRY(analysis(p, gy + b0 * Cout * npix, p->d_spec_b, nb * Cout, st, true, true));
+    const cudaError_t e = traced(p, SHT_KERNEL_FILTER_DW, st, [&] {
+      return launch_filter_dw(p->d_spec_b, p->d_spec_a, (float2 *)gW, p->L, p->M, nb, Cin, Cout, st, b0 > 0 ? 1 : 0);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "weight gradient launch");
+  }
+  (void)LM;
   return SHT_OK;
 }
 

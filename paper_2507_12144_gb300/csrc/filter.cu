@@ -122,7 +122,7 @@ constexpr int kDW = 32;
 constexpr int kDK = 32;
 __global__ void __launch_bounds__(kThreads)
 filter_dw_kernel(const float2 *__restrict__ gy, const float2 *__restrict__ x, float2 *__restrict__ gW, int L, int M,
-                 int64_t Bm, int Cin, int Cout) {
+                 int64_t Bm, int Cin, int Cout, int accumulate) {
   __shared__ float2 Gs[kDW][kDK + 1];
   __shared__ float2 Xs[kDW][kDK + 1];
   const int l = blockIdx.x;
@@ -172,7 +172,10 @@ filter_dw_kernel(const float2 *__restrict__ gy, const float2 *__restrict__ x, fl
 #pragma unroll
     for (int c = 0; c < 2; c++) {
       const int o = o0 + to * 2 + a, i = i0 + ti * 2 + c;
-      if (o < Cout && i < Cin) gW[((int64_t)l * Cout + o) * Cin + i] = acc[a][c];
+      if (o < Cout && i < Cin) {
+        float2 *w = gW + ((int64_t)l * Cout + o) * Cin + i;
+        *w = accumulate ? make_float2(w->x + acc[a][c].x, w->y + acc[a][c].y) : acc[a][c];
+      }
     }
 }
 
@@ -192,9 +195,9 @@ cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L, in
 }
 
 cudaError_t launch_filter_dw(const float2 *gy, const float2 *x, float2 *gW, int L, int M, int64_t Bm, int Cin,
-                             int Cout, cudaStream_t st) {
+                             int Cout, cudaStream_t st, int accumulate) {
   dim3 grid(L, (Cout + kDW - 1) / kDW, (Cin + kDW - 1) / kDW);
-  filter_dw_kernel<<<grid, kThreads, 0, st>>>(gy, x, gW, L, M, Bm, Cin, Cout);
+  filter_dw_kernel<<<grid, kThreads, 0, st>>>(gy, x, gW, L, M, Bm, Cin, Cout, accumulate);
   return cudaGetLastError();
 }
 

@@ -1610,6 +1610,19 @@ bool tc_encode_fold_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tc_encode_rows_mn_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_rows) {
+  auto enc = encoder();
+  if (!enc || !ptr || ldx % 64 != 0 || box_rows < 8 || box_rows > 256) return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)ldx, (cuuint64_t)M, (cuuint64_t)L};
+  const cuuint64_t gstr[2] = {(cuuint64_t)ldx * 2, (cuuint64_t)M * ldx * 2};
+  const cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr),
+             const_cast<cuuint64_t *>(gdim), const_cast<cuuint64_t *>(gstr), const_cast<cuuint32_t *>(box),
+             const_cast<cuuint32_t *>(es), CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool tc_encode_pair_rows_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int Kh, int M, int box_rows) {
   auto enc = encoder();
   if (!enc || !fl.cg || fl.sp != 16 || fl.sk % 4 != 0 || fl.sm != fl.sk * Kh || box_rows < 1 || box_rows > 256)

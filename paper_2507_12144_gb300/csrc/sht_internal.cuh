@@ -264,6 +264,19 @@ cudaError_t launch_c2r45(const float *Gw, float *y, int nlat, int nlon, int M, i
 // (column, k', m) whose load boxes take 32 columns (one 8-field group's E
 // and O) of box_rows orders m of one ring pair, unswizzled.
 bool tc_encode_pair_rows_f32(CUtensorMap *tm, const float *ptr, const FoldLayout &fl, int Kh, int M, int box_rows);
+// bf16 l-major rows [L][M][ldx] as a 3-D map (column, m, l) whose load
+// boxes take 64 columns of box_rows consecutive orders m of one degree l
+// (128-byte swizzle; orders past M read as zero).
+bool tc_encode_rows_mn_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, int M, int L, int box_rows);
+// Weight gradient of the filter from the split bf16 l-major rows of
+// g = ISHT^T(gy) (Cout channels per member, member blocks of kxa columns)
+// and x = SHT(x) (Cin channels, blocks of kxb), both with row stride ldx:
+// gW[l][o][i] (+)= sum_{b < nb, m <= l} g[b][o][l][m] conj(x[b][i][l][m]),
+// FP32 complex [L][Cout][Cin]; accumulate = 0 overwrites.  g_lo / x_lo NULL:
+// the single-part (BF16) operands.  Rows m > l of the buffers must be zero.
+cudaError_t launch_dw_tc(const __nv_bfloat16 *g_hi, const __nv_bfloat16 *g_lo, const __nv_bfloat16 *x_hi,
+                         const __nv_bfloat16 *x_lo, int ldx, float2 *gW, int L, int M, int nb, int Cin, int Cout,
+                         int kxa, int kxb, int accumulate, unsigned *err, cudaStream_t st);
 
 // One problem of a grouped longitude launch: the arguments of launch_r2c45
 // (in = x; outf = Fw or hi/lo) or launch_c2r45 (in = Gw, outf = y).
@@ -344,10 +357,11 @@ cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L,
                           int M, int64_t Bm, int Cin, int Cout, int adjoint,
                           cudaStream_t st);
 
-// Weight adjoint gW[l][o][i] = sum_{b, m <= l} gy[b][o][l][m] conj(x[b][i][l][m]).
+// Weight adjoint gW[l][o][i] (+)= sum_{b, m <= l} gy[b][o][l][m] conj(x[b][i][l][m])
+// (accumulate = 0 overwrites).
 cudaError_t launch_filter_dw(const float2 *gy, const float2 *x, float2 *gW,
                              int L, int M, int64_t Bm, int Cin, int Cout,
-                             cudaStream_t st);
+                             cudaStream_t st, int accumulate = 0);
 
 // FP64 generation of the folded FP32 table on the device.
 cudaError_t launch_table_gen_f32(float *table, const int64_t *off, int Khp,
@@ -399,6 +413,11 @@ struct sht_plan_s {
   int ldr = 0;                 // columns of the FP32 forward rows (in spec_b)
   int max_channels = 0;        // capacity of the real filter weights
   __nv_bfloat16 *d_x_hi = nullptr, *d_x_lo = nullptr;  // l-major forward rows [L M][ldx]
+  // second l-major rows buffer (the weight gradient's ISHT^T(gy) rows) and
+  // the tensor-core view whose forward-row maps describe it; allocated by
+  // the first weight-gradient call
+  __nv_bfloat16 *d_g_hi = nullptr, *d_g_lo = nullptr;
+  shtgb::TcPlanView tc_g{};
   void *d_ftiles = nullptr;    // filter tiles (l, m0)
   int n_ftiles = 0;
   __nv_bfloat16 *d_s_hi = nullptr, *d_s_lo = nullptr;  // bf16 internal rows [srows][ldcb]
