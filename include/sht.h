@@ -595,9 +595,17 @@ sht_status_t sht_disco_forward(sht_disco_t disco, const float *x, float *y,
 
 /* The transpose of sht_disco_forward (its backward): gy: float32
  * [C][K][nlat_out][nlon_out] -> gx: float32 [C][nlat_in][nlon_in]
- * (overwritten). */
+ * (overwritten).  On equal longitude grids whose nlon is a multiple of 4
+ * and of 3, 5 or 9 it runs by runs of consecutive longitude offsets, with
+ * the K gradient rows of each run staged in shared memory by bulk copies
+ * and waits bounded in time; a wait that runs out leaves gx unwritten and
+ * is reported by sht_disco_check.  Both pointers 16-byte aligned. */
 sht_status_t sht_disco_backward(sht_disco_t disco, const float *gy, float *gx,
                                 int64_t C, void *stream);
+
+/* Synchronise the handle's device and report (then clear) a timed-out wait
+ * of an earlier backward: SHT_ERR_TIMEOUT, else SHT_OK. */
+sht_status_t sht_disco_check(sht_disco_t disco);
 
 sht_status_t sht_disco_destroy(sht_disco_t disco);
 

@@ -762,6 +762,10 @@ class Disco:
         _abi.check(_abi.lib().sht_disco_backward(self._h, _ptr(gy), _ptr(gx), C, _stream(gy)))
         return gx
 
+    def check(self):
+        """Synchronise and raise ShtError if a backward's bounded wait ran out."""
+        _abi.check(_abi.lib().sht_disco_check(self._h))
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             h, self._h = self._h, None

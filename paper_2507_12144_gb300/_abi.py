@@ -93,6 +93,7 @@ SIGNATURES = {
     "sht_disco_info": ([_p, _ip, _i64p], _i),
     "sht_disco_forward": ([_p, _p, _p, _i64, _p], _i),
     "sht_disco_backward": ([_p, _p, _p, _i64, _p], _i),
+    "sht_disco_check": ([_p], _i),
     "sht_disco_destroy": ([_p], _i),
     "sht_diffusion_step": ([_p, _p, _i64, _i, _i, _d, _i, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                             ctypes.c_uint64, _p], _i),

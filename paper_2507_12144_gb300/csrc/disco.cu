@@ -19,13 +19,21 @@
 // each entry (other latitude, w', K values).  The kernels take an output
 // (input) latitude per block row and longitudes per thread, CB channels per
 // thread, so that each entry's K values, read once, serve CB channels; the
-// field loads of one entry are coalesced along the longitudes.
+// field loads of one entry are coalesced along the longitudes.  On equal
+// longitude grids the backward runs by runs instead: for one input latitude
+// and one channel, the entries of one output latitude h form runs of
+// consecutive w' (the cap meets a latitude ring in one arc), whose K gradient
+// rows are staged whole in shared memory by bulk copies (double-buffered),
+// and every thread keeps R consecutive input longitudes with a register
+// window that slides along the run, so that each staged value is read once
+// per thread and used R times.
 #include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
 
 #include "sht_internal.cuh"
+#include "tc_common.cuh"
 
 struct sht_disco_s {
   int device = 0;
@@ -38,6 +46,14 @@ struct sht_disco_s {
   int *d_row_b = nullptr;   // [nlat_in + 1]
   int2 *d_idx_b = nullptr;  // (h, w')
   float *d_val_b = nullptr; // [nnz][K]
+  // runs of the backward on equal longitude grids: per input latitude the
+  // entries of one output latitude h whose w' run through a, a + 1, ...
+  // (mod nlon) as (h, first entry, length, a); values in run order
+  int win_R = 0;            // outputs per thread of the run kernel (0: not used)
+  int *d_run_row = nullptr; // [nlat_in + 1]
+  int4 *d_runs = nullptr;
+  float *d_val_w = nullptr; // [nnz][K]
+  unsigned *d_err = nullptr; // error word of the run kernel's bounded waits
 };
 
 namespace shtgb {
@@ -124,6 +140,107 @@ __global__ void __launch_bounds__(kDiscoThreads)
     if (c0 + j < C) gx[(c0 + j) * plane + (int64_t)hi * Wi + wi] = acc[j];
 }
 
+// Backward by runs (nlon_in == nlon_out = W): block (input latitude hi,
+// channel c), W / R threads, thread t owns input longitudes v0 = R t ..
+// v0 + R - 1.  For a run (h, e0, n, a) entry j has w' = a + j (mod W) and
+// adds sum_k psi[e0 + j][k] gy[c][k][h][(v - a - j) mod W] to gx[c][hi][v].
+// Window slots: at step j, output r reads the value of index q = v0 + r -
+// a - j, kept in slot (r - j) mod R; after the step the value q = v0 - a -
+// j - 1 replaces the one output R - 1 no longer needs (slot (-j - 1) mod R).
+// R odd: the lanes' shared-memory reads, R words apart, meet distinct banks.
+constexpr int kRunThreadsMax = 256;
+
+template <int K, int R>
+__global__ void __launch_bounds__(kRunThreadsMax)
+    disco_bwd_run_kernel(const float *__restrict__ gy, float *__restrict__ gx, const int *__restrict__ run_row,
+                         const int4 *__restrict__ runs, const float *__restrict__ val, int Hi, int W, int Ho,
+                         unsigned *err) {
+  extern __shared__ __align__(16) float disco_smem[];
+  __shared__ uint64_t full[2];
+  const int hi = blockIdx.x;
+  const int64_t c = blockIdx.y;
+  const int t = threadIdx.x;
+  const int v0 = R * t;
+  const int64_t oplane = (int64_t)Ho * W;
+  const float *gc = gy + c * K * oplane;
+  const int r0 = run_row[hi], nr = run_row[hi + 1] - r0;
+  const uint32_t row_bytes = 4u * (uint32_t)W;
+  if (t == 0) {
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  // the K rows gy[c][k][h][.] of run i into buffer b
+  auto issue = [&](int i, int b) {
+    const int h = runs[r0 + i].x;
+    float *dst = disco_smem + (size_t)b * K * W;
+    tc::mbar_arrive_expect_tx(&full[b], (uint32_t)K * row_bytes);
+    for (int k = 0; k < K; k++) tc::bulk_load(dst + (size_t)k * W, gc + k * oplane + (int64_t)h * W, row_bytes, &full[b]);
+  };
+  if (t == 0) {
+    if (nr > 0) issue(0, 0);
+    if (nr > 1) issue(1, 1);
+  }
+  float acc[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) acc[r] = 0.f;
+  for (int i = 0; i < nr; i++) {
+    const int b = i & 1;
+    const bool ok = tc::mbar_wait(&full[b], (i >> 1) & 1, err);
+    if (!__syncthreads_and(ok)) {
+      // a wait gave up: let the copies still in flight land (bounded), leave
+      // gx unwritten (the error word reports it)
+      if (t == 0) {
+        tc::mbar_wait(&full[b], (i >> 1) & 1, nullptr, 100000000ull);
+        if (i + 1 < nr) tc::mbar_wait(&full[b ^ 1], ((i + 1) >> 1) & 1, nullptr, 100000000ull);
+      }
+      return;
+    }
+    const int4 run = runs[r0 + i];
+    const int e0 = run.y, n = run.z, a = run.w;
+    const float *S = disco_smem + (size_t)b * K * W;
+    float win[K][R];
+    // step 0: slot r holds index v0 + r - a
+    int q = v0 - a;
+    if (q < 0) q += W;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      int d = q + r;
+      if (d >= W) d -= W;
+#pragma unroll
+      for (int k = 0; k < K; k++) win[k][r] = S[k * W + d];
+    }
+    // the index loaded after step j: v0 - a - j - 1 (mod W)
+    int dn = q - 1;
+    if (dn < 0) dn += W;
+    for (int j0 = 0; j0 < n; j0 += R) {
+#pragma unroll
+      for (int u = 0; u < R; u++) {
+        const int j = j0 + u;
+        if (j < n) {
+          const float *pv = val + (int64_t)(e0 + j) * K;
+#pragma unroll
+          for (int k = 0; k < K; k++) {
+            const float p = __ldg(pv + k);
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r] = fmaf(p, win[k][(r - u + R) % R], acc[r]);
+          }
+#pragma unroll
+          for (int k = 0; k < K; k++) win[k][(R - 1 - u) % R] = S[k * W + dn];
+          dn = dn == 0 ? W - 1 : dn - 1;
+        }
+      }
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0 && i + 2 < nr) issue(i + 2, b);
+  }
+  float *out = gx + (c * Hi + hi) * (int64_t)W + v0;
+#pragma unroll
+  for (int r = 0; r < R; r++) out[r] = acc[r];
+}
+
 constexpr int kCB = 4;
 
 template <int K>
@@ -156,6 +273,47 @@ cudaError_t launch_bwd_k(const sht_disco_s *d, const float *gy, float *gx, int64
   return cudaSuccess;
 }
 
+template <int K, int R>
+cudaError_t launch_bwd_run(const sht_disco_s *d, const float *gy, float *gx, int64_t C, cudaStream_t st) {
+  const int W = d->nlon_in;
+  const size_t smem = sizeof(float) * 2 * (size_t)K * W;
+  cudaError_t e = cudaFuncSetAttribute((const void *)disco_bwd_run_kernel<K, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t per_c = (int64_t)K * d->nlat_out * W, per_x = (int64_t)d->nlat_in * W;
+  for (int64_t c = 0; c < C; c += 65535) {
+    const int64_t nc = std::min<int64_t>(C - c, 65535);
+    disco_bwd_run_kernel<K, R><<<dim3((unsigned)d->nlat_in, (unsigned)nc), W / R, smem, st>>>(
+        gy + c * per_c, gx + c * per_x, d->d_run_row, d->d_runs, d->d_val_w, d->nlat_in, W, d->nlat_out, d->d_err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int K>
+cudaError_t launch_bwd_any(const sht_disco_s *d, const float *gy, float *gx, int64_t C, cudaStream_t st) {
+  switch (d->win_R) {
+    case 9: return launch_bwd_run<K, (K > 17 ? 5 : 9)>(d, gy, gx, C, st);
+    case 5: return launch_bwd_run<K, 5>(d, gy, gx, C, st);
+    case 3: return launch_bwd_run<K, 3>(d, gy, gx, C, st);
+    default: return launch_bwd_k<K>(d, gy, gx, C, st);
+  }
+}
+
+// Outputs per thread of the run kernel for W longitudes and K basis
+// functions (odd, dividing W, at most kRunThreadsMax threads, a register
+// window of K R values), or 0 when it does not apply.
+int run_outputs_per_thread(int W, int K) {
+  if (W % 4 != 0) return 0;  // 16-byte rows for the bulk copies
+  if (sizeof(float) * 2 * (size_t)K * W > 227 * 1024) return 0;
+  for (int R : {9, 5, 3}) {
+    if (K > 17 && R == 9) continue;
+    if (W % R == 0 && W / R <= kRunThreadsMax) return R;
+  }
+  return 0;
+}
+
 // basis values at local coordinates (vartheta, varphi); false outside the cap
 bool basis_values(double vt, double vp, double tc, int n, double *out) {
   const double t = vt / tc;
@@ -182,6 +340,10 @@ void free_disco(sht_disco_s *d) {
   cudaFree(d->d_row_b);
   cudaFree(d->d_idx_b);
   cudaFree(d->d_val_b);
+  cudaFree(d->d_run_row);
+  cudaFree(d->d_runs);
+  cudaFree(d->d_val_w);
+  cudaFree(d->d_err);
   if (prev >= 0 && prev != d->device) cudaSetDevice(prev);
   delete d;
 }
@@ -270,6 +432,45 @@ sht_status_t sht_disco_create(sht_disco_t *out, int nlat_in, int nlon_in, int gr
       idx_b[dst] = make_int2(h, idx_f[e].y);
       for (int k = 0; k < K; k++) val_b[(size_t)dst * K + k] = val_f[(size_t)e * K + k];
     }
+  // runs of consecutive w' (mod nlon) per (input latitude, output latitude)
+  // for the backward on equal longitude grids
+  std::vector<int> run_row(nlat_in + 1, 0);
+  std::vector<int4> runs;
+  std::vector<float> val_w;
+  d->win_R = d->s == 1 ? run_outputs_per_thread(nlon_in, K) : 0;
+  if (d->win_R) {
+    const int W = nlon_in;
+    val_w.reserve(val_b.size());
+    for (int hp = 0; hp < nlat_in; hp++) {
+      for (int e0 = row_b[hp]; e0 < row_b[hp + 1];) {
+        const int h = idx_b[e0].x;
+        int e1 = e0;
+        while (e1 < row_b[hp + 1] && idx_b[e1].x == h) e1++;
+        const int n = e1 - e0;
+        auto wp = [&](int i) { return idx_b[e0 + i % n].y; };
+        // start after a gap in the circular order (none: the whole ring)
+        int start = 0;
+        if (n < W)
+          for (int i = 0; i < n; i++)
+            if ((wp(i + n - 1) + 1) % W != wp(i)) {
+              start = i;
+              break;
+            }
+        for (int i = 0; i < n;) {
+          int len = 1;
+          while (i + len < n && (wp(start + i + len - 1) + 1) % W == wp(start + i + len)) len++;
+          runs.push_back(make_int4(h, (int)(val_w.size() / K), len, wp(start + i)));
+          for (int q = 0; q < len; q++) {
+            const size_t src = (size_t)(e0 + (start + i + q) % n) * K;
+            val_w.insert(val_w.end(), val_b.begin() + src, val_b.begin() + src + K);
+          }
+          i += len;
+        }
+        e0 = e1;
+      }
+      run_row[hp + 1] = (int)runs.size();
+    }
+  }
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
   if (prev != device && cudaSetDevice(device) != cudaSuccess) {
@@ -282,6 +483,11 @@ sht_status_t sht_disco_create(sht_disco_t *out, int nlat_in, int nlon_in, int gr
   if (e == cudaSuccess) e = upload_vec(&d->d_row_b, row_b);
   if (e == cudaSuccess) e = upload_vec(&d->d_idx_b, idx_b);
   if (e == cudaSuccess) e = upload_vec(&d->d_val_b, val_b);
+  if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_run_row, run_row);
+  if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_runs, runs);
+  if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_val_w, val_w);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&d->d_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(d->d_err, 0, sizeof(unsigned));
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     free_disco(d);
@@ -312,10 +518,10 @@ static sht_status_t disco_run(sht_disco_t d, const float *in, float *out, int64_
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   switch (d->K) {
-    case 1: e = fwd ? launch_fwd_k<1>(d, in, out, C, st) : launch_bwd_k<1>(d, in, out, C, st); break;
-    case 7: e = fwd ? launch_fwd_k<7>(d, in, out, C, st) : launch_bwd_k<7>(d, in, out, C, st); break;
-    case 17: e = fwd ? launch_fwd_k<17>(d, in, out, C, st) : launch_bwd_k<17>(d, in, out, C, st); break;
-    default: e = fwd ? launch_fwd_k<31>(d, in, out, C, st) : launch_bwd_k<31>(d, in, out, C, st); break;
+    case 1: e = fwd ? launch_fwd_k<1>(d, in, out, C, st) : launch_bwd_any<1>(d, in, out, C, st); break;
+    case 7: e = fwd ? launch_fwd_k<7>(d, in, out, C, st) : launch_bwd_any<7>(d, in, out, C, st); break;
+    case 17: e = fwd ? launch_fwd_k<17>(d, in, out, C, st) : launch_bwd_any<17>(d, in, out, C, st); break;
+    default: e = fwd ? launch_fwd_k<31>(d, in, out, C, st) : launch_bwd_any<31>(d, in, out, C, st); break;
   }
   if (prev >= 0 && prev != d->device) cudaSetDevice(prev);
   return e == cudaSuccess ? SHT_OK : cuda_fail(e, fwd ? "disco_fwd_kernel" : "disco_bwd_kernel");
@@ -329,6 +535,23 @@ sht_status_t sht_disco_forward(sht_disco_t d, const float *x, float *y, int64_t 
 sht_status_t sht_disco_backward(sht_disco_t d, const float *gy, float *gx, int64_t C, void *stream) {
   NvtxRange nvtx_range("sht_disco_backward");
   return disco_run(d, gy, gx, C, stream, false);
+}
+
+sht_status_t sht_disco_check(sht_disco_t d) {
+  NvtxRange nvtx_range("sht_disco_check");
+  if (!d) return fail(SHT_ERR_INVALID_ARG, "DISCO handle is NULL");
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != d->device && cudaSetDevice(d->device) != cudaSuccess)
+    return fail(SHT_ERR_CUDA, "cannot select the device");
+  unsigned word = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&word, d->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word) e = cudaMemset(d->d_err, 0, sizeof(unsigned));
+  if (prev >= 0 && prev != d->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "DISCO error word read");
+  if (word) return fail(SHT_ERR_TIMEOUT, "a DISCO kernel's wait for its staged rows ran out of time");
+  return SHT_OK;
 }
 
 sht_status_t sht_disco_destroy(sht_disco_t d) {

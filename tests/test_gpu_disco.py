@@ -24,6 +24,9 @@ CASES = [
     (16, 32, "gauss", 16, 32, "gauss", 1, 0.3, 9),
     (91, 180, "equiangular_cc", 91, 180, "equiangular_cc", 1, 0.12, 2),  # two longitude blocks per row
     (61, 120, "equiangular_cc", 31, 60, "gauss", 2, 0.15, 2),
+    (45, 180, "gauss", 45, 180, "gauss", 3, 0.2, 3),  # backward by runs: 9 longitudes per thread
+    (30, 60, "equiangular_cc", 30, 60, "equiangular_cc", 2, 0.35, 4),  # by runs: 5 per thread, whole rings
+    (24, 36, "gauss", 24, 36, "gauss", 4, 0.5, 2),  # by runs: K = 31, 3 per thread
 ]
 
 
@@ -64,6 +67,7 @@ def test_disco_forward_and_backward_match_oracle(case):
     lhs = float(np.sum(y.astype(np.float64) * gy))
     rhs = float(np.sum(x.astype(np.float64) * gx))
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + np.linalg.norm(y) * np.linalg.norm(gy) * 1e-3)
+    d.check()
     d.close()
 
 
