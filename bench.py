@@ -793,22 +793,51 @@ def run_gpu(args):
                     "path": "sht_pipe_block, 2 staging slots, pinned host buffers"},
             "clocks": clk,
         }
+        # the whole step against the fused minimum: fields in, fields out and
+        # the weights, each moved once
+        fused = float(x.numel() * 4 + y.numel() * 4 + W.numel() * 8)
+        line["step_roofline"] = {"fused_minimum_bytes": fused, "achieved": fused / (ms_step * 1e-3) / 1e9,
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": fused / (ms_step * 1e-3) / 1e9 / peak,
+                                 "peak_source": f"{peak_kind} HBM copy bandwidth"}
         if fp32_side is not None:
             line["fp32_form"] = fp32_side
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_line(args.cpu_seconds)
         else:
             line["cpu_baseline"] = None
+    plan.close()
+    if rank == 0 and world == 1 and not args.no_side_workloads:
+        line["side_workloads"] = side_workloads(args)
+    if rank == 0:
         print(json.dumps(line))
         sys.stdout.flush()
-    plan.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 
 
-def run_gpu_block_grad(args):
+def side_workloads(args) -> dict:
+    """Short runs of the batched form and of the block's training step on
+    the same GPU, condensed: each is also a workload of its own
+    (--workload batched / block_grad) with the full line."""
+    import copy
+    out = {}
+    for name, fn, steps in (("batched", run_gpu_batched, 10), ("block_grad", run_gpu_block_grad, 5)):
+        a = copy.copy(args)
+        a.steps, a.warmup, a.no_cpu_baseline, a.e2e_steps = steps, 3, True, 3
+        r = fn(a, emit=False)
+        rl = r["roofline"]
+        out[name] = {"metric": r["metric"], "value": r["value"], "unit": r["unit"], "ms_per_step": r["ms_per_step"],
+                     "steps": steps, "warmup": 3, "workload": r["config"]["workload"],
+                     "roofline": {k: rl.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac")},
+                     "kernels_ms": {k: v["ms_per_launch"] for k, v in r["kernels"].items()},
+                     "e2e": r["e2e"]["value"]}
+    return out
+
+
+def run_gpu_block_grad(args, emit: bool = True):
     """Training step of the spectral block through the C ABI: y =
     sht_spectral_block(x, W), gx = sht_spectral_block_adjoint(gy, W), and
     gW = sht_spectral_block_weight_grad(x, gy) (ISHT^T(gy) against the
@@ -942,13 +971,14 @@ def run_gpu_block_grad(args):
             "clocks": clk,
             "cpu_baseline": cpu_baseline_grad() if world == 1 and not args.no_cpu_baseline else None,
         }
-        print(json.dumps(line))
-        sys.stdout.flush()
+        if emit:
+            print(json.dumps(line))
+            sys.stdout.flush()
     plan.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    return 0
+    return 0 if emit else line
 
 
 def cpu_baseline_grad(target_s: float = 12.0) -> dict:
@@ -986,7 +1016,7 @@ def cpu_baseline_grad(target_s: float = 12.0) -> dict:
                       f"of the step; {t_tr + t_f:.1f} s"}
 
 
-def run_gpu_batched(args):
+def run_gpu_batched(args, emit: bool = True):
     world, rank, local = dist_setup(args.gpus)
     import torch
 
@@ -1095,8 +1125,9 @@ def run_gpu_batched(args):
             "clocks": clk,
             "cpu_baseline": cpu_baseline_batched() if world == 1 and not args.no_cpu_baseline else None,
         }
-        print(json.dumps(line))
-        sys.stdout.flush()
+        if emit:
+            print(json.dumps(line))
+            sys.stdout.flush()
     fb.close()
     ib.close()
     for p in plans:
@@ -1104,7 +1135,7 @@ def run_gpu_batched(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    return 0
+    return 0 if emit else line
 
 
 def run_gpu_scores(args):
@@ -1499,6 +1530,8 @@ def main(argv=None):
                          "16-member ensemble; block_grad: the block's training step (forward, input and "
                          "weight gradients) at 360x720 Gauss with 4 x 256 channels")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
+    ap.add_argument("--no-side-workloads", action="store_true",
+                    help="block workload: skip the short batched and training-step runs attached to the line")
     ap.add_argument("--no-fp32-side", action="store_true",
                     help="skip timing the plain FP32 form beside a tensor-core precision")
     ap.add_argument("--table-source", choices=["streamed", "recurrence", "mixed"], default="streamed",

@@ -1,9 +1,11 @@
 // Batched transforms over several grids: the items' kernels are recorded
-// once into a CUDA graph — one grouped longitude launch, one persistent
-// Legendre launch over the tiles of every item (tensor cores) or one grouped
-// tile grid (FP32), one grouped epilogue launch — and replayed per run.  The
-// launch shape of the Legendre step (column tile width, item order) is
-// chosen by timing candidates at creation, optionally through a text cache.
+// once into a CUDA graph — the longitude step (one grouped launch, or one
+// persistent launch per item), one persistent Legendre launch over the
+// tiles of every item (tensor cores) or one grouped tile grid (FP32), one
+// grouped epilogue launch — and replayed per run.  The launch shape
+// (Legendre column tile width, item order and pipeline stages; grouped or
+// per-item longitude launches) is chosen by timing candidates at creation,
+// optionally through a text cache.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +24,8 @@ constexpr int kMaxItems = 8;
 struct Shape {
   int nt_cap = 256;  // widest column tile of the tensor-core Legendre launch
   int order = 0;     // 0: items as given, 1: most expensive tiles first
+  int stages = 0;    // Legendre pipeline stages (0: as many as fit)
+  int fft = 0;       // longitude step: 0 one grouped launch, 1 one launch per item
 };
 
 struct BatchProfile {
@@ -102,9 +106,9 @@ bool all_fft45(const sht_batch_s *b) {
 
 // ---- the stages -----------------------------------------------------------
 
-cudaError_t stage_r2c(sht_batch_s *b, cudaStream_t st) {
+cudaError_t stage_r2c(sht_batch_s *b, const Shape &sh, cudaStream_t st) {
   const int n = (int)b->items.size();
-  if (all_fft45(b)) {
+  if (all_fft45(b) && sh.fft == 0) {
     Fft45Item it[kMaxItems];
     for (int i = 0; i < n; i++) {
       sht_plan_s *p = b->plans[i];
@@ -143,9 +147,9 @@ cudaError_t stage_r2c(sht_batch_s *b, cudaStream_t st) {
   return cudaSuccess;
 }
 
-cudaError_t stage_c2r(sht_batch_s *b, cudaStream_t st) {
+cudaError_t stage_c2r(sht_batch_s *b, const Shape &sh, cudaStream_t st) {
   const int n = (int)b->items.size();
-  if (all_fft45(b)) {
+  if (all_fft45(b) && sh.fft == 0) {
     Fft45Item it[kMaxItems];
     for (int i = 0; i < n; i++) {
       sht_plan_s *p = b->plans[i];
@@ -192,7 +196,7 @@ cudaError_t stage_legendre(sht_batch_s *b, const Shape &sh, cudaStream_t st) {
         q.ldc = p->ldc;
       }
     }
-    return launch_leg_tc_group(inverse ? 1 : 0, it, n, TcLaunch{}, st);
+    return launch_leg_tc_group(inverse ? 1 : 0, it, n, TcLaunch{0, sh.stages}, st);
   }
   F32LegItem it[kMaxItems];
   for (int j = 0; j < n; j++) {
@@ -268,17 +272,23 @@ void stage_names(sht_batch_s *b) {
 
 cudaError_t run_stage(sht_batch_s *b, int k, const Shape &sh, cudaStream_t st) {
   const char *name = b->stages[k];
-  if (!strcmp(name, "r2c")) return stage_r2c(b, st);
+  if (!strcmp(name, "r2c")) return stage_r2c(b, sh, st);
   if (!strcmp(name, "leg_fwd") || !strcmp(name, "leg_inv")) return stage_legendre(b, sh, st);
   if (!strcmp(name, "zero")) return stage_zero(b, st);
   if (!strcmp(name, "finalize")) return stage_finalize(b, st);
   if (!strcmp(name, "pack")) return stage_pack(b, st);
-  return stage_c2r(b, st);
+  return stage_c2r(b, sh, st);
 }
 
 int legendre_stage(const sht_batch_s *b) {
   for (size_t k = 0; k < b->stages.size(); k++)
     if (!strncmp(b->stages[k], "leg_", 4)) return (int)k;
+  return 0;
+}
+
+int longitude_stage(const sht_batch_s *b) {
+  for (size_t k = 0; k < b->stages.size(); k++)
+    if (!strcmp(b->stages[k], "r2c") || !strcmp(b->stages[k], "c2r")) return (int)k;
   return 0;
 }
 
@@ -312,11 +322,14 @@ bool cache_lookup(const char *path, const std::string &key, Shape &sh) {
     if (!tab) continue;
     *tab = 0;
     if (key != line) continue;
-    int cap = 0, order = 0;
-    if (sscanf(tab + 1, "%d %d", &cap, &order) == 2 && (cap == 64 || cap == 128 || cap == 256) &&
-        (order == 0 || order == 1)) {
+    int cap = 0, order = 0, stages = 0, fft = 0;
+    const int got = sscanf(tab + 1, "%d %d %d %d", &cap, &order, &stages, &fft);
+    if (got >= 2 && (cap == 64 || cap == 128 || cap == 256) && (order == 0 || order == 1) && stages >= 0 &&
+        stages <= 16 && (fft == 0 || fft == 1)) {
       sh.nt_cap = cap;
       sh.order = order;
+      sh.stages = got >= 3 ? stages : 0;
+      sh.fft = got >= 4 ? fft : 0;
       found = true;  // the last entry of a key wins
     }
   }
@@ -328,13 +341,12 @@ void cache_store(const char *path, const std::string &key, const Shape &sh, doub
   std::lock_guard<std::mutex> lock(g_cache_mutex);
   FILE *f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s\t%d %d %.1f\n", key.c_str(), sh.nt_cap, sh.order, us);
+  fprintf(f, "%s\t%d %d %d %d %.1f\n", key.c_str(), sh.nt_cap, sh.order, sh.stages, sh.fft, us);
   fclose(f);
 }
 
-// Median device time of the Legendre stage under one shape (us).
-cudaError_t time_shape(sht_batch_s *b, const Shape &sh, cudaStream_t st, double &us) {
-  const int k = legendre_stage(b);
+// Median device time of stage k under one shape (us).
+cudaError_t time_stage(sht_batch_s *b, int k, const Shape &sh, cudaStream_t st, double &us) {
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);
   if (e != cudaSuccess) return e;
@@ -453,36 +465,56 @@ sht_status_t sht_batch_create(sht_batch_t *out, const sht_batch_item *items, int
   if (o.tune_cache && cache_lookup(o.tune_cache, key, best)) {
     snprintf(how, sizeof(how), "cached");
   } else if (o.tune) {
+    // the Legendre stage over (column tile, item order, pipeline stages),
+    // then the longitude stage over (grouped, per item) with the best
+    // Legendre shape; the two stages do not interact
     std::vector<Shape> cand;
     const int caps_tc[3] = {256, 128, 64};
     for (int order = 0; order < 2; order++) {
       if (b->tc) {
-        for (int cap : caps_tc) cand.push_back(Shape{cap, order});
+        for (int cap : caps_tc)
+          for (int stages : {0, 4}) cand.push_back(Shape{cap, order, stages, 0});
       } else {
-        cand.push_back(Shape{256, order});
+        cand.push_back(Shape{256, order, 0, 0});
       }
     }
-    double best_us = 1e300;
+    double best_us = 1e300, best_fft_us = 0.0;
+    int tried = 0;
+    auto fail_tuning = [&](cudaError_t err) {
+      cudaStreamDestroy(ts);
+      return bail(err, "tuning run");
+    };
     for (const Shape &sh : cand) {
       double us = 0.0;
-      e = time_shape(b, sh, ts, us);
-      if (e != cudaSuccess) {
-        cudaStreamDestroy(ts);
-        return bail(e, "tuning run");
-      }
+      if ((e = time_stage(b, legendre_stage(b), sh, ts, us)) != cudaSuccess) return fail_tuning(e);
+      tried++;
       if (us < best_us) {
         best_us = us;
         best = sh;
       }
     }
-    snprintf(how, sizeof(how), "tuned over %d shapes, %.1f us", (int)cand.size(), best_us);
-    if (o.tune_cache) cache_store(o.tune_cache, key, best, best_us);
+    if (all_fft45(b)) {
+      double us_mode[2] = {0.0, 0.0};
+      for (int mode = 0; mode < 2; mode++) {
+        Shape sh = best;
+        sh.fft = mode;
+        if ((e = time_stage(b, longitude_stage(b), sh, ts, us_mode[mode])) != cudaSuccess) return fail_tuning(e);
+        tried++;
+      }
+      best.fft = us_mode[1] < us_mode[0] ? 1 : 0;
+      best_fft_us = us_mode[best.fft];
+    }
+    snprintf(how, sizeof(how), "tuned over %d shapes, legendre %.1f us, longitude %.1f us", tried, best_us,
+             best_fft_us);
+    if (o.tune_cache) cache_store(o.tune_cache, key, best, best_us + best_fft_us);
   } else {
     snprintf(how, sizeof(how), "default");
   }
   b->shape = best;
-  char desc[320];
-  snprintf(desc, sizeof(desc), "legendre: tile<=%d, order=%s; %s", best.nt_cap, best.order ? "cost" : "given", how);
+  char desc[400];
+  snprintf(desc, sizeof(desc), "legendre: tile<=%d, order=%s, stages=%s; longitude: %s; %s", best.nt_cap,
+           best.order ? "cost" : "given", best.stages ? std::to_string(best.stages).c_str() : "max",
+           best.fft ? "per item" : "grouped", how);
   b->how = desc;
 
   // record the graph

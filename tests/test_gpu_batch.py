@@ -102,16 +102,21 @@ def test_batched_forward_matches_oracle(shtgb, mix, prec):
     assert batch.stages == ["r2c", "leg_fwd", "zero" if prec == "fp32" else "finalize"]
 
 
-@pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("mix", [MIX45, MIXED], ids=["fft45", "mixed"])
-def test_batched_inverse_matches_oracle(shtgb, mix, prec):
+def _inverse_items(shtgb, mix, prec, seed0):
     items, refs = [], []
     for k, (nlat, nlon, grid, L, M, n) in enumerate(mix):
-        coeffs, ref = inverse_batch(nlat, nlon, grid, L, M, n, min(n, 3), 7100 + k)
+        coeffs, ref = inverse_batch(nlat, nlon, grid, L, M, n, min(n, 3), seed0 + k)
         coeffs[:, ~triangle_mask(L, M)] = 3.0 - 1.0j  # ignored
         plan = _plan(shtgb, nlat, nlon, grid, L, M, prec, max_batch=n)
         items.append((plan, _gpu(coeffs, torch.complex64), torch.empty((n, nlat, nlon), device="cuda")))
         refs.append(ref)
+    return items, refs
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mix", [MIX45, MIXED], ids=["fft45", "mixed"])
+def test_batched_inverse_matches_oracle(shtgb, mix, prec):
+    items, refs = _inverse_items(shtgb, mix, prec, 7100)
     batch = shtgb.Batch(items, "inverse")
     batch.run()
     torch.cuda.synchronize()
@@ -141,10 +146,12 @@ def test_batch_tuning_cache_and_profile(shtgb, tmp_path):
     cache = str(tmp_path / "tune.txt")
     items, refs = _forward_items(shtgb, MIX45, "split_bf16", 7300)
     b1 = shtgb.Batch(items, "forward", tune_cache=cache)
-    assert "tuned over 6 shapes" in b1.describe()
+    # 3 column tiles x 2 item orders x 2 stage counts, then 2 longitude modes
+    assert "tuned over 14 shapes" in b1.describe()
     with open(cache) as f:
         lines = f.read().splitlines()
     assert len(lines) == 1 and "\t" in lines[0]
+    assert len(lines[0].split("\t")[1].split()) == 5  # cap, order, stages, longitude mode, us
     b1.close()
     b2 = shtgb.Batch(items, "forward", tune_cache=cache, profile=True)
     assert "cached" in b2.describe()
@@ -216,3 +223,31 @@ def test_full_uneven_mix(shtgb, prec):
         base = oracle.sht_inverse(ref[:nb], *args)
         chain = 2 * BF16_STAGE if is_bf16(prec) else 2 * TOL[prec]
         assert per_field_spatial_err(u[:nb].cpu().numpy(), base).max() <= chain, plan.nlat
+
+
+@pytest.mark.parametrize("direction", ["forward", "inverse"])
+def test_batch_longitude_modes_agree_bitwise(shtgb, tmp_path, direction):
+    """The grouped longitude launch and the per-item persistent launches
+    (chosen through a cache entry) compute the same bits."""
+    cache = str(tmp_path / "tune.txt")
+    if direction == "forward":
+        items, refs = _forward_items(shtgb, MIX45, "split_bf16", 7400)
+    else:
+        items, refs = _inverse_items(shtgb, MIX45, "split_bf16", 7410)
+    b = shtgb.Batch(items, direction, tune_cache=cache)
+    b.close()
+    with open(cache) as f:
+        key, vals = f.read().splitlines()[0].split("\t")
+    cap, order, stages, _, us = vals.split()
+    outs = []
+    for mode in (0, 1):
+        with open(cache, "w") as f:
+            f.write(f"{key}\t{cap} {order} {stages} {mode} {us}\n")
+        b = shtgb.Batch(items, direction, tune_cache=cache)
+        assert ("per item" if mode else "grouped") in b.describe()
+        b.run()
+        torch.cuda.synchronize()
+        outs.append([y.clone() for (_, _, y) in items])
+        b.close()
+    for a, c in zip(*outs):
+        assert torch.equal(a, c)
