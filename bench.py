@@ -85,14 +85,15 @@ GRAD_METRIC = ("spectral-block training field-transforms/s (forward + input and 
                "Gauss, lmax=360, 4 members x 256 channels; roofline fraction")
 
 
-def grad_config(precision: str) -> dict:
+def grad_config(precision: str, members: int = GRAD_MEMBERS) -> dict:
+    gb = members * GRAD_CHANNELS * GRAD_NLAT * GRAD_NLON * 4 / 1e9
     return {
         "workload": "spectral block forward + input gradient (adjoint block) + weight gradient, 360x720 Gauss, "
-                    "lmax=mmax=360, 4 members x 256 channels, W[360][256][256] complex",
+                    f"lmax=mmax=360, {members} members x 256 channels, W[360][256][256] complex",
         "nlat": GRAD_NLAT, "nlon": GRAD_NLON, "grid": GRAD_GRID, "lmax": GRAD_L, "mmax": GRAD_L,
-        "members": GRAD_MEMBERS, "channels": GRAD_CHANNELS, "precision": precision,
+        "members": members, "channels": GRAD_CHANNELS, "precision": precision,
         "spectrum": "(l+1)^-3 angular power, seeded; cotangent: the block output",
-        "l2": "inputs larger than L2: 1.06 GB of fields in per step",
+        "l2": f"inputs larger than L2: {gb:.2f} GB of fields in per step",
         "parallelism": "replicas",
     }
 
@@ -850,7 +851,7 @@ def run_gpu_block_grad(args, emit: bool = True):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    Bm, C, L = GRAD_MEMBERS, GRAD_CHANNELS, GRAD_L
+    Bm, C, L = args.grad_members, GRAD_CHANNELS, GRAD_L
     fields = Bm * C
     plan = shtgb.Plan(GRAD_NLAT, GRAD_NLON, GRAD_GRID, L, L, precision=args.precision, device=dev,
                       max_batch=fields, max_channels=C, table_source=args.table_source)
@@ -962,7 +963,7 @@ def run_gpu_block_grad(args, emit: bool = True):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
             "data": "synthetic: seeded (l+1)^-3 spectra synthesised on the GPU, random-init filter",
-            "config": grad_config(args.precision), "roofline": roofline, "kernels": breakdown,
+            "config": grad_config(args.precision, Bm), "roofline": roofline, "kernels": breakdown,
             "gpu_launches": launches,
             "e2e": {"value": world * fields * e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * x.numel() * 4),
@@ -1530,6 +1531,8 @@ def main(argv=None):
                          "16-member ensemble; block_grad: the block's training step (forward, input and "
                          "weight gradients) at 360x720 Gauss with 4 x 256 channels")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default="split_bf16")
+    ap.add_argument("--grad-members", type=int, default=GRAD_MEMBERS,
+                    help="block_grad workload: members (the workload is 4; fewer for small profiling runs)")
     ap.add_argument("--no-side-workloads", action="store_true",
                     help="block workload: skip the short batched and training-step runs attached to the line")
     ap.add_argument("--no-fp32-side", action="store_true",

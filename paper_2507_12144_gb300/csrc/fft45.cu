@@ -873,8 +873,10 @@ cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl
   dim3 grid((B + kFB - 1) / kFB, (Kh + NPAIR - 1) / NPAIR);
   cudaError_t e;
   constexpr size_t psmem = r2c_pipe_smem<P>();
-  if (aligned16(x) && psmem <= (size_t)max_smem_optin()) {
-    // persistent form: the rows arrive by 16-byte-aligned bulk copies
+  // persistent form (the rows arrive by 16-byte-aligned bulk copies) at
+  // nlon = 1440 only: on the shorter rows its 8 warps per SM lose to the
+  // 16 of the non-persistent kernel (6-16 % slower at nlon = 180 .. 720)
+  if (P == 32 && aligned16(x) && psmem <= (size_t)max_smem_optin()) {
     e = cudaFuncSetAttribute((const void *)r2c45_pipe_kernel<P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)psmem);
     if (e != cudaSuccess) return e;

@@ -36,6 +36,7 @@ SHAPES = [
     (181, 360, "equiangular_cc", 180, 180, 3),   # several row tiles
     (46, 90, "gauss", 46, 46, 1),                # M = nlon/2 + 1, single field
     (361, 720, "equiangular_cc", 360, 360, 10),  # 0.5 degree grid, 16-lane transforms
+    (91, 180, "gauss", 91, 91, 3),               # M = nlon/2 + 1 on a four-step grid, partial field group
 ]
 
 
