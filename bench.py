@@ -178,7 +178,7 @@ def algorithmic_bytes(kernel: str, fields: int, members: int, cin: int, cout: in
     if kernel == "filter":
         return members * (cin + cout) * tri + LMAX_ * cout * cin * 8.0
     if kernel == "filter_prep":
-        return LMAX_ * cout * cin * 8.0
+        return 2.0 * LMAX_ * cout * cin * 8.0  # W read, its conj-transpose written
     if kernel == "filter_dw":
         return members * (cin + cout) * tri + LMAX_ * cout * cin * 8.0
     if kernel == "finalize":
@@ -211,7 +211,7 @@ def kernel_sources(kernel: str, precision: str):
         "leg_fwd": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/legendre_f32.cu"],
         "leg_inv": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/legendre_f32.cu"],
         "filter": ["paper_2507_12144_gb300/csrc/legendre_tc.cu" if tc else "paper_2507_12144_gb300/csrc/filter.cu"],
-        "filter_prep": ["paper_2507_12144_gb300/csrc/legendre_tc.cu"],
+        "filter_prep": ["paper_2507_12144_gb300/csrc/filter.cu"],
         "crps": ["paper_2507_12144_gb300/csrc/scores.cu"],
         "diffusion": ["paper_2507_12144_gb300/csrc/diffusion.cu"],
         "psd": ["paper_2507_12144_gb300/csrc/scores.cu"],

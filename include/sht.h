@@ -626,8 +626,8 @@ typedef enum {
   SHT_KERNEL_LEG_INV = 5,    /* inverse Legendre contraction              */
   SHT_KERNEL_C2R = 6,        /* longitude synthesis (inverse FFT)         */
   SHT_KERNEL_PACK = 7,       /* API coefficients -> internal bf16 rows    */
-  SHT_KERNEL_FILTER_PREP = 8, /* unused (the filter forms its weights on
-                                 chip); kept so the numbering is stable   */
+  SHT_KERNEL_FILTER_PREP = 8, /* weight preparation: the conj-transposed
+                                 W of an adjoint block with large W       */
   SHT_KERNEL_FINALIZE = 9,   /* FP32 l-major rows -> API xhat (+ zeros)   */
   SHT_KERNEL_COUNT = 10
 } sht_kernel_t;

@@ -185,6 +185,7 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_x_lo);
   cudaFree(p->d_g_hi);
   cudaFree(p->d_g_lo);
+  cudaFree(p->d_wt);
   cudaFree(p->d_ftiles);
   cudaFree(p->d_s_hi);
   cudaFree(p->d_s_lo);
@@ -400,6 +401,10 @@ sht_status_t filter_body(sht_plan_s *p, const float2 *x, const float2 *W, float2
 // inverse's mode weights and no latitude weights, the filter with
 // conj(W[l][i][o]), the synthesis with the latitude weights); x then has
 // Cin = the forward's Cout channels, W is the forward's [L][Cin][Cout].
+// Weights above this size (bytes) go through a conj-transposed copy in the
+// adjoint block (the strided reads of the on-chip adjoint builder then miss L2).
+constexpr size_t kAdjointTransposeBytes = size_t(64) << 20;
+
 sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, int64_t nb, int Cin, int Cout,
                       cudaStream_t st, bool adjoint = false) {
   // members' columns packed at kx = 2 Cin rounded to 8: the 64-column K
@@ -417,9 +422,30 @@ sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, in
       !tc_encode_2d(&ta_lo, split ? p->d_x_lo : p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx))
     return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
   cudaError_t e;
+  // the adjoint reads conj(W[l][i][o]) along i for each o: strided, which
+  // costs little while W sits in L2; a larger W is conj-transposed once per
+  // call so that the filter reads it as forward weights, row by row
+  const float2 *Wf = (const float2 *)W;
+  int wadj = adjoint ? 1 : 0;
+  const size_t wbytes = sizeof(float2) * (size_t)p->L * Cin * Cout;
+  if (adjoint && wbytes > kAdjointTransposeBytes) {
+    if (p->wt_bytes < wbytes) {
+      cudaFree(p->d_wt);
+      p->d_wt = nullptr;
+      p->wt_bytes = 0;
+      if ((e = dev_alloc((void **)&p->d_wt, wbytes)) != cudaSuccess) return cuda_fail(e, "adjoint weight allocation");
+      p->wt_bytes = wbytes;
+    }
+    // W is [L][Cin][Cout] in this call's channel names (the forward's [L][Cout][Cin])
+    e = traced(p, SHT_KERNEL_FILTER_PREP, st,
+               [&] { return launch_transpose_conj((const float2 *)W, p->d_wt, p->L, Cin, Cout, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "weight transpose launch");
+    Wf = p->d_wt;
+    wadj = 0;
+  }
   e = traced(p, SHT_KERNEL_FILTER, st, [&] {
-    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, ta_hi, ta_lo, (const float2 *)W, p->d_s_hi,
-                            data_lo(p, p->d_s_lo), p->ldcb, kx, nwr, (int)nb, Cin, Cout, adjoint ? 1 : 0, st);
+    return launch_filter_tc(p->tc, p->d_ftiles, p->n_ftiles, ta_hi, ta_lo, Wf, p->d_s_hi, data_lo(p, p->d_s_lo),
+                            p->ldcb, kx, nwr, (int)nb, Cin, Cout, wadj, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "filter launch");
   return synthesis_rows(p, y, (int)(nb * Cout), st, adjoint);

@@ -309,7 +309,8 @@ struct OutBF16 {
 // 45 q + r tracked without divisions).
 template <int P, class Out>
 __device__ __forceinline__ void r2c45_emit(int bx, int by, const float2 *bufs, Out out, int nlat, int M, int B,
-                                           FoldLayout fl, const float *__restrict__ ring_scale, int inverse_weights) {
+                                           FoldLayout fl, const float *__restrict__ ring_scale, int inverse_weights,
+                                           int tid) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
   constexpr int BUF = seq_pitch<P>();
@@ -317,7 +318,7 @@ __device__ __forceinline__ void r2c45_emit(int bx, int by, const float2 *bufs, O
   constexpr int kMStep = kThreads / kPairs;  // 64
   const int Kh = (nlat + 1) / 2;
   const int b0 = bx * kFB;
-  const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+  const int f2 = tid % kPairs, m0 = tid / kPairs;
   const int fa = 2 * f2;
   if (b0 + fa >= B) return;
   const bool two = b0 + fa + 1 < B;
@@ -406,7 +407,7 @@ __device__ __forceinline__ void r2c45_body(int bx, int by, const float *__restri
   float2 *buf = bufs + s * BUF;
   seq_fft<P>(v, t, buf, tw);
   __syncthreads();
-  r2c45_emit<P, Out>(bx, by, bufs, out, nlat, M, B, fl, ring_scale, inverse_weights);
+  r2c45_emit<P, Out>(bx, by, bufs, out, nlat, M, B, fl, ring_scale, inverse_weights, threadIdx.x);
 }
 
 template <int P, class Out>
@@ -603,15 +604,21 @@ c2r45_kernel(const float *__restrict__ Gw, float *__restrict__ y, int nlat, int 
 // tile's rows by bulk copies (sequence s: its northern row at float 0, its
 // southern row at float N of the buffer; 2 N floats = N float2 <= BUF), is
 // then read into registers by the sequence's lanes, and serves as the
-// sequence buffers of that tile's FFT and output stage.  The copies of tile
-// i + 2 go into the stage of tile i once the CTA is done with it.
+// sequence buffers of that tile's FFT and output stage.  Two warp groups
+// share the CTA (512 threads): the FFT group (warps 0-7, one sequence each)
+// transforms tile i + 1 while the output group (warps 8-15) separates,
+// folds and stores tile i from the other stage; mbarriers hand a stage from
+// the copies to the FFT group (full), to the output group (fftd) and back
+// to the copies of tile i + 2 (freed), which one output thread issues.
 template <int P>
 __host__ __device__ constexpr size_t r2c_pipe_smem() {
-  return 16 + sizeof(float2) * ((size_t)kQ * P + 2 * (size_t)(kThreads / P) * seq_pitch<P>());
+  return 64 + sizeof(float2) * ((size_t)kQ * P + 2 * (size_t)(kThreads / P) * seq_pitch<P>());
 }
 
+constexpr int kWsThreads = 2 * kThreads;
+
 template <int P, class Out>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kWsThreads, 1)
 r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, FoldLayout fl,
                   const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale, int inverse_weights,
                   unsigned *err) {
@@ -619,75 +626,96 @@ r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, 
   constexpr int NPAIR = kThreads / P / kFB;
   constexpr int BUF = seq_pitch<P>();
   constexpr int NSEQ = kThreads / P;
-  constexpr int SPW = 32 / P;  // sequences per warp
+  constexpr int kGroupWarps = kThreads / 32;
   constexpr uint32_t kRowBytes = 4u * N;
   extern __shared__ __align__(1024) unsigned char pipe_smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(pipe_smem);
-  float2 *tw = reinterpret_cast<float2 *>(pipe_smem + 16);
+  uint64_t *full = reinterpret_cast<uint64_t *>(pipe_smem);  // [2]
+  uint64_t *fftd = full + 2, *freed = full + 4;                // [2] each
+  float2 *tw = reinterpret_cast<float2 *>(pipe_smem + 64);
   float2 *stage0 = tw + N;
   const int Kh = (nlat + 1) / 2;
   const int gx = (B + kFB - 1) / kFB;
   const int ntiles = gx * ((Kh + NPAIR - 1) / NPAIR);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool fft_group = threadIdx.x < kThreads;
   const int G = gridDim.x;
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar[0], kThreads / 32);
-    tc::mbar_init(&bar[1], kThreads / 32);
+    for (int q = 0; q < 2; q++) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&fftd[q], kGroupWarps);
+      tc::mbar_init(&freed[q], kGroupWarps);
+    }
     tc::mbar_fence_init();
   }
-  load_twiddles<P>(tw, twiddle);
+  if (fft_group) load_twiddles<P>(tw, twiddle);
   __syncthreads();
-  // the copies of tile `tile` into stage `st`: lane j < 2 SPW of warp w
-  // copies row j % 2 of sequence w SPW + j / 2; lane 0 announces the warp's
-  // bytes (every warp arrives once per phase)
-  auto issue = [&](int tile, int st) {
-    const int bx = tile % gx, by = tile / gx;
-    float2 *sb = stage0 + st * NSEQ * BUF;
-    const int seq = warp * SPW + (lane >> 1), row = lane & 1;
-    const int f = seq % kFB, pp = seq / kFB;
-    const int b = bx * kFB + f, kp = by * NPAIR + pp, ks = nlat - 1 - kp;
-    const bool copy = lane < 2 * SPW && b < B && kp < Kh && (row == 0 || kp != ks);
-    const uint32_t bytes = __reduce_add_sync(0xffffffffu, copy ? kRowBytes : 0u);
-    if (lane == 0) tc::mbar_arrive_expect_tx(&bar[st], bytes);
-    __syncwarp();
-    if (copy)
-      tc::bulk_load(reinterpret_cast<float *>(sb + seq * BUF) + row * N,
-                    x + ((int64_t)b * nlat + (row ? ks : kp)) * N, kRowBytes, &bar[st]);
-  };
-  if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-  if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1);
-  const int s = threadIdx.x / P, t = threadIdx.x % P;
-  const int f = s % kFB, pp = s / kFB;
-  int i = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
-    const int st = i & 1;
-    const bool ok = tc::mbar_wait(&bar[st], (i >> 1) & 1, err);
-    if (!__syncthreads_and(ok)) {
-      if (threadIdx.x == 0) {
-        tc::mbar_wait(&bar[st], (i >> 1) & 1, nullptr, 100000000ull);
-        if (tile + G < ntiles) tc::mbar_wait(&bar[st ^ 1], ((i + 1) >> 1) & 1, nullptr, 100000000ull);
-      }
-      __syncthreads();
-      return;
-    }
-    const int bx = tile % gx, by = tile / gx;
-    float2 *sb = stage0 + st * NSEQ * BUF;
-    const int b = bx * kFB + f, kp = by * NPAIR + pp;
-    const bool live = (b < B) && (kp < Kh);
-    const bool eq = kp == nlat - 1 - kp;
-    float2 *buf = sb + s * BUF;
-    const float *rn = reinterpret_cast<const float *>(buf), *rs = rn + N;
-    float2 v[kQ];
+  if (fft_group) {
+    const int s = threadIdx.x / P, t = threadIdx.x % P;
+    const int f = s % kFB, pp = s / kFB;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
+      const int st = i & 1;
+      if (!tc::mbar_wait(&full[st], (i >> 1) & 1, err)) break;
+      const int bx = tile % gx, by = tile / gx;
+      float2 *buf = stage0 + (st * NSEQ + s) * BUF;
+      const int b = bx * kFB + f, kp = by * NPAIR + pp;
+      const bool live = (b < B) && (kp < Kh);
+      const bool eq = kp == nlat - 1 - kp;
+      const float *rn = reinterpret_cast<const float *>(buf), *rs = rn + N;
+      float2 v[kQ];
 #pragma unroll
-    for (int j = 0; j < kQ; j++)
-      v[j] = live ? make_float2(rn[t + P * j], eq ? 0.f : rs[t + P * j]) : make_float2(0.f, 0.f);
-    __syncwarp();
-    seq_fft<P>(v, t, buf, tw);
-    __syncthreads();
-    r2c45_emit<P, Out>(bx, by, sb, out, nlat, M, B, fl, ring_scale, inverse_weights);
-    tc::fence_proxy_async_smem();
-    __syncthreads();
-    if (tile + 2 * G < ntiles) issue(tile + 2 * G, st);
+      for (int j = 0; j < kQ; j++)
+        v[j] = live ? make_float2(rn[t + P * j], eq ? 0.f : rs[t + P * j]) : make_float2(0.f, 0.f);
+      __syncwarp();
+      seq_fft<P>(v, t, buf, tw);
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&fftd[st]);
+    }
+  } else {
+    const int et = threadIdx.x - kThreads;
+    // the copies of tile `tile` into stage `st`, issued by one thread
+    int last_par[2] = {-1, -1};
+    auto issue = [&](int tile, int st, int par) {
+      const int bx = tile % gx, by = tile / gx;
+      float2 *sb = stage0 + st * NSEQ * BUF;
+      uint32_t bytes = 0;
+      for (int q = 0; q < NSEQ; q++) {
+        const int b = bx * kFB + q % kFB, kp = by * NPAIR + q / kFB;
+        if (b < B && kp < Kh) bytes += (kp == nlat - 1 - kp ? 1u : 2u) * kRowBytes;
+      }
+      tc::mbar_arrive_expect_tx(&full[st], bytes);
+      for (int q = 0; q < NSEQ; q++) {
+        const int b = bx * kFB + q % kFB, kp = by * NPAIR + q / kFB, ks = nlat - 1 - kp;
+        if (b >= B || kp >= Kh) continue;
+        float *dst = reinterpret_cast<float *>(sb + q * BUF);
+        tc::bulk_load(dst, x + ((int64_t)b * nlat + kp) * N, kRowBytes, &full[st]);
+        if (ks != kp) tc::bulk_load(dst + N, x + ((int64_t)b * nlat + ks) * N, kRowBytes, &full[st]);
+      }
+      last_par[st] = par;
+    };
+    if (et == 0) {
+      if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0, 0);
+      if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1, 0);
+    }
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
+      const int st = i & 1;
+      if (!tc::mbar_wait(&fftd[st], (i >> 1) & 1, err)) break;
+      const int bx = tile % gx, by = tile / gx;
+      r2c45_emit<P, Out>(bx, by, stage0 + st * NSEQ * BUF, out, nlat, M, B, fl, ring_scale, inverse_weights, et);
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&freed[st]);
+      if (et == 0 && tile + 2 * G < ntiles) {
+        if (!tc::mbar_wait(&freed[st], (i >> 1) & 1, err)) break;
+        issue(tile + 2 * G, st, ((i >> 1) + 1) & 1);
+      }
+    }
+    // copies still in flight (a wait gave up): let them land (bounded)
+    if (et == 0)
+      for (int q = 0; q < 2; q++)
+        if (last_par[q] >= 0) tc::mbar_wait(&full[q], (uint32_t)last_par[q], nullptr, 100000000ull);
   }
 }
 
@@ -882,7 +910,7 @@ cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (int64_t)grid.x * grid.y;
     const unsigned g = (unsigned)std::min<int64_t>(ntiles, sm_count());
-    r2c45_pipe_kernel<P, Out><<<g, kThreads, psmem, st>>>(x, out, nlat, M, B, fl, tw, ring, wts, err);
+    r2c45_pipe_kernel<P, Out><<<g, kWsThreads, psmem, st>>>(x, out, nlat, M, B, fl, tw, ring, wts, err);
     return cudaGetLastError();
   }
   const size_t smem = smem45<P>();

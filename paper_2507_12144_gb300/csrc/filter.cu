@@ -179,7 +179,36 @@ filter_dw_kernel(const float2 *__restrict__ gy, const float2 *__restrict__ x, fl
     }
 }
 
+// Wt[l][i][o] = conj(W[l][o][i]) through 32 x 32 shared-memory tiles
+// (coalesced reads and writes); grid (Cin / 32, Cout / 32, L).
+__global__ void __launch_bounds__(256) transpose_conj_kernel(const float2 *__restrict__ W, float2 *__restrict__ Wt,
+                                                             int Cout, int Cin) {
+  __shared__ float2 T[32][33];
+  const int i0 = blockIdx.x * 32, o0 = blockIdx.y * 32;
+  const int64_t base = (int64_t)blockIdx.z * Cout * Cin;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int o = o0 + r, i = i0 + tx;
+    if (o < Cout && i < Cin) T[r][tx] = W[base + (int64_t)o * Cin + i];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, o = o0 + tx;
+    if (o < Cout && i < Cin) {
+      const float2 w = T[tx][r];
+      Wt[base + (int64_t)i * Cout + o] = make_float2(w.x, -w.y);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_transpose_conj(const float2 *W, float2 *Wt, int L, int Cout, int Cin, cudaStream_t st) {
+  if (L <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((Cin + 31) / 32), (unsigned)((Cout + 31) / 32), (unsigned)L);
+  transpose_conj_kernel<<<grid, 256, 0, st>>>(W, Wt, Cout, Cin);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L, int M, int64_t Bm, int Cin, int Cout,
                           int adjoint, cudaStream_t st) {

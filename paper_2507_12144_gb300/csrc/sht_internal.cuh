@@ -357,6 +357,8 @@ cudaError_t launch_filter(const float2 *x, const float2 *W, float2 *y, int L,
                           int M, int64_t Bm, int Cin, int Cout, int adjoint,
                           cudaStream_t st);
 
+// Wt[l][i][o] = conj(W[l][o][i]) for W [L][Cout][Cin].
+cudaError_t launch_transpose_conj(const float2 *W, float2 *Wt, int L, int Cout, int Cin, cudaStream_t st);
 // Weight adjoint gW[l][o][i] (+)= sum_{b, m <= l} gy[b][o][l][m] conj(x[b][i][l][m])
 // (accumulate = 0 overwrites).
 cudaError_t launch_filter_dw(const float2 *gy, const float2 *x, float2 *gW,
@@ -418,6 +420,9 @@ struct sht_plan_s {
   // the first weight-gradient call
   __nv_bfloat16 *d_g_hi = nullptr, *d_g_lo = nullptr;
   shtgb::TcPlanView tc_g{};
+  // conj-transposed weights of the adjoint block (large W), grown on demand
+  float2 *d_wt = nullptr;
+  size_t wt_bytes = 0;
   void *d_ftiles = nullptr;    // filter tiles (l, m0)
   int n_ftiles = 0;
   __nv_bfloat16 *d_s_hi = nullptr, *d_s_lo = nullptr;  // bf16 internal rows [srows][ldcb]
