@@ -901,10 +901,11 @@ cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl
   dim3 grid((B + kFB - 1) / kFB, (Kh + NPAIR - 1) / NPAIR);
   cudaError_t e;
   constexpr size_t psmem = r2c_pipe_smem<P>();
-  // persistent form (the rows arrive by 16-byte-aligned bulk copies) at
-  // nlon = 1440 only: on the shorter rows its 8 warps per SM lose to the
-  // 16 of the non-persistent kernel (6-16 % slower at nlon = 180 .. 720)
-  if (P == 32 && aligned16(x) && psmem <= (size_t)max_smem_optin()) {
+  // persistent warp-specialised form (the rows arrive by 16-byte-aligned
+  // bulk copies) at nlon = 720 and 1440; at nlon = 180 and 360 the tiles'
+  // 128 and 64 short rows per copy-issuing thread make it slower than the
+  // non-persistent kernel (measured per grid)
+  if ((P == 32 || P == 16) && aligned16(x) && psmem <= (size_t)max_smem_optin()) {
     e = cudaFuncSetAttribute((const void *)r2c45_pipe_kernel<P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)psmem);
     if (e != cudaSuccess) return e;
