@@ -311,16 +311,19 @@ __device__ __forceinline__ uint32_t chunk_tx_bytes(const TileInfo &ti) {
   return abytes + (uint32_t)b_count(kMode, kSplit) * (uint32_t)((ti.Nt + 63) / 64) * 8192u;
 }
 
-// MMAs of one K chunk (kKc = 64) of a tile, N = the tile's column width.
+// MMAs of one K chunk (kKc = 64) of a tile, N = the tile's column width;
+// only the first nks K steps of 16 (the filter's last chunk ends at 2 Cin).
 // Stage layout (for the launch's widest tile Nmax): A hi, A lo, B hi, B lo.
 template <int kMode, bool kSplit, bool kGen>
-__device__ __forceinline__ void issue_chunk(unsigned char *st, int Nmax, uint32_t tmem, uint32_t idesc, bool first) {
+__device__ __forceinline__ void issue_chunk(unsigned char *st, int Nmax, uint32_t tmem, uint32_t idesc, bool first,
+                                            int nks = kKc / 16) {
   const int na = a_count(kMode, kSplit);
   const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
 #pragma unroll
   for (int ks = 0; ks < kKc / 16; ks++) {
+    if (ks >= nks) break;
     const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
     const uint64_t ah = desc_advance(desc_kmajor_sw128(a_hi), ks * 32);
     if (kMode == kFilt) {
@@ -813,10 +816,13 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       const uint32_t use = g / (uint32_t)S;
       if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, P.err);
       unsigned char *bh = base + (size_t)s * sbytes + na * kABytes, *bl = bh + bb;
+      const int kcov = min(kKc, (2 * P.cin - kc * kKc + 15) / 16 * 16);  // real K the chunk's MMAs read
 #pragma unroll
       for (int u = 0; u < kItems; u++) {
         const int e = gtid + 256 * u;
-        if (e >= ti.Nt * 4) continue;
+        // items past the last K step the MMAs issue (16-column steps up to
+        // 2 Cin) would build zero weights that nothing reads
+        if (e >= ti.Nt * 4 || 8 * (e & 7) >= kcov) continue;
         const int q = e & 7;
         const float wr[4] = {wv[u][0].x, wv[u][0].z, wv[u][1].x, wv[u][1].z};
         const float wi[4] = {wv[u][0].y, wv[u][0].w, wv[u][1].y, wv[u][1].w};
@@ -861,7 +867,9 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
         const uint32_t use = g / (uint32_t)S;
         mbar_wait(&full_bar[s], use & 1, P.err);
         tc_fence_after();
-        issue_chunk<kMode, kSplit, kGen>(base + (size_t)s * sbytes, P.Nmax, tacc, idesc, kc == 0);
+        // filter: K steps past 2 Cin meet zero weights (and another member's columns)
+        const int nks = kMode == kFilt ? min(kKc / 16, (2 * P.cin - kc * kKc + 15) / 16) : kKc / 16;
+        issue_chunk<kMode, kSplit, kGen>(base + (size_t)s * sbytes, P.Nmax, tacc, idesc, kc == 0, nks);
         mma_commit(&empty_bar[s]);
       }
       if (ti.nk > 0)
