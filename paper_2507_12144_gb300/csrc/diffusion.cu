@@ -14,9 +14,11 @@
 // and the Box-Muller transform of the first two output words,
 //   u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8) 2^-24,
 //   eta = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
-// One thread per coefficient of the l >= m triangle: the step reads and
-// writes the state once; the generator adds about 130 instructions per
-// coefficient.  Entries with m > l are neither read nor written.
+// One thread per coefficient of the l >= m triangle, numbered row by row
+// (t = l (l + 1) / 2 + m for l < mmax, then mmax per row), so that no
+// block or lane falls above the diagonal: the step reads and writes the
+// state once; the generator adds about 130 instructions per coefficient.
+// Entries with m > l are neither read nor written.
 #include <cmath>
 
 #include "sht_internal.cuh"
@@ -50,16 +52,33 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 constexpr int kDiffThreads = 128;
 
-// grid (orders / 128, lmax, fields): no index divisions; blocks above the
-// diagonal (m > l) leave at once.
+// (l, m) of triangle index t (row by row, rows l < M holding l + 1 orders,
+// the rest M): l from the square root, corrected in integers.
+__device__ __forceinline__ void tri_lm(int t, int M, int &l, int &m) {
+  const int T0 = M * (M + 1) / 2;  // the rows l < M
+  if (t >= T0) {
+    const int r = (t - T0) / M;
+    l = M + r;
+    m = t - T0 - r * M;
+    return;
+  }
+  int q = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (q * (q + 1) / 2 > t) q--;
+  while ((q + 1) * (q + 2) / 2 <= t) q++;
+  l = q;
+  m = t - q * (q + 1) / 2;
+}
+
+// grid (triangle / 128, fields)
 __global__ void __launch_bounds__(kDiffThreads) diffusion_step_kernel(float2 *__restrict__ z,
                                                                       const float2 *__restrict__ eta, int64_t b0,
-                                                                      int L, int M, DiffusionParams P, uint2 key,
-                                                                      uint2 step) {
-  const int m = blockIdx.x * kDiffThreads + threadIdx.x;
-  const int l = blockIdx.y;
-  if (m >= M || m > l) return;  // never read by the inverse transform
-  const int64_t b = b0 + blockIdx.z;
+                                                                      int L, int M, int ntri, DiffusionParams P,
+                                                                      uint2 key, uint2 step) {
+  const int t = blockIdx.x * kDiffThreads + threadIdx.x;
+  if (t >= ntri) return;
+  int l, m;
+  tri_lm(t, M, l, m);
+  const int64_t b = b0 + blockIdx.y;
   const int64_t idx = (b * L + l) * M + m;
   if (l == 0) {
     z[idx] = make_float2(0.f, 0.f);
@@ -77,7 +96,7 @@ __global__ void __launch_bounds__(kDiffThreads) diffusion_step_kernel(float2 *__
     sincospif(2.0f * u2, &s, &c);
     e = make_float2(rad * c, rad * s);
   }
-  const int k = (int)((P.kbase + blockIdx.z) % (unsigned)P.nk);
+  const int k = (int)((P.kbase + blockIdx.y) % (unsigned)P.nk);
   const float sig = P.F0[k] * expf(-P.half_kT[k] * (float)l * (float)(l + 1));
   const float2 xi = m == 0 ? make_float2(1.41421356237309515f * e.x, 0.f) : e;
   const float2 v = z[idx];
@@ -116,12 +135,12 @@ sht_status_t sht_diffusion_step(void *zhat, const void *eta, int64_t B, int lmax
   }
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   const uint2 st2 = make_uint2((uint32_t)step, (uint32_t)(step >> 32));
+  const int ntri = mmax * (mmax + 1) / 2 + (lmax - mmax) * mmax;  // coefficients with m <= l
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     P.kbase = (unsigned)(b0 % nk);
-    const dim3 grid((unsigned)((mmax + kDiffThreads - 1) / kDiffThreads), (unsigned)lmax,
-                    (unsigned)std::min<int64_t>(65535, B - b0));
+    const dim3 grid((unsigned)((ntri + kDiffThreads - 1) / kDiffThreads), (unsigned)std::min<int64_t>(65535, B - b0));
     diffusion_step_kernel<<<grid, kDiffThreads, 0, (cudaStream_t)stream>>>((float2 *)zhat, (const float2 *)eta, b0,
-                                                                           lmax, mmax, P, key, st2);
+                                                                           lmax, mmax, ntri, P, key, st2);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SHT_OK : cuda_fail(e, "diffusion_step_kernel");
