@@ -37,6 +37,7 @@ SHAPES = [
     (46, 90, "gauss", 46, 46, 1),                # M = nlon/2 + 1, single field
     (361, 720, "equiangular_cc", 360, 360, 10),  # 0.5 degree grid, 16-lane transforms
     (91, 180, "gauss", 91, 91, 3),               # M = nlon/2 + 1 on a four-step grid, partial field group
+    (361, 720, "gauss", 361, 361, 3),            # the same on the warp-specialised 720-point analysis
 ]
 
 
