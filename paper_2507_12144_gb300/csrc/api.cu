@@ -680,32 +680,25 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       T.gen_inv = gen_inv;
       p->table_bytes = 0;
       if (!gen_fwd) {
-        // streamed tables: the forward layout, and the transposed layout
-        // when the inverse streams too
+        // streamed table: the forward layout [rows i of the (m, p) blocks]
+        // [Kp64 latitudes k']; the forward contraction reads it K-major
+        // (boxes of 64 k' x 128 rows), the inverse MN-major (boxes of 64 k'
+        // x 64 rows: A = T^T with k' contiguous), so one table serves both
         const int Kp64 = (p->Kh + 63) / 64 * 64;
-        const int Ip64 = (leg_rows(lmax, 0, 0) + 63) / 64 * 64;
-        const int64_t irows = (int64_t)mmax * 2 * p->Kh;
         const size_t fbytes = sizeof(__nv_bfloat16) * (size_t)frows * Kp64;
-        const size_t ibytes = gen_inv ? 0 : sizeof(__nv_bfloat16) * (size_t)irows * Ip64;
         if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_hi, fbytes);
         if (e == cudaSuccess) e = dev_alloc((void **)&p->d_tf_lo, fbytes);
         if (e == cudaSuccess) e = cudaMemset(p->d_tf_hi, 0, fbytes);
         if (e == cudaSuccess) e = cudaMemset(p->d_tf_lo, 0, fbytes);
-        if (!gen_inv) {
-          if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_hi, ibytes);
-          if (e == cudaSuccess) e = dev_alloc((void **)&p->d_ti_lo, ibytes);
-          if (e == cudaSuccess) e = cudaMemset(p->d_ti_hi, 0, ibytes);
-          if (e == cudaSuccess) e = cudaMemset(p->d_ti_lo, 0, ibytes);
-        }
         if (e == cudaSuccess)
-          e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_ti_hi, p->d_ti_lo, p->d_roff, Kp64, Ip64, d_x, d_s,
-                                    d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
-        p->table_bytes += (int64_t)(fbytes + ibytes) * 2;
+          e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, nullptr, nullptr, p->d_roff, Kp64, 64, d_x, d_s, d_a,
+                                    d_b, d_seed, lmax, mmax, p->Kh, 0);
+        p->table_bytes += (int64_t)fbytes * 2;
         if (e == cudaSuccess &&
             !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, Kp64, frows, 64, 128) &&
               tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, Kp64, frows, 64, 128) &&
-              tc_encode_2d(&T.tab_inv_hi, p->d_ti_hi, Ip64, irows, 64, 128) &&
-              tc_encode_2d(&T.tab_inv_lo, p->d_ti_lo, Ip64, irows, 64, 128)))
+              tc_encode_2d(&T.tab_inv_hi, p->d_tf_hi, Kp64, frows, 64, 64) &&
+              tc_encode_2d(&T.tab_inv_lo, p->d_tf_lo, Kp64, frows, 64, 64)))
           e = cudaErrorInvalidValue;
       }
       if (gen_inv) {

@@ -112,7 +112,8 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 // across tiles; the accumulator is double-buffered in tensor memory so that
 // the epilogue warps drain tile i while the MMAs of tile i + 1 run.
 //   kFwd:  D[i][c]  = sum_k' T[m][p][i][k'] F[m][p][k'][c]   (A = table, B = data, MN-major)
-//   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[(m + p + 2i) M + m][c]   (A = table, B = data, MN-major)
+//   kInv:  D[k'][c] = sum_i  T[m][p][i][k'] S[(m + p + 2i) M + m][c]   (A = table, B = data, MN-major;
+//          A read from the forward table's rows i, k' contiguous: MN-major too)
 //   kFilt: D[m][n]  = sum_k  X[l M + m][b kx + k] WR[l][n][k] (A = data, B = weights, K-major)
 // Table and weights always enter split (hi + lo); data enters split for
 // split BF16 and rounded (hi only) for BF16.  Here the Legendre table of
@@ -171,6 +172,7 @@ struct SegArgs {
   const float4 *coef;
   const float *x2h, *x2l;
   int NB, ldC;
+  const int *roff;        // first forward-table row of block (m, p) at [2m + p]
 };
 
 // TMA maps of one problem: A (table hi/lo, or filter data), B (data, or
@@ -280,7 +282,9 @@ __device__ __forceinline__ TileInfo tile_decode(const TcParams &P, const RawTile
       ti.b_row0 = 2 * ti.m + ti.p;  // (2m + p) coordinate of the folded data map
     } else {
       ti.nk = (leg_rows(g.L, ti.m, ti.p) + kKc - 1) / kKc;
-      ti.a_row = (ti.m * 2 + ti.p) * g.Kh + ti.r0;
+      // A: rows i of the block in the forward table, columns k' from r0
+      ti.a_row = g.roff ? __ldg(g.roff + 2 * ti.m + ti.p) : 0;
+      ti.a_col0 = ti.r0;
       ti.b_row0 = r.d.w;  // first degree m + p of the (m, p) block
     }
   }
@@ -332,13 +336,21 @@ __device__ __forceinline__ void issue_chunk(unsigned char *st, int Nmax, uint32_
       mma_bf16(tmem, ah, bh, idesc, acc0);
       mma_bf16(tmem, ah, bl, idesc, 1u);
       if (kSplit) mma_bf16(tmem, desc_advance(desc_kmajor_sw128(a_lo), ks * 32), bh, idesc, 1u);
-    } else {
+    } else if (kMode == kFwd) {
       // A = table, K-major from TMA
       const uint64_t al = desc_advance(desc_kmajor_sw128(a_lo), ks * 32);
       const uint64_t bh = desc_mnmajor_sw128(b_hi + ks * 2048, 8192, 1024);
       mma_bf16(tmem, ah, bh, idesc, acc0);
       mma_bf16(tmem, al, bh, idesc, 1u);
       if (kSplit) mma_bf16(tmem, ah, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
+    } else {
+      // A = table, MN-major from TMA: two 64-column boxes (k') of 64 rows (i)
+      const uint64_t ahm = desc_mnmajor_sw128(a_hi + ks * 2048, 8192, 1024);
+      const uint64_t alm = desc_mnmajor_sw128(a_lo + ks * 2048, 8192, 1024);
+      const uint64_t bh = desc_mnmajor_sw128(b_hi + ks * 2048, 8192, 1024);
+      mma_bf16(tmem, ahm, bh, idesc, acc0);
+      mma_bf16(tmem, alm, bh, idesc, 1u);
+      if (kSplit) mma_bf16(tmem, ahm, desc_mnmajor_sw128(b_lo + ks * 2048, 8192, 1024), idesc, 1u);
     }
   }
 }
@@ -350,8 +362,18 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
   const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
-  tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
-  if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  if (kMode == kInv) {
+    // the forward table's rows i = 64 kc .. 64 kc + 63 of the block, k'
+    // columns r0 .. r0 + 127 as two 64-column boxes (rows past the block
+    // belong to the next block and meet degrees past lmax: zero data)
+    for (int j = 0; j < 2; j++) {
+      tma_load_2d(a_hi + j * 8192, &mp.a_hi, bar, ti.a_col0 + 64 * j, ti.a_row + kc * kKc);
+      tma_load_2d(a_lo + j * 8192, &mp.a_lo, bar, ti.a_col0 + 64 * j, ti.a_row + kc * kKc);
+    }
+  } else {
+    tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
+    if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+  }
   if (kMode == kFilt) {
     if (!kGen) {
       tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
@@ -856,7 +878,8 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
     uint32_t g = 0, it = 0;
     for (TileWalk<kMode> w(P); w.more(P); it++) {
       const TileInfo ti = w.take(P);
-      const uint32_t idesc = idesc_bf16_f32(kRows, ti.Nt, kMode != kFilt);
+      // B MN-major for the Legendre modes; A MN-major for the inverse
+      const uint32_t idesc = idesc_bf16_f32(kRows, ti.Nt, kMode != kFilt) | (kMode == kInv ? 1u << 15 : 0u);
       const int acc = (int)(it & 1);
       const uint32_t use_a = it >> 1;
       if (use_a > 0) mbar_wait(&tempty[acc], (use_a - 1) & 1, P.err);
@@ -1785,6 +1808,7 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       g.x2l = T.x2l;
       g.NB = T.NB;
       g.ldC = T.ldC;
+      g.roff = T.roff;
       SegMaps &mp = P.maps[nseg];
       if (!inverse) {
         mp.a_hi = T.tab_fwd_hi;
