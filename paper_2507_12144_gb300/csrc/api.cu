@@ -695,10 +695,12 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
                                     d_b, d_seed, lmax, mmax, p->Kh, 0);
         p->table_bytes += (int64_t)fbytes * 2;
         if (e == cudaSuccess &&
-            !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, Kp64, frows, 64, 128) &&
-              tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, Kp64, frows, 64, 128) &&
-              tc_encode_2d(&T.tab_inv_hi, p->d_tf_hi, Kp64, frows, 64, 64) &&
-              tc_encode_2d(&T.tab_inv_lo, p->d_tf_lo, Kp64, frows, 64, 64)))
+            // maps Kh columns wide (row pitch Kp64): the boxes' columns past
+            // Kh read zeros without memory traffic
+            !(tc_encode_2d(&T.tab_fwd_hi, p->d_tf_hi, p->Kh, frows, 64, 128, Kp64) &&
+              tc_encode_2d(&T.tab_fwd_lo, p->d_tf_lo, p->Kh, frows, 64, 128, Kp64) &&
+              tc_encode_2d(&T.tab_inv_hi, p->d_tf_hi, p->Kh, frows, 64, 64, Kp64) &&
+              tc_encode_2d(&T.tab_inv_lo, p->d_tf_lo, p->Kh, frows, 64, 64, Kp64)))
           e = cudaErrorInvalidValue;
       }
       if (gen_inv) {
