@@ -456,14 +456,15 @@ __device__ __forceinline__ void c2r45_put(float2 *Ba, float4 ge, float4 go, int 
 // Zeros between the two halves of every staged sequence of the thread's
 // fields (orders M .. N - M).
 template <int P>
-__device__ __forceinline__ void c2r45_zero_gap(float2 *bufs, int by, int nlat, int M, bool field_ok) {
+__device__ __forceinline__ void c2r45_zero_gap(float2 *bufs, int by, int nlat, int M, bool field_ok,
+                                               int tid = threadIdx.x) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
   constexpr int BUF = seq_pitch<P>();
   constexpr int kPairs = kFB / 2;
   constexpr int kMStep = kThreads / kPairs;
   const int Kh = (nlat + 1) / 2;
-  const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+  const int f2 = tid % kPairs, m0 = tid / kPairs;
   const int fa = 2 * f2;
 #pragma unroll 1
   for (int pq = 0; pq < NPAIR; pq++) {
@@ -482,12 +483,12 @@ __device__ __forceinline__ void c2r45_zero_gap(float2 *bufs, int by, int nlat, i
 // conj(FFT(conj Z)), and the two real rows are written.
 template <int P>
 __device__ __forceinline__ void c2r45_synth(int bx, int by, float2 *bufs, const float2 *tw, float *__restrict__ y,
-                                            int nlat, int B) {
+                                            int nlat, int B, int tid = threadIdx.x) {
   constexpr int N = kQ * P;
   constexpr int NPAIR = kThreads / P / kFB;
   constexpr int BUF = seq_pitch<P>();
   const int Kh = (nlat + 1) / 2;
-  const int s = threadIdx.x / P, t = threadIdx.x % P;
+  const int s = tid / P, t = tid % P;
   const int f = s % kFB, pp = s / kFB;
   const int b = bx * kFB + f;
   const int kp = by * NPAIR + pp;
@@ -814,6 +815,171 @@ c2r45_pipe_kernel(const __grid_constant__ CUtensorMap gmap, float *__restrict__ 
   }
 }
 
+// Synthesis, warp-specialised (nlon = 45 P, P >= 8): two stages of NSEQ
+// sequence buffers, each first filled by the tile's TMA boxes (the staged
+// rows, [NPAIR][nrows][32 floats], fit in the sequence buffers) and then
+// turned into conj(Z) in place: the conversion group (warps 0-7) reads all
+// its staged items into registers, meets at a named barrier, and writes the
+// sequences over them; the FFT group (warps 8-15) transforms and stores the
+// tile of the other stage meanwhile.  mbarriers hand a stage from the boxes
+// to the conversion group (full), to the FFT group (conv) and back to the
+// boxes of the tile after next (freed, which one FFT thread waits for
+// before it issues them).
+constexpr int kC2rItems = 12;  // a thread's (ring pair, order) items: NPAIR x ceil(M / 64) for P >= 8
+
+// AND of v over the `count` threads of named barrier `id` (a barrier too).
+template <int id, int count>
+__device__ __forceinline__ bool group_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "n"(id), "n"(count)
+      : "memory");
+  return r != 0;
+}
+
+template <int P>
+__host__ __device__ constexpr size_t c2r_ws_stage_bytes() {
+  return sizeof(float2) * (size_t)(kThreads / P) * seq_pitch<P>();
+}
+template <int P>
+size_t c2r_ws_smem() {
+  return 2 * c2r_ws_stage_bytes<P>() + 64 + sizeof(float2) * (size_t)kQ * P;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kWsThreads, 1)
+c2r45_ws_kernel(const __grid_constant__ CUtensorMap gmap, float *__restrict__ y, int nlat, int M, int B,
+                int box_rows, int nbox, const float2 *__restrict__ twiddle, const float *__restrict__ ring_scale,
+                int inverse_weights, unsigned *err) {
+  static_assert(P >= 8, "the conversion keeps at most kC2rItems items per thread");
+  constexpr int NPAIR = kThreads / P / kFB;
+  constexpr int BUF = seq_pitch<P>();
+  constexpr int kPairs = kFB / 2;
+  constexpr int kMStep = kThreads / kPairs;  // 64
+  constexpr int kGroupWarps = kThreads / 32;
+  constexpr size_t kStage = c2r_ws_stage_bytes<P>();
+  extern __shared__ __align__(1024) unsigned char pipe_smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(pipe_smem + 2 * kStage);  // [2]
+  uint64_t *conv = full + 2, *freed = full + 4;
+  float2 *tw = reinterpret_cast<float2 *>(pipe_smem + 2 * kStage + 64);
+  const int nrows = nbox * box_rows;
+  const int Kh = (nlat + 1) / 2;
+  const int gx = (B + kFB - 1) / kFB;
+  const int ntiles = gx * ((Kh + NPAIR - 1) / NPAIR);
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  auto stage = [&](int st) { return pipe_smem + (size_t)st * kStage; };
+  if (threadIdx.x == 0) {
+    tc::tma_prefetch_desc(&gmap);
+    for (int q = 0; q < 2; q++) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&conv[q], kGroupWarps);
+      tc::mbar_init(&freed[q], kGroupWarps);
+    }
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < kThreads) load_twiddles<P>(tw, twiddle);
+  __syncthreads();
+  if (threadIdx.x < kThreads) {
+    // conversion group
+    const int f2 = threadIdx.x % kPairs, m0 = threadIdx.x / kPairs;
+    const int fa = 2 * f2;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
+      const int st = i & 1;
+      // the group leaves together (it meets at named barriers below)
+      if (!group_all<2, kThreads>(tc::mbar_wait(&full[st], (i >> 1) & 1, err))) break;
+      const int bx = tile % gx, by = tile / gx;
+      const int b0 = bx * kFB;
+      const bool field_ok = b0 + fa < B;
+      const bool two = b0 + fa + 1 < B;
+      const float *stg = reinterpret_cast<const float *>(stage(st));
+      float4 ge[kC2rItems], go[kC2rItems];
+      int u = 0;
+#pragma unroll
+      for (int pq = 0; pq < NPAIR; pq++) {
+#pragma unroll
+        for (int k = 0; k < kC2rItems / NPAIR; k++, u++) {
+          const int m = m0 + k * kMStep;
+          ge[u] = go[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (field_ok && m < M && by * NPAIR + pq < Kh) {
+            const float *row = stg + ((size_t)pq * nrows + m) * 32 + 4 * f2;
+            ge[u] = *reinterpret_cast<const float4 *>(row);
+            go[u] = *reinterpret_cast<const float4 *>(row + 16);
+            if (!two) {
+              ge[u].z = ge[u].w = 0.f;
+              go[u].z = go[u].w = 0.f;
+            }
+          }
+        }
+      }
+      // every staged item of the stage is in registers: write over them
+      asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+      float2 *bufs = reinterpret_cast<float2 *>(stage(st));
+      u = 0;
+#pragma unroll
+      for (int pq = 0; pq < NPAIR; pq++) {
+        const int kq = by * NPAIR + pq;
+#pragma unroll
+        for (int k = 0; k < kC2rItems / NPAIR; k++, u++) {
+          const int m = m0 + k * kMStep;
+          if (field_ok && m < M && kq < Kh)
+            c2r45_put<P>(bufs + (pq * kFB + fa) * BUF, ge[u], go[u], m, kq, nlat, ring_scale, inverse_weights);
+        }
+      }
+      c2r45_zero_gap<P>(bufs, by, nlat, M, field_ok, threadIdx.x);
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&conv[st]);
+    }
+  } else {
+    // FFT group; thread 0 of the group issues the boxes
+    const int bt = threadIdx.x - kThreads;
+    int last_par[2] = {-1, -1};
+    auto issue = [&](int tile, int st, int par) {
+      const int bx = tile % gx, by = tile / gx;
+      int live = 0;
+      for (int pq = 0; pq < NPAIR; pq++) live += (by * NPAIR + pq < Kh);
+      tc::mbar_arrive_expect_tx(&full[st], (uint32_t)(live * nrows * 128));
+      float *stg = reinterpret_cast<float *>(stage(st));
+      for (int pq = 0; pq < NPAIR; pq++) {
+        const int kq = by * NPAIR + pq;
+        if (kq >= Kh) continue;
+        for (int j = 0; j < nbox; j++)
+          tc::tma_load_3d(stg + ((size_t)pq * nrows + (size_t)j * box_rows) * 32, &gmap, &full[st], 32 * bx, kq,
+                          j * box_rows);
+      }
+      last_par[st] = par;
+    };
+    if (bt == 0) {
+      if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0, 0);
+      if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1, 0);
+    }
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
+      const int st = i & 1;
+      if (!tc::mbar_wait(&conv[st], (i >> 1) & 1, err)) break;
+      const int bx = tile % gx, by = tile / gx;
+      c2r45_synth<P>(bx, by, reinterpret_cast<float2 *>(stage(st)), tw, y, nlat, B, bt);
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&freed[st]);
+      if (bt == 0 && tile + 2 * G < ntiles) {
+        if (!tc::mbar_wait(&freed[st], (i >> 1) & 1, err)) break;
+        issue(tile + 2 * G, st, ((i >> 1) + 1) & 1);
+      }
+    }
+    if (bt == 0)
+      for (int q = 0; q < 2; q++)
+        if (last_par[q] >= 0) tc::mbar_wait(&full[q], (uint32_t)last_par[q], nullptr, 100000000ull);
+  }
+}
+
 // Grouped launches: one grid over several problems (grids and batches) of
 // one batched call.  CTA j belongs to the segment s with blk0[s] <= j <
 // blk0[s + 1]; its (bx, by) follow from gx[s], and the segment's P selects
@@ -935,6 +1101,20 @@ cudaError_t c2r45(const float *G, float *y, int nlat, int M, int B, FoldLayout f
     const int nbox = (M + 255) / 256, box_rows = (M + nbox - 1) / nbox;
     const size_t psmem = c2r_pipe_smem<P>(nbox * box_rows);
     CUtensorMap gm;
+    const bool ws = P >= 8 && (size_t)NPAIR * nbox * box_rows * 128 <= c2r_ws_stage_bytes<P>() &&
+                    c2r_ws_smem<P>() <= (size_t)max_smem_optin();
+    if (ws && tc_encode_pair_rows_f32(&gm, G, fl, Kh, M, box_rows)) {
+      // warp-specialised: conversion and FFT groups on two stages
+      const size_t wsmem = c2r_ws_smem<P>();
+      e = cudaFuncSetAttribute((const void *)c2r45_ws_kernel<P < 8 ? 8 : P>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+      if (e != cudaSuccess) return e;
+      const int64_t ntiles = (int64_t)grid.x * grid.y;
+      const unsigned g = (unsigned)std::min<int64_t>(ntiles, sm_count());
+      c2r45_ws_kernel<P < 8 ? 8 : P><<<g, kWsThreads, wsmem, st>>>(gm, y, nlat, M, B, box_rows, nbox, tw, ring, wts,
+                                                                      err);
+      return cudaGetLastError();
+    }
     if (psmem <= (size_t)max_smem_optin() && tc_encode_pair_rows_f32(&gm, G, fl, Kh, M, box_rows)) {
       e = cudaFuncSetAttribute((const void *)c2r45_pipe_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)psmem);
