@@ -675,18 +675,22 @@ r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, 
     }
   } else {
     const int et = threadIdx.x - kThreads;
-    // the copies of tile `tile` into stage `st`, issued by one thread
+    const bool producer = et < 32;  // the output group's first warp issues the copies
+    // the copies of tile `tile` into stage `st`: lane j of the producer warp
+    // copies the rows of sequences j, j + 32, ...; lane 0 announces the bytes
     int last_par[2] = {-1, -1};
     auto issue = [&](int tile, int st, int par) {
       const int bx = tile % gx, by = tile / gx;
       float2 *sb = stage0 + st * NSEQ * BUF;
       uint32_t bytes = 0;
-      for (int q = 0; q < NSEQ; q++) {
+      for (int q = lane; q < NSEQ; q += 32) {
         const int b = bx * kFB + q % kFB, kp = by * NPAIR + q / kFB;
         if (b < B && kp < Kh) bytes += (kp == nlat - 1 - kp ? 1u : 2u) * kRowBytes;
       }
-      tc::mbar_arrive_expect_tx(&full[st], bytes);
-      for (int q = 0; q < NSEQ; q++) {
+      bytes = __reduce_add_sync(0xffffffffu, bytes);
+      if (lane == 0) tc::mbar_arrive_expect_tx(&full[st], bytes);
+      __syncwarp();
+      for (int q = lane; q < NSEQ; q += 32) {
         const int b = bx * kFB + q % kFB, kp = by * NPAIR + q / kFB, ks = nlat - 1 - kp;
         if (b >= B || kp >= Kh) continue;
         float *dst = reinterpret_cast<float *>(sb + q * BUF);
@@ -695,7 +699,7 @@ r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, 
       }
       last_par[st] = par;
     };
-    if (et == 0) {
+    if (producer) {
       if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0, 0);
       if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1, 0);
     }
@@ -708,8 +712,9 @@ r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, 
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&freed[st]);
-      if (et == 0 && tile + 2 * G < ntiles) {
-        if (!tc::mbar_wait(&freed[st], (i >> 1) & 1, err)) break;
+      if (producer && tile + 2 * G < ntiles) {
+        // the warp leaves together: its lanes issue the copies together
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&freed[st], (i >> 1) & 1, err))) break;
         issue(tile + 2 * G, st, ((i >> 1) + 1) & 1);
       }
     }
@@ -1068,10 +1073,9 @@ cudaError_t r2c45(const float *x, Out out, int nlat, int M, int B, FoldLayout fl
   cudaError_t e;
   constexpr size_t psmem = r2c_pipe_smem<P>();
   // persistent warp-specialised form (the rows arrive by 16-byte-aligned
-  // bulk copies) at nlon = 720 and 1440; at nlon = 180 and 360 the tiles'
-  // 128 and 64 short rows per copy-issuing thread make it slower than the
-  // non-persistent kernel (measured per grid)
-  if ((P == 32 || P == 16) && aligned16(x) && psmem <= (size_t)max_smem_optin()) {
+  // bulk copies) at nlon = 360, 720 and 1440; at nlon = 180 (128 short rows
+  // per tile) the non-persistent kernel is faster (measured per grid)
+  if (P >= 8 && aligned16(x) && psmem <= (size_t)max_smem_optin()) {
     e = cudaFuncSetAttribute((const void *)r2c45_pipe_kernel<P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)psmem);
     if (e != cudaSuccess) return e;
