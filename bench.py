@@ -840,9 +840,9 @@ def side_workloads(args) -> dict:
 
 def run_gpu_block_grad(args, emit: bool = True):
     """Training step of the spectral block through the C ABI: y =
-    sht_spectral_block(x, W), gx = sht_spectral_block_adjoint(gy, W), and
-    gW = sht_spectral_block_weight_grad(x, gy) (ISHT^T(gy) against the
-    recomputed SHT(x), per degree)."""
+    sht_spectral_block(x, W), then sht_spectral_block_backward: gx = the
+    adjoint block and gW = ISHT^T(gy) against the recomputed SHT(x), per
+    degree, with ISHT^T(gy) computed once for both."""
     world, rank, local = dist_setup(args.gpus)
     import torch
 
@@ -870,8 +870,7 @@ def run_gpu_block_grad(args, emit: bool = True):
 
     def step(gy):
         check(lib.sht_spectral_block(plan.handle, P(x), P(W), P(y), Bm, C, C, st))
-        check(lib.sht_spectral_block_adjoint(plan.handle, P(gy), P(W), P(gx), Bm, C, C, st))
-        check(lib.sht_spectral_block_weight_grad(plan.handle, P(x), P(gy), P(gW), Bm, C, C, st))
+        check(lib.sht_spectral_block_backward(plan.handle, P(x), P(gy), P(W), P(gx), P(gW), Bm, C, C, st))
 
     # the cotangent: the block's own output (a field with the data's spectrum)
     check(lib.sht_spectral_block(plan.handle, P(x), P(W), P(y), Bm, C, C, st))
@@ -968,7 +967,7 @@ def run_gpu_block_grad(args, emit: bool = True):
             "e2e": {"value": world * fields * e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * x.numel() * 4),
                     "d2h_bytes_per_step": int(x.numel() * 4 + W.numel() * 8), "steps": e2e_steps,
-                    "path": "the step's three C-ABI calls, x and gy copied in, gx and gW copied out"},
+                    "path": "the step's two C-ABI calls, x and gy copied in, gx and gW copied out"},
             "clocks": clk,
             "cpu_baseline": cpu_baseline_grad() if world == 1 and not args.no_cpu_baseline else None,
         }

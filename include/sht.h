@@ -243,6 +243,17 @@ sht_status_t sht_spectral_block_weight_grad(sht_plan_t plan, const float *x,
                                             int64_t Bm, int Cin, int Cout,
                                             void *stream);
 
+/* The block's backward in one call: gx as sht_spectral_block_adjoint and gW
+ * as sht_spectral_block_weight_grad (either may be NULL: not computed; x is
+ * read only for gW, W only for gx).  Tensor-core plans compute ISHT^T(gy)
+ * once into the gradient rows and read it for both (the two separate calls
+ * compute it twice); FP32 plans run the two calls.  Limits and errors as
+ * sht_spectral_block. */
+sht_status_t sht_spectral_block_backward(sht_plan_t plan, const float *x,
+                                         const float *gy, const void *W,
+                                         float *gx, void *gW, int64_t Bm,
+                                         int Cin, int Cout, void *stream);
+
 /* Fused filter + inverse SHT: y = ISHT(filter(xhat, W)).  xhat: complex64
  * [Bm][Cin][lmax][mmax], y: float32 [Bm][Cout][nlat][nlon]. */
 sht_status_t spectral_filter_inverse(sht_plan_t plan, const void *xhat,

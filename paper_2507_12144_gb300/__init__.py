@@ -22,7 +22,7 @@ from ._abi import ShtError
 
 __all__ = ["Plan", "Batch", "Pipe", "sht_plan", "sht_forward", "sht_inverse", "sht_forward_adjoint", "sht_inverse_adjoint",
            "spectral_filter", "spectral_filter_adjoint", "sht_spectral_block", "sht_spectral_block_adjoint",
-           "sht_spectral_block_weight_grad", "spectral_filter_inverse",
+           "sht_spectral_block_weight_grad", "sht_spectral_block_backward", "spectral_filter_inverse",
            "SpectralBlock", "spectral_block", "Disco", "DiscoContraction", "disco_contraction", "diffusion_step", "SphericalDiffusion", "angular_psd", "zonal_psd",
            "spectral_crps", "spectral_crps_backward",
            "spectral_crps_loss", "SpectralCRPSLoss", "sht_forward_ad", "SHTForward", "spatial_crps", "ShtError"]
@@ -338,6 +338,27 @@ def sht_spectral_block_weight_grad(plan: Plan, x: torch.Tensor, gy: torch.Tensor
     return gW
 
 
+def sht_spectral_block_backward(plan: Plan, x: torch.Tensor, gy: torch.Tensor, W: torch.Tensor,
+                                need_gx: bool = True, need_gW: bool = True):
+    """(gx, gW) of the block in one call: gx = SHT^T(W^H ISHT^T(gy)) [Bm, Cin,
+    nlat, nlon] and gW = the weight gradient [lmax, Cout, Cin] (None where not
+    asked for); ISHT^T(gy) is computed once for both."""
+    x, lead, _ = _spatial_in(plan, x)
+    gy, glead, _ = _spatial_in(plan, gy, "gy")
+    if len(lead) != 2 or len(glead) != 2 or lead[0] != glead[0]:
+        raise ValueError("x must be [Bm, Cin, nlat, nlon] and gy [Bm, Cout, nlat, nlon]")
+    W = _need(W, torch.complex64, "W", plan.device)
+    Bm, Cin = lead
+    Cout = glead[1]
+    if W.shape != (plan.lmax, Cout, Cin):
+        raise ValueError("W must be [lmax, Cout, Cin]")
+    gx = torch.empty((Bm, Cin, plan.nlat, plan.nlon), dtype=torch.float32, device=x.device) if need_gx else None
+    gW = torch.empty((plan.lmax, Cout, Cin), dtype=torch.complex64, device=x.device) if need_gW else None
+    _abi.check(_abi.lib().sht_spectral_block_backward(plan.handle, _ptr(x), _ptr(gy), _ptr(W), _ptr(gx), _ptr(gW),
+                                                      Bm, Cin, Cout, _stream(x)))
+    return gx, gW
+
+
 def spectral_filter_inverse(plan: Plan, xhat: torch.Tensor, W: torch.Tensor) -> torch.Tensor:
     """y = ISHT(filter(xhat, W)); xhat [Bm, Cin, lmax, mmax] -> y [Bm, Cout, nlat, nlon]."""
     xhat, _, _ = _spectral_in(plan, xhat)
@@ -508,8 +529,9 @@ class SpectralBlock(torch.autograd.Function):
       gyhat = ISHT^T(gy);  (gxhat, gW) = filter^T(gyhat);  gx = SHT^T(gxhat).
     The input gradient runs as one adjoint block (sht_spectral_block_adjoint)
     and the weight gradient as one call that reduces gyhat against the
-    recomputed xhat per degree (sht_spectral_block_weight_grad); both on the
-    tensor cores for tensor-core plans."""
+    recomputed xhat per degree (sht_spectral_block_weight_grad); when both
+    are needed, one call (sht_spectral_block_backward) computes gyhat once
+    for the two.  All on the tensor cores for tensor-core plans."""
 
     @staticmethod
     def forward(ctx, x, W, plan):
@@ -523,8 +545,11 @@ class SpectralBlock(torch.autograd.Function):
         plan = ctx.plan
         need_x, need_W = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         gy = gy.contiguous()
-        gx = sht_spectral_block_adjoint(plan, gy, W) if need_x else None
-        gW = sht_spectral_block_weight_grad(plan, x, gy) if need_W else None
+        if need_x and need_W:
+            gx, gW = sht_spectral_block_backward(plan, x, gy, W)
+        else:
+            gx = sht_spectral_block_adjoint(plan, gy, W) if need_x else None
+            gW = sht_spectral_block_weight_grad(plan, x, gy) if need_W else None
         return gx, gW, None
 
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "sht_forward_static_scratch": ([_p, _p, _p, _i64, _p], _i),
     "sht_spectral_block_adjoint": ([_p, _p, _p, _p, _i64, _i, _i, _p], _i),
     "sht_spectral_block_weight_grad": ([_p, _p, _p, _p, _i64, _i, _i, _p], _i),
+    "sht_spectral_block_backward": ([_p, _p, _p, _p, _p, _p, _i64, _i, _i, _p], _i),
     "sht_analysis_rows": ([_p, _p, _p, _i64, _i, _i, _p], _i),
     "sht_synthesis_rows": ([_p, _p, _p, _i64, _i, _i, _p], _i),
     "sht_legendre_orders": ([_p, _i, _p, _p, _i64, _i, _i, _p], _i),

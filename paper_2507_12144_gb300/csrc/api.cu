@@ -405,21 +405,21 @@ sht_status_t filter_body(sht_plan_s *p, const float2 *x, const float2 *W, float2
 // adjoint block (the strided reads of the on-chip adjoint builder then miss L2).
 constexpr size_t kAdjointTransposeBytes = size_t(64) << 20;
 
-sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, int64_t nb, int Cin, int Cout,
-                      cudaStream_t st, bool adjoint = false) {
+// The tensor-core filter of nb members from l-major rows (rows_hi / rows_lo,
+// Cin channels per member at kx = block_kx(Cin) columns) into the inverse's
+// split rows S; adjoint: output i from input o by conj(W[l][i][o]).
+sht_status_t filter_rows_tc(sht_plan_s *p, const __nv_bfloat16 *rows_hi, const __nv_bfloat16 *rows_lo,
+                            const void *W, int64_t nb, int Cin, int Cout, bool adjoint, cudaStream_t st) {
   // members' columns packed at kx = 2 Cin rounded to 8: the 64-column K
   // chunks of one member run into the next member's columns, which meet
   // zero weight columns, or past the last member outside the map (read as
   // zero without memory traffic)
   const int kx = block_kx(Cin);
   const int nwr = (2 * Cout + 15) / 16 * 16;
-  const bool split = p->precision == SHT_PREC_SPLIT_BF16;
-  RowsOut ro{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, kx};
-  SHT_TRY(analysis(p, x, nullptr, nb * Cin, st, adjoint, false, &ro));
   CUtensorMap ta_hi, ta_lo;
   const int64_t width = std::max<int64_t>(64, nb * (int64_t)kx);
-  if (!tc_encode_2d(&ta_hi, p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx) ||
-      !tc_encode_2d(&ta_lo, split ? p->d_x_lo : p->d_x_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx))
+  if (!tc_encode_2d(&ta_hi, rows_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx) ||
+      !tc_encode_2d(&ta_lo, rows_lo ? rows_lo : rows_hi, width, (int64_t)p->L * p->M, 64, 128, p->ldx))
     return fail(SHT_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward rows");
   cudaError_t e;
   // the adjoint reads conj(W[l][i][o]) along i for each o: strided, which
@@ -448,6 +448,15 @@ sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, in
                             p->ldcb, kx, nwr, (int)nb, Cin, Cout, wadj, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+  return SHT_OK;
+}
+
+sht_status_t block_tc(sht_plan_s *p, const float *x, const void *W, float *y, int64_t nb, int Cin, int Cout,
+                      cudaStream_t st, bool adjoint = false) {
+  const bool split = p->precision == SHT_PREC_SPLIT_BF16;
+  RowsOut ro{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, block_kx(Cin)};
+  SHT_TRY(analysis(p, x, nullptr, nb * Cin, st, adjoint, false, &ro));
+  SHT_TRY(filter_rows_tc(p, p->d_x_hi, split ? p->d_x_lo : nullptr, W, nb, Cin, Cout, adjoint, st));
   return synthesis_rows(p, y, (int)(nb * Cout), st, adjoint);
 }
 
@@ -1133,6 +1142,62 @@ sht_status_t sht_spectral_block_weight_grad(sht_plan_t p, const float *x, const 
     if (e != cudaSuccess) return cuda_fail(e, "weight gradient launch");
   }
   (void)LM;
+  return SHT_OK;
+}
+
+sht_status_t sht_spectral_block_backward(sht_plan_t p, const float *x, const float *gy, const void *W, float *gx,
+                                         void *gW, int64_t Bm, int Cin, int Cout, void *stream) {
+  NvtxRange nvtx_range("sht_spectral_block_backward");
+  SHT_TRY(check_plan(p));
+  SHT_TRY(check_batch(Bm));
+  SHT_TRY(check_channels(p, Cin, Cout, true));
+  if (!gx && !gW) return SHT_OK;
+  if (gx) SHT_TRY(check_ptr(W, "W"));
+  if (!is_tc(p)) {
+    // FP32 plans: the two calls (no shared intermediate on this path)
+    if (gx) SHT_TRY(sht_spectral_block_adjoint(p, gy, W, gx, Bm, Cin, Cout, stream));
+    if (gW) SHT_TRY(sht_spectral_block_weight_grad(p, x, gy, gW, Bm, Cin, Cout, stream));
+    return SHT_OK;
+  }
+  DeviceGuard g(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (std::max(Cin, Cout) > p->max_channels)
+    return fail(SHT_ERR_INVALID_ARG, "max(Cin, Cout) exceeds the plan's max_channels");
+  if (Bm == 0) {
+    if (gW) {
+      const cudaError_t e = cudaMemsetAsync(gW, 0, sizeof(float2) * (size_t)p->L * Cout * Cin, st);
+      if (e != cudaSuccess) return cuda_fail(e, "gradient memset");
+    }
+    return SHT_OK;
+  }
+  SHT_TRY(check_ptr(gy, "gy"));
+  if (gW) SHT_TRY(check_ptr(x, "x"));
+  SHT_TRY(ensure_grad_rows(p, st));
+  const int kxa = block_kx(Cout), kxb = block_kx(Cin);
+  int64_t per = p->max_batch / std::max(Cin, Cout);
+  per = std::min<int64_t>(per, p->ldx / std::max(kxa, kxb));
+  const bool split = p->precision == SHT_PREC_SPLIT_BF16;
+  const int64_t npix = (int64_t)p->nlat * p->nlon;
+  for (int64_t b0 = 0; b0 < Bm; b0 += per) {
+    const int64_t nb = std::min(per, Bm - b0);
+    // ISHT^T(gy) once, into the gradient rows: the input gradient's filter
+    // and the weight gradient both read it
+    RowsOut rg{p->d_g_hi, split ? p->d_g_lo : nullptr, p->ldx, Cout, kxa, &p->tc_g};
+    SHT_TRY(analysis(p, gy + b0 * Cout * npix, nullptr, nb * Cout, st, true, false, &rg));
+    if (gx) {
+      SHT_TRY(filter_rows_tc(p, p->d_g_hi, split ? p->d_g_lo : nullptr, W, nb, Cout, Cin, true, st));
+      SHT_TRY(synthesis_rows(p, gx + b0 * Cin * npix, (int)(nb * Cin), st, true));
+    }
+    if (gW) {
+      RowsOut rx{p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx, Cin, kxb, &p->tc};
+      SHT_TRY(analysis(p, x + b0 * Cin * npix, nullptr, nb * Cin, st, false, false, &rx));
+      const cudaError_t e = traced(p, SHT_KERNEL_FILTER_DW, st, [&] {
+        return launch_dw_tc(p->d_g_hi, split ? p->d_g_lo : nullptr, p->d_x_hi, split ? p->d_x_lo : nullptr, p->ldx,
+                            (float2 *)gW, p->L, p->M, (int)nb, Cin, Cout, kxa, kxb, b0 > 0 ? 1 : 0, p->d_err, st);
+      });
+      if (e != cudaSuccess) return cuda_fail(e, "weight gradient launch");
+    }
+  }
   return SHT_OK;
 }
 

@@ -224,6 +224,30 @@ def test_block_weight_grad_matches_oracle(shtgb, prec, dims):
     assert abs(lhs - rhs) <= tol * (abs(lhs) + float(y.double().norm() * gyg.double().norm()))
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dims", [(3, 5, 4), (2, 130, 72)])
+def test_block_backward_equals_the_separate_calls(shtgb, prec, dims):
+    """sht_spectral_block_backward (ISHT^T(gy) once for both gradients)
+    gives the bits of sht_spectral_block_adjoint and
+    sht_spectral_block_weight_grad, and either output alone."""
+    nlat, nlon, grid, L, M = 45, 90, "equiangular_cc", 44, 44
+    Bm, Cin, Cout = dims
+    plan = _plan(shtgb, nlat, nlon, grid, L, M, max_batch=max(Bm * max(Cin, Cout), 8), precision=prec,
+                 max_channels=max(Cin, Cout))
+    x = _to_gpu(inputs.spatial_noise(570, (Bm, Cin, nlat, nlon)), torch.float32)
+    gy = _to_gpu(inputs.spatial_noise(571, (Bm, Cout, nlat, nlon)), torch.float32)
+    W = _to_gpu(inputs.filter_weights(572, L, Cout, Cin).astype(np.complex64), torch.complex64)
+    gx1 = shtgb.sht_spectral_block_adjoint(plan, gy, W)
+    gW1 = shtgb.sht_spectral_block_weight_grad(plan, x, gy)
+    gx, gW = shtgb.sht_spectral_block_backward(plan, x, gy, W)
+    plan.check()
+    assert torch.equal(gx, gx1) and torch.equal(gW, gW1)
+    gxo, none = shtgb.sht_spectral_block_backward(plan, x, gy, W, need_gW=False)
+    none2, gWo = shtgb.sht_spectral_block_backward(plan, x, gy, W, need_gx=False)
+    assert none is None and none2 is None
+    assert torch.equal(gxo, gx1) and torch.equal(gWo, gW1)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
 def test_block_weight_grad_accumulates_over_member_chunks(shtgb, prec):
     """A plan whose batch holds two members at a time: the weight gradient
