@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(kThreadsDw, 1) dw_tc_kernel(const __grid_const
     for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x, it++) {
       const DwTile d = dw_tile(P, t);
       const int acc = (int)(it & 1);
-      if (!mbar_wait(&tfull[acc], (it >> 1) & 1, P.err)) break;
+      // the warp leaves together: its tensor-memory loads are warp-wide
+      if (!__all_sync(0xffffffffu, mbar_wait(&tfull[acc], (it >> 1) & 1, P.err))) break;
       tc_fence_after();
       const int orow = kTileM * d.ot + 32 * q + lane;  // o'
       const int o = orow >> 1;

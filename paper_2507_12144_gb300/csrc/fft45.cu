@@ -656,7 +656,8 @@ r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, 
     int i = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
       const int st = i & 1;
-      if (!tc::mbar_wait(&full[st], (i >> 1) & 1, err)) break;
+      // a warp leaves together (it meets at warp barriers below)
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[st], (i >> 1) & 1, err))) break;
       const int bx = tile % gx, by = tile / gx;
       float2 *buf = stage0 + (st * NSEQ + s) * BUF;
       const int b = bx * kFB + f, kp = by * NPAIR + pp;
@@ -706,7 +707,7 @@ r2c45_pipe_kernel(const float *__restrict__ x, Out out, int nlat, int M, int B, 
     int i = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
       const int st = i & 1;
-      if (!tc::mbar_wait(&fftd[st], (i >> 1) & 1, err)) break;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&fftd[st], (i >> 1) & 1, err))) break;
       const int bx = tile % gx, by = tile / gx;
       r2c45_emit<P, Out>(bx, by, stage0 + st * NSEQ * BUF, out, nlat, M, B, fl, ring_scale, inverse_weights, et);
       tc::fence_proxy_async_smem();
@@ -968,7 +969,7 @@ c2r45_ws_kernel(const __grid_constant__ CUtensorMap gmap, float *__restrict__ y,
     int i = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += G, i++) {
       const int st = i & 1;
-      if (!tc::mbar_wait(&conv[st], (i >> 1) & 1, err)) break;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&conv[st], (i >> 1) & 1, err))) break;
       const int bx = tile % gx, by = tile / gx;
       c2r45_synth<P>(bx, by, reinterpret_cast<float2 *>(stage(st)), tw, y, nlat, B, bt);
       tc::fence_proxy_async_smem();
