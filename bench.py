@@ -658,6 +658,45 @@ def cpu_baseline_line(target_s: float = 15.0) -> dict:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def host_link(xh, yh, dev) -> dict:
+    """Copy rates of the host link on the e2e leg's pinned buffers: host to
+    device alone, device to host alone, and both at once on two streams
+    (best of three each, CUDA events).  The e2e rate cannot exceed the
+    fields per second of the concurrent pair."""
+    import torch
+
+    xd = torch.empty(xh.shape, dtype=xh.dtype, device=dev)
+    yd = torch.zeros(yh.shape, dtype=yh.dtype, device=dev)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def best(h2d: bool, d2h: bool) -> float:
+        ms = []
+        for _ in range(3):
+            e0, e1, eo = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize(dev)
+            e0.record(s_in)
+            s_out.wait_event(e0)
+            if h2d:
+                with torch.cuda.stream(s_in):
+                    xd.copy_(xh, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s_out):
+                    yh.copy_(yd, non_blocking=True)
+            eo.record(s_out)
+            s_in.wait_event(eo)
+            e1.record(s_in)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return min(ms)
+
+    nb_in, nb_out = xh.numel() * xh.element_size(), yh.numel() * yh.element_size()
+    t_in, t_out, t_both = best(True, False), best(False, True), best(True, True)
+    del xd, yd
+    return {"h2d_gbs": nb_in / (t_in * 1e-3) / 1e9, "d2h_gbs": nb_out / (t_out * 1e-3) / 1e9,
+            "both_gbs": (nb_in + nb_out) / (t_both * 1e-3) / 1e9, "both_ms": t_both,
+            "how": "pinned host buffers of the e2e leg, cudaMemcpyAsync on two streams, best of 3"}
+
+
 def run_gpu(args):
     world, rank, local = dist_setup(args.gpus)
     import torch
@@ -752,6 +791,7 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = world * fields * e2e_steps / e2e_s
     pipe.close()
+    link = host_link(xh, yh, dev)
 
     # the plain FP32 form (CUDA cores, FP32 table) on the same workload, for
     # comparison with the tensor-core precision forms
@@ -791,7 +831,12 @@ def run_gpu(args):
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 4),
                     "d2h_bytes_per_step": int(y.numel() * 4), "steps": e2e_steps,
-                    "path": "sht_pipe_block, 2 staging slots, pinned host buffers"},
+                    "path": "sht_pipe_block, 2 staging slots, pinned host buffers",
+                    "link": link,
+                    # a step's copies both ways at the concurrent link rate, or
+                    # the device step, whichever is longer
+                    "link_bound_value": world * fields / (max(link["both_ms"], ms_step) * 1e-3),
+                    "frac_of_link_bound": e2e_value / (world * fields / (max(link["both_ms"], ms_step) * 1e-3))},
             "clocks": clk,
         }
         # the whole step against the fused minimum: fields in, fields out and

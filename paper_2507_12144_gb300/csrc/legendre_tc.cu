@@ -402,11 +402,49 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
 // at j0 goes to (x + j0, y, z) of the 32-column maps, a 16-column tail to
 // the 16-column maps.  nbuf (1 or 2) staging buffers of 4 KB (hi 2 KB, lo
 // 2 KB) at stg; 64-byte rows swizzled for the 32-column box, 32-byte rows
-// for the tail.
+// for the tail.  With one 4 KB buffer all chunks are 16 columns wide, two
+// 2 KB buffers (hi 1 KB, lo 1 KB) in it, so that a chunk waits only for
+// the store of the chunk before the previous one to have read its buffer.
 __device__ __forceinline__ void store_rows_bf16_tma(uint32_t tl, int ncols, const CUtensorMap *m32h,
                                                     const CUtensorMap *m32l, const CUtensorMap *m16h,
                                                     const CUtensorMap *m16l, bool lo, int x, int y, int z,
                                                     unsigned char *stg, int nbuf, int lane) {
+  if (nbuf == 1) {
+    for (int j0 = 0, c = 0; j0 < ncols; j0 += 16, c++) {
+      unsigned char *bh = stg + (c & 1) * 2048, *bl = bh + 1024;
+      if (c >= 2) {
+        if (lane == 0) bulk_wait_read<1>();
+        __syncwarp();
+      }
+      float v[16];
+      tmem_ld16(tl + (uint32_t)j0, v);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        uint32_t h[4], r4[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+          const __nv_bfloat162 hh = __floats2bfloat162_rn(v[8 * u + 2 * w], v[8 * u + 2 * w + 1]);
+          const float2 hf = __bfloat1622float2(hh);
+          const __nv_bfloat162 ll = __floats2bfloat162_rn(v[8 * u + 2 * w] - hf.x, v[8 * u + 2 * w + 1] - hf.y);
+          h[w] = *reinterpret_cast<const uint32_t *>(&hh);
+          r4[w] = *reinterpret_cast<const uint32_t *>(&ll);
+        }
+        const uint32_t off = lane * 32 + u * 16;
+        *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        if (lo) *reinterpret_cast<uint4 *>(bl + off) = make_uint4(r4[0], r4[1], r4[2], r4[3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_3d(m16h, bh, x + j0, y, z);
+        if (lo) tma_store_3d(m16l, bl, x + j0, y, z);
+        bulk_commit();
+      }
+    }
+    if (lane == 0) bulk_wait_read<0>();
+    __syncwarp();
+    return;
+  }
   for (int j0 = 0, c = 0; j0 < ncols; j0 += 32, c++) {
     const bool half = ncols - j0 == 16;
     unsigned char *bh = stg + (c % nbuf) * 4096, *bl = bh + 2048;
@@ -775,15 +813,18 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
     // zero past Cout and Cin.  bf16 hi/lo in the TMA SWIZZLE_128B K-major
     // layout (row n at 128 n bytes, 16-byte chunk q at q ^ (n mod 8)).
     // Thread item (o, q): 4 input channels of output channel o, both rows.
-    // The next chunk's weights are loaded before waiting for its stage.
+    // Two chunks' weights are in flight in two register sets: the loads of
+    // chunk g + 2 are issued once chunk g is built, so they have the build
+    // of chunk g + 1 to land (the stages are usually free by the time the
+    // builders reach them, so one set would leave the load latency exposed).
     constexpr int kItems = 4;  // (Nt / 2) x 8 items <= 1024 over 256 threads
     const int gtid = threadIdx.x - 256;
     const int na = a_count(kMode, kSplit);
     const uint32_t bb = b_bytes_of(kMode, P.Nmax);
     TileWalk<kMode> w(P);
-    TileInfo ti{};
+    TileInfo ti{};  // the walker's chunk (ti, kc): the last one fetched
     ti.nk = 0;
-    int kc = 0;
+    int kc = -1;
     auto next = [&]() {
       kc++;
       while (kc >= ti.nk) {
@@ -793,8 +834,7 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       }
       return true;
     };
-    float4 wv[kItems][2];
-    auto fetch = [&]() {
+    auto fetch = [&](float4 (&wv)[kItems][2]) {
       const float2 *Wl = P.W + (int64_t)ti.l * P.cout * P.cin;
 #pragma unroll
       for (int u = 0; u < kItems; u++) {
@@ -830,21 +870,19 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
         }
       }
     };
-    kc = -1;
-    bool have = next();
-    if (have) fetch();
-    for (uint32_t g = 0; have; g++) {
+    // builds chunk g (tile tb, chunk kb) from wv into its stage
+    auto build = [&](const float4 (&wv)[kItems][2], const TileInfo &tb, int kb, uint32_t g) {
       const int s = (int)(g % (uint32_t)S);
       const uint32_t use = g / (uint32_t)S;
       if (use > 0) mbar_wait(&empty_bar[s], (use - 1) & 1, P.err);
       unsigned char *bh = base + (size_t)s * sbytes + na * kABytes, *bl = bh + bb;
-      const int kcov = min(kKc, (2 * P.cin - kc * kKc + 15) / 16 * 16);  // real K the chunk's MMAs read
+      const int kcov = min(kKc, (2 * P.cin - kb * kKc + 15) / 16 * 16);  // real K the chunk's MMAs read
 #pragma unroll
       for (int u = 0; u < kItems; u++) {
         const int e = gtid + 256 * u;
         // items past the last K step the MMAs issue (16-column steps up to
         // 2 Cin) would build zero weights that nothing reads
-        if (e >= ti.Nt * 4 || 8 * (e & 7) >= kcov) continue;
+        if (e >= tb.Nt * 4 || 8 * (e & 7) >= kcov) continue;
         const int q = e & 7;
         const float wr[4] = {wv[u][0].x, wv[u][0].z, wv[u][1].x, wv[u][1].z};
         const float wi[4] = {wv[u][0].y, wv[u][0].w, wv[u][1].y, wv[u][1].w};
@@ -870,8 +908,37 @@ tc_persistent_kernel(const __grid_constant__ TcParams P) {
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&full_bar[s]);
-      have = next();
-      if (have) fetch();
+    };
+    float4 wa[kItems][2], wb[kItems][2];
+    // chunk g in the current set (cur tile tc / chunk kcur), chunk g + 1 in
+    // the other (tile tn / chunk kn) while have_n
+    bool have = next();
+    TileInfo tc = ti, tn{};
+    int kcur = kc, kn = 0;
+    if (have) fetch(wa);
+    bool have_n = have && next();
+    if (have_n) {
+      tn = ti;
+      kn = kc;
+      fetch(wb);
+    }
+    // one step: build chunk g from cur, then load chunk g + 2 into cur
+    auto step = [&](float4 (&cur)[kItems][2], uint32_t g) {
+      build(cur, tc, kcur, g);
+      have = have_n;
+      tc = tn;
+      kcur = kn;
+      have_n = have && next();
+      if (have_n) {
+        tn = ti;
+        kn = kc;
+        fetch(cur);
+      }
+    };
+    for (uint32_t g = 0; have; g += 2) {
+      step(wa, g);
+      if (!have) break;
+      step(wb, g + 1);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
