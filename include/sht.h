@@ -558,10 +558,12 @@ sht_status_t sht_spatial_crps(sht_plan_t plan, const float *ens, const float *ob
  * has the stationary variance sigma^2 at every point.
  *   zhat: complex64 [B][lmax][mmax] device, updated in place;
  *   eta:  complex64 [B][lmax][mmax] device standard normals, or NULL: drawn
- *         on the GPU from Philox4x32-10 with key = seed and counter =
- *         (flat coefficient index b lmax mmax + l mmax + m, step), then the
- *         Box-Muller transform of its first two words, u1 = ((w0 >> 8) + 1)
- *         2^-24, u2 = (w1 >> 8) 2^-24, eta = sqrt(-2 ln u1) e^{2 pi i u2};
+ *         on the GPU from Philox4x32-10 with key = seed: for the flat
+ *         coefficient index idx = b lmax mmax + l mmax + m, the generator
+ *         at counter (idx >> 1, step) gives words w0 .. w3, of which idx
+ *         takes (wa, wb) = (w0, w1) if idx is even and (w2, w3) if odd,
+ *         then the Box-Muller transform u1 = ((wa >> 8) + 1) 2^-24,
+ *         u2 = (wb >> 8) 2^-24, eta = sqrt(-2 ln u1) e^{2 pi i u2};
  *   kT:   HOST array of nk (1 .. 16) length scales; field b uses kT[b % nk].
  * lambda > 0, sigma >= 0, lmax >= 2, 1 <= mmax <= lmax; B = 0 is a no-op. */
 sht_status_t sht_diffusion_step(void *zhat, const void *eta, int64_t B, int lmax,

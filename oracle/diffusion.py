@@ -59,7 +59,7 @@ def diffusion_step(z, eta, kT, lam: float, sigma: float):
 # ----------------------------------------------------------------------------
 # The counter-based generator, from its published definition: Philox4x32
 # with 10 rounds (Salmon, Moraes, Dror and Shaw, SC 2011), and the
-# Box-Muller transform of its first two words, in FP64.
+# Box-Muller transform of two of its words per coefficient, in FP64.
 # ----------------------------------------------------------------------------
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
@@ -82,14 +82,20 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
 
 
 def philox_normals(seed: int, step: int, idx):
-    """Standard complex normals of flat coefficient indices ``idx`` (the
-    generator's counter is (idx, step), its key the seed):
-    u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8) 2^-24,
+    """Standard complex normals of flat coefficient indices ``idx``.  One
+    generator call serves two coefficients: its counter is (idx >> 1, step),
+    its key the seed, and coefficient idx takes its words (w0, w1) for even
+    idx and (w2, w3) for odd idx as (wa, wb):
+    u1 = ((wa >> 8) + 1) 2^-24, u2 = (wb >> 8) 2^-24,
     eta = sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2)."""
     idx = np.asarray(idx, dtype=np.uint64)
-    w = philox4x32_10(idx & _MASK, idx >> np.uint64(32), np.uint64(step) & _MASK, np.uint64(step) >> np.uint64(32),
+    c = idx >> np.uint64(1)
+    w = philox4x32_10(c & _MASK, c >> np.uint64(32), np.uint64(step) & _MASK, np.uint64(step) >> np.uint64(32),
                       np.uint64(seed) & _MASK, np.uint64(seed) >> np.uint64(32))
-    u1 = ((w[0] >> np.uint64(8)) + np.uint64(1)).astype(np.float64) * 2.0 ** -24
-    u2 = (w[1] >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+    odd = (idx & np.uint64(1)) == np.uint64(1)
+    wa = np.where(odd, w[2], w[0])
+    wb = np.where(odd, w[3], w[1])
+    u1 = ((wa >> np.uint64(8)) + np.uint64(1)).astype(np.float64) * 2.0 ** -24
+    u2 = (wb >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
     r = np.sqrt(-2.0 * np.log(u1))
     return r * np.cos(2.0 * np.pi * u2) + 1j * r * np.sin(2.0 * np.pi * u2)

@@ -10,15 +10,18 @@
 //
 // The standard normals eta are given, or drawn here from Philox4x32-10
 // (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2,
-// 3", SC 2011): key = the 64-bit seed, counter = (coefficient index, step),
-// and the Box-Muller transform of the first two output words,
-//   u1 = ((w0 >> 8) + 1) 2^-24, u2 = (w1 >> 8) 2^-24,
+// 3", SC 2011) under key = the 64-bit seed: one generator call at counter
+// (idx >> 1, step) serves the two coefficients of flat indices idx (even
+// and odd), which take its words (wa, wb) = (w0, w1) and (w2, w3) through
+// the Box-Muller transform
+//   u1 = ((wa >> 8) + 1) 2^-24, u2 = (wb >> 8) 2^-24,
 //   eta = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
-// One thread per coefficient of the l >= m triangle, numbered row by row
-// (t = l (l + 1) / 2 + m for l < mmax, then mmax per row), so that no
-// block or lane falls above the diagonal: the step reads and writes the
-// state once; the generator adds about 130 instructions per coefficient.
-// Entries with m > l are neither read nor written.
+// For even mmax a thread updates the two orders 2j, 2j + 1 of one degree
+// (one generator call, one sigma_l, one 16-byte access), threads numbered
+// over the pairs of the l >= m triangle row by row; for odd mmax one
+// thread per coefficient (the pairs then straddle rows).  No block or lane
+// falls above the diagonal, the state is read and written once, and
+// entries with m > l are neither read nor written.
 #include <cmath>
 
 #include "sht_internal.cuh"
@@ -52,6 +55,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 constexpr int kDiffThreads = 128;
 
+__device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb) {
+  const float u1 = (float)((wa >> 8) + 1u) * 0x1p-24f;
+  const float u2 = (float)(wb >> 8) * 0x1p-24f;
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(rad * c, rad * s);
+}
+
+// the generator's words for the coefficient pair of flat index idx
+__device__ __forceinline__ uint4 philox_pair(int64_t idx, uint2 step, uint2 key) {
+  const uint64_t c = (uint64_t)idx >> 1;
+  return philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), step.x, step.y), key);
+}
+
 // (l, m) of triangle index t (row by row, rows l < M holding l + 1 orders,
 // the rest M): l from the square root, corrected in integers.
 __device__ __forceinline__ void tri_lm(int t, int M, int &l, int &m) {
@@ -69,7 +87,81 @@ __device__ __forceinline__ void tri_lm(int t, int M, int &l, int &m) {
   m = t - q * (q + 1) / 2;
 }
 
-// grid (triangle / 128, fields)
+// (l, j) of pair index t for even M (pair j of degree l: orders 2j, 2j + 1):
+// rows 2q and 2q + 1 hold q + 1 pairs each (q (q + 1) pairs before row 2q),
+// rows l >= M hold M / 2.
+__device__ __forceinline__ void tri_pair(int t, int M, int &l, int &j) {
+  const int Q = M / 2;
+  const int T0 = Q * (Q + 1);  // the rows l < M
+  if (t >= T0) {
+    const int r = (t - T0) / Q;
+    l = M + r;
+    j = t - T0 - r * Q;
+    return;
+  }
+  int q = (int)((sqrtf(4.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (q > 0 && q * (q + 1) > t) q--;
+  while ((q + 1) * (q + 2) <= t) q++;
+  const int r = t - q * (q + 1);
+  if (r <= q) {
+    l = 2 * q;
+    j = r;
+  } else {
+    l = 2 * q + 1;
+    j = r - q - 1;
+  }
+}
+
+__device__ __forceinline__ float diffusion_sigma(const DiffusionParams &P, int64_t b, int l) {
+  const int k = (int)((P.kbase + (unsigned)b) % (unsigned)P.nk);
+  return P.F0[k] * expf(-P.half_kT[k] * (float)l * (float)(l + 1));
+}
+
+// even M, grid (pairs / 128, fields)
+__global__ void __launch_bounds__(kDiffThreads) diffusion_pair_kernel(float2 *__restrict__ z,
+                                                                      const float2 *__restrict__ eta, int64_t b0,
+                                                                      int L, int M, int npair, DiffusionParams P,
+                                                                      uint2 key, uint2 step) {
+  const int t = blockIdx.x * kDiffThreads + threadIdx.x;
+  if (t >= npair) return;
+  int l, j;
+  tri_pair(t, M, l, j);
+  const int64_t b = b0 + blockIdx.y;
+  const int m0 = 2 * j;
+  const int64_t idx = (b * L + l) * M + m0;  // even: the pair's first coefficient
+  if (l == 0) {
+    z[idx] = make_float2(0.f, 0.f);  // the only coefficient of degree 0
+    return;
+  }
+  const bool two = m0 + 1 <= min(l, M - 1);
+  float2 e0, e1 = make_float2(0.f, 0.f);
+  if (eta) {
+    if (two) {
+      const float4 q = __ldg(reinterpret_cast<const float4 *>(eta + idx));
+      e0 = make_float2(q.x, q.y);
+      e1 = make_float2(q.z, q.w);
+    } else {
+      e0 = __ldg(eta + idx);
+    }
+  } else {
+    const uint4 w = philox_pair(idx, step, key);
+    e0 = box_muller(w.x, w.y);
+    if (two) e1 = box_muller(w.z, w.w);
+  }
+  const float sig = diffusion_sigma(P, blockIdx.y, l);
+  const float2 xi0 = m0 == 0 ? make_float2(1.41421356237309515f * e0.x, 0.f) : e0;
+  if (two) {
+    float4 *zp = reinterpret_cast<float4 *>(z + idx);
+    const float4 v = *zp;
+    *zp = make_float4(fmaf(P.phi, v.x, sig * xi0.x), fmaf(P.phi, v.y, sig * xi0.y), fmaf(P.phi, v.z, sig * e1.x),
+                      fmaf(P.phi, v.w, sig * e1.y));
+  } else {
+    const float2 v = z[idx];
+    z[idx] = make_float2(fmaf(P.phi, v.x, sig * xi0.x), fmaf(P.phi, v.y, sig * xi0.y));
+  }
+}
+
+// odd M, grid (triangle / 128, fields): one thread per coefficient
 __global__ void __launch_bounds__(kDiffThreads) diffusion_step_kernel(float2 *__restrict__ z,
                                                                       const float2 *__restrict__ eta, int64_t b0,
                                                                       int L, int M, int ntri, DiffusionParams P,
@@ -88,16 +180,10 @@ __global__ void __launch_bounds__(kDiffThreads) diffusion_step_kernel(float2 *__
   if (eta) {
     e = __ldg(eta + idx);
   } else {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)idx, (uint32_t)((uint64_t)idx >> 32), step.x, step.y), key);
-    const float u1 = (float)((w.x >> 8) + 1u) * 0x1p-24f;
-    const float u2 = (float)(w.y >> 8) * 0x1p-24f;
-    const float rad = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    e = make_float2(rad * c, rad * s);
+    const uint4 w = philox_pair(idx, step, key);
+    e = (idx & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
   }
-  const int k = (int)((P.kbase + blockIdx.y) % (unsigned)P.nk);
-  const float sig = P.F0[k] * expf(-P.half_kT[k] * (float)l * (float)(l + 1));
+  const float sig = diffusion_sigma(P, blockIdx.y, l);
   const float2 xi = m == 0 ? make_float2(1.41421356237309515f * e.x, 0.f) : e;
   const float2 v = z[idx];
   z[idx] = make_float2(fmaf(P.phi, v.x, sig * xi.x), fmaf(P.phi, v.y, sig * xi.y));
@@ -136,11 +222,18 @@ sht_status_t sht_diffusion_step(void *zhat, const void *eta, int64_t B, int lmax
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   const uint2 st2 = make_uint2((uint32_t)step, (uint32_t)(step >> 32));
   const int ntri = mmax * (mmax + 1) / 2 + (lmax - mmax) * mmax;  // coefficients with m <= l
+  const int npair = (mmax / 2) * (mmax / 2 + 1) + (lmax - mmax) * (mmax / 2);  // their pairs (even mmax)
+  const bool pairs = mmax % 2 == 0;
+  const int nthr = pairs ? npair : ntri;
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     P.kbase = (unsigned)(b0 % nk);
-    const dim3 grid((unsigned)((ntri + kDiffThreads - 1) / kDiffThreads), (unsigned)std::min<int64_t>(65535, B - b0));
-    diffusion_step_kernel<<<grid, kDiffThreads, 0, (cudaStream_t)stream>>>((float2 *)zhat, (const float2 *)eta, b0,
-                                                                           lmax, mmax, ntri, P, key, st2);
+    const dim3 grid((unsigned)((nthr + kDiffThreads - 1) / kDiffThreads), (unsigned)std::min<int64_t>(65535, B - b0));
+    if (pairs)
+      diffusion_pair_kernel<<<grid, kDiffThreads, 0, (cudaStream_t)stream>>>((float2 *)zhat, (const float2 *)eta, b0,
+                                                                             lmax, mmax, npair, P, key, st2);
+    else
+      diffusion_step_kernel<<<grid, kDiffThreads, 0, (cudaStream_t)stream>>>((float2 *)zhat, (const float2 *)eta, b0,
+                                                                             lmax, mmax, ntri, P, key, st2);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SHT_OK : cuda_fail(e, "diffusion_step_kernel");

@@ -81,6 +81,9 @@ def test_philox_normals_are_standard_normal():
         assert d < 1.95 / sqrt(n)
     assert abs(np.mean(e0.real * e0.imag)) < 4.5 / sqrt(n)
     assert abs(np.mean(e0.real * e1.real)) < 4.5 / sqrt(n)
+    # the two coefficients of one generator call are uncorrelated too
+    assert abs(np.mean(e0.real[0::2] * e0.real[1::2])) < 4.5 / sqrt(n / 2)
+    assert abs(np.mean(e0.imag[0::2] * e0.imag[1::2])) < 4.5 / sqrt(n / 2)
     # another seed gives other numbers
     assert not np.allclose(diffusion.philox_normals(1, 0, np.arange(8)), e0[:8])
 
@@ -114,3 +117,22 @@ def test_philox_vectorised_matches_known_answers_elementwise():
     got = diffusion.philox4x32_10(*[np.array(c, dtype=np.uint64) for c in cols[:6]])
     for j in range(4):
         assert [int(v) for v in got[j]] == list(cols[6 + j])
+
+
+def test_philox_normals_take_two_words_per_generator_call():
+    """Coefficients 2c and 2c + 1 take the words (w0, w1) and (w2, w3) of
+    the generator at counter (c, step) under the seed: pinned on the
+    published zero-counter, zero-key vector (seed 0, step 0, c = 0) through
+    the Box-Muller transform written out here."""
+    row = _kat_rows()[0]
+    assert row[:6] == [0] * 6
+    w = row[6:]
+
+    def box_muller(a, b):
+        u1 = ((a >> 8) + 1) * 2.0 ** -24
+        u2 = (b >> 8) * 2.0 ** -24
+        r = np.sqrt(-2.0 * np.log(u1))
+        return r * np.cos(2.0 * np.pi * u2) + 1j * r * np.sin(2.0 * np.pi * u2)
+
+    got = diffusion.philox_normals(0, 0, np.array([0, 1]))
+    np.testing.assert_allclose(got, [box_muller(w[0], w[1]), box_muller(w[2], w[3])], rtol=1e-15, atol=0)
