@@ -42,7 +42,7 @@ struct sht_disco_s {
   int64_t nnz = 0;
   int *d_row_f = nullptr;   // [nlat_out + 1]
   int2 *d_idx_f = nullptr;  // (h', w')
-  float *d_val_f = nullptr; // [nnz][K]
+  float *d_val_f = nullptr; // [nnz][2 ceil(K / 2)] (a zero after the last value for odd K)
   int *d_row_b = nullptr;   // [nlat_in + 1]
   int2 *d_idx_b = nullptr;  // (h, w')
   float *d_val_b = nullptr; // [nnz][K]
@@ -52,7 +52,7 @@ struct sht_disco_s {
   int win_R = 0;            // outputs per thread of the run kernel (0: not used)
   int *d_run_row = nullptr; // [nlat_in + 1]
   int4 *d_runs = nullptr;
-  float *d_val_w = nullptr; // [nnz][K]
+  float *d_val_w = nullptr; // [nnz][2 ceil(K / 2)], entries in run order
   unsigned *d_err = nullptr; // error word of the run kernel's bounded waits
 };
 
@@ -60,6 +60,15 @@ namespace shtgb {
 namespace {
 
 constexpr int kDiscoThreads = 128;
+
+// The device keeps the K values of an entry in 2 KP floats (a zero after
+// the last for odd K), so that the run backward reads (psi_k, psi_k+1) as
+// one 8-byte load for one packed FP32x2 FMA (each lane rounds as the
+// scalar FMA).
+template <int K>
+constexpr int kpairs() {
+  return (K + 1) / 2;
+}
 
 template <int K, int CB>
 __global__ void __launch_bounds__(kDiscoThreads)
@@ -85,7 +94,7 @@ __global__ void __launch_bounds__(kDiscoThreads)
     float xv[CB];
 #pragma unroll
     for (int j = 0; j < CB; j++) xv[j] = c0 + j < C ? __ldg(xp + j * plane) : 0.f;
-    const float *vp = val + (int64_t)e * K;
+    const float *vp = val + (int64_t)e * (2 * kpairs<K>());
 #pragma unroll
     for (int k = 0; k < K; k++) {
       const float v = __ldg(vp + k);
@@ -143,7 +152,8 @@ __global__ void __launch_bounds__(kDiscoThreads)
 // Backward by runs (nlon_in == nlon_out = W): block (input latitude hi,
 // channel c), W / R threads, thread t owns input longitudes v0 = R t ..
 // v0 + R - 1.  For a run (h, e0, n, a) entry j has w' = a + j (mod W) and
-// adds sum_k psi[e0 + j][k] gy[c][k][h][(v - a - j) mod W] to gx[c][hi][v].
+// adds sum_k psi[e0 + j][k] gy[c][k][h][(v - a - j) mod W] to gx[c][hi][v]
+// (the even and odd k in the two lanes of packed FMAs, added at the end).
 // Window slots: at step j, output r reads the value of index q = v0 + r -
 // a - j, kept in slot (r - j) mod R; after the step the value q = v0 - a -
 // j - 1 replaces the one output R - 1 no longer needs (slot (-j - 1) mod R).
@@ -151,7 +161,7 @@ __global__ void __launch_bounds__(kDiscoThreads)
 constexpr int kRunThreadsMax = 256;
 
 template <int K, int R>
-__global__ void __launch_bounds__(kRunThreadsMax)
+__global__ void __launch_bounds__(kRunThreadsMax, 1)
     disco_bwd_run_kernel(const float *__restrict__ gy, float *__restrict__ gx, const int *__restrict__ run_row,
                          const int4 *__restrict__ runs, const float *__restrict__ val, int Hi, int W, int Ho,
                          unsigned *err) {
@@ -182,9 +192,10 @@ __global__ void __launch_bounds__(kRunThreadsMax)
     if (nr > 0) issue(0, 0);
     if (nr > 1) issue(1, 1);
   }
-  float acc[R];
+  constexpr int KP = kpairs<K>();
+  float2 acc[R];  // (even k, odd k) partial sums of output r
 #pragma unroll
-  for (int r = 0; r < R; r++) acc[r] = 0.f;
+  for (int r = 0; r < R; r++) acc[r] = make_float2(0.f, 0.f);
   for (int i = 0; i < nr; i++) {
     const int b = i & 1;
     const bool ok = tc::mbar_wait(&full[b], (i >> 1) & 1, err);
@@ -200,7 +211,11 @@ __global__ void __launch_bounds__(kRunThreadsMax)
     const int4 run = runs[r0 + i];
     const int e0 = run.y, n = run.z, a = run.w;
     const float *S = disco_smem + (size_t)b * K * W;
-    float win[K][R];
+    // basis functions in pairs (2 kk, 2 kk + 1; the second zero for odd K)
+    auto pair_at = [&](int kk, int d) {
+      return make_float2(S[2 * kk * W + d], 2 * kk + 1 < K ? S[(2 * kk + 1) * W + d] : 0.f);
+    };
+    float2 win[KP][R];
     // step 0: slot r holds index v0 + r - a
     int q = v0 - a;
     if (q < 0) q += W;
@@ -209,25 +224,39 @@ __global__ void __launch_bounds__(kRunThreadsMax)
       int d = q + r;
       if (d >= W) d -= W;
 #pragma unroll
-      for (int k = 0; k < K; k++) win[k][r] = S[k * W + d];
+      for (int kk = 0; kk < KP; kk++) win[kk][r] = pair_at(kk, d);
     }
     // the index loaded after step j: v0 - a - j - 1 (mod W)
     int dn = q - 1;
     if (dn < 0) dn += W;
+    // the basis values of the next entry load during this entry's FMAs
+    float2 pn[KP];
+    {
+      const float2 *pv = reinterpret_cast<const float2 *>(val) + (int64_t)e0 * KP;
+#pragma unroll
+      for (int kk = 0; kk < KP; kk++) pn[kk] = n > 0 ? __ldg(pv + kk) : make_float2(0.f, 0.f);
+    }
     for (int j0 = 0; j0 < n; j0 += R) {
 #pragma unroll
       for (int u = 0; u < R; u++) {
         const int j = j0 + u;
         if (j < n) {
-          const float *pv = val + (int64_t)(e0 + j) * K;
+          float2 pc[KP];
 #pragma unroll
-          for (int k = 0; k < K; k++) {
-            const float p = __ldg(pv + k);
+          for (int kk = 0; kk < KP; kk++) pc[kk] = pn[kk];
+          if (j + 1 < n) {
+            const float2 *pv = reinterpret_cast<const float2 *>(val) + (int64_t)(e0 + j + 1) * KP;
 #pragma unroll
-            for (int r = 0; r < R; r++) acc[r] = fmaf(p, win[k][(r - u + R) % R], acc[r]);
+            for (int kk = 0; kk < KP; kk++) pn[kk] = __ldg(pv + kk);
           }
 #pragma unroll
-          for (int k = 0; k < K; k++) win[k][(R - 1 - u) % R] = S[k * W + dn];
+          for (int kk = 0; kk < KP; kk++) {
+            const float2 p = pc[kk];
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r] = __ffma2_rn(p, win[kk][(r - u + R) % R], acc[r]);
+          }
+#pragma unroll
+          for (int kk = 0; kk < KP; kk++) win[kk][(R - 1 - u) % R] = pair_at(kk, dn);
           dn = dn == 0 ? W - 1 : dn - 1;
         }
       }
@@ -238,7 +267,7 @@ __global__ void __launch_bounds__(kRunThreadsMax)
   }
   float *out = gx + (c * Hi + hi) * (int64_t)W + v0;
 #pragma unroll
-  for (int r = 0; r < R; r++) out[r] = acc[r];
+  for (int r = 0; r < R; r++) out[r] = acc[r].x + acc[r].y;
 }
 
 constexpr int kCB = 4;
@@ -477,15 +506,23 @@ sht_status_t sht_disco_create(sht_disco_t *out, int nlat_in, int nlon_in, int gr
     delete d;
     return fail(SHT_ERR_CUDA, "cannot select the device");
   }
+  // the forward and run kernels read an entry's values in pairs: 2 ceil(K / 2) floats
+  auto pad_pairs = [&](const std::vector<float> &v) {
+    const int K2 = K + (K & 1);
+    if (K2 == K) return v;
+    std::vector<float> out(v.size() / K * K2, 0.f);
+    for (size_t r = 0; r < v.size() / K; r++) std::copy(v.begin() + r * K, v.begin() + (r + 1) * K, out.begin() + r * K2);
+    return out;
+  };
   cudaError_t e = upload_vec(&d->d_row_f, row_f);
   if (e == cudaSuccess) e = upload_vec(&d->d_idx_f, idx_f);
-  if (e == cudaSuccess) e = upload_vec(&d->d_val_f, val_f);
+  if (e == cudaSuccess) e = upload_vec(&d->d_val_f, pad_pairs(val_f));
   if (e == cudaSuccess) e = upload_vec(&d->d_row_b, row_b);
   if (e == cudaSuccess) e = upload_vec(&d->d_idx_b, idx_b);
   if (e == cudaSuccess) e = upload_vec(&d->d_val_b, val_b);
   if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_run_row, run_row);
   if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_runs, runs);
-  if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_val_w, val_w);
+  if (e == cudaSuccess && d->win_R) e = upload_vec(&d->d_val_w, pad_pairs(val_w));
   if (e == cudaSuccess) e = cudaMalloc((void **)&d->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(d->d_err, 0, sizeof(unsigned));
   if (prev >= 0 && prev != device) cudaSetDevice(prev);
