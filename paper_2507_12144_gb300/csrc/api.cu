@@ -174,8 +174,6 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_err);
   cudaFree(p->d_tf_hi);
   cudaFree(p->d_tf_lo);
-  cudaFree(p->d_ti_hi);
-  cudaFree(p->d_ti_lo);
   cudaFree(p->d_seeds);
   cudaFree(p->d_coef);
   cudaFree(p->d_x2h);
@@ -667,8 +665,8 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
       e = launch_table_gen_f32(p->d_table, p->d_tab_off, p->Khp, d_x, d_s, d_a, d_b, d_seed, lmax, mmax, p->Kh, 0);
     if (e == cudaSuccess && tc) {
       // tensor-core plans: the Legendre table either as bf16 hi/lo tables
-      // streamed by TMA (forward [rows][Kp64], transposed
-      // [(2m + p) Kh + k'][Ip64]), or generated on chip from seeds every 32
+      // streamed by TMA (one layout [rows][Kp64] for both directions), or
+      // generated on chip from seeds every 32
       // rows of every (m, p) (FP64, stored as FP32), FP32 recurrence coefficients (zero past
       // lmax) and the latitudes as hi + lo
       const bool split = o.precision == SHT_PREC_SPLIT_BF16;
@@ -700,7 +698,7 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
         if (e == cudaSuccess) e = cudaMemset(p->d_tf_hi, 0, fbytes);
         if (e == cudaSuccess) e = cudaMemset(p->d_tf_lo, 0, fbytes);
         if (e == cudaSuccess)
-          e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, nullptr, nullptr, p->d_roff, Kp64, 64, d_x, d_s, d_a,
+          e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_roff, Kp64, d_x, d_s, d_a,
                                     d_b, d_seed, lmax, mmax, p->Kh, 0);
         p->table_bytes += (int64_t)fbytes * 2;
         if (e == cudaSuccess &&

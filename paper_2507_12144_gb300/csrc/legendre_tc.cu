@@ -1410,12 +1410,10 @@ __global__ void __launch_bounds__(256) rows_transpose_kernel(const __grid_consta
     finalize_tile(a, mt, lg, bt, T);
 }
 
-// FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64] and,
-// when ihi is given, transposed layout [(m, p, k')][Ip64]); same recurrence
-// as the FP32 table.
+// FP64 generation of the bf16 hi/lo table (layout [rows][Kp64], block (m, p)
+// from row roff[2m + p]); same recurrence as the FP32 table.
 __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bfloat16 *__restrict__ flo,
-                                      __nv_bfloat16 *__restrict__ ihi, __nv_bfloat16 *__restrict__ ilo,
-                                      const int *__restrict__ roff, int Kp64, int Ip64, const double *__restrict__ xk,
+                                      const int *__restrict__ roff, int Kp64, const double *__restrict__ xk,
                                       const double *__restrict__ sk, const double *__restrict__ a,
                                       const double *__restrict__ bcoef, const double *__restrict__ seed, int L, int M,
                                       int Kh) {
@@ -1430,11 +1428,6 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
     const int64_t fo = (int64_t)(roff[2 * m + p] + i) * Kp64 + k;
     fhi[fo] = h;
     flo[fo] = lo;
-    if (ihi) {
-      const int64_t io = ((int64_t)(m * 2 + p) * Kh + k) * Ip64 + i;
-      ihi[io] = h;
-      ilo[io] = lo;
-    }
   };
   double pmm = 0.28209479177387814347;  // 1 / sqrt(4 pi)
   for (int i = 1; i <= m; i++) pmm *= seed[i] * s;
@@ -1819,12 +1812,11 @@ bool tc_encode_lrows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ldx, in
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
-                                  const int *roff, int Kp64, int Ip64, const double *xk, const double *sk,
-                                  const double *a, const double *b, const double *seed, int L, int M, int Kh,
-                                  cudaStream_t st) {
+cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, const int *roff, int Kp64, const double *xk,
+                                  const double *sk, const double *a, const double *b, const double *seed, int L, int M,
+                                  int Kh, cudaStream_t st) {
   dim3 grid((Kh + 127) / 128, M);
-  table_gen_bf16_kernel<<<grid, 128, 0, st>>>(fhi, flo, ihi, ilo, roff, Kp64, Ip64, xk, sk, a, b, seed, L, M, Kh);
+  table_gen_bf16_kernel<<<grid, 128, 0, st>>>(fhi, flo, roff, Kp64, xk, sk, a, b, seed, L, M, Kh);
   return cudaGetLastError();
 }
 

@@ -83,8 +83,9 @@ struct TableF32 {
 };
 
 // Everything the tensor-core contractions of one plan need: TMA descriptors
-// of the bf16 hi/lo Legendre tables (forward layout [rows][Kp64] with block
-// (m, p) at row roff[2m+p]; transposed layout [(2m+p) Kh + k'][Ip64]), of the
+// of the bf16 hi/lo Legendre table (layout [rows][Kp64] with block (m, p)
+// at row roff[2m+p], read K-major by the forward and MN-major by the
+// inverse), of the
 // Fourier workspace F[(2m+p) Kh + k'][ldcb] (hi, lo) and of the internal
 // coefficient rows S[l M + m][ldcb] (hi, lo, l-major), plus the error word.
 struct TcPlanView {
@@ -145,12 +146,11 @@ bool tc_encode_lrows_f32(CUtensorMap *tm, const float *ptr, int ldr, int M, int 
 // l (the filter's epilogue).
 bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int M, int L, bool load,
                           int box_cols, int load_rows = 64);
-// FP64 generation of the bf16 hi/lo tables (forward layout [rows][Kp64],
-// transposed layout [(2m + p) Kh + k'][Ip64]; ihi / ilo NULL: forward only).
-cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, __nv_bfloat16 *ihi, __nv_bfloat16 *ilo,
-                                  const int *roff, int Kp64, int Ip64, const double *xk, const double *sk,
-                                  const double *a, const double *b, const double *seed, int L, int M, int Kh,
-                                  cudaStream_t st);
+// FP64 generation of the bf16 hi/lo table, layout [rows][Kp64] with block
+// (m, p) from row roff[2m + p].
+cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, const int *roff, int Kp64, const double *xk,
+                                  const double *sk, const double *a, const double *b, const double *seed, int L, int M,
+                                  int Kh, cudaStream_t st);
 // Seeds of the on-chip Legendre table (every 32 rows of every (m, p)),
 // computed in FP64 and stored as FP32 pairs.
 cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
@@ -404,7 +404,7 @@ struct sht_plan_s {
   // device memory (all owned)
   unsigned *d_err = nullptr;   // error word of bounded device waits
   shtgb::TcPlanView tc{};      // tensor-core view (bf16 precisions)
-  __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr, *d_ti_hi = nullptr, *d_ti_lo = nullptr;  // bf16 tables
+  __nv_bfloat16 *d_tf_hi = nullptr, *d_tf_lo = nullptr;  // bf16 table (one layout for both directions)
   int table_source = 0;        // 0: streamed bf16 table, 1: on-chip recurrence, 2: forward streamed, inverse on chip
   void *d_seeds = nullptr;     // recurrence seeds of the on-chip table
   float4 *d_coef = nullptr;    // two-step recurrence coefficients [(2m + p) ldC + i]
