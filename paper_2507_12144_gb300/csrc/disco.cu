@@ -86,14 +86,27 @@ __global__ void __launch_bounds__(kDiscoThreads)
     for (int k = 0; k < K; k++) acc[j][k] = 0.f;
   const int sw = s * w;
   const int64_t plane = (int64_t)Hi * Wi;
-  for (int e = row[h]; e < row[h + 1]; e++) {
-    const int2 hw = __ldg(idx + e);
+  const int eb = row[h], ee = row[h + 1];
+  // entry e + 1's inputs and entry e + 2's index load during entry e's FMAs
+  auto xload = [&](int2 hw, float (&xv)[CB]) {
     int col = hw.y + sw;
     if (col >= Wi) col -= Wi;
     const float *xp = x + c0 * plane + (int64_t)hw.x * Wi + col;
-    float xv[CB];
 #pragma unroll
     for (int j = 0; j < CB; j++) xv[j] = c0 + j < C ? __ldg(xp + j * plane) : 0.f;
+  };
+  float xn[CB];
+  int2 hw2 = make_int2(0, 0);
+  if (eb < ee) xload(__ldg(idx + eb), xn);
+  if (eb + 1 < ee) hw2 = __ldg(idx + eb + 1);
+  for (int e = eb; e < ee; e++) {
+    float xv[CB];
+#pragma unroll
+    for (int j = 0; j < CB; j++) xv[j] = xn[j];
+    if (e + 1 < ee) {
+      xload(hw2, xn);
+      if (e + 2 < ee) hw2 = __ldg(idx + e + 2);
+    }
     const float *vp = val + (int64_t)e * (2 * kpairs<K>());
 #pragma unroll
     for (int k = 0; k < K; k++) {
