@@ -49,11 +49,12 @@ def test_diffusion_step_with_given_normals_matches_oracle(B, L, M, kT):
     assert np.array_equal(got[~tri], z64.astype(np.complex64)[~tri])
 
 
-def test_gpu_generator_matches_the_published_philox():
+@pytest.mark.parametrize("B,L,M", [(3, 64, 60), (2, 50, 49), (2, 33, 33)])
+def test_gpu_generator_matches_the_published_philox(B, L, M):
     """One step from zero with kT = 0 gives z = sigma xi: recover the normals
     and compare them with the oracle's generator at the same (seed, step,
-    index)."""
-    B, L, M = 3, 64, 60
+    index).  Even mmax runs one thread per pair of orders, odd mmax one per
+    coefficient (the pairs of flat indices then straddle rows)."""
     seed, step = 0x1234ABCD9876, 7
     z = torch.zeros((B, L, M), dtype=torch.complex64, device="cuda")
     _sht().diffusion_step(z, [0.0], 1.0, 1.0, seed=seed, step=step)
