@@ -194,6 +194,8 @@ void free_plan(sht_plan_s *p) {
   cudaFree(p->d_zonal_c);
   cudaFree(p->d_fwd_tiles);
   cudaFree(p->d_inv_tiles);
+  cudaFree(p->d_fwd_krange);
+  cudaFree(p->d_inv_krange);
   cudaFree(p->d_work);
   cudaFree(p->d_spec_a);
   cudaFree(p->d_spec_b);
@@ -297,6 +299,7 @@ sht_status_t analysis(sht_plan_s *p, const float *x, float2 *xhat, int64_t B, cu
         TcLegItem it{};
         it.T = rows_out && rows_out->T ? rows_out->T : &p->tc;
         it.tiles = p->d_fwd_tiles;
+        it.krange = p->d_fwd_krange;
         it.ntiles = p->n_fwd_tiles;
         it.B = nb;
         if (rows_out) {
@@ -344,7 +347,7 @@ cudaError_t c2r_any(sht_plan_s *p, float *y, int nb, bool adjoint, cudaStream_t 
 // already in the tensor-core internal rows (bf16 hi/lo).
 sht_status_t synthesis_rows(sht_plan_s *p, float *y, int nb, cudaStream_t st, bool adjoint) {
   cudaError_t e = traced(p, SHT_KERNEL_LEG_INV, st, [&] {
-    return launch_leg_inv_tc(p->tc, p->d_inv_tiles, p->n_inv_tiles, p->d_work, p->ldc, nb, st);
+    return launch_leg_inv_tc(p->tc, p->d_inv_tiles, p->d_inv_krange, p->n_inv_tiles, p->d_work, p->ldc, nb, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "inverse Legendre launch");
   e = traced(p, SHT_KERNEL_C2R, st, [&] { return c2r_any(p, y, nb, adjoint, st); });
@@ -701,6 +704,16 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
           e = launch_table_gen_bf16(p->d_tf_hi, p->d_tf_lo, p->d_roff, Kp64, d_x, d_s, d_a,
                                     d_b, d_seed, lmax, mmax, p->Kh, 0);
         p->table_bytes += (int64_t)fbytes * 2;
+        // the K chunks of each tile that hold non-negligible table entries
+        // (polar latitudes of high orders hold none)
+        if (e == cudaSuccess) e = dev_alloc((void **)&p->d_fwd_krange, sizeof(int2) * (size_t)p->n_fwd_tiles);
+        if (e == cudaSuccess)
+          e = launch_tile_krange(p->d_tf_hi, Kp64, p->d_roff, p->d_fwd_tiles, p->n_fwd_tiles, 0, lmax, p->Kh,
+                                 p->d_fwd_krange, 0);
+        if (e == cudaSuccess && !gen_inv) e = dev_alloc((void **)&p->d_inv_krange, sizeof(int2) * (size_t)p->n_inv_tiles);
+        if (e == cudaSuccess && !gen_inv)
+          e = launch_tile_krange(p->d_tf_hi, Kp64, p->d_roff, p->d_inv_tiles, p->n_inv_tiles, 1, lmax, p->Kh,
+                                 p->d_inv_krange, 0);
         if (e == cudaSuccess &&
             // maps Kh columns wide (row pitch Kp64): the boxes' columns past
             // Kh read zeros without memory traffic

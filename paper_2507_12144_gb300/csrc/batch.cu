@@ -184,6 +184,7 @@ cudaError_t stage_legendre(sht_batch_s *b, const Shape &sh, cudaStream_t st) {
       q = TcLegItem{};
       q.T = &p->tc;
       q.tiles = inverse ? p->d_inv_tiles : p->d_fwd_tiles;
+      q.krange = inverse ? p->d_inv_krange : p->d_fwd_krange;
       q.ntiles = inverse ? p->n_inv_tiles : p->n_fwd_tiles;
       q.B = (int)b->items[i].count;
       q.Nt = column_tile(q.B, sh.nt_cap);

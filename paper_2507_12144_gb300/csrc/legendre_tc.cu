@@ -120,7 +120,9 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 // kFwd / kInv streams from a precomputed bf16 table by TMA (kGen = false;
 // the table generated on chip is tc_gen_kernel's); the filter's real-form
 // weights WR are built on chip by 8 extra warps from the complex W (kFilt
-// with kGen = true).
+// with kGen = true).  With the streamed table a tile runs only the K chunks
+// [kc0, kc0 + nk) that hold non-negligible table entries (tile_krange_kernel:
+// near the poles the high orders' Phat are zero to working precision).
 // ---------------------------------------------------------------------------
 enum Mode { kFwd = 0, kInv = 1, kFilt = 2 };
 
@@ -173,6 +175,7 @@ struct SegArgs {
   const float *x2h, *x2l;
   int NB, ldC;
   const int *roff;        // first forward-table row of block (m, p) at [2m + p]
+  const int2 *krange;     // streamed table: K chunks [x, y) of each row tile (nullptr: all)
 };
 
 // TMA maps of one problem: A (table hi/lo, or filter data), B (data, or
@@ -217,6 +220,7 @@ __host__ __device__ inline uint32_t stage_bytes(int mode, bool split, int Nt) {
 struct TileInfo {
   int s, Nt;             // problem, its column tile width
   int nk;                // K chunks
+  int kc0;               // first K chunk (the ones before hold only negligible table entries)
   int a_col0, a_row;     // A: K column of chunk 0, row
   int b_col0, b_row0;    // B: for MN-major (col of box 0, K row of chunk 0); for K-major (K col 0, row)
   // epilogue selectors
@@ -286,6 +290,11 @@ __device__ __forceinline__ TileInfo tile_decode(const TcParams &P, const RawTile
       ti.a_row = g.roff ? __ldg(g.roff + 2 * ti.m + ti.p) : 0;
       ti.a_col0 = ti.r0;
       ti.b_row0 = r.d.w;  // first degree m + p of the (m, p) block
+    }
+    if (g.krange) {
+      const int2 kr = __ldg(g.krange + r.local / g.nct);
+      ti.kc0 = kr.x;
+      ti.nk = kr.y - kr.x;
     }
   }
   return ti;
@@ -362,6 +371,7 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
   const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
+  kc += ti.kc0;  // the tile's K chunks start at kc0 (zero for the filter)
   if (kMode == kInv) {
     // the forward table's rows i = 64 kc .. 64 kc + 63 of the block, k'
     // columns r0 .. r0 + 127 as two 64-column boxes (rows past the block
@@ -1445,6 +1455,74 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
   }
 }
 
+// K-chunk ranges of the streamed-table tiles.  Phat_lm(cos theta) is
+// evanescent for sin(theta) < m / (l + 1/2): it decays exponentially towards
+// the poles, so for large m the table entries at polar latitudes are zero to
+// working precision (the "polar optimisation" of Schaeffer, Efficient
+// spherical harmonic transforms aimed at pseudospectral numerical
+// simulations, G-cubed 2013).  A forward tile (128 rows i of one (m, p)
+// block) runs only the 64-latitude chunks that hold an entry of magnitude
+// >= 2^-40, an inverse tile (128 latitudes) only the 64-row chunks that do;
+// the chunks left out hold no such entry.  The orthonormal Phat is of order
+// one where it oscillates, so a coefficient loses at most 2^-40 times the
+// sum of |data| over the skipped K range: far below the split form's
+// rounding (2^-17 per product).  One block per tile; the range is
+// [first, last + 1) of the chunks with such an entry, or only the tile's
+// last chunk when none has one (sums that are zero to working precision).
+constexpr int kMaxKrange = 64;
+constexpr float kNegligible = 9.094947017729282e-13f;  // 2^-40
+
+__global__ void tile_krange_kernel(const __nv_bfloat16 *__restrict__ thi, int Kp64, const int *__restrict__ roff,
+                                   const LegTile *__restrict__ tiles, int inverse, int L, int Kh,
+                                   int2 *__restrict__ out) {
+  __shared__ int live[kMaxKrange];
+  const LegTile t = tiles[blockIdx.x];
+  const int nrows = leg_rows(L, t.m, t.p);
+  int r_lo, r_hi, c_lo, c_hi, nk;
+  if (!inverse) {
+    // rows of the tile (the rows past its block are discarded), all latitudes
+    r_lo = t.row;
+    r_hi = t.row + min(128, nrows - t.r0);
+    c_lo = 0;
+    c_hi = Kh;
+    nk = (Kh + kKc - 1) / kKc;
+  } else {
+    // every row of the block, the tile's latitudes
+    r_lo = roff[2 * t.m + t.p];
+    r_hi = r_lo + nrows;
+    c_lo = t.r0;
+    c_hi = min(t.r0 + 128, Kh);
+    nk = (nrows + kKc - 1) / kKc;
+  }
+  if (nk > kMaxKrange) {
+    if (threadIdx.x == 0) out[blockIdx.x] = make_int2(0, nk);
+    return;
+  }
+  for (int i = threadIdx.x; i < kMaxKrange; i += blockDim.x) live[i] = 0;
+  __syncthreads();
+  const int w = c_hi - c_lo;
+  const int64_t n = (int64_t)max(r_hi - r_lo, 0) * max(w, 0);
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int r = (int)(e / w), c = c_lo + (int)(e - (int64_t)r * w);
+    const float v = fabsf(__bfloat162float(thi[(int64_t)(r_lo + r) * Kp64 + c]));
+    if (v >= kNegligible) live[inverse ? r / kKc : c / kKc] = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int k0 = 0, k1 = 0;
+    for (int k = 0; k < nk; k++)
+      if (live[k]) {
+        if (k1 == 0) k0 = k;
+        k1 = k + 1;
+      }
+    if (k1 == 0 && nk > 0) {
+      k0 = nk - 1;
+      k1 = nk;
+    }
+    out[blockIdx.x] = make_int2(k0, k1);
+  }
+}
+
 // FP64 recurrence seeds (one thread per (m, k')): at the first row l0 of
 // every 32-row block of both parities, Phat_{l0} and Phat_{l0+2} rounded to
 // FP32 (zero below the FP32 normal range).
@@ -1820,6 +1898,13 @@ cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, const 
   return cudaGetLastError();
 }
 
+cudaError_t launch_tile_krange(const __nv_bfloat16 *thi, int Kp64, const int *roff, const LegTile *tiles, int ntiles,
+                               int inverse, int L, int Kh, int2 *out, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  tile_krange_kernel<<<ntiles, 256, 0, st>>>(thi, Kp64, roff, tiles, inverse, L, Kh, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
                             const double *b, const double *seedf, int L, int M, int Kh, cudaStream_t st) {
   dim3 grid((Kh + 127) / 128, M);
@@ -1868,6 +1953,7 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
       g.NB = T.NB;
       g.ldC = T.ldC;
       g.roff = T.roff;
+      g.krange = gen ? nullptr : it.krange;
       SegMaps &mp = P.maps[nseg];
       if (!inverse) {
         mp.a_hi = T.tab_fwd_hi;
@@ -1912,11 +1998,12 @@ cudaError_t launch_leg_tc_group(int inverse, const TcLegItem *items, int n, cons
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
-                              cudaStream_t st) {
+cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, const int2 *krange, int ntiles, float *Gw,
+                              int ldc, int B, cudaStream_t st) {
   TcLegItem it{};
   it.T = &T;
   it.tiles = tiles;
+  it.krange = krange;
   it.ntiles = ntiles;
   it.B = B;
   it.Gw = Gw;

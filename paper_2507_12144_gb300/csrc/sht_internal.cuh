@@ -151,6 +151,13 @@ bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, const int *roff, int Kp64, const double *xk,
                                   const double *sk, const double *a, const double *b, const double *seed, int L, int M,
                                   int Kh, cudaStream_t st);
+// K-chunk ranges of the streamed-table contractions, one int2 [first, end)
+// per tile (inverse = 0: forward tiles, chunks of 64 latitudes; 1: inverse
+// tiles, chunks of 64 rows i): the chunks holding a table entry of
+// magnitude >= 2^-40 (from the hi table at rows roff[2m + p] + i, pitch
+// Kp64); at least one chunk per tile with rows.
+cudaError_t launch_tile_krange(const __nv_bfloat16 *thi, int Kp64, const int *roff, const LegTile *tiles, int ntiles,
+                               int inverse, int L, int Kh, int2 *out, cudaStream_t st);
 // Seeds of the on-chip Legendre table (every 32 rows of every (m, p)),
 // computed in FP64 and stored as FP32 pairs.
 cudaError_t launch_seed_gen(void *seeds, int NB, const double *xk, const double *sk, const double *a,
@@ -167,7 +174,8 @@ cudaError_t launch_filter_tc(const TcPlanView &T, const void *ftiles, int nftile
                              int lds, int kx, int nwr, int Bm, int Cin, int Cout, int wadj, cudaStream_t st);
 // Inverse contraction on the tensor cores from the bf16 internal rows to the
 // FP32 folded workspace Gw[(2m+p) Kh + k'][ldc].
-cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, int ntiles, float *Gw, int ldc, int B,
+cudaError_t launch_leg_inv_tc(const TcPlanView &T, const LegTile *tiles, const int2 *krange, int ntiles, float *Gw,
+                              int ldc, int B,
                               cudaStream_t st);
 // One problem of a grouped tensor-core Legendre launch: a plan's view, its
 // tiles, its batch, and the destination of the forward (the plan's l-major
@@ -179,6 +187,9 @@ struct TcLegItem {
   const TcPlanView *T;
   const LegTile *tiles;
   int ntiles;
+  // per tile of `tiles`: the K chunks [x, y) whose streamed-table entries
+  // are not all negligible (launch_tile_krange); nullptr: every chunk
+  const int2 *krange;
   int B, Nt;
   __nv_bfloat16 *rows_hi, *rows_lo;
   int ldo, cin, kx;
@@ -436,6 +447,8 @@ struct sht_plan_s {
   int n_fwd_tiles = 0;
   shtgb::LegTile *d_inv_tiles = nullptr;
   int n_inv_tiles = 0;
+  int2 *d_fwd_krange = nullptr;  // K-chunk ranges of the tiles (streamed bf16 table only)
+  int2 *d_inv_krange = nullptr;
   std::vector<int> fwd_tile_m, inv_tile_m;  // first tile of each order m (M + 1 entries)
   float *d_work = nullptr;    // folded Fourier workspace [M][2][Kh][ldc]
   float2 *d_spec_a = nullptr;  // [max_batch][L][M] spectral buffer
