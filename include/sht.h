@@ -111,10 +111,11 @@ typedef enum {
  * for the tensor-core precisions; FP32 plans always stream an FP32 table.
  * STREAMED: bf16 hi/lo tables built once in FP64 at plan time and read by
  *   TMA on every call (table bytes re-read per call, no recurrence work).
- *   A streamed contraction reads and multiplies only the 64-wide chunks of
- *   the table that hold an entry of magnitude >= 2^-40: near the poles the
- *   high orders' Phat are zero to working precision, and what is left out
- *   changes a coefficient by at most 2^-40 times the sum of |data| over it.
+ *   A streamed contraction skips, per tile, the leading latitudes (forward)
+ *   or degrees (inverse) whose table entries are all below 2^-40 in
+ *   magnitude: near the poles the high orders' Phat are zero to working
+ *   precision, and what is left out changes a coefficient by at most 2^-40
+ *   times the sum of |data| over it.
  * RECURRENCE: only seeds every 32 degrees are stored (FP64-computed, kept
  *   as FP32 pairs); extra warps of the Legendre kernels run the three-term
  *   recurrence in FP32 on chip (about 1/16 of the table bytes, more

@@ -107,7 +107,8 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 
 // ---------------------------------------------------------------------------
 // Persistent tensor-core kernel for the three contractions.  One CTA per SM
-// walks its tiles (tile = blockIdx.x + i gridDim.x).  A ring of `stages`
+// walks its tiles (round i: tile i gridDim.x + blockIdx.x, or + gridDim.x
+// - 1 - blockIdx.x on odd rounds).  A ring of `stages`
 // shared-memory stages carries TMA loads to the MMA thread continuously
 // across tiles; the accumulator is double-buffered in tensor memory so that
 // the epilogue warps drain tile i while the MMAs of tile i + 1 run.
@@ -120,9 +121,10 @@ __device__ __forceinline__ void put_bf16x8(__nv_bfloat16 *hi, __nv_bfloat16 *lo,
 // kFwd / kInv streams from a precomputed bf16 table by TMA (kGen = false;
 // the table generated on chip is tc_gen_kernel's); the filter's real-form
 // weights WR are built on chip by 8 extra warps from the complex W (kFilt
-// with kGen = true).  With the streamed table a tile runs only the K chunks
-// [kc0, kc0 + nk) that hold non-negligible table entries (tile_krange_kernel:
-// near the poles the high orders' Phat are zero to working precision).
+// with kGen = true).  With the streamed table a tile runs only the nk
+// chunks from K row k0 that cover its non-negligible table entries
+// (tile_krange_kernel: near the poles the high orders' Phat are zero to
+// working precision).
 // ---------------------------------------------------------------------------
 enum Mode { kFwd = 0, kInv = 1, kFilt = 2 };
 
@@ -175,7 +177,7 @@ struct SegArgs {
   const float *x2h, *x2l;
   int NB, ldC;
   const int *roff;        // first forward-table row of block (m, p) at [2m + p]
-  const int2 *krange;     // streamed table: K chunks [x, y) of each row tile (nullptr: all)
+  const int2 *krange;     // streamed table: K rows [x, y) of each row tile (nullptr: all)
 };
 
 // TMA maps of one problem: A (table hi/lo, or filter data), B (data, or
@@ -220,7 +222,7 @@ __host__ __device__ inline uint32_t stage_bytes(int mode, bool split, int Nt) {
 struct TileInfo {
   int s, Nt;             // problem, its column tile width
   int nk;                // K chunks
-  int kc0;               // first K chunk (the ones before hold only negligible table entries)
+  int k0;                // first K row of chunk 0 (the rows before meet only negligible table entries)
   int a_col0, a_row;     // A: K column of chunk 0, row
   int b_col0, b_row0;    // B: for MN-major (col of box 0, K row of chunk 0); for K-major (K col 0, row)
   // epilogue selectors
@@ -293,24 +295,30 @@ __device__ __forceinline__ TileInfo tile_decode(const TcParams &P, const RawTile
     }
     if (g.krange) {
       const int2 kr = __ldg(g.krange + r.local / g.nct);
-      ti.kc0 = kr.x;
-      ti.nk = kr.y - kr.x;
+      ti.k0 = kr.x;
+      ti.nk = (kr.y - kr.x + kKc - 1) / kKc;
     }
   }
   return ti;
 }
 
-// Tiles of this CTA in order, the next one fetched a tile ahead.
+// Tiles of this CTA in order, the next one fetched a tile ahead.  Round w
+// of the walk covers tiles w G .. w G + G - 1 (G CTAs), in reverse CTA order
+// on odd rounds: tile costs fall along the list (higher orders have fewer
+// rows and K chunks), and the alternation evens out each CTA's total.
 template <int kMode>
 struct TileWalk {
-  int t;
+  int w, t;
   RawTile nxt;
-  __device__ __forceinline__ TileWalk(const TcParams &P) : t(blockIdx.x) { nxt = tile_fetch<kMode>(P, t); }
+  __device__ __forceinline__ static int tile_of(int w) {
+    return w * (int)gridDim.x + ((w & 1) ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x);
+  }
+  __device__ __forceinline__ TileWalk(const TcParams &P) : w(0), t(blockIdx.x) { nxt = tile_fetch<kMode>(P, t); }
   __device__ __forceinline__ bool more(const TcParams &P) const { return t < P.ntiles; }
   // the current tile's info; requests the one after it
   __device__ __forceinline__ TileInfo take(const TcParams &P) {
     const TileInfo ti = tile_decode<kMode>(P, nxt);
-    t += gridDim.x;
+    t = tile_of(++w);
     nxt = tile_fetch<kMode>(P, t);
     return ti;
   }
@@ -371,38 +379,38 @@ __device__ __forceinline__ void load_chunk(unsigned char *st, const TileInfo &ti
   const uint32_t bb = b_bytes_of(kMode, Nmax);
   unsigned char *a_hi = st, *a_lo = st + kABytes;
   unsigned char *b_hi = st + na * kABytes, *b_lo = b_hi + bb;
-  kc += ti.kc0;  // the tile's K chunks start at kc0 (zero for the filter)
+  const int kb = ti.k0 + kc * kKc;  // first K row of the chunk (k0: zero for the filter)
   if (kMode == kInv) {
-    // the forward table's rows i = 64 kc .. 64 kc + 63 of the block, k'
+    // the forward table's rows i = kb .. kb + 63 of the block, k'
     // columns r0 .. r0 + 127 as two 64-column boxes (rows past the block
     // belong to the next block and meet degrees past lmax: zero data)
     for (int j = 0; j < 2; j++) {
-      tma_load_2d(a_hi + j * 8192, &mp.a_hi, bar, ti.a_col0 + 64 * j, ti.a_row + kc * kKc);
-      tma_load_2d(a_lo + j * 8192, &mp.a_lo, bar, ti.a_col0 + 64 * j, ti.a_row + kc * kKc);
+      tma_load_2d(a_hi + j * 8192, &mp.a_hi, bar, ti.a_col0 + 64 * j, ti.a_row + kb);
+      tma_load_2d(a_lo + j * 8192, &mp.a_lo, bar, ti.a_col0 + 64 * j, ti.a_row + kb);
     }
   } else {
-    tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kc * kKc, ti.a_row);
-    if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kc * kKc, ti.a_row);
+    tma_load_2d(a_hi, &mp.a_hi, bar, ti.a_col0 + kb, ti.a_row);
+    if (na == 2) tma_load_2d(a_lo, &mp.a_lo, bar, ti.a_col0 + kb, ti.a_row);
   }
   if (kMode == kFilt) {
     if (!kGen) {
-      tma_load_2d(b_hi, &mp.b_hi, bar, kc * kKc, ti.b_row0);
-      tma_load_2d(b_lo, &mp.b_lo, bar, kc * kKc, ti.b_row0);
+      tma_load_2d(b_hi, &mp.b_hi, bar, kb, ti.b_row0);
+      tma_load_2d(b_lo, &mp.b_lo, bar, kb, ti.b_row0);
     }
   } else if (kMode == kFwd) {
     // the folded data as (column, 2m + p, k'): 64 rows k' of one (m, p)
     const int nbox = (ti.Nt + 63) / 64;
     for (int j = 0; j < nbox; j++) {
-      tma_load_3d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.b_row0, kc * kKc);
-      if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0, kc * kKc);
+      tma_load_3d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.b_row0, kb);
+      if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.b_row0, kb);
     }
   } else {
     // the internal rows as (column, m, l) with every second l: 64 rows
     // l = m + p + 2 i of one (m, p) block per box
     const int nbox = (ti.Nt + 63) / 64;
     for (int j = 0; j < nbox; j++) {
-      tma_load_3d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * kc * kKc);
-      if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * kc * kKc);
+      tma_load_3d(b_hi + j * 8192, &mp.b_hi, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * kb);
+      if (kSplit) tma_load_3d(b_lo + j * 8192, &mp.b_lo, bar, ti.b_col0 + 64 * j, ti.m, ti.b_row0 + 2 * kb);
     }
   }
 }
@@ -1455,71 +1463,74 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
   }
 }
 
-// K-chunk ranges of the streamed-table tiles.  Phat_lm(cos theta) is
-// evanescent for sin(theta) < m / (l + 1/2): it decays exponentially towards
-// the poles, so for large m the table entries at polar latitudes are zero to
+// K ranges of the streamed-table tiles.  Phat_lm(cos theta) is evanescent
+// for sin(theta) < m / (l + 1/2): it decays exponentially towards the
+// poles, so for large m the table entries at polar latitudes are zero to
 // working precision (the "polar optimisation" of Schaeffer, Efficient
 // spherical harmonic transforms aimed at pseudospectral numerical
 // simulations, G-cubed 2013).  A forward tile (128 rows i of one (m, p)
-// block) runs only the 64-latitude chunks that hold an entry of magnitude
-// >= 2^-40, an inverse tile (128 latitudes) only the 64-row chunks that do;
-// the chunks left out hold no such entry.  The orthonormal Phat is of order
-// one where it oscillates, so a coefficient loses at most 2^-40 times the
-// sum of |data| over the skipped K range: far below the split form's
-// rounding (2^-17 per product).  One block per tile; the range is
-// [first, last + 1) of the chunks with such an entry, or only the tile's
-// last chunk when none has one (sums that are zero to working precision).
-constexpr int kMaxKrange = 64;
+// block, K = latitudes k') starts its 64-wide K chunks at the first
+// latitude with a table entry of magnitude >= 2^-40, rounded down to a
+// multiple of 8 (TMA boxes start on 16-byte boundaries along k'); an
+// inverse tile (128 latitudes, K = rows i) at the first such row, rounded
+// the same way.  Near the equator every order oscillates, so the live range
+// runs to the end of K.  The orthonormal Phat is of order one where it
+// oscillates, so a coefficient loses at most 2^-40 times the sum of |data|
+// over the rows left out: far below the split form's rounding (2^-17 per
+// product).  The last chunk may reach past K, where the loads read zeros.
+// One block per tile; out = [first, end) of the live K rows, or the last
+// 8-row group of K when none is live (sums that are zero to working
+// precision), or (0, 0) for a block without rows.
 constexpr float kNegligible = 9.094947017729282e-13f;  // 2^-40
 
 __global__ void tile_krange_kernel(const __nv_bfloat16 *__restrict__ thi, int Kp64, const int *__restrict__ roff,
                                    const LegTile *__restrict__ tiles, int inverse, int L, int Kh,
                                    int2 *__restrict__ out) {
-  __shared__ int live[kMaxKrange];
+  __shared__ int first, last;
   const LegTile t = tiles[blockIdx.x];
   const int nrows = leg_rows(L, t.m, t.p);
-  int r_lo, r_hi, c_lo, c_hi, nk;
+  int r_lo, r_hi, c_lo, c_hi, nK;
   if (!inverse) {
     // rows of the tile (the rows past its block are discarded), all latitudes
     r_lo = t.row;
     r_hi = t.row + min(128, nrows - t.r0);
     c_lo = 0;
     c_hi = Kh;
-    nk = (Kh + kKc - 1) / kKc;
+    nK = Kh;
   } else {
     // every row of the block, the tile's latitudes
     r_lo = roff[2 * t.m + t.p];
     r_hi = r_lo + nrows;
     c_lo = t.r0;
     c_hi = min(t.r0 + 128, Kh);
-    nk = (nrows + kKc - 1) / kKc;
+    nK = nrows;
   }
-  if (nk > kMaxKrange) {
-    if (threadIdx.x == 0) out[blockIdx.x] = make_int2(0, nk);
-    return;
+  if (threadIdx.x == 0) {
+    first = 0x7fffffff;
+    last = -1;
   }
-  for (int i = threadIdx.x; i < kMaxKrange; i += blockDim.x) live[i] = 0;
   __syncthreads();
   const int w = c_hi - c_lo;
   const int64_t n = (int64_t)max(r_hi - r_lo, 0) * max(w, 0);
+  int f = 0x7fffffff, l = -1;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     const int r = (int)(e / w), c = c_lo + (int)(e - (int64_t)r * w);
     const float v = fabsf(__bfloat162float(thi[(int64_t)(r_lo + r) * Kp64 + c]));
-    if (v >= kNegligible) live[inverse ? r / kKc : c / kKc] = 1;
+    if (v >= kNegligible) {
+      const int k = inverse ? r : c;  // the K index of the entry
+      f = min(f, k);
+      l = max(l, k);
+    }
   }
+  if (f != 0x7fffffff) atomicMin(&first, f);
+  if (l >= 0) atomicMax(&last, l);
   __syncthreads();
   if (threadIdx.x == 0) {
-    int k0 = 0, k1 = 0;
-    for (int k = 0; k < nk; k++)
-      if (live[k]) {
-        if (k1 == 0) k0 = k;
-        k1 = k + 1;
-      }
-    if (k1 == 0 && nk > 0) {
-      k0 = nk - 1;
-      k1 = nk;
+    int2 kr = make_int2(0, 0);
+    if (nK > 0) {
+      kr = last >= 0 ? make_int2(first / 8 * 8, last + 1) : make_int2((nK - 1) / 8 * 8, nK);
     }
-    out[blockIdx.x] = make_int2(k0, k1);
+    out[blockIdx.x] = kr;
   }
 }
 

@@ -151,11 +151,11 @@ bool tc_encode_srows_bf16(CUtensorMap *tm, const __nv_bfloat16 *ptr, int ld, int
 cudaError_t launch_table_gen_bf16(__nv_bfloat16 *fhi, __nv_bfloat16 *flo, const int *roff, int Kp64, const double *xk,
                                   const double *sk, const double *a, const double *b, const double *seed, int L, int M,
                                   int Kh, cudaStream_t st);
-// K-chunk ranges of the streamed-table contractions, one int2 [first, end)
-// per tile (inverse = 0: forward tiles, chunks of 64 latitudes; 1: inverse
-// tiles, chunks of 64 rows i): the chunks holding a table entry of
-// magnitude >= 2^-40 (from the hi table at rows roff[2m + p] + i, pitch
-// Kp64); at least one chunk per tile with rows.
+// K ranges of the streamed-table contractions, one int2 [first, end) per
+// tile (inverse = 0: forward tiles, K = latitudes; 1: inverse tiles, K =
+// rows i): from the first K row with a table entry of magnitude >= 2^-40
+// (rounded down to a multiple of 8) to the end of K, read from the hi
+// table at rows roff[2m + p] + i, pitch Kp64; (0, 0) for a block without rows.
 cudaError_t launch_tile_krange(const __nv_bfloat16 *thi, int Kp64, const int *roff, const LegTile *tiles, int ntiles,
                                int inverse, int L, int Kh, int2 *out, cudaStream_t st);
 // Seeds of the on-chip Legendre table (every 32 rows of every (m, p)),
@@ -187,8 +187,8 @@ struct TcLegItem {
   const TcPlanView *T;
   const LegTile *tiles;
   int ntiles;
-  // per tile of `tiles`: the K chunks [x, y) whose streamed-table entries
-  // are not all negligible (launch_tile_krange); nullptr: every chunk
+  // per tile of `tiles`: the K rows [x, y) that meet non-negligible
+  // streamed-table entries (launch_tile_krange); nullptr: all of K
   const int2 *krange;
   int B, Nt;
   __nv_bfloat16 *rows_hi, *rows_lo;
