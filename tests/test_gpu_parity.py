@@ -323,6 +323,33 @@ def test_split_bf16_chain_per_field_at_one_operation_tolerance(shtgb):
     assert per_field_spatial_err(y, ref_y).max() <= TOL["split_bf16"]
 
 
+# Single harmonics of high order: the streamed-table contractions leave out
+# the polar latitudes (forward) and degree rows (inverse) where the table is
+# below 2^-40, which fields with l^-3 spectra barely exercise (their high
+# orders carry little of a field's norm).  A field made of one (l, m) puts
+# all its norm where the skip acts, so a row left out that mattered would
+# show at full size in its relative error.
+HIGH_ORDERS = [(359, 359), (359, 330), (340, 300), (300, 250), (359, 200), (200, 199), (359, 100), (120, 60),
+               (358, 357), (250, 2)]
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_single_high_order_harmonics_361x720(shtgb, prec):
+    nlat, nlon, grid, L = 361, 720, "equiangular_cc", 360
+    c = np.zeros((len(HIGH_ORDERS), L, L), np.complex128)
+    for i, (l, m) in enumerate(HIGH_ORDERS):
+        c[i, l, m] = 1.0 + (1.0j if m > 0 else 0.0)
+    u = oracle.sht_inverse(c, nlat, nlon, grid, L, L)
+    fields = u.astype(np.float32)
+    ref_f = oracle.sht_forward(fields.astype(np.float64), nlat, nlon, grid, L, L)
+    plan = _plan(shtgb, nlat, nlon, grid, L, L, precision=prec)
+    out = shtgb.sht_forward(plan, _to_gpu(fields, torch.float32)).cpu().numpy()
+    inv = shtgb.sht_inverse(plan, _to_gpu(c.astype(np.complex64), torch.complex64)).cpu().numpy()
+    plan.check()
+    assert per_field_spec_err(out, ref_f).max() <= TOL[prec]
+    assert per_field_spatial_err(inv, u).max() <= TOL[prec]
+
+
 def test_round_trip_and_ylm_deltas_gauss_33x64(shtgb):
     """33 x 64 Gaussian grid, lmax = mmax = 32, batch 4, (l+1)^-1.5 spectra."""
     nlat, nlon, L = 33, 64, 32
