@@ -710,7 +710,8 @@ sht_status_t sht_plan(sht_plan_t *out, int nlat, int nlon, int grid, int lmax, i
         if (e == cudaSuccess)
           e = launch_tile_krange(p->d_tf_hi, Kp64, p->d_roff, p->d_fwd_tiles, p->n_fwd_tiles, 0, lmax, p->Kh,
                                  p->d_fwd_krange, 0);
-        if (e == cudaSuccess && !gen_inv) e = dev_alloc((void **)&p->d_inv_krange, sizeof(int2) * (size_t)p->n_inv_tiles);
+        if (e == cudaSuccess && !gen_inv)
+          e = dev_alloc((void **)&p->d_inv_krange, sizeof(int2) * (size_t)p->n_inv_tiles);
         if (e == cudaSuccess && !gen_inv)
           e = launch_tile_krange(p->d_tf_hi, Kp64, p->d_roff, p->d_inv_tiles, p->n_inv_tiles, 1, lmax, p->Kh,
                                  p->d_inv_krange, 0);
