@@ -1477,7 +1477,7 @@ __global__ void table_gen_bf16_kernel(__nv_bfloat16 *__restrict__ fhi, __nv_bflo
 // runs to the end of K.  The orthonormal Phat is of order one where it
 // oscillates, so a coefficient loses at most 2^-40 times the sum of |data|
 // over the rows left out: far below the split form's rounding (2^-17 per
-// product).  The last chunk may reach past K, where the loads read zeros.
+// product).  A last chunk past K meets zeros (the data past K reads zero).
 // One block per tile; out = [first, end) of the live K rows, or the last
 // 8-row group of K when none is live (sums that are zero to working
 // precision), or (0, 0) for a block without rows.
